@@ -1,0 +1,61 @@
+"""Input-frame entry points of the oracle.
+
+The library takes lattice vectors e1, e2 in any orientation, points anywhere
+in the plane (wrapped into the cell), and returns potentials, gradients and
+velocities in the input frame.  These helpers do the same for the oracle:
+canonicalise (``lattice``), evaluate in the canonical frame, rotate vectors
+back (canonical = rot @ input, so input = rot^T @ canonical).
+
+part: "total" (K^(p) q = K^near q + P2 q), "far" (P2 q), "near" (K^near q).
+how : "ewald" (the definition), "plain" (the paper's direct L D R method).
+"""
+import numpy as np
+
+from . import ewald, lattice, method
+
+
+def _rot_vec(rotT, v):
+    # v[..., 2, n] -> rotT @ v
+    return np.einsum("ij,...jn->...in", rotT, v)
+
+
+def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1e-14,
+             want_grad=True, margin_frac=1.0):
+    src = np.asarray(src, np.float64)
+    trg = np.asarray(trg, np.float64)
+    q = np.asarray(q, np.float64)
+    cell, s, t = lattice.to_canonical(e1, e2, src, trg, margin_frac)
+    rot = cell["rot"]
+    if kernel == "stokes":
+        q = np.einsum("ij,rjn->rin", rot, q)
+        want_grad = False
+    pot = 0.0
+    grad = 0.0 if want_grad else None
+    if part in ("total", "near"):
+        p, g = ewald.near_sum(kernel, beta, cell, t, s, q, want_grad)
+        pot = pot + p
+        if want_grad:
+            grad = grad + g
+    if part in ("total", "far"):
+        if how == "ewald":
+            p, g = ewald.far_sum(kernel, beta, cell, t, s, q, want_grad)
+        else:
+            p, g = method.far_field(kernel, beta, cell, t, s, q, eps=eps, want_grad=want_grad)
+        pot = pot + p
+        if want_grad:
+            grad = grad + g
+    if kernel == "stokes":
+        return _rot_vec(rot.T, pot), None
+    return pot, (_rot_vec(rot.T, grad) if want_grad else None)
+
+
+def rel_err(a, b, modconst=False):
+    """Relative l2 error over all entries; modconst removes the best-fit
+    constant per rhs (per component) along the last axis first."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if modconst:
+        a = a - a.mean(-1, keepdims=True)
+        b = b - b.mean(-1, keepdims=True)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))

@@ -1,0 +1,231 @@
+"""The paper's plain method: direct application P q = L (D (R q)) of the
+low-rank factorizations of the four far-field parts (Sec. 6, direct
+application, O(r (N_S + N_T)) work), in FP64, for targets and sources
+already in the canonical cell.
+
+Per part and kernel (theorem / equation labels of the paper):
+
+modhelm  south/north: Theorem south_thm (Eqs. mpk0s, chialphadef,
+         lowranksouth3) and its corollary (Eq. lowranknorth).
+         west/east: Eq. pylw02 / tk0west and Theorem west_thm (Eq. lowrankwest)
+         with its corollary (Eq. lowrankeast), general m0 (App. A, Eq. k0west2:
+         the geometric sum over m <= -(m0+1) gives e^{-(m0+1)kd}/(1-e^{-kd})).
+laplace  south/north: Theorem south_thm_lap, corollary north_thm_lap (m = 0
+         term -(1/(2 d eta)) y sum q y' each, Eq. phis3).  west/east: Theorem
+         west_thm_lap.  Potential gauge (reading of Eq. k1lap/k2lap): the
+         source factor is used as (R - 1) (exact under sum q = 0) and the
+         target factor as (L - 1), which moves the result by a
+         target-independent constant only and removes the 1/lambda
+         non-integrable term of the potential integrand.
+stokes   south: Theorem south_thm_s (Eqs. pssm, pss0, lowranksouth3s),
+         north: the remark after it; west/east: Eq. pssw0 (general m0: the
+         factor (P - (P-1) z)/(1-z), P = m0+1, from summing p z^p),
+         Theorem west_thm_s and the east remark.  The west/east integrals over
+         the whole real line are written as 2 Re of the half line, so the
+         half-line prefactor is 1/(4 pi).  Same (L - 1)/(R - 1) gauge.
+
+Modes: M from Eq. mpk0s.  West/east quadrature: this oracle's own,
+deliberately over-resolved composite Gauss-Legendre rule in lambda' = lambda d
+(panels of width 1/2, 20 points each, dyadic panels toward 0 when
+beta d < 1, truncated where exp(-kappa' x_min') < eps e^-8 with
+x_min' = (m0 d - 2|xi|)/d the smallest scaled west/east gap).  The paper's
+precomputed GGQ tables are not printed, so any accurate rule is a valid
+reading.
+"""
+import math
+import numpy as np
+
+PARTS = ("south", "north", "west", "east")
+
+
+def mpk0s(d, eta, eps):
+    """Eq. mpk0s: number of modes M for precision eps."""
+    r = 2 * math.pi * eta / d
+    return int(math.ceil((d / (2 * math.pi * eta)) * math.log(1.0 / ((1.0 - math.exp(-r)) * eps))))
+
+
+def we_quadrature(cell, beta, eps, width=0.5, npts=20):
+    """Nodes lambda_n > 0 and weights w_n for int_0^inf (.) d lambda."""
+    d, xi = cell["d"], cell["xi"]
+    xmin = (cell["m0"] * d - 2 * abs(xi)) / d
+    bt = beta * d
+    top = (math.log(1.0 / eps) + 8.0) / xmin
+    if top <= bt:
+        return np.zeros(0), np.zeros(0)
+    lam_max = math.sqrt(top * top - bt * bt)
+    edges = [0.0]
+    if 0 < bt < 1:
+        e = bt / 16
+        while e < 0.5:
+            edges.append(e)
+            e *= 2
+    e = edges[-1]
+    while e < lam_max:
+        e = min(lam_max, (math.floor(e / width + 1e-9) + 1) * width)
+        edges.append(e)
+    gx, gw = np.polynomial.legendre.leggauss(npts)
+    nodes, wts = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        nodes.append(0.5 * (b - a) * (gx + 1) + a)
+        wts.append(0.5 * (b - a) * gw)
+    return np.concatenate(nodes) / d, np.concatenate(wts) / d
+
+
+def _scalar_sn(kernel, beta, cell, trg, src, q, eps, part, want_grad):
+    d, xi, eta = cell["d"], cell["xi"], cell["eta"]
+    M = mpk0s(d, eta, eps)
+    m = np.arange(-M, M + 1)
+    if kernel == "laplace":
+        m = m[m != 0]
+    al = 2 * np.pi * m / d
+    chi = np.sqrt(al * al + beta * beta) if kernel == "modhelm" else np.abs(al)
+    Q = chi * eta - 1j * al * xi
+    D = np.exp(-2 * Q) / (2 * d * chi * (1 - np.exp(-Q)))
+    sgn = 1.0 if part == "south" else -1.0
+    if part == "north":
+        D = np.conj(D)
+    R = np.exp(sgn * chi[:, None] * src[1][None, :] - 1j * al[:, None] * src[0][None, :])
+    w = (q.astype(complex) @ R.T) * D  # [nrhs, nm]
+    L = np.exp(-sgn * chi[None, :] * trg[1][:, None] + 1j * al[None, :] * trg[0][:, None])
+    pot = (w @ L.T).real
+    grad = None
+    if want_grad:
+        gx = ((w * (1j * al)) @ L.T).real
+        gy = ((w * (-sgn * chi)) @ L.T).real
+        grad = np.stack([gx, gy], axis=1)
+    if kernel == "laplace":
+        s1 = q @ src[1]  # [nrhs]
+        c0 = -1.0 / (2 * d * eta)
+        pot = pot + c0 * s1[:, None] * trg[1][None, :]
+        if want_grad:
+            grad[:, 1, :] += c0 * s1[:, None]
+    return pot, grad
+
+
+def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad):
+    d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
+    lam, w = we_quadrature(cell, beta if kernel == "modhelm" else 0.0, eps)
+    nrhs, nt = q.shape[0], trg.shape[1]
+    if lam.size == 0:
+        return np.zeros((nrhs, nt)), np.zeros((nrhs, 2, nt)) if want_grad else None
+    kap = np.sqrt(lam * lam + beta * beta) if kernel == "modhelm" else lam
+    P = m0 + 1
+    B = np.exp(kap * xi - 1j * lam * eta) + 1 + np.exp(-kap * xi + 1j * lam * eta)
+    F = np.exp(-P * kap * d) / (1 - np.exp(-kap * d))
+    D = w / (2 * np.pi * kap) * F * B
+    s = 1.0 if part == "west" else -1.0  # east: x -> -x, D -> conj
+    if part == "east":
+        D = np.conj(D)
+    R = np.exp(s * kap[:, None] * src[0][None, :] - 1j * lam[:, None] * src[1][None, :])
+    L = np.exp(-s * kap[None, :] * trg[0][:, None] + 1j * lam[None, :] * trg[1][:, None])
+    if kernel == "laplace":
+        R = R - 1.0
+    wv = (q.astype(complex) @ R.T) * D
+    Lp = (L - 1.0) if kernel == "laplace" else L
+    pot = (wv @ Lp.T).real
+    grad = None
+    if want_grad:
+        gx = ((wv * (-s * kap)) @ L.T).real
+        gy = ((wv * (1j * lam)) @ L.T).real
+        grad = np.stack([gx, gy], axis=1)
+    return pot, grad
+
+
+def _stokes_sn(cell, trg, src, f, eps, part):
+    d, xi, eta = cell["d"], cell["xi"], cell["eta"]
+    M = mpk0s(d, eta, eps)
+    m = np.arange(-M, M + 1)
+    m = m[m != 0]
+    al = 2 * np.pi * m / d
+    a = np.abs(al)
+    sg = np.sign(m)
+    Q = a * eta - 1j * al * xi
+    north = part == "north"
+    if north:
+        Q = np.conj(Q)
+    z = np.exp(-Q)
+    S = np.zeros((m.size, 2, 2), complex)
+    S[:, 0, 0] = 1
+    S[:, 0, 1] = S[:, 1, 0] = 1j * sg
+    S[:, 1, 1] = -1
+    if north:
+        S = np.conj(S)
+    pre = (z * z / (1 - z)) / (4 * d)
+    I2 = np.eye(2)[None]
+    Db = pre[:, None, None] * S
+    Da = pre[:, None, None] * (I2 / a[:, None, None] - (eta * (2 - z) / (1 - z))[:, None, None] * S)
+    sy = -1.0 if north else 1.0
+    R = np.exp(sy * a[:, None] * src[1][None, :] - 1j * al[:, None] * src[0][None, :])  # [nm, ns]
+    L = np.exp(-sy * a[None, :] * trg[1][:, None] + 1j * al[None, :] * trg[0][:, None])  # [nt, nm]
+    fc = f.astype(complex)
+    ca = np.einsum("rcj,mj->rcm", fc, R)
+    cb = np.einsum("rcj,mj->rcm", fc * src[1][None, None, :], R)
+    wa = np.einsum("mij,rjm->rim", Da, ca) + sy * np.einsum("mij,rjm->rim", Db, cb)
+    wb = np.einsum("mij,rjm->rim", Db, ca)
+    vel = np.einsum("lm,rim->ril", L, wa).real - sy * trg[1][None, None, :] * np.einsum("lm,rim->ril", L, wb).real
+    c0 = -1.0 / (2 * d * eta)
+    vel[:, 0, :] += c0 * (f[:, 0, :] @ src[1])[:, None] * trg[1][None, :]
+    return vel
+
+
+def _stokes_we(cell, trg, src, f, eps, part):
+    d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
+    lam, w = we_quadrature(cell, 0.0, eps)
+    P = m0 + 1
+    z = np.exp(-lam * d)
+    ph1 = np.exp(lam * xi - 1j * lam * eta)
+    phm = np.exp(-lam * xi + 1j * lam * eta)
+    B = phm + 1 + ph1
+    Sp = np.zeros((lam.size, 2, 2), complex)
+    Sp[:, 0, 0] = -1
+    Sp[:, 0, 1] = Sp[:, 1, 0] = 1j
+    Sp[:, 1, 1] = 1
+    pref = w / (4 * np.pi) * z ** P / (1 - z)
+    I2 = np.eye(2)[None]
+    Db = (pref * B)[:, None, None] * Sp
+    Da = pref[:, None, None] * (
+        B[:, None, None] * (I2 / lam[:, None, None] - (P * d + d * z / (1 - z))[:, None, None] * Sp)
+        + (xi * (ph1 - phm))[:, None, None] * Sp
+    )
+    east = part == "east"
+    s = -1.0 if east else 1.0
+    if east:
+        Da, Db = np.conj(Da), np.conj(Db)
+    R = np.exp(s * lam[:, None] * src[0][None, :] - 1j * lam[:, None] * src[1][None, :])
+    L = np.exp(-s * lam[None, :] * trg[0][:, None] + 1j * lam[None, :] * trg[1][:, None])
+    fc = f.astype(complex)
+    ca = np.einsum("rcj,mj->rcm", fc, R - 1.0)
+    cb = np.einsum("rcj,mj->rcm", fc * src[0][None, None, :], R)
+    wa = np.einsum("mij,rjm->rim", Da, ca) + s * np.einsum("mij,rjm->rim", Db, cb)
+    wb = np.einsum("mij,rjm->rim", Db, ca)
+    vel = np.einsum("lm,rim->ril", L - 1.0, wa).real - s * trg[0][None, None, :] * np.einsum("lm,rim->ril", L, wb).real
+    return vel
+
+
+def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad=True, chunk=4096):
+    """Sum of the requested far-field parts at the targets.
+    Returns (pot, grad) for scalar kernels, (vel, None) for stokes."""
+    trg = np.asarray(trg, np.float64)
+    src = np.asarray(src, np.float64)
+    q = np.asarray(q, np.float64)
+    nt = trg.shape[1]
+    nrhs = q.shape[0]
+    if kernel == "stokes":
+        out = np.zeros((nrhs, 2, nt))
+        for l0 in range(0, nt, chunk):
+            t = trg[:, l0:l0 + chunk]
+            for p in parts:
+                fn = _stokes_sn if p in ("south", "north") else _stokes_we
+                out[:, :, l0:l0 + chunk] += fn(cell, t, src, q, eps, p)
+        return out, None
+    pot = np.zeros((nrhs, nt))
+    grad = np.zeros((nrhs, 2, nt)) if want_grad else None
+    for l0 in range(0, nt, chunk):
+        t = trg[:, l0:l0 + chunk]
+        for p in parts:
+            fn = _scalar_sn if p in ("south", "north") else _scalar_we
+            pp, gg = fn(kernel, beta, cell, t, src, q, eps, p, want_grad)
+            pot[:, l0:l0 + chunk] += pp
+            if want_grad:
+                grad[:, :, l0:l0 + chunk] += gg
+    return pot, grad
