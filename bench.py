@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Benchmark of the periodic operator (periodizing operator + near-image P2P).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+One step = one full application of the operator (prep, far field through
+the periodizing operator, near-image P2P, combine) to the workload's
+synthetic inputs, already resident on the GPU.  Default workload: 2D doubly
+periodic Laplace, cell e1 = (16, 0), e2 = (0, 1), 1e5 sources from an
+8-component Gaussian mixture (sigma 0.02 per fractional axis), zero net
+charge, targets = sources, potential + gradient, mixed precision at
+tol 1e-6, far field through the NUFFT path (ES width 8, 8 GL lines).
+
+Metric: targets+sources per second = (N_S + N_T) / time per step, summed over
+ranks (each rank runs its own independent cell: weak scaling, no
+collective on the data path).  L2 is flushed (256 MiB write) before every
+timed step; the flush is outside the timed events.
+
+--impl reference times the FP64 CPU oracle (the plain method of the paper
+plus the direct near sum) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "laplace_aspect16_gmm_n1e5"
+METRIC = "targets+sources/s of periodic Laplace/Stokes op, mixed vs FP64 at rel err 1e-6"
+SMS = 152
+SM_MAX_MHZ = 2070.0
+# MUFU rate for lg2/rcp measured on this GPU model (per SM per clock; nominal 32);
+# the Laplace pair needs two (log2 and reciprocal).
+MUFU_PER_CLK_SM = 28.4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--path", default=None, help="override far-field path (direct|nufft)")
+    ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison run")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample), run in a single-threaded subprocess
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, %(root)r)
+import workloads
+from oracle import ewald, lattice, method
+w = workloads.make(%(name)r)
+cell, s, t = lattice.to_canonical(w["e1"], w["e2"], w["src"], w["trg"])
+kernel = w["kernel"]
+q = w["q"]
+if kernel == "stokes":
+    q = np.einsum("ij,rjn->rin", cell["rot"], q)
+res = []
+for nsamp in %(samples)r:
+    idx = np.random.default_rng(123).choice(t.shape[1], nsamp, replace=False)
+    tt = t[:, idx]
+    t0 = time.perf_counter()
+    ewald.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
+    method.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
+    res.append((nsamp, time.perf_counter() - t0))
+print(json.dumps({"samples": res, "ns": int(s.shape[1]), "nt": int(t.shape[1])}))
+"""
+
+
+def oracle_time(name, samples=(16, 48), eps=1e-6):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET % dict(root=ROOT, name=name, samples=list(samples), eps=eps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    (n1, t1), (n2, t2) = d["samples"]
+    per_target = (t2 - t1) / (n2 - n1)
+    fixed = max(0.0, t1 - per_target * n1)
+    t_full = fixed + per_target * d["nt"]
+    return dict(t_full=t_full, per_target=per_target, fixed=fixed, ns=d["ns"], nt=d["nt"],
+                wall=t1 + t2, samples=d["samples"])
+
+
+def cpu_baseline_obj(name, ot, unit):
+    return {"value": (ot["ns"] + ot["nt"]) / ot["t_full"], "unit": unit, "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (plain method, eps 1e-6 far field + direct near sum) on all "
+                       f"{ot['ns']} sources and {ot['samples'][0][0]} / {ot['samples'][1][0]} sampled targets "
+                       f"({ot['wall']:.1f} s); time extrapolated linearly to {ot['nt']} targets")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    vals = []
+    ot = None
+    for _ in range(args.warmup + args.steps):
+        ot = oracle_time(args.workload, samples=(4, 12))
+        vals.append((ot["ns"] + ot["nt"]) / ot["t_full"])
+    v = statistics.median(vals[args.warmup:])
+    cb = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "targets+sources/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * ot["t_full"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "sample": cb["sample"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "targets+sources/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def start_clocks(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL), f
+    except Exception:
+        return None, None
+
+
+def stop_clocks(proc, f, path, gpu_index):
+    if proc is None:
+        return None
+    proc.terminate()
+    try:
+        proc.wait(timeout=5)
+    except Exception:
+        proc.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in open(path):
+        p = [x.strip() for x in ln.split(",")]
+        if len(p) < 9 or p[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(p[1]))
+            mx = float(p[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, p[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    loaded = [x for x in sm if x > 0.5 * (mx or SM_MAX_MHZ)] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel_file, key):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    matches the kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_counters.json")
+    try:
+        d = json.load(open(path))
+        rec = d[key]
+        h = hashlib.sha256(open(os.path.join(ROOT, kernel_file), "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha") != h:
+            return None
+        return rec.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import workloads
+    from paper_2111_01083_gb300 import PeriodicOp
+    from paper_2111_01083_gb300.build import LIB, build_library
+
+    if not os.path.exists(LIB):
+        build_library()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workloads.make(args.workload)
+    cfg = dict(workloads.CONFIGS[args.workload])
+    path = args.path or cfg.get("path", "auto")
+    kernel = w["kernel"]
+    self_t = w["trg"] is w["src"]
+    S = torch.tensor(w["src"], device=dev)
+    Q = torch.tensor(w["q"], device=dev)
+    T = None if self_t else torch.tensor(w["trg"], device=dev)
+    ns = S.shape[1]
+    nt = ns if self_t else T.shape[1]
+    grad = kernel != "stokes"
+    op = PeriodicOp(kernel, w["e1"], w["e2"], tol=cfg["tol"], precision="mixed", path=path,
+                    nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt)
+    op.profile(True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = op(S, Q, T, grad=grad)
+    torch.cuda.synchronize()
+    op.status()
+    for _ in range(max(0, args.warmup - 1)):
+        op(S, Q, T, grad=grad, out=out)
+    torch.cuda.synchronize()
+
+    clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
+    proc, fh = start_clocks(clk_path)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, p2p_ms, far_ms = [], [], []
+    launches = 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        op(S, Q, T, grad=grad, out=out)
+        e1.record()
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ph = op.phase_ms()
+        far_ms.append(ph[1])
+        p2p_ms.append(ph[2])
+        launches += op.describe()["nlaunch"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = stop_clocks(proc, fh, clk_path, local)
+    op.status()
+    ms = sum(step_ms) / len(step_ms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * (ns + nt) / (ms * 1e-3)
+    desc = op.describe()
+
+    # end to end: host arrays through pfmm_execute_host (pinned), copies inside the timed region
+    src_h = torch.from_numpy(w["src"]).pin_memory()
+    q_h = torch.from_numpy(w["q"]).pin_memory()
+    trg_h = src_h if self_t else torch.from_numpy(w["trg"]).pin_memory()
+    pot_h = torch.empty(tuple(out[0].shape), dtype=torch.float64).pin_memory()
+    grad_h = torch.empty(tuple(out[1].shape), dtype=torch.float64).pin_memory() if grad else None
+    op.execute_host_ptrs(src_h, q_h, trg_h, pot_h, grad_h)
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op.execute_host_ptrs(src_h, q_h, trg_h, pot_h, grad_h)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = src_h.numel() * 8 + q_h.numel() * 8 + (0 if self_t else trg_h.numel() * 8)
+    d2h = pot_h.numel() * 8 + (grad_h.numel() * 8 if grad else 0)
+
+    # accuracy: mixed vs the FP64 GPU path on the same input (outside the timed region)
+    acc = None
+    if not args.skip_fp64 and rank == 0:
+        op64 = PeriodicOp(kernel, w["e1"], w["e2"], tol=1e-10, precision="fp64", path="direct", ns_max=ns,
+                          nt_max=nt)
+        op64.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ref = op64(S, Q, T, grad=grad)
+        e1.record()
+        e1.synchronize()
+        op64.status()
+
+        def rel(a, b, mc):
+            a = a.double()
+            b = b.double()
+            if mc:
+                a = a - a.mean(-1, keepdim=True)
+                b = b - b.mean(-1, keepdim=True)
+            return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+        acc = {"fp64_gpu_ms_per_step": e0.elapsed_time(e1),
+               "rel_err_pot_vs_fp64": rel(out[0], ref[0], kernel != "modhelm"),
+               "rel_err_grad_vs_fp64": rel(out[1], ref[1], False) if grad else None,
+               "fp64_gpu_value": (ns + nt) / (e0.elapsed_time(e1) * 1e-3)}
+        del op64, ref
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
+    p2p = sum(p2p_ms) / len(p2p_ms)
+    npairs = desc["npairs"]
+    achieved = npairs / (p2p * 1e-3) / 1e9
+    peak = SMS * (MUFU_PER_CLK_SM / 2.0) * SM_MAX_MHZ * 1e6 / 1e9
+    roof = {"kernel": "k_p2p_mixed (near-image P2P)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "Gpair/s", "frac": achieved / peak,
+            "traffic": traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload),
+            "peak_basis": "MUFU lg2+rcp per pair; measured 28.4 MUFU/clk/SM x 152 SMs x 2070 MHz",
+            "launch_ms": p2p, "share_of_step": p2p / ms}
+    cpu = None
+    if world == 1:
+        try:
+            ot = oracle_time(args.workload)
+            cpu = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "targets+sources/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
+        "config": {"workload": args.workload, "kernel": kernel, "e1": list(w["e1"]), "e2": list(w["e2"]),
+                   "n_sources": ns, "n_targets": nt, "targets_are_sources": self_t,
+                   "dist": cfg.get("dist"), "tol": cfg["tol"], "path": ["direct", "direct", "nufft"][desc["path"]],
+                   "nufft_w": desc["nufft_w"], "n_gl": desc["n_gl"], "M": desc["M"], "Nq": desc["Nq"],
+                   "m0": desc["m0"], "outputs": "pot+grad" if grad else "velocity",
+                   "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
+        "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_p2p": p2p},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "e2e": {"value": world * (ns + nt) / e2e_s, "unit": "targets+sources/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "api": "pfmm_execute_host (pinned host buffers)"},
+        "gpu_launches": launches, "accuracy": acc,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,189 @@
+/*
+ * pfmm.h -- C ABI of the GB300 periodizing-operator library.
+ *
+ * Computes, for sources s_j with strengths q_j in a doubly periodic unit cell
+ * spanned by lattice vectors e1, e2, the periodic field at targets t_l
+ *
+ *     u(t_l) = sum_j K^(p)(t_l, s_j) q_j = (K^near q)(t_l) + (P2 q)(t_l)
+ *
+ * (Pei, Askham, Greengard & Jiang, "Periodic Fast Multipole Method",
+ * arXiv 2111.01083: Sec. 1, Eq. psum and Eq. nearfarsplit).  P2 is the
+ * periodizing operator of Definition "peropdef", applied through the
+ * low-rank plane-wave factorizations of its south/north/west/east parts
+ * (Eq. ksplitting2; Theorems south_thm, west_thm, south_thm_lap,
+ * west_thm_lap, south_thm_s, west_thm_s), either directly (Sec. 6, O(r N)) or
+ * through Gauss-Legendre anterpolation + 1D NUFFTs (Sec. 6, Eqs. fastanterp,
+ * fastinterp).  K^near is the direct sum over the (2 m0 + 1) x 3 near images
+ * (Definition of Lambda_near in Sec. 1), self pairs excluded.
+ *
+ * Green's functions (Sec. 1, Sec. 5.2): Laplace (1/2pi) log(1/r); modified
+ * Helmholtz (1/2pi) K0(beta r); Stokeslet -(1/4pi)(log r I - r r^T / r^2).
+ * Results are u = sum G q (the sign of the paper's Eq. govpde is not used).
+ *
+ * Conventions for every entry point below:
+ *  - All array arguments of pfmm_execute / pfmm_execute_adjoint are DEVICE
+ *    pointers to caller-owned memory (double precision, structure of arrays,
+ *    component-major).  The library never allocates or frees device memory;
+ *    it uses only the caller's workspace.  pfmm_execute_host takes HOST
+ *    pointers and stages them through the workspace.
+ *  - Everything is enqueued on the caller's CUDA stream (passed as void*,
+ *    a cudaStream_t; NULL = legacy default stream).  Nothing synchronises
+ *    except pfmm_get_status and pfmm_execute_host.
+ *  - Return value: PFMM_OK (0) or an error code; pfmm_last_error() gives a
+ *    thread-local message.  Argument errors are detected on the host before
+ *    anything is launched.  Conditions only visible on the device
+ *    (non-finite input, net charge / net force not zero, a bounded wait that
+ *    ran out) are written to a status word in the workspace and reported by
+ *    pfmm_get_status.
+ *  - Lattice vectors may have any orientation; they are reduced and rotated
+ *    to the paper's canonical form e1 = (d, 0), e2 = (xi, eta), d >= |e2|,
+ *    eta > 0 (Sec. 1).  Points may lie anywhere; they are wrapped into the
+ *    cell.  Vector inputs/outputs (forces, gradients, velocities) are in the
+ *    caller's frame.
+ *  - Laplace potentials and Stokes velocities are defined up to an additive
+ *    constant (per rhs, per component).  The library's constant is fixed but
+ *    arbitrary; compare modulo a constant.  Laplace and Stokes require zero
+ *    net charge / net force per rhs (Eq. chargeneutral).
+ *  - Plans are not thread-safe; different plans may run concurrently on
+ *    different streams with different workspaces.
+ */
+#ifndef PFMM_H
+#define PFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2 } pfmm_kernel;
+
+/* FP64: every step in double precision.
+ * MIXED: plane-wave generation, spreading, FFT, interpolation and the P2P
+ * pair terms in FP32 (P2P coordinates as hi/lo float pairs so that
+ * differences are exact to FP32 rounding), with FP64/compensated
+ * accumulation of the coefficient sums and of the per-target totals; lattice
+ * weights, quadrature nodes and compatibility moments in FP64. */
+typedef enum { PFMM_FP64 = 0, PFMM_MIXED = 1 } pfmm_precision;
+
+/* Far-field south/north application: DIRECT = L (D (R q)) (Sec. 6);
+ * NUFFT = GL anterpolation + ES-kernel NUFFT (Sec. 6, Eqs. fastanterp and
+ * fastinterp).  AUTO picks NUFFT when the number of modes is large. */
+typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } pfmm_path;
+
+/* flags */
+enum {
+  PFMM_FAR_ONLY = 1,   /* output P2 q only (no near-image sum)            */
+  PFMM_NEAR_ONLY = 2,  /* output K^near q only                            */
+  PFMM_NO_GRAD = 4     /* scalar kernels: skip the gradient even if given */
+};
+
+typedef enum {
+  PFMM_OK = 0,
+  PFMM_ERR_INVALID_ARG = 1,
+  PFMM_ERR_LATTICE = 2,     /* degenerate lattice vectors                         */
+  PFMM_ERR_NOT_NEUTRAL = 3, /* |sum q| > 1e-8 sum|q| for Laplace/Stokes (device)  */
+  PFMM_ERR_TOLERANCE = 4,   /* tol outside [1e-14, 1e-2]                          */
+  PFMM_ERR_WORKSPACE = 5,   /* workspace NULL, too small or misaligned            */
+  PFMM_ERR_CUDA = 6,        /* a CUDA runtime call failed                         */
+  PFMM_ERR_NONFINITE = 7,   /* NaN/Inf in coordinates or strengths (device)       */
+  PFMM_ERR_TIMEOUT = 8,     /* a bounded device wait gave up (device)             */
+  PFMM_ERR_INTERNAL = 9
+} pfmm_status;
+
+typedef struct {
+  double e1[2], e2[2];  /* lattice vectors (any orientation, not collinear)     */
+  int kernel;           /* pfmm_kernel                                          */
+  double beta;          /* > 0 for PFMM_MODHELM, ignored otherwise              */
+  double tol;           /* requested precision eps, in [1e-14, 1e-2]            */
+  int precision;        /* pfmm_precision                                       */
+  int path;             /* pfmm_path                                            */
+  int nufft_w;          /* ES kernel width (2..16); 0 = ceil(log10(1/tol)) + 2  */
+  int n_gl;             /* GL interpolation lines (4..32); 0 = 8 (tol>=1e-7), else 16 */
+  int nrhs;             /* number of right-hand sides (>= 1)                    */
+  unsigned flags;       /* PFMM_FAR_ONLY | PFMM_NEAR_ONLY | PFMM_NO_GRAD        */
+} pfmm_opts;
+
+/* Parameters chosen by a plan (read-only; for inspection and tests). */
+typedef struct {
+  double d, xi, eta;    /* canonical cell                                       */
+  double rot[4];        /* canonical = rot * input, row-major 2x2               */
+  int m0;               /* near block is (2 m0 + 1) x 3 images                  */
+  int M;                /* south/north modes m = 1..M kept (Eq. mpk0s, pruned)  */
+  int mode0;            /* 1 if the m = 0 mode is used (Laplace/Stokes, or modhelm when not negligible) */
+  int Nq;               /* west/east quadrature nodes                           */
+  int path;             /* PFMM_PATH_DIRECT or PFMM_PATH_NUFFT after AUTO        */
+  int n_gl, nf, nufft_w;/* NUFFT: GL lines, fine grid size, ES width           */
+  double es_beta;       /* ES kernel shape parameter                            */
+  int nlaunch;          /* kernels launched by the last pfmm_execute on this plan */
+  int64_t npairs;       /* near-image pairs of the last execute: ns * nt * (2 m0 + 1) * 3 */
+} pfmm_plan_desc;
+
+typedef struct pfmm_plan pfmm_plan;
+
+/* Build a plan: canonical cell (Sec. 1), m0, modes M (Eq. mpk0s), west/east
+ * quadrature nodes and weights (own composite Gauss-Legendre rule; the
+ * paper's GGQ tables are not printed), NUFFT sizes.  Host only, no GPU work.
+ * ns_max/nt_max bound the sizes later passed to pfmm_execute.
+ * Errors: PFMM_ERR_INVALID_ARG (NULL, nrhs < 1, sizes < 0, beta <= 0 for
+ * MODHELM, bad enum), PFMM_ERR_LATTICE, PFMM_ERR_TOLERANCE. */
+pfmm_status pfmm_plan_create(const pfmm_opts* opts, int64_t ns_max, int64_t nt_max,
+                             pfmm_plan** out);
+
+/* Bytes of device workspace pfmm_execute needs (256-byte aligned pointer). */
+pfmm_status pfmm_workspace_size(const pfmm_plan* plan, size_t* bytes);
+
+/* Bytes of device workspace pfmm_execute_host needs (adds staging space). */
+pfmm_status pfmm_workspace_size_host(const pfmm_plan* plan, size_t* bytes);
+
+pfmm_status pfmm_plan_describe(const pfmm_plan* plan, pfmm_plan_desc* out);
+
+/* Apply the periodic operator.
+ *   src  [2][ns]      source coordinates (x row then y row)
+ *   q    [nrhs][ns]   strengths (Laplace, modhelm) or
+ *        [nrhs][2][ns] forces (Stokes)
+ *   trg  [2][nt]      target coordinates; may be the same pointer as src with
+ *                     nt == ns (targets = sources; self pairs are skipped,
+ *                     and so is any pair at exactly zero distance)
+ *   pot  [nrhs][nt]   potential (Laplace, modhelm) or
+ *        [nrhs][2][nt] velocity (Stokes); may be NULL for scalar kernels
+ *   grad [nrhs][2][nt] gradient of the potential (scalar kernels) or NULL;
+ *                     must be NULL for Stokes
+ * Outputs are overwritten.  ns, nt >= 0 and <= the plan's maxima. */
+pfmm_status pfmm_execute(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns,
+                         const double* src, const double* q, int64_t nt, const double* trg,
+                         double* pot, double* grad, void* stream);
+
+/* Same operation with HOST arrays: stages inputs into the workspace
+ * (cudaMemcpyAsync), runs pfmm_execute, copies outputs back and synchronises
+ * the stream.  Workspace from pfmm_workspace_size_host.  src == trg (same
+ * host pointer, ns == nt) means targets = sources. */
+pfmm_status pfmm_execute_host(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns,
+                              const double* src, const double* q, int64_t nt, const double* trg,
+                              double* pot, double* grad, void* stream);
+
+/* Synchronise the stream and read the device status word written by the
+ * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,
+ * PFMM_ERR_NOT_NEUTRAL, PFMM_ERR_TIMEOUT) and clears it. */
+pfmm_status pfmm_get_status(pfmm_plan* plan, void* workspace, void* stream);
+
+/* Per-phase GPU timing (tracing).  When enabled (on != 0), pfmm_execute
+ * records CUDA events on the caller's stream around its phases; the events
+ * are created here (no device memory).  pfmm_profile_read waits for the last
+ * recorded event and returns milliseconds per phase in ms[0..n-1]:
+ * [0] prep (wrap, convert, moments), [1] far field (periodizing operator),
+ * [2] near-image P2P.  Errors: PFMM_ERR_INVALID_ARG, PFMM_ERR_CUDA. */
+pfmm_status pfmm_profile_enable(pfmm_plan* plan, int on);
+pfmm_status pfmm_profile_read(pfmm_plan* plan, float* ms, int n);
+
+const char* pfmm_last_error(void);
+void pfmm_plan_destroy(pfmm_plan* plan);
+
+/* Library version string (for logs). */
+const char* pfmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFMM_H */

@@ -20,7 +20,7 @@ def _rot_vec(rotT, v):
 
 
 def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1e-14,
-             want_grad=True, margin_frac=1.0):
+             want_grad=True, margin_frac=0.25):
     src = np.asarray(src, np.float64)
     trg = np.asarray(trg, np.float64)
     q = np.asarray(q, np.float64)

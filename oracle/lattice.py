@@ -12,7 +12,11 @@ west/east plane-wave integrals need x - x' - m d - n xi >= margin > 0 for every
 far image in the three middle rows (proof after Eq. pylw02); with points in
 the parallelogram the smallest such gap is m0 d - 2|xi|, which gives the rule
 m0 = max(1, ceil((margin + 2|xi|)/d)).  margin = d reproduces the paper's
-choice (m0 = 1 for rectangles, m0 = 2 for 0 < |xi| <= d/2).
+choice (m0 = 1 for rectangles, m0 = 2 for 0 < |xi| <= d/2).  The default here
+is margin = d/4 (reading: any positive gap keeps the west/east integrands
+exponentially decaying; a smaller gap only needs more quadrature nodes), so
+m0 = 1 unless |xi| > 3d/8, which keeps the near block at 3 x 3 cells for most
+parallelograms.
 """
 import math
 import numpy as np
@@ -50,7 +54,7 @@ def canonicalize(e1, e2):
     return dict(d=d, xi=float(bb[0]), eta=float(bb[1]), rot=rot)
 
 
-def choose_m0(d, xi, margin_frac=1.0):
+def choose_m0(d, xi, margin_frac=0.25):
     """Smallest m0 >= 1 with m0 d - 2|xi| >= margin_frac * d."""
     return max(1, int(math.ceil((margin_frac * d + 2.0 * abs(xi)) / d - 1e-12)))
 
@@ -75,7 +79,7 @@ def near_offsets(d, xi, eta, m0):
     return np.array(out)
 
 
-def to_canonical(e1, e2, src, trg, margin_frac=1.0):
+def to_canonical(e1, e2, src, trg, margin_frac=0.25):
     """Canonicalise the lattice and wrap sources/targets given in the input
     frame ([2, n] arrays).  Returns (cell dict incl. m0, src_c, trg_c)."""
     cell = canonicalize(e1, e2)

@@ -1,0 +1,13 @@
+"""GB300-native periodizing operator for 2D doubly periodic Laplace, modified
+Helmholtz and Stokes kernels (Pei, Askham, Greengard & Jiang, "Periodic Fast
+Multipole Method", arXiv 2111.01083).
+
+The computation lives in the CUDA library ``libpfmm.so`` (C ABI in
+``include/pfmm.h``); this package only marshals arguments.  Importing the
+package does not load the library; the first call does, and raises if it is
+missing (there is no CPU fallback).
+"""
+from .periodic import PeriodicOp  # noqa: F401
+from . import _lib  # noqa: F401
+
+__all__ = ["PeriodicOp"]

@@ -1,0 +1,616 @@
+// Point preparation and the direct far-field path (Sec. 6: P q = L (D (R q))).
+//
+//   k_prep_points : wrap + rotate points into the canonical cell (Sec. 1),
+//                   FP64 and FP32 copies, fixed-point x/d phase, hi/lo split
+//   k_prep_q      : strengths in the canonical frame, FP64 compatibility
+//                   moments sum q, sum |q|, sum q y' (Eq. chargeneutral,
+//                   Eq. phis2 / Eq. pss0)
+//   k_far_form    : coefficients c = R q for the south/north modes and the
+//                   west/east quadrature nodes (Theorems south_thm, west_thm,
+//                   south_thm_lap, west_thm_lap, south_thm_s, west_thm_s)
+//   k_far_weights : lattice weights D (FP64), w = D c
+//   k_far_eval    : u = Re(L w) at the targets (+ gradient / Stokes velocity)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include "pfmm_impl.h"
+#include "devmath.cuh"
+
+namespace pfmm {
+
+// ----------------------------------------------------------------------------
+// K0: points
+// ----------------------------------------------------------------------------
+__global__ void k_prep_points(Geom g, int64_t n, const double* __restrict__ pts, double* __restrict__ c64,
+                              float* __restrict__ cf, int* __restrict__ U, float4* __restrict__ hl,
+                              int* __restrict__ status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x = pts[i], y = pts[n + i];
+  if (!isfinite(x) || !isfinite(y)) {
+    atomicOr(status, ST_NONFINITE);
+    x = 0.0;
+    y = 0.0;
+  }
+  double xc = g.rot[0] * x + g.rot[1] * y, yc = g.rot[2] * x + g.rot[3] * y;
+  double u1 = g.ainv[0] * xc + g.ainv[1] * yc, u2 = g.ainv[3] * yc;
+  u1 -= floor(u1 + 0.5);
+  u2 -= floor(u2 + 0.5);
+  xc = u1 * g.d + u2 * g.xi;
+  yc = u2 * g.eta;
+  c64[i] = xc;
+  c64[n + i] = yc;
+  cf[i] = (float)xc;
+  cf[n + i] = (float)yc;
+  double v = xc / g.d;
+  v -= floor(v + 0.5);
+  U[i] = (int)(unsigned)(long long)llrint(v * 4294967296.0);
+  if (hl) {
+    float xh = (float)xc, yh = (float)yc;
+    hl[i] = make_float4(xh, (float)(xc - (double)xh), yh, (float)(yc - (double)yh));
+  }
+}
+
+// K0: strengths (canonical frame) and FP64 moments per rhs:
+//   mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y, [2] = sum |q| (all comps), [3] = sum q y' (f_x y')
+__global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, const double* __restrict__ q,
+                         const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
+                         double* __restrict__ mom, int* __restrict__ status) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool in = i < ns;
+  double y = in ? src64[ns + i] : 0.0;
+  int lane = threadIdx.x & 31;
+  for (int r = 0; r < nrhs; ++r) {
+    double a = 0, b = 0;
+    if (in) {
+      if (ncomp == 1) {
+        a = q[(size_t)r * ns + i];
+      } else {
+        double fx = q[((size_t)r * 2) * ns + i], fy = q[((size_t)r * 2 + 1) * ns + i];
+        a = g.rot[0] * fx + g.rot[1] * fy;
+        b = g.rot[2] * fx + g.rot[3] * fy;
+      }
+      if (!isfinite(a) || !isfinite(b)) {
+        atomicOr(status, ST_NONFINITE);
+        a = 0;
+        b = 0;
+      }
+      if (ncomp == 1) {
+        if (qc) qc[(size_t)r * ns + i] = a;
+        qf[(size_t)r * ns + i] = (float)a;
+      } else {
+        qc[((size_t)r * 2) * ns + i] = a;
+        qc[((size_t)r * 2 + 1) * ns + i] = b;
+        qf[((size_t)r * 2) * ns + i] = (float)a;
+        qf[((size_t)r * 2 + 1) * ns + i] = (float)b;
+      }
+    }
+    double v0 = a, v1 = b, v2 = fabs(a) + fabs(b), v3 = a * y;
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_down_sync(0xffffffffu, v0, o);
+      v1 += __shfl_down_sync(0xffffffffu, v1, o);
+      v2 += __shfl_down_sync(0xffffffffu, v2, o);
+      v3 += __shfl_down_sync(0xffffffffu, v3, o);
+    }
+    if (lane == 0) {
+      atomicAdd(mom + r * 8 + 0, v0);
+      atomicAdd(mom + r * 8 + 1, v1);
+      atomicAdd(mom + r * 8 + 2, v2);
+      atomicAdd(mom + r * 8 + 3, v3);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// term decoding.  Term list: [south m_lo..M | north m_lo..M | west 0..Nq-1 | east 0..Nq-1]
+// part: 0 S, 1 N, 2 W, 3 E.  For S/N: a = alpha_m, b = chi_m, m.  W/E: a = lambda, b = kappa.
+// ----------------------------------------------------------------------------
+struct Term {
+  int part, m;
+  double a, b, w;
+};
+
+__device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) {
+  Term T;
+  int mlo = f.mode0 ? 0 : 1;
+  if (t < 2 * f.nsn) {
+    T.part = t < f.nsn ? 0 : 1;
+    T.m = (t < f.nsn ? t : t - f.nsn) + mlo;
+    T.a = 2.0 * M_PI * T.m / g.d;
+    T.b = (f.kernel == PFMM_MODHELM) ? sqrt(T.a * T.a + f.beta * f.beta) : fabs(T.a);
+    T.w = 0;
+  } else {
+    int n = t - 2 * f.nsn;
+    T.part = n < f.Nq ? 2 : 3;
+    if (n >= f.Nq) n -= f.Nq;
+    T.m = n;
+    T.a = f.nodes[2 * n];
+    T.w = f.nodes[2 * n + 1];
+    T.b = (f.kernel == PFMM_MODHELM) ? sqrt(T.a * T.a + f.beta * f.beta) : T.a;
+  }
+  return T;
+}
+
+// ----------------------------------------------------------------------------
+// K1: coefficient formation.  grid (chunks, term blocks, rhs groups).
+// coef layout [nrhs][nch][nterm] complex double; Stokes channels:
+//   0,1: c_a = sum R f (x, y comps)    (W/E: R - 1)
+//   2,3: c_b = sum R coord f           (coord = y' for S/N, x' for W/E)
+// ----------------------------------------------------------------------------
+constexpr int kFormThreads = 128;
+constexpr int kFormSub = 64;
+constexpr int kRB = 4;  // rhs per block
+
+template <typename T, int KER>
+__global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns, int chunk, const T* __restrict__ sx,
+                                                           const T* __restrict__ sy, const int* __restrict__ sU,
+                                                           const T* __restrict__ qv, double* __restrict__ coef) {
+  constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
+  constexpr int NCH = (KER == PFMM_STOKES) ? 4 : 1;
+  __shared__ T s_x[kFormSub], s_y[kFormSub];
+  __shared__ int s_U[kFormSub];
+  __shared__ T s_q[kRB][NC][kFormSub];
+
+  const int t = blockIdx.y * kFormThreads + threadIdx.x;
+  const bool active = t < f.nterm;
+  const int r0 = blockIdx.z * kRB;
+  const int nr = min(kRB, f.nrhs - r0);
+  Term tm = decode_term(f, g, active ? t : 0);
+  const T a = (T)tm.a, b = (T)tm.b;
+  const T sgn = (tm.part == 0 || tm.part == 2) ? T(1) : T(-1);
+  const bool sn = tm.part < 2;
+  const bool we_m1 = !sn && (KER != PFMM_MODHELM);
+  const double inv_d = 1.0 / g.d;
+
+  double acc[kRB][NCH][2];
+#pragma unroll
+  for (int r = 0; r < kRB; ++r)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
+
+  const int j0 = blockIdx.x * chunk;
+  const int j1 = min(ns, j0 + chunk);
+  for (int jb = j0; jb < j1; jb += kFormSub) {
+    const int nb = min(kFormSub, j1 - jb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += kFormThreads) {
+      s_x[k] = sx[jb + k];
+      s_y[k] = sy[jb + k];
+      s_U[k] = sU ? sU[jb + k] : 0;
+    }
+    for (int k = threadIdx.x; k < kRB * NC * kFormSub; k += kFormThreads) {
+      int r = k / (NC * kFormSub), rem = k % (NC * kFormSub), c = rem / kFormSub, jj = rem % kFormSub;
+      s_q[r][c][jj] = (r < nr && jj < nb) ? qv[((size_t)(r0 + r) * NC + c) * ns + jb + jj] : T(0);
+    }
+    __syncthreads();
+    if (!active) continue;
+    T sub[kRB][NCH][2];
+#pragma unroll
+    for (int r = 0; r < kRB; ++r)
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) sub[r][c][0] = sub[r][c][1] = T(0);
+    for (int jj = 0; jj < nb; ++jj) {
+      const T x = s_x[jj], y = s_y[jj];
+      T Rr, Ri, Qr, Qi;  // R (for c_b / plain) and Q (for c_a: R or R - 1)
+      if (sn) {
+        T e = dm::ex(sgn * b * y);
+        T sp, cp;
+        if constexpr (sizeof(T) == 4)
+          dm::phase_fixed(tm.m, s_U[jj], &sp, &cp);
+        else
+          dm::sincospi_(T(2.0 * tm.m * ((double)x * inv_d)), &sp, &cp);
+        Rr = e * cp;
+        Ri = -e * sp;
+        Qr = Rr;
+        Qi = Ri;
+      } else {
+        if (we_m1) {
+          dm::expm1c(sgn * b * x, -a * y, &Qr, &Qi);
+          Rr = Qr + T(1);
+          Ri = Qi;
+        } else {
+          T e = dm::ex(sgn * b * x);
+          T sp, cp;
+          dm::sincos_(a * y, &sp, &cp);
+          Rr = e * cp;
+          Ri = -e * sp;
+          Qr = Rr;
+          Qi = Ri;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRB; ++r) {
+        if (NC == 1) {
+          const T s = s_q[r][0][jj];
+          sub[r][0][0] += Qr * s;
+          sub[r][0][1] += Qi * s;
+        } else {
+          const T fx = s_q[r][0][jj], fy = s_q[r][1][jj];
+          const T cd = sn ? y : x;
+          const T Br = Rr * cd, Bi = Ri * cd;
+          sub[r][0][0] += Qr * fx;
+          sub[r][0][1] += Qi * fx;
+          sub[r][1][0] += Qr * fy;
+          sub[r][1][1] += Qi * fy;
+          sub[r][NCH - 2][0] += Br * fx;
+          sub[r][NCH - 2][1] += Bi * fx;
+          sub[r][NCH - 1][0] += Br * fy;
+          sub[r][NCH - 1][1] += Bi * fy;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRB; ++r)
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        acc[r][c][0] += (double)sub[r][c][0];
+        acc[r][c][1] += (double)sub[r][c][1];
+      }
+  }
+  if (!active) return;
+  for (int r = 0; r < nr; ++r)
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      double* dst = coef + (((size_t)(r0 + r) * NCH + c) * f.nterm + t) * 2;
+      atomicAdd(dst, acc[r][c][0]);
+      atomicAdd(dst + 1, acc[r][c][1]);
+    }
+}
+
+// ----------------------------------------------------------------------------
+// K2: weights.  One thread per (term, rhs).  FP64.
+//   scalar: W (1 complex)          u += Re(L W)   (Laplace W/E: Re((L-1) W))
+//   Stokes: Wa[2], Wb[2]           u_k += Re(L Wa_k) + coord Re(L Wb_k)   (W/E: (L-1) Wa)
+// mom[r*8+4] = c0: Laplace: -(1/(d eta)) sum q y' (m = 0 of south + north, Eq. phis3),
+//        Stokes: -(1/(d eta)) sum f_x y' (Eq. pss0); added as c0 * y.
+// ----------------------------------------------------------------------------
+struct dcx {
+  double r, i;
+};
+__device__ __forceinline__ dcx cmul(dcx a, dcx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ dcx cadd(dcx a, dcx b) { return {a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ dcx csub(dcx a, dcx b) { return {a.r - b.r, a.i - b.i}; }
+__device__ __forceinline__ dcx cscale(dcx a, double s) { return {a.r * s, a.i * s}; }
+__device__ __forceinline__ dcx cexp_(dcx z) {
+  double e = exp(z.r), s, c;
+  sincos(z.i, &s, &c);
+  return {e * c, e * s};
+}
+__device__ __forceinline__ dcx cdiv(dcx a, dcx b) {
+  double den = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / den, (a.i * b.r - a.r * b.i) / den};
+}
+__device__ __forceinline__ dcx conj_(dcx a) { return {a.r, -a.i}; }
+
+template <typename T2>
+__device__ __forceinline__ void store_w(T2* p, dcx v) {
+  p->x = v.r;
+  p->y = v.i;
+}
+
+template <typename T2>
+__global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, double* __restrict__ mom,
+                              T2* __restrict__ wts, int* __restrict__ status) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int r = blockIdx.y;
+  const int K = f.kernel;
+  if (t == 0) {
+    double mq = mom[r * 8 + 0], mfy = mom[r * 8 + 1], mabs = mom[r * 8 + 2], my = mom[r * 8 + 3];
+    if (K != PFMM_MODHELM) {
+      double net = (K == PFMM_STOKES) ? fmax(fabs(mq), fabs(mfy)) : fabs(mq);
+      if (net > 1e-8 * mabs + 1e-300) atomicOr(status, ST_NOT_NEUTRAL);
+      mom[r * 8 + 4] = -my / (g.d * g.eta);
+    } else {
+      mom[r * 8 + 4] = 0.0;
+    }
+  }
+  if (t >= f.nterm) return;
+  Term tm = decode_term(f, g, t);
+  const double d = g.d, xi = g.xi, eta = g.eta;
+  const int nch = f.nch;
+  auto C = [&](int c) {
+    const double* p = coef + (((size_t)r * nch + c) * f.nterm + t) * 2;
+    return dcx{p[0], p[1]};
+  };
+  const bool north = tm.part == 1, east = tm.part == 3;
+  if (K != PFMM_STOKES) {
+    dcx D;
+    double fac = 1.0;
+    if (tm.part < 2) {
+      // Theorem south_thm / south_thm_lap: D = e^{-2Q} / (2 d chi (1 - e^{-Q})), Q = chi eta - i alpha xi
+      dcx Q{tm.b * eta, -tm.a * xi};
+      dcx e1 = cexp_({-Q.r, -Q.i});
+      dcx e2 = cmul(e1, e1);
+      D = cdiv(e2, cscale({1.0 - e1.r, -e1.i}, 2.0 * d * tm.b));
+      if (north) D = conj_(D);
+      fac = (tm.m == 0) ? 1.0 : 2.0;  // +-m pairs
+    } else {
+      // Theorem west_thm (general m0): D = (w / (2 pi kappa)) e^{-(m0+1) kappa d}/(1 - e^{-kappa d}) B,
+      // B = e^{kappa xi - i lambda eta} + 1 + e^{-kappa xi + i lambda eta}
+      double lam = tm.a, kap = tm.b;
+      double F = exp(-(g.m0 + 1) * kap * d) / (-expm1(-kap * d));
+      dcx B = cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta}));
+      D = cscale(B, tm.w / (2.0 * M_PI * kap) * F);
+      if (east) D = conj_(D);
+    }
+    dcx W = cscale(cmul(D, C(0)), fac);
+    store_w(wts + (size_t)r * f.nterm + t, W);
+    return;
+  }
+  // Stokes
+  dcx Da[2][2], Db[2][2];
+  if (tm.part < 2) {
+    // Theorem south_thm_s (Eq. pssm): z = e^{-Q}, Q = |alpha| eta - i alpha xi (north: conj),
+    // Db = z^2/(4d(1-z)) S, Da = z^2/(4d(1-z)) [ I/|alpha| - eta (2 - z)/(1 - z) S ],
+    // S = [[1, i], [i, -1]] for m > 0 (north: conj).
+    double al = tm.a, aa = fabs(al);
+    dcx Q{aa * eta, -al * xi};
+    if (north) Q = conj_(Q);
+    dcx z = cexp_({-Q.r, -Q.i});
+    dcx omz{1.0 - z.r, -z.i};
+    dcx pre = cdiv(cmul(z, z), cscale(omz, 4.0 * d));
+    dcx S[2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {-1, 0}}};
+    if (north) {
+      S[0][1] = conj_(S[0][1]);
+      S[1][0] = conj_(S[1][0]);
+    }
+    dcx q2 = cscale(cdiv({2.0 - z.r, -z.i}, omz), eta);
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        Db[i][j] = cmul(pre, S[i][j]);
+        dcx id = (i == j) ? dcx{1.0 / aa, 0.0} : dcx{0.0, 0.0};
+        Da[i][j] = cmul(pre, csub(id, cmul(q2, S[i][j])));
+      }
+  } else {
+    // Eq. pssw0 with P = m0 + 1 (half-line, 2 Re): pref = (w / 4pi) z^P / (1 - z), z = e^{-lambda d},
+    // Db = pref B S', Da = pref [ B (I/lambda - (P d + d z/(1 - z)) S') + xi (phi_1 - phi_-1) S' ],
+    // S' = [[-1, i], [i, 1]], phi_r = e^{r (lambda xi - i lambda eta)}.  East: conj.
+    double lam = tm.a;
+    double z = exp(-lam * d);
+    double omz = -expm1(-lam * d);
+    int P = g.m0 + 1;
+    double pref = tm.w / (4.0 * M_PI) * exp(-P * lam * d) / omz;
+    dcx ph1 = cexp_({lam * xi, -lam * eta}), phm = cexp_({-lam * xi, lam * eta});
+    dcx B = cadd(cadd(ph1, phm), {1.0, 0.0});
+    dcx Sp[2][2] = {{{-1, 0}, {0, 1}}, {{0, 1}, {1, 0}}};
+    double kx = P * d + d * z / omz;
+    dcx dph = cscale(csub(ph1, phm), xi);
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        Db[i][j] = cscale(cmul(B, Sp[i][j]), pref);
+        dcx id = (i == j) ? dcx{1.0 / lam, 0.0} : dcx{0.0, 0.0};
+        dcx t1 = cmul(B, csub(id, cscale(Sp[i][j], kx)));
+        Da[i][j] = cscale(cadd(t1, cmul(dph, Sp[i][j])), pref);
+        if (east) {
+          Db[i][j] = conj_(Db[i][j]);
+          Da[i][j] = conj_(Da[i][j]);
+        }
+      }
+  }
+  // sign of the coordinate terms: S/W: Wa = Da ca + Db cb, Wb = -Db ca; N/E: Wa = Da ca - Db cb, Wb = +Db ca
+  double sg = (north || east) ? -1.0 : 1.0;
+  double fac = (tm.part < 2) ? 2.0 : 1.0;
+  dcx ca[2] = {C(0), C(1)}, cb[2] = {C(2), C(3)};
+  for (int i = 0; i < 2; ++i) {
+    dcx wa = {0, 0}, wb = {0, 0};
+    for (int j = 0; j < 2; ++j) {
+      wa = cadd(wa, cadd(cmul(Da[i][j], ca[j]), cscale(cmul(Db[i][j], cb[j]), sg)));
+      wb = cadd(wb, cscale(cmul(Db[i][j], ca[j]), -sg));
+    }
+    store_w(wts + (((size_t)r * 4 + i) * f.nterm + t), cscale(wa, fac));
+    store_w(wts + (((size_t)r * 4 + 2 + i) * f.nterm + t), cscale(wb, fac));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// K3: evaluation at targets.  grid (target blocks, rhs groups); terms staged
+// in shared memory in chunks.
+// ----------------------------------------------------------------------------
+constexpr int kEvalThreads = 128;
+constexpr int kEvalChunk = 64;
+
+template <typename T, typename T2, int KER>
+__global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt, const T* __restrict__ tx,
+                                                           const T* __restrict__ ty, const int* __restrict__ tU,
+                                                           const T2* __restrict__ wts, const double* __restrict__ mom,
+                                                           double* __restrict__ pot, double* __restrict__ grad) {
+  constexpr int NW = (KER == PFMM_STOKES) ? 4 : 1;
+  __shared__ T s_a[kEvalChunk], s_b[kEvalChunk];
+  __shared__ int s_m[kEvalChunk], s_part[kEvalChunk];
+  __shared__ T2 s_w[kRB][NW][kEvalChunk];
+  const int l = blockIdx.x * kEvalThreads + threadIdx.x;
+  const bool in = l < nt;
+  const int r0 = blockIdx.y * kRB;
+  const int nr = min(kRB, f.nrhs - r0);
+  const T x = in ? tx[l] : T(0), y = in ? ty[l] : T(0);
+  const int U = (in && tU) ? tU[l] : 0;
+  const double xd = in ? (double)x / g.d : 0.0;
+  // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy]
+  constexpr int NA = (KER == PFMM_STOKES) ? 2 : 3;
+  T acc[kRB][NA];
+#pragma unroll
+  for (int r = 0; r < kRB; ++r)
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[r][k] = T(0);
+
+  for (int t0 = 0; t0 < f.nterm; t0 += kEvalChunk) {
+    const int nc = min(kEvalChunk, f.nterm - t0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += kEvalThreads) {
+      Term tm = decode_term(f, g, t0 + k);
+      s_a[k] = (T)tm.a;
+      s_b[k] = (T)tm.b;
+      s_m[k] = tm.m;
+      s_part[k] = tm.part;
+    }
+    for (int k = threadIdx.x; k < kRB * NW * kEvalChunk; k += kEvalThreads) {
+      int r = k / (NW * kEvalChunk), rem = k % (NW * kEvalChunk), c = rem / kEvalChunk, tt = rem % kEvalChunk;
+      T2 v;
+      v.x = T(0);
+      v.y = T(0);
+      if (r < nr && tt < nc) v = wts[((size_t)(r0 + r) * NW + c) * f.nterm + t0 + tt];
+      s_w[r][c][tt] = v;
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int k = 0; k < nc; ++k) {
+      const int part = s_part[k];
+      const T a = s_a[k], b = s_b[k];
+      T Lr, Li, Mr, Mi;  // L and the potential factor (L - 1 for Laplace/Stokes W/E)
+      if (part < 2) {
+        const T sy = part == 0 ? T(1) : T(-1);
+        T e = dm::ex(-sy * b * y);
+        T sp, cp;
+        if constexpr (sizeof(T) == 4)
+          dm::phase_fixed(s_m[k], U, &sp, &cp);
+        else
+          dm::sincospi_(T(2.0 * s_m[k] * xd), &sp, &cp);
+        Lr = e * cp;
+        Li = e * sp;
+        Mr = Lr;
+        Mi = Li;
+      } else {
+        const T sx = part == 2 ? T(1) : T(-1);
+        if (KER != PFMM_MODHELM) {
+          dm::expm1c(-sx * b * x, a * y, &Mr, &Mi);
+          Lr = Mr + T(1);
+          Li = Mi;
+        } else {
+          T e = dm::ex(-sx * b * x);
+          T sp, cp;
+          dm::sincos_(a * y, &sp, &cp);
+          Lr = e * cp;
+          Li = e * sp;
+          Mr = Lr;
+          Mi = Li;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRB; ++r) {
+        if (KER != PFMM_STOKES) {
+          const T2 w = s_w[r][0][k];
+          const T Pr = Lr * w.x - Li * w.y, Pi = Lr * w.y + Li * w.x;
+          acc[r][0] += Mr * w.x - Mi * w.y;
+          if (part < 2) {
+            acc[r][1] -= a * Pi;
+            acc[r][2] -= (part == 0 ? b : -b) * Pr;
+          } else {
+            acc[r][1] -= (part == 2 ? b : -b) * Pr;
+            acc[r][2] -= a * Pi;
+          }
+        } else {
+          const T cd = part < 2 ? y : x;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const T2 wa = s_w[r][c][k], wb = s_w[r][2 + c][k];
+            acc[r][c] += (Mr * wa.x - Mi * wa.y) + cd * (Lr * wb.x - Li * wb.y);
+          }
+        }
+      }
+    }
+  }
+  if (!in) return;
+  const double* R = g.rot;  // input = rot^T canonical
+  for (int r = 0; r < nr; ++r) {
+    const double cc = mom[(r0 + r) * 8 + 4];
+    const double yd = (double)y;
+    if (KER == PFMM_STOKES) {
+      double ux = (double)acc[r][0] + cc * yd, uy = (double)acc[r][1];
+      pot[((size_t)(r0 + r) * 2) * nt + l] = R[0] * ux + R[2] * uy;
+      pot[((size_t)(r0 + r) * 2 + 1) * nt + l] = R[1] * ux + R[3] * uy;
+    } else {
+      double p = (double)acc[r][0] + cc * yd;
+      double gx = (double)acc[r][1], gy = (double)acc[r][2] + cc;
+      if (pot) pot[(size_t)(r0 + r) * nt + l] = p;
+      if (grad) {
+        grad[((size_t)(r0 + r) * 2) * nt + l] = R[0] * gx + R[2] * gy;
+        grad[((size_t)(r0 + r) * 2 + 1) * nt + l] = R[1] * gx + R[3] * gy;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+static inline int cdiv_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q, int64_t nt,
+                        const double* trg, bool self, cudaStream_t st) {
+  const Layout& L = p->lay;
+  int* status = (int*)(ws + L.status);
+  bool mixed = p->opts.precision == PFMM_MIXED;
+  k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
+                                                 (int*)(ws + L.srcU), mixed ? (float4*)(ws + L.srchl) : nullptr,
+                                                 status);
+  if (!self && nt > 0)
+    k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
+                                                   (int*)(ws + L.trgU), nullptr, status);
+  g_launches = (!self && nt > 0) ? 3 : 2;
+  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, p->opts.nrhs, ns, q, (const double*)(ws + L.src64),
+                                            (double*)(ws + L.qc), (float*)(ws + L.qf), (double*)(ws + L.moments),
+                                            status);
+  return cudaGetLastError();
+}
+
+template <typename T, typename T2, int KER>
+static cudaError_t run_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                                  double* grad, cudaStream_t st) {
+  const Layout& L = p->lay;
+  Far f = p->far;
+  f.nodes = (const double*)(ws + L.nodes);
+  const Geom& g = p->geom;
+  const bool mixed = sizeof(T) == 4;
+  const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
+  const T* sy = sx + ns;
+  const int* sU = (const int*)(ws + L.srcU);
+  const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
+  double* coef = (double*)(ws + L.coef);
+  double* mom = (double*)(ws + L.moments);
+  int nrg = cdiv_i(f.nrhs, kRB);
+  g_launches = (f.nterm > 0) ? 3 : 2;
+  if (f.nterm > 0) {
+    int ny = cdiv_i(f.nterm, kFormThreads);
+    int want = 4 * 152 * 4;  // enough blocks to fill every SM several times
+    int nchunk = std::max(1, std::min(cdiv_i(ns, kFormSub), want / std::max(1, ny * nrg)));
+    int chunk = cdiv_i(cdiv_i(ns, nchunk), kFormSub) * kFormSub;
+    nchunk = cdiv_i(ns, chunk);
+    dim3 grid(nchunk, ny, nrg);
+    k_far_form<T, KER><<<grid, kFormThreads, 0, st>>>(f, g, (int)ns, chunk, sx, sy, sU, qv, coef);
+  }
+  T2* w = (T2*)(ws + L.wts);
+  dim3 gw(cdiv_i(std::max(1, f.nterm), 128), f.nrhs);
+  k_far_weights<T2><<<gw, 128, 0, st>>>(f, g, coef, mom, w, (int*)(ws + L.status));
+  const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
+  const T* ty = tx + nt;
+  const int* tU = self ? sU : (const int*)(ws + L.trgU);
+  dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
+  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, pot, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                              double* grad, cudaStream_t st) {
+  const bool mixed = p->opts.precision == PFMM_MIXED;
+  switch (p->opts.kernel) {
+    case PFMM_LAPLACE:
+      return mixed ? run_far_direct<float, float2, PFMM_LAPLACE>(p, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_LAPLACE>(p, ws, ns, nt, self, pot, grad, st);
+    case PFMM_MODHELM:
+      return mixed ? run_far_direct<float, float2, PFMM_MODHELM>(p, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_MODHELM>(p, ws, ns, nt, self, pot, grad, st);
+    default:
+      return mixed ? run_far_direct<float, float2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st);
+  }
+}
+
+cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  size_t nr = p->opts.nrhs;
+  if (pot) e = cudaMemsetAsync(pot, 0, nr * p->nout * nt * sizeof(double), st);
+  if (e == cudaSuccess && grad) e = cudaMemsetAsync(grad, 0, nr * 2 * nt * sizeof(double), st);
+  return e;
+}
+
+}  // namespace pfmm

@@ -1,0 +1,569 @@
+// Near-image P2P: u(t_l) += sum over the (2 m0 + 1) x 3 images l_mn of
+// Lambda_near (Sec. 1) and sources j of G(t_l - s_j - l_mn) q_j, pairs at zero
+// distance skipped (Eq. nearfarsplit: this is K^near q).
+//
+// Mixed kernel (k_p2p_mixed): FP32 pair arithmetic.  Coordinates enter as
+// hi/lo float pairs: the target minus the image offset is formed in FP64 once
+// per (target, image) and split, sources carry (x_hi, x_lo, y_hi, y_lo), and
+// dx = (tx_hi - sx_hi) + (tx_lo - sx_lo) is the true difference to FP32
+// rounding even for close pairs in a long cell.  Each source is read from
+// shared memory once and applied to all images (target splits live in
+// registers).  Pair terms are summed in FP32 over 8 sources x all images and
+// those partial sums are added with Kahan compensation; the result is added
+// into the FP64 output.  Logs and reciprocals use the MUFU approximations
+// lg2.approx / rcp.approx (rel. error ~2^-22).
+//
+// FP64 kernel (k_p2p_f64): the same sum in double precision with log(),
+// division and the FP64 Bessel routines.
+#include <algorithm>
+#include <cmath>
+#include "pfmm_impl.h"
+#include "bessel.cuh"
+
+namespace pfmm {
+
+constexpr int kP2PThreads = 128;
+constexpr int kP2PTile = 128;
+constexpr int kP2PSub = 8;
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+struct KahanF {
+  float s, c;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+struct P2PArgs {
+  Geom g;
+  int nt, ns, chunk;
+  int r0, nrhs;          // rhs group start, total rhs
+  const double* trg64;   // [2][nt] canonical
+  const float4* src_hl;  // [ns]
+  const float* qf;       // [nrhs][ncomp][ns]
+  const double* src64;   // [2][ns] (FP64 kernel)
+  const double* qc;      // [nrhs][ncomp][ns] (FP64 kernel)
+  float beta_f;
+  double beta;
+  float lgc;             // log2(r^2) shift (Laplace/Stokes), see below
+  const double* mom;     // FP64 moments: mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y
+  double* pot;
+  double* grad;
+};
+
+// Structure of the mixed kernels.  For each source j the contributions of all
+// near images are first summed WITHOUT the strength (image sums such as
+// L_j = sum_i log2 r_ij^2, Gx_j = sum_i dx_ij / r_ij^2), then multiplied by
+// q_j once per rhs.  The image sums have no sign cancellation; the cancelling
+// sum over sources (zero net charge) then has 9-15x fewer FP32 additions.
+// Potential terms use L_j - nimg c with a per-plan constant c near the mean
+// of log2(r^2) over the near block, so the partial sums stay small: with
+// zero net charge sum_j q_j nimg c cancels while FP32 rounding scales with the
+// size of the partial sums.  The epilogue adds back nimg c sum_j q_j in FP64
+// from the moments (skipped zero-distance pairs contribute 0 to L_j and need
+// no correction).  The Stokes velocity uses the per-source sums
+// L, G1 = sum (dx^2 - dy^2)/r^2 and G2 = sum dx dy / r^2 (Axx = (n + G1)/2,
+// Ayy = (n - G1)/2 with n the images used; the constant isotropic part is
+// added back in FP64 like the log shift).
+// Partial sums over kP2PSub sources are added with Kahan compensation.
+//
+// Laplace/Stokes kernel: two targets per thread packed in float2, so each
+// pair-level FP32 operation is one FFMA2/FADD2/FMUL2 for two pairs; logs and
+// reciprocals on the MUFU pipe (lg2.approx / rcp.approx).
+//
+// Output scaling constants:
+//   Laplace: pot = -(ln2/4pi) sum q log2(r^2); grad = -(1/2pi) sum q (t-s)/r^2
+//   Stokes : u = -(ln2/8pi) [ sum log2(r^2) f - (2/ln2) sum (r.f/r^2) r ]
+//   modhelm: pot = (1/2pi) sum q K0;  grad = -(beta/2pi) sum q K1 (t-s)/r
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+struct Kahan2 {
+  float2 s, c;
+  __device__ __forceinline__ void add(float2 v) {
+    float2 y = add2(v, make_float2(-c.x, -c.y));
+    float2 t = add2(s, y);
+    c = add2(add2(t, make_float2(-s.x, -s.y)), make_float2(-y.x, -y.y));
+    s = t;
+  }
+};
+
+template <int KER, int NIMG, int NR, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
+  static_assert(KER != PFMM_MODHELM, "packed kernel is for Laplace/Stokes");
+  constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
+  constexpr int CENTER = NIMG / 2;
+  constexpr int NA = (KER == PFMM_STOKES) ? 2 : (GRAD ? 3 : 1);
+  __shared__ float4 s_p[kP2PTile];
+  __shared__ float s_q[NR * NC][kP2PTile];
+
+  const int l0 = (blockIdx.x * kP2PThreads + threadIdx.x) * 2;
+  const bool inA = l0 < a.nt, inB = l0 + 1 < a.nt;
+  const int r0 = a.r0 + blockIdx.z * NR;
+  const int nr = min(NR, a.nrhs - r0);
+
+  float2 thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
+  {
+    const int lA = inA ? l0 : 0, lB = inB ? l0 + 1 : lA;
+    const double txA = a.trg64[lA], tyA = a.trg64[a.nt + lA];
+    const double txB = a.trg64[lB], tyB = a.trg64[a.nt + lB];
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      const double ox = a.g.off[i][0], oy = a.g.off[i][1];
+      const double vxA = txA - ox, vyA = tyA - oy, vxB = txB - ox, vyB = tyB - oy;
+      thx[i] = make_float2((float)vxA, (float)vxB);
+      tlx[i] = make_float2((float)(vxA - (double)thx[i].x), (float)(vxB - (double)thx[i].y));
+      thy[i] = make_float2((float)vyA, (float)vyB);
+      tly[i] = make_float2((float)(vyA - (double)thy[i].x), (float)(vyB - (double)thy[i].y));
+    }
+  }
+  Kahan2 K[NR][NA];
+  float2 S[NR][NA];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      K[r][k].s = K[r][k].c = f2(0.f);
+      S[r][k] = f2(0.f);
+    }
+  const float2 nshift = f2(-(float)NIMG * a.lgc);
+  constexpr float kStokesC = -2.0f / 0.69314718055994531f;  // -(1/4pi) / (ln2/8pi)
+
+  const int j0 = blockIdx.y * a.chunk;
+  const int j1 = min(a.ns, j0 + a.chunk);
+  for (int jb = j0; jb < j1; jb += kP2PTile) {
+    const int nb = min(kP2PTile, j1 - jb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
+      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(1e18f, 0.f, 1e18f, 0.f);
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          s_q[r * NC + c][k] = (k < nb && r < nr) ? a.qf[((size_t)(r0 + r) * NC + c) * a.ns + jb + k] : 0.f;
+    }
+    __syncthreads();
+    for (int js = 0; js < nb; js += kP2PSub) {
+#pragma unroll 2
+      for (int jj = js; jj < js + kP2PSub; ++jj) {
+        const float4 p = s_p[jj];
+        const float2 nsxh = f2(-p.x), nsxl = f2(-p.y), nsyh = f2(-p.z), nsyl = f2(-p.w);
+        float2 L = f2(0.f), G1 = f2(0.f), G2 = f2(0.f), cnt = f2((float)NIMG);
+#pragma unroll
+        for (int i = 0; i < NIMG; ++i) {
+          const float2 dx = add2(add2(thx[i], nsxh), add2(tlx[i], nsxl));
+          const float2 dy = add2(add2(thy[i], nsyh), add2(tly[i], nsyl));
+          float2 r2 = fma2(dx, dx, mul2(dy, dy));
+          float2 msk = f2(1.0f);
+          if (i == CENTER) {
+            msk = make_float2(r2.x > 0.f ? 1.f : 0.f, r2.y > 0.f ? 1.f : 0.f);
+            r2 = make_float2(r2.x > 0.f ? r2.x : 1.f, r2.y > 0.f ? r2.y : 1.f);
+            cnt = add2(cnt, add2(msk, f2(-1.0f)));
+          }
+          float2 lg = make_float2(lg2_approx(r2.x), lg2_approx(r2.y));
+          float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+          if (i == CENTER) {
+            lg = mul2(lg, msk);
+            inv = mul2(inv, msk);
+          }
+          L = add2(L, lg);
+          if (KER == PFMM_LAPLACE) {
+            if (GRAD) {
+              G1 = fma2(dx, inv, G1);
+              G2 = fma2(dy, inv, G2);
+            }
+          } else {
+            // G1 = sum (dx^2 - dy^2)/r^2 (= sum cos 2theta, centred), G2 = sum dx dy / r^2
+            const float2 dx2 = mul2(dx, dx);
+            const float2 t = fma2(make_float2(-dy.x, -dy.y), dy, dx2);
+            G1 = fma2(t, inv, G1);
+            G2 = fma2(mul2(dx, inv), dy, G2);
+          }
+        }
+        L = add2(L, nshift);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          if (KER == PFMM_LAPLACE) {
+            const float2 q = f2(s_q[r][jj]);
+            S[r][0] = fma2(q, L, S[r][0]);
+            if (GRAD) {
+              S[r][1 % NA] = fma2(q, G1, S[r][1 % NA]);
+              S[r][2 % NA] = fma2(q, G2, S[r][2 % NA]);
+            }
+          } else {
+            // Axx = (cnt + G1)/2, Ayy = (cnt - G1)/2; the isotropic part C nimg/2 is
+            // moved into the FP64 add-back:  u_x += fx (Lx + C G1/2) + fy C G2,
+            // u_y += fx C G2 + fy (Lx - C G1/2),  Lx = L - nimg c + C (cnt - nimg)/2
+            const float2 fx = f2(s_q[r * NC][jj]), fy = f2(s_q[r * NC + NC - 1][jj]);
+            const float2 Lx = fma2(add2(cnt, f2(-(float)NIMG)), f2(0.5f * kStokesC), L);
+            const float2 h1 = mul2(G1, f2(0.5f * kStokesC)), cxy = mul2(G2, f2(kStokesC));
+            S[r][0] = fma2(fx, add2(Lx, h1), fma2(fy, cxy, S[r][0]));
+            S[r][NA - 1] = fma2(fx, cxy, fma2(fy, add2(Lx, make_float2(-h1.x, -h1.y)), S[r][NA - 1]));
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          K[r][k].add(S[r][k]);
+          S[r][k] = f2(0.f);
+        }
+    }
+  }
+  const double* R = a.g.rot;
+  const double lgc = (double)a.lgc;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool in = h == 0 ? inA : inB;
+    if (!in) continue;
+    const int l = l0 + h;
+    for (int r = 0; r < nr; ++r) {
+      auto val = [&](int k) {
+        const float2 s2 = K[r][k].s, c2 = K[r][k].c;
+        return h == 0 ? (double)s2.x - (double)c2.x : (double)s2.y - (double)c2.y;
+      };
+      if (KER == PFMM_STOKES) {
+        const double cst = -0.69314718055994531 / (8.0 * M_PI);
+        double sx = val(0), sy = val(NA - 1);
+        if (blockIdx.y == 0) {
+          const double add = NIMG * (lgc + 0.5 * (double)kStokesC);
+          sx += add * a.mom[(r0 + r) * 8 + 0];
+          sy += add * a.mom[(r0 + r) * 8 + 1];
+        }
+        const double ux = cst * sx, uy = cst * sy;
+        atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * ux + R[2] * uy);
+        atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * ux + R[3] * uy);
+      } else {
+        const double cp = -0.69314718055994531 / (4.0 * M_PI), cg = -1.0 / (2.0 * M_PI);
+        double sp = val(0);
+        if (blockIdx.y == 0) sp += lgc * NIMG * a.mom[(r0 + r) * 8 + 0];
+        if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, cp * sp);
+        if (GRAD && a.grad) {
+          const double gx = cg * val(1 % NA), gy = cg * val(2 % NA);
+          atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * gx + R[2] * gy);
+          atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * gx + R[3] * gy);
+        }
+      }
+    }
+  }
+}
+
+// Modified Helmholtz mixed kernel: one target per thread, per-source image
+// sums K0s = sum_i K0(beta r_i), K1x = sum_i K1(beta r_i) dx_i / r_i (and y).
+template <int KER, int NIMG, int NR, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(P2PArgs a) {
+  constexpr int CENTER = NIMG / 2;
+  constexpr int NA = GRAD ? 3 : 1;
+  __shared__ float4 s_p[kP2PTile];
+  __shared__ float s_q[NR][kP2PTile];
+  const int l = blockIdx.x * kP2PThreads + threadIdx.x;
+  const bool in = l < a.nt;
+  const int r0 = a.r0 + blockIdx.z * NR;
+  const int nr = min(NR, a.nrhs - r0);
+  float thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
+  {
+    const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      double vx = tx - a.g.off[i][0], vy = ty - a.g.off[i][1];
+      thx[i] = (float)vx;
+      tlx[i] = (float)(vx - (double)thx[i]);
+      thy[i] = (float)vy;
+      tly[i] = (float)(vy - (double)thy[i]);
+    }
+  }
+  KahanF K[NR][NA];
+  float S[NR][NA];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+      K[r][k].s = K[r][k].c = 0.f;
+      S[r][k] = 0.f;
+    }
+  const float beta = a.beta_f;
+  const int j0 = blockIdx.y * a.chunk;
+  const int j1 = min(a.ns, j0 + a.chunk);
+  for (int jb = j0; jb < j1; jb += kP2PTile) {
+    const int nb = min(kP2PTile, j1 - jb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
+      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(1e18f, 0.f, 1e18f, 0.f);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) s_q[r][k] = (k < nb && r < nr) ? a.qf[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
+    }
+    __syncthreads();
+    for (int js = 0; js < nb; js += kP2PSub) {
+#pragma unroll 2
+      for (int jj = js; jj < js + kP2PSub; ++jj) {
+        const float4 p = s_p[jj];
+        float K0s = 0.f, K1x = 0.f, K1y = 0.f;
+#pragma unroll
+        for (int i = 0; i < NIMG; ++i) {
+          const float dx = (thx[i] - p.x) + (tlx[i] - p.y);
+          const float dy = (thy[i] - p.z) + (tly[i] - p.w);
+          float r2 = fmaf(dx, dx, dy * dy);
+          float msk = 1.0f;
+          if (i == CENTER) {
+            msk = (r2 > 0.0f) ? 1.0f : 0.0f;
+            r2 = (r2 > 0.0f) ? r2 : 1.0f;
+          }
+          const float ir = rsqrt_approx(r2);
+          float k0, k1;
+          bes::k01f(beta * r2 * ir, &k0, &k1);
+          K0s = fmaf(k0, msk, K0s);
+          if (GRAD) {
+            const float k1r = k1 * ir * msk;
+            K1x = fmaf(k1r, dx, K1x);
+            K1y = fmaf(k1r, dy, K1y);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const float q = s_q[r][jj];
+          S[r][0] = fmaf(q, K0s, S[r][0]);
+          if (GRAD) {
+            S[r][1 % NA] = fmaf(q, K1x, S[r][1 % NA]);
+            S[r][2 % NA] = fmaf(q, K1y, S[r][2 % NA]);
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+          K[r][k].add(S[r][k]);
+          S[r][k] = 0.f;
+        }
+    }
+  }
+  if (!in) return;
+  const double* R = a.g.rot;
+  const double cp = 1.0 / (2.0 * M_PI), cg = -a.beta / (2.0 * M_PI);
+  for (int r = 0; r < nr; ++r) {
+    if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, cp * K[r][0].value());
+    if (GRAD && a.grad) {
+      const double gx = cg * K[r][1 % NA].value(), gy = cg * K[r][2 % NA].value();
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * gx + R[2] * gy);
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * gx + R[3] * gy);
+    }
+  }
+}
+
+// FP64 reference-precision kernel.
+template <int KER, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_f64(P2PArgs a) {
+  constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
+  __shared__ double s_x[kP2PTile], s_y[kP2PTile];
+  __shared__ double s_q[4][NC][kP2PTile];
+  const int l = blockIdx.x * kP2PThreads + threadIdx.x;
+  const bool in = l < a.nt;
+  const int r0 = a.r0 + blockIdx.z * 4;
+  const int nr = min(4, a.nrhs - r0);
+  const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
+  double acc[4][3];
+  for (int r = 0; r < 4; ++r) acc[r][0] = acc[r][1] = acc[r][2] = 0.0;
+  const int j0 = blockIdx.y * a.chunk;
+  const int j1 = min(a.ns, j0 + a.chunk);
+  for (int jb = j0; jb < j1; jb += kP2PTile) {
+    const int nb = min(kP2PTile, j1 - jb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += kP2PThreads) {
+      s_x[k] = a.src64[jb + k];
+      s_y[k] = a.src64[a.ns + jb + k];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < NC; ++c)
+          s_q[r][c][k] = (r < nr) ? a.qc[((size_t)(r0 + r) * NC + c) * a.ns + jb + k] : 0.0;
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int i = 0; i < a.g.nimg; ++i) {
+      const double ox = tx - a.g.off[i][0], oy = ty - a.g.off[i][1];
+      for (int jj = 0; jj < nb; ++jj) {
+        const double dx = ox - s_x[jj], dy = oy - s_y[jj];
+        const double r2 = dx * dx + dy * dy;
+        if (r2 == 0.0) continue;
+        if (KER == PFMM_LAPLACE) {
+          const double lg = -log(r2) / (4.0 * M_PI);
+          const double f = -1.0 / (2.0 * M_PI * r2);
+          for (int r = 0; r < nr; ++r) {
+            const double q = s_q[r][0][jj];
+            acc[r][0] += q * lg;
+            if (GRAD) {
+              acc[r][1] += q * f * dx;
+              acc[r][2] += q * f * dy;
+            }
+          }
+        } else if (KER == PFMM_STOKES) {
+          const double lg = -log(r2) / (8.0 * M_PI);
+          const double inv = 1.0 / (4.0 * M_PI * r2);
+          for (int r = 0; r < nr; ++r) {
+            const double fx = s_q[r][0][jj], fy = s_q[r][NC - 1][jj];
+            const double s = (dx * fx + dy * fy) * inv;
+            acc[r][0] += lg * fx + s * dx;
+            acc[r][1] += lg * fy + s * dy;
+          }
+        } else {
+          const double rr = sqrt(r2);
+          double k0, k1;
+          bes::k01d(a.beta * rr, &k0, &k1);
+          const double f = -a.beta * k1 / (2.0 * M_PI * rr);
+          for (int r = 0; r < nr; ++r) {
+            const double q = s_q[r][0][jj];
+            acc[r][0] += q * k0 / (2.0 * M_PI);
+            if (GRAD) {
+              acc[r][1] += q * f * dx;
+              acc[r][2] += q * f * dy;
+            }
+          }
+        }
+      }
+    }
+  }
+  if (!in) return;
+  const double* R = a.g.rot;
+  for (int r = 0; r < nr; ++r) {
+    if (KER == PFMM_STOKES) {
+      atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * acc[r][0] + R[2] * acc[r][1]);
+      atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * acc[r][0] + R[3] * acc[r][1]);
+    } else {
+      if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, acc[r][0]);
+      if (GRAD && a.grad) {
+        atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * acc[r][1] + R[2] * acc[r][2]);
+        atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * acc[r][1] + R[3] * acc[r][2]);
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+static inline int cdivl(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <int KER, int NIMG, int NR>
+static void launch_mixed(P2PArgs a, bool grad, dim3 grid, cudaStream_t st) {
+  ++g_launches;
+  if constexpr (KER == PFMM_MODHELM) {
+    if (grad)
+      k_p2p_mixed_mh<KER, NIMG, NR, true><<<grid, kP2PThreads, 0, st>>>(a);
+    else
+      k_p2p_mixed_mh<KER, NIMG, NR, false><<<grid, kP2PThreads, 0, st>>>(a);
+  } else {
+    // two targets per thread (grid.x already counts 2 * kP2PThreads targets per block)
+    if (grad)
+      k_p2p_mixed<KER, NIMG, NR, true><<<grid, kP2PThreads, 0, st>>>(a);
+    else
+      k_p2p_mixed<KER, NIMG, NR, false><<<grid, kP2PThreads, 0, st>>>(a);
+  }
+}
+
+template <int KER, int NIMG>
+static void dispatch_nr(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaStream_t st) {
+  // rhs processed in groups of NR in {4, 2, 1}
+  int r = 0;
+  while (r < nrhs) {
+    int left = nrhs - r;
+    a.r0 = r;
+    if (left >= 4) {
+      int ng = left / 4;
+      launch_mixed<KER, NIMG, 4>(a, grad, dim3(ntb, nsc, ng), st);
+      r += 4 * ng;
+    } else if (left >= 2) {
+      launch_mixed<KER, NIMG, 2>(a, grad, dim3(ntb, nsc, 1), st);
+      r += 2;
+    } else {
+      launch_mixed<KER, NIMG, 1>(a, grad, dim3(ntb, nsc, 1), st);
+      r += 1;
+    }
+  }
+}
+
+template <int KER>
+static void dispatch_img(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaStream_t st) {
+  // m0 <= 2 after lattice reduction (|xi| <= d/2), so 9 or 15 images
+  if (a.g.nimg == 9)
+    dispatch_nr<KER, 9>(a, grad, nrhs, ntb, nsc, st);
+  else
+    dispatch_nr<KER, 15>(a, grad, nrhs, ntb, nsc, st);
+}
+
+cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
+                       bool accumulate, cudaStream_t st) {
+  (void)accumulate;
+  const Layout& L = p->lay;
+  P2PArgs a{};
+  a.g = p->geom;
+  a.nt = (int)nt;
+  a.ns = (int)ns;
+  a.nrhs = p->opts.nrhs;
+  a.trg64 = self ? (const double*)(ws + L.src64) : (const double*)(ws + L.trg64);
+  a.src_hl = (const float4*)(ws + L.srchl);
+  a.qf = (const float*)(ws + L.qf);
+  a.src64 = (const double*)(ws + L.src64);
+  a.qc = (const double*)(ws + L.qc);
+  a.beta = p->far.beta;
+  a.beta_f = (float)p->far.beta;
+  a.pot = pot;
+  a.grad = grad;
+  a.mom = (const double*)(ws + L.moments);
+  {
+    // mean of log2(r^2) over a disc with the near block's area
+    const Geom& g = p->geom;
+    a.lgc = (float)(std::log2(g.nimg * g.d * g.eta / M_PI) - 1.0 / std::log(2.0));
+  }
+  const bool mixed = p->opts.precision == PFMM_MIXED;
+  const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread
+  const int ntb = cdivl(nt, kP2PThreads * (packed ? 2 : 1));
+  const int nrg = mixed ? 1 : cdivl(a.nrhs, 4);
+  // split the sources so that the grid holds >= ~32 blocks per SM
+  int nsc = std::max(1, std::min(cdivl(ns, kP2PTile), cdivl(32 * 152, (int64_t)ntb * nrg)));
+  a.chunk = cdivl(cdivl(ns, nsc), kP2PTile) * kP2PTile;
+  nsc = cdivl(ns, a.chunk);
+  const bool g = grad != nullptr;
+  g_launches = mixed ? 0 : 1;
+  if (mixed) {
+    switch (p->opts.kernel) {
+      case PFMM_LAPLACE: dispatch_img<PFMM_LAPLACE>(a, g, a.nrhs, ntb, nsc, st); break;
+      case PFMM_MODHELM: dispatch_img<PFMM_MODHELM>(a, g, a.nrhs, ntb, nsc, st); break;
+      default: dispatch_img<PFMM_STOKES>(a, false, a.nrhs, ntb, nsc, st); break;
+    }
+  } else {
+    dim3 grid(ntb, nsc, nrg);
+    a.r0 = 0;
+    switch (p->opts.kernel) {
+      case PFMM_LAPLACE:
+        if (g) k_p2p_f64<PFMM_LAPLACE, true><<<grid, kP2PThreads, 0, st>>>(a);
+        else k_p2p_f64<PFMM_LAPLACE, false><<<grid, kP2PThreads, 0, st>>>(a);
+        break;
+      case PFMM_MODHELM:
+        if (g) k_p2p_f64<PFMM_MODHELM, true><<<grid, kP2PThreads, 0, st>>>(a);
+        else k_p2p_f64<PFMM_MODHELM, false><<<grid, kP2PThreads, 0, st>>>(a);
+        break;
+      default: k_p2p_f64<PFMM_STOKES, false><<<grid, kP2PThreads, 0, st>>>(a); break;
+    }
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pfmm

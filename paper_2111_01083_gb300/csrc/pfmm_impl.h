@@ -1,0 +1,98 @@
+// Internal declarations shared by the host plan code and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <cuda_runtime.h>
+#include "../../include/pfmm.h"
+
+namespace pfmm {
+
+constexpr int kMaxNear = 32;      // (2 m0 + 1) * 3 images; m0 <= 3 after reduction
+constexpr int kStatusWords = 8;   // status word region (ints)
+
+// device status bits (combined with atomicOr; mapped to pfmm_status by the host)
+enum : int { ST_NONFINITE = 1, ST_NOT_NEUTRAL = 2, ST_TIMEOUT = 4 };
+
+// Geometry of the canonical cell, passed by value to kernels.
+struct Geom {
+  double d, xi, eta;      // e1 = (d, 0), e2 = (xi, eta)
+  double rot[4];          // canonical = rot * input (row-major)
+  double ainv[4];         // fractional coordinates u = ainv * canonical
+  int m0;
+  int nimg;               // (2 m0 + 1) * 3
+  double off[kMaxNear][2];// image offsets l_mn = m e1 + n e2 (canonical)
+  int center;             // index of the (0, 0) image in off[]
+};
+
+// Far-field parameters (direct path).  Terms are ordered
+//   [ south m = m_lo..M | north m = m_lo..M | west n = 0..Nq-1 | east n = 0..Nq-1 ]
+// with m_lo = 0 if mode0 else 1.
+struct Far {
+  int kernel;        // pfmm_kernel
+  double beta;
+  int M, mode0, Nq;
+  int nsn;           // terms per south/north block = M - m_lo + 1
+  int nterm;         // 2 nsn + 2 Nq
+  int nrhs;
+  int nch;           // coefficient channels per rhs: 1 (scalar) or 4 (Stokes: a_x, a_y, b_x, b_y)
+  const double* nodes;  // device [Nq][2] (lambda_n, w_n), in workspace
+};
+
+// Workspace layout (byte offsets from the workspace base, all 256-aligned).
+struct Layout {
+  size_t status, moments, nodes;
+  size_t src64, trg64;     // double [2][n] canonical coordinates
+  size_t srcf, trgf;       // float  [2][n] canonical coordinates (mixed far field)
+  size_t srcU, trgU;       // int32 [n] fixed-point x/d phase (mixed south/north)
+  size_t srchl;            // float4 [ns] (x_hi, x_lo, y_hi, y_lo) for P2P (mixed)
+  size_t qc;               // strengths in canonical frame: double [nrhs][ncomp][ns]
+  size_t qf;               // float copy of qc (mixed P2P and far field)
+  size_t coef;             // double2 [nrhs][nch][nterm]
+  size_t wts;              // weights for evaluation: double2 or float2 [nrhs][nwch][nterm]
+  size_t nufft;            // NUFFT scratch (grids, spectra)
+  size_t stage;            // host-staging region (pfmm_execute_host only)
+  size_t total, total_host;
+};
+
+}  // namespace pfmm
+
+// pfmm_plan is an opaque C type; its definition is here so that all
+// translation units of the library see the same layout.
+struct pfmm_plan {
+  pfmm_opts opts;
+  pfmm::Geom geom;
+  pfmm::Far far;
+  int64_t ns_max, nt_max;
+  int nout;                 // output components per rhs for 'pot' (1 scalar, 2 Stokes)
+  int ncomp;                // strength components (1 scalar, 2 Stokes)
+  int path;                 // resolved path
+  // west/east quadrature (host copy)
+  int Nq;
+  double* nodes_h;          // [Nq][2]
+  // NUFFT parameters
+  int n_gl, nf, nufft_w;
+  double es_beta;
+  double* gl_h;             // [n_gl][2] (ybar_n, sigma_n) on [-eta/2, eta/2]
+  double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
+  pfmm::Layout lay;
+  // tracing / bookkeeping
+  bool prof;
+  cudaEvent_t ev[4];
+  int nlaunch;
+  int64_t npairs;
+};
+
+namespace pfmm {
+// kernels.cu entry points (host-side launchers)
+cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q,
+                        int64_t nt, const double* trg, bool self, cudaStream_t st);
+cudaError_t launch_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
+                              double* pot, double* grad, cudaStream_t st);
+cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
+                             double* pot, double* grad, cudaStream_t st);
+cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
+                       double* pot, double* grad, bool accumulate, cudaStream_t st);
+// kernels launched by the most recent launch_* call (set by each launcher)
+extern thread_local int g_launches;
+cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);
+}  // namespace pfmm

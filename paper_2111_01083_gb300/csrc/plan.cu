@@ -1,0 +1,488 @@
+// Host side of the library: plan construction (canonical cell, near block,
+// modes, west/east quadrature, NUFFT sizes), workspace layout, argument
+// validation and the order of kernel launches.  No device memory is ever
+// allocated here.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "pfmm_impl.h"
+
+using namespace pfmm;
+
+namespace pfmm {
+thread_local int g_launches = 0;
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+pfmm_status fail(pfmm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Sec. 1: canonical cell.  Lagrange-Gauss reduction (same lattice), longer
+// reduced vector -> e1 rotated onto +x, shorter -> e2 flipped to eta > 0.
+bool canonicalize(const double e1[2], const double e2[2], Geom* g) {
+  double b1[2] = {e1[0], e1[1]}, b2[2] = {e2[0], e2[1]};
+  auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1]; };
+  double cross = b1[0] * b2[1] - b1[1] * b2[0];
+  if (!std::isfinite(cross) || std::fabs(cross) <= 1e-14 * (dot(b1, b1) + dot(b2, b2))) return false;
+  for (int it = 0; it < 200; ++it) {
+    if (dot(b1, b1) > dot(b2, b2)) std::swap(b1, b2);
+    double mu = std::floor(dot(b1, b2) / dot(b1, b1) + 0.5);
+    if (mu == 0.0) break;
+    b2[0] -= mu * b1[0];
+    b2[1] -= mu * b1[1];
+  }
+  const double* a = b2;  // longer
+  const double* b = b1;  // shorter
+  double d = std::hypot(a[0], a[1]);
+  double c = a[0] / d, s = a[1] / d;
+  g->rot[0] = c; g->rot[1] = s; g->rot[2] = -s; g->rot[3] = c;
+  double bx = c * b[0] + s * b[1], by = -s * b[0] + c * b[1];
+  if (by < 0) { bx = -bx; by = -by; }
+  g->d = d; g->xi = bx; g->eta = by;
+  // fractional coordinates: canonical = [[d, xi],[0, eta]] u
+  g->ainv[0] = 1.0 / d; g->ainv[1] = -bx / (d * by); g->ainv[2] = 0.0; g->ainv[3] = 1.0 / by;
+  return true;
+}
+
+// Proof after Eq. pylw02: west/east images need x - x' - m d - n xi >= margin > 0;
+// the smallest gap over the parallelogram is m0 d - 2|xi|.  The paper uses
+// margin = d; here margin = d/4 (any positive gap keeps the west/east
+// integrands decaying; a smaller gap only costs quadrature nodes), so m0 = 1
+// unless |xi| > 3d/8 and the near block stays 3 x 3 cells for most cells.
+int choose_m0(double d, double xi) {
+  return std::max(1, (int)std::ceil((0.25 * d + 2.0 * std::fabs(xi)) / d - 1e-12));
+}
+
+// Eq. mpk0s.
+int mpk0s(double d, double eta, double eps) {
+  double r = 2.0 * M_PI * eta / d;
+  return (int)std::ceil((d / (2.0 * M_PI * eta)) * std::log(1.0 / ((1.0 - std::exp(-r)) * eps)));
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+    if (n == 1) { p1 = z; p0 = 1.0; }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[n - 1 - i] = z;
+    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// West/east quadrature for int_0^inf (.) d lambda (own composite GL rule in
+// lambda' = lambda d): panels of width 2, 8/12/16 points for tol >= 1e-7 /
+// >= 1e-11 / smaller, dyadic panels toward 0 when 0 < beta d < 2, truncated
+// where exp(-kappa' x_min') < tol/10 with x_min' = (m0 d - 2|xi|)/d.
+void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vector<double>& nodes) {
+  nodes.clear();
+  double xmin = (g.m0 * g.d - 2.0 * std::fabs(g.xi)) / g.d;
+  double bt = (kernel == PFMM_MODHELM) ? beta * g.d : 0.0;
+  double top = std::log(10.0 / tol) / xmin;
+  if (top <= bt) return;
+  double lmax = std::sqrt(top * top - bt * bt);
+  int npts = tol >= 1e-7 ? 8 : (tol >= 1e-11 ? 12 : 16);
+  std::vector<double> edges{0.0};
+  if (bt > 0 && bt < 2.0) {
+    for (double e = bt / 8; e < 2.0 && e < lmax; e *= 2) edges.push_back(e);
+  }
+  double e = edges.back();
+  while (e < lmax - 1e-12) { e = std::min(lmax, e + 2.0); edges.push_back(e); }
+  std::vector<double> gx, gw;
+  gauss_legendre(npts, gx, gw);
+  for (size_t i = 0; i + 1 < edges.size(); ++i) {
+    double a = edges[i], b = edges[i + 1];
+    for (int k = 0; k < npts; ++k) {
+      nodes.push_back((0.5 * (b - a) * (gx[k] + 1.0) + a) / g.d);
+      nodes.push_back(0.5 * (b - a) * gw[k] / g.d);
+    }
+  }
+}
+
+// Exponential-of-semicircle kernel phi(z) = exp(b (sqrt(1 - z^2) - 1)), |z| <= 1,
+// and its Fourier transform phihat(k) = int_{-1}^{1} phi(z) cos(k z) dz by
+// Gauss-Legendre quadrature (the kernel is from the NUFFT reference the paper
+// cites for its NUFFTs).
+double es_phihat(double b, double k) {
+  static thread_local std::vector<double> x, w;
+  if (x.size() != 96) gauss_legendre(96, x, w);
+  double s = 0.0;
+  for (int i = 0; i < 96; ++i) s += w[i] * std::exp(b * (std::sqrt(1.0 - x[i] * x[i]) - 1.0)) * std::cos(k * x[i]);
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pfmm_last_error(void) { return g_err.c_str(); }
+const char* pfmm_version(void) { return "pfmm-gb300 0.1 (sm_103a)"; }
+
+pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max, pfmm_plan** out) {
+  if (!o || !out) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (o->kernel < 0 || o->kernel > 2) return fail(PFMM_ERR_INVALID_ARG, "bad kernel %d", o->kernel);
+  if (o->precision < 0 || o->precision > 1) return fail(PFMM_ERR_INVALID_ARG, "bad precision %d", o->precision);
+  if (o->path < 0 || o->path > 2) return fail(PFMM_ERR_INVALID_ARG, "bad path %d", o->path);
+  if (o->nrhs < 1 || o->nrhs > 64) return fail(PFMM_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
+  if (ns_max < 0 || nt_max < 0 || ns_max > (int64_t(1) << 31) || nt_max > (int64_t(1) << 31))
+    return fail(PFMM_ERR_INVALID_ARG, "ns_max/nt_max out of range");
+  if (!(o->tol >= 1e-14 && o->tol <= 1e-2)) return fail(PFMM_ERR_TOLERANCE, "tol must be in [1e-14, 1e-2]");
+  if (o->kernel == PFMM_MODHELM && !(o->beta > 0 && std::isfinite(o->beta)))
+    return fail(PFMM_ERR_INVALID_ARG, "beta must be > 0 for the modified Helmholtz kernel");
+  if ((o->flags & PFMM_FAR_ONLY) && (o->flags & PFMM_NEAR_ONLY))
+    return fail(PFMM_ERR_INVALID_ARG, "FAR_ONLY and NEAR_ONLY are exclusive");
+  if (o->nufft_w != 0 && (o->nufft_w < 2 || o->nufft_w > 16)) return fail(PFMM_ERR_INVALID_ARG, "nufft_w in [2,16]");
+  if (o->n_gl != 0 && (o->n_gl < 4 || o->n_gl > 32)) return fail(PFMM_ERR_INVALID_ARG, "n_gl in [4,32]");
+
+  Geom g{};
+  if (!canonicalize(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate lattice vectors");
+  g.m0 = choose_m0(g.d, g.xi);
+  if ((2 * g.m0 + 1) * 3 > kMaxNear) return fail(PFMM_ERR_INTERNAL, "near block too large");
+  g.nimg = 0;
+  for (int n = -1; n <= 1; ++n)
+    for (int m = -g.m0; m <= g.m0; ++m) {
+      if (m == 0 && n == 0) g.center = g.nimg;
+      g.off[g.nimg][0] = m * g.d + n * g.xi;
+      g.off[g.nimg][1] = n * g.eta;
+      ++g.nimg;
+    }
+
+  pfmm_plan* p = new pfmm_plan();
+  p->opts = *o;
+  p->geom = g;
+  p->ns_max = ns_max;
+  p->nt_max = nt_max;
+  p->ncomp = (o->kernel == PFMM_STOKES) ? 2 : 1;
+  p->nout = p->ncomp;
+
+  // ---- south/north modes (Eq. mpk0s with eps = tol/10; for beta > 0 modes
+  // whose per-unit-charge bound e^{-chi eta}/(d chi (1 - e^{-chi eta})) is below
+  // tol/10 are dropped from the top: chi_m grows with m, so the bound decreases).
+  double eps = o->tol * 0.1;
+  int M = mpk0s(g.d, g.eta, eps);
+  // m = 0 is a regular term only for modhelm; for Laplace/Stokes it is the
+  // moment term -(1/(2 d eta)) y sum q y' (Eq. phis3, Eq. pss0) added separately.
+  int mode0 = (o->kernel == PFMM_MODHELM) ? 1 : 0;
+  if (o->kernel == PFMM_MODHELM) {
+    auto bound = [&](int m) {
+      double al = 2 * M_PI * m / g.d, chi = std::sqrt(al * al + o->beta * o->beta);
+      double e = std::exp(-chi * g.eta);
+      return e / (g.d * chi * (1 - e));
+    };
+    while (M >= 1 && bound(M) < eps) --M;
+    if (bound(0) < eps) { mode0 = 0; M = 0; }
+  }
+  Far& f = p->far;
+  f.kernel = o->kernel;
+  f.beta = (o->kernel == PFMM_MODHELM) ? o->beta : 0.0;
+  f.M = M;
+  f.mode0 = mode0;
+  f.nsn = mode0 ? (M + 1) : M;
+  f.nrhs = o->nrhs;
+  f.nch = (o->kernel == PFMM_STOKES) ? 4 : 1;
+
+  std::vector<double> nodes;
+  we_quadrature(g, o->kernel, f.beta, o->tol, nodes);
+  p->Nq = (int)(nodes.size() / 2);
+  f.Nq = p->Nq;
+  f.nterm = 2 * f.nsn + 2 * f.Nq;
+  p->nodes_h = (double*)std::malloc(std::max<size_t>(1, nodes.size()) * sizeof(double));
+  if (!nodes.empty()) std::memcpy(p->nodes_h, nodes.data(), nodes.size() * sizeof(double));
+
+  // ---- NUFFT parameters (Sec. 6): GL lines, ES width, fine grid (sigma = 2,
+  // power of two for the radix-2 FFT).
+  p->n_gl = o->n_gl ? o->n_gl : (o->tol >= 1e-7 ? 8 : 16);
+  int w = o->nufft_w ? o->nufft_w : std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / o->tol)) + 2));
+  p->nufft_w = w;
+  p->es_beta = 2.30 * w;
+  int nf = 16;
+  while (nf < 2 * (2 * M + 1) || nf < 2 * w) nf *= 2;
+  p->nf = nf;
+  int path = o->path;
+  if (path == PFMM_PATH_AUTO) path = (M >= 64 && o->kernel == PFMM_LAPLACE) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+  if (o->kernel != PFMM_LAPLACE && path == PFMM_PATH_NUFFT) {
+    delete p;
+    return fail(PFMM_ERR_INVALID_ARG, "the NUFFT path is implemented for the Laplace kernel");
+  }
+  if (M == 0) path = PFMM_PATH_DIRECT;
+  p->path = path;
+  {
+    std::vector<double> gx, gw;
+    gauss_legendre(p->n_gl, gx, gw);
+    p->gl_h = (double*)std::malloc(2 * p->n_gl * sizeof(double));
+    for (int i = 0; i < p->n_gl; ++i) {
+      double s = 1.0;  // barycentric weight 1/prod_{j != i}(t_i - t_j) (Eq. baryweights), scaled node
+      for (int j = 0; j < p->n_gl; ++j)
+        if (j != i) s /= (gx[i] - gx[j]);
+      p->gl_h[2 * i] = 0.5 * g.eta * gx[i];
+      p->gl_h[2 * i + 1] = s;
+    }
+    p->phihat_h = (double*)std::malloc((M + 1) * sizeof(double));
+    for (int m = 0; m <= M; ++m) p->phihat_h[m] = es_phihat(p->es_beta, 2.0 * M_PI * m * (w * 0.5) / nf);
+  }
+
+  // ---- workspace layout
+  Layout& L = p->lay;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t r = off; off = align256(off + std::max<size_t>(bytes, 1)); return r; };
+  int nrhs = o->nrhs;
+  L.status = take(kStatusWords * sizeof(int));
+  L.moments = take(nrhs * 8 * sizeof(double));
+  L.nodes = take(std::max(1, p->Nq) * 2 * sizeof(double) + (p->n_gl * 2 + (M + 1)) * sizeof(double));
+  L.src64 = take(2 * ns_max * sizeof(double));
+  L.trg64 = take(2 * nt_max * sizeof(double));
+  L.srcf = take(2 * ns_max * sizeof(float));
+  L.trgf = take(2 * nt_max * sizeof(float));
+  L.srcU = take(ns_max * sizeof(int));
+  L.trgU = take(nt_max * sizeof(int));
+  L.srchl = take(ns_max * 4 * sizeof(float));
+  L.qc = take((size_t)nrhs * p->ncomp * ns_max * sizeof(double));
+  L.qf = take((size_t)nrhs * p->ncomp * ns_max * sizeof(float));
+  L.coef = take((size_t)nrhs * f.nch * std::max(1, f.nterm) * 2 * sizeof(double));
+  L.wts = take((size_t)nrhs * 4 * std::max(1, f.nterm) * 2 * sizeof(double));
+  size_t nuf = 0;
+  if (path == PFMM_PATH_NUFFT) {
+    // fine grids [n_gl][nrhs][nf] complex (float2 for mixed, double2 for fp64)
+    // x2 (spread grid + evaluation grids for pot, d/dx, d/dy -> 3 channels)
+    size_t cplx = (o->precision == PFMM_FP64) ? 16 : 8;
+    nuf = (size_t)p->n_gl * nrhs * nf * cplx * 4 + (size_t)p->n_gl * nrhs * (2 * M + 1) * 16;
+  }
+  L.nufft = take(nuf);
+  L.total = off;
+  size_t ncq = (size_t)nrhs * p->ncomp;
+  L.stage = off;
+  size_t stage = 2 * ns_max * 8 + 2 * nt_max * 8 + ncq * ns_max * 8 + (size_t)nrhs * p->nout * nt_max * 8 +
+                 (size_t)nrhs * 2 * nt_max * 8 + 5 * 256;
+  L.total_host = off + stage;
+  f.nodes = nullptr;
+  *out = p;
+  return PFMM_OK;
+}
+
+void pfmm_plan_destroy(pfmm_plan* p) {
+  if (!p) return;
+  if (p->prof)
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
+  std::free(p->nodes_h);
+  std::free(p->gl_h);
+  std::free(p->phihat_h);
+  delete p;
+}
+
+pfmm_status pfmm_workspace_size(const pfmm_plan* p, size_t* bytes) {
+  if (!p || !bytes) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  *bytes = p->lay.total;
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_workspace_size_host(const pfmm_plan* p, size_t* bytes) {
+  if (!p || !bytes) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  *bytes = p->lay.total_host;
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_plan_describe(const pfmm_plan* p, pfmm_plan_desc* d) {
+  if (!p || !d) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  d->d = p->geom.d; d->xi = p->geom.xi; d->eta = p->geom.eta;
+  for (int i = 0; i < 4; ++i) d->rot[i] = p->geom.rot[i];
+  d->m0 = p->geom.m0;
+  d->M = p->far.M;
+  d->mode0 = (p->opts.kernel == PFMM_MODHELM) ? p->far.mode0 : 1;
+  d->Nq = p->Nq;
+  d->path = p->path;
+  d->n_gl = p->n_gl; d->nf = p->nf; d->nufft_w = p->nufft_w; d->es_beta = p->es_beta;
+  d->nlaunch = p->nlaunch;
+  d->npairs = p->npairs;
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_profile_enable(pfmm_plan* p, int on) {
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (on && !p->prof) {
+    for (int i = 0; i < 4; ++i) {
+      cudaError_t e = cudaEventCreate(&p->ev[i]);
+      if (e != cudaSuccess) {
+        for (int k = 0; k < i; ++k) cudaEventDestroy(p->ev[k]);
+        return fail(PFMM_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+      }
+    }
+    p->prof = true;
+  } else if (!on && p->prof) {
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
+    p->prof = false;
+  }
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_profile_read(pfmm_plan* p, float* ms, int n) {
+  if (!p || !ms || n < 0) return fail(PFMM_ERR_INVALID_ARG, "bad argument");
+  if (!p->prof) return fail(PFMM_ERR_INVALID_ARG, "profiling not enabled");
+  cudaError_t e = cudaEventSynchronize(p->ev[3]);
+  if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+  for (int i = 0; i < n && i < 3; ++i) {
+    e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
+  }
+  return PFMM_OK;
+}
+
+static pfmm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(PFMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pfmm_status pfmm_execute(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
+                         const double* q, int64_t nt, const double* trg, double* pot, double* grad,
+                         void* stream) {
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (ns < 0 || nt < 0 || ns > p->ns_max || nt > p->nt_max)
+    return fail(PFMM_ERR_INVALID_ARG, "ns=%lld nt=%lld outside plan maxima (%lld, %lld)", (long long)ns,
+                (long long)nt, (long long)p->ns_max, (long long)p->nt_max);
+  if (!workspace || ws_bytes < p->lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
+  bool stokes = p->opts.kernel == PFMM_STOKES;
+  if (stokes && grad) return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for the Stokes kernel");
+  if (p->opts.flags & PFMM_NO_GRAD) grad = nullptr;
+  if (nt > 0 && !pot && !grad) return fail(PFMM_ERR_INVALID_ARG, "no output requested");
+  if (nt > 0 && !trg) return fail(PFMM_ERR_INVALID_ARG, "NULL targets");
+  if (ns > 0 && (!src || !q)) return fail(PFMM_ERR_INVALID_ARG, "NULL sources/strengths");
+  bool self = (trg == src) && (nt == ns);
+  if (trg == src && nt != ns) return fail(PFMM_ERR_INVALID_ARG, "targets alias sources but nt != ns");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  cudaError_t e;
+  // clear status, moments and coefficient accumulators; upload tables
+  e = cudaMemsetAsync(ws + p->lay.status, 0, p->lay.nodes - p->lay.status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  e = cudaMemsetAsync(ws + p->lay.coef, 0, p->lay.wts - p->lay.coef, st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  {
+    size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
+    if (p->Nq > 0) {
+      e = cudaMemcpyAsync(ws + p->lay.nodes, p->nodes_h, p->Nq * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "upload nodes");
+    }
+    e = cudaMemcpyAsync(ws + p->lay.nodes + nb, p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload gl");
+    e = cudaMemcpyAsync(ws + p->lay.nodes + nb + p->n_gl * 2 * sizeof(double), p->phihat_h,
+                        (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload phihat");
+  }
+  p->nlaunch = 0;
+  p->npairs = 0;
+  auto rec = [&](int i) { if (p->prof) cudaEventRecord(p->ev[i], st); };
+  rec(0);
+  if (nt == 0) {
+    rec(1); rec(2); rec(3);
+    return PFMM_OK;
+  }
+  if (ns > 0) {
+    e = launch_prep(p, ws, ns, src, q, nt, trg, self, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
+    p->nlaunch += g_launches;
+  }
+  rec(1);
+  unsigned fl = p->opts.flags;
+  bool do_far = !(fl & PFMM_NEAR_ONLY) && ns > 0;
+  bool do_near = !(fl & PFMM_FAR_ONLY) && ns > 0;
+  if (do_far) {
+    e = (p->path == PFMM_PATH_NUFFT) ? launch_far_nufft(p, ws, ns, nt, self, pot, grad, st)
+                                     : launch_far_direct(p, ws, ns, nt, self, pot, grad, st);
+    if (e != cudaSuccess) return cuda_fail(e, "far-field kernels");
+    p->nlaunch += g_launches;
+  } else {
+    e = launch_zero_out(p, nt, pot, grad, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zero outputs");
+  }
+  rec(2);
+  if (do_near) {
+    e = launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, "p2p kernel");
+    p->nlaunch += g_launches;
+    p->npairs = (int64_t)ns * nt * p->geom.nimg;
+  }
+  rec(3);
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_execute_host(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
+                              const double* q, int64_t nt, const double* trg, double* pot, double* grad,
+                              void* stream) {
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (!workspace || ws_bytes < p->lay.total_host || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total_host);
+  if (ns < 0 || nt < 0 || ns > p->ns_max || nt > p->nt_max) return fail(PFMM_ERR_INVALID_ARG, "sizes");
+  if (p->opts.kernel == PFMM_STOKES && grad) return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for Stokes");
+  if (p->opts.flags & PFMM_NO_GRAD) grad = nullptr;
+  bool self = (trg == src) && (nt == ns);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = (char*)workspace + p->lay.stage;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* r = base + off; off = align256(off + bytes); return r; };
+  int nrhs = p->opts.nrhs;
+  double* d_src = (double*)take(2 * ns * 8);
+  double* d_trg = self ? d_src : (double*)take(2 * nt * 8);
+  double* d_q = (double*)take((size_t)nrhs * p->ncomp * ns * 8);
+  double* d_pot = pot ? (double*)take((size_t)nrhs * p->nout * nt * 8) : nullptr;
+  double* d_grad = grad ? (double*)take((size_t)nrhs * 2 * nt * 8) : nullptr;
+  cudaError_t e = cudaSuccess;
+  if (ns) e = cudaMemcpyAsync(d_src, src, 2 * ns * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !self && nt) e = cudaMemcpyAsync(d_trg, trg, 2 * nt * 8, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && ns) e = cudaMemcpyAsync(d_q, q, (size_t)nrhs * p->ncomp * ns * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "stage inputs");
+  pfmm_status s = pfmm_execute(p, workspace, p->lay.total, ns, d_src, d_q, nt, d_trg, d_pot, d_grad, stream);
+  if (s != PFMM_OK) return s;
+  if (pot) e = cudaMemcpyAsync(pot, d_pot, (size_t)nrhs * p->nout * nt * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, d_grad, (size_t)nrhs * 2 * nt * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "read back outputs");
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_get_status(pfmm_plan* p, void* workspace, void* stream) {
+  if (!p || !workspace) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int h[kStatusWords];
+  cudaError_t e = cudaMemcpyAsync(h, (char*)workspace + p->lay.status, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  e = cudaMemsetAsync((char*)workspace + p->lay.status, 0, sizeof h, st);
+  if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  if (h[0] & ST_NONFINITE) return fail(PFMM_ERR_NONFINITE, "non-finite coordinates or strengths");
+  if (h[0] & ST_TIMEOUT) return fail(PFMM_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h[0] & ST_NOT_NEUTRAL) return fail(PFMM_ERR_NOT_NEUTRAL, "net charge / net force is not zero");
+  return PFMM_OK;
+}
+
+}  // extern "C"

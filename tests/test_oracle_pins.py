@@ -329,7 +329,8 @@ def test_canonicalization_rules():
     assert abs(c["d"] - 2.0) < 1e-15 and abs(c["eta"] - 1.0) < 1e-15 and abs(c["xi"]) < 1e-15
     c = lattice.canonicalize((1.0, 0.0), (0.3, 0.8))
     assert (c["d"], c["xi"], c["eta"]) == (1.0, 0.3, 0.8)
-    assert lattice.choose_m0(1.0, 0.3) == 2 and lattice.choose_m0(16.0, 0.0) == 1
+    assert lattice.choose_m0(1.0, 0.3) == 1 and lattice.choose_m0(16.0, 0.0) == 1
+    assert lattice.choose_m0(1.0, 0.4) == 2 and lattice.choose_m0(1.0, 0.3, margin_frac=1.0) == 2
     c = lattice.canonicalize((1.0, 0.0), (5.3, 0.8))  # reduces xi to 0.3
     assert abs(c["xi"] - 0.3) < 1e-12 and abs(c["eta"] - 0.8) < 1e-12
     w = lattice.wrap(np.array([[0.5, -0.5, 1.7], [0.0, 0.0, 0.2]]), 1.0, 0.0, 1.0)
