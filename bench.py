@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--path", default=None, help="override far-field path (direct|nufft)")
     ap.add_argument("--skip-fp64", action="store_true", help="skip the FP64-path comparison run")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--scale", type=float, default=1.0, help="scale point counts (profiling on a small case)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
 
@@ -207,7 +209,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    w = workloads.make(args.workload)
+    w = workloads.make(args.workload, scale=args.scale)
     cfg = dict(workloads.CONFIGS[args.workload])
     path = args.path or cfg.get("path", "auto")
     kernel = w["kernel"]
@@ -327,7 +329,7 @@ def main():
             "peak_basis": "MUFU lg2+rcp per pair; measured 28.4 MUFU/clk/SM x 152 SMs x 2070 MHz",
             "launch_ms": p2p, "share_of_step": p2p / ms}
     cpu = None
-    if world == 1:
+    if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
             ot = oracle_time(args.workload)
             cpu = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
@@ -337,7 +339,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "targets+sources/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
-        "config": {"workload": args.workload, "kernel": kernel, "e1": list(w["e1"]), "e2": list(w["e2"]),
+        "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
+                   "kernel": kernel, "e1": list(w["e1"]), "e2": list(w["e2"]),
                    "n_sources": ns, "n_targets": nt, "targets_are_sources": self_t,
                    "dist": cfg.get("dist"), "tol": cfg["tol"], "path": ["direct", "direct", "nufft"][desc["path"]],
                    "nufft_w": desc["nufft_w"], "n_gl": desc["n_gl"], "M": desc["M"], "Nq": desc["Nq"],
