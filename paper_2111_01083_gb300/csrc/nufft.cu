@@ -1,7 +1,383 @@
-// NUFFT far-field path (Sec. 6, Eqs. fastanterp, fastinterp).
+// NUFFT far-field path for the south/north parts (Sec. 6, Eqs. fastanterp,
+// fastinterp; Fig. nufftgrids), Laplace kernel.
+//
+// Formation (Eq. fastanterp):  c^S_m = sum_n e^{ chi_m ybar_n} F_n(m),
+//                              c^N_m = sum_n e^{-chi_m ybar_n} F_n(m),
+//   F_n(m) = sum_j gamma(y'_j, n) q_j e^{-i alpha_m x'_j}   (type-1 NUFFT per GL line n)
+// with gamma the barycentric Gauss-Legendre interpolation weights on
+// ybar_n in [-eta/2, eta/2] (Sec. 2.4, Eq. baryweights).
+// Evaluation (Eq. fastinterp):  u(t) = sum_n gamma(y, n) G_n(x),
+//   G_n(x) = Re sum_{m>=1} e^{i alpha_m x} v_n(m),
+//   v_n(m) = w^S_m e^{-chi_m ybar_n} + w^N_m e^{chi_m ybar_n}  (type-2 NUFFT per line)
+// and the y-derivative through v^y_n(m) = -chi_m w^S_m e^{-chi ybar} + chi_m w^N_m e^{chi ybar}.
+//
+// Type-1/type-2 transforms: exponential-of-semicircle kernel
+// phi(z) = exp(b (sqrt(1 - z^2) - 1)) of width w grid points, b = 2.30 w,
+// fine grid of nf >= 2 (2M + 1) points (power of two) on theta = 2 pi x / d,
+// a radix-2 FFT in shared memory, deconvolution by the kernel's Fourier
+// transform.  With h = 2 pi / nf and alpha = w h / 2:
+//   type 1:  F(k) = (2/w) B(k) / phihat(alpha k),  B = FFT(spread grid)
+//   type 2:  G(theta) = (2/w) sum_l b_l phi((theta - theta_l)/alpha),
+//            b = IFFT(v(k) / phihat(alpha k)).
+// Two real lines share one complex FFT (real + i imag).
+#include <algorithm>
+#include <cmath>
 #include "pfmm_impl.h"
+#include "devmath.cuh"
+
 namespace pfmm {
-cudaError_t launch_far_nufft(const pfmm_plan*, char*, int64_t, int64_t, bool, double*, double*, cudaStream_t) {
-  return cudaErrorNotSupported;
+
+struct NufftArgs {
+  int nf, logn, w, M, n_gl, nrhs, ns, nt;
+  double es_beta, d, eta, xi;
+  const double* gl;      // [n_gl][2] (ybar_n, sigma_n)
+  const double* phihat;  // [M+1] phihat(alpha k), k = 0..M
+};
+
+// ES kernel values at the w grid points around theta (in grid units u = theta / h).
+// l0 = first grid index; z_k = (u - (l0 + k)) / (w/2).
+template <typename T>
+__device__ __forceinline__ int es_weights(T u, int w, T beta, T* ker) {
+  const T half = T(0.5) * w;
+  const int l0 = (int)ceil(u - half);
+#pragma unroll 16
+  for (int k = 0; k < 16; ++k) {
+    if (k < w) {
+      const T z = (u - (T)(l0 + k)) / half;
+      const T s = T(1) - z * z;
+      ker[k] = s > T(0) ? dm::ex(beta * (sqrt(s) - T(1))) : T(0);
+    }
+  }
+  return l0;
 }
+
+// Barycentric interpolation weights gamma(y, n) (second form).
+template <typename T>
+__device__ __forceinline__ void bary(T y, const double* gl, int n_gl, T* g) {
+  T sum = T(0);
+  int hit = -1;
+  for (int n = 0; n < n_gl; ++n) {
+    const T dy = y - (T)gl[2 * n];
+    if (dy == T(0)) hit = n;
+    g[n] = (T)gl[2 * n + 1] / (dy == T(0) ? T(1) : dy);
+    sum += g[n];
+  }
+  if (hit >= 0) {
+    for (int n = 0; n < n_gl; ++n) g[n] = (n == hit) ? T(1) : T(0);
+    return;
+  }
+  const T inv = T(1) / sum;
+  for (int n = 0; n < n_gl; ++n) g[n] *= inv;
+}
+
+// ---------------------------------------------------------------------------
+// K4: anterpolation + spreading.  One block per source chunk; the block
+// spreads into a shared-memory grid [n_gl][nf] for one rhs at a time and adds
+// it to the global FP64 grid [nrhs][n_gl][nf].
+// ---------------------------------------------------------------------------
+constexpr int kSpreadThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, int chunk, const T* __restrict__ sx,
+                                                                 const T* __restrict__ sy, const T* __restrict__ qv,
+                                                                 double* __restrict__ grid, int use_smem) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sg = reinterpret_cast<T*>(smem_raw);  // [n_gl][nf] when use_smem
+  const int ngrid = a.n_gl * a.nf;
+  const int j0 = blockIdx.x * chunk, j1 = min(a.ns, j0 + chunk);
+  const T twopi_over_d = (T)(2.0 * M_PI / a.d);
+  const T inv_h = (T)(a.nf / (2.0 * M_PI));
+  const T beta = (T)a.es_beta;
+  for (int r = 0; r < a.nrhs; ++r) {
+    if (use_smem)
+      for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) sg[k] = T(0);
+    __syncthreads();
+    for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
+      const T x = sx[j], y = sy[j], q = qv[(size_t)r * a.ns + j];
+      T th = x * twopi_over_d;  // in [-pi (1 + |xi|/d), ...]; reduced below
+      T u = th * inv_h;
+      u -= (T)a.nf * floor(u / (T)a.nf);  // u in [0, nf)
+      T ker[16], gam[32];
+      const int l0 = es_weights(u, a.w, beta, ker);
+      bary(y, a.gl, a.n_gl, gam);
+      double* gr = grid + (size_t)r * ngrid;
+      for (int n = 0; n < a.n_gl; ++n) {
+        const T gq = gam[n] * q;
+        for (int k = 0; k < a.w; ++k) {
+          const int l = (l0 + k) & (a.nf - 1);
+          if (use_smem)
+            atomicAdd(sg + n * a.nf + l, gq * ker[k]);
+          else
+            atomicAdd(gr + n * a.nf + l, (double)(gq * ker[k]));
+        }
+      }
+    }
+    __syncthreads();
+    if (use_smem) {
+      double* g = grid + (size_t)r * ngrid;
+      for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) {
+        const T v = sg[k];
+        if (v != T(0)) atomicAdd(g + k, (double)v);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K5: radix-2 complex FFT in shared memory (iterative, decimation in time,
+// bit-reversed load).  One block per transform.  sign = -1 forward, +1 inverse.
+// ---------------------------------------------------------------------------
+template <typename T, typename T2>
+__device__ void fft_smem(T2* s, int n, int logn, int sign) {
+  for (int len = 2; len <= n; len <<= 1) {
+    const int half = len >> 1;
+    for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
+      const int grp = b / half, k = b % half;
+      const int i0 = grp * len + k, i1 = i0 + half;
+      T sn, cs;
+      dm::sincospi_((T)(sign * 2) * (T)k / (T)len, &sn, &cs);
+      const T2 x1 = s[i1];
+      const T2 t = {x1.x * cs - x1.y * sn, x1.x * sn + x1.y * cs};
+      const T2 x0 = s[i0];
+      s[i0] = {x0.x + t.x, x0.y + t.y};
+      s[i1] = {x0.x - t.x, x0.y - t.y};
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int bitrev(int i, int logn) { return __brev(i) >> (32 - logn); }
+
+// Forward transforms of the spread grids, two lines per FFT, then
+// deconvolution: F_n(k) for k = 0..M written to Fk [nrhs][n_gl][M+1] (double2).
+template <typename T, typename T2>
+__global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double2* __restrict__ Fk) {
+  extern __shared__ unsigned char smem_raw[];
+  T2* s = reinterpret_cast<T2*>(smem_raw);
+  const int npair = (a.n_gl + 1) / 2;
+  const int r = blockIdx.x / npair, p = blockIdx.x % npair;
+  const int n0 = 2 * p, n1 = 2 * p + 1;
+  const double* g0 = grid + ((size_t)r * a.n_gl + n0) * a.nf;
+  const double* g1 = (n1 < a.n_gl) ? grid + ((size_t)r * a.n_gl + n1) * a.nf : nullptr;
+  for (int i = threadIdx.x; i < a.nf; i += blockDim.x) {
+    const int j = bitrev(i, a.logn);
+    s[j] = {(T)g0[i], g1 ? (T)g1[i] : T(0)};
+  }
+  __syncthreads();
+  fft_smem<T, T2>(s, a.nf, a.logn, -1);
+  const double scale = 2.0 / a.w;
+  for (int k = threadIdx.x; k <= a.M; k += blockDim.x) {
+    const T2 zk = s[k], zm = s[(a.nf - k) & (a.nf - 1)];
+    // X = (Z_k + conj Z_-k)/2, Y = (Z_k - conj Z_-k)/(2i)
+    const double xr = 0.5 * ((double)zk.x + zm.x), xi = 0.5 * ((double)zk.y - zm.y);
+    const double yr = 0.5 * ((double)zk.y + zm.y), yi = -0.5 * ((double)zk.x - zm.x);
+    const double dec = scale / a.phihat[k];
+    Fk[((size_t)r * a.n_gl + n0) * (a.M + 1) + k] = make_double2(xr * dec, xi * dec);
+    if (n1 < a.n_gl) Fk[((size_t)r * a.n_gl + n1) * (a.M + 1) + k] = make_double2(yr * dec, yi * dec);
+  }
+}
+
+// Mode combination, lattice weights and evaluation-line spectra (FP64).
+// One thread per (rhs, mode m = 1..M).  Writes the type-2 input spectra:
+//   Zp_n = pot_n + i gy_n   (pack 0, one per line)
+//   Zx_p = gx_{2p} + i gx_{2p+1}  (pack 1, one per line pair)
+// layout spec [nrhs][npack_lines][nf] (T2), zero elsewhere (cleared before).
+template <typename T2>
+__global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, T2* __restrict__ spec, int want_grad) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int r = blockIdx.y;
+  if (m > a.M) return;
+  const double al = 2.0 * M_PI * m / a.d, chi = fabs(al);
+  // D^S = e^{-2Q}/(2 d chi (1 - e^{-Q})), Q = chi eta - i alpha xi (Theorem south_thm_lap); D^N = conj
+  const double er = exp(-chi * a.eta);
+  double sq, cq;
+  sincos(al * a.xi, &sq, &cq);
+  const double e1r = er * cq, e1i = er * sq;  // e^{-Q}
+  const double e2r = e1r * e1r - e1i * e1i, e2i = 2 * e1r * e1i;
+  const double dr = 1.0 - e1r, di = -e1i, den = 2.0 * a.d * chi * (dr * dr + di * di);
+  const double DSr = (e2r * dr + e2i * di) / den, DSi = (e2i * dr - e2r * di) / den;
+  double cSr = 0, cSi = 0, cNr = 0, cNi = 0;
+  for (int n = 0; n < a.n_gl; ++n) {
+    const double yb = a.gl[2 * n];
+    const double2 F = Fk[((size_t)r * a.n_gl + n) * (a.M + 1) + m];
+    const double ep = exp(chi * yb), em = exp(-chi * yb);
+    cSr += ep * F.x;
+    cSi += ep * F.y;
+    cNr += em * F.x;
+    cNi += em * F.y;
+  }
+  // w = 2 D c (factor 2: the +-m pair, real part taken at the end)
+  const double wSr = 2 * (DSr * cSr - DSi * cSi), wSi = 2 * (DSr * cSi + DSi * cSr);
+  const double wNr = 2 * (DSr * cNr + DSi * cNi), wNi = 2 * (DSr * cNi - DSi * cNr);  // conj(D^S) c^N
+  const double pre = (2.0 / a.w) / a.phihat[m];
+  const int npk = a.n_gl + (a.n_gl + 1) / 2;
+  T2* base = spec + (size_t)r * npk * a.nf;
+  // one-sided spectrum a_m -> two real outputs: H_m = a + i b, H_-m = conj(a) + i conj(b), a = v/2
+  auto put = [&](int line, double ar, double ai, double br, double bi) {
+    T2* row = base + (size_t)line * a.nf;
+    row[m] = {(decltype(row->x))(0.5 * pre * (ar - bi)), (decltype(row->x))(0.5 * pre * (ai + br))};
+    row[a.nf - m] = {(decltype(row->x))(0.5 * pre * (ar + bi)), (decltype(row->x))(0.5 * pre * (-ai + br))};
+  };
+  double vxr_prev = 0, vxi_prev = 0;
+  for (int n = 0; n < a.n_gl; ++n) {
+    const double yb = a.gl[2 * n];
+    const double es = exp(-chi * yb), en = exp(chi * yb);
+    const double vr = wSr * es + wNr * en, vi = wSi * es + wNi * en;
+    const double vyr = chi * (-wSr * es + wNr * en), vyi = chi * (-wSi * es + wNi * en);
+    put(n, vr, vi, want_grad ? vyr : 0.0, want_grad ? vyi : 0.0);
+    // d/dx: multiply by i alpha
+    const double vxr = -al * vi, vxi = al * vr;
+    if (want_grad) {
+      if (n & 1)
+        put(a.n_gl + n / 2, vxr_prev, vxi_prev, vxr, vxi);
+      else if (n == a.n_gl - 1)
+        put(a.n_gl + n / 2, vxr, vxi, 0.0, 0.0);
+    }
+    vxr_prev = vxr;
+    vxi_prev = vxi;
+  }
+}
+
+// Inverse FFT of each packed line spectrum in place (bit-reversed load into smem).
+template <typename T, typename T2>
+__global__ void k_nufft_inv(NufftArgs a, T2* __restrict__ spec) {
+  extern __shared__ unsigned char smem_raw[];
+  T2* s = reinterpret_cast<T2*>(smem_raw);
+  T2* row = spec + (size_t)blockIdx.x * a.nf;
+  for (int i = threadIdx.x; i < a.nf; i += blockDim.x) s[bitrev(i, a.logn)] = row[i];
+  __syncthreads();
+  fft_smem<T, T2>(s, a.nf, a.logn, +1);
+  for (int i = threadIdx.x; i < a.nf; i += blockDim.x) row[i] = s[i];
+}
+
+// Interpolation at targets + barycentric combination over lines; adds the
+// south/north field to pot / grad (input frame).
+template <typename T, typename T2>
+__global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, const T* __restrict__ ty,
+                               const T2* __restrict__ spec, double* __restrict__ pot, double* __restrict__ grad) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= a.nt) return;
+  const T x = tx[l], y = ty[l];
+  T u = x * (T)(2.0 * M_PI / a.d) * (T)(a.nf / (2.0 * M_PI));
+  u -= (T)a.nf * floor(u / (T)a.nf);
+  T ker[16], gam[32];
+  const int l0 = es_weights(u, a.w, (T)a.es_beta, ker);
+  bary(y, a.gl, a.n_gl, gam);
+  const int npk = a.n_gl + (a.n_gl + 1) / 2;
+  const double* R = g.rot;
+  for (int r = 0; r < a.nrhs; ++r) {
+    const T2* base = spec + (size_t)r * npk * a.nf;
+    T p = 0, gx = 0, gy = 0;
+    for (int n = 0; n < a.n_gl; ++n) {
+      const T2* row = base + (size_t)n * a.nf;
+      const T2* rowx = base + (size_t)(a.n_gl + n / 2) * a.nf;
+      T sp = 0, sy = 0, sx = 0;
+      for (int k = 0; k < a.w; ++k) {
+        const int li = (l0 + k) & (a.nf - 1);
+        const T2 v = row[li];
+        sp += ker[k] * v.x;
+        sy += ker[k] * v.y;
+        if (grad) {
+          const T2 vx = rowx[li];
+          sx += ker[k] * ((n & 1) ? vx.y : vx.x);
+        }
+      }
+      p += gam[n] * sp;
+      gy += gam[n] * sy;
+      gx += gam[n] * sx;
+    }
+    if (pot) pot[(size_t)r * a.nt + l] += (double)p;
+    if (grad) {
+      const double gxd = gx, gyd = gy;
+      grad[((size_t)r * 2) * a.nt + l] += R[0] * gxd + R[2] * gyd;
+      grad[((size_t)r * 2 + 1) * a.nt + l] += R[1] * gxd + R[3] * gyd;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, typename T2>
+static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                             double* grad, cudaStream_t st) {
+  const Layout& L = p->lay;
+  const bool mixed = sizeof(T) == 4;
+  NufftArgs a{};
+  a.nf = p->nf;
+  a.logn = 0;
+  while ((1 << a.logn) < a.nf) ++a.logn;
+  a.w = p->nufft_w;
+  a.M = p->far.M;
+  a.n_gl = p->n_gl;
+  a.nrhs = p->opts.nrhs;
+  a.ns = (int)ns;
+  a.nt = (int)nt;
+  a.es_beta = p->es_beta;
+  a.d = p->geom.d;
+  a.eta = p->geom.eta;
+  a.xi = p->geom.xi;
+  size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
+  a.gl = (const double*)(ws + L.nodes + nb);
+  a.phihat = (const double*)(ws + L.nodes + nb + p->n_gl * 2 * sizeof(double));
+  // workspace partition of the NUFFT scratch
+  char* base = ws + L.nufft;
+  double* grid = (double*)base;                                   // [nrhs][n_gl][nf] double
+  size_t off = (size_t)a.nrhs * a.n_gl * a.nf * sizeof(double);
+  double2* Fk = (double2*)(base + off);                           // [nrhs][n_gl][M+1]
+  off += (size_t)a.nrhs * a.n_gl * (a.M + 1) * sizeof(double2);
+  off = (off + 255) & ~size_t(255);
+  T2* spec = (T2*)(base + off);                                   // [nrhs][npk][nf]
+  const int npk = a.n_gl + (a.n_gl + 1) / 2;
+  cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)a.nrhs * a.n_gl * a.nf * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * npk * a.nf * sizeof(T2), st);
+  if (e != cudaSuccess) return e;
+  const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
+  const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
+  int nchunk = std::max(1, std::min((int)((ns + 255) / 256), 2 * 152));
+  int chunk = (int)((ns + nchunk - 1) / nchunk);
+  nchunk = (int)((ns + chunk - 1) / chunk);
+  size_t sm_spread = (size_t)a.n_gl * a.nf * sizeof(T);
+  const int use_smem = sm_spread <= 96 * 1024;
+  if (!use_smem) sm_spread = 0;
+  if (sm_spread > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_nufft_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spread);
+    if (e != cudaSuccess) return e;
+  }
+  k_nufft_spread<T><<<nchunk, kSpreadThreads, sm_spread, st>>>(a, chunk, sx, sx + ns, qv, grid, use_smem);
+  const int fth = std::min(512, std::max(32, a.nf / 2));
+  const size_t sm_fft = (size_t)a.nf * sizeof(T2);
+  if (sm_fft > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_nufft_fwd<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_nufft_inv<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
+    if (e != cudaSuccess) return e;
+  }
+  k_nufft_fwd<T, T2><<<a.nrhs * ((a.n_gl + 1) / 2), fth, sm_fft, st>>>(a, grid, Fk);
+  dim3 gm((a.M + 127) / 128, a.nrhs);
+  if (a.M > 0) k_nufft_modes<T2><<<gm, 128, 0, st>>>(a, Fk, spec, grad != nullptr);
+  k_nufft_inv<T, T2><<<a.nrhs * npk, fth, sm_fft, st>>>(a, spec);
+  const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
+  k_nufft_interp<T, T2><<<(int)((nt + 127) / 128), 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+  g_launches += 5;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                             double* grad, cudaStream_t st) {
+  // west/east terms and the m = 0 moment term on the direct kernels (their
+  // number of nodes does not grow with the aspect ratio), south/north here.
+  pfmm_plan q = *p;
+  q.far.nsn = 0;
+  q.far.M = 0;
+  q.far.nterm = 2 * q.far.Nq;
+  cudaError_t e = launch_far_direct(&q, ws, ns, nt, self, pot, grad, st);
+  if (e != cudaSuccess) return e;
+  if (p->far.M > 0) {
+    e = (p->opts.precision == PFMM_MIXED) ? run_nufft<float, float2>(p, ws, ns, nt, self, pot, grad, st)
+                                          : run_nufft<double, double2>(p, ws, ns, nt, self, pot, grad, st);
+  }
+  return e;
+}
+
 }  // namespace pfmm

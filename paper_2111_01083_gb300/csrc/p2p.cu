@@ -64,7 +64,8 @@ struct P2PArgs {
   const double* qc;      // [nrhs][ncomp][ns] (FP64 kernel)
   float beta_f;
   double beta;
-  float lgc;             // log2(r^2) shift (Laplace/Stokes), see below
+  float lgc;             // log2(r^2) shift (Laplace/Stokes, FP64 add-back), see below
+  float kimg[kMaxNear];  // per-image scale 2^-e_i of r^2 (exact powers of two)
   const double* mom;     // FP64 moments: mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y
   double* pot;
   double* grad;
@@ -75,12 +76,15 @@ struct P2PArgs {
 // L_j = sum_i log2 r_ij^2, Gx_j = sum_i dx_ij / r_ij^2), then multiplied by
 // q_j once per rhs.  The image sums have no sign cancellation; the cancelling
 // sum over sources (zero net charge) then has 9-15x fewer FP32 additions.
-// Potential terms use L_j - nimg c with a per-plan constant c near the mean
-// of log2(r^2) over the near block, so the partial sums stay small: with
-// zero net charge sum_j q_j nimg c cancels while FP32 rounding scales with the
-// size of the partial sums.  The epilogue adds back nimg c sum_j q_j in FP64
-// from the moments (skipped zero-distance pairs contribute 0 to L_j and need
-// no correction).  The Stokes velocity uses the per-source sums
+// The log terms of source j are combined through one logarithm of a product:
+//   L_j = log2( prod_i r_ij^2 2^-e_i ) = sum_i log2 r_ij^2 - E,  E = sum_i e_i,
+// with e_i an integer close to the mean of log2 r^2 over image i, so the
+// product stays near 1 and L_j is small: its FP32 error is then a few 1e-7
+// absolute whatever the cell size, and one MUFU lg2 serves all images of the
+// pair (target, source).  With zero net charge sum_j q_j E cancels; the
+// epilogue adds E sum_j q_j back in FP64 from the moments.  A skipped
+// zero-distance pair enters the product as 1 * 2^-e_i, which the same
+// add-back accounts for.  The Stokes velocity uses the per-source sums
 // L, G1 = sum (dx^2 - dy^2)/r^2 and G2 = sum dx dy / r^2 (Axx = (n + G1)/2,
 // Ayy = (n - G1)/2 with n the images used; the constant isotropic part is
 // added back in FP64 like the log shift).
@@ -147,7 +151,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
       K[r][k].s = K[r][k].c = f2(0.f);
       S[r][k] = f2(0.f);
     }
-  const float2 nshift = f2(-(float)NIMG * a.lgc);
   constexpr float kStokesC = -2.0f / 0.69314718055994531f;  // -(1/4pi) / (ln2/8pi)
 
   const int j0 = blockIdx.y * a.chunk;
@@ -156,7 +159,9 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
     for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
-      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(1e18f, 0.f, 1e18f, 0.f);
+      // padding: a zero-strength source at the origin (finite r^2 in every image;
+      // a zero distance can only occur in the centre image, which is masked)
+      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
       for (int jj = js; jj < js + kP2PSub; ++jj) {
         const float4 p = s_p[jj];
         const float2 nsxh = f2(-p.x), nsxl = f2(-p.y), nsyh = f2(-p.z), nsyl = f2(-p.w);
-        float2 L = f2(0.f), G1 = f2(0.f), G2 = f2(0.f), cnt = f2((float)NIMG);
+        float2 P = f2(1.f), G1 = f2(0.f), G2 = f2(0.f), cnt = f2((float)NIMG);
 #pragma unroll
         for (int i = 0; i < NIMG; ++i) {
           const float2 dx = add2(add2(thx[i], nsxh), add2(tlx[i], nsxl));
@@ -181,13 +186,9 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
             r2 = make_float2(r2.x > 0.f ? r2.x : 1.f, r2.y > 0.f ? r2.y : 1.f);
             cnt = add2(cnt, add2(msk, f2(-1.0f)));
           }
-          float2 lg = make_float2(lg2_approx(r2.x), lg2_approx(r2.y));
           float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
-          if (i == CENTER) {
-            lg = mul2(lg, msk);
-            inv = mul2(inv, msk);
-          }
-          L = add2(L, lg);
+          if (i == CENTER) inv = mul2(inv, msk);
+          P = mul2(P, mul2(r2, f2(a.kimg[i])));
           if (KER == PFMM_LAPLACE) {
             if (GRAD) {
               G1 = fma2(dx, inv, G1);
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
             G2 = fma2(mul2(dx, inv), dy, G2);
           }
         }
-        L = add2(L, nshift);
+        const float2 L = make_float2(lg2_approx(P.x), lg2_approx(P.y));
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           if (KER == PFMM_LAPLACE) {
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
           } else {
             // Axx = (cnt + G1)/2, Ayy = (cnt - G1)/2; the isotropic part C nimg/2 is
             // moved into the FP64 add-back:  u_x += fx (Lx + C G1/2) + fy C G2,
-            // u_y += fx C G2 + fy (Lx - C G1/2),  Lx = L - nimg c + C (cnt - nimg)/2
+            // u_y += fx C G2 + fy (Lx - C G1/2),  Lx = L + C (cnt - nimg)/2
             const float2 fx = f2(s_q[r * NC][jj]), fy = f2(s_q[r * NC + NC - 1][jj]);
             const float2 Lx = fma2(add2(cnt, f2(-(float)NIMG)), f2(0.5f * kStokesC), L);
             const float2 h1 = mul2(G1, f2(0.5f * kStokesC)), cxy = mul2(G2, f2(kStokesC));
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
     }
   }
   const double* R = a.g.rot;
-  const double lgc = (double)a.lgc;
+  const double lgc = (double)a.lgc;  // = E (sum of the image exponents)
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const bool in = h == 0 ? inA : inB;
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
         const double cst = -0.69314718055994531 / (8.0 * M_PI);
         double sx = val(0), sy = val(NA - 1);
         if (blockIdx.y == 0) {
-          const double add = NIMG * (lgc + 0.5 * (double)kStokesC);
+          const double add = lgc + NIMG * 0.5 * (double)kStokesC;
           sx += add * a.mom[(r0 + r) * 8 + 0];
           sy += add * a.mom[(r0 + r) * 8 + 1];
         }
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
       } else {
         const double cp = -0.69314718055994531 / (4.0 * M_PI), cg = -1.0 / (2.0 * M_PI);
         double sp = val(0);
-        if (blockIdx.y == 0) sp += lgc * NIMG * a.mom[(r0 + r) * 8 + 0];
+        if (blockIdx.y == 0) sp += lgc * a.mom[(r0 + r) * 8 + 0];
         if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, cp * sp);
         if (GRAD && a.grad) {
           const double gx = cg * val(1 % NA), gy = cg * val(2 % NA);
@@ -528,9 +529,28 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
   a.grad = grad;
   a.mom = (const double*)(ws + L.moments);
   {
-    // mean of log2(r^2) over a disc with the near block's area
+    // e_i = nearest integer to the mean of log2 |t - s - l_i|^2 over t, s on a
+    // 16 x 16 lattice of fractional positions in the cell (deterministic)
     const Geom& g = p->geom;
-    a.lgc = (float)(std::log2(g.nimg * g.d * g.eta / M_PI) - 1.0 / std::log(2.0));
+    double E = 0.0;
+    for (int i = 0; i < g.nimg; ++i) {
+      double acc = 0.0;
+      int cntp = 0;
+      for (int a1 = 0; a1 < 16; ++a1)
+        for (int a2 = 0; a2 < 16; ++a2)
+          for (int b1 = 0; b1 < 16; b1 += 3)
+            for (int b2 = 0; b2 < 16; b2 += 3) {
+              double u1 = (a1 + 0.5) / 16 - 0.5 - ((b1 + 0.5) / 16 - 0.5);
+              double u2 = (a2 + 0.5) / 16 - 0.5 - ((b2 + 0.5) / 16 - 0.5);
+              double dx = u1 * g.d + u2 * g.xi - g.off[i][0], dy = u2 * g.eta - g.off[i][1];
+              double r2 = dx * dx + dy * dy;
+              if (r2 > 0) { acc += std::log2(r2); ++cntp; }
+            }
+      double e = std::nearbyint(acc / std::max(1, cntp));
+      a.kimg[i] = (float)std::ldexp(1.0, -(int)e);
+      E += e;
+    }
+    a.lgc = (float)E;
   }
   const bool mixed = p->opts.precision == PFMM_MIXED;
   const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread

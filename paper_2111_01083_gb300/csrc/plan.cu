@@ -231,7 +231,13 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   while (nf < 2 * (2 * M + 1) || nf < 2 * w) nf *= 2;
   p->nf = nf;
   int path = o->path;
-  if (path == PFMM_PATH_AUTO) path = (M >= 64 && o->kernel == PFMM_LAPLACE) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+  // the single-block shared-memory FFT handles fine grids up to 8192 points
+  if (path == PFMM_PATH_AUTO)
+    path = (M >= 64 && o->kernel == PFMM_LAPLACE && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+  if (path == PFMM_PATH_NUFFT && nf > 8192) {
+    delete p;
+    return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
+  }
   if (o->kernel != PFMM_LAPLACE && path == PFMM_PATH_NUFFT) {
     delete p;
     return fail(PFMM_ERR_INVALID_ARG, "the NUFFT path is implemented for the Laplace kernel");
@@ -276,8 +282,12 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (path == PFMM_PATH_NUFFT) {
     // fine grids [n_gl][nrhs][nf] complex (float2 for mixed, double2 for fp64)
     // x2 (spread grid + evaluation grids for pot, d/dx, d/dy -> 3 channels)
+    // FP64 spread grid [nrhs][n_gl][nf], FP64 spectra F_n(k) [nrhs][n_gl][M+1],
+    // evaluation spectra [nrhs][n_gl + ceil(n_gl/2)][nf] complex (float2 or double2)
     size_t cplx = (o->precision == PFMM_FP64) ? 16 : 8;
-    nuf = (size_t)p->n_gl * nrhs * nf * cplx * 4 + (size_t)p->n_gl * nrhs * (2 * M + 1) * 16;
+    int npk = p->n_gl + (p->n_gl + 1) / 2;
+    nuf = (size_t)nrhs * p->n_gl * nf * 8 + (size_t)nrhs * p->n_gl * (M + 1) * 16 + 256 +
+          (size_t)nrhs * npk * nf * cplx + 256;
   }
   L.nufft = take(nuf);
   L.total = off;

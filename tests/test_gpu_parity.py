@@ -138,3 +138,46 @@ def test_not_neutral_reported():
     e1, e2, src, q, _ = _case("laplace", "square", 64, seed=8)
     with pytest.raises(PfmmError, match="NOT_NEUTRAL"):
         run_lib("laplace", e1, e2, src, q + 0.1, None, tol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# NUFFT path (Sec. 6, Eqs. fastanterp / fastinterp)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("e1,e2", [((8.0, 0.0), (0.0, 1.0)), ((16.0, 0.0), (3.0, 1.0)), ((40.0, 0.0), (0.0, 1.0))])
+def test_laplace_nufft_path(precision, e1, e2):
+    rng = np.random.default_rng(11)
+    src = workloads.points(rng, e1, e2, 1500, "gmm")
+    q = workloads.strengths(rng, 2, 1500)
+    trg = workloads.points(rng, e1, e2, 400)
+    tol = TOL[precision]
+    for part in ("far", "total"):
+        got = run_lib("laplace", e1, e2, src, q, trg, tol=tol, precision=precision, part=part, path="nufft")
+        assert got[2].describe()["path"] == 2
+        ref = oracle("laplace", e1, e2, src, q, trg, part=part)
+        if part == "far":
+            # far part alone, measured against the total field's scale (the quantity the tolerance is for)
+            tot = oracle("laplace", e1, e2, src, q, trg, part="total")
+            sc_p = np.linalg.norm(tot[0] - tot[0].mean(-1, keepdims=True))
+            d = (got[0] - got[0].mean(-1, keepdims=True)) - (ref[0] - ref[0].mean(-1, keepdims=True))
+            assert np.linalg.norm(d) / sc_p < tol
+            assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(tot[1]) < tol
+        else:
+            ep, eg = errs("laplace", got, ref)
+            assert ep < tol and eg < tol, (ep, eg)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nufft_matches_direct(precision):
+    e1, e2 = (24.0, 0.0), (1.5, 1.0)
+    rng = np.random.default_rng(12)
+    src = workloads.points(rng, e1, e2, 2500, "gmm")
+    q = workloads.strengths(rng, 1, 2500)
+    tol = TOL[precision]
+    a = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="far", path="nufft")
+    b = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="far", path="direct")
+    tot = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="total", path="direct")
+    sc = np.linalg.norm(tot[0] - tot[0].mean(-1, keepdims=True))
+    d = (a[0] - a[0].mean(-1, keepdims=True)) - (b[0] - b[0].mean(-1, keepdims=True))
+    assert np.linalg.norm(d) / sc < tol
+    assert np.linalg.norm(a[1] - b[1]) / np.linalg.norm(tot[1]) < tol
