@@ -163,6 +163,22 @@ pfmm_status pfmm_execute_host(pfmm_plan* plan, void* workspace, size_t ws_bytes,
                               const double* src, const double* q, int64_t nt, const double* trg,
                               double* pot, double* grad, void* stream);
 
+/* The same operation as pfmm_execute for callers that cannot allocate device
+ * memory (for example a C host program that is handed device pointers by
+ * another component and has no device allocator, or a caller that must not
+ * call cudaMalloc/cudaFree between launches because they synchronise the
+ * device).  The paper has no counterpart: this is a library convenience.
+ * Scratch comes from a 32 MiB array compiled into the library (held on every
+ * GPU that loads the library until the process exits) instead of a
+ * workspace argument; plans whose pfmm_workspace_size exceeds 32 MiB are
+ * rejected with PFMM_ERR_WORKSPACE.  Nothing is allocated.  The first call
+ * on each device looks up the array's device address (make it before any
+ * stream capture).  All calls on one device share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Arguments,
+ * outputs and errors otherwise as pfmm_execute (device pointers). */
+pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const double* src, const double* q, int64_t nt,
+                                const double* trg, double* pot, double* grad, void* stream);
+
 /* Synchronise the stream and read the device status word written by the
  * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,
  * PFMM_ERR_NOT_NEUTRAL, PFMM_ERR_TIMEOUT) and clears it. */

@@ -21,7 +21,7 @@ STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PF
 # Every symbol declared in include/pfmm.h (checked by the CPU test suite).
 EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host", "pfmm_plan_describe",
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
-           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read"]
+           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static"]
 
 
 class Opts(ctypes.Structure):
@@ -68,6 +68,8 @@ def lib():
     L.pfmm_execute.restype = ctypes.c_int
     L.pfmm_execute_host.argtypes = [vp, vp, sz, i64, vp, vp, i64, vp, vp, vp, vp]
     L.pfmm_execute_host.restype = ctypes.c_int
+    L.pfmm_execute_static.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp]
+    L.pfmm_execute_static.restype = ctypes.c_int
     L.pfmm_get_status.argtypes = [vp, vp, vp]
     L.pfmm_get_status.restype = ctypes.c_int
     L.pfmm_last_error.argtypes = []

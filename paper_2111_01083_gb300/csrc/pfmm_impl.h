@@ -92,6 +92,8 @@ cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
                              double* pot, double* grad, cudaStream_t st);
 cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
                        double* pot, double* grad, bool accumulate, cudaStream_t st);
+// records a thread-local error message (pfmm_last_error) and returns s
+pfmm_status set_error(pfmm_status s, const char* fmt, ...);
 // kernels launched by the most recent launch_* call (set by each launcher)
 extern thread_local int g_launches;
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);

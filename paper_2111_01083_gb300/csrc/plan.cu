@@ -144,6 +144,18 @@ double es_phihat(double b, double k) {
 
 }  // namespace
 
+namespace pfmm {
+pfmm_status set_error(pfmm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+}  // namespace pfmm
+
 extern "C" {
 
 const char* pfmm_last_error(void) { return g_err.c_str(); }
