@@ -1,0 +1,132 @@
+"""Host-only checks of the C-ABI library (no GPU needed).
+
+* the shared library loads and exports every function declared in include/pfmm.h
+* plan parameters: canonical cell, m0, M from Eq. mpk0s, west/east nodes
+* argument validation happens on the host before any launch
+"""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2111_01083_gb300.build import build_library
+    from paper_2111_01083_gb300 import _lib
+    build_library()
+    return _lib.lib()
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(pfmm_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 12
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    from paper_2111_01083_gb300 import _lib
+    assert set(_lib.EXPORTS) == set(names)
+
+
+def test_version(L):
+    assert b"sm_103a" in L.pfmm_version()
+
+
+def _op(**kw):
+    from paper_2111_01083_gb300 import PeriodicOp
+    base = dict(kernel="laplace", e1=(1.0, 0.0), e2=(0.0, 1.0), tol=1e-6, ns_max=100, nt_max=100)
+    base.update(kw)
+    return PeriodicOp(**base)
+
+
+def _mpk0s(d, eta, eps):
+    r = 2 * math.pi * eta / d
+    return math.ceil(d / (2 * math.pi * eta) * math.log(1 / ((1 - math.exp(-r)) * eps)))
+
+
+@pytest.mark.parametrize("e1,e2,d,xi,eta,m0", [
+    ((1.0, 0.0), (0.0, 1.0), 1.0, 0.0, 1.0, 1),
+    ((0.0, 2.0), (1.0, 0.0), 2.0, 0.0, 1.0, 1),
+    ((1.0, 0.0), (0.3, 0.8), 1.0, 0.3, 0.8, 1),
+    ((1.0, 0.0), (0.45, 0.8), 1.0, 0.45, 0.8, 2),
+    ((1.0, 0.0), (5.3, 0.8), 1.0, 0.3, 0.8, 1),
+    ((16.0, 0.0), (0.0, 1.0), 16.0, 0.0, 1.0, 1),
+])
+def test_canonical_cell_and_m0(L, e1, e2, d, xi, eta, m0):
+    desc = _op(e1=e1, e2=e2).describe()
+    assert abs(desc["d"] - d) < 1e-12 and abs(abs(desc["xi"]) - abs(xi)) < 1e-12 and abs(desc["eta"] - eta) < 1e-12
+    assert desc["m0"] == m0
+    r = desc["rot"]
+    # rot is a rotation and maps a lattice vector of length d onto the x axis
+    assert abs(r[0] * r[3] - r[1] * r[2] - 1) < 1e-12 and abs(r[0] * r[1] + r[2] * r[3]) < 1e-12
+    ok = False
+    for a, b in ((1, 0), (0, 1), (1, 1), (1, -1), (1, -5), (-5, 1)):
+        v = (a * e1[0] + b * e2[0], a * e1[1] + b * e2[1])
+        x = r[0] * v[0] + r[1] * v[1]
+        y = r[2] * v[0] + r[3] * v[1]
+        ok |= abs(abs(x) - d) < 1e-9 and abs(y) < 1e-9
+    assert ok
+
+
+@pytest.mark.parametrize("d,tol", [(1.0, 1e-10), (16.0, 1e-6), (64.0, 1e-6)])
+def test_modes_follow_mpk0s(L, d, tol):
+    desc = _op(e1=(d, 0.0), e2=(0.0, 1.0), tol=tol).describe()
+    assert desc["M"] == _mpk0s(d, 1.0, tol / 10)
+    assert desc["Nq"] > 0 and desc["mode0"] == 1
+
+
+def test_modhelm_pruning(L):
+    big = _op(kernel="modhelm", beta=100.0, e1=(3.0, 0.0)).describe()
+    assert big["M"] == 0 and big["mode0"] == 0 and big["Nq"] == 0
+    small = _op(kernel="modhelm", beta=1.0, e1=(16.0, 0.0)).describe()
+    assert 0 < small["M"] <= _mpk0s(16.0, 1.0, 1e-7)
+
+
+def test_nufft_parameters(L):
+    desc = _op(e1=(16.0, 0.0), path="nufft", nufft_w=8, n_gl=8).describe()
+    assert desc["path"] == 2 and desc["nufft_w"] == 8 and desc["n_gl"] == 8
+    nf = desc["nf"]
+    assert nf & (nf - 1) == 0 and nf >= 2 * (2 * desc["M"] + 1)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(e1=(1.0, 0.0), e2=(2.0, 0.0)), 2),
+    (dict(tol=0.5), 4),
+    (dict(tol=1e-16), 4),
+    (dict(kernel="modhelm", beta=0.0), 1),
+    (dict(nrhs=0), 1),
+    (dict(kernel="stokes", path="nufft"), 1),
+])
+def test_host_validation(L, kw, code):
+    from paper_2111_01083_gb300._lib import PfmmError
+    with pytest.raises(PfmmError) as ei:
+        _op(**kw)
+    assert ei.value.code == code
+
+
+def test_execute_rejects_bad_workspace_before_launch(L):
+    op = _op()
+    # NULL workspace: rejected on the host, nothing launched
+    code = L.pfmm_execute(op._h, None, 0, 10, None, None, 10, None, None, None, None)
+    assert code in (1, 5)
+    code = L.pfmm_execute(op._h, ctypes.c_void_p(256), 1 << 40, 1000, None, None, 10, None, None, None, None)
+    assert code == 1  # ns beyond the plan maximum
+
+
+def test_workspace_size_grows_with_n(L):
+    a = _op(ns_max=1000, nt_max=1000).ws_bytes
+    b = _op(ns_max=100000, nt_max=100000).ws_bytes
+    assert b > 50 * a / 2
