@@ -163,6 +163,31 @@ pfmm_status pfmm_execute_host(pfmm_plan* plan, void* workspace, size_t ws_bytes,
                               const double* src, const double* q, int64_t nt, const double* trg,
                               double* pot, double* grad, void* stream);
 
+/* ---- Batched execution (many independent cells in one call) ----
+ * Cell c has its own lattice, beta and tolerance (opts[c]); all cells share
+ * kernel, precision and nrhs, and compute the full operator.  Sources of
+ * cell c are columns src_off[c] .. src_off[c+1]-1 of the concatenated arrays
+ * src [2][NS], q [nrhs][NS] (Stokes [nrhs][2][NS]); targets likewise with
+ * trg_off (NULL: targets = sources).  Outputs pot [nrhs][NT] (Stokes
+ * [nrhs][2][NT]) and grad [nrhs][2][NT].  Per-cell prep and far field are
+ * launched per cell; the near-image P2P of all cells runs as one persistent
+ * kernel per near-block shape over a cost-sorted list of (cell, target block,
+ * source range of p2p_chunk sources, rhs group) items (p2p_chunk 0 = 4096;
+ * else a multiple of 128).  The first execute on a given set of buffers
+ * uploads descriptors (cudaMemcpyAsync); later executes on the same buffers
+ * issue only memsets and kernels and may be captured in a CUDA graph.  The
+ * paper treats one cell at a time; batching is a library feature.
+ * Errors as for the single-cell calls. */
+typedef struct pfmm_batch pfmm_batch;
+pfmm_status pfmm_batch_create(const pfmm_opts* opts, int ncell, const int64_t* src_off,
+                              const int64_t* trg_off, int p2p_chunk, pfmm_batch** out);
+pfmm_status pfmm_batch_workspace_size(const pfmm_batch* batch, size_t* bytes);
+pfmm_status pfmm_batch_execute(pfmm_batch* batch, void* workspace, size_t ws_bytes, const double* src,
+                               const double* q, const double* trg, double* pot, double* grad, void* stream);
+/* Synchronise and return the first device status error of any cell (see pfmm_get_status). */
+pfmm_status pfmm_batch_get_status(pfmm_batch* batch, void* workspace, void* stream);
+void pfmm_batch_destroy(pfmm_batch* batch);
+
 /* The same operation as pfmm_execute for callers that cannot allocate device
  * memory (for example a C host program that is handed device pointers by
  * another component and has no device allocator, or a caller that must not

@@ -21,7 +21,9 @@ STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PF
 # Every symbol declared in include/pfmm.h (checked by the CPU test suite).
 EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host", "pfmm_plan_describe",
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
-           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static"]
+           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static",
+           "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
+           "pfmm_batch_destroy"]
 
 
 class Opts(ctypes.Structure):
@@ -70,6 +72,17 @@ def lib():
     L.pfmm_execute_host.restype = ctypes.c_int
     L.pfmm_execute_static.argtypes = [vp, i64, vp, vp, i64, vp, vp, vp, vp]
     L.pfmm_execute_static.restype = ctypes.c_int
+    L.pfmm_batch_create.argtypes = [ctypes.POINTER(Opts), ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                    ctypes.c_int, ctypes.POINTER(vp)]
+    L.pfmm_batch_create.restype = ctypes.c_int
+    L.pfmm_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.pfmm_batch_workspace_size.restype = ctypes.c_int
+    L.pfmm_batch_execute.argtypes = [vp, vp, sz, vp, vp, vp, vp, vp, vp]
+    L.pfmm_batch_execute.restype = ctypes.c_int
+    L.pfmm_batch_get_status.argtypes = [vp, vp, vp]
+    L.pfmm_batch_get_status.restype = ctypes.c_int
+    L.pfmm_batch_destroy.argtypes = [vp]
+    L.pfmm_batch_destroy.restype = None
     L.pfmm_get_status.argtypes = [vp, vp, vp]
     L.pfmm_get_status.restype = ctypes.c_int
     L.pfmm_last_error.argtypes = []

@@ -1,0 +1,207 @@
+// Batched execution: many independent cells (own lattice, parameter beta,
+// tolerance and point count) in one call on one stream.
+//
+// Each cell keeps its own plan and a private region of the workspace; the
+// inputs and outputs are concatenated structure-of-arrays with per-cell
+// offsets.  The small per-cell phases (prep, far field: < 1 % of the work) are
+// launched per cell.  The near-image P2P, which carries almost all the work
+// and the N^2 imbalance between cells, runs as one persistent kernel per
+// near-block shape over a global list of (cell, target block, source range,
+// rhs group) items sorted by decreasing cost and pulled from an atomic
+// counter.  Descriptors and item lists are uploaded by the first execute on a
+// given set of buffers; later executes on the same buffers issue only
+// memsets and kernel launches, so they can be captured in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pfmm_impl.h"
+#include "p2p.h"
+
+using namespace pfmm;
+
+struct pfmm_batch {
+  int ncell = 0, kernel = 0, precision = 0, nrhs = 1;
+  bool self = true;
+  std::vector<pfmm_plan*> plans;
+  std::vector<int64_t> soff, toff;
+  int64_t NS = 0, NT = 0;
+  std::vector<size_t> wsoff;
+  size_t off_cells = 0, off_items = 0, off_counter = 0, total = 0;
+  struct Group {
+    int nimg, nr;
+    size_t first;
+    int n, grid;
+  };
+  std::vector<Group> groups;
+  std::vector<P2PItem> items;
+  std::vector<P2PArgs> hcells;
+  const void* last[7] = {};
+  int p2p_chunk = 4096;
+};
+
+static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+extern "C" {
+
+pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* src_off, const int64_t* trg_off,
+                              int p2p_chunk, pfmm_batch** out) {
+  if (!cells || !src_off || !out || ncell < 1) return set_error(PFMM_ERR_INVALID_ARG, "bad batch arguments");
+  *out = nullptr;
+  const pfmm_opts& c0 = cells[0];
+  for (int c = 0; c < ncell; ++c) {
+    if (cells[c].kernel != c0.kernel || cells[c].precision != c0.precision || cells[c].nrhs != c0.nrhs)
+      return set_error(PFMM_ERR_INVALID_ARG, "batch cells must share kernel, precision and nrhs (cell %d)", c);
+    if (cells[c].flags & (PFMM_FAR_ONLY | PFMM_NEAR_ONLY))
+      return set_error(PFMM_ERR_INVALID_ARG, "batch cells compute the full operator (cell %d)", c);
+    if (src_off[c + 1] < src_off[c] || (trg_off && trg_off[c + 1] < trg_off[c]))
+      return set_error(PFMM_ERR_INVALID_ARG, "offsets must be non-decreasing (cell %d)", c);
+  }
+  if (src_off[0] != 0 || (trg_off && trg_off[0] != 0)) return set_error(PFMM_ERR_INVALID_ARG, "offsets start at 0");
+  if (p2p_chunk != 0 && (p2p_chunk < 128 || p2p_chunk % 128))
+    return set_error(PFMM_ERR_INVALID_ARG, "p2p_chunk must be 0 or a positive multiple of 128");
+  pfmm_batch* b = new pfmm_batch();
+  b->ncell = ncell;
+  b->kernel = c0.kernel;
+  b->precision = c0.precision;
+  b->nrhs = c0.nrhs;
+  b->self = trg_off == nullptr;
+  b->p2p_chunk = p2p_chunk ? p2p_chunk : 4096;
+  b->soff.assign(src_off, src_off + ncell + 1);
+  b->toff = b->self ? b->soff : std::vector<int64_t>(trg_off, trg_off + ncell + 1);
+  b->NS = b->soff[ncell];
+  b->NT = b->toff[ncell];
+  size_t off = 0;
+  for (int c = 0; c < ncell; ++c) {
+    int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
+    pfmm_plan* p = nullptr;
+    pfmm_status s = pfmm_plan_create(&cells[c], ns, nt, &p);
+    if (s != PFMM_OK) {
+      for (auto* q : b->plans) pfmm_plan_destroy(q);
+      delete b;
+      return s;
+    }
+    b->plans.push_back(p);
+    b->wsoff.push_back(off);
+    off = al256(off + p->lay.total);
+  }
+  // P2P work items (mixed precision: one persistent kernel per near-block shape)
+  const int tpb = p2p_targets_per_block(b->kernel);
+  const int nr = b->nrhs % 4 == 0 ? 4 : (b->nrhs % 2 == 0 ? 2 : 1);
+  for (int nimg : {9, 15}) {
+    pfmm_batch::Group g{nimg, nr, b->items.size(), 0, 0};
+    std::vector<std::pair<double, P2PItem>> v;
+    for (int c = 0; c < ncell; ++c) {
+      const pfmm_plan* p = b->plans[c];
+      if (p->geom.nimg != nimg) continue;
+      int ns = (int)(b->soff[c + 1] - b->soff[c]), nt = (int)(b->toff[c + 1] - b->toff[c]);
+      for (int bx = 0; bx * tpb < nt; ++bx)
+        for (int j0 = 0; j0 < ns; j0 += b->p2p_chunk)
+          for (int r0 = 0; r0 < b->nrhs; r0 += nr) {
+            int j1 = std::min(ns, j0 + b->p2p_chunk);
+            double cost = (double)std::min(tpb, nt - bx * tpb) * (j1 - j0) + 2000.0;
+            v.push_back({cost, P2PItem{c, bx, j0, j1, r0}});
+          }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    for (auto& e : v) b->items.push_back(e.second);
+    g.n = (int)v.size();
+    if (g.n > 0) b->groups.push_back(g);
+  }
+  b->off_cells = off;
+  off = al256(off + sizeof(P2PArgs) * ncell);
+  b->off_items = off;
+  off = al256(off + sizeof(P2PItem) * std::max<size_t>(1, b->items.size()));
+  b->off_counter = off;
+  off = al256(off + 256);
+  b->total = off;
+  b->hcells.resize(ncell);
+  *out = b;
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_batch_workspace_size(const pfmm_batch* b, size_t* bytes) {
+  if (!b || !bytes) return set_error(PFMM_ERR_INVALID_ARG, "NULL argument");
+  *bytes = b->total;
+  return PFMM_OK;
+}
+
+void pfmm_batch_destroy(pfmm_batch* b) {
+  if (!b) return;
+  for (auto* p : b->plans) pfmm_plan_destroy(p);
+  delete b;
+}
+
+pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, const double* src, const double* q,
+                               const double* trg, double* pot, double* grad, void* stream) {
+  if (!b) return set_error(PFMM_ERR_INVALID_ARG, "NULL batch");
+  if (!workspace || ws_bytes < b->total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return set_error(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", b->total);
+  if (!src || !q || !pot) return set_error(PFMM_ERR_INVALID_ARG, "NULL sources, strengths or potential");
+  if (!b->self && !trg) return set_error(PFMM_ERR_INVALID_ARG, "NULL targets");
+  if (b->kernel == PFMM_STOKES && grad) return set_error(PFMM_ERR_INVALID_ARG, "grad must be NULL for Stokes");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const double* tr = b->self ? src : trg;
+  const bool mixed = b->precision == PFMM_MIXED;
+  // per-cell strides: the caller's arrays are concatenated over cells
+  for (int c = 0; c < b->ncell; ++c) {
+    pfmm_plan* p = b->plans[c];
+    p->s_stride = b->NS;
+    p->t_stride = b->NT;
+    p->o_stride = b->NT;
+  }
+  const void* cur[7] = {workspace, src, q, tr, pot, grad, (const void*)(uintptr_t)b->p2p_chunk};
+  const bool upload = std::memcmp(cur, b->last, sizeof cur) != 0;
+  cudaError_t e;
+  if (upload) {
+    for (int c = 0; c < b->ncell; ++c) {
+      pfmm_plan* p = b->plans[c];
+      char* wc = ws + b->wsoff[c];
+      e = upload_tables(p, wc, st);
+      if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload tables: %s", cudaGetErrorString(e));
+      int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
+      fill_p2p_args(p, wc, ns, nt, b->self, pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, &b->hcells[c]);
+    }
+    e = cudaMemcpyAsync(ws + b->off_cells, b->hcells.data(), sizeof(P2PArgs) * b->ncell, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !b->items.empty())
+      e = cudaMemcpyAsync(ws + b->off_items, b->items.data(), sizeof(P2PItem) * b->items.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload descriptors: %s", cudaGetErrorString(e));
+    for (auto& g : b->groups) g.grid = p2p_batch_grid(b->kernel, g.nimg, g.nr, grad != nullptr);
+    std::memcpy(b->last, cur, sizeof cur);
+  }
+  e = cudaMemsetAsync(ws + b->off_counter, 0, 256, st);
+  if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  for (int c = 0; c < b->ncell; ++c) {
+    int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
+    pfmm_status s = execute_cell(b->plans[c], ws + b->wsoff[c], ns, src + b->soff[c], q + b->soff[c], nt,
+                                 tr + b->toff[c], pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, st, b->self,
+                                 false, !mixed);
+    if (s != PFMM_OK) return s;
+  }
+  if (mixed) {
+    int gi = 0;
+    for (auto& g : b->groups) {
+      e = launch_p2p_batch(b->kernel, g.nimg, g.nr, grad != nullptr, (const P2PArgs*)(ws + b->off_cells),
+                           (const P2PItem*)(ws + b->off_items) + g.first, g.n, (int*)(ws + b->off_counter) + gi,
+                           g.grid, st);
+      if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "batched p2p: %s", cudaGetErrorString(e));
+      ++gi;
+    }
+  }
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_batch_get_status(pfmm_batch* b, void* workspace, void* stream) {
+  if (!b || !workspace) return set_error(PFMM_ERR_INVALID_ARG, "NULL argument");
+  pfmm_status worst = PFMM_OK;
+  for (int c = 0; c < b->ncell; ++c) {
+    pfmm_status s = pfmm_get_status(b->plans[c], (char*)workspace + b->wsoff[c], stream);
+    if (s != PFMM_OK && worst == PFMM_OK) worst = s;
+  }
+  return worst;
+}
+
+}  // extern "C"

@@ -21,12 +21,12 @@ namespace pfmm {
 // ----------------------------------------------------------------------------
 // K0: points
 // ----------------------------------------------------------------------------
-__global__ void k_prep_points(Geom g, int64_t n, const double* __restrict__ pts, double* __restrict__ c64,
+__global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* __restrict__ pts, double* __restrict__ c64,
                               float* __restrict__ cf, int* __restrict__ U, float4* __restrict__ hl,
                               int* __restrict__ status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double x = pts[i], y = pts[n + i];
+  double x = pts[i], y = pts[istride + i];
   if (!isfinite(x) || !isfinite(y)) {
     atomicOr(status, ST_NONFINITE);
     x = 0.0;
@@ -53,7 +53,7 @@ __global__ void k_prep_points(Geom g, int64_t n, const double* __restrict__ pts,
 
 // K0: strengths (canonical frame) and FP64 moments per rhs:
 //   mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y, [2] = sum |q| (all comps), [3] = sum q y' (f_x y')
-__global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, const double* __restrict__ q,
+__global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
                          const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
                          double* __restrict__ mom, int* __restrict__ status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -64,9 +64,9 @@ __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, const double* 
     double a = 0, b = 0;
     if (in) {
       if (ncomp == 1) {
-        a = q[(size_t)r * ns + i];
+        a = q[(size_t)r * qs + i];
       } else {
-        double fx = q[((size_t)r * 2) * ns + i], fy = q[((size_t)r * 2 + 1) * ns + i];
+        double fx = q[((size_t)r * 2) * qs + i], fy = q[((size_t)r * 2 + 1) * qs + i];
         a = g.rot[0] * fx + g.rot[1] * fy;
         b = g.rot[2] * fx + g.rot[3] * fy;
       }
@@ -413,7 +413,7 @@ template <typename T, typename T2, int KER>
 __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt, const T* __restrict__ tx,
                                                            const T* __restrict__ ty, const int* __restrict__ tU,
                                                            const T2* __restrict__ wts, const double* __restrict__ mom,
-                                                           double* __restrict__ pot, double* __restrict__ grad) {
+                                                           int64_t os, double* __restrict__ pot, double* __restrict__ grad) {
   constexpr int NW = (KER == PFMM_STOKES) ? 4 : 1;
   __shared__ T s_a[kEvalChunk], s_b[kEvalChunk];
   __shared__ int s_m[kEvalChunk], s_part[kEvalChunk];
@@ -516,15 +516,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
     const double yd = (double)y;
     if (KER == PFMM_STOKES) {
       double ux = (double)acc[r][0] + cc * yd, uy = (double)acc[r][1];
-      pot[((size_t)(r0 + r) * 2) * nt + l] = R[0] * ux + R[2] * uy;
-      pot[((size_t)(r0 + r) * 2 + 1) * nt + l] = R[1] * ux + R[3] * uy;
+      pot[((size_t)(r0 + r) * 2) * os + l] = R[0] * ux + R[2] * uy;
+      pot[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * ux + R[3] * uy;
     } else {
       double p = (double)acc[r][0] + cc * yd;
       double gx = (double)acc[r][1], gy = (double)acc[r][2] + cc;
-      if (pot) pot[(size_t)(r0 + r) * nt + l] = p;
+      if (pot) pot[(size_t)(r0 + r) * os + l] = p;
       if (grad) {
-        grad[((size_t)(r0 + r) * 2) * nt + l] = R[0] * gx + R[2] * gy;
-        grad[((size_t)(r0 + r) * 2 + 1) * nt + l] = R[1] * gx + R[3] * gy;
+        grad[((size_t)(r0 + r) * 2) * os + l] = R[0] * gx + R[2] * gy;
+        grad[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * gx + R[3] * gy;
       }
     }
   }
@@ -540,14 +540,14 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   const Layout& L = p->lay;
   int* status = (int*)(ws + L.status);
   bool mixed = p->opts.precision == PFMM_MIXED;
-  k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
+  k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
                                                  (int*)(ws + L.srcU), mixed ? (float4*)(ws + L.srchl) : nullptr,
                                                  status);
   if (!self && nt > 0)
-    k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
+    k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
                                                    (int*)(ws + L.trgU), nullptr, status);
   g_launches = (!self && nt > 0) ? 3 : 2;
-  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, p->opts.nrhs, ns, q, (const double*)(ws + L.src64),
+  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
                                             (double*)(ws + L.qc), (float*)(ws + L.qf), (double*)(ws + L.moments),
                                             status);
   return cudaGetLastError();
@@ -585,7 +585,7 @@ static cudaError_t run_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int6
   const T* ty = tx + nt;
   const int* tU = self ? sU : (const int*)(ws + L.trgU);
   dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
-  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, pot, grad);
+  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad);
   return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ namespace pfmm {
 
 struct NufftArgs {
   int nf, logn, w, M, n_gl, nrhs, ns, nt;
+  int64_t os;  // output row stride
   double es_beta, d, eta, xi;
   const double* gl;      // [n_gl][2] (ybar_n, sigma_n)
   const double* phihat;  // [M+1] phihat(alpha k), k = 0..M
@@ -287,11 +288,11 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
       gy += gam[n] * sy;
       gx += gam[n] * sx;
     }
-    if (pot) pot[(size_t)r * a.nt + l] += (double)p;
+    if (pot) pot[(size_t)r * a.os + l] += (double)p;
     if (grad) {
       const double gxd = gx, gyd = gy;
-      grad[((size_t)r * 2) * a.nt + l] += R[0] * gxd + R[2] * gyd;
-      grad[((size_t)r * 2 + 1) * a.nt + l] += R[1] * gxd + R[3] * gyd;
+      grad[((size_t)r * 2) * a.os + l] += R[0] * gxd + R[2] * gyd;
+      grad[((size_t)r * 2 + 1) * a.os + l] += R[1] * gxd + R[3] * gyd;
     }
   }
 }
@@ -312,6 +313,7 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   a.nrhs = p->opts.nrhs;
   a.ns = (int)ns;
   a.nt = (int)nt;
+  a.os = p->o_stride;
   a.es_beta = p->es_beta;
   a.d = p->geom.d;
   a.eta = p->geom.eta;

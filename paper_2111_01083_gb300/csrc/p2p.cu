@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include "pfmm_impl.h"
+#include "p2p.h"
 #include "bessel.cuh"
 
 namespace pfmm {
@@ -53,23 +54,7 @@ struct KahanF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-struct P2PArgs {
-  Geom g;
-  int nt, ns, chunk;
-  int r0, nrhs;          // rhs group start, total rhs
-  const double* trg64;   // [2][nt] canonical
-  const float4* src_hl;  // [ns]
-  const float* qf;       // [nrhs][ncomp][ns]
-  const double* src64;   // [2][ns] (FP64 kernel)
-  const double* qc;      // [nrhs][ncomp][ns] (FP64 kernel)
-  float beta_f;
-  double beta;
-  float lgc;             // log2(r^2) shift (Laplace/Stokes, FP64 add-back), see below
-  float kimg[kMaxNear];  // per-image scale 2^-e_i of r^2 (exact powers of two)
-  const double* mom;     // FP64 moments: mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y
-  double* pot;
-  double* grad;
-};
+// P2PArgs is declared in p2p.h
 
 // Structure of the mixed kernels.  For each source j the contributions of all
 // near images are first summed WITHOUT the strength (image sums such as
@@ -113,8 +98,10 @@ struct Kahan2 {
   }
 };
 
+// Body of the Laplace/Stokes mixed kernel for one work item: target block bx
+// (2 * kP2PThreads targets), sources [j0, j1), rhs r0 .. r0 + NR - 1.
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
+__device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   static_assert(KER != PFMM_MODHELM, "packed kernel is for Laplace/Stokes");
   constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
   constexpr int CENTER = NIMG / 2;
@@ -122,10 +109,12 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
   __shared__ float4 s_p[kP2PTile];
   __shared__ float s_q[NR * NC][kP2PTile];
 
-  const int l0 = (blockIdx.x * kP2PThreads + threadIdx.x) * 2;
+  const int l0 = (bx * kP2PThreads + threadIdx.x) * 2;
   const bool inA = l0 < a.nt, inB = l0 + 1 < a.nt;
-  const int r0 = a.r0 + blockIdx.z * NR;
   const int nr = min(NR, a.nrhs - r0);
+  float kimg[NIMG];
+#pragma unroll
+  for (int i = 0; i < NIMG; ++i) kimg[i] = a.kimg[i];
 
   float2 thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
   {
@@ -153,8 +142,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
     }
   constexpr float kStokesC = -2.0f / 0.69314718055994531f;  // -(1/4pi) / (ln2/8pi)
 
-  const int j0 = blockIdx.y * a.chunk;
-  const int j1 = min(a.ns, j0 + a.chunk);
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
@@ -188,7 +175,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
           }
           float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
           if (i == CENTER) inv = mul2(inv, msk);
-          P = mul2(P, mul2(r2, f2(a.kimg[i])));
+          P = mul2(P, mul2(r2, f2(kimg[i])));
           if (KER == PFMM_LAPLACE) {
             if (GRAD) {
               G1 = fma2(dx, inv, G1);
@@ -248,40 +235,45 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(P2PArgs a) {
       if (KER == PFMM_STOKES) {
         const double cst = -0.69314718055994531 / (8.0 * M_PI);
         double sx = val(0), sy = val(NA - 1);
-        if (blockIdx.y == 0) {
+        if (j0 == 0) {
           const double add = lgc + NIMG * 0.5 * (double)kStokesC;
           sx += add * a.mom[(r0 + r) * 8 + 0];
           sy += add * a.mom[(r0 + r) * 8 + 1];
         }
         const double ux = cst * sx, uy = cst * sy;
-        atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * ux + R[2] * uy);
-        atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * ux + R[3] * uy);
+        atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * ux + R[2] * uy);
+        atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * ux + R[3] * uy);
       } else {
         const double cp = -0.69314718055994531 / (4.0 * M_PI), cg = -1.0 / (2.0 * M_PI);
         double sp = val(0);
-        if (blockIdx.y == 0) sp += lgc * a.mom[(r0 + r) * 8 + 0];
-        if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, cp * sp);
+        if (j0 == 0) sp += lgc * a.mom[(r0 + r) * 8 + 0];
+        if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.os + l, cp * sp);
         if (GRAD && a.grad) {
           const double gx = cg * val(1 % NA), gy = cg * val(2 % NA);
-          atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * gx + R[2] * gy);
-          atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * gx + R[3] * gy);
+          atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * gx + R[2] * gy);
+          atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * gx + R[3] * gy);
         }
       }
     }
   }
 }
 
+template <int KER, int NIMG, int NR, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(const __grid_constant__ P2PArgs a) {
+  const int j0 = blockIdx.y * a.chunk;
+  p2p_mixed_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
+}
+
 // Modified Helmholtz mixed kernel: one target per thread, per-source image
 // sums K0s = sum_i K0(beta r_i), K1x = sum_i K1(beta r_i) dx_i / r_i (and y).
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(P2PArgs a) {
+__device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   constexpr int CENTER = NIMG / 2;
   constexpr int NA = GRAD ? 3 : 1;
   __shared__ float4 s_p[kP2PTile];
   __shared__ float s_q[NR][kP2PTile];
-  const int l = blockIdx.x * kP2PThreads + threadIdx.x;
+  const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
-  const int r0 = a.r0 + blockIdx.z * NR;
   const int nr = min(NR, a.nrhs - r0);
   float thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
   {
@@ -305,8 +297,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(P2PArgs a) {
       S[r][k] = 0.f;
     }
   const float beta = a.beta_f;
-  const int j0 = blockIdx.y * a.chunk;
-  const int j1 = min(a.ns, j0 + a.chunk);
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
@@ -364,12 +354,43 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(P2PArgs a) {
   const double* R = a.g.rot;
   const double cp = 1.0 / (2.0 * M_PI), cg = -a.beta / (2.0 * M_PI);
   for (int r = 0; r < nr; ++r) {
-    if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, cp * K[r][0].value());
+    if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.os + l, cp * K[r][0].value());
     if (GRAD && a.grad) {
       const double gx = cg * K[r][1 % NA].value(), gy = cg * K[r][2 % NA].value();
-      atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * gx + R[2] * gy);
-      atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * gx + R[3] * gy);
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * gx + R[2] * gy);
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * gx + R[3] * gy);
     }
+  }
+}
+
+template <int KER, int NIMG, int NR, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(const __grid_constant__ P2PArgs a) {
+  const int j0 = blockIdx.y * a.chunk;
+  p2p_mixed_mh_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
+}
+
+// Persistent batched kernel: blocks pull work items (cell, target block,
+// source range, rhs group) from an atomic counter until the list is done.
+// Items are sorted by decreasing cost on the host.  No block ever waits on
+// another; the counter is the only shared state.
+// P2PItem is declared in p2p.h
+
+template <int KER, int NIMG, int NR, bool GRAD>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_batch(const P2PArgs* __restrict__ cells,
+                                                           const P2PItem* __restrict__ items, int nitems,
+                                                           int* __restrict__ counter) {
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const P2PItem w = items[it];
+    if constexpr (KER == PFMM_MODHELM)
+      p2p_mixed_mh_body<KER, NIMG, NR, GRAD>(cells[w.cell], w.bx, w.j0, w.j1, w.r0);
+    else
+      p2p_mixed_body<KER, NIMG, NR, GRAD>(cells[w.cell], w.bx, w.j0, w.j1, w.r0);
   }
 }
 
@@ -447,13 +468,13 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_f64(P2PArgs a) {
   const double* R = a.g.rot;
   for (int r = 0; r < nr; ++r) {
     if (KER == PFMM_STOKES) {
-      atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * acc[r][0] + R[2] * acc[r][1]);
-      atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * acc[r][0] + R[3] * acc[r][1]);
+      atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * acc[r][0] + R[2] * acc[r][1]);
+      atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * acc[r][0] + R[3] * acc[r][1]);
     } else {
-      if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.nt + l, acc[r][0]);
+      if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.os + l, acc[r][0]);
       if (GRAD && a.grad) {
-        atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.nt + l, R[0] * acc[r][1] + R[2] * acc[r][2]);
-        atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.nt + l, R[1] * acc[r][1] + R[3] * acc[r][2]);
+        atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * acc[r][1] + R[2] * acc[r][2]);
+        atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * acc[r][1] + R[3] * acc[r][2]);
       }
     }
   }
@@ -509,14 +530,14 @@ static void dispatch_img(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaS
     dispatch_nr<KER, 15>(a, grad, nrhs, ntb, nsc, st);
 }
 
-cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
-                       bool accumulate, cudaStream_t st) {
-  (void)accumulate;
+void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
+                   P2PArgs* out) {
   const Layout& L = p->lay;
   P2PArgs a{};
   a.g = p->geom;
   a.nt = (int)nt;
   a.ns = (int)ns;
+  a.os = p->o_stride;
   a.nrhs = p->opts.nrhs;
   a.trg64 = self ? (const double*)(ws + L.src64) : (const double*)(ws + L.trg64);
   a.src_hl = (const float4*)(ws + L.srchl);
@@ -552,6 +573,16 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
     }
     a.lgc = (float)E;
   }
+  *out = a;
+}
+
+int p2p_targets_per_block(int kernel) { return kP2PThreads * (kernel == PFMM_MODHELM ? 1 : 2); }
+
+cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
+                       bool accumulate, cudaStream_t st) {
+  (void)accumulate;
+  P2PArgs a;
+  fill_p2p_args(p, ws, ns, nt, self, pot, grad, &a);
   const bool mixed = p->opts.precision == PFMM_MIXED;
   const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread
   const int ntb = cdivl(nt, kP2PThreads * (packed ? 2 : 1));
@@ -584,6 +615,66 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
     }
   }
   return cudaGetLastError();
+}
+
+
+template <int KER, int NIMG, int NR, bool GRAD>
+static cudaError_t launch_batch_t(const P2PArgs* cells, const P2PItem* items, int nitems, int* counter, int grid,
+                                  cudaStream_t st) {
+  k_p2p_batch<KER, NIMG, NR, GRAD><<<grid, kP2PThreads, 0, st>>>(cells, items, nitems, counter);
+  return cudaGetLastError();
+}
+
+template <int KER, int NIMG, int NR, bool GRAD>
+static int grid_t() {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_p2p_batch<KER, NIMG, NR, GRAD>, kP2PThreads, 0);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, nb) * std::max(1, sms);
+}
+
+// dispatch over (kernel, nimg in {9, 15}, nr in {1, 2, 4}, grad); Stokes has no grad variant
+#define PFMM_P2P_BATCH_DISPATCH(FN, ...)                                                          \
+  do {                                                                                            \
+    const int ki = kernel == PFMM_LAPLACE ? 0 : (kernel == PFMM_MODHELM ? 1 : 2);                 \
+    const int ii = nimg == 9 ? 0 : 1, ri = nr == 4 ? 2 : (nr == 2 ? 1 : 0), gi = grad ? 1 : 0;    \
+    const int code = ((ki * 2 + ii) * 3 + ri) * 2 + gi;                                           \
+    switch (code) {                                                                               \
+      PFMM_P2P_CASES(FN, __VA_ARGS__)                                                             \
+      default: return FN<PFMM_STOKES, 15, 1, false>(__VA_ARGS__);                                 \
+    }                                                                                             \
+  } while (0)
+#define PFMM_P2P_CASE(FN, K, KI, NI, II, R, RI, G, GI, ...) \
+  case ((KI * 2 + II) * 3 + RI) * 2 + GI: return FN<K, NI, R, G>(__VA_ARGS__);
+#define PFMM_P2P_CASES_KI(FN, K, KI, ...)                                   \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 1, 0, false, 0, __VA_ARGS__)               \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 1, 0, true, 1, __VA_ARGS__)                \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 2, 1, false, 0, __VA_ARGS__)               \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 2, 1, true, 1, __VA_ARGS__)                \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 4, 2, false, 0, __VA_ARGS__)               \
+  PFMM_P2P_CASE(FN, K, KI, 9, 0, 4, 2, true, 1, __VA_ARGS__)                \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 1, 0, false, 0, __VA_ARGS__)              \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 1, 0, true, 1, __VA_ARGS__)               \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 2, 1, false, 0, __VA_ARGS__)              \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 2, 1, true, 1, __VA_ARGS__)               \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 4, 2, false, 0, __VA_ARGS__)              \
+  PFMM_P2P_CASE(FN, K, KI, 15, 1, 4, 2, true, 1, __VA_ARGS__)
+#define PFMM_P2P_CASES(FN, ...)                                  \
+  PFMM_P2P_CASES_KI(FN, PFMM_LAPLACE, 0, __VA_ARGS__)            \
+  PFMM_P2P_CASES_KI(FN, PFMM_MODHELM, 1, __VA_ARGS__)            \
+  PFMM_P2P_CASES_KI(FN, PFMM_STOKES, 2, __VA_ARGS__)
+
+cudaError_t launch_p2p_batch(int kernel, int nimg, int nr, bool grad, const P2PArgs* cells, const P2PItem* items,
+                             int nitems, int* counter, int grid, cudaStream_t st) {
+  if (kernel == PFMM_STOKES) grad = false;
+  PFMM_P2P_BATCH_DISPATCH(launch_batch_t, cells, items, nitems, counter, grid, st);
+}
+
+int p2p_batch_grid(int kernel, int nimg, int nr, bool grad) {
+  if (kernel == PFMM_STOKES) grad = false;
+  PFMM_P2P_BATCH_DISPATCH(grid_t);
 }
 
 }  // namespace pfmm

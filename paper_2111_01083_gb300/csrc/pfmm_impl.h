@@ -75,6 +75,11 @@ struct pfmm_plan {
   double* gl_h;             // [n_gl][2] (ybar_n, sigma_n) on [-eta/2, eta/2]
   double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
   pfmm::Layout lay;
+  // row strides of the caller's arrays for the current execute: sources
+  // (src [2][*], q [nrhs][comp][*]), targets (trg [2][*]) and outputs
+  // (pot/grad [nrhs][comp][*]); equal to ns / nt for a single cell, to the
+  // concatenated totals for a batch
+  int64_t s_stride, t_stride, o_stride;
   // tracing / bookkeeping
   bool prof;
   cudaEvent_t ev[4];
@@ -94,6 +99,10 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
                        double* pot, double* grad, bool accumulate, cudaStream_t st);
 // records a thread-local error message (pfmm_last_error) and returns s
 pfmm_status set_error(pfmm_status s, const char* fmt, ...);
+cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st);
+pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q, int64_t nt,
+                         const double* trg, double* pot, double* grad, cudaStream_t st, bool self, bool upload,
+                         bool near);
 // kernels launched by the most recent launch_* call (set by each launcher)
 extern thread_local int g_launches;
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);

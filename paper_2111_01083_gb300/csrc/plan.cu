@@ -35,6 +35,10 @@ pfmm_status fail(pfmm_status s, const char* fmt, ...) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+pfmm_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(PFMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
 // Sec. 1: canonical cell.  Lagrange-Gauss reduction (same lattice), longer
 // reduced vector -> e1 rotated onto +x, shorter -> e2 flipped to eta > 0.
 bool canonicalize(const double e1[2], const double e2[2], Geom* g) {
@@ -153,6 +157,72 @@ pfmm_status set_error(pfmm_status s, const char* fmt, ...) {
   va_end(ap);
   g_err = buf;
   return s;
+}
+
+// Copy the plan's host tables (west/east nodes, GL lines, ES transform) into
+// the workspace.
+cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st) {
+  size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (p->Nq > 0) e = cudaMemcpyAsync(ws + p->lay.nodes, p->nodes_h, p->Nq * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + p->lay.nodes + nb, p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ws + p->lay.nodes + nb + p->n_gl * 2 * sizeof(double), p->phihat_h,
+                        (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+  return e;
+}
+
+// One cell: clear accumulators, (optionally) upload tables, prep, far field,
+// (optionally) near-image P2P.  Arguments were validated by the caller, which
+// also set p->s_stride / t_stride / o_stride.
+pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q, int64_t nt,
+                         const double* trg, double* pot, double* grad, cudaStream_t st, bool self, bool upload,
+                         bool near) {
+  cudaError_t e;
+  e = cudaMemsetAsync(ws + p->lay.status, 0, p->lay.nodes - p->lay.status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  e = cudaMemsetAsync(ws + p->lay.coef, 0, p->lay.wts - p->lay.coef, st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  if (upload) {
+    e = upload_tables(p, ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload tables");
+  }
+  p->nlaunch = 0;
+  p->npairs = 0;
+  auto rec = [&](int i) { if (p->prof) cudaEventRecord(p->ev[i], st); };
+  rec(0);
+  if (nt == 0) {
+    rec(1); rec(2); rec(3);
+    return PFMM_OK;
+  }
+  if (ns > 0) {
+    e = launch_prep(p, ws, ns, src, q, nt, trg, self, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
+    p->nlaunch += g_launches;
+  }
+  rec(1);
+  unsigned fl = p->opts.flags;
+  bool do_far = !(fl & PFMM_NEAR_ONLY) && ns > 0;
+  bool do_near = near && ns > 0;
+  if (do_far) {
+    e = (p->path == PFMM_PATH_NUFFT) ? launch_far_nufft(p, ws, ns, nt, self, pot, grad, st)
+                                     : launch_far_direct(p, ws, ns, nt, self, pot, grad, st);
+    if (e != cudaSuccess) return cuda_fail(e, "far-field kernels");
+    p->nlaunch += g_launches;
+  } else {
+    e = launch_zero_out(p, nt, pot, grad, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zero outputs");
+  }
+  rec(2);
+  if (do_near) {
+    e = launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, "p2p kernel");
+    p->nlaunch += g_launches;
+    p->npairs = (int64_t)ns * nt * p->geom.nimg;
+  }
+  rec(3);
+  return PFMM_OK;
 }
 }  // namespace pfmm
 
@@ -380,10 +450,6 @@ pfmm_status pfmm_profile_read(pfmm_plan* p, float* ms, int n) {
   return PFMM_OK;
 }
 
-static pfmm_status cuda_fail(cudaError_t e, const char* what) {
-  return fail(PFMM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
 pfmm_status pfmm_execute(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
                          const double* q, int64_t nt, const double* trg, double* pot, double* grad,
                          void* stream) {
@@ -401,61 +467,11 @@ pfmm_status pfmm_execute(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t
   if (ns > 0 && (!src || !q)) return fail(PFMM_ERR_INVALID_ARG, "NULL sources/strengths");
   bool self = (trg == src) && (nt == ns);
   if (trg == src && nt != ns) return fail(PFMM_ERR_INVALID_ARG, "targets alias sources but nt != ns");
-  cudaStream_t st = (cudaStream_t)stream;
-  char* ws = (char*)workspace;
-  cudaError_t e;
-  // clear status, moments and coefficient accumulators; upload tables
-  e = cudaMemsetAsync(ws + p->lay.status, 0, p->lay.nodes - p->lay.status, st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  e = cudaMemsetAsync(ws + p->lay.coef, 0, p->lay.wts - p->lay.coef, st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  {
-    size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
-    if (p->Nq > 0) {
-      e = cudaMemcpyAsync(ws + p->lay.nodes, p->nodes_h, p->Nq * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
-      if (e != cudaSuccess) return cuda_fail(e, "upload nodes");
-    }
-    e = cudaMemcpyAsync(ws + p->lay.nodes + nb, p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "upload gl");
-    e = cudaMemcpyAsync(ws + p->lay.nodes + nb + p->n_gl * 2 * sizeof(double), p->phihat_h,
-                        (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "upload phihat");
-  }
-  p->nlaunch = 0;
-  p->npairs = 0;
-  auto rec = [&](int i) { if (p->prof) cudaEventRecord(p->ev[i], st); };
-  rec(0);
-  if (nt == 0) {
-    rec(1); rec(2); rec(3);
-    return PFMM_OK;
-  }
-  if (ns > 0) {
-    e = launch_prep(p, ws, ns, src, q, nt, trg, self, st);
-    if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
-    p->nlaunch += g_launches;
-  }
-  rec(1);
-  unsigned fl = p->opts.flags;
-  bool do_far = !(fl & PFMM_NEAR_ONLY) && ns > 0;
-  bool do_near = !(fl & PFMM_FAR_ONLY) && ns > 0;
-  if (do_far) {
-    e = (p->path == PFMM_PATH_NUFFT) ? launch_far_nufft(p, ws, ns, nt, self, pot, grad, st)
-                                     : launch_far_direct(p, ws, ns, nt, self, pot, grad, st);
-    if (e != cudaSuccess) return cuda_fail(e, "far-field kernels");
-    p->nlaunch += g_launches;
-  } else {
-    e = launch_zero_out(p, nt, pot, grad, st);
-    if (e != cudaSuccess) return cuda_fail(e, "zero outputs");
-  }
-  rec(2);
-  if (do_near) {
-    e = launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
-    if (e != cudaSuccess) return cuda_fail(e, "p2p kernel");
-    p->nlaunch += g_launches;
-    p->npairs = (int64_t)ns * nt * p->geom.nimg;
-  }
-  rec(3);
-  return PFMM_OK;
+  p->s_stride = ns;
+  p->t_stride = nt;
+  p->o_stride = nt;
+  return pfmm::execute_cell(p, (char*)workspace, ns, src, q, nt, trg, pot, grad, (cudaStream_t)stream, self, true,
+                            !(p->opts.flags & PFMM_FAR_ONLY));
 }
 
 pfmm_status pfmm_execute_host(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,

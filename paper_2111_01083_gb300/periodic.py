@@ -148,3 +148,155 @@ class PeriodicOp:
         ws = self.workspace()
         st = stream if stream is not None else torch.cuda.current_stream(ws.device).cuda_stream
         _lib.check(_lib.lib().pfmm_get_status(self._h, _ptr(ws), ctypes.c_void_p(st)))
+
+
+def _opts(kernel, e1, e2, beta, tol, precision, path, nufft_w, n_gl, nrhs, flags):
+    o = _lib.Opts()
+    o.e1[0], o.e1[1] = float(e1[0]), float(e1[1])
+    o.e2[0], o.e2[1] = float(e2[0]), float(e2[1])
+    o.kernel = _KER[kernel]
+    o.beta = float(beta)
+    o.tol = float(tol)
+    o.precision = _PREC[precision]
+    o.path = _PATH[path]
+    o.nufft_w = int(nufft_w)
+    o.n_gl = int(n_gl)
+    o.nrhs = int(nrhs)
+    o.flags = int(flags)
+    return o
+
+
+class BatchOp:
+    """Many independent cells in one call (pfmm_batch_*).
+
+    cells: list of dicts with e1, e2 and optionally beta, tol; shared kernel,
+    precision and nrhs.  src_counts / trg_counts: points per cell (targets
+    default to the sources).  Inputs are the concatenated arrays
+    src [2, NS], q [nrhs, NS] (Stokes [nrhs, 2, NS]), trg [2, NT]."""
+
+    def __init__(self, kernel, cells, src_counts, trg_counts=None, precision="mixed", nrhs=1, tol=1e-6,
+                 path="auto", p2p_chunk=0):
+        L = _lib.lib()
+        n = len(cells)
+        arr = (_lib.Opts * n)()
+        for i, c in enumerate(cells):
+            arr[i] = _opts(kernel, c["e1"], c["e2"], c.get("beta", 0.0), c.get("tol", tol), precision, path, 0, 0,
+                           nrhs, 0)
+        so = np.concatenate([[0], np.cumsum(src_counts)]).astype(np.int64)
+        self._so = (ctypes.c_int64 * (n + 1))(*so.tolist())
+        self._to = None
+        if trg_counts is not None:
+            to = np.concatenate([[0], np.cumsum(trg_counts)]).astype(np.int64)
+            self._to = (ctypes.c_int64 * (n + 1))(*to.tolist())
+        h = ctypes.c_void_p()
+        _lib.check(L.pfmm_batch_create(arr, n, self._so, self._to, int(p2p_chunk), ctypes.byref(h)))
+        self._h = h
+        sz = ctypes.c_size_t()
+        _lib.check(L.pfmm_batch_workspace_size(h, ctypes.byref(sz)))
+        self.ws_bytes = sz.value
+        self.kernel, self.nrhs, self.ncell = kernel, int(nrhs), n
+        self.NS = int(so[-1])
+        self.NT = int(self.NS if trg_counts is None else np.sum(trg_counts))
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            try:
+                _lib.lib().pfmm_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def workspace(self, device):
+        import torch
+        if self._ws is None:
+            self._ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def alloc_out(self, device, grad=True):
+        import torch
+        stokes = self.kernel == "stokes"
+        pot = torch.empty((self.nrhs, 2, self.NT) if stokes else (self.nrhs, self.NT), dtype=torch.float64,
+                          device=device)
+        g = torch.empty((self.nrhs, 2, self.NT), dtype=torch.float64, device=device) if (grad and not stokes) else None
+        return pot, g
+
+    def __call__(self, src, q, trg=None, out=None, grad=True, stream=None):
+        import torch
+        if out is None:
+            out = self.alloc_out(src.device, grad)
+        pot, g = out
+        ws = self.workspace(src.device)
+        st = stream if stream is not None else torch.cuda.current_stream(src.device).cuda_stream
+        _lib.check(_lib.lib().pfmm_batch_execute(self._h, _ptr(ws), ws.numel(), _ptr(src), _ptr(q), _ptr(trg),
+                                                 _ptr(pot), _ptr(g), ctypes.c_void_p(st)))
+        return pot, g
+
+    def status(self, device, stream=None):
+        import torch
+        ws = self.workspace(device)
+        st = stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
+        _lib.check(_lib.lib().pfmm_batch_get_status(self._h, _ptr(ws), ctypes.c_void_p(st)))
+
+    def capture(self, src, q, trg=None, out=None, grad=True):
+        """Record one execute in a CUDA graph (after a first execute on the same
+        buffers, which uploads the descriptors).  Returns (graph, out)."""
+        import torch
+        if out is None:
+            out = self.alloc_out(src.device, grad)
+        self(src, q, trg, out=out)  # uploads descriptors for these buffers
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(src.device)
+        s.wait_stream(torch.cuda.current_stream(src.device))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            # the upload is keyed on the buffers; the same buffers -> kernels only
+            with torch.cuda.graph(graph, stream=s):
+                self(src, q, trg, out=out, stream=s.cuda_stream)
+        torch.cuda.current_stream(src.device).wait_stream(s)
+        return graph, out
+
+
+def autotune_batch(make_op, src, q, trg=None, candidates=(1024, 2048, 4096, 8192), reps=2, cache=None, key=None):
+    """Pick the P2P source-chunk size of a batch by timing each candidate
+    (CUDA events); make_op(p2p_chunk) -> BatchOp.  With a cache path and key,
+    results persist across runs as JSON.  Returns (best_chunk, timings_ms)."""
+    import json
+    import os
+    import torch
+    if cache and key and os.path.exists(cache):
+        try:
+            d = json.load(open(cache))
+            if key in d:
+                return d[key]["p2p_chunk"], d[key]["ms"]
+        except Exception:
+            pass
+    times = {}
+    for c in candidates:
+        op = make_op(c)
+        out = op(src, q, trg)
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            op(src, q, trg, out=out)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        times[c] = best
+        del op
+    chunk = min(times, key=times.get)
+    if cache and key:
+        d = {}
+        if os.path.exists(cache):
+            try:
+                d = json.load(open(cache))
+            except Exception:
+                d = {}
+        d[key] = {"p2p_chunk": chunk, "ms": times}
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        json.dump(d, open(cache, "w"), indent=1)
+    return chunk, times
