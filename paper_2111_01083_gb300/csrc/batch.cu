@@ -88,7 +88,9 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
   }
   // P2P work items (mixed precision: one persistent kernel per near-block shape)
   const int tpb = p2p_targets_per_block(b->kernel);
-  const int nr = b->nrhs % 4 == 0 ? 4 : (b->nrhs % 2 == 0 ? 2 : 1);
+  // rhs per item: 8 for modified Helmholtz (one Bessel evaluation serves 8 rhs), else up to 4
+  const int nr = (b->kernel == PFMM_MODHELM && b->nrhs % 8 == 0) ? 8
+                 : (b->nrhs % 4 == 0 ? 4 : (b->nrhs % 2 == 0 ? 2 : 1));
   for (int nimg : {9, 15}) {
     pfmm_batch::Group g{nimg, nr, b->items.size(), 0, 0};
     std::vector<std::pair<double, P2PItem>> v;

@@ -28,6 +28,19 @@ __device__ __forceinline__ void k01f(float x, float* k0, float* k1) {
   }
 }
 
+// FP32 K0 only (same fits as k01f).
+__device__ __forceinline__ float k0f(float x) {
+  if (x <= 2.0f) {
+    float t = x * (1.0f / 3.75f);
+    float t2 = t * t;
+    float i0 = 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f + t2 * (0.0360768f + t2 * 0.0045813f)))));
+    float y = 0.25f * x * x;
+    return -__logf(0.5f * x) * i0 + (-0.57721566f + y * (0.42278420f + y * (0.23069756f + y * (0.03488590f + y * (0.00262698f + y * (0.00010750f + y * 0.0000074f))))));
+  }
+  float y = 2.0f / x;
+  return __expf(-x) * rsqrtf(x) * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+}
+
 // FP64.  x <= 2: the ascending series (DLMF 10.31.1-10.31.2),
 //   K0 = -(ln(x/2) + gamma) I0(x) + sum_{k>=1} H_k (x^2/4)^k / (k!)^2,
 //   K1 = 1/x + ln(x/2) I1(x) - (x/4) sum_{k>=0} (psi(k+1) + psi(k+2)) (x^2/4)^k / (k! (k+1)!).

@@ -297,6 +297,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
       S[r][k] = 0.f;
     }
   const float beta = a.beta_f;
+  const float cut2 = (50.0f / beta) * (50.0f / beta);
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
@@ -321,14 +322,20 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
             msk = (r2 > 0.0f) ? 1.0f : 0.0f;
             r2 = (r2 > 0.0f) ? r2 : 1.0f;
           }
-          const float ir = rsqrt_approx(r2);
-          float k0, k1;
-          bes::k01f(beta * r2 * ir, &k0, &k1);
-          K0s = fmaf(k0, msk, K0s);
-          if (GRAD) {
-            const float k1r = k1 * ir * msk;
-            K1x = fmaf(k1r, dx, K1x);
-            K1y = fmaf(k1r, dy, K1y);
+          // K0(beta r) < 1e-22 for beta r > 50: such pairs are skipped (the
+          // branch is not taken at all when no lane of the warp needs it)
+          if (r2 < cut2) {
+            const float ir = rsqrt_approx(r2);
+            if (GRAD) {
+              float k0, k1;
+              bes::k01f(beta * r2 * ir, &k0, &k1);
+              K0s = fmaf(k0, msk, K0s);
+              const float k1r = k1 * ir * msk;
+              K1x = fmaf(k1r, dx, K1x);
+              K1y = fmaf(k1r, dy, K1y);
+            } else {
+              K0s = fmaf(bes::k0f(beta * r2 * ir), msk, K0s);
+            }
           }
         }
 #pragma unroll
@@ -507,6 +514,14 @@ static void dispatch_nr(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaSt
   while (r < nrhs) {
     int left = nrhs - r;
     a.r0 = r;
+    if constexpr (KER == PFMM_MODHELM) {
+      if (left >= 8) {
+        int ng = left / 8;
+        launch_mixed<KER, NIMG, 8>(a, grad, dim3(ntb, nsc, ng), st);
+        r += 8 * ng;
+        continue;
+      }
+    }
     if (left >= 4) {
       int ng = left / 4;
       launch_mixed<KER, NIMG, 4>(a, grad, dim3(ntb, nsc, ng), st);
@@ -640,9 +655,13 @@ static int grid_t() {
   do {                                                                                            \
     const int ki = kernel == PFMM_LAPLACE ? 0 : (kernel == PFMM_MODHELM ? 1 : 2);                 \
     const int ii = nimg == 9 ? 0 : 1, ri = nr == 4 ? 2 : (nr == 2 ? 1 : 0), gi = grad ? 1 : 0;    \
-    const int code = ((ki * 2 + ii) * 3 + ri) * 2 + gi;                                           \
+    const int code = nr == 8 ? 1000 + ii * 2 + gi : ((ki * 2 + ii) * 3 + ri) * 2 + gi;            \
     switch (code) {                                                                               \
       PFMM_P2P_CASES(FN, __VA_ARGS__)                                                             \
+      case 1000: return FN<PFMM_MODHELM, 9, 8, false>(__VA_ARGS__);                               \
+      case 1001: return FN<PFMM_MODHELM, 9, 8, true>(__VA_ARGS__);                                \
+      case 1002: return FN<PFMM_MODHELM, 15, 8, false>(__VA_ARGS__);                              \
+      case 1003: return FN<PFMM_MODHELM, 15, 8, true>(__VA_ARGS__);                               \
       default: return FN<PFMM_STOKES, 15, 1, false>(__VA_ARGS__);                                 \
     }                                                                                             \
   } while (0)
