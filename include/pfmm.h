@@ -76,7 +76,9 @@ typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } p
 enum {
   PFMM_FAR_ONLY = 1,   /* output P2 q only (no near-image sum)            */
   PFMM_NEAR_ONLY = 2,  /* output K^near q only                            */
-  PFMM_NO_GRAD = 4     /* scalar kernels: skip the gradient even if given */
+  PFMM_NO_GRAD = 4,    /* scalar kernels: skip the gradient even if given */
+  PFMM_PROJECT_NEUTRAL = 8 /* Laplace/Stokes: subtract the mean strength (force) per rhs
+                              before use, i.e. apply the operator to the zero-net part */
 };
 
 typedef enum {
@@ -203,6 +205,31 @@ void pfmm_batch_destroy(pfmm_batch* batch);
  * outputs and errors otherwise as pfmm_execute (device pointers). */
 pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const double* src, const double* q, int64_t nt,
                                 const double* trg, double* pot, double* grad, void* stream);
+
+/* Adjoint (reverse-mode derivative) of pfmm_execute for the potential output.
+ * Given g = dL/dpot [nrhs][nt] (device), computes, each only if its pointer is
+ * non-NULL:
+ *   dq   [nrhs][ns]   dL/dq_j     = sum_l g_l K(t_l, s_j)      (= (P^T g)_j = (P g)_j:
+ *                     the periodic operator is symmetric since the far lattice is
+ *                     symmetric and G is even; computed by the same kernels with the
+ *                     roles of sources and targets swapped)
+ *   dsrc [2][ns]      dL/ds_j     = sum_r q_rj grad psi_r(s_j), psi_r = field of the
+ *                     charges g_r placed at the targets (scalar kernels only)
+ *   dtrg [2][nt]      dL/dt_l     = sum_r g_rl grad u_r(t_l); needs grad_fwd
+ *                     [nrhs][2][nt], the gradient output of the forward call.
+ *                     With targets = sources, dtrg == dsrc (same pointer) returns
+ *                     the sum of both roles in that one array.
+ * Laplace/Stokes potentials are defined up to a constant, so only the
+ * mean-free part of g matters; g is projected to zero mean per rhs (and
+ * component) before use.  Stokes: dq only (g is [nrhs][2][nt], dq [nrhs][2][ns]).
+ * The plan must admit the swapped sizes: nt <= ns_max and ns <= nt_max
+ * (automatic when targets = sources).  src, q, trg as in the forward call.
+ * Nothing is stored between the forward and the adjoint: the plane-wave
+ * factors are recomputed.  Not in the paper (it applies the operator only). */
+pfmm_status pfmm_execute_adjoint(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns,
+                                 const double* src, const double* q, int64_t nt, const double* trg,
+                                 const double* g, const double* grad_fwd, double* dq, double* dsrc,
+                                 double* dtrg, void* stream);
 
 /* Synchronise the stream and read the device status word written by the
  * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,

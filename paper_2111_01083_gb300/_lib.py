@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libpfmm.so")
 PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES = 0, 1, 2
 PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
-PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD = 1, 2, 4
+PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL = 1, 2, 4, 8
 
 STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PFMM_ERR_NOT_NEUTRAL",
           4: "PFMM_ERR_TOLERANCE", 5: "PFMM_ERR_WORKSPACE", 6: "PFMM_ERR_CUDA", 7: "PFMM_ERR_NONFINITE",
@@ -23,7 +23,7 @@ EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host"
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
            "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static",
            "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
-           "pfmm_batch_destroy"]
+           "pfmm_batch_destroy", "pfmm_execute_adjoint"]
 
 
 class Opts(ctypes.Structure):
@@ -83,6 +83,8 @@ def lib():
     L.pfmm_batch_get_status.restype = ctypes.c_int
     L.pfmm_batch_destroy.argtypes = [vp]
     L.pfmm_batch_destroy.restype = None
+    L.pfmm_execute_adjoint.argtypes = [vp, vp, sz, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
+    L.pfmm_execute_adjoint.restype = ctypes.c_int
     L.pfmm_get_status.argtypes = [vp, vp, vp]
     L.pfmm_get_status.restype = ctypes.c_int
     L.pfmm_last_error.argtypes = []

@@ -51,11 +51,27 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   }
 }
 
+// Optional projection to zero net charge / force: net sums per rhs and
+// component (input frame) into mom[r*8 + 5 + c]; k_prep_q then subtracts the
+// mean before using the strengths.
+__global__ void k_net(int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
+                      double* __restrict__ mom) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int lane = threadIdx.x & 31;
+  for (int r = 0; r < nrhs; ++r)
+    for (int c = 0; c < ncomp; ++c) {
+      double v = (i < ns) ? q[((size_t)r * ncomp + c) * qs + i] : 0.0;
+      if (!isfinite(v)) v = 0.0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) atomicAdd(mom + r * 8 + 5 + c, v);
+    }
+}
+
 // K0: strengths (canonical frame) and FP64 moments per rhs:
 //   mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y, [2] = sum |q| (all comps), [3] = sum q y' (f_x y')
 __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
                          const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
-                         double* __restrict__ mom, int* __restrict__ status) {
+                         double* __restrict__ mom, int* __restrict__ status, int project) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool in = i < ns;
   double y = in ? src64[ns + i] : 0.0;
@@ -65,8 +81,13 @@ __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, co
     if (in) {
       if (ncomp == 1) {
         a = q[(size_t)r * qs + i];
+        if (project) a -= mom[r * 8 + 5] / (double)ns;
       } else {
         double fx = q[((size_t)r * 2) * qs + i], fy = q[((size_t)r * 2 + 1) * qs + i];
+        if (project) {
+          fx -= mom[r * 8 + 5] / (double)ns;
+          fy -= mom[r * 8 + 6] / (double)ns;
+        }
         a = g.rot[0] * fx + g.rot[1] * fy;
         b = g.rot[2] * fx + g.rot[3] * fy;
       }
@@ -547,9 +568,14 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
     k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
                                                    (int*)(ws + L.trgU), nullptr, status);
   g_launches = (!self && nt > 0) ? 3 : 2;
+  const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) && p->opts.kernel != PFMM_MODHELM;
+  if (project) {
+    k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (double*)(ws + L.moments));
+    ++g_launches;
+  }
   k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
                                             (double*)(ws + L.qc), (float*)(ws + L.qf), (double*)(ws + L.moments),
-                                            status);
+                                            status, project);
   return cudaGetLastError();
 }
 
@@ -603,6 +629,38 @@ cudaError_t launch_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t 
       return mixed ? run_far_direct<float, float2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st)
                    : run_far_direct<double, double2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st);
   }
+}
+
+// Adjoint contractions:  out[k][j] = sum_r a[r][j] * b[r][k][j]  (k = 0, 1), with
+// row strides sa for a and sb for b; used for dL/ds_j = sum_r q_rj grad psi_r(s_j)
+// and dL/dt_l = sum_r g_rl grad u_r(t_l).
+// A second pair (c, d) is added when c != NULL (targets = sources: both the
+// source and the target role of a point contribute to one derivative).
+__global__ void k_contract(int nrhs, int64_t n, const double* __restrict__ a, int64_t sa,
+                           const double* __restrict__ b, int64_t sb, const double* __restrict__ c,
+                           const double* __restrict__ d, double* __restrict__ out) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double x = 0.0, y = 0.0;
+  for (int r = 0; r < nrhs; ++r) {
+    const double w = a[(size_t)r * sa + j];
+    x += w * b[((size_t)r * 2) * sb + j];
+    y += w * b[((size_t)r * 2 + 1) * sb + j];
+    if (c) {
+      const double v = c[(size_t)r * sa + j];
+      x += v * d[((size_t)r * 2) * sb + j];
+      y += v * d[((size_t)r * 2 + 1) * sb + j];
+    }
+  }
+  out[j] = x;
+  out[n + j] = y;
+}
+
+cudaError_t launch_contract(int nrhs, int64_t n, const double* a, int64_t sa, const double* b, int64_t sb,
+                            const double* c, const double* d, double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_contract<<<cdiv_i(n, 256), 256, 0, st>>>(nrhs, n, a, sa, b, sb, c, d, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st) {

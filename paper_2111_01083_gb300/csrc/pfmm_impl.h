@@ -50,6 +50,7 @@ struct Layout {
   size_t coef;             // double2 [nrhs][nch][nterm]
   size_t wts;              // weights for evaluation: double2 or float2 [nrhs][nwch][nterm]
   size_t nufft;            // NUFFT scratch (grids, spectra)
+  size_t adj;              // adjoint scratch (gradient of the adjoint field, potential if dq is not wanted)
   size_t stage;            // host-staging region (pfmm_execute_host only)
   size_t total, total_host;
 };
@@ -106,4 +107,6 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
 // kernels launched by the most recent launch_* call (set by each launcher)
 extern thread_local int g_launches;
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);
+cudaError_t launch_contract(int nrhs, int64_t n, const double* a, int64_t sa, const double* b, int64_t sb,
+                            const double* c, const double* d, double* out, cudaStream_t st);
 }  // namespace pfmm

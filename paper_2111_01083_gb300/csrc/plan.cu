@@ -372,6 +372,10 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
           (size_t)nrhs * npk * nf * cplx + 256;
   }
   L.nufft = take(nuf);
+  // adjoint scratch: dL/dpot projected as strengths is handled in place; the
+  // gradient of the adjoint field at the sources needs [nrhs][2][max n]
+  L.adj = take((size_t)nrhs * 2 * std::max(ns_max, nt_max) * sizeof(double) +
+               (size_t)nrhs * p->ncomp * std::max(ns_max, nt_max) * sizeof(double));
   L.total = off;
   size_t ncq = (size_t)nrhs * p->ncomp;
   L.stage = off;
@@ -505,6 +509,56 @@ pfmm_status pfmm_execute_host(pfmm_plan* p, void* workspace, size_t ws_bytes, in
   if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, d_grad, (size_t)nrhs * 2 * nt * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "read back outputs");
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_execute_adjoint(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
+                                 const double* q, int64_t nt, const double* trg, const double* g,
+                                 const double* grad_fwd, double* dq, double* dsrc, double* dtrg, void* stream) {
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (ns < 0 || nt < 0 || nt > p->ns_max || ns > p->nt_max || ns > p->ns_max || nt > p->nt_max)
+    return fail(PFMM_ERR_INVALID_ARG, "adjoint needs nt <= ns_max and ns <= nt_max (ns=%lld nt=%lld)", (long long)ns,
+                (long long)nt);
+  if (!workspace || ws_bytes < p->lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
+  const bool stokes = p->opts.kernel == PFMM_STOKES;
+  if (stokes && (dsrc || dtrg)) return fail(PFMM_ERR_INVALID_ARG, "Stokes adjoint: strengths only (dq)");
+  if (dtrg && !grad_fwd) return fail(PFMM_ERR_INVALID_ARG, "dtrg needs the forward gradient grad_fwd");
+  if (p->opts.flags & (PFMM_FAR_ONLY | PFMM_NEAR_ONLY))
+    return fail(PFMM_ERR_INVALID_ARG, "the adjoint is defined for the full operator");
+  if ((ns > 0 && (!src || !q)) || (nt > 0 && (!trg || !g))) return fail(PFMM_ERR_INVALID_ARG, "NULL inputs");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const bool self = (trg == src) && (nt == ns);
+  const int nrhs = p->opts.nrhs;
+  const int64_t nmax = std::max(p->ns_max, p->nt_max);
+  double* adj_grad = (double*)(ws + p->lay.adj);             // [nrhs][2][ns]
+  double* adj_pot = adj_grad + (size_t)nrhs * 2 * nmax;      // [nrhs][ncomp][ns]
+  cudaError_t e;
+  if (dq || dsrc) {
+    // sources = targets of the forward call with strengths g, targets = forward sources
+    const unsigned saved = p->opts.flags;
+    p->opts.flags = saved | PFMM_PROJECT_NEUTRAL;
+    p->s_stride = nt;
+    p->t_stride = ns;
+    p->o_stride = ns;
+    double* pot_out = dq ? dq : adj_pot;
+    pfmm_status s = pfmm::execute_cell(p, ws, nt, self ? src : trg, g, ns, src, pot_out, dsrc ? adj_grad : nullptr,
+                                       st, self, true, true);
+    p->opts.flags = saved;
+    if (s != PFMM_OK) return s;
+    if (dsrc) {
+      // targets = sources with dsrc == dtrg: one array receives both roles
+      const bool both = self && dtrg == dsrc;
+      e = launch_contract(nrhs, ns, q, ns, adj_grad, ns, both ? g : nullptr, both ? grad_fwd : nullptr, dsrc, st);
+      if (e != cudaSuccess) return cuda_fail(e, "contract");
+      if (both) return PFMM_OK;
+    }
+  }
+  if (dtrg) {
+    e = launch_contract(nrhs, nt, g, nt, grad_fwd, nt, nullptr, nullptr, dtrg, st);
+    if (e != cudaSuccess) return cuda_fail(e, "contract");
+  }
   return PFMM_OK;
 }
 

@@ -300,3 +300,71 @@ def autotune_batch(make_op, src, q, trg=None, candidates=(1024, 2048, 4096, 8192
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
         json.dump(d, open(cache, "w"), indent=1)
     return chunk, times
+
+
+def _adjoint(op, src, q, trg, g, grad_fwd, need_q, need_s, need_t):
+    import torch
+    self_t = trg is None
+    tr = src if self_t else trg
+    ns, nt = src.shape[1], tr.shape[1]
+    g = g.contiguous()
+    dq = torch.empty_like(q) if need_q else None
+    dsrc = torch.empty_like(src) if need_s else None
+    if self_t and need_s and need_t:
+        dtrg = dsrc  # one array receives both roles
+    else:
+        dtrg = torch.empty_like(tr) if (need_t and not self_t) else None
+    ws = op.workspace()
+    st = torch.cuda.current_stream(src.device).cuda_stream
+    _lib.check(_lib.lib().pfmm_execute_adjoint(op._h, _ptr(ws), ws.numel(), ns, _ptr(src), _ptr(q), nt, _ptr(tr),
+                                               _ptr(g), _ptr(grad_fwd), _ptr(dq), _ptr(dsrc), _ptr(dtrg),
+                                               ctypes.c_void_p(st)))
+    return dq, dsrc, (None if self_t else dtrg)
+
+
+def _make_function():
+    import torch
+
+    class PeriodicFunction(torch.autograd.Function):
+        """u = K^(p) q as a differentiable function of (src, q, trg).  Backward
+        runs pfmm_execute_adjoint (the operator with sources and targets swapped,
+        derivative-kernel evaluation for positions); nothing but the inputs and
+        the forward gradient is stored.  Derivatives through the gradient output
+        (second derivatives of G) are not provided."""
+
+        @staticmethod
+        def forward(ctx, op, src, q, trg):
+            pot, grad = op(src, q, trg, grad=op.kernel != "stokes")
+            ctx.op = op
+            ctx.self_t = trg is None
+            ctx.save_for_backward(src, q, trg if trg is not None else src, grad if grad is not None else pot)
+            if grad is not None:
+                ctx.mark_non_differentiable(grad)
+                return pot, grad
+            return pot
+
+        @staticmethod
+        def backward(ctx, g_pot, *rest):
+            src, q, trg, grad = ctx.saved_tensors
+            op = ctx.op
+            need_s, need_q, need_t = ctx.needs_input_grad[1], ctx.needs_input_grad[2], ctx.needs_input_grad[3]
+            if ctx.self_t:
+                need_t = need_s
+            dq, dsrc, dtrg = _adjoint(op, src, q, None if ctx.self_t else trg, g_pot, grad if op.kernel != "stokes"
+                                      else None, need_q, need_s and op.kernel != "stokes",
+                                      need_t and op.kernel != "stokes")
+            return None, dsrc, dq, dtrg
+
+    return PeriodicFunction
+
+
+_FN = None
+
+
+def periodic(op, src, q, trg=None):
+    """Differentiable application of a PeriodicOp: returns pot (and, for the
+    scalar kernels, the gradient as a non-differentiable second output)."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    return _FN.apply(op, src, q, trg)
