@@ -241,6 +241,58 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def run_adjoint(args, rank, world, local):
+    """Differentiation workload: E = 1/2 sum q_i phi(x_i) (Laplace, targets =
+    sources); one step = forward operator + backward (dE/dq and the forces
+    dE/dx through pfmm_execute_adjoint)."""
+    import torch
+    import workloads
+    from paper_2111_01083_gb300 import PeriodicOp, periodic
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.make(args.workload, scale=args.scale)
+    n = w["src"].shape[1]
+    S = torch.tensor(w["src"], device=dev, requires_grad=True)
+    Q = torch.tensor(w["q"], device=dev, requires_grad=True)
+    op = PeriodicOp("laplace", w["e1"], w["e2"], tol=w["tol"], precision="mixed", ns_max=n, nt_max=n)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        S.grad = None
+        Q.grad = None
+        pot, _ = periodic(op, S, Q)
+        (0.5 * (Q * pot).sum()).backward()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    op.status()
+    clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
+    proc, fh = start_clocks(clk_path)
+    time.sleep(0.3)
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    clocks = stop_clocks(proc, fh, clk_path, local)
+    ms = sum(ts) / len(ts)
+    line = {"metric": METRIC, "value": world * 2 * n / (ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
+            "config": {"workload": args.workload, "kernel": "laplace", "n": n, "step": "forward + backward (dE/dq, dE/dx)",
+                       "l2": "flushed (256 MiB write) before each timed step"},
+            "roofline": None, "cpu_baseline": None, "clocks": clocks, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +302,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload.startswith("batch_modhelm_beta"):
         return run_batch(args, rank, world, local)
+    if "adjoint" in args.workload:
+        return run_adjoint(args, rank, world, local)
 
     import numpy as np
     import torch

@@ -7,7 +7,8 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpfmm.so")
+# PFMM_LIB overrides the library path (profiling experiments only)
+LIB_PATH = os.environ.get("PFMM_LIB") or os.path.join(HERE, "libpfmm.so")
 
 PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES = 0, 1, 2
 PFMM_FP64, PFMM_MIXED = 0, 1

@@ -23,9 +23,19 @@
 
 namespace pfmm {
 
+#ifndef PFMM_P2P_SUB
+#define PFMM_P2P_SUB 16
+#endif
+#ifndef PFMM_P2P_MINB
+#define PFMM_P2P_MINB 1
+#endif
+#ifndef PFMM_P2P_UNROLL
+#define PFMM_P2P_UNROLL 4
+#endif
 constexpr int kP2PThreads = 128;
 constexpr int kP2PTile = 128;
-constexpr int kP2PSub = 8;
+constexpr int kP2PSub = PFMM_P2P_SUB;  // sources per FP32 partial sum (then Kahan)
+constexpr int kP2PUnroll = PFMM_P2P_UNROLL;
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -84,9 +94,23 @@ struct KahanF {
 //   Stokes : u = -(ln2/8pi) [ sum log2(r^2) f - (2/ln2) sum (r.f/r^2) r ]
 //   modhelm: pot = (1/2pi) sum q K0;  grad = -(beta/2pi) sum q K1 (t-s)/r
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+#if defined(PFMM_P2P_SCALAR)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
+#elif defined(PFMM_P2P_FMA_ONLY)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __ffma2_rn(a, make_float2(1.f, 1.f), b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __ffma2_rn(a, b, make_float2(0.f, 0.f)); }
+#else
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+#endif
+#if defined(PFMM_P2P_SCALAR)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+}
+#else
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+#endif
 
 struct Kahan2 {
   float2 s, c;
@@ -157,7 +181,7 @@ __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0,
     }
     __syncthreads();
     for (int js = 0; js < nb; js += kP2PSub) {
-#pragma unroll 2
+#pragma unroll kP2PUnroll
       for (int jj = js; jj < js + kP2PSub; ++jj) {
         const float4 p = s_p[jj];
         const float2 nsxh = f2(-p.x), nsxl = f2(-p.y), nsyh = f2(-p.z), nsyl = f2(-p.w);
@@ -259,7 +283,7 @@ __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0,
 }
 
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed(const __grid_constant__ P2PArgs a) {
+__global__ void __launch_bounds__(kP2PThreads, PFMM_P2P_MINB) k_p2p_mixed(const __grid_constant__ P2PArgs a) {
   const int j0 = blockIdx.y * a.chunk;
   p2p_mixed_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
 }
