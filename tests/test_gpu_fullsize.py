@@ -1,0 +1,123 @@
+"""Full-size parity: each workload at its full size and in the configuration
+the benchmark times, compared on sampled targets with the oracle evaluated
+one target at a time (direct near-image sum + the plain L D R method with the
+oracle's own quadrature, eps 1e-11).  Potentials/velocities are compared
+modulo a constant (the sample mean), gradients directly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import api as oapi
+from oracle import ewald, lattice, method
+
+pytestmark = pytest.mark.gpu
+NSAMP = 160
+
+
+def _oracle_at(kernel, beta, e1, e2, src, q, trg_sample, eps=1e-11):
+    cell, s, t = lattice.to_canonical(e1, e2, src, trg_sample)
+    rot = cell["rot"]
+    qq = np.einsum("ij,rjn->rin", rot, q) if kernel == "stokes" else q
+    g = kernel != "stokes"
+    p0, g0 = ewald.near_sum(kernel, beta, cell, t, s, qq, want_grad=g)
+    p1, g1 = method.far_field(kernel, beta, cell, t, s, qq, eps=eps, want_grad=g)
+    pot, grad = p0 + p1, (g0 + g1 if g else None)
+    if kernel == "stokes":
+        return np.einsum("ij,rjn->rin", rot.T, pot), None
+    return pot, np.einsum("ij,rjn->rin", rot.T, grad)
+
+
+def _cmp(got, ref, mc):
+    return oapi.rel_err(got, ref, modconst=mc)
+
+
+def _run(w, precision, tol, path, idx=None):
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp
+    dev = torch.device("cuda", 0)
+    S = torch.tensor(w["src"], device=dev)
+    Q = torch.tensor(w["q"], device=dev)
+    self_t = w["trg"] is w["src"]
+    T = None if self_t else torch.tensor(w["trg"], device=dev)
+    ns = S.shape[1]
+    nt = ns if self_t else T.shape[1]
+    op = PeriodicOp(w["kernel"], w["e1"], w["e2"], tol=tol, precision=precision, path=path,
+                    nufft_w=w.get("nufft_w", 0), n_gl=w.get("n_gl", 0), ns_max=ns, nt_max=nt)
+    pot, grad = op(S, Q, T, grad=w["kernel"] != "stokes")
+    torch.cuda.synchronize()
+    op.status()
+    return pot.cpu().numpy(), (None if grad is None else grad.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision,tol,path", [("mixed", 1e-6, "nufft"), ("fp64", 1e-10, "direct")])
+def test_laplace_aspect16_gmm_full(precision, tol, path):
+    """1e5 Gaussian-mixture sources in the 16 x 1 cell: the mixed path through the
+    NUFFT (w = 8, 8 lines, the timed configuration) and the plain FP64 path."""
+    w = workloads.make("laplace_aspect16_gmm_n1e5")
+    if precision == "fp64":
+        w = dict(w, nufft_w=0, n_gl=0)
+    pot, grad = _run(w, precision, tol, path)
+    idx = np.random.default_rng(0).choice(w["src"].shape[1], NSAMP, replace=False)
+    ref_p, ref_g = _oracle_at("laplace", 0.0, w["e1"], w["e2"], w["src"], w["q"], w["src"][:, idx])
+    assert _cmp(pot[:, idx], ref_p, True) < tol
+    assert _cmp(grad[:, :, idx], ref_g, False) < tol
+
+
+def test_stokes_skew_full():
+    """2e5 Stokeslets, 2e5 separate targets, skew cell, mixed precision."""
+    w = workloads.make("stokes_skew_n2e5")
+    vel, _ = _run(w, "mixed", 1e-6, "direct")
+    idx = np.random.default_rng(1).choice(w["trg"].shape[1], NSAMP, replace=False)
+    ref, _ = _oracle_at("stokes", 0.0, w["e1"], w["e2"], w["src"], w["q"], w["trg"][:, idx])
+    assert _cmp(vel[:, :, idx], ref, True) < 1e-6
+
+
+def test_laplace_adjoint_full():
+    """5e4 charges in the 4 x 1 cell: dE/dq = phi, dE/dx = q grad phi at sampled points."""
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp, periodic
+    w = workloads.make("laplace_adjoint_4x1_n5e4")
+    dev = torch.device("cuda", 0)
+    n = w["src"].shape[1]
+    S = torch.tensor(w["src"], device=dev, requires_grad=True)
+    Q = torch.tensor(w["q"], device=dev, requires_grad=True)
+    op = PeriodicOp("laplace", w["e1"], w["e2"], tol=1e-6, precision="mixed", ns_max=n, nt_max=n)
+    pot, _ = periodic(op, S, Q)
+    (0.5 * (Q * pot).sum()).backward()
+    idx = np.random.default_rng(2).choice(n, NSAMP, replace=False)
+    ref_p, ref_g = _oracle_at("laplace", 0.0, w["e1"], w["e2"], w["src"], w["q"], w["src"][:, idx])
+    assert _cmp(Q.grad.detach().cpu().numpy()[:, idx], ref_p, True) < 1e-6
+    force = w["q"][0][idx][None, :] * ref_g[0]
+    assert _cmp(S.grad.detach().cpu().numpy()[:, idx], force, False) < 1e-6
+
+
+def test_batch_modhelm_full_beta1():
+    """256 cells, N log-uniform in [500, 5e4], aspect in [1, 64], 8 rhs, beta = 1,
+    one graph replay; sampled cells and targets against the oracle."""
+    import torch
+    from paper_2111_01083_gb300 import BatchOp
+    cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8)
+    counts = [c["src"].shape[1] for c in cells]
+    dev = torch.device("cuda", 0)
+    S = torch.tensor(np.concatenate([c["src"] for c in cells], axis=1), device=dev)
+    Q = torch.tensor(np.concatenate([c["q"] for c in cells], axis=1), device=dev)
+    op = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=1.0) for c in cells], counts, precision="mixed",
+                 nrhs=8, tol=1e-6)
+    graph, out = op.capture(S, Q, grad=False)
+    graph.replay()
+    torch.cuda.synchronize()
+    op.status(dev)
+    pot = out[0].cpu().numpy()
+    edges = np.concatenate([[0], np.cumsum(counts)])
+    rng = np.random.default_rng(4)
+    big = int(np.argmax(counts))
+    for c in [big] + list(rng.choice(256, 3, replace=False)):
+        cell = cells[c]
+        n = counts[c]
+        idx = rng.choice(n, min(48, n), replace=False)
+        ref, _ = _oracle_at("modhelm", 1.0, cell["e1"], cell["e2"], cell["src"], cell["q"], cell["src"][:, idx])
+        got = pot[:, edges[c]:edges[c + 1]][:, idx]
+        assert _cmp(got, ref, False) < 1e-6, (c, n)
