@@ -69,7 +69,8 @@ typedef enum { PFMM_FP64 = 0, PFMM_MIXED = 1 } pfmm_precision;
 
 /* Far-field south/north application: DIRECT = L (D (R q)) (Sec. 6);
  * NUFFT = GL anterpolation + ES-kernel NUFFT (Sec. 6, Eqs. fastanterp and
- * fastinterp).  AUTO picks NUFFT when the number of modes is large. */
+ * fastinterp), for all three kernels.  AUTO picks NUFFT when M >= 64 and the
+ * fine grid (power of two >= 2 (2M + 1)) has at most 8192 points. */
 typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } pfmm_path;
 
 /* flags */

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include "pfmm_impl.h"
 #include "devmath.cuh"
+#include "lattice_weights.cuh"
 
 namespace pfmm {
 
@@ -285,24 +286,6 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
 // mom[r*8+4] = c0: Laplace: -(1/(d eta)) sum q y' (m = 0 of south + north, Eq. phis3),
 //        Stokes: -(1/(d eta)) sum f_x y' (Eq. pss0); added as c0 * y.
 // ----------------------------------------------------------------------------
-struct dcx {
-  double r, i;
-};
-__device__ __forceinline__ dcx cmul(dcx a, dcx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-__device__ __forceinline__ dcx cadd(dcx a, dcx b) { return {a.r + b.r, a.i + b.i}; }
-__device__ __forceinline__ dcx csub(dcx a, dcx b) { return {a.r - b.r, a.i - b.i}; }
-__device__ __forceinline__ dcx cscale(dcx a, double s) { return {a.r * s, a.i * s}; }
-__device__ __forceinline__ dcx cexp_(dcx z) {
-  double e = exp(z.r), s, c;
-  sincos(z.i, &s, &c);
-  return {e * c, e * s};
-}
-__device__ __forceinline__ dcx cdiv(dcx a, dcx b) {
-  double den = b.r * b.r + b.i * b.i;
-  return {(a.r * b.r + a.i * b.i) / den, (a.i * b.r - a.r * b.i) / den};
-}
-__device__ __forceinline__ dcx conj_(dcx a) { return {a.r, -a.i}; }
-
 template <typename T2>
 __device__ __forceinline__ void store_w(T2* p, dcx v) {
   p->x = v.r;
@@ -338,88 +321,25 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
     dcx D;
     double fac = 1.0;
     if (tm.part < 2) {
-      // Theorem south_thm / south_thm_lap: D = e^{-2Q} / (2 d chi (1 - e^{-Q})), Q = chi eta - i alpha xi
-      dcx Q{tm.b * eta, -tm.a * xi};
-      dcx e1 = cexp_({-Q.r, -Q.i});
-      dcx e2 = cmul(e1, e1);
-      D = cdiv(e2, cscale({1.0 - e1.r, -e1.i}, 2.0 * d * tm.b));
-      if (north) D = conj_(D);
+      D = lw::sn_scalar(d, xi, eta, tm.a, tm.b, north);
       fac = (tm.m == 0) ? 1.0 : 2.0;  // +-m pairs
     } else {
-      // Theorem west_thm (general m0): D = (w / (2 pi kappa)) e^{-(m0+1) kappa d}/(1 - e^{-kappa d}) B,
-      // B = e^{kappa xi - i lambda eta} + 1 + e^{-kappa xi + i lambda eta}
-      double lam = tm.a, kap = tm.b;
-      double F = exp(-(g.m0 + 1) * kap * d) / (-expm1(-kap * d));
-      dcx B = cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta}));
-      D = cscale(B, tm.w / (2.0 * M_PI * kap) * F);
-      if (east) D = conj_(D);
+      D = lw::we_scalar(d, xi, eta, g.m0, tm.a, tm.b, tm.w, east);
     }
-    dcx W = cscale(cmul(D, C(0)), fac);
-    store_w(wts + (size_t)r * f.nterm + t, W);
+    store_w(wts + (size_t)r * f.nterm + t, cscale(cmul(D, C(0)), fac));
     return;
   }
-  // Stokes
   dcx Da[2][2], Db[2][2];
-  if (tm.part < 2) {
-    // Theorem south_thm_s (Eq. pssm): z = e^{-Q}, Q = |alpha| eta - i alpha xi (north: conj),
-    // Db = z^2/(4d(1-z)) S, Da = z^2/(4d(1-z)) [ I/|alpha| - eta (2 - z)/(1 - z) S ],
-    // S = [[1, i], [i, -1]] for m > 0 (north: conj).
-    double al = tm.a, aa = fabs(al);
-    dcx Q{aa * eta, -al * xi};
-    if (north) Q = conj_(Q);
-    dcx z = cexp_({-Q.r, -Q.i});
-    dcx omz{1.0 - z.r, -z.i};
-    dcx pre = cdiv(cmul(z, z), cscale(omz, 4.0 * d));
-    dcx S[2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {-1, 0}}};
-    if (north) {
-      S[0][1] = conj_(S[0][1]);
-      S[1][0] = conj_(S[1][0]);
-    }
-    dcx q2 = cscale(cdiv({2.0 - z.r, -z.i}, omz), eta);
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) {
-        Db[i][j] = cmul(pre, S[i][j]);
-        dcx id = (i == j) ? dcx{1.0 / aa, 0.0} : dcx{0.0, 0.0};
-        Da[i][j] = cmul(pre, csub(id, cmul(q2, S[i][j])));
-      }
-  } else {
-    // Eq. pssw0 with P = m0 + 1 (half-line, 2 Re): pref = (w / 4pi) z^P / (1 - z), z = e^{-lambda d},
-    // Db = pref B S', Da = pref [ B (I/lambda - (P d + d z/(1 - z)) S') + xi (phi_1 - phi_-1) S' ],
-    // S' = [[-1, i], [i, 1]], phi_r = e^{r (lambda xi - i lambda eta)}.  East: conj.
-    double lam = tm.a;
-    double z = exp(-lam * d);
-    double omz = -expm1(-lam * d);
-    int P = g.m0 + 1;
-    double pref = tm.w / (4.0 * M_PI) * exp(-P * lam * d) / omz;
-    dcx ph1 = cexp_({lam * xi, -lam * eta}), phm = cexp_({-lam * xi, lam * eta});
-    dcx B = cadd(cadd(ph1, phm), {1.0, 0.0});
-    dcx Sp[2][2] = {{{-1, 0}, {0, 1}}, {{0, 1}, {1, 0}}};
-    double kx = P * d + d * z / omz;
-    dcx dph = cscale(csub(ph1, phm), xi);
-    for (int i = 0; i < 2; ++i)
-      for (int j = 0; j < 2; ++j) {
-        Db[i][j] = cscale(cmul(B, Sp[i][j]), pref);
-        dcx id = (i == j) ? dcx{1.0 / lam, 0.0} : dcx{0.0, 0.0};
-        dcx t1 = cmul(B, csub(id, cscale(Sp[i][j], kx)));
-        Da[i][j] = cscale(cadd(t1, cmul(dph, Sp[i][j])), pref);
-        if (east) {
-          Db[i][j] = conj_(Db[i][j]);
-          Da[i][j] = conj_(Da[i][j]);
-        }
-      }
-  }
-  // sign of the coordinate terms: S/W: Wa = Da ca + Db cb, Wb = -Db ca; N/E: Wa = Da ca - Db cb, Wb = +Db ca
-  double sg = (north || east) ? -1.0 : 1.0;
-  double fac = (tm.part < 2) ? 2.0 : 1.0;
-  dcx ca[2] = {C(0), C(1)}, cb[2] = {C(2), C(3)};
+  if (tm.part < 2)
+    lw::sn_stokes(d, xi, eta, tm.a, north, Da, Db);
+  else
+    lw::we_stokes(d, xi, eta, g.m0, tm.a, tm.w, east, Da, Db);
+  const dcx ca[2] = {C(0), C(1)}, cb[2] = {C(2), C(3)};
+  dcx wa[2], wb[2];
+  lw::stokes_apply(Da, Db, ca, cb, north || east, (tm.part < 2) ? 2.0 : 1.0, wa, wb);
   for (int i = 0; i < 2; ++i) {
-    dcx wa = {0, 0}, wb = {0, 0};
-    for (int j = 0; j < 2; ++j) {
-      wa = cadd(wa, cadd(cmul(Da[i][j], ca[j]), cscale(cmul(Db[i][j], cb[j]), sg)));
-      wb = cadd(wb, cscale(cmul(Db[i][j], ca[j]), -sg));
-    }
-    store_w(wts + (((size_t)r * 4 + i) * f.nterm + t), cscale(wa, fac));
-    store_w(wts + (((size_t)r * 4 + 2 + i) * f.nterm + t), cscale(wb, fac));
+    store_w(wts + (((size_t)r * 4 + i) * f.nterm + t), wa[i]);
+    store_w(wts + (((size_t)r * 4 + 2 + i) * f.nterm + t), wb[i]);
   }
 }
 

@@ -1,0 +1,130 @@
+// Lattice weights D of the low-rank factorizations of the far part of the
+// periodizing operator (FP64).  Shared by the direct far-field kernels and the
+// NUFFT south/north path so that both apply one set of formulas.
+//
+//   scalar south/north   Theorem south_thm (modified Helmholtz, chi = sqrt(alpha^2 + beta^2))
+//                        and Theorem south_thm_lap (Laplace, chi = |alpha|)
+//   scalar west/east     Theorem west_thm / west_thm_lap, general m0
+//   Stokes south/north   Theorem south_thm_s (Eq. pssm)
+//   Stokes west/east     Theorem west_thm_s (Eq. pssw0), general m0
+//
+// North is the complex conjugate of south (coordinate terms change sign for
+// Stokes), east the conjugate of west.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pfmm {
+
+struct dcx {
+  double r, i;
+};
+__device__ __forceinline__ dcx cmul(dcx a, dcx b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ dcx cadd(dcx a, dcx b) { return {a.r + b.r, a.i + b.i}; }
+__device__ __forceinline__ dcx csub(dcx a, dcx b) { return {a.r - b.r, a.i - b.i}; }
+__device__ __forceinline__ dcx cscale(dcx a, double s) { return {a.r * s, a.i * s}; }
+__device__ __forceinline__ dcx cexp_(dcx z) {
+  double e = exp(z.r), s, c;
+  sincos(z.i, &s, &c);
+  return {e * c, e * s};
+}
+__device__ __forceinline__ dcx cdiv(dcx a, dcx b) {
+  double den = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / den, (a.i * b.r - a.r * b.i) / den};
+}
+__device__ __forceinline__ dcx conj_(dcx a) { return {a.r, -a.i}; }
+
+namespace lw {
+
+// Scalar south (north: conj): D = e^{-2Q} / (2 d chi (1 - e^{-Q})), Q = chi eta - i alpha xi.
+__device__ __forceinline__ dcx sn_scalar(double d, double xi, double eta, double alpha, double chi, bool north) {
+  dcx Q{chi * eta, -alpha * xi};
+  dcx e1 = cexp_({-Q.r, -Q.i});
+  dcx e2 = cmul(e1, e1);
+  dcx D = cdiv(e2, cscale({1.0 - e1.r, -e1.i}, 2.0 * d * chi));
+  return north ? conj_(D) : D;
+}
+
+// Scalar west (east: conj), quadrature node (lambda, kappa) with weight w:
+//   D = (w / (2 pi kappa)) e^{-(m0+1) kappa d} / (1 - e^{-kappa d}) B,
+//   B = e^{kappa xi - i lambda eta} + 1 + e^{-kappa xi + i lambda eta}.
+__device__ __forceinline__ dcx we_scalar(double d, double xi, double eta, int m0, double lam, double kap, double w,
+                                         bool east) {
+  double F = exp(-(m0 + 1) * kap * d) / (-expm1(-kap * d));
+  dcx B = cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta}));
+  dcx D = cscale(B, w / (2.0 * M_PI * kap) * F);
+  return east ? conj_(D) : D;
+}
+
+// Stokes south (m != 0): z = e^{-Q}, Q = |alpha| eta - i alpha xi,
+//   Db = z^2/(4d(1-z)) S,  Da = z^2/(4d(1-z)) [ I/|alpha| - eta (2 - z)/(1 - z) S ],
+//   S = [[1, i], [i, -1]].  North: Q and S conjugated.
+__device__ __forceinline__ void sn_stokes(double d, double xi, double eta, double alpha, bool north, dcx Da[2][2],
+                                          dcx Db[2][2]) {
+  double aa = fabs(alpha);
+  dcx Q{aa * eta, -alpha * xi};
+  if (north) Q = conj_(Q);
+  dcx z = cexp_({-Q.r, -Q.i});
+  dcx omz{1.0 - z.r, -z.i};
+  dcx pre = cdiv(cmul(z, z), cscale(omz, 4.0 * d));
+  dcx S[2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {-1, 0}}};
+  if (north) {
+    S[0][1] = conj_(S[0][1]);
+    S[1][0] = conj_(S[1][0]);
+  }
+  dcx q2 = cscale(cdiv({2.0 - z.r, -z.i}, omz), eta);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      Db[i][j] = cmul(pre, S[i][j]);
+      dcx id = (i == j) ? dcx{1.0 / aa, 0.0} : dcx{0.0, 0.0};
+      Da[i][j] = cmul(pre, csub(id, cmul(q2, S[i][j])));
+    }
+}
+
+// Stokes west (east: conj), node (lambda, w), P = m0 + 1, z = e^{-lambda d}:
+//   pref = (w / 4 pi) z^P / (1 - z),  phi_r = e^{r (lambda xi - i lambda eta)},  B = phi_1 + 1 + phi_-1,
+//   Db = pref B S',  Da = pref [ B (I/lambda - (P d + d z/(1 - z)) S') + xi (phi_1 - phi_-1) S' ],
+//   S' = [[-1, i], [i, 1]].
+__device__ __forceinline__ void we_stokes(double d, double xi, double eta, int m0, double lam, double w, bool east,
+                                          dcx Da[2][2], dcx Db[2][2]) {
+  double z = exp(-lam * d);
+  double omz = -expm1(-lam * d);
+  int P = m0 + 1;
+  double pref = w / (4.0 * M_PI) * exp(-P * lam * d) / omz;
+  dcx ph1 = cexp_({lam * xi, -lam * eta}), phm = cexp_({-lam * xi, lam * eta});
+  dcx B = cadd(cadd(ph1, phm), {1.0, 0.0});
+  dcx Sp[2][2] = {{{-1, 0}, {0, 1}}, {{0, 1}, {1, 0}}};
+  double kx = P * d + d * z / omz;
+  dcx dph = cscale(csub(ph1, phm), xi);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      Db[i][j] = cscale(cmul(B, Sp[i][j]), pref);
+      dcx id = (i == j) ? dcx{1.0 / lam, 0.0} : dcx{0.0, 0.0};
+      dcx t1 = cmul(B, csub(id, cscale(Sp[i][j], kx)));
+      Da[i][j] = cscale(cadd(t1, cmul(dph, Sp[i][j])), pref);
+      if (east) {
+        Db[i][j] = conj_(Db[i][j]);
+        Da[i][j] = conj_(Da[i][j]);
+      }
+    }
+}
+
+// Stokes weights from the coefficients c_a = R f, c_b = R coord f:
+//   south/west:  Wa = fac (Da c_a + Db c_b),  Wb = -fac Db c_a
+//   north/east:  Wa = fac (Da c_a - Db c_b),  Wb = +fac Db c_a
+// (the coordinate terms of the kernel change sign with the direction).
+__device__ __forceinline__ void stokes_apply(const dcx Da[2][2], const dcx Db[2][2], const dcx ca[2], const dcx cb[2],
+                                             bool flip, double fac, dcx wa[2], dcx wb[2]) {
+  const double sg = flip ? -1.0 : 1.0;
+  for (int i = 0; i < 2; ++i) {
+    dcx a = {0, 0}, b = {0, 0};
+    for (int j = 0; j < 2; ++j) {
+      a = cadd(a, cadd(cmul(Da[i][j], ca[j]), cscale(cmul(Db[i][j], cb[j]), sg)));
+      b = cadd(b, cscale(cmul(Db[i][j], ca[j]), -sg));
+    }
+    wa[i] = cscale(a, fac);
+    wb[i] = cscale(b, fac);
+  }
+}
+
+}  // namespace lw
+}  // namespace pfmm

@@ -1,15 +1,22 @@
 // NUFFT far-field path for the south/north parts (Sec. 6, Eqs. fastanterp,
-// fastinterp; Fig. nufftgrids), Laplace kernel.
+// fastinterp; Fig. nufftgrids) of the Laplace, modified Helmholtz and Stokes
+// kernels.
 //
 // Formation (Eq. fastanterp):  c^S_m = sum_n e^{ chi_m ybar_n} F_n(m),
 //                              c^N_m = sum_n e^{-chi_m ybar_n} F_n(m),
 //   F_n(m) = sum_j gamma(y'_j, n) q_j e^{-i alpha_m x'_j}   (type-1 NUFFT per GL line n)
 // with gamma the barycentric Gauss-Legendre interpolation weights on
-// ybar_n in [-eta/2, eta/2] (Sec. 2.4, Eq. baryweights).
+// ybar_n in [-eta/2, eta/2] (Sec. 2.4, Eq. baryweights), chi_m = |alpha_m|
+// (Laplace, Stokes) or sqrt(alpha_m^2 + beta^2) (modified Helmholtz, m = 0
+// included).  Stokes spreads four charge channels per right-hand side,
+// f_x, f_y, y' f_x, y' f_y: the first two give c_a, the last two c_b of
+// Theorem south_thm_s.
 // Evaluation (Eq. fastinterp):  u(t) = sum_n gamma(y, n) G_n(x),
-//   G_n(x) = Re sum_{m>=1} e^{i alpha_m x} v_n(m),
+//   G_n(x) = Re sum_m e^{i alpha_m x} v_n(m),
 //   v_n(m) = w^S_m e^{-chi_m ybar_n} + w^N_m e^{chi_m ybar_n}  (type-2 NUFFT per line)
 // and the y-derivative through v^y_n(m) = -chi_m w^S_m e^{-chi ybar} + chi_m w^N_m e^{chi ybar}.
+// Stokes: u_k(t) = sum_n gamma(y, n) (Ga_{k,n}(x) + y Gb_{k,n}(x)), with the
+// lines of the weights Wa and Wb of Theorem south_thm_s.
 //
 // Type-1/type-2 transforms: exponential-of-semicircle kernel
 // phi(z) = exp(b (sqrt(1 - z^2) - 1)) of width w grid points, b = 2.30 w,
@@ -24,13 +31,15 @@
 #include <cmath>
 #include "pfmm_impl.h"
 #include "devmath.cuh"
+#include "lattice_weights.cuh"
 
 namespace pfmm {
 
 struct NufftArgs {
   int nf, logn, w, M, n_gl, nrhs, ns, nt;
-  int64_t os;  // output row stride
-  double es_beta, d, eta, xi;
+  int kernel, nch, npk, mlo;  // pfmm_kernel, charge channels per rhs, spectrum lines per rhs, first mode
+  int64_t os;                 // output row stride
+  double es_beta, d, eta, xi, beta;
   const double* gl;      // [n_gl][2] (ybar_n, sigma_n)
   const double* phihat;  // [M+1] phihat(alpha k), k = 0..M
 };
@@ -73,8 +82,9 @@ __device__ __forceinline__ void bary(T y, const double* gl, int n_gl, T* g) {
 
 // ---------------------------------------------------------------------------
 // K4: anterpolation + spreading.  One block per source chunk; the block
-// spreads into a shared-memory grid [n_gl][nf] for one rhs at a time and adds
-// it to the global FP64 grid [nrhs][n_gl][nf].
+// spreads into a shared-memory grid [n_gl][nf] for one charge vector at a
+// time (rhs r, channel c) and adds it to the global FP64 grid
+// [nrhs][nch][n_gl][nf].  Channels: scalar q; Stokes f_x, f_y, y' f_x, y' f_y.
 // ---------------------------------------------------------------------------
 constexpr int kSpreadThreads = 256;
 
@@ -89,19 +99,24 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
   const T twopi_over_d = (T)(2.0 * M_PI / a.d);
   const T inv_h = (T)(a.nf / (2.0 * M_PI));
   const T beta = (T)a.es_beta;
-  for (int r = 0; r < a.nrhs; ++r) {
+  const int ncomp = a.nch == 4 ? 2 : 1;
+  for (int v = 0; v < a.nrhs * a.nch; ++v) {
+    const int r = v / a.nch, c = v % a.nch;
+    const T* qrow = qv + ((size_t)r * ncomp + (c & 1)) * a.ns;
+    const bool ymul = c >= 2;
     if (use_smem)
       for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) sg[k] = T(0);
     __syncthreads();
     for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
-      const T x = sx[j], y = sy[j], q = qv[(size_t)r * a.ns + j];
+      const T x = sx[j], y = sy[j];
+      const T q = ymul ? qrow[j] * y : qrow[j];
       T th = x * twopi_over_d;  // in [-pi (1 + |xi|/d), ...]; reduced below
       T u = th * inv_h;
       u -= (T)a.nf * floor(u / (T)a.nf);  // u in [0, nf)
       T ker[16], gam[32];
       const int l0 = es_weights(u, a.w, beta, ker);
       bary(y, a.gl, a.n_gl, gam);
-      double* gr = grid + (size_t)r * ngrid;
+      double* gr = grid + (size_t)v * ngrid;
       for (int n = 0; n < a.n_gl; ++n) {
         const T gq = gam[n] * q;
         for (int k = 0; k < a.w; ++k) {
@@ -115,10 +130,10 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
     }
     __syncthreads();
     if (use_smem) {
-      double* g = grid + (size_t)r * ngrid;
+      double* g = grid + (size_t)v * ngrid;
       for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) {
-        const T v = sg[k];
-        if (v != T(0)) atomicAdd(g + k, (double)v);
+        const T val = sg[k];
+        if (val != T(0)) atomicAdd(g + k, (double)val);
       }
       __syncthreads();
     }
@@ -150,17 +165,17 @@ __device__ void fft_smem(T2* s, int n, int logn, int sign) {
 
 __device__ __forceinline__ int bitrev(int i, int logn) { return __brev(i) >> (32 - logn); }
 
-// Forward transforms of the spread grids, two lines per FFT, then
-// deconvolution: F_n(k) for k = 0..M written to Fk [nrhs][n_gl][M+1] (double2).
+// Forward transforms of the spread grids, two real lines per FFT, then
+// deconvolution: F(k) for k = 0..M of every line (charge vector, GL line)
+// written to Fk [nrhs][nch][n_gl][M+1] (double2).
 template <typename T, typename T2>
 __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double2* __restrict__ Fk) {
   extern __shared__ unsigned char smem_raw[];
   T2* s = reinterpret_cast<T2*>(smem_raw);
-  const int npair = (a.n_gl + 1) / 2;
-  const int r = blockIdx.x / npair, p = blockIdx.x % npair;
-  const int n0 = 2 * p, n1 = 2 * p + 1;
-  const double* g0 = grid + ((size_t)r * a.n_gl + n0) * a.nf;
-  const double* g1 = (n1 < a.n_gl) ? grid + ((size_t)r * a.n_gl + n1) * a.nf : nullptr;
+  const int nline = a.nrhs * a.nch * a.n_gl;
+  const int n0 = 2 * blockIdx.x, n1 = 2 * blockIdx.x + 1;
+  const double* g0 = grid + (size_t)n0 * a.nf;
+  const double* g1 = (n1 < nline) ? grid + (size_t)n1 * a.nf : nullptr;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) {
     const int j = bitrev(i, a.logn);
     s[j] = {(T)g0[i], g1 ? (T)g1[i] : T(0)};
@@ -174,69 +189,100 @@ __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double
     const double xr = 0.5 * ((double)zk.x + zm.x), xi = 0.5 * ((double)zk.y - zm.y);
     const double yr = 0.5 * ((double)zk.y + zm.y), yi = -0.5 * ((double)zk.x - zm.x);
     const double dec = scale / a.phihat[k];
-    Fk[((size_t)r * a.n_gl + n0) * (a.M + 1) + k] = make_double2(xr * dec, xi * dec);
-    if (n1 < a.n_gl) Fk[((size_t)r * a.n_gl + n1) * (a.M + 1) + k] = make_double2(yr * dec, yi * dec);
+    Fk[(size_t)n0 * (a.M + 1) + k] = make_double2(xr * dec, xi * dec);
+    if (n1 < nline) Fk[(size_t)n1 * (a.M + 1) + k] = make_double2(yr * dec, yi * dec);
   }
 }
 
 // Mode combination, lattice weights and evaluation-line spectra (FP64).
-// One thread per (rhs, mode m = 1..M).  Writes the type-2 input spectra:
-//   Zp_n = pot_n + i gy_n   (pack 0, one per line)
-//   Zx_p = gx_{2p} + i gx_{2p+1}  (pack 1, one per line pair)
-// layout spec [nrhs][npack_lines][nf] (T2), zero elsewhere (cleared before).
-template <typename T2>
+// One thread per (rhs, mode m = mlo..M).  Writes the type-2 input spectra,
+// layout spec [nrhs][npk][nf] (T2), zero elsewhere (cleared before):
+//   scalar: line n: pot_n + i gy_n;  line n_gl + p: gx_{2p} + i gx_{2p+1}
+//   Stokes: line n: Ga_{x,n} + i Ga_{y,n};  line n_gl + n: Gb_{x,n} + i Gb_{y,n}
+// A real output line Re sum_m e^{i m theta} a_m packed with a second one
+// (b_m) into a complex line has H_m = (a_m + i b_m)/2, H_-m = (conj a_m + i conj b_m)/2
+// for m >= 1, and H_0 = a_0 + i b_0 (a_0, b_0 real).
+template <typename T2, int KER>
 __global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, T2* __restrict__ spec, int want_grad) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  using TT = decltype(T2::x);
+  const int m = blockIdx.x * blockDim.x + threadIdx.x + a.mlo;
   const int r = blockIdx.y;
   if (m > a.M) return;
-  const double al = 2.0 * M_PI * m / a.d, chi = fabs(al);
-  // D^S = e^{-2Q}/(2 d chi (1 - e^{-Q})), Q = chi eta - i alpha xi (Theorem south_thm_lap); D^N = conj
-  const double er = exp(-chi * a.eta);
-  double sq, cq;
-  sincos(al * a.xi, &sq, &cq);
-  const double e1r = er * cq, e1i = er * sq;  // e^{-Q}
-  const double e2r = e1r * e1r - e1i * e1i, e2i = 2 * e1r * e1i;
-  const double dr = 1.0 - e1r, di = -e1i, den = 2.0 * a.d * chi * (dr * dr + di * di);
-  const double DSr = (e2r * dr + e2i * di) / den, DSi = (e2i * dr - e2r * di) / den;
-  double cSr = 0, cSi = 0, cNr = 0, cNi = 0;
+  const double al = 2.0 * M_PI * m / a.d;
+  const double chi = (KER == PFMM_MODHELM) ? sqrt(al * al + a.beta * a.beta) : fabs(al);
+  const double pre = (2.0 / a.w) / a.phihat[m];
+  T2* base = spec + (size_t)r * a.npk * a.nf;
+  auto put = [&](int line, dcx va, dcx vb) {
+    T2* row = base + (size_t)line * a.nf;
+    if (m == 0) {
+      row[0] = {(TT)(pre * (va.r - vb.i)), (TT)(pre * (va.i + vb.r))};
+      return;
+    }
+    row[m] = {(TT)(0.5 * pre * (va.r - vb.i)), (TT)(0.5 * pre * (va.i + vb.r))};
+    row[a.nf - m] = {(TT)(0.5 * pre * (va.r + vb.i)), (TT)(0.5 * pre * (-va.i + vb.r))};
+  };
+  auto F = [&](int c, int n) {
+    const double2 v = Fk[(((size_t)r * a.nch + c) * a.n_gl + n) * (a.M + 1) + m];
+    return dcx{v.x, v.y};
+  };
+  if (KER != PFMM_STOKES) {
+    // Theorem south_thm_lap / south_thm: D^S, D^N = conj(D^S); w = fac D c (fac 2: the +-m pair)
+    const dcx DS = lw::sn_scalar(a.d, a.xi, a.eta, al, chi, false);
+    dcx cS{0, 0}, cN{0, 0};
+    for (int n = 0; n < a.n_gl; ++n) {
+      const double yb = a.gl[2 * n];
+      const dcx Fn = F(0, n);
+      cS = cadd(cS, cscale(Fn, exp(chi * yb)));
+      cN = cadd(cN, cscale(Fn, exp(-chi * yb)));
+    }
+    const double fac = (m == 0) ? 1.0 : 2.0;
+    const dcx wS = cscale(cmul(DS, cS), fac), wN = cscale(cmul(conj_(DS), cN), fac);
+    dcx vx_prev{0, 0};
+    for (int n = 0; n < a.n_gl; ++n) {
+      const double yb = a.gl[2 * n];
+      const double es = exp(-chi * yb), en = exp(chi * yb);
+      const dcx v = cadd(cscale(wS, es), cscale(wN, en));
+      const dcx vy = want_grad ? cscale(csub(cscale(wN, en), cscale(wS, es)), chi) : dcx{0, 0};
+      put(n, v, vy);
+      if (want_grad) {
+        const dcx vx{-al * v.i, al * v.r};  // d/dx: multiply by i alpha
+        if (n & 1)
+          put(a.n_gl + n / 2, vx_prev, vx);
+        else if (n == a.n_gl - 1)
+          put(a.n_gl + n / 2, vx, {0, 0});
+        vx_prev = vx;
+      }
+    }
+    return;
+  }
+  // Stokes (Theorem south_thm_s): c_a = R f, c_b = R y' f for south (e^{+chi ybar}) and north (e^{-chi ybar})
+  dcx caS[2] = {{0, 0}, {0, 0}}, cbS[2] = {{0, 0}, {0, 0}}, caN[2] = {{0, 0}, {0, 0}}, cbN[2] = {{0, 0}, {0, 0}};
   for (int n = 0; n < a.n_gl; ++n) {
     const double yb = a.gl[2 * n];
-    const double2 F = Fk[((size_t)r * a.n_gl + n) * (a.M + 1) + m];
     const double ep = exp(chi * yb), em = exp(-chi * yb);
-    cSr += ep * F.x;
-    cSi += ep * F.y;
-    cNr += em * F.x;
-    cNi += em * F.y;
+    for (int k = 0; k < 2; ++k) {
+      const dcx fa = F(k, n), fb = F(2 + k, n);
+      caS[k] = cadd(caS[k], cscale(fa, ep));
+      cbS[k] = cadd(cbS[k], cscale(fb, ep));
+      caN[k] = cadd(caN[k], cscale(fa, em));
+      cbN[k] = cadd(cbN[k], cscale(fb, em));
+    }
   }
-  // w = 2 D c (factor 2: the +-m pair, real part taken at the end)
-  const double wSr = 2 * (DSr * cSr - DSi * cSi), wSi = 2 * (DSr * cSi + DSi * cSr);
-  const double wNr = 2 * (DSr * cNr + DSi * cNi), wNi = 2 * (DSr * cNi - DSi * cNr);  // conj(D^S) c^N
-  const double pre = (2.0 / a.w) / a.phihat[m];
-  const int npk = a.n_gl + (a.n_gl + 1) / 2;
-  T2* base = spec + (size_t)r * npk * a.nf;
-  // one-sided spectrum a_m -> two real outputs: H_m = a + i b, H_-m = conj(a) + i conj(b), a = v/2
-  auto put = [&](int line, double ar, double ai, double br, double bi) {
-    T2* row = base + (size_t)line * a.nf;
-    row[m] = {(decltype(row->x))(0.5 * pre * (ar - bi)), (decltype(row->x))(0.5 * pre * (ai + br))};
-    row[a.nf - m] = {(decltype(row->x))(0.5 * pre * (ar + bi)), (decltype(row->x))(0.5 * pre * (-ai + br))};
-  };
-  double vxr_prev = 0, vxi_prev = 0;
+  dcx Da[2][2], Db[2][2], waS[2], wbS[2], waN[2], wbN[2];
+  lw::sn_stokes(a.d, a.xi, a.eta, al, false, Da, Db);
+  lw::stokes_apply(Da, Db, caS, cbS, false, 2.0, waS, wbS);
+  lw::sn_stokes(a.d, a.xi, a.eta, al, true, Da, Db);
+  lw::stokes_apply(Da, Db, caN, cbN, true, 2.0, waN, wbN);
   for (int n = 0; n < a.n_gl; ++n) {
     const double yb = a.gl[2 * n];
     const double es = exp(-chi * yb), en = exp(chi * yb);
-    const double vr = wSr * es + wNr * en, vi = wSi * es + wNi * en;
-    const double vyr = chi * (-wSr * es + wNr * en), vyi = chi * (-wSi * es + wNi * en);
-    put(n, vr, vi, want_grad ? vyr : 0.0, want_grad ? vyi : 0.0);
-    // d/dx: multiply by i alpha
-    const double vxr = -al * vi, vxi = al * vr;
-    if (want_grad) {
-      if (n & 1)
-        put(a.n_gl + n / 2, vxr_prev, vxi_prev, vxr, vxi);
-      else if (n == a.n_gl - 1)
-        put(a.n_gl + n / 2, vxr, vxi, 0.0, 0.0);
+    dcx va[2], vb[2];
+    for (int k = 0; k < 2; ++k) {
+      va[k] = cadd(cscale(waS[k], es), cscale(waN[k], en));
+      vb[k] = cadd(cscale(wbS[k], es), cscale(wbN[k], en));
     }
-    vxr_prev = vxr;
-    vxi_prev = vxi;
+    put(n, va[0], va[1]);
+    put(a.n_gl + n, vb[0], vb[1]);
   }
 }
 
@@ -254,7 +300,7 @@ __global__ void k_nufft_inv(NufftArgs a, T2* __restrict__ spec) {
 
 // Interpolation at targets + barycentric combination over lines; adds the
 // south/north field to pot / grad (input frame).
-template <typename T, typename T2>
+template <typename T, typename T2, int KER>
 __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, const T* __restrict__ ty,
                                const T2* __restrict__ spec, double* __restrict__ pot, double* __restrict__ grad) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -265,10 +311,31 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
   T ker[16], gam[32];
   const int l0 = es_weights(u, a.w, (T)a.es_beta, ker);
   bary(y, a.gl, a.n_gl, gam);
-  const int npk = a.n_gl + (a.n_gl + 1) / 2;
   const double* R = g.rot;
   for (int r = 0; r < a.nrhs; ++r) {
-    const T2* base = spec + (size_t)r * npk * a.nf;
+    const T2* base = spec + (size_t)r * a.npk * a.nf;
+    if (KER == PFMM_STOKES) {
+      T ux = 0, uy = 0;
+      for (int n = 0; n < a.n_gl; ++n) {
+        const T2* ra = base + (size_t)n * a.nf;
+        const T2* rb = base + (size_t)(a.n_gl + n) * a.nf;
+        T sax = 0, say = 0, sbx = 0, sby = 0;
+        for (int k = 0; k < a.w; ++k) {
+          const int li = (l0 + k) & (a.nf - 1);
+          const T2 va = ra[li], vb = rb[li];
+          sax += ker[k] * va.x;
+          say += ker[k] * va.y;
+          sbx += ker[k] * vb.x;
+          sby += ker[k] * vb.y;
+        }
+        ux += gam[n] * (sax + y * sbx);
+        uy += gam[n] * (say + y * sby);
+      }
+      const double uxd = ux, uyd = uy;
+      pot[((size_t)r * 2) * a.os + l] += R[0] * uxd + R[2] * uyd;
+      pot[((size_t)r * 2 + 1) * a.os + l] += R[1] * uxd + R[3] * uyd;
+      continue;
+    }
     T p = 0, gx = 0, gy = 0;
     for (int n = 0; n < a.n_gl; ++n) {
       const T2* row = base + (size_t)n * a.nf;
@@ -303,6 +370,7 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
                              double* grad, cudaStream_t st) {
   const Layout& L = p->lay;
   const bool mixed = sizeof(T) == 4;
+  const int K = p->opts.kernel;
   NufftArgs a{};
   a.nf = p->nf;
   a.logn = 0;
@@ -313,26 +381,31 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   a.nrhs = p->opts.nrhs;
   a.ns = (int)ns;
   a.nt = (int)nt;
+  a.kernel = K;
+  a.nch = nufft_nch(K);
+  a.npk = nufft_npk(K, a.n_gl);
+  a.mlo = p->far.mode0 ? 0 : 1;
   a.os = p->o_stride;
   a.es_beta = p->es_beta;
   a.d = p->geom.d;
   a.eta = p->geom.eta;
   a.xi = p->geom.xi;
+  a.beta = p->far.beta;
   size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
   a.gl = (const double*)(ws + L.nodes + nb);
   a.phihat = (const double*)(ws + L.nodes + nb + p->n_gl * 2 * sizeof(double));
   // workspace partition of the NUFFT scratch
+  const int nline = a.nrhs * a.nch * a.n_gl;
   char* base = ws + L.nufft;
-  double* grid = (double*)base;                                   // [nrhs][n_gl][nf] double
-  size_t off = (size_t)a.nrhs * a.n_gl * a.nf * sizeof(double);
-  double2* Fk = (double2*)(base + off);                           // [nrhs][n_gl][M+1]
-  off += (size_t)a.nrhs * a.n_gl * (a.M + 1) * sizeof(double2);
+  double* grid = (double*)base;                                   // [nrhs][nch][n_gl][nf] double
+  size_t off = (size_t)nline * a.nf * sizeof(double);
+  double2* Fk = (double2*)(base + off);                           // [nrhs][nch][n_gl][M+1]
+  off += (size_t)nline * (a.M + 1) * sizeof(double2);
   off = (off + 255) & ~size_t(255);
   T2* spec = (T2*)(base + off);                                   // [nrhs][npk][nf]
-  const int npk = a.n_gl + (a.n_gl + 1) / 2;
-  cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)a.nrhs * a.n_gl * a.nf * sizeof(double), st);
+  cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)nline * a.nf * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * npk * a.nf * sizeof(T2), st);
+  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * a.npk * a.nf * sizeof(T2), st);
   if (e != cudaSuccess) return e;
   const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
   const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
@@ -355,12 +428,29 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
       e = cudaFuncSetAttribute(k_nufft_inv<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_fwd<T, T2><<<a.nrhs * ((a.n_gl + 1) / 2), fth, sm_fft, st>>>(a, grid, Fk);
-  dim3 gm((a.M + 127) / 128, a.nrhs);
-  if (a.M > 0) k_nufft_modes<T2><<<gm, 128, 0, st>>>(a, Fk, spec, grad != nullptr);
-  k_nufft_inv<T, T2><<<a.nrhs * npk, fth, sm_fft, st>>>(a, spec);
+  k_nufft_fwd<T, T2><<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
+  const int nmode = a.M - a.mlo + 1;
+  dim3 gm((nmode + 127) / 128, a.nrhs);
   const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
-  k_nufft_interp<T, T2><<<(int)((nt + 127) / 128), 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+  const int ni = (int)((nt + 127) / 128);
+  const int wg = grad != nullptr;
+  switch (K) {
+    case PFMM_LAPLACE:
+      k_nufft_modes<T2, PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
+      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, T2, PFMM_LAPLACE><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+      break;
+    case PFMM_MODHELM:
+      k_nufft_modes<T2, PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
+      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, T2, PFMM_MODHELM><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+      break;
+    default:
+      k_nufft_modes<T2, PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
+      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, T2, PFMM_STOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, nullptr);
+      break;
+  }
   g_launches += 5;
   return cudaGetLastError();
 }

@@ -38,6 +38,13 @@ struct Far {
   const double* nodes;  // device [Nq][2] (lambda_n, w_n), in workspace
 };
 
+// NUFFT path: charge channels per rhs (scalar q; Stokes f_x, f_y, y' f_x,
+// y' f_y) and complex evaluation-spectrum lines per rhs (scalar: potential +
+// y-derivative per GL line, x-derivatives two lines per spectrum; Stokes:
+// the a and b weight lines per GL line).
+inline int nufft_nch(int kernel) { return kernel == PFMM_STOKES ? 4 : 1; }
+inline int nufft_npk(int kernel, int n_gl) { return kernel == PFMM_STOKES ? 2 * n_gl : n_gl + (n_gl + 1) / 2; }
+
 // Workspace layout (byte offsets from the workspace base, all 256-aligned).
 struct Layout {
   size_t status, moments, nodes;

@@ -315,14 +315,10 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int path = o->path;
   // the single-block shared-memory FFT handles fine grids up to 8192 points
   if (path == PFMM_PATH_AUTO)
-    path = (M >= 64 && o->kernel == PFMM_LAPLACE && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+    path = (M >= 64 && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
     delete p;
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
-  }
-  if (o->kernel != PFMM_LAPLACE && path == PFMM_PATH_NUFFT) {
-    delete p;
-    return fail(PFMM_ERR_INVALID_ARG, "the NUFFT path is implemented for the Laplace kernel");
   }
   if (M == 0) path = PFMM_PATH_DIRECT;
   p->path = path;
@@ -362,14 +358,12 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   L.wts = take((size_t)nrhs * 4 * std::max(1, f.nterm) * 2 * sizeof(double));
   size_t nuf = 0;
   if (path == PFMM_PATH_NUFFT) {
-    // fine grids [n_gl][nrhs][nf] complex (float2 for mixed, double2 for fp64)
-    // x2 (spread grid + evaluation grids for pot, d/dx, d/dy -> 3 channels)
-    // FP64 spread grid [nrhs][n_gl][nf], FP64 spectra F_n(k) [nrhs][n_gl][M+1],
-    // evaluation spectra [nrhs][n_gl + ceil(n_gl/2)][nf] complex (float2 or double2)
+    // FP64 spread grid [nrhs][nch][n_gl][nf], FP64 spectra F_n(k) [nrhs][nch][n_gl][M+1],
+    // evaluation spectra [nrhs][npk][nf] complex (float2 for mixed, double2 for fp64)
     size_t cplx = (o->precision == PFMM_FP64) ? 16 : 8;
-    int npk = p->n_gl + (p->n_gl + 1) / 2;
-    nuf = (size_t)nrhs * p->n_gl * nf * 8 + (size_t)nrhs * p->n_gl * (M + 1) * 16 + 256 +
-          (size_t)nrhs * npk * nf * cplx + 256;
+    size_t nline = (size_t)nrhs * pfmm::nufft_nch(o->kernel) * p->n_gl;
+    nuf = nline * nf * 8 + nline * (M + 1) * 16 + 256 +
+          (size_t)nrhs * pfmm::nufft_npk(o->kernel, p->n_gl) * nf * cplx + 256;
   }
   L.nufft = take(nuf);
   // adjoint scratch: dL/dpot projected as strengths is handled in place; the

@@ -168,16 +168,48 @@ def test_laplace_nufft_path(precision, e1, e2):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_nufft_matches_direct(precision):
+@pytest.mark.parametrize("kernel,beta", [("modhelm", 0.5), ("modhelm", 3.0), ("stokes", 0.0)])
+@pytest.mark.parametrize("e1,e2", [((40.0, 0.0), (0.0, 1.0)), ((48.0, 0.0), (0.5, 1.0))])
+def test_nufft_path_modhelm_stokes(precision, kernel, beta, e1, e2):
+    """Modified Helmholtz (m = 0 mode included, chi = sqrt(alpha^2 + beta^2))
+    and Stokes (four spread channels, 2 x 2 weight blocks) through the NUFFT
+    south/north path; far part against the total field's scale, and the total."""
+    stokes = kernel == "stokes"
+    mc = kernel != "modhelm"
+    rng = np.random.default_rng(13)
+    src = workloads.points(rng, e1, e2, 1500, "gmm")
+    q = workloads.strengths(rng, 2, 1500, stokes=stokes, neutral=mc)
+    trg = workloads.points(rng, e1, e2, 400)
+    tol = TOL[precision]
+    tot = oracle(kernel, e1, e2, src, q, trg, beta=beta, part="total", grad=not stokes)
+    cen = (lambda a: a - a.mean(-1, keepdims=True)) if mc else (lambda a: a)
+    for part in ("far", "total"):
+        got = run_lib(kernel, e1, e2, src, q, trg, beta=beta, tol=tol, precision=precision, part=part,
+                      path="nufft", grad=not stokes)
+        desc = got[2].describe()
+        assert desc["path"] == 2 and desc["M"] >= 48
+        ref = tot if part == "total" else oracle(kernel, e1, e2, src, q, trg, beta=beta, part=part,
+                                                 grad=not stokes)
+        assert np.linalg.norm(cen(got[0]) - cen(ref[0])) / np.linalg.norm(cen(tot[0])) < tol
+        if not stokes:
+            assert np.linalg.norm(got[1] - ref[1]) / np.linalg.norm(tot[1]) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 1.0), ("stokes", 0.0)])
+def test_nufft_matches_direct(precision, kernel, beta):
     e1, e2 = (24.0, 0.0), (1.5, 1.0)
+    stokes = kernel == "stokes"
+    mc = kernel != "modhelm"
     rng = np.random.default_rng(12)
     src = workloads.points(rng, e1, e2, 2500, "gmm")
-    q = workloads.strengths(rng, 1, 2500)
+    q = workloads.strengths(rng, 1, 2500, stokes=stokes, neutral=mc)
     tol = TOL[precision]
-    a = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="far", path="nufft")
-    b = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="far", path="direct")
-    tot = run_lib("laplace", e1, e2, src, q, None, tol=tol, precision=precision, part="total", path="direct")
-    sc = np.linalg.norm(tot[0] - tot[0].mean(-1, keepdims=True))
-    d = (a[0] - a[0].mean(-1, keepdims=True)) - (b[0] - b[0].mean(-1, keepdims=True))
-    assert np.linalg.norm(d) / sc < tol
-    assert np.linalg.norm(a[1] - b[1]) / np.linalg.norm(tot[1]) < tol
+    kw = dict(beta=beta, tol=tol, precision=precision, grad=not stokes)
+    a = run_lib(kernel, e1, e2, src, q, None, part="far", path="nufft", **kw)
+    b = run_lib(kernel, e1, e2, src, q, None, part="far", path="direct", **kw)
+    tot = run_lib(kernel, e1, e2, src, q, None, part="total", path="direct", **kw)
+    cen = (lambda x: x - x.mean(-1, keepdims=True)) if mc else (lambda x: x)
+    assert np.linalg.norm(cen(a[0]) - cen(b[0])) / np.linalg.norm(cen(tot[0])) < tol
+    if not stokes:
+        assert np.linalg.norm(a[1] - b[1]) / np.linalg.norm(tot[1]) < tol

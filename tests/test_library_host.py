@@ -103,13 +103,22 @@ def test_nufft_parameters(L):
     assert nf & (nf - 1) == 0 and nf >= 2 * (2 * desc["M"] + 1)
 
 
+@pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 0.5), ("stokes", 0.0)])
+def test_auto_path_picks_nufft_for_many_modes(L, kernel, beta):
+    """AUTO takes the NUFFT path once M >= 64, for every kernel, and the direct
+    path for a square cell."""
+    long = _op(kernel=kernel, beta=beta, e1=(40.0, 0.0)).describe()
+    assert long["M"] >= 64 and long["path"] == 2
+    assert _op(kernel=kernel, beta=max(beta, 0.5) if kernel == "modhelm" else 0.0).describe()["path"] == 1
+
+
 @pytest.mark.parametrize("kw,code", [
     (dict(e1=(1.0, 0.0), e2=(2.0, 0.0)), 2),
     (dict(tol=0.5), 4),
     (dict(tol=1e-16), 4),
     (dict(kernel="modhelm", beta=0.0), 1),
     (dict(nrhs=0), 1),
-    (dict(kernel="stokes", path="nufft"), 1),
+    (dict(e1=(2000.0, 0.0), path="nufft"), 1),  # fine grid above 8192 points
 ])
 def test_host_validation(L, kw, code):
     from paper_2111_01083_gb300._lib import PfmmError
