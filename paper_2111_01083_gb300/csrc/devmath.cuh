@@ -35,5 +35,24 @@ __device__ __forceinline__ void expm1c(T a, T b, T* re, T* im) {
   *im = (em + T(1)) * (T(2) * sh * ch);
 }
 
+// Running sum of many terms.  FP32: Kahan compensation (the error stays at a
+// few ulp of the result instead of growing with the number of terms); FP64:
+// plain sum.
+template <typename T>
+struct KSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    if constexpr (sizeof(T) == 4) {
+      const T y = v - c;
+      const T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += v;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 }  // namespace dm
 }  // namespace pfmm

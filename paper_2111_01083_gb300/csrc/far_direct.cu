@@ -366,13 +366,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   const T x = in ? tx[l] : T(0), y = in ? ty[l] : T(0);
   const int U = (in && tU) ? tU[l] : 0;
   const double xd = in ? (double)x / g.d : 0.0;
-  // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy]
+  // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy].  Compensated in FP32:
+  // a few hundred terms of the size of the result are summed per target.
   constexpr int NA = (KER == PFMM_STOKES) ? 2 : 3;
-  T acc[kRB][NA];
-#pragma unroll
-  for (int r = 0; r < kRB; ++r)
-#pragma unroll
-    for (int k = 0; k < NA; ++k) acc[r][k] = T(0);
+  dm::KSum<T> acc[kRB][NA];
 
   for (int t0 = 0; t0 < f.nterm; t0 += kEvalChunk) {
     const int nc = min(kEvalChunk, f.nterm - t0);
@@ -431,20 +428,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
         if (KER != PFMM_STOKES) {
           const T2 w = s_w[r][0][k];
           const T Pr = Lr * w.x - Li * w.y, Pi = Lr * w.y + Li * w.x;
-          acc[r][0] += Mr * w.x - Mi * w.y;
+          acc[r][0].add(Mr * w.x - Mi * w.y);
           if (part < 2) {
-            acc[r][1] -= a * Pi;
-            acc[r][2] -= (part == 0 ? b : -b) * Pr;
+            acc[r][1].add(-a * Pi);
+            acc[r][2].add(-(part == 0 ? b : -b) * Pr);
           } else {
-            acc[r][1] -= (part == 2 ? b : -b) * Pr;
-            acc[r][2] -= a * Pi;
+            acc[r][1].add(-(part == 2 ? b : -b) * Pr);
+            acc[r][2].add(-a * Pi);
           }
         } else {
           const T cd = part < 2 ? y : x;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const T2 wa = s_w[r][c][k], wb = s_w[r][2 + c][k];
-            acc[r][c] += (Mr * wa.x - Mi * wa.y) + cd * (Lr * wb.x - Li * wb.y);
+            acc[r][c].add((Mr * wa.x - Mi * wa.y) + cd * (Lr * wb.x - Li * wb.y));
           }
         }
       }
@@ -456,12 +453,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
     const double cc = mom[(r0 + r) * 8 + 4];
     const double yd = (double)y;
     if (KER == PFMM_STOKES) {
-      double ux = (double)acc[r][0] + cc * yd, uy = (double)acc[r][1];
+      double ux = acc[r][0].value() + cc * yd, uy = acc[r][1].value();
       pot[((size_t)(r0 + r) * 2) * os + l] = R[0] * ux + R[2] * uy;
       pot[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * ux + R[3] * uy;
     } else {
-      double p = (double)acc[r][0] + cc * yd;
-      double gx = (double)acc[r][1], gy = (double)acc[r][2] + cc;
+      double p = acc[r][0].value() + cc * yd;
+      double gx = acc[r][1].value(), gy = acc[r][2].value() + cc;
       if (pot) pot[(size_t)(r0 + r) * os + l] = p;
       if (grad) {
         grad[((size_t)(r0 + r) * 2) * os + l] = R[0] * gx + R[2] * gy;

@@ -42,23 +42,45 @@ struct NufftArgs {
   double es_beta, d, eta, xi, beta;
   const double* gl;      // [n_gl][2] (ybar_n, sigma_n)
   const double* phihat;  // [M+1] phihat(alpha k), k = 0..M
+  const double* tw;      // [nf/2][2] (cos, sin)(2 pi k / nf)
 };
 
-// ES kernel values at the w grid points around theta (in grid units u = theta / h).
-// l0 = first grid index; z_k = (u - (l0 + k)) / (w/2).
+// Position on the fine grid, u = theta / h = nf x / d (mod nf), split as
+// u = i + f with i an integer and 0 <= f <= 1.  FP32 path: from the 32-bit
+// fixed-point phase U = 2^32 x / d (mod 2^32) written by the point
+// preparation, so that f is exact to 2^-24 whatever the cell width (an FP32
+// product x nf / d would lose ~ulp(nf/2) grid units at the cell edge).  FP64
+// path: from x.
 template <typename T>
-__device__ __forceinline__ int es_weights(T u, int w, T beta, T* ker) {
+__device__ __forceinline__ void grid_pos(T x, int U, const NufftArgs& a, int* i, T* f) {
+  if constexpr (sizeof(T) == 4) {
+    const unsigned v = (unsigned)U;
+    *i = (int)(v >> (32 - a.logn));
+    *f = (float)(v << a.logn) * 2.3283064365386963e-10f;  // 2^-32
+  } else {
+    T u = x * (T)(a.nf / a.d);
+    u -= (T)a.nf * floor(u / (T)a.nf);
+    const T fl = floor(u);
+    *i = (int)fl;
+    *f = u - fl;
+  }
+}
+
+// ES kernel values at the w grid points around u = i + f (grid units).
+// Returns l0, the first grid index (not reduced mod nf); z_k = (u - (l0 + k)) / (w/2).
+template <typename T>
+__device__ __forceinline__ int es_weights(int i, T f, int w, T beta, T* ker) {
   const T half = T(0.5) * w;
-  const int l0 = (int)ceil(u - half);
+  const int c = (int)ceil(f - half);
 #pragma unroll 16
   for (int k = 0; k < 16; ++k) {
     if (k < w) {
-      const T z = (u - (T)(l0 + k)) / half;
+      const T z = (f - (T)(c + k)) / half;
       const T s = T(1) - z * z;
       ker[k] = s > T(0) ? dm::ex(beta * (sqrt(s) - T(1))) : T(0);
     }
   }
-  return l0;
+  return i + c;
 }
 
 // Barycentric interpolation weights gamma(y, n) (second form).
@@ -90,14 +112,13 @@ constexpr int kSpreadThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, int chunk, const T* __restrict__ sx,
-                                                                 const T* __restrict__ sy, const T* __restrict__ qv,
-                                                                 double* __restrict__ grid, int use_smem) {
+                                                                 const T* __restrict__ sy, const int* __restrict__ sU,
+                                                                 const T* __restrict__ qv, double* __restrict__ grid,
+                                                                 int use_smem) {
   extern __shared__ unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);  // [n_gl][nf] when use_smem
   const int ngrid = a.n_gl * a.nf;
   const int j0 = blockIdx.x * chunk, j1 = min(a.ns, j0 + chunk);
-  const T twopi_over_d = (T)(2.0 * M_PI / a.d);
-  const T inv_h = (T)(a.nf / (2.0 * M_PI));
   const T beta = (T)a.es_beta;
   const int ncomp = a.nch == 4 ? 2 : 1;
   for (int v = 0; v < a.nrhs * a.nch; ++v) {
@@ -110,11 +131,10 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
     for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
       const T x = sx[j], y = sy[j];
       const T q = ymul ? qrow[j] * y : qrow[j];
-      T th = x * twopi_over_d;  // in [-pi (1 + |xi|/d), ...]; reduced below
-      T u = th * inv_h;
-      u -= (T)a.nf * floor(u / (T)a.nf);  // u in [0, nf)
-      T ker[16], gam[32];
-      const int l0 = es_weights(u, a.w, beta, ker);
+      int gi;
+      T gf, ker[16], gam[32];
+      grid_pos(x, sU[j], a, &gi, &gf);
+      const int l0 = es_weights(gi, gf, a.w, beta, ker);
       bary(y, a.gl, a.n_gl, gam);
       double* gr = grid + (size_t)v * ngrid;
       for (int n = 0; n < a.n_gl; ++n) {
@@ -142,20 +162,19 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
 
 // ---------------------------------------------------------------------------
 // K5: radix-2 complex FFT in shared memory (iterative, decimation in time,
-// bit-reversed load).  One block per transform.  sign = -1 forward, +1 inverse.
+// bit-reversed load), FP64 with twiddles from the plan's FP64 table.  One
+// block per transform.  sign = -1 forward, +1 inverse.
 // ---------------------------------------------------------------------------
-template <typename T, typename T2>
-__device__ void fft_smem(T2* s, int n, int logn, int sign) {
+__device__ void fft_smem(double2* s, int n, const double* __restrict__ tw, int sign) {
   for (int len = 2; len <= n; len <<= 1) {
-    const int half = len >> 1;
+    const int half = len >> 1, step = n / len;
     for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
       const int grp = b / half, k = b % half;
       const int i0 = grp * len + k, i1 = i0 + half;
-      T sn, cs;
-      dm::sincospi_((T)(sign * 2) * (T)k / (T)len, &sn, &cs);
-      const T2 x1 = s[i1];
-      const T2 t = {x1.x * cs - x1.y * sn, x1.x * sn + x1.y * cs};
-      const T2 x0 = s[i0];
+      const double cs = __ldg(tw + 2 * k * step), sn = sign * __ldg(tw + 2 * k * step + 1);
+      const double2 x1 = s[i1];
+      const double2 t = {x1.x * cs - x1.y * sn, x1.x * sn + x1.y * cs};
+      const double2 x0 = s[i0];
       s[i0] = {x0.x + t.x, x0.y + t.y};
       s[i1] = {x0.x - t.x, x0.y - t.y};
     }
@@ -168,26 +187,25 @@ __device__ __forceinline__ int bitrev(int i, int logn) { return __brev(i) >> (32
 // Forward transforms of the spread grids, two real lines per FFT, then
 // deconvolution: F(k) for k = 0..M of every line (charge vector, GL line)
 // written to Fk [nrhs][nch][n_gl][M+1] (double2).
-template <typename T, typename T2>
 __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double2* __restrict__ Fk) {
   extern __shared__ unsigned char smem_raw[];
-  T2* s = reinterpret_cast<T2*>(smem_raw);
+  double2* s = reinterpret_cast<double2*>(smem_raw);
   const int nline = a.nrhs * a.nch * a.n_gl;
   const int n0 = 2 * blockIdx.x, n1 = 2 * blockIdx.x + 1;
   const double* g0 = grid + (size_t)n0 * a.nf;
   const double* g1 = (n1 < nline) ? grid + (size_t)n1 * a.nf : nullptr;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) {
     const int j = bitrev(i, a.logn);
-    s[j] = {(T)g0[i], g1 ? (T)g1[i] : T(0)};
+    s[j] = {g0[i], g1 ? g1[i] : 0.0};
   }
   __syncthreads();
-  fft_smem<T, T2>(s, a.nf, a.logn, -1);
+  fft_smem(s, a.nf, a.tw, -1);
   const double scale = 2.0 / a.w;
   for (int k = threadIdx.x; k <= a.M; k += blockDim.x) {
-    const T2 zk = s[k], zm = s[(a.nf - k) & (a.nf - 1)];
+    const double2 zk = s[k], zm = s[(a.nf - k) & (a.nf - 1)];
     // X = (Z_k + conj Z_-k)/2, Y = (Z_k - conj Z_-k)/(2i)
-    const double xr = 0.5 * ((double)zk.x + zm.x), xi = 0.5 * ((double)zk.y - zm.y);
-    const double yr = 0.5 * ((double)zk.y + zm.y), yi = -0.5 * ((double)zk.x - zm.x);
+    const double xr = 0.5 * (zk.x + zm.x), xi = 0.5 * (zk.y - zm.y);
+    const double yr = 0.5 * (zk.y + zm.y), yi = -0.5 * (zk.x - zm.x);
     const double dec = scale / a.phihat[k];
     Fk[(size_t)n0 * (a.M + 1) + k] = make_double2(xr * dec, xi * dec);
     if (n1 < nline) Fk[(size_t)n1 * (a.M + 1) + k] = make_double2(yr * dec, yi * dec);
@@ -196,30 +214,29 @@ __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double
 
 // Mode combination, lattice weights and evaluation-line spectra (FP64).
 // One thread per (rhs, mode m = mlo..M).  Writes the type-2 input spectra,
-// layout spec [nrhs][npk][nf] (T2), zero elsewhere (cleared before):
+// layout spec [nrhs][npk][nf] (double2), zero elsewhere (cleared before):
 //   scalar: line n: pot_n + i gy_n;  line n_gl + p: gx_{2p} + i gx_{2p+1}
 //   Stokes: line n: Ga_{x,n} + i Ga_{y,n};  line n_gl + n: Gb_{x,n} + i Gb_{y,n}
 // A real output line Re sum_m e^{i m theta} a_m packed with a second one
 // (b_m) into a complex line has H_m = (a_m + i b_m)/2, H_-m = (conj a_m + i conj b_m)/2
 // for m >= 1, and H_0 = a_0 + i b_0 (a_0, b_0 real).
-template <typename T2, int KER>
-__global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, T2* __restrict__ spec, int want_grad) {
-  using TT = decltype(T2::x);
+template <int KER>
+__global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, double2* __restrict__ spec, int want_grad) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x + a.mlo;
   const int r = blockIdx.y;
   if (m > a.M) return;
   const double al = 2.0 * M_PI * m / a.d;
   const double chi = (KER == PFMM_MODHELM) ? sqrt(al * al + a.beta * a.beta) : fabs(al);
   const double pre = (2.0 / a.w) / a.phihat[m];
-  T2* base = spec + (size_t)r * a.npk * a.nf;
+  double2* base = spec + (size_t)r * a.npk * a.nf;
   auto put = [&](int line, dcx va, dcx vb) {
-    T2* row = base + (size_t)line * a.nf;
+    double2* row = base + (size_t)line * a.nf;
     if (m == 0) {
-      row[0] = {(TT)(pre * (va.r - vb.i)), (TT)(pre * (va.i + vb.r))};
+      row[0] = {pre * (va.r - vb.i), pre * (va.i + vb.r)};
       return;
     }
-    row[m] = {(TT)(0.5 * pre * (va.r - vb.i)), (TT)(0.5 * pre * (va.i + vb.r))};
-    row[a.nf - m] = {(TT)(0.5 * pre * (va.r + vb.i)), (TT)(0.5 * pre * (-va.i + vb.r))};
+    row[m] = {0.5 * pre * (va.r - vb.i), 0.5 * pre * (va.i + vb.r)};
+    row[a.nf - m] = {0.5 * pre * (va.r + vb.i), 0.5 * pre * (-va.i + vb.r)};
   };
   auto F = [&](int c, int n) {
     const double2 v = Fk[(((size_t)r * a.nch + c) * a.n_gl + n) * (a.M + 1) + m];
@@ -287,77 +304,78 @@ __global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, T2* _
 }
 
 // Inverse FFT of each packed line spectrum in place (bit-reversed load into smem).
-template <typename T, typename T2>
-__global__ void k_nufft_inv(NufftArgs a, T2* __restrict__ spec) {
+__global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec) {
   extern __shared__ unsigned char smem_raw[];
-  T2* s = reinterpret_cast<T2*>(smem_raw);
-  T2* row = spec + (size_t)blockIdx.x * a.nf;
+  double2* s = reinterpret_cast<double2*>(smem_raw);
+  double2* row = spec + (size_t)blockIdx.x * a.nf;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) s[bitrev(i, a.logn)] = row[i];
   __syncthreads();
-  fft_smem<T, T2>(s, a.nf, a.logn, +1);
+  fft_smem(s, a.nf, a.tw, +1);
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) row[i] = s[i];
 }
 
 // Interpolation at targets + barycentric combination over lines; adds the
-// south/north field to pot / grad (input frame).
-template <typename T, typename T2, int KER>
+// south/north field to pot / grad (input frame).  The spectra are FP64; the
+// mixed path interpolates in FP32 and sums over lines with compensation.
+template <typename T, int KER>
 __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, const T* __restrict__ ty,
-                               const T2* __restrict__ spec, double* __restrict__ pot, double* __restrict__ grad) {
+                               const int* __restrict__ tU, const double2* __restrict__ spec, double* __restrict__ pot,
+                               double* __restrict__ grad) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= a.nt) return;
   const T x = tx[l], y = ty[l];
-  T u = x * (T)(2.0 * M_PI / a.d) * (T)(a.nf / (2.0 * M_PI));
-  u -= (T)a.nf * floor(u / (T)a.nf);
-  T ker[16], gam[32];
-  const int l0 = es_weights(u, a.w, (T)a.es_beta, ker);
+  int gi;
+  T gf, ker[16], gam[32];
+  grid_pos(x, tU[l], a, &gi, &gf);
+  const int l0 = es_weights(gi, gf, a.w, (T)a.es_beta, ker);
   bary(y, a.gl, a.n_gl, gam);
   const double* R = g.rot;
   for (int r = 0; r < a.nrhs; ++r) {
-    const T2* base = spec + (size_t)r * a.npk * a.nf;
+    const double2* base = spec + (size_t)r * a.npk * a.nf;
     if (KER == PFMM_STOKES) {
-      T ux = 0, uy = 0;
+      dm::KSum<T> ux, uy;
       for (int n = 0; n < a.n_gl; ++n) {
-        const T2* ra = base + (size_t)n * a.nf;
-        const T2* rb = base + (size_t)(a.n_gl + n) * a.nf;
+        const double2* ra = base + (size_t)n * a.nf;
+        const double2* rb = base + (size_t)(a.n_gl + n) * a.nf;
         T sax = 0, say = 0, sbx = 0, sby = 0;
         for (int k = 0; k < a.w; ++k) {
           const int li = (l0 + k) & (a.nf - 1);
-          const T2 va = ra[li], vb = rb[li];
-          sax += ker[k] * va.x;
-          say += ker[k] * va.y;
-          sbx += ker[k] * vb.x;
-          sby += ker[k] * vb.y;
+          const double2 va = ra[li], vb = rb[li];
+          sax += ker[k] * (T)va.x;
+          say += ker[k] * (T)va.y;
+          sbx += ker[k] * (T)vb.x;
+          sby += ker[k] * (T)vb.y;
         }
-        ux += gam[n] * (sax + y * sbx);
-        uy += gam[n] * (say + y * sby);
+        ux.add(gam[n] * (sax + y * sbx));
+        uy.add(gam[n] * (say + y * sby));
       }
-      const double uxd = ux, uyd = uy;
+      const double uxd = ux.value(), uyd = uy.value();
       pot[((size_t)r * 2) * a.os + l] += R[0] * uxd + R[2] * uyd;
       pot[((size_t)r * 2 + 1) * a.os + l] += R[1] * uxd + R[3] * uyd;
       continue;
     }
-    T p = 0, gx = 0, gy = 0;
+    dm::KSum<T> p, gx, gy;
     for (int n = 0; n < a.n_gl; ++n) {
-      const T2* row = base + (size_t)n * a.nf;
-      const T2* rowx = base + (size_t)(a.n_gl + n / 2) * a.nf;
+      const double2* row = base + (size_t)n * a.nf;
+      const double2* rowx = base + (size_t)(a.n_gl + n / 2) * a.nf;
       T sp = 0, sy = 0, sx = 0;
       for (int k = 0; k < a.w; ++k) {
         const int li = (l0 + k) & (a.nf - 1);
-        const T2 v = row[li];
-        sp += ker[k] * v.x;
-        sy += ker[k] * v.y;
+        const double2 v = row[li];
+        sp += ker[k] * (T)v.x;
+        sy += ker[k] * (T)v.y;
         if (grad) {
-          const T2 vx = rowx[li];
-          sx += ker[k] * ((n & 1) ? vx.y : vx.x);
+          const double2 vx = rowx[li];
+          sx += ker[k] * (T)((n & 1) ? vx.y : vx.x);
         }
       }
-      p += gam[n] * sp;
-      gy += gam[n] * sy;
-      gx += gam[n] * sx;
+      p.add(gam[n] * sp);
+      gy.add(gam[n] * sy);
+      gx.add(gam[n] * sx);
     }
-    if (pot) pot[(size_t)r * a.os + l] += (double)p;
+    if (pot) pot[(size_t)r * a.os + l] += p.value();
     if (grad) {
-      const double gxd = gx, gyd = gy;
+      const double gxd = gx.value(), gyd = gy.value();
       grad[((size_t)r * 2) * a.os + l] += R[0] * gxd + R[2] * gyd;
       grad[((size_t)r * 2 + 1) * a.os + l] += R[1] * gxd + R[3] * gyd;
     }
@@ -365,7 +383,7 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, typename T2>
+template <typename T>
 static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
                              double* grad, cudaStream_t st) {
   const Layout& L = p->lay;
@@ -391,9 +409,9 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   a.eta = p->geom.eta;
   a.xi = p->geom.xi;
   a.beta = p->far.beta;
-  size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
-  a.gl = (const double*)(ws + L.nodes + nb);
-  a.phihat = (const double*)(ws + L.nodes + nb + p->n_gl * 2 * sizeof(double));
+  a.gl = (const double*)(ws + L.nodes + off_gl(p));
+  a.phihat = (const double*)(ws + L.nodes + off_phihat(p));
+  a.tw = (const double*)(ws + L.nodes + off_twiddle(p));
   // workspace partition of the NUFFT scratch
   const int nline = a.nrhs * a.nch * a.n_gl;
   char* base = ws + L.nufft;
@@ -402,10 +420,10 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   double2* Fk = (double2*)(base + off);                           // [nrhs][nch][n_gl][M+1]
   off += (size_t)nline * (a.M + 1) * sizeof(double2);
   off = (off + 255) & ~size_t(255);
-  T2* spec = (T2*)(base + off);                                   // [nrhs][npk][nf]
+  double2* spec = (double2*)(base + off);                         // [nrhs][npk][nf]
   cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)nline * a.nf * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * a.npk * a.nf * sizeof(T2), st);
+  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * a.npk * a.nf * sizeof(double2), st);
   if (e != cudaSuccess) return e;
   const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
   const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
@@ -419,36 +437,38 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
     e = cudaFuncSetAttribute(k_nufft_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spread);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_spread<T><<<nchunk, kSpreadThreads, sm_spread, st>>>(a, chunk, sx, sx + ns, qv, grid, use_smem);
+  const int* sU = (const int*)(ws + L.srcU);
+  k_nufft_spread<T><<<nchunk, kSpreadThreads, sm_spread, st>>>(a, chunk, sx, sx + ns, sU, qv, grid, use_smem);
   const int fth = std::min(512, std::max(32, a.nf / 2));
-  const size_t sm_fft = (size_t)a.nf * sizeof(T2);
+  const size_t sm_fft = (size_t)a.nf * sizeof(double2);
   if (sm_fft > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_nufft_fwd<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
+    e = cudaFuncSetAttribute(k_nufft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_nufft_inv<T, T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
+      e = cudaFuncSetAttribute(k_nufft_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_fwd<T, T2><<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
+  k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
   const int nmode = a.M - a.mlo + 1;
   dim3 gm((nmode + 127) / 128, a.nrhs);
   const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
+  const int* tU = self ? sU : (const int*)(ws + L.trgU);
   const int ni = (int)((nt + 127) / 128);
   const int wg = grad != nullptr;
   switch (K) {
     case PFMM_LAPLACE:
-      k_nufft_modes<T2, PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, T2, PFMM_LAPLACE><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+      k_nufft_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, PFMM_LAPLACE><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, grad);
       break;
     case PFMM_MODHELM:
-      k_nufft_modes<T2, PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, T2, PFMM_MODHELM><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, grad);
+      k_nufft_modes<PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, PFMM_MODHELM><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, grad);
       break;
     default:
-      k_nufft_modes<T2, PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
-      k_nufft_inv<T, T2><<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, T2, PFMM_STOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, spec, pot, nullptr);
+      k_nufft_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, PFMM_STOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, nullptr);
       break;
   }
   g_launches += 5;
@@ -466,8 +486,8 @@ cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   cudaError_t e = launch_far_direct(&q, ws, ns, nt, self, pot, grad, st);
   if (e != cudaSuccess) return e;
   if (p->far.M > 0) {
-    e = (p->opts.precision == PFMM_MIXED) ? run_nufft<float, float2>(p, ws, ns, nt, self, pot, grad, st)
-                                          : run_nufft<double, double2>(p, ws, ns, nt, self, pot, grad, st);
+    e = (p->opts.precision == PFMM_MIXED) ? run_nufft<float>(p, ws, ns, nt, self, pot, grad, st)
+                                          : run_nufft<double>(p, ws, ns, nt, self, pot, grad, st);
   }
   return e;
 }

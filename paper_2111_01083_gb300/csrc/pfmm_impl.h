@@ -82,6 +82,7 @@ struct pfmm_plan {
   double es_beta;
   double* gl_h;             // [n_gl][2] (ybar_n, sigma_n) on [-eta/2, eta/2]
   double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
+  double* tw_h;             // [nf/2][2] FFT twiddles (cos, sin)(2 pi k / nf), NUFFT path only
   pfmm::Layout lay;
   // row strides of the caller's arrays for the current execute: sources
   // (src [2][*], q [nrhs][comp][*]), targets (trg [2][*]) and outputs
@@ -96,6 +97,18 @@ struct pfmm_plan {
 };
 
 namespace pfmm {
+// Byte offsets inside the node-table region (L.nodes): west/east nodes
+// [max(1,Nq)][2], GL lines [n_gl][2], phihat [M+1], then (16-aligned) the FFT
+// twiddles [nf/2][2].
+inline size_t off_gl(const pfmm_plan* p) { return (size_t)(p->Nq > 0 ? p->Nq : 1) * 2 * sizeof(double); }
+inline size_t off_phihat(const pfmm_plan* p) { return off_gl(p) + (size_t)p->n_gl * 2 * sizeof(double); }
+inline size_t off_twiddle(const pfmm_plan* p) {
+  return (off_phihat(p) + (size_t)(p->far.M + 1) * sizeof(double) + 15) & ~size_t(15);
+}
+inline size_t node_region_bytes(const pfmm_plan* p) {
+  return off_twiddle(p) + (p->tw_h ? (size_t)p->nf * sizeof(double) : 0);
+}
+
 // kernels.cu entry points (host-side launchers)
 cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q,
                         int64_t nt, const double* trg, bool self, cudaStream_t st);

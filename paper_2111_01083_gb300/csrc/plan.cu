@@ -162,14 +162,16 @@ pfmm_status set_error(pfmm_status s, const char* fmt, ...) {
 // Copy the plan's host tables (west/east nodes, GL lines, ES transform) into
 // the workspace.
 cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st) {
-  size_t nb = std::max(1, p->Nq) * 2 * sizeof(double);
+  char* base = ws + p->lay.nodes;
   cudaError_t e = cudaSuccess;
-  if (p->Nq > 0) e = cudaMemcpyAsync(ws + p->lay.nodes, p->nodes_h, p->Nq * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (p->Nq > 0) e = cudaMemcpyAsync(base, p->nodes_h, p->Nq * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + p->lay.nodes + nb, p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(base + off_gl(p), p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + p->lay.nodes + nb + p->n_gl * 2 * sizeof(double), p->phihat_h,
-                        (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(base + off_phihat(p), p->phihat_h, (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess && p->tw_h)
+    e = cudaMemcpyAsync(base + off_twiddle(p), p->tw_h, p->nf * sizeof(double), cudaMemcpyHostToDevice, st);
   return e;
 }
 
@@ -317,7 +319,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (path == PFMM_PATH_AUTO)
     path = (M >= 64 && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
-    delete p;
+    pfmm_plan_destroy(p);
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
   }
   if (M == 0) path = PFMM_PATH_DIRECT;
@@ -335,6 +337,15 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     }
     p->phihat_h = (double*)std::malloc((M + 1) * sizeof(double));
     for (int m = 0; m <= M; ++m) p->phihat_h[m] = es_phihat(p->es_beta, 2.0 * M_PI * m * (w * 0.5) / nf);
+    p->tw_h = nullptr;
+    if (path == PFMM_PATH_NUFFT) {
+      // FP64 twiddles for the shared-memory FFT: (cos, sin)(2 pi k / nf), k < nf/2
+      p->tw_h = (double*)std::malloc(nf * sizeof(double));
+      for (int k = 0; k < nf / 2; ++k) {
+        p->tw_h[2 * k] = std::cos(2.0 * M_PI * k / nf);
+        p->tw_h[2 * k + 1] = std::sin(2.0 * M_PI * k / nf);
+      }
+    }
   }
 
   // ---- workspace layout
@@ -344,7 +355,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int nrhs = o->nrhs;
   L.status = take(kStatusWords * sizeof(int));
   L.moments = take(nrhs * 8 * sizeof(double));
-  L.nodes = take(std::max(1, p->Nq) * 2 * sizeof(double) + (p->n_gl * 2 + (M + 1)) * sizeof(double));
+  L.nodes = take(pfmm::node_region_bytes(p));
   L.src64 = take(2 * ns_max * sizeof(double));
   L.trg64 = take(2 * nt_max * sizeof(double));
   L.srcf = take(2 * ns_max * sizeof(float));
@@ -360,7 +371,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (path == PFMM_PATH_NUFFT) {
     // FP64 spread grid [nrhs][nch][n_gl][nf], FP64 spectra F_n(k) [nrhs][nch][n_gl][M+1],
     // evaluation spectra [nrhs][npk][nf] complex (float2 for mixed, double2 for fp64)
-    size_t cplx = (o->precision == PFMM_FP64) ? 16 : 8;
+    size_t cplx = 16;  // FFTs and spectra are FP64 on both precision paths
     size_t nline = (size_t)nrhs * pfmm::nufft_nch(o->kernel) * p->n_gl;
     nuf = nline * nf * 8 + nline * (M + 1) * 16 + 256 +
           (size_t)nrhs * pfmm::nufft_npk(o->kernel, p->n_gl) * nf * cplx + 256;
@@ -388,6 +399,7 @@ void pfmm_plan_destroy(pfmm_plan* p) {
   std::free(p->nodes_h);
   std::free(p->gl_h);
   std::free(p->phihat_h);
+  std::free(p->tw_h);
   delete p;
 }
 

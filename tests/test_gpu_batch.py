@@ -92,6 +92,37 @@ def test_batch_separate_targets_mixed(kernel):
             assert eg < 1e-6, (c, eg)
 
 
+@pytest.mark.parametrize("kernel", ["modhelm", "stokes"])
+def test_batch_mixes_nufft_and_direct_cells(kernel):
+    """Wide cells (M >= 64) take the NUFFT south/north path inside a batch next
+    to square ones on the direct path; graph replay against the oracle."""
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp
+    rng = np.random.default_rng(21)
+    beta = 0.5 if kernel == "modhelm" else 0.0
+    shapes = [((48.0, 0.0), (0.0, 1.0)), ((1.0, 0.0), (0.2, 1.0)), ((64.0, 0.0), (0.3, 1.0)), ((2.0, 0.0), (0.0, 1.0))]
+    cells, srcs, qs = [], [], []
+    for e1, e2 in shapes:
+        n = int(rng.integers(300, 900))
+        srcs.append(workloads.points(rng, e1, e2, n, "gmm"))
+        qs.append(workloads.strengths(rng, 2, n, stokes=kernel == "stokes", neutral=kernel != "modhelm"))
+        cells.append(dict(e1=e1, e2=e2, beta=beta))
+    paths = [PeriodicOp(kernel, c["e1"], c["e2"], beta=beta, tol=1e-6, precision="mixed", nrhs=2, ns_max=10,
+                        nt_max=10).describe()["path"] for c in cells]
+    assert paths == [2, 1, 2, 1]
+    pot, gr = _run_batch(kernel, cells, srcs, qs, "mixed", 1e-6, 2, graph=True)
+    counts = [s.shape[1] for s in srcs]
+    pots = _split(pot, counts)
+    grs = _split(gr, counts) if gr is not None else [None] * len(counts)
+    for c in range(len(cells)):
+        ref = oracle(kernel, cells[c]["e1"], cells[c]["e2"], srcs[c], qs[c], None, beta=beta,
+                     grad=kernel != "stokes")
+        ep, eg = errs(kernel, (pots[c], grs[c]), ref)
+        assert ep < 1e-6, (c, ep)
+        if eg is not None:
+            assert eg < 1e-6, (c, eg)
+
+
 def test_batch_graph_replay_matches_eager():
     cells, srcs, qs = _cells(6, 7, "modhelm", 300, 1200, 16.0, betas=(1.0, 10.0), nrhs=8)
     a = _run_batch("modhelm", cells, srcs, qs, "mixed", 1e-6, 8, p2p_chunk=512)
