@@ -36,9 +36,48 @@ WORKLOAD = "laplace_aspect16_gmm_n1e5"
 METRIC = "targets+sources/s of periodic Laplace/Stokes op, mixed vs FP64 at rel err 1e-6"
 SMS = 152
 SM_MAX_MHZ = 2070.0
-# MUFU rate for lg2/rcp measured on this GPU model (per SM per clock; nominal 32);
-# the Laplace pair needs two (log2 and reciprocal).
-MUFU_PER_CLK_SM = 28.4
+
+# Per-pair algorithmic work of the near-image P2P, one pair = (target, source,
+# near image): (FP32 operations, MUFU operations).  Laplace potential +
+# gradient: differences, r^2, 1/r^2 and log r^2, three accumulations.  Stokes
+# velocity: the same plus the dyadic (x^2 - y^2, x y over r^2) and two
+# components.  Modified Helmholtz K0(beta r) by the A&S 9.8 fits: differences,
+# r^2, sqrt, exp or log, a 7-term polynomial, one accumulation per rhs (with
+# the gradient also K1 and two more accumulations per rhs).
+def p2p_work(kernel, nrhs, grad):
+    if kernel == "laplace":
+        return (12, 2) if grad else (6, 1)
+    if kernel == "stokes":
+        return (20, 2)
+    return (26 + 3 * nrhs, 2) if grad else (17 + nrhs, 2)
+
+
+def alu_rates():
+    """Results per clock per SM measured on this GPU model by
+    paper_2111_01083_gb300/alu_peaks.py (committed as profiles/alu_peaks.json)."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "profiles", "alu_peaks.json")))
+        return {"fp32": d["ffma2_packed"], "mufu": min(d["mufu_lg2"], d["mufu_rcp"], d["mufu_ex2"], d["mufu_rsqrt"]),
+                "source": "profiles/alu_peaks.json (measured)"}
+    except Exception:
+        return {"fp32": 256.0, "mufu": 28.4, "source": "fallback constants (profiles/alu_peaks.json missing)"}
+
+
+def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=None):
+    """Bound = min(FP32 rate / FP32 ops per pair, MUFU rate / MUFU ops per pair)
+    x 152 SMs x the maximum SM clock; achieved = pairs per launch / launch time."""
+    fp32_ops, mufu_ops = p2p_work(kernel, nrhs, grad)
+    r = alu_rates()
+    f_fp32 = r["fp32"] / fp32_ops
+    f_mufu = r["mufu"] / mufu_ops
+    peak = SMS * min(f_fp32, f_mufu) * SM_MAX_MHZ * 1e6 / 1e9
+    achieved = pairs / (launch_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_basis": (f"min(FP32 {r['fp32']:.1f}/clk/SM / {fp32_ops} ops, MUFU {r['mufu']:.1f}/clk/SM / "
+                           f"{mufu_ops} ops) per pair x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz; "
+                           f"{'FP32' if f_fp32 < f_mufu else 'MUFU'}-bound; rates from {r['source']}"),
+            "pairs_per_launch": pairs, "launch_ms": launch_ms, "share_of_step": launch_ms / step_ms}
 
 
 def parse():
@@ -186,6 +225,101 @@ def traffic_for(kernel_file, key):
         return None
 
 
+BATCH_ORACLE_SNIPPET = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, %(root)r)
+import workloads
+from oracle import ewald, lattice, method
+cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8)
+counts = np.array([c["src"].shape[1] for c in cells])
+order = np.argsort(counts)
+pick = [int(order[int(f * (len(order) - 1))]) for f in %(quantiles)r]
+rng = np.random.default_rng(5)
+res = []
+for c in pick:
+    cell = cells[c]
+    cl, s, t = lattice.to_canonical(cell["e1"], cell["e2"], cell["src"], cell["src"])
+    idx = rng.choice(s.shape[1], %(ntarg)d, replace=False)
+    t0 = time.perf_counter()
+    ewald.near_sum("modhelm", %(beta)r, cl, t[:, idx], s, cell["q"], want_grad=False)
+    method.far_field("modhelm", %(beta)r, cl, t[:, idx], s, cell["q"], eps=1e-7, want_grad=False)
+    res.append((int(s.shape[1]), %(ntarg)d, time.perf_counter() - t0))
+print(json.dumps({"samples": res, "sum_n2": float(np.sum(counts.astype(float) ** 2)), "sum_n": int(counts.sum())}))
+"""
+
+
+def batch_oracle_time(beta, quantiles=(0.25, 0.5, 0.75, 0.9), ntarg=12):
+    """FP64 oracle on a bounded sample of the batch: ntarg targets in each of a
+    few cells (quantiles of N), all their sources, 8 rhs; the cost per
+    (target, source) is extrapolated to sum_c N_c^2 (targets = sources)."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = BATCH_ORACLE_SNIPPET % dict(root=ROOT, quantiles=list(quantiles), ntarg=ntarg, beta=beta)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    work = sum(n * k for n, k, _ in d["samples"])
+    wall = sum(t for _, _, t in d["samples"])
+    t_full = wall / work * d["sum_n2"]
+    return {"value": 2 * d["sum_n"] / t_full, "unit": "targets+sources/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (near sum + plain far field, 8 rhs) for {ntarg} targets in each of "
+                       f"{len(d['samples'])} cells (N = {', '.join(str(n) for n, _, _ in d['samples'])}; "
+                       f"{wall:.1f} s); cost per (target, source) extrapolated to sum_c N_c^2")}
+
+
+def init_dist(world, dev):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    dist.init_process_group("nccl", device_id=dev)
+    return dist
+
+
+def max_over_ranks(dist, x, dev):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_region(step, args, dist, dev, local):
+    """W untimed steps, then K steps timed with CUDA events on the launching
+    stream (L2 flushed by a 256 MiB write before each, outside the events),
+    with a barrier + synchronize on both sides; clocks sampled meanwhile.
+    Returns (mean ms per step, max over ranks; clocks)."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
+    proc, fh = start_clocks(clk_path)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = stop_clocks(proc, fh, clk_path, local)
+    return max_over_ranks(dist, sum(ts) / len(ts), dev), clocks
+
+
 def run_batch(args, rank, world, local):
     """Batched modified Helmholtz: 256 cells (eta = 1, d log-uniform in [1, 64],
     N log-uniform in [500, 5e4]), 8 rhs, one beta per run, the whole batch
@@ -197,47 +331,76 @@ def run_batch(args, rank, world, local):
     beta = float(args.workload.split("beta")[-1])
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    dist = init_dist(world, dev)
     cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8, scale=args.scale)
     counts = [c["src"].shape[1] for c in cells]
-    S = torch.tensor(np.concatenate([c["src"] for c in cells], axis=1), device=dev)
-    Q = torch.tensor(np.concatenate([c["q"] for c in cells], axis=1), device=dev)
+    S_h = torch.from_numpy(np.ascontiguousarray(np.concatenate([c["src"] for c in cells], axis=1))).pin_memory()
+    Q_h = torch.from_numpy(np.ascontiguousarray(np.concatenate([c["q"] for c in cells], axis=1))).pin_memory()
+    S = S_h.to(dev)
+    Q = Q_h.to(dev)
     op = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=beta) for c in cells], counts, precision="mixed",
                  nrhs=8, tol=1e-6)
     graph, out = op.capture(S, Q, grad=False)
     torch.cuda.synchronize()
     op.status(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
-    clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
-    proc, fh = start_clocks(clk_path)
-    time.sleep(0.3)
-    step_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        graph.replay()
-        e1.record()
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-    clocks = stop_clocks(proc, fh, clk_path, local)
-    ms = sum(step_ms) / len(step_ms)
+    ms, clocks = timed_region(graph.replay, args, dist, dev, local)
     ns = int(sum(counts))
     pairs = int(sum(9 * n * n for n in counts))
+
+    # phase split and launch count: eager executes on the same buffers, profiled
+    op.profile(True)
+    ph = []
+    for _ in range(3):
+        op(S, Q, out=out, grad=False)
+        ph.append(op.phase_ms())
+    op.profile(False)
+    cell_ms = statistics.median(p[0] for p in ph)
+    p2p_ms = statistics.median(p[1] for p in ph)
+    nlaunch = ph[-1][2]
+
+    # end to end: pinned host inputs -> device, graph replay, potentials -> pinned host
+    pot_h = torch.empty(tuple(out[0].shape), dtype=torch.float64).pin_memory()
+    cur = torch.cuda.current_stream(dev)
+    e2e_t = []
+    for _ in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.copy_(S_h, non_blocking=True)
+        Q.copy_(Q_h, non_blocking=True)
+        graph.replay()
+        pot_h.copy_(out[0], non_blocking=True)
+        cur.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(dist, statistics.median(e2e_t[1:]), dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu and args.scale == 1.0:
+        try:
+            cpu = batch_oracle_time(beta)
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[:200]}
     line = {"metric": METRIC, "value": world * 2 * ns / (ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
-            "config": {"workload": args.workload, "kernel": "modhelm", "beta": beta, "ncell": 256, "nrhs": 8,
+            "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
+                       "kernel": "modhelm", "beta": beta, "ncell": 256, "nrhs": 8,
                        "n_sources_total": ns, "targets_are_sources": True, "near_block_pairs": pairs,
                        "execution": "one CUDA graph per step (per-cell far field + one persistent P2P kernel)",
-                       "l2": "flushed (256 MiB write) before each timed step"},
-            "near_pairs_per_s": pairs / (ms * 1e-3), "roofline": None, "cpu_baseline": None, "clocks": clocks,
-            "gpu_launches": None}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+                       "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
+            "phases_ms": {"per_cell_prep_and_far_field": cell_ms, "batched_p2p": p2p_ms, "measured": "eager execute"},
+            "roofline": p2p_roofline("modhelm", 8, False, pairs, p2p_ms, cell_ms + p2p_ms,
+                                     "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz)"),
+            "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": {"value": world * 2 * ns / e2e_s, "unit": "targets+sources/s",
+                    "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8, "d2h_bytes_per_step": pot_h.numel() * 8,
+                    "api": "BatchOp CUDA-graph replay with pinned host copies in the timed region"},
+            "gpu_launches": nlaunch * args.steps}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -250,12 +413,14 @@ def run_adjoint(args, rank, world, local):
     from paper_2111_01083_gb300 import PeriodicOp, periodic
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    dist = init_dist(world, dev)
     w = workloads.make(args.workload, scale=args.scale)
     n = w["src"].shape[1]
-    S = torch.tensor(w["src"], device=dev, requires_grad=True)
-    Q = torch.tensor(w["q"], device=dev, requires_grad=True)
+    S_h = torch.from_numpy(w["src"]).pin_memory()
+    Q_h = torch.from_numpy(w["q"]).pin_memory()
+    S = S_h.to(dev).requires_grad_(True)
+    Q = Q_h.to(dev).requires_grad_(True)
     op = PeriodicOp("laplace", w["e1"], w["e2"], tol=w["tol"], precision="mixed", ns_max=n, nt_max=n)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
         S.grad = None
@@ -263,33 +428,68 @@ def run_adjoint(args, rank, world, local):
         pot, _ = periodic(op, S, Q)
         (0.5 * (Q * pot).sum()).backward()
 
-    for _ in range(args.warmup):
-        step()
+    step()
     torch.cuda.synchronize()
     op.status()
-    clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
-    proc, fh = start_clocks(clk_path)
-    time.sleep(0.3)
-    ts = []
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+    ms, clocks = timed_region(step, args, dist, dev, local)
+    # the adjoint execute is the last one of a step: its P2P phase and launch count
+    op.profile(True)
+    p2p, nl = [], []
+    for _ in range(3):
         step()
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    clocks = stop_clocks(proc, fh, clk_path, local)
-    ms = sum(ts) / len(ts)
+        p2p.append(op.phase_ms()[2])
+        nl.append(op.describe()["nlaunch"])
+    op.profile(False)
+    desc = op.describe()
+    p2p_ms = statistics.median(p2p)
+    # end to end: pinned host inputs -> device, forward + backward, gradients -> pinned host
+    dq_h = torch.empty((1, n), dtype=torch.float64).pin_memory()
+    dx_h = torch.empty((2, n), dtype=torch.float64).pin_memory()
+    cur = torch.cuda.current_stream(dev)
+    e2e_t = []
+    for _ in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.no_grad():
+            S.copy_(S_h, non_blocking=True)
+            Q.copy_(Q_h, non_blocking=True)
+        step()
+        dq_h.copy_(Q.grad, non_blocking=True)
+        dx_h.copy_(S.grad, non_blocking=True)
+        cur.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(dist, statistics.median(e2e_t[1:]), dev)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu and args.scale == 1.0:
+        try:
+            ot = oracle_time(args.workload)
+            cpu = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
+            cpu["sample"] += "; one oracle evaluation (potential + gradient) gives dE/dq and dE/dx"
+        except Exception as e:  # reported, not fatal
+            cpu = {"error": str(e)[:200]}
     line = {"metric": METRIC, "value": world * 2 * n / (ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
-            "config": {"workload": args.workload, "kernel": "laplace", "n": n, "step": "forward + backward (dE/dq, dE/dx)",
-                       "l2": "flushed (256 MiB write) before each timed step"},
-            "roofline": None, "cpu_baseline": None, "clocks": clocks, "gpu_launches": None}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+            "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
+                       "kernel": "laplace", "n": n, "step": "forward + backward (dE/dq, dE/dx)",
+                       "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
+            "roofline": p2p_roofline("laplace", 1, True, desc["npairs"], p2p_ms, ms,
+                                     "k_p2p_mixed (near-image P2P of the adjoint execute)"),
+            "cpu_baseline": cpu, "clocks": clocks,
+            "e2e": {"value": world * 2 * n / e2e_s, "unit": "targets+sources/s",
+                    "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8,
+                    "d2h_bytes_per_step": dq_h.numel() * 8 + dx_h.numel() * 8,
+                    "api": "periodic() autograd forward + backward with pinned host copies in the timed region"},
+            "gpu_launches": None}
+    # forward + adjoint executes per step (the adjoint adds one contraction kernel)
+    line["gpu_launches"] = args.steps * (2 * nl[-1] + 1)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
     return 0
 
 
@@ -431,14 +631,8 @@ def main():
         return 0
     # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
     p2p = sum(p2p_ms) / len(p2p_ms)
-    npairs = desc["npairs"]
-    achieved = npairs / (p2p * 1e-3) / 1e9
-    peak = SMS * (MUFU_PER_CLK_SM / 2.0) * SM_MAX_MHZ * 1e6 / 1e9
-    roof = {"kernel": "k_p2p_mixed (near-image P2P)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "Gpair/s", "frac": achieved / peak,
-            "traffic": traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload),
-            "peak_basis": "MUFU lg2+rcp per pair; measured 28.4 MUFU/clk/SM x 152 SMs x 2070 MHz",
-            "launch_ms": p2p, "share_of_step": p2p / ms}
+    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, "k_p2p_mixed (near-image P2P)",
+                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload))
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:

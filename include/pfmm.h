@@ -189,6 +189,16 @@ pfmm_status pfmm_batch_execute(pfmm_batch* batch, void* workspace, size_t ws_byt
                                const double* q, const double* trg, double* pot, double* grad, void* stream);
 /* Synchronise and return the first device status error of any cell (see pfmm_get_status). */
 pfmm_status pfmm_batch_get_status(pfmm_batch* batch, void* workspace, void* stream);
+/* Phase timing of batch executes with CUDA events (library tracing, not in
+ * the paper).  While enabled, each execute that is not being captured into a
+ * graph records three events on its stream.  pfmm_batch_profile_read waits
+ * for them and writes ms[0] = the per-cell phases (preparation and far field
+ * of every cell), ms[1] = the batched near-image P2P (n >= 2), and
+ * *nlaunch (may be NULL) = kernels launched by the last execute.
+ * Errors: PFMM_ERR_INVALID_ARG (NULL batch, n < 2, no timed execute yet),
+ * PFMM_ERR_CUDA. */
+pfmm_status pfmm_batch_profile_enable(pfmm_batch* batch, int on);
+pfmm_status pfmm_batch_profile_read(pfmm_batch* batch, float* ms, int n, int* nlaunch);
 void pfmm_batch_destroy(pfmm_batch* batch);
 
 /* The same operation as pfmm_execute for callers that cannot allocate device

@@ -24,7 +24,7 @@ EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host"
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
            "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static",
            "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
-           "pfmm_batch_destroy", "pfmm_execute_adjoint"]
+           "pfmm_batch_destroy", "pfmm_batch_profile_enable", "pfmm_batch_profile_read", "pfmm_execute_adjoint"]
 
 
 class Opts(ctypes.Structure):
@@ -82,6 +82,10 @@ def lib():
     L.pfmm_batch_execute.restype = ctypes.c_int
     L.pfmm_batch_get_status.argtypes = [vp, vp, vp]
     L.pfmm_batch_get_status.restype = ctypes.c_int
+    L.pfmm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.pfmm_batch_profile_enable.restype = ctypes.c_int
+    L.pfmm_batch_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.pfmm_batch_profile_read.restype = ctypes.c_int
     L.pfmm_batch_destroy.argtypes = [vp]
     L.pfmm_batch_destroy.restype = None
     L.pfmm_execute_adjoint.argtypes = [vp, vp, sz, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]

@@ -39,6 +39,10 @@ struct pfmm_batch {
   std::vector<P2PArgs> hcells;
   const void* last[7] = {};
   int p2p_chunk = 4096;
+  // tracing (pfmm_batch_profile_*)
+  bool prof = false, timed = false;
+  cudaEvent_t ev[3] = {};
+  int nlaunch = 0;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -132,7 +136,35 @@ pfmm_status pfmm_batch_workspace_size(const pfmm_batch* b, size_t* bytes) {
 void pfmm_batch_destroy(pfmm_batch* b) {
   if (!b) return;
   for (auto* p : b->plans) pfmm_plan_destroy(p);
+  if (b->prof)
+    for (auto& e : b->ev) cudaEventDestroy(e);
   delete b;
+}
+
+pfmm_status pfmm_batch_profile_enable(pfmm_batch* b, int on) {
+  if (!b) return set_error(PFMM_ERR_INVALID_ARG, "NULL batch");
+  if (on && !b->prof) {
+    for (auto& e : b->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "cudaEventCreate failed");
+    b->prof = true;
+    b->timed = false;
+  } else if (!on && b->prof) {
+    for (auto& e : b->ev) cudaEventDestroy(e);
+    b->prof = false;
+    b->timed = false;
+  }
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_batch_profile_read(pfmm_batch* b, float* ms, int n, int* nlaunch) {
+  if (!b || !ms || n < 2) return set_error(PFMM_ERR_INVALID_ARG, "NULL batch or output, or n < 2");
+  if (!b->prof || !b->timed) return set_error(PFMM_ERR_INVALID_ARG, "no profiled batch execute yet");
+  if (cudaEventSynchronize(b->ev[2]) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event synchronize failed");
+  if (cudaEventElapsedTime(ms, b->ev[0], b->ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(ms + 1, b->ev[1], b->ev[2]) != cudaSuccess)
+    return set_error(PFMM_ERR_CUDA, "cudaEventElapsedTime failed");
+  if (nlaunch) *nlaunch = b->nlaunch;
+  return PFMM_OK;
 }
 
 pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, const double* src, const double* q,
@@ -176,13 +208,19 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   }
   e = cudaMemsetAsync(ws + b->off_counter, 0, 256, st);
   if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool rec = b->prof && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+  if (rec) cudaEventRecord(b->ev[0], st);
+  b->nlaunch = 0;
   for (int c = 0; c < b->ncell; ++c) {
     int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
     pfmm_status s = execute_cell(b->plans[c], ws + b->wsoff[c], ns, src + b->soff[c], q + b->soff[c], nt,
                                  tr + b->toff[c], pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, st, b->self,
                                  false, !mixed);
     if (s != PFMM_OK) return s;
+    b->nlaunch += b->plans[c]->nlaunch;
   }
+  if (rec) cudaEventRecord(b->ev[1], st);
   if (mixed) {
     int gi = 0;
     for (auto& g : b->groups) {
@@ -191,7 +229,12 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
                            g.grid, st);
       if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "batched p2p: %s", cudaGetErrorString(e));
       ++gi;
+      ++b->nlaunch;
     }
+  }
+  if (rec) {
+    cudaEventRecord(b->ev[2], st);
+    b->timed = true;
   }
   return PFMM_OK;
 }

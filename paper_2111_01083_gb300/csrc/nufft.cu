@@ -382,6 +382,20 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
   }
 }
 
+// Raise a kernel's dynamic shared-memory limit once per device and size, so
+// that executes after the first (including ones captured in a CUDA graph)
+// make no attribute calls.
+static cudaError_t raise_smem(const void* fn, int slot, size_t bytes) {
+  static int done[32][4] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  const bool cached = dev >= 0 && dev < 32;
+  if (cached && done[dev][slot] >= (int)bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess && cached) done[dev][slot] = (int)bytes;
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 template <typename T>
 static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
@@ -434,7 +448,7 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   const int use_smem = sm_spread <= 96 * 1024;
   if (!use_smem) sm_spread = 0;
   if (sm_spread > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_nufft_spread<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_spread);
+    e = raise_smem((const void*)k_nufft_spread<T>, sizeof(T) == 4 ? 0 : 1, sm_spread);
     if (e != cudaSuccess) return e;
   }
   const int* sU = (const int*)(ws + L.srcU);
@@ -442,9 +456,8 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   const int fth = std::min(512, std::max(32, a.nf / 2));
   const size_t sm_fft = (size_t)a.nf * sizeof(double2);
   if (sm_fft > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_nufft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_nufft_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_fft);
+    e = raise_smem((const void*)k_nufft_fwd, 2, sm_fft);
+    if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 3, sm_fft);
     if (e != cudaSuccess) return e;
   }
   k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);

@@ -239,6 +239,19 @@ class BatchOp:
         st = stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
         _lib.check(_lib.lib().pfmm_batch_get_status(self._h, _ptr(ws), ctypes.c_void_p(st)))
 
+    def profile(self, on=True):
+        """Record CUDA events around the per-cell phases and the batched P2P
+        of every execute not captured in a graph (pfmm_batch_profile_enable)."""
+        _lib.check(_lib.lib().pfmm_batch_profile_enable(self._h, int(bool(on))))
+
+    def phase_ms(self):
+        """(per-cell phases ms, batched P2P ms, kernels launched) of the last
+        profiled execute; waits for its events."""
+        ms = (ctypes.c_float * 2)()
+        n = ctypes.c_int()
+        _lib.check(_lib.lib().pfmm_batch_profile_read(self._h, ms, 2, ctypes.byref(n)))
+        return float(ms[0]), float(ms[1]), int(n.value)
+
     def capture(self, src, q, trg=None, out=None, grad=True):
         """Record one execute in a CUDA graph (after a first execute on the same
         buffers, which uploads the descriptors).  Returns (graph, out)."""
