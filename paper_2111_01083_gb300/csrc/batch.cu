@@ -37,6 +37,11 @@ struct pfmm_batch {
   std::vector<Group> groups;
   std::vector<P2PItem> items;
   std::vector<P2PArgs> hcells;
+  // mixed path: spatial sort of every cell's sources (and modified Helmholtz
+  // targets) in one radix sort over the concatenated slots
+  std::vector<SortCell> hsort;
+  int64_t sort_total = 0;
+  size_t off_sort = 0, off_sortscr = 0;
   const void* last[7] = {};
   int p2p_chunk = 4096;
   // tracing (pfmm_batch_profile_*)
@@ -65,6 +70,7 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
   if (src_off[0] != 0 || (trg_off && trg_off[0] != 0)) return set_error(PFMM_ERR_INVALID_ARG, "offsets start at 0");
   if (p2p_chunk != 0 && (p2p_chunk < 128 || p2p_chunk % 128))
     return set_error(PFMM_ERR_INVALID_ARG, "p2p_chunk must be 0 or a positive multiple of 128");
+  if (ncell > 32768) return set_error(PFMM_ERR_INVALID_ARG, "at most 32768 cells per batch");
   pfmm_batch* b = new pfmm_batch();
   b->ncell = ncell;
   b->kernel = c0.kernel;
@@ -114,6 +120,15 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
     for (auto& e : v) b->items.push_back(e.second);
     g.n = (int)v.size();
     if (g.n > 0) b->groups.push_back(g);
+  }
+  if (b->precision == PFMM_MIXED) {
+    const bool sort_t = !b->self;
+    b->hsort.resize((size_t)ncell * (sort_t ? 2 : 1));
+    b->sort_total = b->NS + (sort_t ? b->NT : 0);
+    b->off_sort = off;
+    off = al256(off + sizeof(SortCell) * b->hsort.size());
+    b->off_sortscr = off;
+    off = al256(off + sort_scratch_bytes(b->sort_total, (int)b->hsort.size()));
   }
   b->off_cells = off;
   off = al256(off + sizeof(P2PArgs) * ncell);
@@ -188,7 +203,7 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   }
   const void* cur[7] = {workspace, src, q, tr, pot, grad, (const void*)(uintptr_t)b->p2p_chunk};
   const bool upload = std::memcmp(cur, b->last, sizeof cur) != 0;
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (upload) {
     for (int c = 0; c < b->ncell; ++c) {
       pfmm_plan* p = b->plans[c];
@@ -197,7 +212,17 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
       if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload tables: %s", cudaGetErrorString(e));
       int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
       fill_p2p_args(p, wc, ns, nt, b->self, pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, &b->hcells[c]);
+      if (mixed) {
+        SortCell two[2];
+        const int k = fill_sort_cells(p, wc, ns, nt, b->self, b->soff[c], b->NS + b->toff[c], two);
+        b->hsort[c] = two[0];
+        if (k > 1) b->hsort[b->ncell + c] = two[1];
+      }
     }
+    if (mixed)
+      e = cudaMemcpyAsync(ws + b->off_sort, b->hsort.data(), sizeof(SortCell) * b->hsort.size(),
+                          cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload sort descriptors: %s", cudaGetErrorString(e));
     e = cudaMemcpyAsync(ws + b->off_cells, b->hcells.data(), sizeof(P2PArgs) * b->ncell, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !b->items.empty())
       e = cudaMemcpyAsync(ws + b->off_items, b->items.data(), sizeof(P2PItem) * b->items.size(),
@@ -222,6 +247,11 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   }
   if (rec) cudaEventRecord(b->ev[1], st);
   if (mixed) {
+    int nl = 0;
+    e = sort_cells((const SortCell*)(ws + b->off_sort), b->hsort.data(), (int)b->hsort.size(), b->sort_total,
+                   ws + b->off_sortscr, st, &nl);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "spatial sort: %s", cudaGetErrorString(e));
+    b->nlaunch += nl;
     int gi = 0;
     for (auto& g : b->groups) {
       e = launch_p2p_batch(b->kernel, g.nimg, g.nr, grad != nullptr, (const P2PArgs*)(ws + b->off_cells),

@@ -41,6 +41,57 @@ __device__ __forceinline__ float k0f(float x) {
   return __expf(-x) * rsqrtf(x) * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
 }
 
+// FP32 from x^2 (x = beta r), no division, MUFU approximations: the same
+// A&S 9.8 fits written in x^2 so that the small-argument branch needs no
+// square root and the large-argument branch gets 1/x, x and x^-1/2 from two
+// rsqrt: ix = rsqrt(x^2), x = x^2 ix, rx = rsqrt(x).
+namespace mufu {
+__device__ __forceinline__ float rsqrt(float x) { float r; asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float rcp(float x) { float r; asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float ex2(float x) { float r; asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+__device__ __forceinline__ float lg2(float x) { float r; asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x)); return r; }
+}  // namespace mufu
+
+__device__ __forceinline__ float k0f_x2(float x2) {
+  if (x2 <= 4.0f) {
+    const float t2 = x2 * (1.0f / 14.0625f);  // (x / 3.75)^2
+    const float i0 = 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f + t2 * (0.0360768f + t2 * 0.0045813f)))));
+    const float y = 0.25f * x2;
+    const float lg = 0.34657359027997264f * mufu::lg2(y);  // ln(x / 2) = (ln 2 / 2) log2(x^2 / 4)
+    return -lg * i0 + (-0.57721566f + y * (0.42278420f + y * (0.23069756f + y * (0.03488590f + y * (0.00262698f + y * (0.00010750f + y * 0.0000074f))))));
+  }
+  const float ix = mufu::rsqrt(x2);
+  const float x = x2 * ix;
+  const float rx = mufu::rsqrt(x);
+  const float e = mufu::ex2(-1.4426950408889634f * x);
+  const float y = 2.0f * ix;
+  return e * rx * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+}
+
+// K0(x) and K1(x) / x from x^2.
+__device__ __forceinline__ void k01f_x2(float x2, float* k0, float* k1ix) {
+  if (x2 <= 4.0f) {
+    const float t2 = x2 * (1.0f / 14.0625f);
+    const float i0 = 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f + t2 * (0.0360768f + t2 * 0.0045813f)))));
+    // I1(x) = x p1(t2)
+    const float p1 = 0.5f + t2 * (0.87890594f + t2 * (0.51498869f + t2 * (0.15084934f + t2 * (0.02658733f + t2 * (0.00301532f + t2 * 0.00032411f)))));
+    const float y = 0.25f * x2;
+    const float lg = 0.34657359027997264f * mufu::lg2(y);
+    *k0 = -lg * i0 + (-0.57721566f + y * (0.42278420f + y * (0.23069756f + y * (0.03488590f + y * (0.00262698f + y * (0.00010750f + y * 0.0000074f))))));
+    // K1(x) = (x^2 ln(x/2) p1 + q1(y)) / x  ->  K1 / x = ln(x/2) p1 + q1(y) / x^2
+    const float q1 = 1.0f + y * (0.15443144f + y * (-0.67278579f + y * (-0.18156897f + y * (-0.01919402f + y * (-0.00110404f + y * (-0.00004686f))))));
+    *k1ix = lg * p1 + q1 * mufu::rcp(x2);
+    return;
+  }
+  const float ix = mufu::rsqrt(x2);
+  const float x = x2 * ix;
+  const float rx = mufu::rsqrt(x);
+  const float e = mufu::ex2(-1.4426950408889634f * x) * rx;
+  const float y = 2.0f * ix;
+  *k0 = e * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+  *k1ix = e * ix * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
+}
+
 // FP64.  x <= 2: the ascending series (DLMF 10.31.1-10.31.2),
 //   K0 = -(ln(x/2) + gamma) I0(x) + sum_{k>=1} H_k (x^2/4)^k / (k!)^2,
 //   K1 = 1/x + ln(x/2) I1(x) - (x/4) sum_{k>=0} (psi(k+1) + psi(k+2)) (x^2/4)^k / (k! (k+1)!).

@@ -1,7 +1,7 @@
 // Point preparation and the direct far-field path (Sec. 6: P q = L (D (R q))).
 //
 //   k_prep_points : wrap + rotate points into the canonical cell (Sec. 1),
-//                   FP64 and FP32 copies, fixed-point x/d phase, hi/lo split
+//                   FP64 and FP32 copies, fixed-point x/d phase
 //   k_prep_q      : strengths in the canonical frame, FP64 compatibility
 //                   moments sum q, sum |q|, sum q y' (Eq. chargeneutral,
 //                   Eq. phis2 / Eq. pss0)
@@ -23,7 +23,7 @@ namespace pfmm {
 // K0: points
 // ----------------------------------------------------------------------------
 __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* __restrict__ pts, double* __restrict__ c64,
-                              float* __restrict__ cf, int* __restrict__ U, float4* __restrict__ hl,
+                              float* __restrict__ cf, int* __restrict__ U,
                               int* __restrict__ status) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -46,10 +46,6 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   double v = xc / g.d;
   v -= floor(v + 0.5);
   U[i] = (int)(unsigned)(long long)llrint(v * 4294967296.0);
-  if (hl) {
-    float xh = (float)xc, yh = (float)yc;
-    hl[i] = make_float4(xh, (float)(xc - (double)xh), yh, (float)(yc - (double)yh));
-  }
 }
 
 // Optional projection to zero net charge / force: net sums per rhs and
@@ -479,11 +475,11 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   int* status = (int*)(ws + L.status);
   bool mixed = p->opts.precision == PFMM_MIXED;
   k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
-                                                 (int*)(ws + L.srcU), mixed ? (float4*)(ws + L.srchl) : nullptr,
+                                                 (int*)(ws + L.srcU),
                                                  status);
   if (!self && nt > 0)
     k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
-                                                   (int*)(ws + L.trgU), nullptr, status);
+                                                   (int*)(ws + L.trgU), status);
   g_launches = (!self && nt > 0) ? 3 : 2;
   const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) && p->opts.kernel != PFMM_MODHELM;
   if (project) {

@@ -19,6 +19,7 @@
 #include <cmath>
 #include "pfmm_impl.h"
 #include "p2p.h"
+#include "sort.h"
 #include "bessel.cuh"
 
 namespace pfmm {
@@ -112,6 +113,13 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 #endif
 
+// Hi/lo coordinates of the padding source at slot k of a tile: its subtile
+// centre (so that the exact and the relative paths see the same point).
+__device__ __forceinline__ float4 s_c_src(const P2PArgs& a, int jb, int k, int nb) {
+  const int sub = k / kSubtile;
+  return (sub * kSubtile < nb) ? a.s_sub[jb / kSubtile + sub] : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 struct Kahan2 {
   float2 s, c;
   __device__ __forceinline__ void add(float2 v) {
@@ -123,14 +131,27 @@ struct Kahan2 {
 };
 
 // Body of the Laplace/Stokes mixed kernel for one work item: target block bx
-// (2 * kP2PThreads targets), sources [j0, j1), rhs r0 .. r0 + NR - 1.
+// (2 * kP2PThreads sorted targets), sorted sources [j0, j1), rhs r0 .. r0 + NR - 1.
+//
+// Coordinate differences.  Sources come in subtiles of 16 with a common centre
+// c; per (target, image, subtile) the target minus image minus centre is
+// formed once from its hi/lo parts, and per source one FP32 subtraction gives
+// dx.  Its absolute error is a few ulp of the subtile extent h, so where a
+// target lies within about h of the subtile (the expanded-box test below,
+// rarely true since targets and sources are sorted) that subtile instead takes
+// the exact path dx = (t_hi - s_hi) + (t_lo - s_lo).  Elsewhere r >= h and the
+// relative error of dx stays near 1e-7.
 template <int KER, int NIMG, int NR, bool GRAD>
 __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   static_assert(KER != PFMM_MODHELM, "packed kernel is for Laplace/Stokes");
   constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
   constexpr int CENTER = NIMG / 2;
   constexpr int NA = (KER == PFMM_STOKES) ? 2 : (GRAD ? 3 : 1);
-  __shared__ float4 s_p[kP2PTile];
+  constexpr int NSUB = kP2PTile / kSubtile;
+  __shared__ float2 s_p[kP2PTile];
+  __shared__ float4 s_h[kP2PTile];
+  __shared__ float4 s_c[NSUB];
+  __shared__ float2 s_e[NSUB];
   __shared__ float s_q[NR * NC][kP2PTile];
 
   const int l0 = (bx * kP2PThreads + threadIdx.x) * 2;
@@ -166,73 +187,115 @@ __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0,
     }
   constexpr float kStokesC = -2.0f / 0.69314718055994531f;  // -(1/4pi) / (ln2/8pi)
 
+  // image sums of one source (dx, dy per image from `diff`), then one FMA per rhs
+  auto source = [&](int jj, auto diff) {
+    float2 P = f2(1.f), G1 = f2(0.f), G2 = f2(0.f), cnt = f2((float)NIMG);
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      float2 dx, dy;
+      diff(i, dx, dy);
+      float2 r2 = fma2(dx, dx, mul2(dy, dy));
+      float2 msk = f2(1.0f);
+      if (i == CENTER) {
+        msk = make_float2(r2.x > 0.f ? 1.f : 0.f, r2.y > 0.f ? 1.f : 0.f);
+        r2 = make_float2(r2.x > 0.f ? r2.x : 1.f, r2.y > 0.f ? r2.y : 1.f);
+        cnt = add2(cnt, add2(msk, f2(-1.0f)));
+      }
+      float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
+      if (i == CENTER) inv = mul2(inv, msk);
+      P = mul2(P, mul2(r2, f2(kimg[i])));
+      if (KER == PFMM_LAPLACE) {
+        if (GRAD) {
+          G1 = fma2(dx, inv, G1);
+          G2 = fma2(dy, inv, G2);
+        }
+      } else {
+        // G1 = sum (dx^2 - dy^2)/r^2 (= sum cos 2theta, centred), G2 = sum dx dy / r^2
+        const float2 dx2 = mul2(dx, dx);
+        const float2 t = fma2(make_float2(-dy.x, -dy.y), dy, dx2);
+        G1 = fma2(t, inv, G1);
+        G2 = fma2(mul2(dx, inv), dy, G2);
+      }
+    }
+    const float2 L = make_float2(lg2_approx(P.x), lg2_approx(P.y));
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      if (KER == PFMM_LAPLACE) {
+        const float2 q = f2(s_q[r][jj]);
+        S[r][0] = fma2(q, L, S[r][0]);
+        if (GRAD) {
+          S[r][1 % NA] = fma2(q, G1, S[r][1 % NA]);
+          S[r][2 % NA] = fma2(q, G2, S[r][2 % NA]);
+        }
+      } else {
+        // Axx = (cnt + G1)/2, Ayy = (cnt - G1)/2; the isotropic part C nimg/2 is
+        // moved into the FP64 add-back:  u_x += fx (Lx + C G1/2) + fy C G2,
+        // u_y += fx C G2 + fy (Lx - C G1/2),  Lx = L + C (cnt - nimg)/2
+        const float2 fx = f2(s_q[r * NC][jj]), fy = f2(s_q[r * NC + NC - 1][jj]);
+        const float2 Lx = fma2(add2(cnt, f2(-(float)NIMG)), f2(0.5f * kStokesC), L);
+        const float2 h1 = mul2(G1, f2(0.5f * kStokesC)), cxy = mul2(G2, f2(kStokesC));
+        S[r][0] = fma2(fx, add2(Lx, h1), fma2(fy, cxy, S[r][0]));
+        S[r][NA - 1] = fma2(fx, cxy, fma2(fy, add2(Lx, make_float2(-h1.x, -h1.y)), S[r][NA - 1]));
+      }
+    }
+  };
+
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
     for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
-      // padding: a zero-strength source at the origin (finite r^2 in every image;
-      // a zero distance can only occur in the centre image, which is masked)
-      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // padding: a zero-strength source at its subtile centre (inside the cell:
+      // finite r^2 in every image; a zero distance can only occur in the centre
+      // image, which is masked)
+      const bool v = k < nb;
+      s_p[k] = v ? a.s_rel[jb + k] : make_float2(0.f, 0.f);
+      s_h[k] = v ? a.s_hl[jb + k] : s_c_src(a, jb, k, nb);
+      if (k < NSUB) {
+        s_c[k] = (k * kSubtile < nb) ? a.s_sub[jb / kSubtile + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s_e[k] = (k * kSubtile < nb) ? a.s_ext[jb / kSubtile + k] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
       for (int r = 0; r < NR; ++r)
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          s_q[r * NC + c][k] = (k < nb && r < nr) ? a.qf[((size_t)(r0 + r) * NC + c) * a.ns + jb + k] : 0.f;
+        for (int c2 = 0; c2 < NC; ++c2)
+          s_q[r * NC + c2][k] = (v && r < nr) ? a.qs[((size_t)(r0 + r) * NC + c2) * a.ns + jb + k] : 0.f;
     }
     __syncthreads();
     for (int js = 0; js < nb; js += kP2PSub) {
-#pragma unroll kP2PUnroll
-      for (int jj = js; jj < js + kP2PSub; ++jj) {
-        const float4 p = s_p[jj];
-        const float2 nsxh = f2(-p.x), nsxl = f2(-p.y), nsyh = f2(-p.z), nsyl = f2(-p.w);
-        float2 P = f2(1.f), G1 = f2(0.f), G2 = f2(0.f), cnt = f2((float)NIMG);
+      // target minus image minus subtile centre, from the hi/lo parts
+      float2 txr[NIMG], tyr[NIMG];
+      bool near = false;
+      {
+        const float4 c = s_c[js / kSubtile];
+        const float2 e = s_e[js / kSubtile];
+        const float bxe = 2.f * e.x + e.y, bye = e.x + 2.f * e.y;  // expanded half extents
+        const float2 nch = f2(-c.x), ncl = f2(-c.y), nyh = f2(-c.z), nyl = f2(-c.w);
 #pragma unroll
         for (int i = 0; i < NIMG; ++i) {
-          const float2 dx = add2(add2(thx[i], nsxh), add2(tlx[i], nsxl));
-          const float2 dy = add2(add2(thy[i], nsyh), add2(tly[i], nsyl));
-          float2 r2 = fma2(dx, dx, mul2(dy, dy));
-          float2 msk = f2(1.0f);
-          if (i == CENTER) {
-            msk = make_float2(r2.x > 0.f ? 1.f : 0.f, r2.y > 0.f ? 1.f : 0.f);
-            r2 = make_float2(r2.x > 0.f ? r2.x : 1.f, r2.y > 0.f ? r2.y : 1.f);
-            cnt = add2(cnt, add2(msk, f2(-1.0f)));
-          }
-          float2 inv = make_float2(rcp_approx(r2.x), rcp_approx(r2.y));
-          if (i == CENTER) inv = mul2(inv, msk);
-          P = mul2(P, mul2(r2, f2(kimg[i])));
-          if (KER == PFMM_LAPLACE) {
-            if (GRAD) {
-              G1 = fma2(dx, inv, G1);
-              G2 = fma2(dy, inv, G2);
-            }
-          } else {
-            // G1 = sum (dx^2 - dy^2)/r^2 (= sum cos 2theta, centred), G2 = sum dx dy / r^2
-            const float2 dx2 = mul2(dx, dx);
-            const float2 t = fma2(make_float2(-dy.x, -dy.y), dy, dx2);
-            G1 = fma2(t, inv, G1);
-            G2 = fma2(mul2(dx, inv), dy, G2);
-          }
+          txr[i] = add2(add2(thx[i], nch), add2(tlx[i], ncl));
+          tyr[i] = add2(add2(thy[i], nyh), add2(tly[i], nyl));
+          near |= (fabsf(txr[i].x) < bxe && fabsf(tyr[i].x) < bye) || (fabsf(txr[i].y) < bxe && fabsf(tyr[i].y) < bye);
         }
-        const float2 L = make_float2(lg2_approx(P.x), lg2_approx(P.y));
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          if (KER == PFMM_LAPLACE) {
-            const float2 q = f2(s_q[r][jj]);
-            S[r][0] = fma2(q, L, S[r][0]);
-            if (GRAD) {
-              S[r][1 % NA] = fma2(q, G1, S[r][1 % NA]);
-              S[r][2 % NA] = fma2(q, G2, S[r][2 % NA]);
-            }
-          } else {
-            // Axx = (cnt + G1)/2, Ayy = (cnt - G1)/2; the isotropic part C nimg/2 is
-            // moved into the FP64 add-back:  u_x += fx (Lx + C G1/2) + fy C G2,
-            // u_y += fx C G2 + fy (Lx - C G1/2),  Lx = L + C (cnt - nimg)/2
-            const float2 fx = f2(s_q[r * NC][jj]), fy = f2(s_q[r * NC + NC - 1][jj]);
-            const float2 Lx = fma2(add2(cnt, f2(-(float)NIMG)), f2(0.5f * kStokesC), L);
-            const float2 h1 = mul2(G1, f2(0.5f * kStokesC)), cxy = mul2(G2, f2(kStokesC));
-            S[r][0] = fma2(fx, add2(Lx, h1), fma2(fy, cxy, S[r][0]));
-            S[r][NA - 1] = fma2(fx, cxy, fma2(fy, add2(Lx, make_float2(-h1.x, -h1.y)), S[r][NA - 1]));
-          }
+      }
+      if (near) {
+#pragma unroll 1
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float4 h = s_h[jj];
+          const float2 nxh = f2(-h.x), nxl = f2(-h.y), nyh = f2(-h.z), nyl = f2(-h.w);
+          source(jj, [&](int i, float2& dx, float2& dy) {
+            dx = add2(add2(thx[i], nxh), add2(tlx[i], nxl));
+            dy = add2(add2(thy[i], nyh), add2(tly[i], nyl));
+          });
+        }
+      } else {
+#pragma unroll kP2PUnroll
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float2 p = s_p[jj];
+          const float2 nsx = f2(-p.x), nsy = f2(-p.y);
+          source(jj, [&](int i, float2& dx, float2& dy) {
+            dx = add2(txr[i], nsx);
+            dy = add2(tyr[i], nsy);
+          });
         }
       }
 #pragma unroll
@@ -250,7 +313,7 @@ __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0,
   for (int h = 0; h < 2; ++h) {
     const bool in = h == 0 ? inA : inB;
     if (!in) continue;
-    const int l = l0 + h;
+    const int l = a.t_perm ? a.t_perm[l0 + h] : l0 + h;
     for (int r = 0; r < nr; ++r) {
       auto val = [&](int k) {
         const float2 s2 = K[r][k].s, c2 = K[r][k].c;
@@ -288,14 +351,23 @@ __global__ void __launch_bounds__(kP2PThreads, PFMM_P2P_MINB) k_p2p_mixed(const 
   p2p_mixed_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
 }
 
-// Modified Helmholtz mixed kernel: one target per thread, per-source image
-// sums K0s = sum_i K0(beta r_i), K1x = sum_i K1(beta r_i) dx_i / r_i (and y).
+// Modified Helmholtz mixed kernel: one target per thread, targets and sources
+// in spatially sorted order, per-source image sums K0s = sum_i K0(beta r_i),
+// K1x = sum_i K1(beta r_i) dx_i / r_i (and y).  K0(x) < 1e-22 for x > 50: a
+// (target block, source tile, image) triple whose boxes are farther apart
+// than 50 / beta is skipped as a whole (the test is exact in FP64 on FP32
+// boxes rounded outward), and single pairs beyond the cutoff are skipped too.
 template <int KER, int NIMG, int NR, bool GRAD>
 __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   constexpr int CENTER = NIMG / 2;
   constexpr int NA = GRAD ? 3 : 1;
-  __shared__ float4 s_p[kP2PTile];
+  constexpr int NSUB = kP2PTile / kSubtile;
+  __shared__ float2 s_p[kP2PTile];
+  __shared__ float4 s_h[kP2PTile];
+  __shared__ float4 s_c[NSUB];
+  __shared__ float2 s_e[NSUB];
   __shared__ float s_q[NR][kP2PTile];
+  __shared__ unsigned s_mask;
   const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
@@ -321,55 +393,113 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
       S[r][k] = 0.f;
     }
   const float beta = a.beta_f;
+  const float beta2 = beta * beta;
   const float cut2 = (50.0f / beta) * (50.0f / beta);
+  const float4 tb = a.t_box ? a.t_box[bx] : make_float4(0.f, 0.f, 1e30f, 1e30f);
+
+  // image sums of one source over the images in `mask`, then one FMA per rhs
+  auto source = [&](int jj, unsigned mask, auto diff) {
+    float K0s = 0.f, K1x = 0.f, K1y = 0.f;
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      if (!(mask & (1u << i))) continue;
+      float dx, dy;
+      diff(i, dx, dy);
+      float r2 = fmaf(dx, dx, dy * dy);
+      float msk = 1.0f;
+      if (i == CENTER) {
+        msk = (r2 > 0.0f) ? 1.0f : 0.0f;
+        r2 = (r2 > 0.0f) ? r2 : 1.0f;
+      }
+      // K0(beta r) < 1e-22 for beta r > 50: such pairs are skipped (the
+      // branch is not taken at all when no lane of the warp needs it)
+      if (r2 < cut2) {
+        const float x2 = beta2 * r2;
+        if (GRAD) {
+          float k0, k1ix;
+          bes::k01f_x2(x2, &k0, &k1ix);  // k1ix = K1(x) / x
+          K0s = fmaf(k0, msk, K0s);
+          const float k1r = k1ix * beta * msk;  // K1(beta r) / r = beta K1(x) / x
+          K1x = fmaf(k1r, dx, K1x);
+          K1y = fmaf(k1r, dy, K1y);
+        } else {
+          K0s = fmaf(bes::k0f_x2(x2), msk, K0s);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const float q = s_q[r][jj];
+      S[r][0] = fmaf(q, K0s, S[r][0]);
+      if (GRAD) {
+        S[r][1 % NA] = fmaf(q, K1x, S[r][1 % NA]);
+        S[r][2 % NA] = fmaf(q, K1y, S[r][2 % NA]);
+      }
+    }
+  };
+
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
+    if (threadIdx.x < 32) {
+      // images whose boxes come within the cutoff (FP64 test, one lane per image)
+      bool near = false;
+      if (threadIdx.x < NIMG) {
+        const float4 sb = a.s_box ? a.s_box[jb / kBoxTile] : make_float4(0.f, 0.f, 1e30f, 1e30f);
+        const double ex = fmax(0.0, fabs((double)tb.x - a.g.off[threadIdx.x][0] - (double)sb.x) - (double)tb.z - (double)sb.z);
+        const double ey = fmax(0.0, fabs((double)tb.y - a.g.off[threadIdx.x][1] - (double)sb.y) - (double)tb.w - (double)sb.w);
+        near = ex * ex + ey * ey <= (double)a.cut * (double)a.cut;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, near);
+      if (threadIdx.x == 0) s_mask = m;
+    }
+    __syncthreads();
+    const unsigned mask = s_mask;
+    if (mask == 0u) continue;
     for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
-      s_p[k] = (k < nb) ? a.src_hl[jb + k] : make_float4(1e18f, 0.f, 1e18f, 0.f);
+      // padding: zero strength at the subtile centre (finite distances)
+      const bool v = k < nb;
+      s_p[k] = v ? a.s_rel[jb + k] : make_float2(0.f, 0.f);
+      s_h[k] = v ? a.s_hl[jb + k] : s_c_src(a, jb, k, nb);
+      if (k < NSUB) {
+        s_c[k] = (k * kSubtile < nb) ? a.s_sub[jb / kSubtile + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+        s_e[k] = (k * kSubtile < nb) ? a.s_ext[jb / kSubtile + k] : make_float2(0.f, 0.f);
+      }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) s_q[r][k] = (k < nb && r < nr) ? a.qf[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
+      for (int r = 0; r < NR; ++r) s_q[r][k] = (v && r < nr) ? a.qs[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
     }
     __syncthreads();
     for (int js = 0; js < nb; js += kP2PSub) {
-#pragma unroll 2
-      for (int jj = js; jj < js + kP2PSub; ++jj) {
-        const float4 p = s_p[jj];
-        float K0s = 0.f, K1x = 0.f, K1y = 0.f;
+      float txr[NIMG], tyr[NIMG];
+      bool near = false;
+      {
+        const float4 c = s_c[js / kSubtile];
+        const float2 e = s_e[js / kSubtile];
+        const float bxe = 2.f * e.x + e.y, bye = e.x + 2.f * e.y;
 #pragma unroll
         for (int i = 0; i < NIMG; ++i) {
-          const float dx = (thx[i] - p.x) + (tlx[i] - p.y);
-          const float dy = (thy[i] - p.z) + (tly[i] - p.w);
-          float r2 = fmaf(dx, dx, dy * dy);
-          float msk = 1.0f;
-          if (i == CENTER) {
-            msk = (r2 > 0.0f) ? 1.0f : 0.0f;
-            r2 = (r2 > 0.0f) ? r2 : 1.0f;
-          }
-          // K0(beta r) < 1e-22 for beta r > 50: such pairs are skipped (the
-          // branch is not taken at all when no lane of the warp needs it)
-          if (r2 < cut2) {
-            const float ir = rsqrt_approx(r2);
-            if (GRAD) {
-              float k0, k1;
-              bes::k01f(beta * r2 * ir, &k0, &k1);
-              K0s = fmaf(k0, msk, K0s);
-              const float k1r = k1 * ir * msk;
-              K1x = fmaf(k1r, dx, K1x);
-              K1y = fmaf(k1r, dy, K1y);
-            } else {
-              K0s = fmaf(bes::k0f(beta * r2 * ir), msk, K0s);
-            }
-          }
+          txr[i] = (thx[i] - c.x) + (tlx[i] - c.y);
+          tyr[i] = (thy[i] - c.z) + (tly[i] - c.w);
+          near |= fabsf(txr[i]) < bxe && fabsf(tyr[i]) < bye;
         }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-          const float q = s_q[r][jj];
-          S[r][0] = fmaf(q, K0s, S[r][0]);
-          if (GRAD) {
-            S[r][1 % NA] = fmaf(q, K1x, S[r][1 % NA]);
-            S[r][2 % NA] = fmaf(q, K1y, S[r][2 % NA]);
-          }
+      }
+      if (near) {
+#pragma unroll 1
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float4 h = s_h[jj];
+          source(jj, mask, [&](int i, float& dx, float& dy) {
+            dx = (thx[i] - h.x) + (tlx[i] - h.y);
+            dy = (thy[i] - h.z) + (tly[i] - h.w);
+          });
+        }
+      } else {
+#pragma unroll 2
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float2 p = s_p[jj];
+          source(jj, mask, [&](int i, float& dx, float& dy) {
+            dx = txr[i] - p.x;
+            dy = tyr[i] - p.y;
+          });
         }
       }
 #pragma unroll
@@ -382,14 +512,15 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
     }
   }
   if (!in) return;
+  const int lo = a.t_perm ? a.t_perm[l] : l;
   const double* R = a.g.rot;
   const double cp = 1.0 / (2.0 * M_PI), cg = -a.beta / (2.0 * M_PI);
   for (int r = 0; r < nr; ++r) {
-    if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.os + l, cp * K[r][0].value());
+    if (a.pot) atomicAdd(a.pot + (size_t)(r0 + r) * a.os + lo, cp * K[r][0].value());
     if (GRAD && a.grad) {
       const double gx = cg * K[r][1 % NA].value(), gy = cg * K[r][2 % NA].value();
-      atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * gx + R[2] * gy);
-      atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * gx + R[3] * gy);
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2) * a.os + lo, R[0] * gx + R[2] * gy);
+      atomicAdd(a.grad + ((size_t)(r0 + r) * 2 + 1) * a.os + lo, R[1] * gx + R[3] * gy);
     }
   }
 }
@@ -579,8 +710,19 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
   a.os = p->o_stride;
   a.nrhs = p->opts.nrhs;
   a.trg64 = self ? (const double*)(ws + L.src64) : (const double*)(ws + L.trg64);
-  a.src_hl = (const float4*)(ws + L.srchl);
-  a.qf = (const float*)(ws + L.qf);
+  if (p->opts.precision == PFMM_MIXED) {
+    a.s_rel = (const float2*)(ws + L.s_rel);
+    a.s_hl = (const float4*)(ws + L.s_hl);
+    a.s_sub = (const float4*)(ws + L.s_sub);
+    a.s_ext = (const float2*)(ws + L.s_ext);
+    a.s_box = (const float4*)(ws + L.s_box);
+    a.qs = (const float*)(ws + L.qs);
+    // targets in sorted order too; outputs go back through the permutation
+    a.trg64 = self ? (const double*)(ws + L.s_sorted) : (const double*)(ws + L.t_sorted);
+    a.t_perm = self ? (const int*)(ws + L.s_perm) : (const int*)(ws + L.t_perm);
+    a.t_box = self ? (const float4*)(ws + L.s_box) : (const float4*)(ws + L.t_box);
+  }
+  a.cut = (float)(50.0 / std::max(p->far.beta, 1e-300));
   a.src64 = (const double*)(ws + L.src64);
   a.qc = (const double*)(ws + L.qc);
   a.beta = p->far.beta;
@@ -617,12 +759,54 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
 
 int p2p_targets_per_block(int kernel) { return kP2PThreads * (kernel == PFMM_MODHELM ? 1 : 2); }
 
+int fill_sort_cells(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, int64_t off_s, int64_t off_t,
+                    SortCell* out) {
+  const Layout& L = p->lay;
+  SortCell c{};
+  c.n = (int)ns;
+  c.off = off_s;
+  c.xy = (const double*)(ws + L.src64);
+  sort_grid(p->geom, (int)ns, &c);
+  c.q_in = (const float*)(ws + L.qf);
+  c.nq = p->opts.nrhs * p->ncomp;
+  c.q_out = (float*)(ws + L.qs);
+  c.rel = (float2*)(ws + L.s_rel);
+  c.hl = (float4*)(ws + L.s_hl);
+  c.sub = (float4*)(ws + L.s_sub);
+  c.ext = (float2*)(ws + L.s_ext);
+  c.box = (float4*)(ws + L.s_box);
+  c.perm = (int*)(ws + L.s_perm);
+  c.xy_sorted = self ? (double*)(ws + L.s_sorted) : nullptr;
+  out[0] = c;
+  if (self) return 1;
+  SortCell t{};
+  t.n = (int)nt;
+  t.off = off_t;
+  t.xy = (const double*)(ws + L.trg64);
+  sort_grid(p->geom, (int)nt, &t);
+  t.box = (float4*)(ws + L.t_box);
+  t.perm = (int*)(ws + L.t_perm);
+  t.xy_sorted = (double*)(ws + L.t_sorted);
+  out[1] = t;
+  return 2;
+}
+
 cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
                        bool accumulate, cudaStream_t st) {
   (void)accumulate;
+  const bool mixed = p->opts.precision == PFMM_MIXED;
+  int sort_launches = 0;
+  if (mixed) {
+    // spatial sort of the sources (and modified Helmholtz targets) of this cell
+    const int nc = fill_sort_cells(p, ws, ns, nt, self, 0, ns, p->sort_h);
+    SortCell* dcells = (SortCell*)(ws + p->lay.sortd);
+    cudaError_t e = cudaMemcpyAsync(dcells, p->sort_h, nc * sizeof(SortCell), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = sort_cells(dcells, p->sort_h, nc, ns + (nc > 1 ? nt : 0), ws + p->lay.sortscr, st, &sort_launches);
+    if (e != cudaSuccess) return e;
+  }
   P2PArgs a;
   fill_p2p_args(p, ws, ns, nt, self, pot, grad, &a);
-  const bool mixed = p->opts.precision == PFMM_MIXED;
   const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread
   const int ntb = cdivl(nt, kP2PThreads * (packed ? 2 : 1));
   const int nrg = mixed ? 1 : cdivl(a.nrhs, 4);
@@ -631,7 +815,7 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
   a.chunk = cdivl(cdivl(ns, nsc), kP2PTile) * kP2PTile;
   nsc = cdivl(ns, a.chunk);
   const bool g = grad != nullptr;
-  g_launches = mixed ? 0 : 1;
+  g_launches = (mixed ? 0 : 1) + sort_launches;
   if (mixed) {
     switch (p->opts.kernel) {
       case PFMM_LAPLACE: dispatch_img<PFMM_LAPLACE>(a, g, a.nrhs, ntb, nsc, st); break;

@@ -2,6 +2,7 @@
 // batched launchers).
 #pragma once
 #include "pfmm_impl.h"
+#include "sort.h"
 
 namespace pfmm {
 
@@ -10,9 +11,17 @@ struct P2PArgs {
   int nt, ns, chunk;
   int64_t os;            // output row stride
   int r0, nrhs;          // rhs group start, total rhs
-  const double* trg64;   // [2][nt] canonical
-  const float4* src_hl;  // [ns]
-  const float* qf;       // [nrhs][ncomp][ns]
+  const double* trg64;   // [2][nt] canonical (sorted on the mixed path, see t_perm)
+  const int* t_perm;     // output index of target l (NULL: l itself)
+  const float4* t_box;   // [ceil(nt/128)] boxes of target blocks (modified Helmholtz culling)
+  // mixed kernels: sources in spatially sorted order (sort.h)
+  const float2* s_rel;   // [ns] coordinates relative to the subtile centre
+  const float4* s_hl;    // [ns] (x_hi, x_lo, y_hi, y_lo)
+  const float4* s_sub;   // [ceil(ns/16)] subtile centres (x_hi, x_lo, y_hi, y_lo)
+  const float2* s_ext;   // [ceil(ns/16)] subtile half extents
+  const float4* s_box;   // [ceil(ns/128)] source tile boxes
+  const float* qs;       // [nrhs][ncomp][ns] FP32 strengths in sorted order
+  float cut;             // modified Helmholtz: pairs with beta r > 50 are skipped (cut = 50 / beta)
   const double* src64;   // [2][ns] (FP64 kernel)
   const double* qc;      // [nrhs][ncomp][ns] (FP64 kernel)
   float beta_f;
@@ -41,5 +50,10 @@ cudaError_t launch_p2p_batch(int kernel, int nimg, int nr, bool grad, const P2PA
 int p2p_batch_grid(int kernel, int nimg, int nr, bool grad);
 // Targets per block of the mixed P2P kernels (2 per thread for Laplace/Stokes).
 int p2p_targets_per_block(int kernel);
+// Sort descriptors of one cell (mixed path): sources, and for modified
+// Helmholtz with separate targets also the targets.  off_s / off_t: first
+// slot of each set in the concatenated sort arrays.  Returns 1 or 2.
+int fill_sort_cells(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, int64_t off_s, int64_t off_t,
+                    SortCell* out);
 
 }  // namespace pfmm

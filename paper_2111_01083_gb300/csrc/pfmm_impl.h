@@ -51,7 +51,20 @@ struct Layout {
   size_t src64, trg64;     // double [2][n] canonical coordinates
   size_t srcf, trgf;       // float  [2][n] canonical coordinates (mixed far field)
   size_t srcU, trgU;       // int32 [n] fixed-point x/d phase (mixed south/north)
-  size_t srchl;            // float4 [ns] (x_hi, x_lo, y_hi, y_lo) for P2P (mixed)
+  // mixed P2P: spatially sorted sources (and, for modified Helmholtz, targets)
+  size_t s_rel;            // float2 [ns] coordinates relative to the subtile centre
+  size_t s_hl;             // float4 [ns] sorted (x_hi, x_lo, y_hi, y_lo)
+  size_t s_sub;            // float4 [ceil(ns/16)] subtile centres (hi/lo)
+  size_t s_ext;            // float2 [ceil(ns/16)] subtile half extents
+  size_t s_box;            // float4 [ceil(ns/128)] source tile boxes
+  size_t qs;               // float [nrhs][ncomp][ns] strengths in sorted order
+  size_t s_perm;           // int [ns] input index of sorted source p
+  size_t s_sorted;         // double [2][ns] sorted coordinates (targets = sources)
+  size_t t_sorted;         // double [2][nt] sorted target coordinates (separate targets)
+  size_t t_perm;           // int [nt]
+  size_t t_box;            // float4 [ceil(nt/128)]
+  size_t sortd;            // SortCell [2] device descriptors
+  size_t sortscr;          // radix-sort scratch
   size_t qc;               // strengths in canonical frame: double [nrhs][ncomp][ns]
   size_t qf;               // float copy of qc (mixed P2P and far field)
   size_t coef;             // double2 [nrhs][nch][nterm]
@@ -63,6 +76,10 @@ struct Layout {
 };
 
 }  // namespace pfmm
+
+namespace pfmm {
+struct SortCell;
+}
 
 // pfmm_plan is an opaque C type; its definition is here so that all
 // translation units of the library see the same layout.
@@ -84,6 +101,9 @@ struct pfmm_plan {
   double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
   double* tw_h;             // [nf/2][2] FFT twiddles (cos, sin)(2 pi k / nf), NUFFT path only
   pfmm::Layout lay;
+  // host copies of the sort descriptors of the last execute (sources, targets);
+  // kept in the plan so that the asynchronous upload reads live memory
+  pfmm::SortCell* sort_h;
   // row strides of the caller's arrays for the current execute: sources
   // (src [2][*], q [nrhs][comp][*]), targets (trg [2][*]) and outputs
   // (pot/grad [nrhs][comp][*]); equal to ns / nt for a single cell, to the

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "pfmm_impl.h"
+#include "sort.h"
 
 using namespace pfmm;
 
@@ -264,6 +265,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     }
 
   pfmm_plan* p = new pfmm_plan();
+  p->sort_h = new pfmm::SortCell[2]();
   p->opts = *o;
   p->geom = g;
   p->ns_max = ns_max;
@@ -362,9 +364,28 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   L.trgf = take(2 * nt_max * sizeof(float));
   L.srcU = take(ns_max * sizeof(int));
   L.trgU = take(nt_max * sizeof(int));
-  L.srchl = take(ns_max * 4 * sizeof(float));
   L.qc = take((size_t)nrhs * p->ncomp * ns_max * sizeof(double));
   L.qf = take((size_t)nrhs * p->ncomp * ns_max * sizeof(float));
+  {
+    // sorted-source arrays of the mixed P2P (sort.h)
+    // (targets are sorted as well: with targets = sources they share the order)
+    const bool mixed = o->precision == PFMM_MIXED;
+    const size_t ns_m = mixed ? (size_t)ns_max : 0, nt_m = mixed ? (size_t)nt_max : 0;
+    const size_t nsub = (ns_m + pfmm::kSubtile - 1) / pfmm::kSubtile;
+    L.s_rel = take(ns_m * sizeof(float2));
+    L.s_hl = take(ns_m * sizeof(float4));
+    L.s_sub = take(nsub * sizeof(float4));
+    L.s_ext = take(nsub * sizeof(float2));
+    L.s_box = take((ns_m + pfmm::kBoxTile - 1) / pfmm::kBoxTile * sizeof(float4));
+    L.qs = take((size_t)nrhs * p->ncomp * ns_m * sizeof(float));
+    L.s_perm = take(ns_m * sizeof(int));
+    L.s_sorted = take(ns_m * 2 * sizeof(double));
+    L.t_sorted = take(nt_m * 2 * sizeof(double));
+    L.t_perm = take(nt_m * sizeof(int));
+    L.t_box = take((nt_m + pfmm::kBoxTile - 1) / pfmm::kBoxTile * sizeof(float4));
+    L.sortd = take(2 * sizeof(pfmm::SortCell));
+    L.sortscr = take(mixed ? pfmm::sort_scratch_bytes((int64_t)ns_m + (int64_t)nt_m, 2) : 0);
+  }
   L.coef = take((size_t)nrhs * f.nch * std::max(1, f.nterm) * 2 * sizeof(double));
   L.wts = take((size_t)nrhs * 4 * std::max(1, f.nterm) * 2 * sizeof(double));
   size_t nuf = 0;
@@ -400,6 +421,7 @@ void pfmm_plan_destroy(pfmm_plan* p) {
   std::free(p->gl_h);
   std::free(p->phihat_h);
   std::free(p->tw_h);
+  delete[] p->sort_h;
   delete p;
 }
 
