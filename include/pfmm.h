@@ -193,12 +193,13 @@ pfmm_status pfmm_batch_get_status(pfmm_batch* batch, void* workspace, void* stre
  * the paper).  While enabled, each execute that is not being captured into a
  * graph records three events on its stream.  pfmm_batch_profile_read waits
  * for them and writes ms[0] = the per-cell phases (preparation and far field
- * of every cell), ms[1] = the batched near-image P2P (n >= 2), and
- * *nlaunch (may be NULL) = kernels launched by the last execute.
+ * of every cell), ms[1] = the batched near-image P2P (n >= 2),
+ * *nlaunch (may be NULL) = kernels launched by the last execute and *pairs
+ * (may be NULL) = near-image pairs evaluated (see pfmm_profile_pairs).
  * Errors: PFMM_ERR_INVALID_ARG (NULL batch, n < 2, no timed execute yet),
  * PFMM_ERR_CUDA. */
 pfmm_status pfmm_batch_profile_enable(pfmm_batch* batch, int on);
-pfmm_status pfmm_batch_profile_read(pfmm_batch* batch, float* ms, int n, int* nlaunch);
+pfmm_status pfmm_batch_profile_read(pfmm_batch* batch, float* ms, int n, int* nlaunch, double* pairs);
 void pfmm_batch_destroy(pfmm_batch* batch);
 
 /* The same operation as pfmm_execute for callers that cannot allocate device
@@ -255,6 +256,12 @@ pfmm_status pfmm_get_status(pfmm_plan* plan, void* workspace, void* stream);
  * [2] near-image P2P.  Errors: PFMM_ERR_INVALID_ARG, PFMM_ERR_CUDA. */
 pfmm_status pfmm_profile_enable(pfmm_plan* plan, int on);
 pfmm_status pfmm_profile_read(pfmm_plan* plan, float* ms, int n);
+/* Near-image pairs (target, source, image) the P2P evaluated in the last
+ * profiled execute on `workspace`: ns * nt * images, except for the mixed
+ * modified Helmholtz kernel, which skips (target block, source tile, image)
+ * triples beyond beta r = 50 and counts what it evaluates.  Synchronises
+ * `stream`.  Errors: PFMM_ERR_INVALID_ARG (NULL, profiling off), PFMM_ERR_CUDA. */
+pfmm_status pfmm_profile_pairs(pfmm_plan* plan, const void* workspace, void* stream, double* pairs);
 
 const char* pfmm_last_error(void);
 void pfmm_plan_destroy(pfmm_plan* plan);

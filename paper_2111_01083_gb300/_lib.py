@@ -22,7 +22,7 @@ STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PF
 # Every symbol declared in include/pfmm.h (checked by the CPU test suite).
 EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host", "pfmm_plan_describe",
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
-           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_execute_static",
+           "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_profile_pairs", "pfmm_execute_static",
            "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
            "pfmm_batch_destroy", "pfmm_batch_profile_enable", "pfmm_batch_profile_read", "pfmm_execute_adjoint"]
 
@@ -84,7 +84,8 @@ def lib():
     L.pfmm_batch_get_status.restype = ctypes.c_int
     L.pfmm_batch_profile_enable.argtypes = [vp, ctypes.c_int]
     L.pfmm_batch_profile_enable.restype = ctypes.c_int
-    L.pfmm_batch_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.pfmm_batch_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_double)]
     L.pfmm_batch_profile_read.restype = ctypes.c_int
     L.pfmm_batch_destroy.argtypes = [vp]
     L.pfmm_batch_destroy.restype = None
@@ -100,6 +101,8 @@ def lib():
     L.pfmm_profile_enable.restype = ctypes.c_int
     L.pfmm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     L.pfmm_profile_read.restype = ctypes.c_int
+    L.pfmm_profile_pairs.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    L.pfmm_profile_pairs.restype = ctypes.c_int
     L.pfmm_version.argtypes = []
     L.pfmm_version.restype = ctypes.c_char_p
     _lib = L

@@ -45,7 +45,7 @@ struct pfmm_batch {
   const void* last[7] = {};
   int p2p_chunk = 4096;
   // tracing (pfmm_batch_profile_*)
-  bool prof = false, timed = false;
+  bool prof = false, timed = false, counting = false;
   cudaEvent_t ev[3] = {};
   int nlaunch = 0;
 };
@@ -171,7 +171,7 @@ pfmm_status pfmm_batch_profile_enable(pfmm_batch* b, int on) {
   return PFMM_OK;
 }
 
-pfmm_status pfmm_batch_profile_read(pfmm_batch* b, float* ms, int n, int* nlaunch) {
+pfmm_status pfmm_batch_profile_read(pfmm_batch* b, float* ms, int n, int* nlaunch, double* pairs) {
   if (!b || !ms || n < 2) return set_error(PFMM_ERR_INVALID_ARG, "NULL batch or output, or n < 2");
   if (!b->prof || !b->timed) return set_error(PFMM_ERR_INVALID_ARG, "no profiled batch execute yet");
   if (cudaEventSynchronize(b->ev[2]) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event synchronize failed");
@@ -179,6 +179,24 @@ pfmm_status pfmm_batch_profile_read(pfmm_batch* b, float* ms, int n, int* nlaunc
       cudaEventElapsedTime(ms + 1, b->ev[1], b->ev[2]) != cudaSuccess)
     return set_error(PFMM_ERR_CUDA, "cudaEventElapsedTime failed");
   if (nlaunch) *nlaunch = b->nlaunch;
+  if (pairs) {
+    // sum the per-cell counters (modified Helmholtz mixed), else the nominal count
+    double tot = 0.0;
+    for (int c = 0; c < b->ncell; ++c) {
+      const pfmm_plan* p = b->plans[c];
+      const double ns = (double)(b->soff[c + 1] - b->soff[c]), nt = (double)(b->toff[c + 1] - b->toff[c]);
+      if (b->kernel == PFMM_MODHELM && b->precision == PFMM_MIXED) {
+        unsigned long long w = 0;
+        if (cudaMemcpy(&w, (const char*)b->last[0] + b->wsoff[c] + p->lay.work, sizeof w, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+          return set_error(PFMM_ERR_CUDA, "read pair count");
+        tot += (double)w;
+      } else {
+        tot += ns * nt * p->geom.nimg;
+      }
+    }
+    *pairs = tot;
+  }
   return PFMM_OK;
 }
 
@@ -212,6 +230,7 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
       if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload tables: %s", cudaGetErrorString(e));
       int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
       fill_p2p_args(p, wc, ns, nt, b->self, pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, &b->hcells[c]);
+      set_work_counter(p, wc, b->counting, &b->hcells[c]);
       if (mixed) {
         SortCell two[2];
         const int k = fill_sort_cells(p, wc, ns, nt, b->self, b->soff[c], b->NS + b->toff[c], two);
@@ -235,6 +254,13 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   const bool rec = b->prof && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+  if (mixed && b->kernel == PFMM_MODHELM && rec != b->counting) {
+    // evaluated-pair counters in the P2P descriptors only while profiling
+    for (int c = 0; c < b->ncell; ++c) set_work_counter(b->plans[c], ws + b->wsoff[c], rec, &b->hcells[c]);
+    e = cudaMemcpyAsync(ws + b->off_cells, b->hcells.data(), sizeof(P2PArgs) * b->ncell, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload descriptors: %s", cudaGetErrorString(e));
+    b->counting = rec;
+  }
   if (rec) cudaEventRecord(b->ev[0], st);
   b->nlaunch = 0;
   for (int c = 0; c < b->ncell; ++c) {

@@ -4,6 +4,7 @@
 // the published methods named below.
 #pragma once
 #include <cuda_runtime.h>
+#include "packed.cuh"
 
 namespace pfmm {
 namespace bes {
@@ -91,6 +92,82 @@ __device__ __forceinline__ void k01f_x2(float x2, float* k0, float* k1ix) {
   *k0 = e * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
   *k1ix = e * ix * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
 }
+
+// Packed (two lanes) versions of k0f_x2 / k01f_x2, one branch per formula:
+// a lane pair whose lanes fall on different sides of x = 2 evaluates both
+// formulas and selects per lane.
+namespace pk {
+__device__ __forceinline__ float2 poly6(float2 t, float c0, float c1, float c2, float c3, float c4, float c5, float c6) {
+  float2 p = fma2(t, f2(c6), f2(c5));
+  p = fma2(t, p, f2(c4));
+  p = fma2(t, p, f2(c3));
+  p = fma2(t, p, f2(c2));
+  p = fma2(t, p, f2(c1));
+  return fma2(t, p, f2(c0));
+}
+__device__ __forceinline__ float2 lnhalf(float2 y) {  // ln(x/2) from y = x^2/4
+  return mul2(make_float2(mufu::lg2(y.x), mufu::lg2(y.y)), f2(0.34657359027997264f));
+}
+__device__ __forceinline__ float2 k0_small(float2 x2) {
+  const float2 t2 = mul2(x2, f2(1.0f / 14.0625f));
+  const float2 i0 = poly6(t2, 1.0f, 3.5156229f, 3.0899424f, 1.2067492f, 0.2659732f, 0.0360768f, 0.0045813f);
+  const float2 y = mul2(x2, f2(0.25f));
+  const float2 lg = lnhalf(y);
+  const float2 p = poly6(y, -0.57721566f, 0.42278420f, 0.23069756f, 0.03488590f, 0.00262698f, 0.00010750f, 0.0000074f);
+  return fma2(make_float2(-lg.x, -lg.y), i0, p);
+}
+// e^-x x^-1/2 and 1/x from x^2
+__device__ __forceinline__ void large_common(float2 x2, float2* e, float2* ix) {
+  *ix = make_float2(mufu::rsqrt(x2.x), mufu::rsqrt(x2.y));
+  const float2 x = mul2(x2, *ix);
+  const float2 rx = make_float2(mufu::rsqrt(x.x), mufu::rsqrt(x.y));
+  const float2 a = mul2(x, f2(-1.4426950408889634f));
+  *e = mul2(make_float2(mufu::ex2(a.x), mufu::ex2(a.y)), rx);
+}
+__device__ __forceinline__ float2 k0_large(float2 x2) {
+  float2 e, ix;
+  large_common(x2, &e, &ix);
+  const float2 y = add2(ix, ix);
+  return mul2(e, poly6(y, 1.25331414f, -0.07832358f, 0.02189568f, -0.01062446f, 0.00587872f, -0.00251540f, 0.00053208f));
+}
+__device__ __forceinline__ float2 k0(float2 x2) {
+  const bool sx = x2.x <= 4.0f, sy = x2.y <= 4.0f;
+  if (sx && sy) return k0_small(x2);
+  if (!sx && !sy) return k0_large(x2);
+  const float2 a = k0_small(x2), b = k0_large(x2);
+  return make_float2(sx ? a.x : b.x, sy ? a.y : b.y);
+}
+// K0 and K1/x
+__device__ __forceinline__ void k01_small(float2 x2, float2* k0v, float2* k1ix) {
+  const float2 t2 = mul2(x2, f2(1.0f / 14.0625f));
+  const float2 i0 = poly6(t2, 1.0f, 3.5156229f, 3.0899424f, 1.2067492f, 0.2659732f, 0.0360768f, 0.0045813f);
+  const float2 p1 = poly6(t2, 0.5f, 0.87890594f, 0.51498869f, 0.15084934f, 0.02658733f, 0.00301532f, 0.00032411f);
+  const float2 y = mul2(x2, f2(0.25f));
+  const float2 lg = lnhalf(y);
+  const float2 p = poly6(y, -0.57721566f, 0.42278420f, 0.23069756f, 0.03488590f, 0.00262698f, 0.00010750f, 0.0000074f);
+  *k0v = fma2(make_float2(-lg.x, -lg.y), i0, p);
+  const float2 q1 = poly6(y, 1.0f, 0.15443144f, -0.67278579f, -0.18156897f, -0.01919402f, -0.00110404f, -0.00004686f);
+  *k1ix = fma2(lg, p1, mul2(q1, make_float2(mufu::rcp(x2.x), mufu::rcp(x2.y))));
+}
+__device__ __forceinline__ void k01_large(float2 x2, float2* k0v, float2* k1ix) {
+  float2 e, ix;
+  large_common(x2, &e, &ix);
+  const float2 y = add2(ix, ix);
+  *k0v = mul2(e, poly6(y, 1.25331414f, -0.07832358f, 0.02189568f, -0.01062446f, 0.00587872f, -0.00251540f, 0.00053208f));
+  *k1ix = mul2(mul2(e, ix),
+               poly6(y, 1.25331414f, 0.23498619f, -0.03655620f, 0.01504268f, -0.00780353f, 0.00325614f, -0.00068245f));
+}
+__device__ __forceinline__ void k01(float2 x2, float2* k0v, float2* k1ix) {
+  const bool sx = x2.x <= 4.0f, sy = x2.y <= 4.0f;
+  if (sx && sy) { k01_small(x2, k0v, k1ix); return; }
+  if (!sx && !sy) { k01_large(x2, k0v, k1ix); return; }
+  float2 a0, a1, b0, b1;
+  k01_small(x2, &a0, &a1);
+  k01_large(x2, &b0, &b1);
+  *k0v = make_float2(sx ? a0.x : b0.x, sy ? a0.y : b0.y);
+  *k1ix = make_float2(sx ? a1.x : b1.x, sy ? a1.y : b1.y);
+}
+}  // namespace pk
 
 // FP64.  x <= 2: the ascending series (DLMF 10.31.1-10.31.2),
 //   K0 = -(ln(x/2) + gamma) I0(x) + sum_{k>=1} H_k (x^2/4)^k / (k!)^2,

@@ -20,6 +20,7 @@
 #include "pfmm_impl.h"
 #include "p2p.h"
 #include "sort.h"
+#include "packed.cuh"
 #include "bessel.cuh"
 
 namespace pfmm {
@@ -94,25 +95,6 @@ struct KahanF {
 //   Laplace: pot = -(ln2/4pi) sum q log2(r^2); grad = -(1/2pi) sum q (t-s)/r^2
 //   Stokes : u = -(ln2/8pi) [ sum log2(r^2) f - (2/ln2) sum (r.f/r^2) r ]
 //   modhelm: pot = (1/2pi) sum q K0;  grad = -(beta/2pi) sum q K1 (t-s)/r
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-#if defined(PFMM_P2P_SCALAR)
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return make_float2(a.x * b.x, a.y * b.y); }
-#elif defined(PFMM_P2P_FMA_ONLY)
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __ffma2_rn(a, make_float2(1.f, 1.f), b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __ffma2_rn(a, b, make_float2(0.f, 0.f)); }
-#else
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-#endif
-#if defined(PFMM_P2P_SCALAR)
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
-}
-#else
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-#endif
-
 // Hi/lo coordinates of the padding source at slot k of a tile: its subtile
 // centre (so that the exact and the relative paths see the same point).
 __device__ __forceinline__ float4 s_c_src(const P2PArgs& a, int jb, int k, int nb) {
@@ -353,10 +335,13 @@ __global__ void __launch_bounds__(kP2PThreads, PFMM_P2P_MINB) k_p2p_mixed(const 
 
 // Modified Helmholtz mixed kernel: one target per thread, targets and sources
 // in spatially sorted order, per-source image sums K0s = sum_i K0(beta r_i),
-// K1x = sum_i K1(beta r_i) dx_i / r_i (and y).  K0(x) < 1e-22 for x > 50: a
-// (target block, source tile, image) triple whose boxes are farther apart
-// than 50 / beta is skipped as a whole (the test is exact in FP64 on FP32
-// boxes rounded outward), and single pairs beyond the cutoff are skipped too.
+// K1x = sum_i K1(beta r_i) dx_i / r_i (and y), then one FMA per rhs (strengths
+// read four at a time).  K0(x) < 1e-22 for x > 50: per (target block, source
+// tile, image) an FP64 test on the outward-rounded boxes classifies the image
+// as skipped (boxes farther apart than 50 / beta), complete (every pair within
+// the cutoff: no per-pair test) or partial (pairs beyond the cutoff skipped).
+// Two targets per thread in packed FP32 was measured slower here (register
+// pressure halves the resident warps of this branch-heavy kernel).
 template <int KER, int NIMG, int NR, bool GRAD>
 __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   constexpr int CENTER = NIMG / 2;
@@ -366,8 +351,9 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   __shared__ float4 s_h[kP2PTile];
   __shared__ float4 s_c[NSUB];
   __shared__ float2 s_e[NSUB];
-  __shared__ float s_q[NR][kP2PTile];
-  __shared__ unsigned s_mask;
+  constexpr int NQ4 = (NR + 3) / 4;
+  __shared__ float4 s_q4[NQ4][kP2PTile];
+  __shared__ unsigned s_any, s_all;
   const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
@@ -395,14 +381,17 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   const float beta = a.beta_f;
   const float beta2 = beta * beta;
   const float cut2 = (50.0f / beta) * (50.0f / beta);
-  const float4 tb = a.t_box ? a.t_box[bx] : make_float4(0.f, 0.f, 1e30f, 1e30f);
+  const float4 tb = a.t_box[bx];
+  const float rsm = 2.0f / beta * 1.001f + 1e-6f;  // beta r <= 2 region, with margin
+  float txr[NIMG], tyr[NIMG];
 
-  // image sums of one source over the images in `mask`, then one FMA per rhs
-  auto source = [&](int jj, unsigned mask, auto diff) {
+  // image sums of one source over the images in `any` (`all`: no per-pair
+  // cutoff test), then one FMA per rhs
+  auto source = [&](int jj, unsigned any, unsigned all, auto diff) {
     float K0s = 0.f, K1x = 0.f, K1y = 0.f;
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
-      if (!(mask & (1u << i))) continue;
+      if (!(any & (1u << i))) continue;
       float dx, dy;
       diff(i, dx, dy);
       float r2 = fmaf(dx, dx, dy * dy);
@@ -411,9 +400,9 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         msk = (r2 > 0.0f) ? 1.0f : 0.0f;
         r2 = (r2 > 0.0f) ? r2 : 1.0f;
       }
-      // K0(beta r) < 1e-22 for beta r > 50: such pairs are skipped (the
-      // branch is not taken at all when no lane of the warp needs it)
-      if (r2 < cut2) {
+      // K0(beta r) < 1e-22 for beta r > 50: such pairs of a partial image are
+      // skipped (the branch is not taken at all when no lane of the warp needs it)
+      if ((all & (1u << i)) || r2 < cut2) {
         const float x2 = beta2 * r2;
         if (GRAD) {
           float k0, k1ix;
@@ -428,12 +417,58 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
       }
     }
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      const float q = s_q[r][jj];
-      S[r][0] = fmaf(q, K0s, S[r][0]);
+    for (int g = 0; g < NQ4; ++g) {
+      const float4 q4 = s_q4[g][jj];
+      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 4 * g + k;
+        if (r >= NR) break;
+        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
+        if (GRAD) {
+          S[r][1 % NA] = fmaf(qv[k], K1x, S[r][1 % NA]);
+          S[r][2 % NA] = fmaf(qv[k], K1y, S[r][2 % NA]);
+        }
+      }
+    }
+  };
+
+  // Branch-free variant for subtiles where no pair of the warp can have
+  // beta r <= 2: every image takes the large-argument fit (K0 at beta r > 88
+  // underflows to 0), so the nine chains are independent and interleave.
+  auto source_far = [&](int jj, unsigned any, float p0, float p1) {
+    float K0s = 0.f, K1x = 0.f, K1y = 0.f;
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      if (!(any & (1u << i))) continue;
+      const float dx = txr[i] - p0, dy = tyr[i] - p1;
+      const float r2 = fmaf(dx, dx, dy * dy);
+      const float x2 = beta2 * r2;
+      const float ix = bes::mufu::rsqrt(x2);
+      const float x = x2 * ix;
+      const float e = bes::mufu::ex2(-1.4426950408889634f * x) * bes::mufu::rsqrt(x);
+      const float y = 2.0f * ix;
+      const float k0 = e * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+      K0s += k0;
       if (GRAD) {
-        S[r][1 % NA] = fmaf(q, K1x, S[r][1 % NA]);
-        S[r][2 % NA] = fmaf(q, K1y, S[r][2 % NA]);
+        const float k1r = e * ix * beta * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
+        K1x = fmaf(k1r, dx, K1x);
+        K1y = fmaf(k1r, dy, K1y);
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < NQ4; ++g) {
+      const float4 q4 = s_q4[g][jj];
+      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 4 * g + k;
+        if (r >= NR) break;
+        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
+        if (GRAD) {
+          S[r][1 % NA] = fmaf(qv[k], K1x, S[r][1 % NA]);
+          S[r][2 % NA] = fmaf(qv[k], K1y, S[r][2 % NA]);
+        }
       }
     }
   };
@@ -442,20 +477,35 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
     if (threadIdx.x < 32) {
-      // images whose boxes come within the cutoff (FP64 test, one lane per image)
-      bool near = false;
+      // per image: some pair within the cutoff (any), every pair within it (all);
+      // FP64 on the outward-rounded boxes, one lane per image
+      bool anyi = false, alli = false;
       if (threadIdx.x < NIMG) {
-        const float4 sb = a.s_box ? a.s_box[jb / kBoxTile] : make_float4(0.f, 0.f, 1e30f, 1e30f);
-        const double ex = fmax(0.0, fabs((double)tb.x - a.g.off[threadIdx.x][0] - (double)sb.x) - (double)tb.z - (double)sb.z);
-        const double ey = fmax(0.0, fabs((double)tb.y - a.g.off[threadIdx.x][1] - (double)sb.y) - (double)tb.w - (double)sb.w);
-        near = ex * ex + ey * ey <= (double)a.cut * (double)a.cut;
+        const float4 sb = a.s_box[jb / kBoxTile];
+        const double ox = a.g.off[threadIdx.x][0], oy = a.g.off[threadIdx.x][1];
+        // target - image - source over the boxes, per axis: [lo, hi]
+        const double dxl = ((double)tb.x - tb.z) - ox - ((double)sb.x + sb.z);
+        const double dxh = ((double)tb.x + tb.z) - ox - ((double)sb.x - sb.z);
+        const double dyl = ((double)tb.y - tb.w) - oy - ((double)sb.y + sb.w);
+        const double dyh = ((double)tb.y + tb.w) - oy - ((double)sb.y - sb.w);
+        const double ex = fmax(0.0, fmax(dxl, -dxh)), ey = fmax(0.0, fmax(dyl, -dyh));
+        const double fx = fmax(fabs(dxl), fabs(dxh)), fy = fmax(fabs(dyl), fabs(dyh));
+        const double c2 = (double)a.cut * (double)a.cut;
+        anyi = ex * ex + ey * ey <= c2;
+        alli = fx * fx + fy * fy < c2 * (1.0 - 1e-6);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, near);
-      if (threadIdx.x == 0) s_mask = m;
+      const unsigned m = __ballot_sync(0xffffffffu, anyi), mall = __ballot_sync(0xffffffffu, alli);
+      if (threadIdx.x == 0) {
+        s_any = m;
+        s_all = mall;
+        if (a.work && m)
+          atomicAdd(a.work, (unsigned long long)__popc(m) * (unsigned long long)nb *
+                                (unsigned long long)min(kP2PThreads, a.nt - bx * kP2PThreads));
+      }
     }
     __syncthreads();
-    const unsigned mask = s_mask;
-    if (mask == 0u) continue;
+    const unsigned any = s_any, all = s_all;
+    if (any == 0u) continue;
     for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
       // padding: zero strength at the subtile centre (finite distances)
       const bool v = k < nb;
@@ -466,28 +516,45 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         s_e[k] = (k * kSubtile < nb) ? a.s_ext[jb / kSubtile + k] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) s_q[r][k] = (v && r < nr) ? a.qs[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
+      for (int g = 0; g < NQ4; ++g) {
+        float qv[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int r = 4 * g + t;
+          qv[t] = (v && r < nr) ? a.qs[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
+        }
+        s_q4[g][k] = make_float4(qv[0], qv[1], qv[2], qv[3]);
+      }
     }
     __syncthreads();
     for (int js = 0; js < nb; js += kP2PSub) {
-      float txr[NIMG], tyr[NIMG];
-      bool near = false;
+      bool near = false, small = false;
       {
         const float4 c = s_c[js / kSubtile];
         const float2 e = s_e[js / kSubtile];
         const float bxe = 2.f * e.x + e.y, bye = e.x + 2.f * e.y;
+        // beta r <= 2 possible: target within 2 / beta (+ margin) of the subtile box
+        const float sxe = e.x + rsm, sye = e.y + rsm;
 #pragma unroll
         for (int i = 0; i < NIMG; ++i) {
           txr[i] = (thx[i] - c.x) + (tlx[i] - c.y);
           tyr[i] = (thy[i] - c.z) + (tly[i] - c.w);
-          near |= fabsf(txr[i]) < bxe && fabsf(tyr[i]) < bye;
+          const bool act = (any & (1u << i)) != 0u;
+          near |= act && fabsf(txr[i]) < bxe && fabsf(tyr[i]) < bye;
+          small |= act && fabsf(txr[i]) < sxe && fabsf(tyr[i]) < sye;
         }
       }
-      if (near) {
+      if (!__any_sync(0xffffffffu, near || small)) {
+#pragma unroll 2
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float2 p = s_p[jj];
+          source_far(jj, any, p.x, p.y);
+        }
+      } else if (near) {
 #pragma unroll 1
         for (int jj = js; jj < js + kP2PSub; ++jj) {
           const float4 h = s_h[jj];
-          source(jj, mask, [&](int i, float& dx, float& dy) {
+          source(jj, any, all, [&](int i, float& dx, float& dy) {
             dx = (thx[i] - h.x) + (tlx[i] - h.y);
             dy = (thy[i] - h.z) + (tly[i] - h.w);
           });
@@ -496,7 +563,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
 #pragma unroll 2
         for (int jj = js; jj < js + kP2PSub; ++jj) {
           const float2 p = s_p[jj];
-          source(jj, mask, [&](int i, float& dx, float& dy) {
+          source(jj, any, all, [&](int i, float& dx, float& dy) {
             dx = txr[i] - p.x;
             dy = tyr[i] - p.y;
           });
@@ -807,6 +874,7 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
   }
   P2PArgs a;
   fill_p2p_args(p, ws, ns, nt, self, pot, grad, &a);
+  set_work_counter(p, ws, p->prof, &a);
   const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread
   const int ntb = cdivl(nt, kP2PThreads * (packed ? 2 : 1));
   const int nrg = mixed ? 1 : cdivl(a.nrhs, 4);

@@ -31,6 +31,7 @@ struct P2PArgs {
   const double* mom;     // FP64 moments: mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y
   double* pot;
   double* grad;
+  unsigned long long* work;  // evaluated-pair counter (profiling), NULL otherwise
 };
 
 // One unit of work of the persistent batched P2P kernel: target block bx of
@@ -53,6 +54,10 @@ int p2p_targets_per_block(int kernel);
 // Sort descriptors of one cell (mixed path): sources, and for modified
 // Helmholtz with separate targets also the targets.  off_s / off_t: first
 // slot of each set in the concatenated sort arrays.  Returns 1 or 2.
+// Set or clear the evaluated-pair counter of a cell's P2P arguments.
+inline void set_work_counter(const pfmm_plan* p, char* ws, bool on, P2PArgs* a) {
+  a->work = on ? (unsigned long long*)(ws + p->lay.work) : nullptr;
+}
 int fill_sort_cells(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, int64_t off_s, int64_t off_t,
                     SortCell* out);
 

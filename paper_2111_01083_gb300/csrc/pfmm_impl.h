@@ -47,7 +47,9 @@ inline int nufft_npk(int kernel, int n_gl) { return kernel == PFMM_STOKES ? 2 * 
 
 // Workspace layout (byte offsets from the workspace base, all 256-aligned).
 struct Layout {
-  size_t status, moments, nodes;
+  size_t status, moments;
+  size_t work;             // uint64: near-image pairs evaluated (counted while profiling)
+  size_t nodes;
   size_t src64, trg64;     // double [2][n] canonical coordinates
   size_t srcf, trgf;       // float  [2][n] canonical coordinates (mixed far field)
   size_t srcU, trgU;       // int32 [n] fixed-point x/d phase (mixed south/north)

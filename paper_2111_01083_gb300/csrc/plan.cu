@@ -357,6 +357,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int nrhs = o->nrhs;
   L.status = take(kStatusWords * sizeof(int));
   L.moments = take(nrhs * 8 * sizeof(double));
+  L.work = take(sizeof(unsigned long long));
   L.nodes = take(pfmm::node_region_bytes(p));
   L.src64 = take(2 * ns_max * sizeof(double));
   L.trg64 = take(2 * nt_max * sizeof(double));
@@ -479,6 +480,20 @@ pfmm_status pfmm_profile_read(pfmm_plan* p, float* ms, int n) {
     e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
     if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
   }
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_profile_pairs(pfmm_plan* p, const void* workspace, void* stream, double* pairs) {
+  if (!p || !workspace || !pairs) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  if (!p->prof) return fail(PFMM_ERR_INVALID_ARG, "profiling not enabled");
+  *pairs = (double)p->npairs;
+  if (p->opts.kernel != PFMM_MODHELM || p->opts.precision != PFMM_MIXED) return PFMM_OK;
+  unsigned long long w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, (const char*)workspace + p->lay.work, sizeof w, cudaMemcpyDeviceToHost,
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "read pair count: %s", cudaGetErrorString(e));
+  *pairs = (double)w;
   return PFMM_OK;
 }
 

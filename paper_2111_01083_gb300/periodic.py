@@ -142,6 +142,16 @@ class PeriodicOp:
         _lib.check(_lib.lib().pfmm_profile_read(self._h, ms, 3))
         return list(ms)
 
+    def pairs(self, stream=None):
+        """Near-image pairs the P2P evaluated in the last profiled execute
+        (pfmm_profile_pairs; synchronises)."""
+        import torch
+        ws = self.workspace()
+        st = stream if stream is not None else torch.cuda.current_stream(ws.device).cuda_stream
+        v = ctypes.c_double()
+        _lib.check(_lib.lib().pfmm_profile_pairs(self._h, _ptr(ws), ctypes.c_void_p(st), ctypes.byref(v)))
+        return float(v.value)
+
     def status(self, stream=None):
         """Synchronise and return the device status of the last execute (raises on error)."""
         import torch
@@ -245,12 +255,13 @@ class BatchOp:
         _lib.check(_lib.lib().pfmm_batch_profile_enable(self._h, int(bool(on))))
 
     def phase_ms(self):
-        """(per-cell phases ms, batched P2P ms, kernels launched) of the last
-        profiled execute; waits for its events."""
+        """(per-cell phases ms, batched P2P ms, kernels launched, near-image
+        pairs evaluated) of the last profiled execute; waits for its events."""
         ms = (ctypes.c_float * 2)()
         n = ctypes.c_int()
-        _lib.check(_lib.lib().pfmm_batch_profile_read(self._h, ms, 2, ctypes.byref(n)))
-        return float(ms[0]), float(ms[1]), int(n.value)
+        pairs = ctypes.c_double()
+        _lib.check(_lib.lib().pfmm_batch_profile_read(self._h, ms, 2, ctypes.byref(n), ctypes.byref(pairs)))
+        return float(ms[0]), float(ms[1]), int(n.value), float(pairs.value)
 
     def capture(self, src, q, trg=None, out=None, grad=True):
         """Record one execute in a CUDA graph (after a first execute on the same
