@@ -37,30 +37,41 @@ METRIC = "targets+sources/s of periodic Laplace/Stokes op, mixed vs FP64 at rel 
 SMS = 152
 SM_MAX_MHZ = 2070.0
 
-# Per-pair algorithmic work of the near-image P2P, one pair = (target, source,
-# near image): (FP32 operations, MUFU operations).  Laplace potential +
-# gradient: differences, r^2, 1/r^2 and log r^2, three accumulations.  Stokes
-# velocity: the same plus the dyadic (x^2 - y^2, x y over r^2) and two
-# components.  Modified Helmholtz K0(beta r) by the A&S 9.8 fits: differences,
-# r^2, sqrt, exp or log, a 7-term polynomial, one accumulation per rhs (with
-# the gradient also K1 and two more accumulations per rhs).
+# Per-pair work of the near-image P2P, one pair = (target, source, near
+# image): (FP32 operations, MUFU operations in units of the 16/clk/SM rate;
+# ex2 runs at twice that rate and counts 1/2).  These are the operations of
+# the implemented formulation: per-source image sums, one log2 of a product of
+# scaled r^2 per (target, source) (1/9 per pair), coordinate differences
+# against a subtile centre.
+#   Laplace pot + grad: dx, dy, r^2 (2), product (2), sum dx/r^2, dy/r^2 (2) = 8;
+#                       rcp + lg2/9
+#   Laplace pot:        dx, dy, r^2 (2), product (2) = 6; lg2/9
+#   Stokes velocity:    dx, dy, r^2 (2), product (2), dx^2 - dy^2 (2),
+#                       sum cos 2t (1), sum sin t cos t (2) = 11; rcp + lg2/9
+#   mod. Helmholtz K0:  dx, dy, r^2 (2), x^2, x, exponent, y = 2/x, 7-term fit (6),
+#                       two products, image sum = 16, + nrhs/9 strength FMAs;
+#                       2 rsqrt + ex2 (2.5 units); with K1: + fit (6), scaling (2),
+#                       two sums (2) and 2 nrhs/9 more FMAs
 def p2p_work(kernel, nrhs, grad):
     if kernel == "laplace":
-        return (12, 2) if grad else (6, 1)
+        return (8.0, 1.0 + 1.0 / 9.0) if grad else (6.0, 1.0 / 9.0)
     if kernel == "stokes":
-        return (20, 2)
-    return (26 + 3 * nrhs, 2) if grad else (17 + nrhs, 2)
+        return (11.0, 1.0 + 1.0 / 9.0)
+    if grad:
+        return (26.0 + 3.0 * nrhs / 9.0, 2.5)
+    return (16.0 + nrhs / 9.0, 2.5)
 
 
 def alu_rates():
     """Results per clock per SM measured on this GPU model by
-    paper_2111_01083_gb300/alu_peaks.py (committed as profiles/alu_peaks.json)."""
+    paper_2111_01083_gb300/alu_peaks.py (committed as profiles/alu_peaks.json):
+    FP32 = scalar FFMA rate, MUFU = the lg2/rcp/rsqrt rate."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "alu_peaks.json")))
-        return {"fp32": d["ffma2_packed"], "mufu": min(d["mufu_lg2"], d["mufu_rcp"], d["mufu_ex2"], d["mufu_rsqrt"]),
+        return {"fp32": max(d["ffma"], d["ffma2_packed"]), "mufu": min(d["mufu_lg2"], d["mufu_rcp"], d["mufu_rsqrt"]),
                 "source": "profiles/alu_peaks.json (measured)"}
     except Exception:
-        return {"fp32": 256.0, "mufu": 28.4, "source": "fallback constants (profiles/alu_peaks.json missing)"}
+        return {"fp32": 128.0, "mufu": 16.0, "source": "fallback: nominal 128 FP32 / 16 MUFU per clock per SM"}
 
 
 def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=None):
@@ -74,8 +85,8 @@ def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=No
     achieved = pairs / (launch_ms * 1e-3) / 1e9
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": traffic,
-            "peak_basis": (f"min(FP32 {r['fp32']:.1f}/clk/SM / {fp32_ops} ops, MUFU {r['mufu']:.1f}/clk/SM / "
-                           f"{mufu_ops} ops) per pair x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz; "
+            "peak_basis": (f"min(FP32 {r['fp32']:.1f}/clk/SM / {fp32_ops:.2f} ops, MUFU {r['mufu']:.1f}/clk/SM / "
+                           f"{mufu_ops:.2f} ops) per pair x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz; "
                            f"{'FP32' if f_fp32 < f_mufu else 'MUFU'}-bound; rates from {r['source']}"),
             "pairs_per_launch": pairs, "launch_ms": launch_ms, "share_of_step": launch_ms / step_ms}
 

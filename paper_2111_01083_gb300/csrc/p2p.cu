@@ -353,7 +353,6 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   __shared__ float2 s_e[NSUB];
   constexpr int NQ4 = (NR + 3) / 4;
   __shared__ float4 s_q4[NQ4][kP2PTile];
-  __shared__ unsigned s_any, s_all;
   const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
@@ -473,39 +472,49 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
     }
   };
 
-  for (int jb = j0; jb < j1; jb += kP2PTile) {
-    const int nb = min(kP2PTile, j1 - jb);
+  // Tiles are classified kP2PThreads at a time, one thread per tile: per
+  // image, some pair within the cutoff (any) or every pair within it (all).
+  // FP32 on the outward-rounded boxes with a relative margin: a tile
+  // misjudged at the margin only adds or drops terms of size K0(50) ~ 1e-22.
+  // Culled tiles then cost no barrier.
+  __shared__ unsigned s_tany[kP2PThreads], s_tall[kP2PThreads];
+  const int ntile = (j1 - j0 + kP2PTile - 1) / kP2PTile;
+  for (int g0 = 0; g0 < ntile; g0 += kP2PThreads) {
     __syncthreads();
-    if (threadIdx.x < 32) {
-      // per image: some pair within the cutoff (any), every pair within it (all);
-      // FP64 on the outward-rounded boxes, one lane per image
-      bool anyi = false, alli = false;
-      if (threadIdx.x < NIMG) {
-        const float4 sb = a.s_box[jb / kBoxTile];
-        const double ox = a.g.off[threadIdx.x][0], oy = a.g.off[threadIdx.x][1];
-        // target - image - source over the boxes, per axis: [lo, hi]
-        const double dxl = ((double)tb.x - tb.z) - ox - ((double)sb.x + sb.z);
-        const double dxh = ((double)tb.x + tb.z) - ox - ((double)sb.x - sb.z);
-        const double dyl = ((double)tb.y - tb.w) - oy - ((double)sb.y + sb.w);
-        const double dyh = ((double)tb.y + tb.w) - oy - ((double)sb.y - sb.w);
-        const double ex = fmax(0.0, fmax(dxl, -dxh)), ey = fmax(0.0, fmax(dyl, -dyh));
-        const double fx = fmax(fabs(dxl), fabs(dxh)), fy = fmax(fabs(dyl), fabs(dyh));
-        const double c2 = (double)a.cut * (double)a.cut;
-        anyi = ex * ex + ey * ey <= c2;
-        alli = fx * fx + fy * fy < c2 * (1.0 - 1e-6);
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, anyi), mall = __ballot_sync(0xffffffffu, alli);
-      if (threadIdx.x == 0) {
-        s_any = m;
-        s_all = mall;
-        if (a.work && m)
-          atomicAdd(a.work, (unsigned long long)__popc(m) * (unsigned long long)nb *
+    {
+      const int t = g0 + threadIdx.x;
+      unsigned many = 0u, mall = 0u;
+      if (t < ntile) {
+        const float4 sb = a.s_box[(j0 + t * kP2PTile) / kBoxTile];
+        const float c2 = a.cut * a.cut;
+        const float hx = tb.z + sb.z, hy = tb.w + sb.w;
+#pragma unroll 1
+        for (int i = 0; i < NIMG; ++i) {
+          const float cx = fabsf(tb.x - a.offf[i][0] - sb.x), cy = fabsf(tb.y - a.offf[i][1] - sb.y);
+          const float mx = 1e-5f * (fabsf(tb.x) + fabsf(sb.x) + fabsf(a.offf[i][0])) + 1e-6f * hx;
+          const float my = 1e-5f * (fabsf(tb.y) + fabsf(sb.y) + fabsf(a.offf[i][1])) + 1e-6f * hy;
+          const float ex = fmaxf(0.f, cx - hx - mx), ey = fmaxf(0.f, cy - hy - my);
+          const float fx = cx + hx + mx, fy = cy + hy + my;
+          if (ex * ex + ey * ey <= c2) many |= 1u << i;
+          if (fx * fx + fy * fy < c2) mall |= 1u << i;
+        }
+        if (a.work && many) {
+          const int nbt = min(kP2PTile, j1 - (j0 + t * kP2PTile));
+          atomicAdd(a.work, (unsigned long long)__popc(many) * (unsigned long long)nbt *
                                 (unsigned long long)min(kP2PThreads, a.nt - bx * kP2PThreads));
+        }
       }
+      s_tany[threadIdx.x] = many;
+      s_tall[threadIdx.x] = mall;
     }
     __syncthreads();
-    const unsigned any = s_any, all = s_all;
+    const int gn = min(kP2PThreads, ntile - g0);
+  for (int tt = 0; tt < gn; ++tt) {
+    const unsigned any = s_tany[tt], all = s_tall[tt];
     if (any == 0u) continue;
+    const int jb = j0 + (g0 + tt) * kP2PTile;
+    const int nb = min(kP2PTile, j1 - jb);
+    __syncthreads();
     for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
       // padding: zero strength at the subtile centre (finite distances)
       const bool v = k < nb;
@@ -577,6 +586,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
           S[r][k] = 0.f;
         }
     }
+  }
   }
   if (!in) return;
   const int lo = a.t_perm ? a.t_perm[l] : l;
@@ -790,6 +800,10 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
     a.t_box = self ? (const float4*)(ws + L.s_box) : (const float4*)(ws + L.t_box);
   }
   a.cut = (float)(50.0 / std::max(p->far.beta, 1e-300));
+  for (int i = 0; i < p->geom.nimg; ++i) {
+    a.offf[i][0] = (float)p->geom.off[i][0];
+    a.offf[i][1] = (float)p->geom.off[i][1];
+  }
   a.src64 = (const double*)(ws + L.src64);
   a.qc = (const double*)(ws + L.qc);
   a.beta = p->far.beta;
