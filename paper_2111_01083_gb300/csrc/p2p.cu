@@ -559,22 +559,16 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
           const float2 p = s_p[jj];
           source_far(jj, any, p.x, p.y);
         }
-      } else if (near) {
+      } else {
+        // close pairs or beta r <= 2 in reach: exact differences, both K0 fits
+        // (one code path for both cases keeps the kernel small in the
+        // instruction cache)
 #pragma unroll 1
         for (int jj = js; jj < js + kP2PSub; ++jj) {
           const float4 h = s_h[jj];
           source(jj, any, all, [&](int i, float& dx, float& dy) {
             dx = (thx[i] - h.x) + (tlx[i] - h.y);
             dy = (thy[i] - h.z) + (tly[i] - h.w);
-          });
-        }
-      } else {
-#pragma unroll 2
-        for (int jj = js; jj < js + kP2PSub; ++jj) {
-          const float2 p = s_p[jj];
-          source(jj, any, all, [&](int i, float& dx, float& dy) {
-            dx = txr[i] - p.x;
-            dy = tyr[i] - p.y;
           });
         }
       }
