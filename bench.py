@@ -282,20 +282,32 @@ def batch_oracle_time(beta, quantiles=(0.25, 0.5, 0.75, 0.9), ntarg=12):
 
 
 def init_dist(world, dev):
+    """One process per GPU (torchrun): NCCL for the barrier and the max over
+    ranks only; no collective on the data path (every rank runs its own cells)."""
     if world <= 1:
         return None
     import torch.distributed as dist
-    dist.init_process_group("nccl", device_id=dev)
+    if dev.type == "cuda":
+        dist.init_process_group("nccl", device_id=dev)
+    else:
+        dist.init_process_group("gloo")
     return dist
 
 
 def max_over_ranks(dist, x, dev):
+    """The slowest rank's time (the job ends when it does)."""
     if not dist:
         return x
     import torch
     t = torch.tensor([x], device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world, units_per_rank, seconds):
+    """Whole-job throughput: every rank processes units_per_rank units (weak
+    scaling), and the job takes the max-over-ranks time."""
+    return world * units_per_rank / seconds
 
 
 def timed_region(step, args, dist, dev, local):
@@ -394,7 +406,7 @@ def run_batch(args, rank, world, local):
             cpu = batch_oracle_time(beta)
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[:200]}
-    line = {"metric": METRIC, "value": world * 2 * ns / (ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": job_value(world, 2 * ns, ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
             "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
@@ -408,7 +420,7 @@ def run_batch(args, rank, world, local):
                                      "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
                                      "pairs = those evaluated: triples beyond beta r = 50 are skipped)"),
             "cpu_baseline": cpu, "clocks": clocks,
-            "e2e": {"value": world * 2 * ns / e2e_s, "unit": "targets+sources/s",
+            "e2e": {"value": job_value(world, 2 * ns, e2e_s), "unit": "targets+sources/s",
                     "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8, "d2h_bytes_per_step": pot_h.numel() * 8,
                     "api": "BatchOp CUDA-graph replay with pinned host copies in the timed region"},
             "gpu_launches": nlaunch * args.steps}
@@ -485,7 +497,7 @@ def run_adjoint(args, rank, world, local):
             cpu["sample"] += "; one oracle evaluation (potential + gradient) gives dE/dq and dE/dx"
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[:200]}
-    line = {"metric": METRIC, "value": world * 2 * n / (ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
+    line = {"metric": METRIC, "value": job_value(world, 2 * n, ms * 1e-3), "unit": "targets+sources/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
             "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
@@ -494,7 +506,7 @@ def run_adjoint(args, rank, world, local):
             "roofline": p2p_roofline("laplace", 1, True, desc["npairs"], p2p_ms, ms,
                                      "k_p2p_mixed (near-image P2P of the adjoint execute)"),
             "cpu_baseline": cpu, "clocks": clocks,
-            "e2e": {"value": world * 2 * n / e2e_s, "unit": "targets+sources/s",
+            "e2e": {"value": job_value(world, 2 * n, e2e_s), "unit": "targets+sources/s",
                     "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8,
                     "d2h_bytes_per_step": dq_h.numel() * 8 + dx_h.numel() * 8,
                     "api": "periodic() autograd forward + backward with pinned host copies in the timed region"},
@@ -529,10 +541,7 @@ def main():
         build_library()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    dist = init_dist(world, dev)
 
     w = workloads.make(args.workload, scale=args.scale)
     cfg = dict(workloads.CONFIGS[args.workload])
@@ -582,12 +591,8 @@ def main():
         dist.barrier()
     clocks = stop_clocks(proc, fh, clk_path, local)
     op.status()
-    ms = sum(step_ms) / len(step_ms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * (ns + nt) / (ms * 1e-3)
+    ms = max_over_ranks(dist, sum(step_ms) / len(step_ms), dev)
+    value = job_value(world, ns + nt, ms * 1e-3)
     desc = op.describe()
 
     # end to end: host arrays through pfmm_execute_host (pinned), copies inside the timed region
@@ -604,11 +609,7 @@ def main():
         t0 = time.perf_counter()
         op.execute_host_ptrs(src_h, q_h, trg_h, pot_h, grad_h)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(dist, statistics.median(e2e_t), dev)
     h2d = src_h.numel() * 8 + q_h.numel() * 8 + (0 if self_t else trg_h.numel() * 8)
     d2h = pot_h.numel() * 8 + (grad_h.numel() * 8 if grad else 0)
 
@@ -667,7 +668,7 @@ def main():
                    "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
         "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_p2p": p2p},
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-        "e2e": {"value": world * (ns + nt) / e2e_s, "unit": "targets+sources/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(world, ns + nt, e2e_s), "unit": "targets+sources/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "pfmm_execute_host (pinned host buffers)"},
         "gpu_launches": launches, "accuracy": acc,
     }
