@@ -48,6 +48,13 @@ struct pfmm_batch {
   bool prof = false, timed = false, counting = false;
   cudaEvent_t ev[3] = {};
   int nlaunch = 0;
+  // per-cell phases fan out over kFan streams (fork/join with events), so the
+  // many small per-cell kernels overlap; under stream capture this becomes
+  // kFan parallel branches of the graph
+  static constexpr int kFan = 8;
+  cudaStream_t fan[kFan] = {};
+  cudaEvent_t fork = nullptr, join[kFan] = {};
+  bool fan_ready = false;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -153,7 +160,27 @@ void pfmm_batch_destroy(pfmm_batch* b) {
   for (auto* p : b->plans) pfmm_plan_destroy(p);
   if (b->prof)
     for (auto& e : b->ev) cudaEventDestroy(e);
+  if (b->fan_ready) {
+    for (int k = 0; k < pfmm_batch::kFan; ++k) {
+      cudaStreamDestroy(b->fan[k]);
+      cudaEventDestroy(b->join[k]);
+    }
+    cudaEventDestroy(b->fork);
+  }
   delete b;
+}
+
+// Streams and events of the per-cell fan-out, created at the first execute
+// (on the current device) and reused; nothing is created while capturing.
+static cudaError_t fan_setup(pfmm_batch* b) {
+  if (b->fan_ready) return cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < pfmm_batch::kFan && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->fan[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) b->fan_ready = true;
+  return e;
 }
 
 pfmm_status pfmm_batch_profile_enable(pfmm_batch* b, int on) {
@@ -253,7 +280,8 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   e = cudaMemsetAsync(ws + b->off_counter, 0, 256, st);
   if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  const bool rec = b->prof && cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+  const bool rec = b->prof && cap == cudaStreamCaptureStatusNone;
   if (mixed && b->kernel == PFMM_MODHELM && rec != b->counting) {
     // evaluated-pair counters in the P2P descriptors only while profiling
     for (int c = 0; c < b->ncell; ++c) set_work_counter(b->plans[c], ws + b->wsoff[c], rec, &b->hcells[c]);
@@ -263,13 +291,29 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   }
   if (rec) cudaEventRecord(b->ev[0], st);
   b->nlaunch = 0;
+  // per-cell phases: cell c on fan stream c % kFan, forked from and joined
+  // back into the caller's stream
+  const bool fan = b->ncell > 1 && (b->fan_ready || (cap == cudaStreamCaptureStatusNone && fan_setup(b) == cudaSuccess));
+  if (fan) {
+    e = cudaEventRecord(b->fork, st);
+    for (int k = 0; k < pfmm_batch::kFan && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->fan[k], b->fork, 0);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "fork: %s", cudaGetErrorString(e));
+  }
   for (int c = 0; c < b->ncell; ++c) {
     int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
+    cudaStream_t sc = fan ? b->fan[c % pfmm_batch::kFan] : st;
     pfmm_status s = execute_cell(b->plans[c], ws + b->wsoff[c], ns, src + b->soff[c], q + b->soff[c], nt,
-                                 tr + b->toff[c], pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, st, b->self,
+                                 tr + b->toff[c], pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, sc, b->self,
                                  false, !mixed);
     if (s != PFMM_OK) return s;
     b->nlaunch += b->plans[c]->nlaunch;
+  }
+  if (fan) {
+    for (int k = 0; k < pfmm_batch::kFan && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b->join[k], b->fan[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->join[k], 0);
+    }
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "join: %s", cudaGetErrorString(e));
   }
   if (rec) cudaEventRecord(b->ev[1], st);
   if (mixed) {
