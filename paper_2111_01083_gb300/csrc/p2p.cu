@@ -16,6 +16,7 @@
 // FP64 kernel (k_p2p_f64): the same sum in double precision with log(),
 // division and the FP64 Bessel routines.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include "pfmm_impl.h"
 #include "p2p.h"
@@ -348,6 +349,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   constexpr int NA = GRAD ? 3 : 1;
   constexpr int NSUB = kP2PTile / kSubtile;
   __shared__ float2 s_p[kP2PTile];
+  __shared__ float2 s_pb[kP2PTile];  // beta-scaled relative coordinates (far path)
   __shared__ float4 s_h[kP2PTile];
   __shared__ float4 s_c[NSUB];
   __shared__ float2 s_e[NSUB];
@@ -382,7 +384,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   const float cut2 = (50.0f / beta) * (50.0f / beta);
   const float4 tb = a.t_box[bx];
   const float rsm = 2.0f / beta * 1.001f + 1e-6f;  // beta r <= 2 region, with margin
-  float txr[NIMG], tyr[NIMG];
+  float txr[NIMG], tyr[NIMG], txb[NIMG], tyb[NIMG];
 
   // image sums of one source over the images in `any` (`all`: no per-pair
   // cutoff test), then one FMA per rhs
@@ -435,24 +437,27 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   // Branch-free variant for subtiles where no pair of the warp can have
   // beta r <= 2: every image takes the large-argument fit (K0 at beta r > 88
   // underflows to 0), so the nine chains are independent and interleave.
-  auto source_far = [&](int jj, unsigned any, float p0, float p1) {
+  // Coordinates here are pre-scaled by beta (txb, tyb per subtile, the
+  // source's in shared memory), so x^2 = dx^2 + dy^2 and K1(x)/x multiplies
+  // the scaled difference directly; the fits' variable y = 2/x is folded into
+  // their coefficients (c_k 2^k).  ALL: every image active, no per-image test.
+  auto source_far = [&](int jj, unsigned any, float p0, float p1, auto all_tag) {
+    constexpr bool ALL = decltype(all_tag)::value;
     float K0s = 0.f, K1x = 0.f, K1y = 0.f;
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
-      if (!(any & (1u << i))) continue;
-      const float dx = txr[i] - p0, dy = tyr[i] - p1;
-      const float r2 = fmaf(dx, dx, dy * dy);
-      const float x2 = beta2 * r2;
+      if (!ALL && !(any & (1u << i))) continue;
+      const float dx = txb[i] - p0, dy = tyb[i] - p1;
+      const float x2 = fmaf(dx, dx, dy * dy);
       const float ix = bes::mufu::rsqrt(x2);
       const float x = x2 * ix;
       const float e = bes::mufu::ex2(-1.4426950408889634f * x) * bes::mufu::rsqrt(x);
-      const float y = 2.0f * ix;
-      const float k0 = e * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+      const float k0 = e * (1.25331414f + ix * (-0.15664716f + ix * (0.08758272f + ix * (-0.08499568f + ix * (0.09405952f + ix * (-0.0804928f + ix * 0.03405312f))))));
       K0s += k0;
       if (GRAD) {
-        const float k1r = e * ix * beta * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
-        K1x = fmaf(k1r, dx, K1x);
-        K1y = fmaf(k1r, dy, K1y);
+        const float k1ix = e * ix * (1.25331414f + ix * (0.46997238f + ix * (-0.1462248f + ix * (0.12034144f + ix * (-0.12485648f + ix * (0.10419648f + ix * (-0.0436768f)))))));
+        K1x = fmaf(k1ix, dx, K1x);
+        K1y = fmaf(k1ix, dy, K1y);
       }
     }
 #pragma unroll
@@ -519,6 +524,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
       // padding: zero strength at the subtile centre (finite distances)
       const bool v = k < nb;
       s_p[k] = v ? a.s_rel[jb + k] : make_float2(0.f, 0.f);
+      s_pb[k] = make_float2(beta * s_p[k].x, beta * s_p[k].y);
       s_h[k] = v ? a.s_hl[jb + k] : s_c_src(a, jb, k, nb);
       if (k < NSUB) {
         s_c[k] = (k * kSubtile < nb) ? a.s_sub[jb / kSubtile + k] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -554,10 +560,23 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         }
       }
       if (!__any_sync(0xffffffffu, near || small)) {
+#pragma unroll
+        for (int i = 0; i < NIMG; ++i) {
+          txb[i] = beta * txr[i];
+          tyb[i] = beta * tyr[i];
+        }
+        if (any == (1u << NIMG) - 1u) {
 #pragma unroll 2
-        for (int jj = js; jj < js + kP2PSub; ++jj) {
-          const float2 p = s_p[jj];
-          source_far(jj, any, p.x, p.y);
+          for (int jj = js; jj < js + kP2PSub; ++jj) {
+            const float2 p = s_pb[jj];
+            source_far(jj, any, p.x, p.y, std::true_type{});
+          }
+        } else {
+#pragma unroll 2
+          for (int jj = js; jj < js + kP2PSub; ++jj) {
+            const float2 p = s_pb[jj];
+            source_far(jj, any, p.x, p.y, std::false_type{});
+          }
         }
       } else {
         // close pairs or beta r <= 2 in reach: exact differences, both K0 fits
