@@ -246,6 +246,21 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* plan, void* workspace, size_t ws_byt
 /* Synchronise the stream and read the device status word written by the
  * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,
  * PFMM_ERR_NOT_NEUTRAL, PFMM_ERR_TIMEOUT) and clears it. */
+/* Pressure of the periodic Stokeslet sum (the Stokes kernel of Sec. 5 and
+ * its lattice sum, Eq. psum): for the Stokeslet u = (1/4pi)(-log r I +
+ * r r^T / r^2) f the pressure is p = (1/2pi) f . r / r^2 = -f . grad G_L with
+ * G_L = -(1/2pi) log r, so the periodic pressure is
+ *   p(t) = -(d/dx phi[f_x] + d/dy phi[f_y])(t),
+ * phi[c] the periodic Laplace potential of charges c (zero net force makes
+ * both Laplace sums converge).  It is computed by the Laplace operator of
+ * `plan`, which must be a PFMM_LAPLACE plan on the same lattice with an even
+ * nrhs = 2 * (Stokes rhs).  f [nrhs/2][2][ns] (input frame) is read as nrhs
+ * charge vectors; pres [nrhs/2][nt].  The gradient lives in the plan's
+ * workspace.  Errors: as pfmm_execute; PFMM_ERR_INVALID_ARG if the plan is not
+ * Laplace or nrhs is odd; PFMM_ERR_NOT_NEUTRAL via pfmm_get_status. */
+pfmm_status pfmm_stokes_pressure(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
+                                 const double* f, int64_t nt, const double* trg, double* pres, void* stream);
+
 pfmm_status pfmm_get_status(pfmm_plan* plan, void* workspace, void* stream);
 
 /* Per-phase GPU timing (tracing).  When enabled (on != 0), pfmm_execute

@@ -49,6 +49,24 @@ def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1
     return pot, (_rot_vec(rot.T, grad) if want_grad else None)
 
 
+def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.25):
+    """Pressure of the periodic Stokeslet sum, input frame, [nrhs][nt].
+
+    The free-space Stokeslet of this normalisation, u = (1/4pi)(-log r I +
+    r r^T / r^2) f, has pressure p = (1/2pi) f . r / r^2 = -f . grad G_L with
+    G_L = -(1/2pi) log r the Laplace kernel; summed over the lattice (zero net
+    force) this is p = -(d/dx phi[f_x] + d/dy phi[f_y]), phi[c] the periodic
+    Laplace potential of charges c.  Evaluated with the Laplace field of this
+    oracle (part="total": near images plus the periodizing part).
+    """
+    f = np.asarray(f, np.float64)
+    nrhs = f.shape[0]
+    q = f.reshape(2 * nrhs, -1)  # [r][c][n] -> rows (r, c)
+    _, g = evaluate("laplace", 0.0, e1, e2, src, q, trg, how=how, eps=eps, margin_frac=margin_frac)
+    g = g.reshape(nrhs, 2, 2, -1)  # [r][c][component][n]
+    return -(g[:, 0, 0] + g[:, 1, 1])
+
+
 def rel_err(a, b, modconst=False):
     """Relative l2 error over all entries; modconst removes the best-fit
     constant per rhs (per component) along the last axis first."""

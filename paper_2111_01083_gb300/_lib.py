@@ -24,7 +24,8 @@ EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host"
            "pfmm_execute", "pfmm_execute_host", "pfmm_get_status", "pfmm_last_error", "pfmm_plan_destroy",
            "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_profile_pairs", "pfmm_execute_static",
            "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
-           "pfmm_batch_destroy", "pfmm_batch_profile_enable", "pfmm_batch_profile_read", "pfmm_execute_adjoint"]
+           "pfmm_batch_destroy", "pfmm_batch_profile_enable", "pfmm_batch_profile_read", "pfmm_execute_adjoint",
+           "pfmm_stokes_pressure"]
 
 
 class Opts(ctypes.Structure):
@@ -91,6 +92,8 @@ def lib():
     L.pfmm_batch_destroy.restype = None
     L.pfmm_execute_adjoint.argtypes = [vp, vp, sz, i64, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp]
     L.pfmm_execute_adjoint.restype = ctypes.c_int
+    L.pfmm_stokes_pressure.argtypes = [vp, vp, sz, i64, vp, vp, i64, vp, vp, vp]
+    L.pfmm_stokes_pressure.restype = ctypes.c_int
     L.pfmm_get_status.argtypes = [vp, vp, vp]
     L.pfmm_get_status.restype = ctypes.c_int
     L.pfmm_last_error.argtypes = []

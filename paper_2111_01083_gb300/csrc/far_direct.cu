@@ -576,6 +576,19 @@ cudaError_t launch_contract(int nrhs, int64_t n, const double* a, int64_t sa, co
   return cudaGetLastError();
 }
 
+__global__ void k_pressure(int nrhs, int64_t nt, const double* __restrict__ g, double* __restrict__ pres) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= nt) return;
+  for (int r = 0; r < nrhs; ++r)
+    pres[(size_t)r * nt + l] = -(g[((size_t)(2 * r) * 2) * nt + l] + g[((size_t)(2 * r + 1) * 2 + 1) * nt + l]);
+}
+
+cudaError_t launch_pressure(int nrhs, int64_t nt, const double* g, double* pres, cudaStream_t st) {
+  if (nt == 0) return cudaSuccess;
+  k_pressure<<<cdiv_i(nt, 256), 256, 0, st>>>(nrhs, nt, g, pres);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   size_t nr = p->opts.nrhs;

@@ -149,6 +149,9 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
 // kernels launched by the most recent launch_* call (set by each launcher)
 extern thread_local int g_launches;
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);
+// pres[r][l] = -(g[2r][0][l] + g[2r+1][1][l]): the Stokes pressure from the
+// gradients of the Laplace fields of the force components.
+cudaError_t launch_pressure(int nrhs, int64_t nt, const double* g, double* pres, cudaStream_t st);
 cudaError_t launch_contract(int nrhs, int64_t n, const double* a, int64_t sa, const double* b, int64_t sb,
                             const double* c, const double* d, double* out, cudaStream_t st);
 }  // namespace pfmm

@@ -555,6 +555,33 @@ pfmm_status pfmm_execute_host(pfmm_plan* p, void* workspace, size_t ws_bytes, in
   return PFMM_OK;
 }
 
+pfmm_status pfmm_stokes_pressure(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
+                                 const double* f, int64_t nt, const double* trg, double* pres, void* stream) {
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (p->opts.kernel != PFMM_LAPLACE || (p->opts.nrhs & 1))
+    return fail(PFMM_ERR_INVALID_ARG, "the pressure needs a Laplace plan with an even nrhs (2 per Stokes rhs)");
+  if (p->opts.flags & (PFMM_FAR_ONLY | PFMM_NEAR_ONLY | PFMM_NO_GRAD))
+    return fail(PFMM_ERR_INVALID_ARG, "the pressure is defined for the full operator with the gradient");
+  if (ns < 0 || nt < 0 || ns > p->ns_max || nt > p->nt_max)
+    return fail(PFMM_ERR_INVALID_ARG, "ns=%lld nt=%lld outside plan maxima", (long long)ns, (long long)nt);
+  if (!workspace || ws_bytes < p->lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
+  if ((ns > 0 && (!src || !f)) || (nt > 0 && (!trg || !pres))) return fail(PFMM_ERR_INVALID_ARG, "NULL inputs");
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  const bool self = (trg == src) && (nt == ns);
+  // gradient of the nrhs Laplace fields into the adjoint scratch [nrhs][2][nt]
+  double* g = (double*)(ws + p->lay.adj);
+  p->s_stride = ns;
+  p->t_stride = nt;
+  p->o_stride = nt;
+  pfmm_status s = pfmm::execute_cell(p, ws, ns, src, f, nt, trg, nullptr, g, st, self, true, true);
+  if (s != PFMM_OK) return s;
+  cudaError_t e = pfmm::launch_pressure(p->opts.nrhs / 2, nt, g, pres, st);
+  if (e != cudaSuccess) return cuda_fail(e, "pressure kernel");
+  return PFMM_OK;
+}
+
 pfmm_status pfmm_execute_adjoint(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
                                  const double* q, int64_t nt, const double* trg, const double* g,
                                  const double* grad_fwd, double* dq, double* dsrc, double* dtrg, void* stream) {

@@ -282,6 +282,36 @@ class BatchOp:
         return graph, out
 
 
+class StokesPressure:
+    """Pressure of the periodic Stokeslet sum, p = -(d/dx phi[f_x] + d/dy phi[f_y])
+    with phi the periodic Laplace potential (pfmm_stokes_pressure): a Laplace
+    PeriodicOp with 2 * nrhs right-hand sides on the same lattice.
+
+        pres = StokesPressure(e1, e2, tol=1e-6, precision="mixed")(src, f, trg)
+    """
+
+    def __init__(self, e1, e2, tol=1e-6, precision="mixed", path="auto", nrhs=1, ns_max=0, nt_max=0):
+        self.nrhs = int(nrhs)
+        self.op = PeriodicOp("laplace", e1, e2, tol=tol, precision=precision, path=path, nrhs=2 * self.nrhs,
+                             ns_max=ns_max, nt_max=nt_max)
+
+    def __call__(self, src, f, trg=None, out=None, stream=None):
+        import torch
+        tr = src if trg is None else trg
+        ns, nt = src.shape[1], tr.shape[1]
+        if out is None:
+            out = torch.empty((self.nrhs, nt), dtype=torch.float64, device=src.device)
+        ws = self.op.workspace()
+        st = stream if stream is not None else torch.cuda.current_stream(src.device).cuda_stream
+        _lib.check(_lib.lib().pfmm_stokes_pressure(self.op._h, _ptr(ws), ws.numel(), ns, _ptr(src),
+                                                   _ptr(f.contiguous()), nt, _ptr(tr), _ptr(out),
+                                                   ctypes.c_void_p(st)))
+        return out
+
+    def status(self, stream=None):
+        self.op.status(stream)
+
+
 def autotune_batch(make_op, src, q, trg=None, candidates=(1024, 2048, 4096, 8192), reps=2, cache=None, key=None):
     """Pick the P2P source-chunk size of a batch by timing each candidate
     (CUDA events); make_op(p2p_chunk) -> BatchOp.  With a cache path and key,

@@ -213,3 +213,26 @@ def test_nufft_matches_direct(precision, kernel, beta):
     assert np.linalg.norm(cen(a[0]) - cen(b[0])) / np.linalg.norm(cen(tot[0])) < tol
     if not stokes:
         assert np.linalg.norm(a[1] - b[1]) / np.linalg.norm(tot[1]) < tol
+
+
+# ---------------------------------------------------------------------------
+# Stokes pressure (pfmm_stokes_pressure: Laplace gradients of the force components)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+@pytest.mark.parametrize("lat", ["square", "skew", "rotated", "aspect16"])
+def test_stokes_pressure(precision, tol, lat):
+    import torch
+    from oracle import api as oapi
+    from paper_2111_01083_gb300 import StokesPressure
+    e1, e2, src, f, trg = _case("stokes", lat, 900, nt=400, seed=5, nrhs=2)
+    dev = torch.device("cuda", 0)
+    op = StokesPressure(e1, e2, tol=tol, precision=precision, nrhs=2, ns_max=900, nt_max=900)
+    S = torch.tensor(src, device=dev)
+    F = torch.tensor(f, device=dev)
+    T = torch.tensor(trg, device=dev)
+    p = op(S, F, T)
+    torch.cuda.synchronize()
+    op.status()
+    ref = oapi.stokes_pressure(e1, e2, src, f, trg)
+    err = np.linalg.norm(p.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err < tol, err

@@ -226,6 +226,42 @@ def _boundary_targets(e1, e2, n):
     return cell, left, left + A[:, :1], bottom, bottom + A[:, 1:]
 
 
+
+
+def test_stokes_pressure_closes_the_pde():
+    """oracle.api.stokes_pressure (Laplace gradients of the force components)
+    is the pressure of the periodic Stokes flow: with it, -Lap u + grad p = 0
+    away from the sources (4th-order differences), and it is periodic."""
+    e1, e2 = (1.0, 0.0), (0.3, 0.8)
+    n = 12
+    src = _cell_pts(e1, e2, n, 14)
+    f = _q(n, nrhs=1, stokes=True)
+    pts = _away_points(e1, e2, src, 4, 0.12, 15)
+    h = 2e-3
+    d1, d2 = _fd_stencil(h)
+    sh = np.arange(-2, 3) * h
+    P = []
+    for p in pts.T:
+        for s_ in sh:
+            P.append(p + [s_, 0.0])
+        for s_ in sh:
+            P.append(p + [0.0, s_])
+    P = np.array(P).T
+    u, _ = api.evaluate("stokes", 0.0, e1, e2, src, f, P, want_grad=False)
+    p = api.stokes_pressure(e1, e2, src, f, P)
+    u = u[0].reshape(2, -1, 2, 5)
+    p = p[0].reshape(-1, 2, 5)
+    lap = u[:, :, 0, :] @ d2 + u[:, :, 1, :] @ d2
+    gradp = np.stack([p[:, 0, :] @ d1, p[:, 1, :] @ d1])
+    assert np.abs(lap - gradp).max() / np.abs(gradp).max() < 2e-6
+    # periodic: p(t + e1) = p(t), p(t + e2) = p(t)
+    t = pts
+    p0 = api.stokes_pressure(e1, e2, src, f, t)
+    for e in (e1, e2):
+        pe = api.stokes_pressure(e1, e2, src, f, t + np.array(e, float)[:, None])
+        assert np.abs(pe - p0).max() < 1e-10 * np.abs(p0).max()
+
+
 @pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 1.0), ("stokes", 0.0)])
 @pytest.mark.parametrize("e1,e2", [((1, 0), (0, 1)), ((1, 0), (0.3, 0.8)), ((8, 0), (0, 1))])
 def test_method_periodicity(kernel, beta, e1, e2):
