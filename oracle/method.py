@@ -102,7 +102,7 @@ def _scalar_sn(kernel, beta, cell, trg, src, q, eps, part, want_grad):
     return pot, grad
 
 
-def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad):
+def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad, rows=(-1, 0, 1)):
     d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
     lam, w = we_quadrature(cell, beta if kernel == "modhelm" else 0.0, eps)
     nrhs, nt = q.shape[0], trg.shape[1]
@@ -110,7 +110,8 @@ def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad):
         return np.zeros((nrhs, nt)), np.zeros((nrhs, 2, nt)) if want_grad else None
     kap = np.sqrt(lam * lam + beta * beta) if kernel == "modhelm" else lam
     P = m0 + 1
-    B = np.exp(kap * xi - 1j * lam * eta) + 1 + np.exp(-kap * xi + 1j * lam * eta)
+    # rows n of image columns m <= -(m0+1): sum_n e^{n (kappa xi - i lambda eta)}
+    B = sum(np.exp(n * (kap * xi - 1j * lam * eta)) for n in rows)
     F = np.exp(-P * kap * d) / (1 - np.exp(-kap * d))
     D = w / (2 * np.pi * kap) * F * B
     s = 1.0 if part == "west" else -1.0  # east: x -> -x, D -> conj
@@ -168,14 +169,15 @@ def _stokes_sn(cell, trg, src, f, eps, part):
     return vel
 
 
-def _stokes_we(cell, trg, src, f, eps, part):
+def _stokes_we(cell, trg, src, f, eps, part, rows=(-1, 0, 1)):
     d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
     lam, w = we_quadrature(cell, 0.0, eps)
     P = m0 + 1
     z = np.exp(-lam * d)
-    ph1 = np.exp(lam * xi - 1j * lam * eta)
-    phm = np.exp(-lam * xi + 1j * lam * eta)
-    B = phm + 1 + ph1
+    ph = {n: np.exp(n * (lam * xi - 1j * lam * eta)) for n in rows}
+    B = sum(ph.values())
+    # the x-shift n xi of row n enters the coordinate factor: sum_n n xi phi_n
+    dph = xi * sum(n * ph[n] for n in rows)
     Sp = np.zeros((lam.size, 2, 2), complex)
     Sp[:, 0, 0] = -1
     Sp[:, 0, 1] = Sp[:, 1, 0] = 1j
@@ -185,7 +187,7 @@ def _stokes_we(cell, trg, src, f, eps, part):
     Db = (pref * B)[:, None, None] * Sp
     Da = pref[:, None, None] * (
         B[:, None, None] * (I2 / lam[:, None, None] - (P * d + d * z / (1 - z))[:, None, None] * Sp)
-        + (xi * (ph1 - phm))[:, None, None] * Sp
+        + dph[:, None, None] * Sp
     )
     east = part == "east"
     s = -1.0 if east else 1.0
@@ -202,9 +204,12 @@ def _stokes_we(cell, trg, src, f, eps, part):
     return vel
 
 
-def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad=True, chunk=4096):
+def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad=True, chunk=4096,
+              rows=(-1, 0, 1)):
     """Sum of the requested far-field parts at the targets.
-    Returns (pot, grad) for scalar kernels, (vel, None) for stokes."""
+    Returns (pot, grad) for scalar kernels, (vel, None) for stokes.
+    rows: the image rows n of the west/east parts (all three for the doubly
+    periodic sum; (0,) for the singly periodic one)."""
     trg = np.asarray(trg, np.float64)
     src = np.asarray(src, np.float64)
     q = np.asarray(q, np.float64)
@@ -215,16 +220,20 @@ def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad
         for l0 in range(0, nt, chunk):
             t = trg[:, l0:l0 + chunk]
             for p in parts:
-                fn = _stokes_sn if p in ("south", "north") else _stokes_we
-                out[:, :, l0:l0 + chunk] += fn(cell, t, src, q, eps, p)
+                if p in ("south", "north"):
+                    out[:, :, l0:l0 + chunk] += _stokes_sn(cell, t, src, q, eps, p)
+                else:
+                    out[:, :, l0:l0 + chunk] += _stokes_we(cell, t, src, q, eps, p, rows)
         return out, None
     pot = np.zeros((nrhs, nt))
     grad = np.zeros((nrhs, 2, nt)) if want_grad else None
     for l0 in range(0, nt, chunk):
         t = trg[:, l0:l0 + chunk]
         for p in parts:
-            fn = _scalar_sn if p in ("south", "north") else _scalar_we
-            pp, gg = fn(kernel, beta, cell, t, src, q, eps, p, want_grad)
+            if p in ("south", "north"):
+                pp, gg = _scalar_sn(kernel, beta, cell, t, src, q, eps, p, want_grad)
+            else:
+                pp, gg = _scalar_we(kernel, beta, cell, t, src, q, eps, p, want_grad, rows)
             pot[:, l0:l0 + chunk] += pp
             if want_grad:
                 grad[:, :, l0:l0 + chunk] += gg
