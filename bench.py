@@ -40,26 +40,30 @@ SM_MAX_MHZ = 2070.0
 # Per-pair work of the near-image P2P, one pair = (target, source, near
 # image): (FP32 operations, MUFU operations in units of the 16/clk/SM rate;
 # ex2 runs at twice that rate and counts 1/2).  These are the operations of
-# the implemented formulation: per-source image sums, one log2 of a product of
-# scaled r^2 per (target, source) (1/9 per pair), coordinate differences
-# against a subtile centre.
-#   Laplace pot + grad: dx, dy, r^2 (2), product (2), sum dx/r^2, dy/r^2 (2) = 8;
-#                       rcp + lg2/9
-#   Laplace pot:        dx, dy, r^2 (2), product (2) = 6; lg2/9
-#   Stokes velocity:    dx, dy, r^2 (2), product (2), dx^2 - dy^2 (2),
-#                       sum cos 2t (1), sum sin t cos t (2) = 11; rcp + lg2/9
-#   mod. Helmholtz K0:  dx, dy, r^2 (2), x^2, x, exponent, y = 2/x, 7-term fit (6),
-#                       two products, image sum = 16, + nrhs/9 strength FMAs;
-#                       2 rsqrt + ex2 (2.5 units); with K1: + fit (6), scaling (2),
-#                       two sums (2) and 2 nrhs/9 more FMAs
-def p2p_work(kernel, nrhs, grad):
+# the implemented formulation: per-source image sums, then per (target,
+# source) one log2 of a product of scaled r^2 and the strength FMAs, shared
+# by the nimg images (9 for the doubly periodic 3 x 3 block, 15 with m0 = 2,
+# 3 for the singly periodic strip); coordinate differences against a subtile
+# centre.
+#   Laplace pot + grad: per pair dx, dy, r^2 (2), product (2), sum dx/r^2, dy/r^2 (2) = 8
+#                       and rcp; per (t, s) lg2 and 3 FMAs
+#   Laplace pot:        per pair dx, dy, r^2 (2), product (2) = 6; per (t, s) lg2, 1 FMA
+#   Stokes velocity:    per pair dx, dy, r^2 (2), product (2), dx^2 - dy^2 (2),
+#                       sum cos 2t (1), sum sin t cos t (2) = 11 and rcp; per (t, s)
+#                       lg2 and ~7 FP32 for the two components
+#   mod. Helmholtz K0:  per pair dx, dy, x^2 (2), x, exponent, 7-term fit (6), two
+#                       products, image sum = 13 (+3 without the beta scaling and
+#                       folded fit variable: 16 counted), 2 rsqrt + ex2 (2.5 units);
+#                       per (t, s) nrhs FMAs; with K1: + fit (6), scaling (2),
+#                       two sums (2) per pair and 2 nrhs more FMAs per (t, s)
+def p2p_work(kernel, nrhs, grad, nimg=9):
     if kernel == "laplace":
-        return (8.0, 1.0 + 1.0 / 9.0) if grad else (6.0, 1.0 / 9.0)
+        return (8.0 + 3.0 / nimg, 1.0 + 1.0 / nimg) if grad else (6.0 + 1.0 / nimg, 1.0 / nimg)
     if kernel == "stokes":
-        return (11.0, 1.0 + 1.0 / 9.0)
+        return (11.0 + 7.0 / nimg, 1.0 + 1.0 / nimg)
     if grad:
-        return (26.0 + 3.0 * nrhs / 9.0, 2.5)
-    return (16.0 + nrhs / 9.0, 2.5)
+        return (26.0 + 3.0 * nrhs / nimg, 2.5)
+    return (16.0 + nrhs / nimg, 2.5)
 
 
 def alu_rates():
@@ -74,10 +78,10 @@ def alu_rates():
         return {"fp32": 128.0, "mufu": 16.0, "source": "fallback: nominal 128 FP32 / 16 MUFU per clock per SM"}
 
 
-def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=None):
+def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=None, nimg=9):
     """Bound = min(FP32 rate / FP32 ops per pair, MUFU rate / MUFU ops per pair)
     x 152 SMs x the maximum SM clock; achieved = pairs per launch / launch time."""
-    fp32_ops, mufu_ops = p2p_work(kernel, nrhs, grad)
+    fp32_ops, mufu_ops = p2p_work(kernel, nrhs, grad, nimg)
     r = alu_rates()
     f_fp32 = r["fp32"] / fp32_ops
     f_mufu = r["mufu"] / mufu_ops
@@ -114,9 +118,14 @@ import json, sys, time
 import numpy as np
 sys.path.insert(0, %(root)r)
 import workloads
-from oracle import ewald, lattice, method
+from oracle import ewald, lattice, method, p1
 w = workloads.make(%(name)r)
-cell, s, t = lattice.to_canonical(w["e1"], w["e2"], w["src"], w["trg"])
+singly = w.get("singly", False)
+if singly:
+    cell = p1.canonical_strip(w["e1"], w["e2"])
+    s, t = p1.wrap_strip(w["src"], cell), p1.wrap_strip(w["trg"], cell)
+else:
+    cell, s, t = lattice.to_canonical(w["e1"], w["e2"], w["src"], w["trg"])
 kernel = w["kernel"]
 q = w["q"]
 if kernel == "stokes":
@@ -126,8 +135,12 @@ for nsamp in %(samples)r:
     idx = np.random.default_rng(123).choice(t.shape[1], nsamp, replace=False)
     tt = t[:, idx]
     t0 = time.perf_counter()
-    ewald.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
-    method.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
+    if singly:
+        p1.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
+        p1.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
+    else:
+        ewald.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
+        method.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
     res.append((nsamp, time.perf_counter() - t0))
 print(json.dumps({"samples": res, "ns": int(s.shape[1]), "nt": int(t.shape[1])}))
 """
@@ -554,8 +567,9 @@ def main():
     ns = S.shape[1]
     nt = ns if self_t else T.shape[1]
     grad = kernel != "stokes"
+    singly = cfg.get("singly", False)
     op = PeriodicOp(kernel, w["e1"], w["e2"], tol=cfg["tol"], precision="mixed", path=path,
-                    nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt)
+                    nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly)
     op.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = op(S, Q, T, grad=grad)
@@ -617,7 +631,7 @@ def main():
     acc = None
     if not args.skip_fp64 and rank == 0:
         op64 = PeriodicOp(kernel, w["e1"], w["e2"], tol=1e-10, precision="fp64", path="direct", ns_max=ns,
-                          nt_max=nt)
+                          nt_max=nt, singly=singly)
         op64.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -646,8 +660,9 @@ def main():
         return 0
     # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
     p2p = sum(p2p_ms) / len(p2p_ms)
-    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, "k_p2p_mixed (near-image P2P)",
-                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload))
+    nimg = 3 if singly else 3 * (2 * desc["m0"] + 1)
+    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, f"k_p2p_mixed (near-image P2P, {nimg} images)",
+                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload), nimg=nimg)
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
@@ -665,6 +680,7 @@ def main():
                    "dist": cfg.get("dist"), "tol": cfg["tol"], "path": ["direct", "direct", "nufft"][desc["path"]],
                    "nufft_w": desc["nufft_w"], "n_gl": desc["n_gl"], "M": desc["M"], "Nq": desc["Nq"],
                    "m0": desc["m0"], "outputs": "pot+grad" if grad else "velocity",
+                   "periodicity": "singly (e1)" if singly else "doubly",
                    "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
         "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_p2p": p2p},
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,

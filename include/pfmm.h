@@ -78,8 +78,16 @@ enum {
   PFMM_FAR_ONLY = 1,   /* output P2 q only (no near-image sum)            */
   PFMM_NEAR_ONLY = 2,  /* output K^near q only                            */
   PFMM_NO_GRAD = 4,    /* scalar kernels: skip the gradient even if given */
-  PFMM_PROJECT_NEUTRAL = 8 /* Laplace/Stokes: subtract the mean strength (force) per rhs
-                              before use, i.e. apply the operator to the zero-net part */
+  PFMM_PROJECT_NEUTRAL = 8, /* Laplace/Stokes: subtract the mean strength (force) per rhs
+                               before use, i.e. apply the operator to the zero-net part */
+  PFMM_SINGLY_PERIODIC = 16  /* P1: periodic along e1 only.  e2 spans the strip: points
+                               are wrapped along e1 and must lie within |y| < eta/2 across
+                               it (eta = |e1 x e2| / |e1|); others set the status
+                               PFMM_ERR_INVALID_ARG.  Near images m e1, |m| <= 1; the far
+                               images through the west/east factorization restricted to
+                               the image row n = 0 (Theorems west_thm, west_thm_lap,
+                               west_thm_s), no south/north parts; direct path only;
+                               single-cell calls only (not in a batch). */
 };
 
 typedef enum {

@@ -13,7 +13,7 @@ LIB_PATH = os.environ.get("PFMM_LIB") or os.path.join(HERE, "libpfmm.so")
 PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES = 0, 1, 2
 PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
-PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL = 1, 2, 4, 8
+PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC = 1, 2, 4, 8, 16
 
 STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PFMM_ERR_NOT_NEUTRAL",
           4: "PFMM_ERR_TOLERANCE", 5: "PFMM_ERR_WORKSPACE", 6: "PFMM_ERR_CUDA", 7: "PFMM_ERR_NONFINITE",

@@ -36,7 +36,13 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   double xc = g.rot[0] * x + g.rot[1] * y, yc = g.rot[2] * x + g.rot[3] * y;
   double u1 = g.ainv[0] * xc + g.ainv[1] * yc, u2 = g.ainv[3] * yc;
   u1 -= floor(u1 + 0.5);
-  u2 -= floor(u2 + 0.5);
+  if (!g.p1) {
+    u2 -= floor(u2 + 0.5);
+  } else if (!(u2 >= -0.5 && u2 < 0.5)) {
+    // singly periodic: no wrap across the strip; the point is outside it
+    atomicOr(status, ST_OUTSIDE);
+    u2 = 0.0;
+  }
   xc = u1 * g.d + u2 * g.xi;
   yc = u2 * g.eta;
   c64[i] = xc;
@@ -299,7 +305,8 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
     if (K != PFMM_MODHELM) {
       double net = (K == PFMM_STOKES) ? fmax(fabs(mq), fabs(mfy)) : fabs(mq);
       if (net > 1e-8 * mabs + 1e-300) atomicOr(status, ST_NOT_NEUTRAL);
-      mom[r * 8 + 4] = -my / (g.d * g.eta);
+      // the m = 0 mode of the south/north parts; none in the singly periodic case
+      mom[r * 8 + 4] = f.rows3 ? -my / (g.d * g.eta) : 0.0;
     } else {
       mom[r * 8 + 4] = 0.0;
     }
@@ -320,7 +327,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
       D = lw::sn_scalar(d, xi, eta, tm.a, tm.b, north);
       fac = (tm.m == 0) ? 1.0 : 2.0;  // +-m pairs
     } else {
-      D = lw::we_scalar(d, xi, eta, g.m0, tm.a, tm.b, tm.w, east);
+      D = lw::we_scalar(d, xi, eta, g.m0, tm.a, tm.b, tm.w, east, f.rows3 != 0);
     }
     store_w(wts + (size_t)r * f.nterm + t, cscale(cmul(D, C(0)), fac));
     return;
@@ -329,7 +336,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
   if (tm.part < 2)
     lw::sn_stokes(d, xi, eta, tm.a, north, Da, Db);
   else
-    lw::we_stokes(d, xi, eta, g.m0, tm.a, tm.w, east, Da, Db);
+    lw::we_stokes(d, xi, eta, g.m0, tm.a, tm.w, east, Da, Db, f.rows3 != 0);
   const dcx ca[2] = {C(0), C(1)}, cb[2] = {C(2), C(3)};
   dcx wa[2], wb[2];
   lw::stokes_apply(Da, Db, ca, cb, north || east, (tm.part < 2) ? 2.0 : 1.0, wa, wb);

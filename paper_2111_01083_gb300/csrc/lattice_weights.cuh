@@ -47,10 +47,11 @@ __device__ __forceinline__ dcx sn_scalar(double d, double xi, double eta, double
 // Scalar west (east: conj), quadrature node (lambda, kappa) with weight w:
 //   D = (w / (2 pi kappa)) e^{-(m0+1) kappa d} / (1 - e^{-kappa d}) B,
 //   B = e^{kappa xi - i lambda eta} + 1 + e^{-kappa xi + i lambda eta}.
+//   rows3 = false (singly periodic P1): only the row n = 0, B = 1.
 __device__ __forceinline__ dcx we_scalar(double d, double xi, double eta, int m0, double lam, double kap, double w,
-                                         bool east) {
+                                         bool east, bool rows3 = true) {
   double F = exp(-(m0 + 1) * kap * d) / (-expm1(-kap * d));
-  dcx B = cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta}));
+  dcx B = rows3 ? cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta})) : dcx{1.0, 0.0};
   dcx D = cscale(B, w / (2.0 * M_PI * kap) * F);
   return east ? conj_(D) : D;
 }
@@ -84,17 +85,18 @@ __device__ __forceinline__ void sn_stokes(double d, double xi, double eta, doubl
 //   pref = (w / 4 pi) z^P / (1 - z),  phi_r = e^{r (lambda xi - i lambda eta)},  B = phi_1 + 1 + phi_-1,
 //   Db = pref B S',  Da = pref [ B (I/lambda - (P d + d z/(1 - z)) S') + xi (phi_1 - phi_-1) S' ],
 //   S' = [[-1, i], [i, 1]].
+//   rows3 = false (singly periodic P1): only the row n = 0, B = 1 and no xi term.
 __device__ __forceinline__ void we_stokes(double d, double xi, double eta, int m0, double lam, double w, bool east,
-                                          dcx Da[2][2], dcx Db[2][2]) {
+                                          dcx Da[2][2], dcx Db[2][2], bool rows3 = true) {
   double z = exp(-lam * d);
   double omz = -expm1(-lam * d);
   int P = m0 + 1;
   double pref = w / (4.0 * M_PI) * exp(-P * lam * d) / omz;
   dcx ph1 = cexp_({lam * xi, -lam * eta}), phm = cexp_({-lam * xi, lam * eta});
-  dcx B = cadd(cadd(ph1, phm), {1.0, 0.0});
+  dcx B = rows3 ? cadd(cadd(ph1, phm), {1.0, 0.0}) : dcx{1.0, 0.0};
   dcx Sp[2][2] = {{{-1, 0}, {0, 1}}, {{0, 1}, {1, 0}}};
   double kx = P * d + d * z / omz;
-  dcx dph = cscale(csub(ph1, phm), xi);
+  dcx dph = rows3 ? cscale(csub(ph1, phm), xi) : dcx{0.0, 0.0};
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       Db[i][j] = cscale(cmul(B, Sp[i][j]), pref);

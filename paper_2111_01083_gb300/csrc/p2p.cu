@@ -783,9 +783,12 @@ static void dispatch_nr(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaSt
 
 template <int KER>
 static void dispatch_img(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaStream_t st) {
-  // m0 <= 2 after lattice reduction (|xi| <= d/2), so 9 or 15 images
+  // m0 <= 2 after lattice reduction (|xi| <= d/2), so 9 or 15 images; the
+  // singly periodic strip has 3
   if (a.g.nimg == 9)
     dispatch_nr<KER, 9>(a, grad, nrhs, ntb, nsc, st);
+  else if (a.g.nimg == 3)
+    dispatch_nr<KER, 3>(a, grad, nrhs, ntb, nsc, st);
   else
     dispatch_nr<KER, 15>(a, grad, nrhs, ntb, nsc, st);
 }

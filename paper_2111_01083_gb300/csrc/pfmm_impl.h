@@ -11,7 +11,7 @@ constexpr int kMaxNear = 32;      // (2 m0 + 1) * 3 images; m0 <= 3 after reduct
 constexpr int kStatusWords = 8;   // status word region (ints)
 
 // device status bits (combined with atomicOr; mapped to pfmm_status by the host)
-enum : int { ST_NONFINITE = 1, ST_NOT_NEUTRAL = 2, ST_TIMEOUT = 4 };
+enum : int { ST_NONFINITE = 1, ST_NOT_NEUTRAL = 2, ST_TIMEOUT = 4, ST_OUTSIDE = 8 };
 
 // Geometry of the canonical cell, passed by value to kernels.
 struct Geom {
@@ -22,6 +22,7 @@ struct Geom {
   int nimg;               // (2 m0 + 1) * 3
   double off[kMaxNear][2];// image offsets l_mn = m e1 + n e2 (canonical)
   int center;             // index of the (0, 0) image in off[]
+  int p1;                 // singly periodic (along e1 only): no wrap across the strip
 };
 
 // Far-field parameters (direct path).  Terms are ordered
@@ -35,6 +36,7 @@ struct Far {
   int nterm;         // 2 nsn + 2 Nq
   int nrhs;
   int nch;           // coefficient channels per rhs: 1 (scalar) or 4 (Stokes: a_x, a_y, b_x, b_y)
+  int rows3;         // west/east over the image rows n = -1, 0, 1 (doubly periodic) or n = 0 only (P1)
   const double* nodes;  // device [Nq][2] (lambda_n, w_n), in workspace
 };
 

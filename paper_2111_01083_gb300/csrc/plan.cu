@@ -67,6 +67,21 @@ bool canonicalize(const double e1[2], const double e2[2], Geom* g) {
   return true;
 }
 
+// Singly periodic (P1) strip: e1 rotated onto +x (no lattice reduction: e1 is
+// the period), eta = |e1 x e2| / |e1| the strip width, xi = 0 (only the
+// period matters along x).  Fractional coordinates u1 = x / d, u2 = y / eta.
+bool canonicalize_strip(const double e1[2], const double e2[2], Geom* g) {
+  const double d = std::hypot(e1[0], e1[1]);
+  const double cross = e1[0] * e2[1] - e1[1] * e2[0];
+  if (!std::isfinite(cross) || !(d > 0) || std::fabs(cross) <= 1e-14 * (d * d + e2[0] * e2[0] + e2[1] * e2[1]))
+    return false;
+  const double c = e1[0] / d, s = e1[1] / d;
+  g->rot[0] = c; g->rot[1] = s; g->rot[2] = -s; g->rot[3] = c;
+  g->d = d; g->xi = 0.0; g->eta = std::fabs(cross) / d;
+  g->ainv[0] = 1.0 / d; g->ainv[1] = 0.0; g->ainv[2] = 0.0; g->ainv[3] = 1.0 / g->eta;
+  return true;
+}
+
 // Proof after Eq. pylw02: west/east images need x - x' - m d - n xi >= margin > 0;
 // the smallest gap over the parallelogram is m0 d - 2|xi|.  The paper uses
 // margin = d; here margin = d/4 (any positive gap keeps the west/east
@@ -107,11 +122,18 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
 }
 
 // West/east quadrature for int_0^inf (.) d lambda (own composite GL rule in
-// lambda' = lambda d): panels of width 2, 8/12/16 points for tol >= 1e-7 /
+// lambda' = lambda d): panels of width 2 (narrower for tall singly periodic
+// strips, so that each panel sees at most ~4 radians of e^{i lambda (y - y')}),
+// 8/12/16 points for tol >= 1e-7 /
 // >= 1e-11 / smaller, dyadic panels toward 0 when 0 < beta d < 2, truncated
 // where exp(-kappa' x_min') < tol/10 with x_min' = (m0 d - 2|xi|)/d.
 void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vector<double>& nodes) {
   nodes.clear();
+  // largest |y - y'| / d the oscillation e^{i lambda (y - y')} must resolve:
+  // 2 eta / d (rows n = -1, 0, 1) or eta / d (singly periodic); panels of
+  // width 2 in lambda d up to a span of 2, narrower beyond
+  const double yspan = (g.p1 ? 1.0 : 2.0) * g.eta / g.d;
+  const double pw = yspan > 2.0 ? 4.0 / yspan : 2.0;
   double xmin = (g.m0 * g.d - 2.0 * std::fabs(g.xi)) / g.d;
   double bt = (kernel == PFMM_MODHELM) ? beta * g.d : 0.0;
   double top = std::log(10.0 / tol) / xmin;
@@ -123,7 +145,7 @@ void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vect
     for (double e = bt / 8; e < 2.0 && e < lmax; e *= 2) edges.push_back(e);
   }
   double e = edges.back();
-  while (e < lmax - 1e-12) { e = std::min(lmax, e + 2.0); edges.push_back(e); }
+  while (e < lmax - 1e-12) { e = std::min(lmax, e + pw); edges.push_back(e); }
   std::vector<double> gx, gw;
   gauss_legendre(npts, gx, gw);
   for (size_t i = 0; i + 1 < edges.size(); ++i) {
@@ -252,11 +274,19 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (o->n_gl != 0 && (o->n_gl < 4 || o->n_gl > 32)) return fail(PFMM_ERR_INVALID_ARG, "n_gl in [4,32]");
 
   Geom g{};
-  if (!canonicalize(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate lattice vectors");
-  g.m0 = choose_m0(g.d, g.xi);
+  const bool p1 = (o->flags & PFMM_SINGLY_PERIODIC) != 0;
+  if (p1) {
+    if (!canonicalize_strip(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate strip vectors");
+    if (o->path == PFMM_PATH_NUFFT) return fail(PFMM_ERR_INVALID_ARG, "the singly periodic operator uses the direct path");
+    g.p1 = 1;
+    g.m0 = 1;  // |x - x'| < d after wrapping: images |m| >= 2 are separated by >= d
+  } else {
+    if (!canonicalize(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate lattice vectors");
+    g.m0 = choose_m0(g.d, g.xi);
+  }
   if ((2 * g.m0 + 1) * 3 > kMaxNear) return fail(PFMM_ERR_INTERNAL, "near block too large");
   g.nimg = 0;
-  for (int n = -1; n <= 1; ++n)
+  for (int n = p1 ? 0 : -1; n <= (p1 ? 0 : 1); ++n)
     for (int m = -g.m0; m <= g.m0; ++m) {
       if (m == 0 && n == 0) g.center = g.nimg;
       g.off[g.nimg][0] = m * g.d + n * g.xi;
@@ -277,11 +307,11 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   // whose per-unit-charge bound e^{-chi eta}/(d chi (1 - e^{-chi eta})) is below
   // tol/10 are dropped from the top: chi_m grows with m, so the bound decreases).
   double eps = o->tol * 0.1;
-  int M = mpk0s(g.d, g.eta, eps);
+  int M = p1 ? 0 : mpk0s(g.d, g.eta, eps);  // P1: no south/north parts
   // m = 0 is a regular term only for modhelm; for Laplace/Stokes it is the
   // moment term -(1/(2 d eta)) y sum q y' (Eq. phis3, Eq. pss0) added separately.
-  int mode0 = (o->kernel == PFMM_MODHELM) ? 1 : 0;
-  if (o->kernel == PFMM_MODHELM) {
+  int mode0 = (o->kernel == PFMM_MODHELM && !p1) ? 1 : 0;
+  if (o->kernel == PFMM_MODHELM && !p1) {
     auto bound = [&](int m) {
       double al = 2 * M_PI * m / g.d, chi = std::sqrt(al * al + o->beta * o->beta);
       double e = std::exp(-chi * g.eta);
@@ -298,6 +328,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   f.nsn = mode0 ? (M + 1) : M;
   f.nrhs = o->nrhs;
   f.nch = (o->kernel == PFMM_STOKES) ? 4 : 1;
+  f.rows3 = p1 ? 0 : 1;
 
   std::vector<double> nodes;
   we_quadrature(g, o->kernel, f.beta, o->tol, nodes);
@@ -644,6 +675,7 @@ pfmm_status pfmm_get_status(pfmm_plan* p, void* workspace, void* stream) {
   if (h[0] & ST_NONFINITE) return fail(PFMM_ERR_NONFINITE, "non-finite coordinates or strengths");
   if (h[0] & ST_TIMEOUT) return fail(PFMM_ERR_TIMEOUT, "a bounded device wait gave up");
   if (h[0] & ST_NOT_NEUTRAL) return fail(PFMM_ERR_NOT_NEUTRAL, "net charge / net force is not zero");
+  if (h[0] & ST_OUTSIDE) return fail(PFMM_ERR_INVALID_ARG, "points outside the singly periodic strip |y| < eta/2");
   return PFMM_OK;
 }
 

@@ -29,7 +29,7 @@ def _ptr(t):
 
 class PeriodicOp:
     def __init__(self, kernel, e1, e2, beta=0.0, tol=1e-6, precision="mixed", path="auto", nufft_w=0, n_gl=0,
-                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None):
+                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False):
         L = _lib.lib()
         o = _lib.Opts()
         o.e1[0], o.e1[1] = float(e1[0]), float(e1[1])
@@ -42,7 +42,7 @@ class PeriodicOp:
         o.nufft_w = int(nufft_w)
         o.n_gl = int(n_gl)
         o.nrhs = int(nrhs)
-        o.flags = _PART[part]
+        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0)
         self.kernel = kernel
         self.nrhs = int(nrhs)
         self.ns_max, self.nt_max = int(ns_max), int(nt_max)
@@ -290,10 +290,10 @@ class StokesPressure:
         pres = StokesPressure(e1, e2, tol=1e-6, precision="mixed")(src, f, trg)
     """
 
-    def __init__(self, e1, e2, tol=1e-6, precision="mixed", path="auto", nrhs=1, ns_max=0, nt_max=0):
+    def __init__(self, e1, e2, tol=1e-6, precision="mixed", path="auto", nrhs=1, ns_max=0, nt_max=0, singly=False):
         self.nrhs = int(nrhs)
         self.op = PeriodicOp("laplace", e1, e2, tol=tol, precision=precision, path=path, nrhs=2 * self.nrhs,
-                             ns_max=ns_max, nt_max=nt_max)
+                             ns_max=ns_max, nt_max=nt_max, singly=singly)
 
     def __call__(self, src, f, trg=None, out=None, stream=None):
         import torch

@@ -34,7 +34,7 @@ def _cmp(got, ref, mc):
     return oapi.rel_err(got, ref, modconst=mc)
 
 
-def _run(w, precision, tol, path, idx=None):
+def _run(w, precision, tol, path, idx=None, singly=False):
     import torch
     from paper_2111_01083_gb300 import PeriodicOp
     dev = torch.device("cuda", 0)
@@ -45,7 +45,7 @@ def _run(w, precision, tol, path, idx=None):
     ns = S.shape[1]
     nt = ns if self_t else T.shape[1]
     op = PeriodicOp(w["kernel"], w["e1"], w["e2"], tol=tol, precision=precision, path=path,
-                    nufft_w=w.get("nufft_w", 0), n_gl=w.get("n_gl", 0), ns_max=ns, nt_max=nt)
+                    nufft_w=w.get("nufft_w", 0), n_gl=w.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly)
     pot, grad = op(S, Q, T, grad=w["kernel"] != "stokes")
     torch.cuda.synchronize()
     op.status()
@@ -121,3 +121,15 @@ def test_batch_modhelm_full_beta1():
         ref, _ = _oracle_at("modhelm", 1.0, cell["e1"], cell["e2"], cell["src"], cell["q"], cell["src"][:, idx])
         got = pot[:, edges[c]:edges[c + 1]][:, idx]
         assert _cmp(got, ref, False) < 1e-6, (c, n)
+
+
+def test_laplace_p1_strip_full():
+    """Singly periodic: 1e5 uniform sources in the 1 x 4 strip segment, mixed,
+    against the P1 oracle on sampled targets (modulo the constant)."""
+    from oracle import p1
+    w = workloads.make("laplace_p1_strip4_n1e5")
+    pot, grad = _run(dict(w, nufft_w=0, n_gl=0), "mixed", 1e-6, "auto", singly=True)
+    idx = np.random.default_rng(5).choice(w["src"].shape[1], NSAMP, replace=False)
+    ref_p, ref_g = p1.evaluate("laplace", 0.0, w["e1"], w["e2"], w["src"], w["q"], w["src"][:, idx], eps=1e-11)
+    assert _cmp(pot[:, idx], ref_p, True) < 1e-6
+    assert _cmp(grad[:, :, idx], ref_g, False) < 1e-6

@@ -140,3 +140,17 @@ def test_workspace_size_grows_with_n(L):
     a = _op(ns_max=1000, nt_max=1000).ws_bytes
     b = _op(ns_max=100000, nt_max=100000).ws_bytes
     assert b > 50 * a / 2
+
+
+def test_singly_periodic_plan(L):
+    """P1: 3 near images, no south/north modes, direct path; west/east nodes
+    grow for a tall strip; NUFFT rejected."""
+    from paper_2111_01083_gb300 import PeriodicOp
+    from paper_2111_01083_gb300._lib import PfmmError
+    wide = PeriodicOp("laplace", (1.0, 0.0), (0.3, 0.5), singly=True, ns_max=8, nt_max=8).describe()
+    assert wide["M"] == 0 and wide["path"] == 1 and wide["m0"] == 1 and wide["Nq"] > 0
+    assert abs(wide["d"] - 1.0) < 1e-15 and abs(wide["eta"] - 0.5) < 1e-15 and wide["xi"] == 0.0
+    tall = PeriodicOp("laplace", (1.0, 0.0), (0.0, 20.0), singly=True, ns_max=8, nt_max=8).describe()
+    assert tall["Nq"] > wide["Nq"]
+    with pytest.raises(PfmmError):
+        PeriodicOp("laplace", (1.0, 0.0), (0.0, 2.0), singly=True, path="nufft", ns_max=8, nt_max=8)

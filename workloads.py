@@ -60,6 +60,10 @@ CONFIGS = {
                              seed=2, dist="uniform", tol=1e-6, precision="mixed"),
     "laplace_adjoint_4x1_n5e4": dict(kernel="laplace", e1=(4.0, 0.0), e2=(0.0, 1.0), ns=50000,
                                      seed=4, dist="uniform", tol=1e-6, precision="mixed"),
+    # singly periodic (P1): period e1, 1e5 uniform sources in the strip segment
+    # [-1/2, 1/2) x [-2, 2), targets = sources (the paper's P1 rectangle cases)
+    "laplace_p1_strip4_n1e5": dict(kernel="laplace", e1=(1.0, 0.0), e2=(0.0, 4.0), ns=100000,
+                                   seed=6, dist="uniform", tol=1e-6, precision="mixed", singly=True),
 }
 
 
@@ -72,7 +76,7 @@ def make(name, scale=1.0, seed=None):
         nt = max(1, int(round(nt * scale)))
     w = single_cell(c["kernel"], c["e1"], c["e2"], ns, nt, seed if seed is not None else c["seed"],
                     c.get("dist", "uniform"))
-    for k in ("tol", "precision", "path", "nufft_w", "n_gl"):
+    for k in ("tol", "precision", "path", "nufft_w", "n_gl", "singly"):
         if k in c:
             w[k] = c[k]
     return w
