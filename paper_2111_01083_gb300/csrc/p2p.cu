@@ -441,13 +441,14 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   // source's in shared memory), so x^2 = dx^2 + dy^2 and K1(x)/x multiplies
   // the scaled difference directly; the fits' variable y = 2/x is folded into
   // their coefficients (c_k 2^k).  ALL: every image active, no per-image test.
-  auto source_far = [&](int jj, unsigned any, float p0, float p1, auto all_tag) {
+  auto source_far = [&](int jj, unsigned any, auto diff, auto all_tag) {
     constexpr bool ALL = decltype(all_tag)::value;
     float K0s = 0.f, K1x = 0.f, K1y = 0.f;
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
       if (!ALL && !(any & (1u << i))) continue;
-      const float dx = txb[i] - p0, dy = tyb[i] - p1;
+      float dx, dy;
+      diff(i, dx, dy);
       const float x2 = fmaf(dx, dx, dy * dy);
       const float ix = bes::mufu::rsqrt(x2);
       const float x = x2 * ix;
@@ -569,14 +570,27 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
 #pragma unroll 2
           for (int jj = js; jj < js + kP2PSub; ++jj) {
             const float2 p = s_pb[jj];
-            source_far(jj, any, p.x, p.y, std::true_type{});
+            source_far(jj, any, [&](int i, float& dx, float& dy) { dx = txb[i] - p.x; dy = tyb[i] - p.y; },
+                       std::true_type{});
           }
         } else {
 #pragma unroll 2
           for (int jj = js; jj < js + kP2PSub; ++jj) {
             const float2 p = s_pb[jj];
-            source_far(jj, any, p.x, p.y, std::false_type{});
+            source_far(jj, any, [&](int i, float& dx, float& dy) { dx = txb[i] - p.x; dy = tyb[i] - p.y; },
+                       std::false_type{});
           }
+        }
+      } else if (!__any_sync(0xffffffffu, small)) {
+        // close pairs but none with beta r <= 2: exact differences (beta-scaled),
+        // the branch-free large-argument fit
+#pragma unroll 1
+        for (int jj = js; jj < js + kP2PSub; ++jj) {
+          const float4 h = s_h[jj];
+          source_far(jj, any, [&](int i, float& dx, float& dy) {
+            dx = beta * ((thx[i] - h.x) + (tlx[i] - h.y));
+            dy = beta * ((thy[i] - h.z) + (tly[i] - h.w));
+          }, std::false_type{});
         }
       } else {
         // close pairs or beta r <= 2 in reach: exact differences, both K0 fits
