@@ -20,11 +20,13 @@ def _rot_vec(rotT, v):
 
 
 def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1e-14,
-             want_grad=True, margin_frac=0.25):
+             want_grad=True, margin_frac=0.25, we="axis"):
+    """we: west/east plane-wave direction, "axis", "rotated" (App. A) or
+    "auto" (lattice.choose_we); it sets m0 and so the near/far split."""
     src = np.asarray(src, np.float64)
     trg = np.asarray(trg, np.float64)
     q = np.asarray(q, np.float64)
-    cell, s, t = lattice.to_canonical(e1, e2, src, trg, margin_frac)
+    cell, s, t = lattice.to_canonical(e1, e2, src, trg, margin_frac, we)
     rot = cell["rot"]
     if kernel == "stokes":
         q = np.einsum("ij,rjn->rin", rot, q)
@@ -49,7 +51,7 @@ def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1
     return pot, (_rot_vec(rot.T, grad) if want_grad else None)
 
 
-def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.25):
+def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.25, we="axis"):
     """Pressure of the periodic Stokeslet sum, input frame, [nrhs][nt].
 
     The free-space Stokeslet of this normalisation, u = (1/4pi)(-log r I +
@@ -62,7 +64,7 @@ def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.2
     f = np.asarray(f, np.float64)
     nrhs = f.shape[0]
     q = f.reshape(2 * nrhs, -1)  # [r][c][n] -> rows (r, c)
-    _, g = evaluate("laplace", 0.0, e1, e2, src, q, trg, how=how, eps=eps, margin_frac=margin_frac)
+    _, g = evaluate("laplace", 0.0, e1, e2, src, q, trg, how=how, eps=eps, margin_frac=margin_frac, we=we)
     g = g.reshape(nrhs, 2, 2, -1)  # [r][c][component][n]
     return -(g[:, 0, 0] + g[:, 1, 1])
 

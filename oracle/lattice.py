@@ -79,11 +79,24 @@ def near_offsets(d, xi, eta, m0):
     return np.array(out)
 
 
-def to_canonical(e1, e2, src, trg, margin_frac=0.25):
+def choose_we(d, xi, we="axis", margin_frac=0.25):
+    """West/east plane-wave direction and m0.  "axis": decay along e1 with m0
+    from choose_m0; "rotated": decay along e2-perp (App. A), m0 = 1 for any
+    cell; "auto": rotated exactly when the axis direction would need m0 >= 2.
+    Returns (we_rot, m0)."""
+    if we not in ("axis", "rotated", "auto"):
+        raise ValueError("we must be axis, rotated or auto")
+    m0 = choose_m0(d, xi, margin_frac)
+    rot = we == "rotated" or (we == "auto" and m0 >= 2)
+    return rot, (1 if rot else m0)
+
+
+def to_canonical(e1, e2, src, trg, margin_frac=0.25, we="axis"):
     """Canonicalise the lattice and wrap sources/targets given in the input
-    frame ([2, n] arrays).  Returns (cell dict incl. m0, src_c, trg_c)."""
+    frame ([2, n] arrays).  Returns (cell dict incl. m0 and we_rot, src_c,
+    trg_c)."""
     cell = canonicalize(e1, e2)
-    cell["m0"] = choose_m0(cell["d"], cell["xi"], margin_frac)
+    cell["we_rot"], cell["m0"] = choose_we(cell["d"], cell["xi"], we, margin_frac)
     R = cell["rot"]
     s = wrap(R @ np.asarray(src, np.float64), cell["d"], cell["xi"], cell["eta"])
     t = wrap(R @ np.asarray(trg, np.float64), cell["d"], cell["xi"], cell["eta"])

@@ -24,13 +24,22 @@ stokes   south: Theorem south_thm_s (Eqs. pssm, pss0, lowranksouth3s),
          the whole real line are written as 2 Re of the half line, so the
          half-line prefactor is 1/(4 pi).  Same (L - 1)/(R - 1) gauge.
 
+West/east frame (App. A).  By default the west/east plane waves decay
+along x (e1).  With cell["we_rot"] they decay along x~ = e2-perp instead:
+coordinates (x~, y~) = (c x - s y, s x + c y) with c = eta/|e2|, s = xi/|e2|,
+in which e2 = (0, |e2|) and e1 = (d c, d s) (Eq. k0west2).  The geometric sum
+over the image columns m <= -(m0+1) then has the complex ratio
+e^{-(kappa d c - i lambda d s)}, the rows n = -1, 0, 1 shift only y~, and
+m0 = 1 suffices for every parallelogram (smallest gap d c).  Stokes: forces
+are rotated into the frame and velocities back; scalar gradients likewise.
+
 Modes: M from Eq. mpk0s.  West/east quadrature: this oracle's own,
 deliberately over-resolved composite Gauss-Legendre rule in lambda' = lambda d
-(panels of width 1/2, 20 points each, dyadic panels toward 0 when
-beta d < 1, truncated where exp(-kappa' x_min') < eps e^-8 with
-x_min' = (m0 d - 2|xi|)/d the smallest scaled west/east gap).  The paper's
-precomputed GGQ tables are not printed, so any accurate rule is a valid
-reading.
+(panels of width 1/2, narrower when the oscillation span exceeds 2d, 20
+points each, dyadic panels toward 0 when beta d < 1, truncated where
+exp(-kappa' x_min') < eps e^-8 with x_min' the smallest scaled west/east gap).
+The paper's precomputed GGQ tables are not printed, so any accurate rule is a
+valid reading.
 """
 import math
 import numpy as np
@@ -44,10 +53,38 @@ def mpk0s(d, eta, eps):
     return int(math.ceil((d / (2 * math.pi * eta)) * math.log(1.0 / ((1.0 - math.exp(-r)) * eps))))
 
 
+def we_frame(cell):
+    """West/east frame: rotation (c, s) to (x~, y~), the image-column step
+    (dx, dy) and row step (xr, yr) in that frame, the smallest gap x - x' -
+    (image x) over the far columns, and the largest lambda-frequency of the
+    integrand (|y~ - y~'| + row shifts + the phase of the first far column)."""
+    d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
+    if not cell.get("we_rot", False):
+        return dict(c=1.0, s=0.0, dx=d, dy=0.0, xr=xi, yr=eta, gap=m0 * d - 2 * abs(xi), freq=2 * eta)
+    h = math.hypot(xi, eta)
+    c, s = eta / h, xi / h
+    dx, dy = d * c, d * s
+    # x~ of a point in the cell spans exactly dx (e2 has no x~ part)
+    return dict(c=c, s=s, dx=dx, dy=dy, xr=0.0, yr=h, gap=m0 * dx,
+                freq=2 * h + (m0 + 2) * abs(dy))
+
+
+def _to_frame(fr, pts):
+    return np.stack([fr["c"] * pts[0] - fr["s"] * pts[1], fr["s"] * pts[0] + fr["c"] * pts[1]])
+
+
+def _from_frame(fr, v):
+    # v[..., 2, n] in the frame -> canonical (the transpose rotation)
+    c, s = fr["c"], fr["s"]
+    return np.stack([c * v[..., 0, :] + s * v[..., 1, :], -s * v[..., 0, :] + c * v[..., 1, :]], axis=-2)
+
+
 def we_quadrature(cell, beta, eps, width=0.5, npts=20):
     """Nodes lambda_n > 0 and weights w_n for int_0^inf (.) d lambda."""
-    d, xi = cell["d"], cell["xi"]
-    xmin = (cell["m0"] * d - 2 * abs(xi)) / d
+    d = cell["d"]
+    fr = we_frame(cell)
+    xmin = fr["gap"] / d
+    width = width * min(1.0, 2.0 * d / fr["freq"])
     bt = beta * d
     top = (math.log(1.0 / eps) + 8.0) / xmin
     if top <= bt:
@@ -103,16 +140,20 @@ def _scalar_sn(kernel, beta, cell, trg, src, q, eps, part, want_grad):
 
 
 def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad, rows=(-1, 0, 1)):
-    d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
+    m0 = cell["m0"]
+    fr = we_frame(cell)
     lam, w = we_quadrature(cell, beta if kernel == "modhelm" else 0.0, eps)
     nrhs, nt = q.shape[0], trg.shape[1]
     if lam.size == 0:
         return np.zeros((nrhs, nt)), np.zeros((nrhs, 2, nt)) if want_grad else None
+    trg, src = _to_frame(fr, trg), _to_frame(fr, src)
     kap = np.sqrt(lam * lam + beta * beta) if kernel == "modhelm" else lam
     P = m0 + 1
-    # rows n of image columns m <= -(m0+1): sum_n e^{n (kappa xi - i lambda eta)}
-    B = sum(np.exp(n * (kap * xi - 1j * lam * eta)) for n in rows)
-    F = np.exp(-P * kap * d) / (1 - np.exp(-kap * d))
+    # rows n of image columns m <= -(m0+1): sum_n e^{n (kappa xr - i lambda yr)}
+    B = sum(np.exp(n * (kap * fr["xr"] - 1j * lam * fr["yr"])) for n in rows)
+    # columns: sum_{p >= P} e^{-p g}, g = kappa dx - i lambda dy
+    g = kap * fr["dx"] - 1j * lam * fr["dy"]
+    F = np.exp(-P * g) / (1 - np.exp(-g))
     D = w / (2 * np.pi * kap) * F * B
     s = 1.0 if part == "west" else -1.0  # east: x -> -x, D -> conj
     if part == "east":
@@ -128,7 +169,7 @@ def _scalar_we(kernel, beta, cell, trg, src, q, eps, part, want_grad, rows=(-1, 
     if want_grad:
         gx = ((wv * (-s * kap)) @ L.T).real
         gy = ((wv * (1j * lam)) @ L.T).real
-        grad = np.stack([gx, gy], axis=1)
+        grad = _from_frame(fr, np.stack([gx, gy], axis=1))
     return pot, grad
 
 
@@ -170,14 +211,19 @@ def _stokes_sn(cell, trg, src, f, eps, part):
 
 
 def _stokes_we(cell, trg, src, f, eps, part, rows=(-1, 0, 1)):
-    d, xi, eta, m0 = cell["d"], cell["xi"], cell["eta"], cell["m0"]
+    m0 = cell["m0"]
+    fr = we_frame(cell)
     lam, w = we_quadrature(cell, 0.0, eps)
+    trg, src = _to_frame(fr, trg), _to_frame(fr, src)
+    f = _to_frame(fr, f.transpose(1, 0, 2)).transpose(1, 0, 2)  # [r][c][n] forces in the frame
+    d = fr["dx"]
     P = m0 + 1
-    z = np.exp(-lam * d)
-    ph = {n: np.exp(n * (lam * xi - 1j * lam * eta)) for n in rows}
+    # column ratio (complex when the columns also shift y~)
+    z = np.exp(-lam * fr["dx"] + 1j * lam * fr["dy"])
+    ph = {n: np.exp(n * (lam * fr["xr"] - 1j * lam * fr["yr"])) for n in rows}
     B = sum(ph.values())
-    # the x-shift n xi of row n enters the coordinate factor: sum_n n xi phi_n
-    dph = xi * sum(n * ph[n] for n in rows)
+    # the x-shift n xr of row n enters the coordinate factor: sum_n n xr phi_n
+    dph = fr["xr"] * sum(n * ph[n] for n in rows)
     Sp = np.zeros((lam.size, 2, 2), complex)
     Sp[:, 0, 0] = -1
     Sp[:, 0, 1] = Sp[:, 1, 0] = 1j
@@ -201,7 +247,7 @@ def _stokes_we(cell, trg, src, f, eps, part, rows=(-1, 0, 1)):
     wa = np.einsum("mij,rjm->rim", Da, ca) + s * np.einsum("mij,rjm->rim", Db, cb)
     wb = np.einsum("mij,rjm->rim", Db, ca)
     vel = np.einsum("lm,rim->ril", L - 1.0, wa).real - s * trg[0][None, None, :] * np.einsum("lm,rim->ril", L, wb).real
-    return vel
+    return _from_frame(fr, vel)
 
 
 def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad=True, chunk=4096,

@@ -7,6 +7,9 @@
 * Stokes: the periodic velocity solves -Lap u + grad p = 0 and div u = 0 away
   from the sources, with p built from the (theta-pinned) Laplace gradient
   (pressurelet p = (1/2pi) f.r/|r|^2 = -f.grad G_Laplace, Sec. 5.2).
+* Rotated west/east direction (App. A): each rotated part vs its brute-force
+  image sum (modified Helmholtz), Laplace and Stokes vs Ewald, planted
+  mistakes (column phase dropped, rotation transposed) caught.
 * Ewald: independence of the splitting parameter tau.
 * Method invariants: periodicity across cell edges (the paper's own error
   metric, Sec. 7), symmetry of P2, gradient = derivative of potential,
@@ -142,6 +145,83 @@ def test_method_matches_ewald_stokes(e1, e2):
     ve, _ = api.evaluate("stokes", 0.0, e1, e2, src, f, trg, part="far", how="ewald")
     vm, _ = api.evaluate("stokes", 0.0, e1, e2, src, f, trg, part="far", how="plain")
     assert api.rel_err(vm, ve, modconst=True) < 1e-12
+
+
+HEX = ((1.0, 0.0), (0.5, math.sqrt(3) / 2))
+ROT_CELLS = [HEX, ((1, 0), (0.42, 0.5)), ((2, 0), (0.9, 1.1)), ((1, 0), (0.3, 0.8))]
+
+
+@pytest.mark.parametrize("e1,e2", ROT_CELLS)
+@pytest.mark.parametrize("part", ["west", "east"])
+def test_rotated_we_parts_match_brute_modhelm(e1, e2, part):
+    """App. A (Eq. k0west2): west/east plane waves decaying along e2-perp with
+    m0 = 1, each part against its own absolutely convergent image sum over
+    m <= -2 (m >= 2), |n| <= 1."""
+    beta = 1.5
+    src = _cell_pts(e1, e2, 30, 40)
+    trg = _cell_pts(e1, e2, 20, 41)
+    q = np.random.default_rng(4).standard_normal((2, 30))
+    cell, s, t = lattice.to_canonical(e1, e2, src, trg, we="rotated")
+    assert cell["we_rot"] and cell["m0"] == 1
+    pb, gb = brute.modhelm_part(cell, beta, t, s, q, part)
+    pm, gm = method.far_field("modhelm", beta, cell, t, s, q, parts=(part,))
+    assert np.linalg.norm(pm - pb) / np.linalg.norm(pb) < 1e-11
+    assert np.linalg.norm(gm - gb) / np.linalg.norm(gb) < 1e-11
+
+
+@pytest.mark.parametrize("e1,e2", ROT_CELLS)
+def test_rotated_method_matches_ewald(e1, e2):
+    """Laplace (potential up to a constant, gradient) and Stokes with the
+    rotated west/east direction against the Ewald definition of P2 for the
+    3 x 3 near block."""
+    src = _cell_pts(e1, e2, 40, 42)
+    trg = _cell_pts(e1, e2, 25, 43)
+    q = _q(40, seed=5)
+    f = _q(40, seed=6, stokes=True)
+    pe, ge = api.evaluate("laplace", 0.0, e1, e2, src, q, trg, part="far", how="ewald", we="rotated")
+    pm, gm = api.evaluate("laplace", 0.0, e1, e2, src, q, trg, part="far", how="plain", we="rotated")
+    assert api.rel_err(pm, pe, modconst=True) < 1e-12
+    assert api.rel_err(gm, ge) < 1e-12
+    ve, _ = api.evaluate("stokes", 0.0, e1, e2, src, f, trg, part="far", how="ewald", we="rotated")
+    vm, _ = api.evaluate("stokes", 0.0, e1, e2, src, f, trg, part="far", how="plain", we="rotated")
+    assert api.rel_err(vm, ve, modconst=True) < 1e-12
+
+
+def test_rotated_direction_rule():
+    d, xi = 1.0, 0.5  # hexagonal cell: the axis direction needs m0 = 2
+    assert lattice.choose_we(d, xi, "axis") == (False, 2)
+    assert lattice.choose_we(d, xi, "auto") == (True, 1)
+    assert lattice.choose_we(d, 0.3, "auto") == (False, 1)
+    assert lattice.choose_we(d, 0.0, "rotated") == (True, 1)
+    fr = method.we_frame(dict(d=1.0, xi=0.5, eta=math.sqrt(3) / 2, m0=1, we_rot=True))
+    # e2 maps to (0, |e2|), e1 to (d eta/|e2|, d xi/|e2|)
+    assert abs(fr["c"] * 0.5 - fr["s"] * math.sqrt(3) / 2) < 1e-15
+    assert abs(fr["dx"] - math.sqrt(3) / 2) < 1e-15 and abs(fr["dy"] - 0.5) < 1e-15
+
+
+@pytest.mark.parametrize("mistake", ["no_column_phase", "transposed_rotation"])
+def test_rotated_planted_mistakes_are_caught(mistake, monkeypatch):
+    """A west part that drops the y~ shift of the image columns, or rotates
+    the wrong way, must disagree with the brute image sum."""
+    e1, e2 = HEX
+    src = _cell_pts(e1, e2, 20, 44)
+    trg = _cell_pts(e1, e2, 12, 45)
+    q = np.random.default_rng(7).standard_normal((1, 20))
+    cell, s, t = lattice.to_canonical(e1, e2, src, trg, we="rotated")
+    pb, _ = brute.modhelm_part(cell, 1.5, t, s, q, "west")
+    good = method.we_frame
+
+    def bad(c):
+        fr = dict(good(c))
+        if mistake == "no_column_phase":
+            fr["dy"] = 0.0
+        else:
+            fr["s"] = -fr["s"]
+        return fr
+
+    monkeypatch.setattr(method, "we_frame", bad)
+    pm, _ = method.far_field("modhelm", 1.5, cell, t, s, q, parts=("west",))
+    assert np.linalg.norm(pm - pb) / np.linalg.norm(pb) > 1e-3
 
 
 def _away_points(e1, e2, src, n, dmin, seed):
