@@ -107,6 +107,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--scale", type=float, default=1.0, help="scale point counts (profiling on a small case)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--we", default=None, choices=["auto", "axis", "rotated"],
+                    help="override the west/east plane-wave direction")
     return ap.parse_args()
 
 
@@ -568,8 +570,10 @@ def main():
     nt = ns if self_t else T.shape[1]
     grad = kernel != "stokes"
     singly = cfg.get("singly", False)
+    we = args.we or cfg.get("we", "auto")
     op = PeriodicOp(kernel, w["e1"], w["e2"], tol=cfg["tol"], precision="mixed", path=path,
-                    nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly)
+                    nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly,
+                    we=we)
     op.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = op(S, Q, T, grad=grad)
@@ -631,7 +635,7 @@ def main():
     acc = None
     if not args.skip_fp64 and rank == 0:
         op64 = PeriodicOp(kernel, w["e1"], w["e2"], tol=1e-10, precision="fp64", path="direct", ns_max=ns,
-                          nt_max=nt, singly=singly)
+                          nt_max=nt, singly=singly, we=we)
         op64.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -681,6 +685,7 @@ def main():
                    "nufft_w": desc["nufft_w"], "n_gl": desc["n_gl"], "M": desc["M"], "Nq": desc["Nq"],
                    "m0": desc["m0"], "outputs": "pot+grad" if grad else "velocity",
                    "periodicity": "singly (e1)" if singly else "doubly",
+                   "west_east": "rotated (e2-perp)" if desc["we_rotated"] else "axis (e1)",
                    "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
         "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_p2p": p2p},
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,

@@ -80,7 +80,7 @@ enum {
   PFMM_NO_GRAD = 4,    /* scalar kernels: skip the gradient even if given */
   PFMM_PROJECT_NEUTRAL = 8, /* Laplace/Stokes: subtract the mean strength (force) per rhs
                                before use, i.e. apply the operator to the zero-net part */
-  PFMM_SINGLY_PERIODIC = 16  /* P1: periodic along e1 only.  e2 spans the strip: points
+  PFMM_SINGLY_PERIODIC = 16, /* P1: periodic along e1 only.  e2 spans the strip: points
                                are wrapped along e1 and must lie within |y| < eta/2 across
                                it (eta = |e1 x e2| / |e1|); others set the status
                                PFMM_ERR_INVALID_ARG.  Near images m e1, |m| <= 1; the far
@@ -88,6 +88,15 @@ enum {
                                the image row n = 0 (Theorems west_thm, west_thm_lap,
                                west_thm_s), no south/north parts; direct path only;
                                single-cell calls only (not in a batch). */
+  PFMM_WE_ROTATED = 32,    /* west/east plane waves decay along e2-perp instead of e1
+                               (App. A, Eq. k0west2): the near block is 3 x 3 images
+                               (m0 = 1) for every parallelogram, at the price of more
+                               west/east quadrature nodes on strongly skewed cells */
+  PFMM_WE_AXIS = 64        /* west/east plane waves decay along e1; m0 = 1 unless the
+                               canonical skew |xi| > 3d/8, then m0 = 2 (15 images).
+                               Neither flag (default): rotated exactly when the axis
+                               direction would need m0 = 2.  Both: PFMM_ERR_INVALID_ARG.
+                               The singly periodic operator always uses the axis. */
 };
 
 typedef enum {
@@ -129,6 +138,9 @@ typedef struct {
   double es_beta;       /* ES kernel shape parameter                            */
   int nlaunch;          /* kernels launched by the last pfmm_execute on this plan */
   int64_t npairs;       /* near-image pairs of the last execute: ns * nt * (2 m0 + 1) * 3 */
+  int we_rotated;       /* 1 if the west/east plane waves decay along e2-perp   */
+  double we_dir[2];     /* (cos, sin) of that direction's rotation: canonical
+                           (x, y) -> (cos x - sin y, sin x + cos y); (1, 0) on the axis */
 } pfmm_plan_desc;
 
 typedef struct pfmm_plan pfmm_plan;

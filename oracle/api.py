@@ -20,7 +20,7 @@ def _rot_vec(rotT, v):
 
 
 def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1e-14,
-             want_grad=True, margin_frac=0.25, we="axis"):
+             want_grad=True, margin_frac=0.25, we="auto"):
     """we: west/east plane-wave direction, "axis", "rotated" (App. A) or
     "auto" (lattice.choose_we); it sets m0 and so the near/far split."""
     src = np.asarray(src, np.float64)
@@ -51,7 +51,7 @@ def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1
     return pot, (_rot_vec(rot.T, grad) if want_grad else None)
 
 
-def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.25, we="axis"):
+def stokes_pressure(e1, e2, src, f, trg, how="ewald", eps=1e-14, margin_frac=0.25, we="auto"):
     """Pressure of the periodic Stokeslet sum, input frame, [nrhs][nt].
 
     The free-space Stokeslet of this normalisation, u = (1/4pi)(-log r I +

@@ -79,7 +79,7 @@ def near_offsets(d, xi, eta, m0):
     return np.array(out)
 
 
-def choose_we(d, xi, we="axis", margin_frac=0.25):
+def choose_we(d, xi, we="auto", margin_frac=0.25):
     """West/east plane-wave direction and m0.  "axis": decay along e1 with m0
     from choose_m0; "rotated": decay along e2-perp (App. A), m0 = 1 for any
     cell; "auto": rotated exactly when the axis direction would need m0 >= 2.
@@ -91,7 +91,7 @@ def choose_we(d, xi, we="axis", margin_frac=0.25):
     return rot, (1 if rot else m0)
 
 
-def to_canonical(e1, e2, src, trg, margin_frac=0.25, we="axis"):
+def to_canonical(e1, e2, src, trg, margin_frac=0.25, we="auto"):
     """Canonicalise the lattice and wrap sources/targets given in the input
     frame ([2, n] arrays).  Returns (cell dict incl. m0 and we_rot, src_c,
     trg_c)."""

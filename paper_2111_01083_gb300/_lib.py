@@ -14,6 +14,7 @@ PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES = 0, 1, 2
 PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
 PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC = 1, 2, 4, 8, 16
+PFMM_WE_ROTATED, PFMM_WE_AXIS = 32, 64
 
 STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PFMM_ERR_NOT_NEUTRAL",
           4: "PFMM_ERR_TOLERANCE", 5: "PFMM_ERR_WORKSPACE", 6: "PFMM_ERR_CUDA", 7: "PFMM_ERR_NONFINITE",
@@ -40,7 +41,7 @@ class PlanDesc(ctypes.Structure):
                 ("rot", ctypes.c_double * 4), ("m0", ctypes.c_int), ("M", ctypes.c_int), ("mode0", ctypes.c_int),
                 ("Nq", ctypes.c_int), ("path", ctypes.c_int), ("n_gl", ctypes.c_int), ("nf", ctypes.c_int),
                 ("nufft_w", ctypes.c_int), ("es_beta", ctypes.c_double), ("nlaunch", ctypes.c_int),
-                ("npairs", ctypes.c_int64)]
+                ("npairs", ctypes.c_int64), ("we_rotated", ctypes.c_int), ("we_dir", ctypes.c_double * 2)]
 
 
 class PfmmError(RuntimeError):

@@ -159,7 +159,7 @@ __device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) 
 // K1: coefficient formation.  grid (chunks, term blocks, rhs groups).
 // coef layout [nrhs][nch][nterm] complex double; Stokes channels:
 //   0,1: c_a = sum R f (x, y comps)    (W/E: R - 1)
-//   2,3: c_b = sum R coord f           (coord = y' for S/N, x' for W/E)
+//   2,3: c_b = sum R coord f           (coord = y' for S/N, x~' for W/E: the west/east frame)
 // ----------------------------------------------------------------------------
 constexpr int kFormThreads = 128;
 constexpr int kFormSub = 64;
@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
   constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
   constexpr int NCH = (KER == PFMM_STOKES) ? 4 : 1;
   __shared__ T s_x[kFormSub], s_y[kFormSub];
+  __shared__ T s_xw[kFormSub], s_yw[kFormSub];  // west/east frame coordinates
   __shared__ int s_U[kFormSub];
   __shared__ T s_q[kRB][NC][kFormSub];
 
@@ -198,8 +199,11 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
     const int nb = min(kFormSub, j1 - jb);
     __syncthreads();
     for (int k = threadIdx.x; k < nb; k += kFormThreads) {
-      s_x[k] = sx[jb + k];
-      s_y[k] = sy[jb + k];
+      const T x = sx[jb + k], y = sy[jb + k];
+      s_x[k] = x;
+      s_y[k] = y;
+      s_xw[k] = T(g.wc) * x - T(g.ws) * y;
+      s_yw[k] = T(g.ws) * x + T(g.wc) * y;
       s_U[k] = sU ? sU[jb + k] : 0;
     }
     for (int k = threadIdx.x; k < kRB * NC * kFormSub; k += kFormThreads) {
@@ -214,7 +218,8 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
 #pragma unroll
       for (int c = 0; c < NCH; ++c) sub[r][c][0] = sub[r][c][1] = T(0);
     for (int jj = 0; jj < nb; ++jj) {
-      const T x = s_x[jj], y = s_y[jj];
+      // south/north: canonical (x, y); west/east: the west/east frame
+      const T x = sn ? s_x[jj] : s_xw[jj], y = sn ? s_y[jj] : s_yw[jj];
       T Rr, Ri, Qr, Qi;  // R (for c_b / plain) and Q (for c_a: R or R - 1)
       if (sn) {
         T e = dm::ex(sgn * b * y);
@@ -314,6 +319,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
   if (t >= f.nterm) return;
   Term tm = decode_term(f, g, t);
   const double d = g.d, xi = g.xi, eta = g.eta;
+  const lw::WeFrame fr{g.wdx, g.wdy, g.wxr, g.wyr};
   const int nch = f.nch;
   auto C = [&](int c) {
     const double* p = coef + (((size_t)r * nch + c) * f.nterm + t) * 2;
@@ -327,7 +333,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
       D = lw::sn_scalar(d, xi, eta, tm.a, tm.b, north);
       fac = (tm.m == 0) ? 1.0 : 2.0;  // +-m pairs
     } else {
-      D = lw::we_scalar(d, xi, eta, g.m0, tm.a, tm.b, tm.w, east, f.rows3 != 0);
+      D = lw::we_scalar(fr, g.m0, tm.a, tm.b, tm.w, east, f.rows3 != 0);
     }
     store_w(wts + (size_t)r * f.nterm + t, cscale(cmul(D, C(0)), fac));
     return;
@@ -336,7 +342,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
   if (tm.part < 2)
     lw::sn_stokes(d, xi, eta, tm.a, north, Da, Db);
   else
-    lw::we_stokes(d, xi, eta, g.m0, tm.a, tm.w, east, Da, Db, f.rows3 != 0);
+    lw::we_stokes(fr, g.wc, g.ws, g.m0, tm.a, tm.w, east, Da, Db, f.rows3 != 0);
   const dcx ca[2] = {C(0), C(1)}, cb[2] = {C(2), C(3)};
   dcx wa[2], wb[2];
   lw::stokes_apply(Da, Db, ca, cb, north || east, (tm.part < 2) ? 2.0 : 1.0, wa, wb);
@@ -367,6 +373,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   const int r0 = blockIdx.y * kRB;
   const int nr = min(kRB, f.nrhs - r0);
   const T x = in ? tx[l] : T(0), y = in ? ty[l] : T(0);
+  // west/east frame coordinates; its gradient is rotated back per term
+  const T wc = T(g.wc), ws = T(g.ws);
+  const T xw = wc * x - ws * y, yw = ws * x + wc * y;
   const int U = (in && tU) ? tU[l] : 0;
   const double xd = in ? (double)x / g.d : 0.0;
   // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy].  Compensated in FP32:
@@ -413,13 +422,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
       } else {
         const T sx = part == 2 ? T(1) : T(-1);
         if (KER != PFMM_MODHELM) {
-          dm::expm1c(-sx * b * x, a * y, &Mr, &Mi);
+          dm::expm1c(-sx * b * xw, a * yw, &Mr, &Mi);
           Lr = Mr + T(1);
           Li = Mi;
         } else {
-          T e = dm::ex(-sx * b * x);
+          T e = dm::ex(-sx * b * xw);
           T sp, cp;
-          dm::sincos_(a * y, &sp, &cp);
+          dm::sincos_(a * yw, &sp, &cp);
           Lr = e * cp;
           Li = e * sp;
           Mr = Lr;
@@ -436,11 +445,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
             acc[r][1].add(-a * Pi);
             acc[r][2].add(-(part == 0 ? b : -b) * Pr);
           } else {
-            acc[r][1].add(-(part == 2 ? b : -b) * Pr);
-            acc[r][2].add(-a * Pi);
+            const T gx = -(part == 2 ? b : -b) * Pr, gy = -a * Pi;  // in the west/east frame
+            acc[r][1].add(wc * gx + ws * gy);
+            acc[r][2].add(wc * gy - ws * gx);
           }
         } else {
-          const T cd = part < 2 ? y : x;
+          const T cd = part < 2 ? y : xw;
 #pragma unroll
           for (int c = 0; c < 2; ++c) {
             const T2 wa = s_w[r][c][k], wb = s_w[r][2 + c][k];

@@ -10,6 +10,13 @@
 //
 // North is the complex conjugate of south (coordinate terms change sign for
 // Stokes), east the conjugate of west.
+//
+// West/east frame (WeFrame): the plane waves decay along x~ of a frame in
+// which the image column m is shifted by m (dx, dy) and the row n by
+// n (xr, yr).  Along e1 (the paper's main text): (d, 0) and (xi, eta).  Along
+// e2-perp (App. A, Eq. k0west2): (d c, d s) and (0, |e2|) with c = eta/|e2|,
+// s = xi/|e2|.  The geometric sum over the columns m <= -(m0+1) then has the
+// complex ratio e^{-(kappa dx - i lambda dy)}.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,15 +51,29 @@ __device__ __forceinline__ dcx sn_scalar(double d, double xi, double eta, double
   return north ? conj_(D) : D;
 }
 
+struct WeFrame {
+  double dx, dy;  // image column step in the frame
+  double xr, yr;  // image row step in the frame
+};
+
+// 1 - e^{-g} for complex g = gr + i gi, without cancellation for small |g|:
+// 1 - e^{-gr} (cos gi - i sin gi) = -expm1(-gr) + e^{-gr} 2 sin^2(gi/2) + i e^{-gr} sin gi.
+__device__ __forceinline__ dcx one_minus_exp_neg(double gr, double gi) {
+  const double e = exp(-gr), sh = sin(0.5 * gi);
+  return {-expm1(-gr) + 2.0 * e * sh * sh, e * sin(gi)};
+}
+
 // Scalar west (east: conj), quadrature node (lambda, kappa) with weight w:
-//   D = (w / (2 pi kappa)) e^{-(m0+1) kappa d} / (1 - e^{-kappa d}) B,
-//   B = e^{kappa xi - i lambda eta} + 1 + e^{-kappa xi + i lambda eta}.
+//   D = (w / (2 pi kappa)) e^{-(m0+1) g} / (1 - e^{-g}) B,   g = kappa dx - i lambda dy,
+//   B = e^{kappa xr - i lambda yr} + 1 + e^{-kappa xr + i lambda yr}.
 //   rows3 = false (singly periodic P1): only the row n = 0, B = 1.
-__device__ __forceinline__ dcx we_scalar(double d, double xi, double eta, int m0, double lam, double kap, double w,
-                                         bool east, bool rows3 = true) {
-  double F = exp(-(m0 + 1) * kap * d) / (-expm1(-kap * d));
-  dcx B = rows3 ? cadd(cadd(cexp_({kap * xi, -lam * eta}), {1.0, 0.0}), cexp_({-kap * xi, lam * eta})) : dcx{1.0, 0.0};
-  dcx D = cscale(B, w / (2.0 * M_PI * kap) * F);
+__device__ __forceinline__ dcx we_scalar(const WeFrame& fr, int m0, double lam, double kap, double w, bool east,
+                                         bool rows3 = true) {
+  const double gr = kap * fr.dx, gi = -lam * fr.dy;
+  const dcx F = cdiv(cexp_({-(m0 + 1) * gr, -(m0 + 1) * gi}), one_minus_exp_neg(gr, gi));
+  dcx B = rows3 ? cadd(cadd(cexp_({kap * fr.xr, -lam * fr.yr}), {1.0, 0.0}), cexp_({-kap * fr.xr, lam * fr.yr}))
+                : dcx{1.0, 0.0};
+  dcx D = cscale(cmul(B, F), w / (2.0 * M_PI * kap));
   return east ? conj_(D) : D;
 }
 
@@ -81,32 +102,51 @@ __device__ __forceinline__ void sn_stokes(double d, double xi, double eta, doubl
     }
 }
 
-// Stokes west (east: conj), node (lambda, w), P = m0 + 1, z = e^{-lambda d}:
-//   pref = (w / 4 pi) z^P / (1 - z),  phi_r = e^{r (lambda xi - i lambda eta)},  B = phi_1 + 1 + phi_-1,
-//   Db = pref B S',  Da = pref [ B (I/lambda - (P d + d z/(1 - z)) S') + xi (phi_1 - phi_-1) S' ],
-//   S' = [[-1, i], [i, 1]].
-//   rows3 = false (singly periodic P1): only the row n = 0, B = 1 and no xi term.
-__device__ __forceinline__ void we_stokes(double d, double xi, double eta, int m0, double lam, double w, bool east,
-                                          dcx Da[2][2], dcx Db[2][2], bool rows3 = true) {
-  double z = exp(-lam * d);
-  double omz = -expm1(-lam * d);
-  int P = m0 + 1;
-  double pref = w / (4.0 * M_PI) * exp(-P * lam * d) / omz;
-  dcx ph1 = cexp_({lam * xi, -lam * eta}), phm = cexp_({-lam * xi, lam * eta});
+// Stokes west (east: conj), node (lambda, w), P = m0 + 1, z = e^{-lambda dx + i lambda dy}:
+//   pref = (w / 4 pi) z^P / (1 - z),  phi_r = e^{r (lambda xr - i lambda yr)},  B = phi_1 + 1 + phi_-1,
+//   Db = pref B S',  Da = pref [ B (I/lambda - (P dx + dx z/(1 - z)) S') + xr (phi_1 - phi_-1) S' ],
+//   S' = [[-1, i], [i, 1]], all in the west/east frame.
+//   rows3 = false (singly periodic P1): only the row n = 0, B = 1 and no xr term.
+//   c, s: the frame's rotation (canonical -> frame).  The blocks are returned
+//   as Q^T D Q, Q = [[c, -s], [s, c]], so that they act on canonical forces
+//   and give canonical velocities (the coordinate factors stay the frame's x~).
+__device__ __forceinline__ void we_stokes(const WeFrame& fr, double c, double s, int m0, double lam, double w,
+                                          bool east, dcx Da[2][2], dcx Db[2][2], bool rows3 = true) {
+  const double gr = lam * fr.dx, gi = -lam * fr.dy;  // z = e^{-(gr + i gi)}
+  const dcx z = cexp_({-gr, -gi});
+  const dcx omz = one_minus_exp_neg(gr, gi);
+  const int P = m0 + 1;
+  const dcx pref = cscale(cdiv(cexp_({-P * gr, -P * gi}), omz), w / (4.0 * M_PI));
+  dcx ph1 = cexp_({lam * fr.xr, -lam * fr.yr}), phm = cexp_({-lam * fr.xr, lam * fr.yr});
   dcx B = rows3 ? cadd(cadd(ph1, phm), {1.0, 0.0}) : dcx{1.0, 0.0};
   dcx Sp[2][2] = {{{-1, 0}, {0, 1}}, {{0, 1}, {1, 0}}};
-  double kx = P * d + d * z / omz;
-  dcx dph = rows3 ? cscale(csub(ph1, phm), xi) : dcx{0.0, 0.0};
+  const dcx kx = cadd({P * fr.dx, 0.0}, cscale(cdiv(z, omz), fr.dx));
+  dcx dph = rows3 ? cscale(csub(ph1, phm), fr.xr) : dcx{0.0, 0.0};
+  dcx A[2][2], Bb[2][2];
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
-      Db[i][j] = cscale(cmul(B, Sp[i][j]), pref);
+      Bb[i][j] = cmul(cmul(B, Sp[i][j]), pref);
       dcx id = (i == j) ? dcx{1.0 / lam, 0.0} : dcx{0.0, 0.0};
-      dcx t1 = cmul(B, csub(id, cscale(Sp[i][j], kx)));
-      Da[i][j] = cscale(cadd(t1, cmul(dph, Sp[i][j])), pref);
+      dcx t1 = cmul(B, csub(id, cmul(Sp[i][j], kx)));
+      A[i][j] = cmul(cadd(t1, cmul(dph, Sp[i][j])), pref);
       if (east) {
-        Db[i][j] = conj_(Db[i][j]);
-        Da[i][j] = conj_(Da[i][j]);
+        Bb[i][j] = conj_(Bb[i][j]);
+        A[i][j] = conj_(A[i][j]);
       }
+    }
+  // Q^T X Q
+  const double Q[2][2] = {{c, -s}, {s, c}};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      dcx a = {0, 0}, b = {0, 0};
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l) {
+          const double qq = Q[k][i] * Q[l][j];
+          a = cadd(a, cscale(A[k][l], qq));
+          b = cadd(b, cscale(Bb[k][l], qq));
+        }
+      Da[i][j] = a;
+      Db[i][j] = b;
     }
 }
 

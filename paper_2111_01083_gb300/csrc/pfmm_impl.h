@@ -23,6 +23,10 @@ struct Geom {
   double off[kMaxNear][2];// image offsets l_mn = m e1 + n e2 (canonical)
   int center;             // index of the (0, 0) image in off[]
   int p1;                 // singly periodic (along e1 only): no wrap across the strip
+  // west/east frame: (x~, y~) = (wc x - ws y, ws x + wc y); image column step
+  // (wdx, wdy) and row step (wxr, wyr) in it.  Axis: (1, 0), (d, 0), (xi, eta).
+  int we_rot;
+  double wc, ws, wdx, wdy, wxr, wyr;
 };
 
 // Far-field parameters (direct path).  Terms are ordered

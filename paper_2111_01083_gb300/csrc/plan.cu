@@ -121,20 +121,41 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// West/east frame.  Axis (the paper's main text): x along e1, columns step
+// (d, 0), rows (xi, eta).  Rotated (App. A, Eq. k0west2): x~ along e2-perp,
+// (x~, y~) = (c x - s y, s x + c y) with c = eta/|e2|, s = xi/|e2|, so that
+// e2 -> (0, |e2|) and e1 -> (d c, d s); a point's x~ spans exactly d c, and
+// m0 = 1 leaves the gap d c > 0 for every parallelogram.
+void set_we_frame(Geom* g, bool rotated) {
+  g->we_rot = rotated ? 1 : 0;
+  if (!rotated) {
+    g->wc = 1.0; g->ws = 0.0;
+    g->wdx = g->d; g->wdy = 0.0; g->wxr = g->xi; g->wyr = g->eta;
+    return;
+  }
+  const double h = std::hypot(g->xi, g->eta);
+  g->wc = g->eta / h; g->ws = g->xi / h;
+  g->wdx = g->d * g->wc; g->wdy = g->d * g->ws; g->wxr = 0.0; g->wyr = h;
+}
+
 // West/east quadrature for int_0^inf (.) d lambda (own composite GL rule in
-// lambda' = lambda d): panels of width 2 (narrower for tall singly periodic
-// strips, so that each panel sees at most ~4 radians of e^{i lambda (y - y')}),
+// lambda' = lambda d): panels of width 2 (narrower when the integrand's
+// lambda-frequency exceeds 2d, so that each panel sees at most ~4 radians),
 // 8/12/16 points for tol >= 1e-7 /
 // >= 1e-11 / smaller, dyadic panels toward 0 when 0 < beta d < 2, truncated
-// where exp(-kappa' x_min') < tol/10 with x_min' = (m0 d - 2|xi|)/d.
+// where exp(-kappa' x_min') < tol/10 with x_min' the smallest scaled gap
+// between a point and a far image column: (m0 d - 2|xi|)/d on the axis,
+// m0 d c / d rotated.
 void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vector<double>& nodes) {
   nodes.clear();
-  // largest |y - y'| / d the oscillation e^{i lambda (y - y')} must resolve:
-  // 2 eta / d (rows n = -1, 0, 1) or eta / d (singly periodic); panels of
-  // width 2 in lambda d up to a span of 2, narrower beyond
-  const double yspan = (g.p1 ? 1.0 : 2.0) * g.eta / g.d;
+  // largest lambda-frequency of the integrand, over d: axis: |y - y'| < eta
+  // plus the row shifts +-eta (eta alone for the singly periodic row);
+  // rotated: |y~ - y~'| < |e2| + d|s|, row shifts +-|e2|, and the first far
+  // column's phase (m0 + 1) d|s|
+  const double yspan = g.we_rot ? (2.0 * g.wyr + (g.m0 + 2) * std::fabs(g.wdy)) / g.d
+                                : (g.p1 ? 1.0 : 2.0) * g.eta / g.d;
   const double pw = yspan > 2.0 ? 4.0 / yspan : 2.0;
-  double xmin = (g.m0 * g.d - 2.0 * std::fabs(g.xi)) / g.d;
+  double xmin = g.we_rot ? g.m0 * g.wdx / g.d : (g.m0 * g.d - 2.0 * std::fabs(g.xi)) / g.d;
   double bt = (kernel == PFMM_MODHELM) ? beta * g.d : 0.0;
   double top = std::log(10.0 / tol) / xmin;
   if (top <= bt) return;
@@ -268,6 +289,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (!(o->tol >= 1e-14 && o->tol <= 1e-2)) return fail(PFMM_ERR_TOLERANCE, "tol must be in [1e-14, 1e-2]");
   if (o->kernel == PFMM_MODHELM && !(o->beta > 0 && std::isfinite(o->beta)))
     return fail(PFMM_ERR_INVALID_ARG, "beta must be > 0 for the modified Helmholtz kernel");
+  if (o->flags & ~127u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~127u);
   if ((o->flags & PFMM_FAR_ONLY) && (o->flags & PFMM_NEAR_ONLY))
     return fail(PFMM_ERR_INVALID_ARG, "FAR_ONLY and NEAR_ONLY are exclusive");
   if (o->nufft_w != 0 && (o->nufft_w < 2 || o->nufft_w > 16)) return fail(PFMM_ERR_INVALID_ARG, "nufft_w in [2,16]");
@@ -283,6 +305,14 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   } else {
     if (!canonicalize(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate lattice vectors");
     g.m0 = choose_m0(g.d, g.xi);
+  }
+  {
+    const bool want_rot = (o->flags & PFMM_WE_ROTATED) != 0, want_axis = (o->flags & PFMM_WE_AXIS) != 0;
+    if (want_rot && want_axis) return fail(PFMM_ERR_INVALID_ARG, "WE_ROTATED and WE_AXIS are exclusive");
+    if (p1 && want_rot) return fail(PFMM_ERR_INVALID_ARG, "the singly periodic operator uses the axis direction");
+    const bool rot = !p1 && (want_rot || (!want_axis && g.m0 >= 2));
+    if (rot) g.m0 = 1;
+    set_we_frame(&g, rot);
   }
   if ((2 * g.m0 + 1) * 3 > kMaxNear) return fail(PFMM_ERR_INTERNAL, "near block too large");
   g.nimg = 0;
@@ -474,6 +504,9 @@ pfmm_status pfmm_plan_describe(const pfmm_plan* p, pfmm_plan_desc* d) {
   d->d = p->geom.d; d->xi = p->geom.xi; d->eta = p->geom.eta;
   for (int i = 0; i < 4; ++i) d->rot[i] = p->geom.rot[i];
   d->m0 = p->geom.m0;
+  d->we_rotated = p->geom.we_rot;
+  d->we_dir[0] = p->geom.wc;
+  d->we_dir[1] = p->geom.ws;
   d->M = p->far.M;
   d->mode0 = (p->opts.kernel == PFMM_MODHELM) ? p->far.mode0 : 1;
   d->Nq = p->Nq;

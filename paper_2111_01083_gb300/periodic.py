@@ -21,6 +21,7 @@ _KER = {"laplace": _lib.PFMM_LAPLACE, "modhelm": _lib.PFMM_MODHELM, "stokes": _l
 _PREC = {"fp64": _lib.PFMM_FP64, "mixed": _lib.PFMM_MIXED}
 _PATH = {"auto": _lib.PFMM_PATH_AUTO, "direct": _lib.PFMM_PATH_DIRECT, "nufft": _lib.PFMM_PATH_NUFFT}
 _PART = {"total": 0, "far": _lib.PFMM_FAR_ONLY, "near": _lib.PFMM_NEAR_ONLY}
+_WE = {"auto": 0, "rotated": _lib.PFMM_WE_ROTATED, "axis": _lib.PFMM_WE_AXIS}
 
 
 def _ptr(t):
@@ -29,7 +30,7 @@ def _ptr(t):
 
 class PeriodicOp:
     def __init__(self, kernel, e1, e2, beta=0.0, tol=1e-6, precision="mixed", path="auto", nufft_w=0, n_gl=0,
-                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False):
+                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False, we="auto"):
         L = _lib.lib()
         o = _lib.Opts()
         o.e1[0], o.e1[1] = float(e1[0]), float(e1[1])
@@ -42,7 +43,7 @@ class PeriodicOp:
         o.nufft_w = int(nufft_w)
         o.n_gl = int(n_gl)
         o.nrhs = int(nrhs)
-        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0)
+        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0) | _WE[we]
         self.kernel = kernel
         self.nrhs = int(nrhs)
         self.ns_max, self.nt_max = int(ns_max), int(nt_max)
@@ -61,7 +62,7 @@ class PeriodicOp:
     def describe(self):
         d = _lib.PlanDesc()
         _lib.check(_lib.lib().pfmm_plan_describe(self._h, ctypes.byref(d)))
-        return {k: (list(getattr(d, k)) if k == "rot" else getattr(d, k)) for k, _ in d._fields_}
+        return {k: (list(getattr(d, k)) if k in ("rot", "we_dir") else getattr(d, k)) for k, _ in d._fields_}
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -191,7 +192,7 @@ class BatchOp:
         arr = (_lib.Opts * n)()
         for i, c in enumerate(cells):
             arr[i] = _opts(kernel, c["e1"], c["e2"], c.get("beta", 0.0), c.get("tol", tol), precision, path, 0, 0,
-                           nrhs, 0)
+                           nrhs, _WE[c.get("we", "auto")])
         so = np.concatenate([[0], np.cumsum(src_counts)]).astype(np.int64)
         self._so = (ctypes.c_int64 * (n + 1))(*so.tolist())
         self._to = None
@@ -290,10 +291,11 @@ class StokesPressure:
         pres = StokesPressure(e1, e2, tol=1e-6, precision="mixed")(src, f, trg)
     """
 
-    def __init__(self, e1, e2, tol=1e-6, precision="mixed", path="auto", nrhs=1, ns_max=0, nt_max=0, singly=False):
+    def __init__(self, e1, e2, tol=1e-6, precision="mixed", path="auto", nrhs=1, ns_max=0, nt_max=0, singly=False,
+                 we="auto"):
         self.nrhs = int(nrhs)
         self.op = PeriodicOp("laplace", e1, e2, tol=tol, precision=precision, path=path, nrhs=2 * self.nrhs,
-                             ns_max=ns_max, nt_max=nt_max, singly=singly)
+                             ns_max=ns_max, nt_max=nt_max, singly=singly, we=we)
 
     def __call__(self, src, f, trg=None, out=None, stream=None):
         import torch

@@ -22,9 +22,9 @@ def run_lib(kernel, e1, e2, src, q, trg=None, beta=0.0, tol=1e-6, precision="mix
     return pot.cpu().numpy(), (None if g is None else g.cpu().numpy()), op
 
 
-def oracle(kernel, e1, e2, src, q, trg=None, beta=0.0, part="total", how="ewald", grad=True):
+def oracle(kernel, e1, e2, src, q, trg=None, beta=0.0, part="total", how="ewald", grad=True, we="auto"):
     t = src if trg is None else trg
-    return oapi.evaluate(kernel, beta, e1, e2, src, q, t, part=part, how=how, want_grad=grad)
+    return oapi.evaluate(kernel, beta, e1, e2, src, q, t, part=part, how=how, want_grad=grad, we=we)
 
 
 def errs(kernel, got, ref):

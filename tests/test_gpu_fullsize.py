@@ -75,6 +75,16 @@ def test_stokes_skew_full():
     assert _cmp(vel[:, :, idx], ref, True) < 1e-6
 
 
+def test_stokes_hex_full():
+    """2e5 Stokeslets, 2e5 separate targets, hexagonal cell: the default
+    rotated west/east direction (3 x 3 near block), mixed precision."""
+    w = workloads.make("stokes_hex_n2e5")
+    vel, _ = _run(w, "mixed", 1e-6, "direct")
+    idx = np.random.default_rng(5).choice(w["trg"].shape[1], NSAMP, replace=False)
+    ref, _ = _oracle_at("stokes", 0.0, w["e1"], w["e2"], w["src"], w["q"], w["trg"][:, idx])
+    assert _cmp(vel[:, :, idx], ref, True) < 1e-6
+
+
 def test_laplace_adjoint_full():
     """5e4 charges in the 4 x 1 cell: dE/dq = phi, dE/dx = q grad phi at sampled points."""
     import torch

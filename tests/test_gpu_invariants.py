@@ -38,7 +38,8 @@ def _edge_pairs(desc, n, which, rng, eps=1e-13):
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
 @pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 2.0), ("stokes", 0.0)])
-@pytest.mark.parametrize("e1,e2", [((1.0, 0.0), (0.3, 0.8)), ((16.0, 0.0), (0.0, 1.0))])
+@pytest.mark.parametrize("e1,e2", [((1.0, 0.0), (0.3, 0.8)), ((16.0, 0.0), (0.0, 1.0)),
+                                   ((1.0, 0.0), (0.5, 0.8660254037844386))])
 def test_periodicity(precision, tol, kernel, beta, e1, e2):
     from paper_2111_01083_gb300 import PeriodicOp
     rng = np.random.default_rng(31)

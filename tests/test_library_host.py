@@ -66,10 +66,11 @@ def test_canonical_cell_and_m0(L, e1, e2):
     """Library canonicalisation vs the oracle's independent implementation."""
     from oracle import lattice
     c = lattice.canonicalize(e1, e2)
-    d, xi, eta, m0 = c["d"], c["xi"], c["eta"], lattice.choose_m0(c["d"], c["xi"])
+    d, xi, eta = c["d"], c["xi"], c["eta"]
+    rot, m0 = lattice.choose_we(d, xi, "auto")
     desc = _op(e1=e1, e2=e2).describe()
     assert abs(desc["d"] - d) < 1e-12 and abs(abs(desc["xi"]) - abs(xi)) < 1e-12 and abs(desc["eta"] - eta) < 1e-12
-    assert desc["m0"] == m0
+    assert desc["m0"] == m0 and desc["we_rotated"] == int(rot)
     r = desc["rot"]
     # rot is a rotation and maps a lattice vector of length d onto the x axis
     assert abs(r[0] * r[3] - r[1] * r[2] - 1) < 1e-12 and abs(r[0] * r[1] + r[2] * r[3]) < 1e-12
@@ -80,6 +81,36 @@ def test_canonical_cell_and_m0(L, e1, e2):
         y = r[2] * v[0] + r[3] * v[1]
         ok |= abs(abs(x) - d) < 1e-9 and abs(y) < 1e-9
     assert ok
+
+
+def test_west_east_direction_flags(L):
+    """App. A: WE_ROTATED gives the 3 x 3 near block on any cell, with the
+    frame (cos, sin) = (eta, xi)/|e2|; WE_AXIS keeps m0 = 2 on the hexagonal
+    cell; the default rotates exactly there."""
+    hexe2 = (0.5, math.sqrt(3) / 2)
+    r = _op(e2=hexe2, we="rotated").describe()
+    a = _op(e2=hexe2, we="axis").describe()
+    dflt = _op(e2=hexe2).describe()
+    assert (r["m0"], r["we_rotated"]) == (1, 1) and (a["m0"], a["we_rotated"]) == (2, 0)
+    assert (dflt["m0"], dflt["we_rotated"]) == (1, 1)
+    h = math.hypot(r["xi"], r["eta"])
+    assert abs(r["we_dir"][0] - r["eta"] / h) < 1e-14 and abs(r["we_dir"][1] - r["xi"] / h) < 1e-14
+    assert a["we_dir"] == [1.0, 0.0]
+    sq = _op(we="rotated").describe()  # rectangle: the rotated frame is the axis frame
+    assert sq["m0"] == 1 and sq["we_dir"] == [1.0, 0.0] and sq["Nq"] == _op().describe()["Nq"]
+    skew = _op(e2=(0.3, 0.8)).describe()
+    assert (skew["m0"], skew["we_rotated"]) == (1, 0)
+
+
+@pytest.mark.parametrize("kw", [dict(flags=96), dict(flags=128), dict(flags=48)])
+def test_west_east_flag_errors(L, kw):
+    from paper_2111_01083_gb300 import _lib
+    o = _lib.Opts()
+    o.e1[0], o.e1[1], o.e2[0], o.e2[1] = 1.0, 0.0, 0.0, 1.0
+    o.kernel, o.tol, o.precision, o.path, o.nrhs = 0, 1e-6, 1, 1, 1
+    o.flags = kw["flags"]  # both directions / unknown bit / rotated singly periodic
+    h = ctypes.c_void_p()
+    assert L.pfmm_plan_create(ctypes.byref(o), 10, 10, ctypes.byref(h)) == 1  # PFMM_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("d,tol", [(1.0, 1e-10), (16.0, 1e-6), (64.0, 1e-6)])

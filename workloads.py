@@ -58,6 +58,10 @@ CONFIGS = {
                                       path="nufft", nufft_w=8, n_gl=8),
     "stokes_skew_n2e5": dict(kernel="stokes", e1=(1.0, 0.0), e2=(0.3, 0.8), ns=200000, nt=200000,
                              seed=2, dist="uniform", tol=1e-6, precision="mixed"),
+    # hexagonal lattice (|xi| = d/2): the axis west/east direction needs a 5 x 3
+    # near block, the rotated one (e2-perp) a 3 x 3 block
+    "stokes_hex_n2e5": dict(kernel="stokes", e1=(1.0, 0.0), e2=(0.5, 0.8660254037844386), ns=200000,
+                            nt=200000, seed=7, dist="uniform", tol=1e-6, precision="mixed"),
     "laplace_adjoint_4x1_n5e4": dict(kernel="laplace", e1=(4.0, 0.0), e2=(0.0, 1.0), ns=50000,
                                      seed=4, dist="uniform", tol=1e-6, precision="mixed"),
     # singly periodic (P1): period e1, 1e5 uniform sources in the strip segment
