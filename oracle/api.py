@@ -8,6 +8,10 @@ back (canonical = rot @ input, so input = rot^T @ canonical).
 
 part: "total" (K^(p) q = K^near q + P2 q), "far" (P2 q), "near" (K^near q).
 how : "ewald" (the definition), "plain" (the paper's direct L D R method).
+The modified Stokeslet ("mstokes") has no Ewald form here: its periodic sum
+is defined in the paper's order (image rows), which the plain method follows
+and tests/test_oracle_mstokes_pins.py pins against exact row sums; "ewald"
+is refused for it.
 """
 import numpy as np
 
@@ -28,7 +32,9 @@ def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1
     q = np.asarray(q, np.float64)
     cell, s, t = lattice.to_canonical(e1, e2, src, trg, margin_frac, we)
     rot = cell["rot"]
-    if kernel == "stokes":
+    if kernel == "mstokes" and how == "ewald" and part != "near":
+        raise ValueError("mstokes: use how='plain' (no Ewald form)")
+    if kernel in ("stokes", "mstokes"):
         q = np.einsum("ij,rjn->rin", rot, q)
         want_grad = False
     pot = 0.0
@@ -46,7 +52,7 @@ def evaluate(kernel, beta, e1, e2, src, q, trg, part="total", how="ewald", eps=1
         pot = pot + p
         if want_grad:
             grad = grad + g
-    if kernel == "stokes":
+    if kernel in ("stokes", "mstokes"):
         return _rot_vec(rot.T, pot), None
     return pot, (_rot_vec(rot.T, grad) if want_grad else None)
 

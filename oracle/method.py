@@ -33,6 +33,20 @@ e^{-(kappa d c - i lambda d s)}, the rows n = -1, 0, 1 shift only y~, and
 m0 = 1 suffices for every parallelogram (smallest gap d c).  Stokes: forces
 are rotated into the frame and velocities back; scalar gradients likewise.
 
+mstokes  (modified Stokeslet, beta > 0) south/north: Theorem south_thm_ms
+         (Eqs. pmss1, chialphadefms, lowranksouth3ms): per mode m a beta
+         family (decay chi_m, block [[chi, i alpha], [i alpha, -alpha^2/chi]])
+         and a Laplace family (decay |alpha_m|, block [[-|a|, -i a], [-i a, |a|]]),
+         each with the scalar lattice factor e^{-2Q}/(1 - e^{-Q}) / (2 beta^2 d);
+         north: conjugate blocks.  The Laplace family has no m = 0 term: each
+         image row is Poisson-summed on its own, and the row's zero mode of
+         grad grad^T log r vanishes (its integral over x is 0).
+         west/east: Theorem west_thm_ms (Eq. pmsw0, general m0): blocks
+         [[-lambda^2/kappa, i lambda], [i lambda, kappa]] (kappa = sqrt(lambda^2 +
+         beta^2)) and [[|l|, -i l], [-i l, -|l|]] (kappa = |lambda|), 2 Re of the
+         half line, prefactor 1/(2 pi beta^2); east: conjugate blocks.  No gauge
+         and no coordinate channels: both families are integrable at lambda = 0.
+
 Modes: M from Eq. mpk0s.  West/east quadrature: this oracle's own,
 deliberately over-resolved composite Gauss-Legendre rule in lambda' = lambda d
 (panels of width 1/2, narrower when the oscillation span exceeds 2d, 20
@@ -250,6 +264,83 @@ def _stokes_we(cell, trg, src, f, eps, part, rows=(-1, 0, 1)):
     return _from_frame(fr, vel)
 
 
+def _mstokes_sn(beta, cell, trg, src, f, eps, part):
+    d, xi, eta = cell["d"], cell["xi"], cell["eta"]
+    M = mpk0s(d, eta, eps)
+    m = np.arange(-M, M + 1)
+    al = 2 * np.pi * m / d
+    chi = np.sqrt(al * al + beta * beta)
+    a = np.abs(al)
+    north = part == "north"
+    sy = -1.0 if north else 1.0
+    fc = f.astype(complex)
+    vel = np.zeros((f.shape[0], 2, trg.shape[1]))
+    fams = []
+    # beta family, every m
+    Qb = chi * eta - 1j * al * xi
+    Mb = np.empty((m.size, 2, 2), complex)
+    Mb[:, 0, 0] = chi
+    Mb[:, 0, 1] = Mb[:, 1, 0] = 1j * al
+    Mb[:, 1, 1] = -al * al / chi
+    fams.append((chi, al, np.exp(-2 * Qb) / (1 - np.exp(-Qb)), Mb))
+    # Laplace family, m != 0
+    nz = m != 0
+    Q0 = a[nz] * eta - 1j * al[nz] * xi
+    M0 = np.empty((nz.sum(), 2, 2), complex)
+    M0[:, 0, 0] = -a[nz]
+    M0[:, 0, 1] = M0[:, 1, 0] = -1j * al[nz]
+    M0[:, 1, 1] = a[nz]
+    fams.append((a[nz], al[nz], np.exp(-2 * Q0) / (1 - np.exp(-Q0)), M0))
+    for dec, alp, lat, Mat in fams:
+        D = (lat / (2 * beta * beta * d))[:, None, None] * Mat
+        if north:
+            D = np.conj(D)
+        R = np.exp(sy * dec[:, None] * src[1][None, :] - 1j * alp[:, None] * src[0][None, :])
+        L = np.exp(-sy * dec[None, :] * trg[1][:, None] + 1j * alp[None, :] * trg[0][:, None])
+        c = np.einsum("rcj,mj->rcm", fc, R)
+        w = np.einsum("mij,rjm->rim", D, c)
+        vel += np.einsum("lm,rim->ril", L, w).real
+    return vel
+
+
+def _mstokes_we(beta, cell, trg, src, f, eps, part):
+    m0 = cell["m0"]
+    fr = we_frame(cell)
+    trg, src = _to_frame(fr, trg), _to_frame(fr, src)
+    f = _to_frame(fr, f.transpose(1, 0, 2)).transpose(1, 0, 2)
+    P = m0 + 1
+    east = part == "east"
+    s = -1.0 if east else 1.0
+    fc = f.astype(complex)
+    vel = np.zeros((f.shape[0], 2, trg.shape[1]))
+    for fam_beta in (beta, 0.0):
+        lam, w = we_quadrature(cell, fam_beta, eps)
+        if lam.size == 0:
+            continue
+        kap = np.sqrt(lam * lam + fam_beta * fam_beta)
+        B = sum(np.exp(n * (kap * fr["xr"] - 1j * lam * fr["yr"])) for n in (-1, 0, 1))
+        g = kap * fr["dx"] - 1j * lam * fr["dy"]
+        F = np.exp(-P * g) / (1 - np.exp(-g))
+        Mat = np.empty((lam.size, 2, 2), complex)
+        if fam_beta > 0:
+            Mat[:, 0, 0] = -lam * lam / kap
+            Mat[:, 0, 1] = Mat[:, 1, 0] = 1j * lam
+            Mat[:, 1, 1] = kap
+        else:
+            Mat[:, 0, 0] = lam
+            Mat[:, 0, 1] = Mat[:, 1, 0] = -1j * lam
+            Mat[:, 1, 1] = -lam
+        D = (w / (2 * np.pi * beta * beta) * F * B)[:, None, None] * Mat
+        if east:
+            D = np.conj(D)
+        R = np.exp(s * kap[:, None] * src[0][None, :] - 1j * lam[:, None] * src[1][None, :])
+        L = np.exp(-s * kap[None, :] * trg[0][:, None] + 1j * lam[None, :] * trg[1][:, None])
+        c = np.einsum("rcj,mj->rcm", fc, R)
+        wv = np.einsum("mij,rjm->rim", D, c)
+        vel += np.einsum("lm,rim->ril", L, wv).real
+    return _from_frame(fr, vel)
+
+
 def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad=True, chunk=4096,
               rows=(-1, 0, 1)):
     """Sum of the requested far-field parts at the targets.
@@ -270,6 +361,18 @@ def far_field(kernel, beta, cell, trg, src, q, eps=1e-14, parts=PARTS, want_grad
                     out[:, :, l0:l0 + chunk] += _stokes_sn(cell, t, src, q, eps, p)
                 else:
                     out[:, :, l0:l0 + chunk] += _stokes_we(cell, t, src, q, eps, p, rows)
+        return out, None
+    if kernel == "mstokes":
+        if tuple(rows) != (-1, 0, 1):
+            raise ValueError("mstokes: doubly periodic only")
+        out = np.zeros((nrhs, 2, nt))
+        for l0 in range(0, nt, chunk):
+            t = trg[:, l0:l0 + chunk]
+            for p in parts:
+                if p in ("south", "north"):
+                    out[:, :, l0:l0 + chunk] += _mstokes_sn(beta, cell, t, src, q, eps, p)
+                else:
+                    out[:, :, l0:l0 + chunk] += _mstokes_we(beta, cell, t, src, q, eps, p)
         return out, None
     pot = np.zeros((nrhs, nt))
     grad = np.zeros((nrhs, 2, nt)) if want_grad else None
