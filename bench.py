@@ -61,6 +61,11 @@ def p2p_work(kernel, nrhs, grad, nimg=9):
         return (8.0 + 3.0 / nimg, 1.0 + 1.0 / nimg) if grad else (6.0 + 1.0 / nimg, 1.0 / nimg)
     if kernel == "stokes":
         return (11.0 + 7.0 / nimg, 1.0 + 1.0 / nimg)
+    if kernel == "mstokes":
+        # k_p2p_ms, x = beta r <= 2 branch: hi/lo differences 6, r^2 and x^2 3,
+        # I0 / p1 / K0 / q1' polynomials 24, logs and E 5, A and B/r^2 3, the
+        # 2 x 2 image sum 6, plus 4 FMAs per source and rhs; MUFU lg2 + rcp
+        return (48.0 + 4.0 * nrhs / nimg, 2.0)
     if grad:
         return (26.0 + 3.0 * nrhs / nimg, 2.5)
     return (16.0 + nrhs / nimg, 2.5)
@@ -129,8 +134,10 @@ if singly:
 else:
     cell, s, t = lattice.to_canonical(w["e1"], w["e2"], w["src"], w["trg"])
 kernel = w["kernel"]
+beta = w.get("beta", 0.0)
+vec = kernel in ("stokes", "mstokes")
 q = w["q"]
-if kernel == "stokes":
+if vec:
     q = np.einsum("ij,rjn->rin", cell["rot"], q)
 res = []
 for nsamp in %(samples)r:
@@ -138,11 +145,11 @@ for nsamp in %(samples)r:
     tt = t[:, idx]
     t0 = time.perf_counter()
     if singly:
-        p1.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
-        p1.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
+        p1.near_sum(kernel, beta, cell, tt, s, q, want_grad=not vec)
+        p1.far_field(kernel, beta, cell, tt, s, q, eps=%(eps)r, want_grad=not vec)
     else:
-        ewald.near_sum(kernel, 0.0, cell, tt, s, q, want_grad=kernel != "stokes")
-        method.far_field(kernel, 0.0, cell, tt, s, q, eps=%(eps)r, want_grad=kernel != "stokes")
+        ewald.near_sum(kernel, beta, cell, tt, s, q, want_grad=not vec)
+        method.far_field(kernel, beta, cell, tt, s, q, eps=%(eps)r, want_grad=not vec)
     res.append((nsamp, time.perf_counter() - t0))
 print(json.dumps({"samples": res, "ns": int(s.shape[1]), "nt": int(t.shape[1])}))
 """
@@ -568,10 +575,11 @@ def main():
     T = None if self_t else torch.tensor(w["trg"], device=dev)
     ns = S.shape[1]
     nt = ns if self_t else T.shape[1]
-    grad = kernel != "stokes"
+    grad = kernel not in ("stokes", "mstokes")
     singly = cfg.get("singly", False)
     we = args.we or cfg.get("we", "auto")
-    op = PeriodicOp(kernel, w["e1"], w["e2"], tol=cfg["tol"], precision="mixed", path=path,
+    beta = cfg.get("beta", 0.0)
+    op = PeriodicOp(kernel, w["e1"], w["e2"], beta=beta, tol=cfg["tol"], precision="mixed", path=path,
                     nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly,
                     we=we)
     op.profile(True)
@@ -634,8 +642,8 @@ def main():
     # accuracy: mixed vs the FP64 GPU path on the same input (outside the timed region)
     acc = None
     if not args.skip_fp64 and rank == 0:
-        op64 = PeriodicOp(kernel, w["e1"], w["e2"], tol=1e-10, precision="fp64", path="direct", ns_max=ns,
-                          nt_max=nt, singly=singly, we=we)
+        op64 = PeriodicOp(kernel, w["e1"], w["e2"], beta=beta, tol=1e-10, precision="fp64", path="direct",
+                          ns_max=ns, nt_max=nt, singly=singly, we=we)
         op64.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -653,7 +661,7 @@ def main():
                 b = b - b.mean(-1, keepdim=True)
             return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
         acc = {"fp64_gpu_ms_per_step": e0.elapsed_time(e1),
-               "rel_err_pot_vs_fp64": rel(out[0], ref[0], kernel != "modhelm"),
+               "rel_err_pot_vs_fp64": rel(out[0], ref[0], kernel in ("laplace", "stokes")),
                "rel_err_grad_vs_fp64": rel(out[1], ref[1], False) if grad else None,
                "fp64_gpu_value": (ns + nt) / (e0.elapsed_time(e1) * 1e-3)}
         del op64, ref
@@ -665,7 +673,8 @@ def main():
     # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
     p2p = sum(p2p_ms) / len(p2p_ms)
     nimg = 3 if singly else 3 * (2 * desc["m0"] + 1)
-    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, f"k_p2p_mixed (near-image P2P, {nimg} images)",
+    kname = "k_p2p_ms" if kernel == "mstokes" else "k_p2p_mixed"
+    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
                         traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload), nimg=nimg)
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:

@@ -57,7 +57,15 @@
 extern "C" {
 #endif
 
-typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2 } pfmm_kernel;
+/* MSTOKES: the modified Stokeslet (Eq. msgreen), u = G f with
+ * G = (grad grad^T - Lap I) G_MB, G_MB = -(1/(2 pi beta^2))(K0(beta r) - log(1/r)),
+ * the fundamental solution of (beta^2 - Lap) u + grad p = 0, div u = 0
+ * (beta > 0; no net-force condition).  Forces and velocities are laid out as
+ * for STOKES.  Far field by Theorems south_thm_ms / west_thm_ms (direct path
+ * only), periodic sum in the paper's order (image rows).  Single-cell
+ * pfmm_execute / pfmm_execute_host / pfmm_execute_static only: not in a batch,
+ * not for the adjoint, not singly periodic. */
+typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2, PFMM_MSTOKES = 3 } pfmm_kernel;
 
 /* FP64: every step in double precision.
  * MIXED: plane-wave generation, spreading, FFT, interpolation and the P2P
@@ -69,8 +77,9 @@ typedef enum { PFMM_FP64 = 0, PFMM_MIXED = 1 } pfmm_precision;
 
 /* Far-field south/north application: DIRECT = L (D (R q)) (Sec. 6);
  * NUFFT = GL anterpolation + ES-kernel NUFFT (Sec. 6, Eqs. fastanterp and
- * fastinterp), for all three kernels.  AUTO picks NUFFT when M >= 64 and the
- * fine grid (power of two >= 2 (2M + 1)) has at most 8192 points. */
+ * fastinterp), for the Laplace, modified Helmholtz and Stokes kernels.  AUTO
+ * picks NUFFT when M >= 64 and the fine grid (power of two >= 2 (2M + 1)) has
+ * at most 8192 points; MSTOKES always takes DIRECT (NUFFT: INVALID_ARG). */
 typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } pfmm_path;
 
 /* flags */
@@ -115,7 +124,7 @@ typedef enum {
 typedef struct {
   double e1[2], e2[2];  /* lattice vectors (any orientation, not collinear)     */
   int kernel;           /* pfmm_kernel                                          */
-  double beta;          /* > 0 for PFMM_MODHELM, ignored otherwise              */
+  double beta;          /* > 0 for PFMM_MODHELM and PFMM_MSTOKES, ignored otherwise */
   double tol;           /* requested precision eps, in [1e-14, 1e-2]            */
   int precision;        /* pfmm_precision                                       */
   int path;             /* pfmm_path                                            */
@@ -165,14 +174,15 @@ pfmm_status pfmm_plan_describe(const pfmm_plan* plan, pfmm_plan_desc* out);
 /* Apply the periodic operator.
  *   src  [2][ns]      source coordinates (x row then y row)
  *   q    [nrhs][ns]   strengths (Laplace, modhelm) or
- *        [nrhs][2][ns] forces (Stokes)
+ *        [nrhs][2][ns] forces (Stokes, modified Stokes)
  *   trg  [2][nt]      target coordinates; may be the same pointer as src with
  *                     nt == ns (targets = sources; self pairs are skipped,
  *                     and so is any pair at exactly zero distance)
  *   pot  [nrhs][nt]   potential (Laplace, modhelm) or
- *        [nrhs][2][nt] velocity (Stokes); may be NULL for scalar kernels
+ *        [nrhs][2][nt] velocity (Stokes, modified Stokes); may be NULL for
+ *                     scalar kernels
  *   grad [nrhs][2][nt] gradient of the potential (scalar kernels) or NULL;
- *                     must be NULL for Stokes
+ *                     must be NULL for Stokes and modified Stokes
  * Outputs are overwritten.  ns, nt >= 0 and <= the plan's maxima. */
 pfmm_status pfmm_execute(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns,
                          const double* src, const double* q, int64_t nt, const double* trg,

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # PFMM_LIB overrides the library path (profiling experiments only)
 LIB_PATH = os.environ.get("PFMM_LIB") or os.path.join(HERE, "libpfmm.so")
 
-PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES = 0, 1, 2
+PFMM_LAPLACE, PFMM_MODHELM, PFMM_STOKES, PFMM_MSTOKES = 0, 1, 2, 3
 PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
 PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC = 1, 2, 4, 8, 16

@@ -1,6 +1,7 @@
 // Modified Bessel functions K0, K1 of real argument x > 0 for the modified
 // Helmholtz Green's function (1/2pi) K0(beta r) and its gradient
-// -(beta/2pi) K1(beta r) r_hat.  CUDA has no K0/K1; these are written from
+// -(beta/2pi) K1(beta r) r_hat, and the combination K1(x)/x - 1/x^2 of the
+// modified Stokeslet.  CUDA has no K0/K1; these are written from
 // the published methods named below.
 #pragma once
 #include <cuda_runtime.h>
@@ -91,6 +92,32 @@ __device__ __forceinline__ void k01f_x2(float x2, float* k0, float* k1ix) {
   const float y = 2.0f * ix;
   *k0 = e * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
   *k1ix = e * ix * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
+}
+
+// K0(x) and E(x) = K1(x)/x - 1/x^2 from x^2 (the modified Stokeslet).  For
+// x <= 2 the A&S 9.8.7 form x K1 = x^2 ln(x/2) p1 + q1(y), q1 = 1 + y q1'(y),
+// gives E = ln(x/2) p1 + q1'(y) / 4 (y / x^2 = 1/4) with no cancellation; for
+// x > 2, E = K1/x - 1/x^2 directly (|1/x^2| <= 1/4, no cancellation either).
+__device__ __forceinline__ void k0ef_x2(float x2, float* k0, float* e) {
+  if (x2 <= 4.0f) {
+    const float t2 = x2 * (1.0f / 14.0625f);
+    const float i0 = 1.0f + t2 * (3.5156229f + t2 * (3.0899424f + t2 * (1.2067492f + t2 * (0.2659732f + t2 * (0.0360768f + t2 * 0.0045813f)))));
+    const float p1 = 0.5f + t2 * (0.87890594f + t2 * (0.51498869f + t2 * (0.15084934f + t2 * (0.02658733f + t2 * (0.00301532f + t2 * 0.00032411f)))));
+    const float y = 0.25f * x2;
+    const float lg = 0.34657359027997264f * mufu::lg2(y);
+    *k0 = -lg * i0 + (-0.57721566f + y * (0.42278420f + y * (0.23069756f + y * (0.03488590f + y * (0.00262698f + y * (0.00010750f + y * 0.0000074f))))));
+    const float q1p = 0.15443144f + y * (-0.67278579f + y * (-0.18156897f + y * (-0.01919402f + y * (-0.00110404f + y * (-0.00004686f)))));
+    *e = lg * p1 + 0.25f * q1p;
+    return;
+  }
+  const float ix = mufu::rsqrt(x2);
+  const float x = x2 * ix;
+  const float rx = mufu::rsqrt(x);
+  const float ex = mufu::ex2(-1.4426950408889634f * x) * rx;
+  const float y = 2.0f * ix;
+  *k0 = ex * (1.25331414f + y * (-0.07832358f + y * (0.02189568f + y * (-0.01062446f + y * (0.00587872f + y * (-0.00251540f + y * 0.00053208f))))));
+  const float k1ix = ex * ix * (1.25331414f + y * (0.23498619f + y * (-0.03655620f + y * (0.01504268f + y * (-0.00780353f + y * (0.00325614f + y * (-0.00068245f)))))));
+  *e = k1ix - ix * ix;
 }
 
 // Packed (two lanes) versions of k0f_x2 / k01f_x2, one branch per formula:
@@ -212,6 +239,37 @@ __device__ __forceinline__ void k01d(double x, double* k0, double* k1) {
     double e = exp(-x) * h;
     *k0 = e * s0;
     *k1 = e * s1;
+  }
+}
+
+// FP64 K0(x) and E(x) = K1(x)/x - 1/x^2: for x <= 2 from the series of k01d
+// with the 1/x term of K1 left out (E = ln(x/2) I1(x)/x - S1/4), otherwise
+// from k01d.
+__device__ __forceinline__ void k0ed(double x, double* k0, double* e) {
+  const double eg = 0.57721566490153286061;
+  if (x <= 2.0) {
+    double z = 0.25 * x * x;
+    double tk = 1.0, t1 = 1.0, H = 0.0;
+    double I0 = 0.0, S0 = 0.0, I1x = 0.0, S1 = 0.0;
+    for (int k = 0; k < 30; ++k) {
+      if (k > 0) {
+        tk *= z / ((double)k * k);
+        t1 *= z / ((double)k * (k + 1));
+        H += 1.0 / k;
+      }
+      I0 += tk;
+      S0 += H * tk;
+      I1x += t1;
+      S1 += (-2.0 * eg + 2.0 * H + 1.0 / (k + 1)) * t1;
+    }
+    I1x *= 0.5;  // I1(x) / x
+    double lg = log(0.5 * x);
+    *k0 = -(lg + eg) * I0 + S0;
+    *e = lg * I1x - 0.25 * S1;
+  } else {
+    double k1;
+    k01d(x, k0, &k1);
+    *e = k1 / x - 1.0 / (x * x);
   }
 }
 

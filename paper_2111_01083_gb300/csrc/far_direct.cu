@@ -10,6 +10,11 @@
 //                   south_thm_lap, west_thm_lap, south_thm_s, west_thm_s)
 //   k_far_weights : lattice weights D (FP64), w = D c
 //   k_far_eval    : u = Re(L w) at the targets (+ gradient / Stokes velocity)
+//
+// Modified Stokes (Theorems south_thm_ms, west_thm_ms) runs the three far
+// kernels twice, once per plane-wave family (Far::msfam): the beta family
+// (decay chi_m, kappa) and the Laplace family (|alpha_m|, |lambda|), each with
+// two force channels and 2 x 2 blocks; the second pass adds to the first.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -134,6 +139,12 @@ struct Term {
   double a, b, w;
 };
 
+// plane waves with decay sqrt(a^2 + beta^2) (modified Helmholtz, the modified
+// Stokes beta family) or |a| (Laplace, Stokes, the modified Stokes Laplace family)
+__device__ __forceinline__ bool decays_beta(const Far& f) {
+  return f.kernel == PFMM_MODHELM || (f.kernel == PFMM_MSTOKES && f.msfam == 0);
+}
+
 __device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) {
   Term T;
   int mlo = f.mode0 ? 0 : 1;
@@ -141,7 +152,7 @@ __device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) 
     T.part = t < f.nsn ? 0 : 1;
     T.m = (t < f.nsn ? t : t - f.nsn) + mlo;
     T.a = 2.0 * M_PI * T.m / g.d;
-    T.b = (f.kernel == PFMM_MODHELM) ? sqrt(T.a * T.a + f.beta * f.beta) : fabs(T.a);
+    T.b = decays_beta(f) ? sqrt(T.a * T.a + f.beta * f.beta) : fabs(T.a);
     T.w = 0;
   } else {
     int n = t - 2 * f.nsn;
@@ -150,7 +161,7 @@ __device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) 
     T.m = n;
     T.a = f.nodes[2 * n];
     T.w = f.nodes[2 * n + 1];
-    T.b = (f.kernel == PFMM_MODHELM) ? sqrt(T.a * T.a + f.beta * f.beta) : T.a;
+    T.b = decays_beta(f) ? sqrt(T.a * T.a + f.beta * f.beta) : T.a;
   }
   return T;
 }
@@ -169,8 +180,8 @@ template <typename T, int KER>
 __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns, int chunk, const T* __restrict__ sx,
                                                            const T* __restrict__ sy, const int* __restrict__ sU,
                                                            const T* __restrict__ qv, double* __restrict__ coef) {
-  constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
-  constexpr int NCH = (KER == PFMM_STOKES) ? 4 : 1;
+  constexpr int NC = (KER == PFMM_STOKES || KER == PFMM_MSTOKES) ? 2 : 1;
+  constexpr int NCH = (KER == PFMM_STOKES) ? 4 : NC;
   __shared__ T s_x[kFormSub], s_y[kFormSub];
   __shared__ T s_xw[kFormSub], s_yw[kFormSub];  // west/east frame coordinates
   __shared__ int s_U[kFormSub];
@@ -184,7 +195,7 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
   const T a = (T)tm.a, b = (T)tm.b;
   const T sgn = (tm.part == 0 || tm.part == 2) ? T(1) : T(-1);
   const bool sn = tm.part < 2;
-  const bool we_m1 = !sn && (KER != PFMM_MODHELM);
+  const bool we_m1 = !sn && (KER == PFMM_LAPLACE || KER == PFMM_STOKES);
   const double inv_d = 1.0 / g.d;
 
   double acc[kRB][NCH][2];
@@ -253,6 +264,12 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
           const T s = s_q[r][0][jj];
           sub[r][0][0] += Qr * s;
           sub[r][0][1] += Qi * s;
+        } else if (KER == PFMM_MSTOKES) {
+          const T fx = s_q[r][0][jj], fy = s_q[r][1][jj];
+          sub[r][0][0] += Qr * fx;
+          sub[r][0][1] += Qi * fx;
+          sub[r][NCH - 1][0] += Qr * fy;
+          sub[r][NCH - 1][1] += Qi * fy;
         } else {
           const T fx = s_q[r][0][jj], fy = s_q[r][1][jj];
           const T cd = sn ? y : x;
@@ -307,7 +324,7 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
   const int K = f.kernel;
   if (t == 0) {
     double mq = mom[r * 8 + 0], mfy = mom[r * 8 + 1], mabs = mom[r * 8 + 2], my = mom[r * 8 + 3];
-    if (K != PFMM_MODHELM) {
+    if (K == PFMM_LAPLACE || K == PFMM_STOKES) {
       double net = (K == PFMM_STOKES) ? fmax(fabs(mq), fabs(mfy)) : fabs(mq);
       if (net > 1e-8 * mabs + 1e-300) atomicOr(status, ST_NOT_NEUTRAL);
       // the m = 0 mode of the south/north parts; none in the singly periodic case
@@ -326,6 +343,20 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
     return dcx{p[0], p[1]};
   };
   const bool north = tm.part == 1, east = tm.part == 3;
+  if (K == PFMM_MSTOKES) {
+    dcx D[2][2];
+    double fac = 1.0;
+    if (tm.part < 2) {
+      lw::ms_sn(d, xi, eta, tm.a, tm.b, f.beta, f.msfam, north, D);
+      fac = (tm.m == 0) ? 1.0 : 2.0;  // +-m pairs
+    } else {
+      lw::ms_we(fr, g.wc, g.ws, g.m0, tm.a, tm.b, tm.w, f.beta, f.msfam, east, D);
+    }
+    const dcx c[2] = {C(0), C(1)};
+    for (int i = 0; i < 2; ++i)
+      store_w(wts + (((size_t)r * 2 + i) * f.nterm + t), cscale(cadd(cmul(D[i][0], c[0]), cmul(D[i][1], c[1])), fac));
+    return;
+  }
   if (K != PFMM_STOKES) {
     dcx D;
     double fac = 1.0;
@@ -363,8 +394,10 @@ template <typename T, typename T2, int KER>
 __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt, const T* __restrict__ tx,
                                                            const T* __restrict__ ty, const int* __restrict__ tU,
                                                            const T2* __restrict__ wts, const double* __restrict__ mom,
-                                                           int64_t os, double* __restrict__ pot, double* __restrict__ grad) {
-  constexpr int NW = (KER == PFMM_STOKES) ? 4 : 1;
+                                                           int64_t os, double* __restrict__ pot, double* __restrict__ grad,
+                                                           int accum) {
+  constexpr bool VEC = KER == PFMM_STOKES || KER == PFMM_MSTOKES;
+  constexpr int NW = (KER == PFMM_STOKES) ? 4 : (KER == PFMM_MSTOKES ? 2 : 1);
   __shared__ T s_a[kEvalChunk], s_b[kEvalChunk];
   __shared__ int s_m[kEvalChunk], s_part[kEvalChunk];
   __shared__ T2 s_w[kRB][NW][kEvalChunk];
@@ -380,7 +413,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   const double xd = in ? (double)x / g.d : 0.0;
   // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy].  Compensated in FP32:
   // a few hundred terms of the size of the result are summed per target.
-  constexpr int NA = (KER == PFMM_STOKES) ? 2 : 3;
+  constexpr int NA = VEC ? 2 : 3;
   dm::KSum<T> acc[kRB][NA];
 
   for (int t0 = 0; t0 < f.nterm; t0 += kEvalChunk) {
@@ -421,7 +454,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
         Mi = Li;
       } else {
         const T sx = part == 2 ? T(1) : T(-1);
-        if (KER != PFMM_MODHELM) {
+        if (KER == PFMM_LAPLACE || KER == PFMM_STOKES) {
           dm::expm1c(-sx * b * xw, a * yw, &Mr, &Mi);
           Lr = Mr + T(1);
           Li = Mi;
@@ -437,7 +470,13 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
       }
 #pragma unroll
       for (int r = 0; r < kRB; ++r) {
-        if (KER != PFMM_STOKES) {
+        if (KER == PFMM_MSTOKES) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const T2 w = s_w[r][c][k];
+            acc[r][c].add(Lr * w.x - Li * w.y);
+          }
+        } else if (KER != PFMM_STOKES) {
           const T2 w = s_w[r][0][k];
           const T Pr = Lr * w.x - Li * w.y, Pi = Lr * w.y + Li * w.x;
           acc[r][0].add(Mr * w.x - Mi * w.y);
@@ -465,10 +504,12 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   for (int r = 0; r < nr; ++r) {
     const double cc = mom[(r0 + r) * 8 + 4];
     const double yd = (double)y;
-    if (KER == PFMM_STOKES) {
+    if (VEC) {
       double ux = acc[r][0].value() + cc * yd, uy = acc[r][1].value();
-      pot[((size_t)(r0 + r) * 2) * os + l] = R[0] * ux + R[2] * uy;
-      pot[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * ux + R[3] * uy;
+      double* px = pot + ((size_t)(r0 + r) * 2) * os + l;
+      double* py = pot + ((size_t)(r0 + r) * 2 + 1) * os + l;
+      *px = (accum ? *px : 0.0) + R[0] * ux + R[2] * uy;
+      *py = (accum ? *py : 0.0) + R[1] * ux + R[3] * uy;
     } else {
       double p = acc[r][0].value() + cc * yd;
       double gx = acc[r][1].value(), gy = acc[r][2].value() + cc;
@@ -498,7 +539,8 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
     k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
                                                    (int*)(ws + L.trgU), status);
   g_launches = (!self && nt > 0) ? 3 : 2;
-  const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) && p->opts.kernel != PFMM_MODHELM;
+  const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) &&
+                      (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);
   if (project) {
     k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (double*)(ws + L.moments));
     ++g_launches;
@@ -509,19 +551,23 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   return cudaGetLastError();
 }
 
+// One pass of formation, weights and evaluation for the terms of `f`.  The
+// modified Stokes Laplace family (second = true) takes its nodes after the
+// beta family's, its coefficients and weights after the beta family's, and
+// adds to the velocity the first pass wrote.
 template <typename T, typename T2, int KER>
-static cudaError_t run_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
-                                  double* grad, cudaStream_t st) {
+static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* ws, int64_t ns, int64_t nt,
+                                  bool self, double* pot, double* grad, cudaStream_t st) {
   const Layout& L = p->lay;
-  Far f = p->far;
-  f.nodes = (const double*)(ws + L.nodes);
+  const int nw = (KER == PFMM_STOKES) ? 4 : (KER == PFMM_MSTOKES ? 2 : 1);  // weight rows per rhs
+  f.nodes = (const double*)(ws + L.nodes) + (second ? 2 * p->far.Nq : 0);
   const Geom& g = p->geom;
   const bool mixed = sizeof(T) == 4;
   const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
   const T* sy = sx + ns;
   const int* sU = (const int*)(ws + L.srcU);
   const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
-  double* coef = (double*)(ws + L.coef);
+  double* coef = (double*)(ws + L.coef) + (second ? (size_t)f.nrhs * p->far.nch * p->far.nterm * 2 : 0);
   double* mom = (double*)(ws + L.moments);
   int nrg = cdiv_i(f.nrhs, kRB);
   g_launches = (f.nterm > 0) ? 3 : 2;
@@ -534,14 +580,15 @@ static cudaError_t run_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int6
     dim3 grid(nchunk, ny, nrg);
     k_far_form<T, KER><<<grid, kFormThreads, 0, st>>>(f, g, (int)ns, chunk, sx, sy, sU, qv, coef);
   }
-  T2* w = (T2*)(ws + L.wts);
+  T2* w = (T2*)(ws + L.wts) + (second ? (size_t)f.nrhs * nw * p->far.nterm : 0);
   dim3 gw(cdiv_i(std::max(1, f.nterm), 128), f.nrhs);
   k_far_weights<T2><<<gw, 128, 0, st>>>(f, g, coef, mom, w, (int*)(ws + L.status));
   const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
   const T* ty = tx + nt;
   const int* tU = self ? sU : (const int*)(ws + L.trgU);
   dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
-  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad);
+  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad,
+                                                       second ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -550,14 +597,25 @@ cudaError_t launch_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t 
   const bool mixed = p->opts.precision == PFMM_MIXED;
   switch (p->opts.kernel) {
     case PFMM_LAPLACE:
-      return mixed ? run_far_direct<float, float2, PFMM_LAPLACE>(p, ws, ns, nt, self, pot, grad, st)
-                   : run_far_direct<double, double2, PFMM_LAPLACE>(p, ws, ns, nt, self, pot, grad, st);
+      return mixed ? run_far_direct<float, float2, PFMM_LAPLACE>(p, p->far, false, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_LAPLACE>(p, p->far, false, ws, ns, nt, self, pot, grad, st);
     case PFMM_MODHELM:
-      return mixed ? run_far_direct<float, float2, PFMM_MODHELM>(p, ws, ns, nt, self, pot, grad, st)
-                   : run_far_direct<double, double2, PFMM_MODHELM>(p, ws, ns, nt, self, pot, grad, st);
+      return mixed ? run_far_direct<float, float2, PFMM_MODHELM>(p, p->far, false, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_MODHELM>(p, p->far, false, ws, ns, nt, self, pot, grad, st);
+    case PFMM_MSTOKES: {
+      cudaError_t e = mixed
+          ? run_far_direct<float, float2, PFMM_MSTOKES>(p, p->far, false, ws, ns, nt, self, pot, grad, st)
+          : run_far_direct<double, double2, PFMM_MSTOKES>(p, p->far, false, ws, ns, nt, self, pot, grad, st);
+      const int n1 = g_launches;
+      if (e != cudaSuccess) return e;
+      e = mixed ? run_far_direct<float, float2, PFMM_MSTOKES>(p, p->far2, true, ws, ns, nt, self, pot, grad, st)
+                : run_far_direct<double, double2, PFMM_MSTOKES>(p, p->far2, true, ws, ns, nt, self, pot, grad, st);
+      g_launches += n1;
+      return e;
+    }
     default:
-      return mixed ? run_far_direct<float, float2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st)
-                   : run_far_direct<double, double2, PFMM_STOKES>(p, ws, ns, nt, self, pot, grad, st);
+      return mixed ? run_far_direct<float, float2, PFMM_STOKES>(p, p->far, false, ws, ns, nt, self, pot, grad, st)
+                   : run_far_direct<double, double2, PFMM_STOKES>(p, p->far, false, ws, ns, nt, self, pot, grad, st);
   }
 }
 

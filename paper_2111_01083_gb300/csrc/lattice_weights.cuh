@@ -7,6 +7,7 @@
 //   scalar west/east     Theorem west_thm / west_thm_lap, general m0
 //   Stokes south/north   Theorem south_thm_s (Eq. pssm)
 //   Stokes west/east     Theorem west_thm_s (Eq. pssw0), general m0
+//   mod. Stokes          Theorems south_thm_ms, west_thm_ms (Eqs. pmss1, pmsw0)
 //
 // North is the complex conjugate of south (coordinate terms change sign for
 // Stokes), east the conjugate of west.
@@ -147,6 +148,69 @@ __device__ __forceinline__ void we_stokes(const WeFrame& fr, double c, double s,
         }
       Da[i][j] = a;
       Db[i][j] = b;
+    }
+}
+
+// Modified Stokes south (north: conj), mode m with alpha = a, decay b:
+//   beta family (fam 0, b = chi):      D = F [[chi, i a], [i a, -a^2/chi]],
+//   Laplace family (fam 1, b = |a|):   D = F [[-|a|, -i a], [-i a, |a|]],
+//   F = e^{-2Q} / ((1 - e^{-Q}) 2 beta^2 d),  Q = b eta - i a xi.
+__device__ __forceinline__ void ms_sn(double d, double xi, double eta, double a, double b, double beta, int fam,
+                                      bool north, dcx D[2][2]) {
+  const dcx e1 = cexp_({-b * eta, a * xi});
+  const dcx F = cdiv(cmul(e1, e1), cscale({1.0 - e1.r, -e1.i}, 2.0 * beta * beta * d));
+  dcx M[2][2];
+  if (fam == 0) {
+    M[0][0] = {b, 0.0};
+    M[0][1] = M[1][0] = {0.0, a};
+    M[1][1] = {-a * a / b, 0.0};
+  } else {
+    M[0][0] = {-b, 0.0};
+    M[0][1] = M[1][0] = {0.0, -a};
+    M[1][1] = {b, 0.0};
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      D[i][j] = cmul(F, M[i][j]);
+      if (north) D[i][j] = conj_(D[i][j]);
+    }
+}
+
+// Modified Stokes west (east: conj), node (lambda, w), decay kappa, in the
+// west/east frame (rotation c, s; blocks returned as Q^T D Q):
+//   D = (w / (2 pi beta^2)) e^{-(m0+1) g} / (1 - e^{-g}) B  Mat,  g = kappa dx - i lambda dy,
+//   B = e^{kappa xr - i lambda yr} + 1 + e^{-kappa xr + i lambda yr},
+//   Mat = [[-lambda^2/kappa, i lambda], [i lambda, kappa]] (fam 0) or
+//         [[lambda, -i lambda], [-i lambda, -lambda]] (fam 1, kappa = lambda).
+__device__ __forceinline__ void ms_we(const WeFrame& fr, double c, double s, int m0, double lam, double kap,
+                                      double w, double beta, int fam, bool east, dcx D[2][2]) {
+  const double gr = kap * fr.dx, gi = -lam * fr.dy;
+  const dcx F = cdiv(cexp_({-(m0 + 1) * gr, -(m0 + 1) * gi}), one_minus_exp_neg(gr, gi));
+  const dcx B = cadd(cadd(cexp_({kap * fr.xr, -lam * fr.yr}), {1.0, 0.0}), cexp_({-kap * fr.xr, lam * fr.yr}));
+  const dcx pre = cscale(cmul(F, B), w / (2.0 * M_PI * beta * beta));
+  dcx M[2][2];
+  if (fam == 0) {
+    M[0][0] = {-lam * lam / kap, 0.0};
+    M[0][1] = M[1][0] = {0.0, lam};
+    M[1][1] = {kap, 0.0};
+  } else {
+    M[0][0] = {lam, 0.0};
+    M[0][1] = M[1][0] = {0.0, -lam};
+    M[1][1] = {-lam, 0.0};
+  }
+  dcx A[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      A[i][j] = cmul(pre, M[i][j]);
+      if (east) A[i][j] = conj_(A[i][j]);
+    }
+  const double Q[2][2] = {{c, -s}, {s, c}};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      dcx v = {0, 0};
+      for (int k = 0; k < 2; ++k)
+        for (int l = 0; l < 2; ++l) v = cadd(v, cscale(A[k][l], Q[k][i] * Q[l][j]));
+      D[i][j] = v;
     }
 }
 

@@ -660,10 +660,117 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_batch(const P2PArgs* __rest
   }
 }
 
+// Modified Stokeslet near-image sum (mixed precision).  Per (target, source)
+// the image sum of the kernel is formed as one symmetric 2 x 2 matrix
+//   G = sum_i (A_i I - B_i r_i r_i^T / r_i^2),  A = K0 + E,  B = K0 + 2E,
+//   E = K1(x)/x - 1/x^2,  x = beta r   (times 1/2pi at the end),
+// then applied to each rhs's force (4 FMAs).  Differences are the exact hi/lo
+// form for every pair (there is no cutoff: the kernel decays like 1/r^2), so
+// the target order does not matter; targets are still taken in the sorted
+// order with outputs through the permutation.  Per-source terms are summed
+// 16 at a time in FP32 and those partial sums Kahan-added.
+template <int NIMG, int NR>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_ms(const __grid_constant__ P2PArgs a) {
+  constexpr int CENTER = NIMG / 2;
+  __shared__ float4 s_h[kP2PTile];
+  __shared__ float2 s_f[NR][kP2PTile];
+  const int l = blockIdx.x * kP2PThreads + threadIdx.x;
+  const bool in = l < a.nt;
+  const int r0 = a.r0 + blockIdx.z * NR;
+  const int nr = min(NR, a.nrhs - r0);
+  float thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
+  {
+    const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
+#pragma unroll
+    for (int i = 0; i < NIMG; ++i) {
+      const double vx = tx - a.g.off[i][0], vy = ty - a.g.off[i][1];
+      thx[i] = (float)vx;
+      tlx[i] = (float)(vx - (double)thx[i]);
+      thy[i] = (float)vy;
+      tly[i] = (float)(vy - (double)thy[i]);
+    }
+  }
+  const float beta2 = a.beta_f * a.beta_f;
+  KahanF K[NR][2];
+  float S[NR][2];
+#pragma unroll
+  for (int r = 0; r < NR; ++r)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      K[r][k].s = K[r][k].c = 0.f;
+      S[r][k] = 0.f;
+    }
+  const int j0 = blockIdx.y * a.chunk;
+  const int j1 = min(a.ns, j0 + a.chunk);
+  for (int jb = j0; jb < j1; jb += kP2PTile) {
+    const int nb = min(kP2PTile, j1 - jb);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb; k += kP2PThreads) {
+      s_h[k] = a.s_hl[jb + k];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const bool v = r < nr;
+        s_f[r][k] = make_float2(v ? a.qs[((size_t)(r0 + r) * 2) * a.ns + jb + k] : 0.f,
+                                v ? a.qs[((size_t)(r0 + r) * 2 + 1) * a.ns + jb + k] : 0.f);
+      }
+    }
+    __syncthreads();
+    for (int js = 0; js < nb; js += kSubtile) {
+      const int je = min(nb, js + kSubtile);
+#pragma unroll 1
+      for (int jj = js; jj < je; ++jj) {
+        const float4 h = s_h[jj];
+        float g11 = 0.f, g12 = 0.f, g22 = 0.f;
+#pragma unroll
+        for (int i = 0; i < NIMG; ++i) {
+          const float dx = (thx[i] - h.x) + (tlx[i] - h.y);
+          const float dy = (thy[i] - h.z) + (tly[i] - h.w);
+          float r2 = fmaf(dx, dx, dy * dy);
+          float msk = 1.0f;
+          if (i == CENTER) {
+            msk = (r2 > 0.0f) ? 1.0f : 0.0f;  // a target on a source: the pair is skipped
+            r2 = (r2 > 0.0f) ? r2 : 1.0f;
+          }
+          float k0, e;
+          bes::k0ef_x2(beta2 * r2, &k0, &e);
+          const float A = (k0 + e) * msk;
+          const float Bn = (k0 + 2.0f * e) * msk * bes::mufu::rcp(r2);
+          const float bx = Bn * dx;
+          g11 += A - bx * dx;
+          g12 -= bx * dy;
+          g22 += A - Bn * dy * dy;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          const float2 f = s_f[r][jj];
+          S[r][0] = fmaf(g11, f.x, fmaf(g12, f.y, S[r][0]));
+          S[r][1] = fmaf(g12, f.x, fmaf(g22, f.y, S[r][1]));
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          K[r][k].add(S[r][k]);
+          S[r][k] = 0.f;
+        }
+    }
+  }
+  if (!in) return;
+  const int lo = a.t_perm ? a.t_perm[l] : l;
+  const double* R = a.g.rot;
+  const double c = 1.0 / (2.0 * M_PI);
+  for (int r = 0; r < nr; ++r) {
+    const double ux = c * K[r][0].value(), uy = c * K[r][1].value();
+    atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.os + lo, R[0] * ux + R[2] * uy);
+    atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.os + lo, R[1] * ux + R[3] * uy);
+  }
+}
+
 // FP64 reference-precision kernel.
 template <int KER, bool GRAD>
 __global__ void __launch_bounds__(kP2PThreads) k_p2p_f64(P2PArgs a) {
-  constexpr int NC = (KER == PFMM_STOKES) ? 2 : 1;
+  constexpr int NC = (KER == PFMM_STOKES || KER == PFMM_MSTOKES) ? 2 : 1;
   __shared__ double s_x[kP2PTile], s_y[kP2PTile];
   __shared__ double s_q[4][NC][kP2PTile];
   const int l = blockIdx.x * kP2PThreads + threadIdx.x;
@@ -713,6 +820,18 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_f64(P2PArgs a) {
             acc[r][0] += lg * fx + s * dx;
             acc[r][1] += lg * fy + s * dy;
           }
+        } else if (KER == PFMM_MSTOKES) {
+          // (1/2pi) (A I - B r r^T / r^2), A = K0 + E, B = K0 + 2E
+          double k0, e;
+          bes::k0ed(a.beta * sqrt(r2), &k0, &e);
+          const double c = 1.0 / (2.0 * M_PI);
+          const double A = c * (k0 + e), Bn = c * (k0 + 2.0 * e) / r2;
+          for (int r = 0; r < nr; ++r) {
+            const double fx = s_q[r][0][jj], fy = s_q[r][NC - 1][jj];
+            const double s = (dx * fx + dy * fy) * Bn;
+            acc[r][0] += A * fx - s * dx;
+            acc[r][1] += A * fy - s * dy;
+          }
         } else {
           const double rr = sqrt(r2);
           double k0, k1;
@@ -733,7 +852,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_f64(P2PArgs a) {
   if (!in) return;
   const double* R = a.g.rot;
   for (int r = 0; r < nr; ++r) {
-    if (KER == PFMM_STOKES) {
+    if (KER == PFMM_STOKES || KER == PFMM_MSTOKES) {
       atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.os + l, R[0] * acc[r][0] + R[2] * acc[r][1]);
       atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.os + l, R[1] * acc[r][0] + R[3] * acc[r][1]);
     } else {
@@ -807,6 +926,35 @@ static void dispatch_img(P2PArgs a, bool grad, int nrhs, int ntb, int nsc, cudaS
     dispatch_nr<KER, 15>(a, grad, nrhs, ntb, nsc, st);
 }
 
+// Modified Stokes: rhs in groups of 4, 2, 1; 9 or 15 images.
+template <int NIMG>
+static void launch_ms_img(P2PArgs a, int nrhs, int ntb, int nsc, cudaStream_t st) {
+  int r = 0;
+  while (r < nrhs) {
+    const int left = nrhs - r;
+    a.r0 = r;
+    ++g_launches;
+    if (left >= 4) {
+      const int ng = left / 4;
+      k_p2p_ms<NIMG, 4><<<dim3(ntb, nsc, ng), kP2PThreads, 0, st>>>(a);
+      r += 4 * ng;
+    } else if (left >= 2) {
+      k_p2p_ms<NIMG, 2><<<dim3(ntb, nsc, 1), kP2PThreads, 0, st>>>(a);
+      r += 2;
+    } else {
+      k_p2p_ms<NIMG, 1><<<dim3(ntb, nsc, 1), kP2PThreads, 0, st>>>(a);
+      r += 1;
+    }
+  }
+}
+
+static void launch_ms(const P2PArgs& a, int nrhs, int ntb, int nsc, cudaStream_t st) {
+  if (a.g.nimg == 9)
+    launch_ms_img<9>(a, nrhs, ntb, nsc, st);
+  else
+    launch_ms_img<15>(a, nrhs, ntb, nsc, st);
+}
+
 void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
                    P2PArgs* out) {
   const Layout& L = p->lay;
@@ -868,7 +1016,9 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
   *out = a;
 }
 
-int p2p_targets_per_block(int kernel) { return kP2PThreads * (kernel == PFMM_MODHELM ? 1 : 2); }
+int p2p_targets_per_block(int kernel) {
+  return kP2PThreads * ((kernel == PFMM_LAPLACE || kernel == PFMM_STOKES) ? 2 : 1);
+}
 
 int fill_sort_cells(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, int64_t off_s, int64_t off_t,
                     SortCell* out) {
@@ -919,7 +1069,7 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
   P2PArgs a;
   fill_p2p_args(p, ws, ns, nt, self, pot, grad, &a);
   set_work_counter(p, ws, p->prof, &a);
-  const bool packed = mixed && p->opts.kernel != PFMM_MODHELM;  // two targets per thread
+  const bool packed = mixed && (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);  // two targets per thread
   const int ntb = cdivl(nt, kP2PThreads * (packed ? 2 : 1));
   const int nrg = mixed ? 1 : cdivl(a.nrhs, 4);
   // split the sources so that the grid holds >= ~32 blocks per SM
@@ -932,6 +1082,7 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
     switch (p->opts.kernel) {
       case PFMM_LAPLACE: dispatch_img<PFMM_LAPLACE>(a, g, a.nrhs, ntb, nsc, st); break;
       case PFMM_MODHELM: dispatch_img<PFMM_MODHELM>(a, g, a.nrhs, ntb, nsc, st); break;
+      case PFMM_MSTOKES: launch_ms(a, a.nrhs, ntb, nsc, st); break;
       default: dispatch_img<PFMM_STOKES>(a, false, a.nrhs, ntb, nsc, st); break;
     }
   } else {
@@ -946,6 +1097,7 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
         if (g) k_p2p_f64<PFMM_MODHELM, true><<<grid, kP2PThreads, 0, st>>>(a);
         else k_p2p_f64<PFMM_MODHELM, false><<<grid, kP2PThreads, 0, st>>>(a);
         break;
+      case PFMM_MSTOKES: k_p2p_f64<PFMM_MSTOKES, false><<<grid, kP2PThreads, 0, st>>>(a); break;
       default: k_p2p_f64<PFMM_STOKES, false><<<grid, kP2PThreads, 0, st>>>(a); break;
     }
   }

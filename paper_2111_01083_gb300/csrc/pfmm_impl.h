@@ -41,6 +41,7 @@ struct Far {
   int nrhs;
   int nch;           // coefficient channels per rhs: 1 (scalar) or 4 (Stokes: a_x, a_y, b_x, b_y)
   int rows3;         // west/east over the image rows n = -1, 0, 1 (doubly periodic) or n = 0 only (P1)
+  int msfam;         // modified Stokes: 0 the beta family (decay chi, kappa), 1 the Laplace family (|alpha|, |lambda|)
   const double* nodes;  // device [Nq][2] (lambda_n, w_n), in workspace
 };
 
@@ -95,11 +96,13 @@ struct pfmm_plan {
   pfmm_opts opts;
   pfmm::Geom geom;
   pfmm::Far far;
+  pfmm::Far far2;           // modified Stokes: the Laplace family (far: the beta family); nterm 0 otherwise
   int64_t ns_max, nt_max;
   int nout;                 // output components per rhs for 'pot' (1 scalar, 2 Stokes)
   int ncomp;                // strength components (1 scalar, 2 Stokes)
   int path;                 // resolved path
-  // west/east quadrature (host copy)
+  // west/east quadrature (host copy); modified Stokes: the beta family's
+  // far.Nq nodes, then the Laplace family's far2.Nq
   int Nq;
   double* nodes_h;          // [Nq][2]
   // NUFFT parameters

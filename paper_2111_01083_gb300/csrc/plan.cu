@@ -280,15 +280,20 @@ const char* pfmm_version(void) { return "pfmm-gb300 0.1 (sm_103a)"; }
 pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max, pfmm_plan** out) {
   if (!o || !out) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
-  if (o->kernel < 0 || o->kernel > 2) return fail(PFMM_ERR_INVALID_ARG, "bad kernel %d", o->kernel);
+  if (o->kernel < 0 || o->kernel > 3) return fail(PFMM_ERR_INVALID_ARG, "bad kernel %d", o->kernel);
   if (o->precision < 0 || o->precision > 1) return fail(PFMM_ERR_INVALID_ARG, "bad precision %d", o->precision);
   if (o->path < 0 || o->path > 2) return fail(PFMM_ERR_INVALID_ARG, "bad path %d", o->path);
   if (o->nrhs < 1 || o->nrhs > 64) return fail(PFMM_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
   if (ns_max < 0 || nt_max < 0 || ns_max > (int64_t(1) << 31) || nt_max > (int64_t(1) << 31))
     return fail(PFMM_ERR_INVALID_ARG, "ns_max/nt_max out of range");
   if (!(o->tol >= 1e-14 && o->tol <= 1e-2)) return fail(PFMM_ERR_TOLERANCE, "tol must be in [1e-14, 1e-2]");
-  if (o->kernel == PFMM_MODHELM && !(o->beta > 0 && std::isfinite(o->beta)))
-    return fail(PFMM_ERR_INVALID_ARG, "beta must be > 0 for the modified Helmholtz kernel");
+  if ((o->kernel == PFMM_MODHELM || o->kernel == PFMM_MSTOKES) && !(o->beta > 0 && std::isfinite(o->beta)))
+    return fail(PFMM_ERR_INVALID_ARG, "beta must be > 0 for the modified Helmholtz and modified Stokes kernels");
+  if (o->kernel == PFMM_MSTOKES) {
+    if (o->flags & PFMM_SINGLY_PERIODIC)
+      return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel is doubly periodic only");
+    if (o->path == PFMM_PATH_NUFFT) return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel uses the direct path");
+  }
   if (o->flags & ~127u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~127u);
   if ((o->flags & PFMM_FAR_ONLY) && (o->flags & PFMM_NEAR_ONLY))
     return fail(PFMM_ERR_INVALID_ARG, "FAR_ONLY and NEAR_ONLY are exclusive");
@@ -330,7 +335,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   p->geom = g;
   p->ns_max = ns_max;
   p->nt_max = nt_max;
-  p->ncomp = (o->kernel == PFMM_STOKES) ? 2 : 1;
+  p->ncomp = (o->kernel == PFMM_STOKES || o->kernel == PFMM_MSTOKES) ? 2 : 1;
   p->nout = p->ncomp;
 
   // ---- south/north modes (Eq. mpk0s with eps = tol/10; for beta > 0 modes
@@ -350,21 +355,43 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     while (M >= 1 && bound(M) < eps) --M;
     if (bound(0) < eps) { mode0 = 0; M = 0; }
   }
+  // modified Stokes (Theorem south_thm_ms): the beta family has an m = 0 term
+  // (its block [[beta, 0], [0, 0]]); the Laplace family has none (each image
+  // row is Poisson-summed on its own and the row integral of grad grad^T log r
+  // vanishes).  No pruning: the Laplace family decays like Eq. mpk0s assumes.
+  const bool ms = o->kernel == PFMM_MSTOKES;
+  if (ms) mode0 = 1;
   Far& f = p->far;
   f.kernel = o->kernel;
-  f.beta = (o->kernel == PFMM_MODHELM) ? o->beta : 0.0;
+  f.beta = (o->kernel == PFMM_MODHELM || ms) ? o->beta : 0.0;
   f.M = M;
   f.mode0 = mode0;
   f.nsn = mode0 ? (M + 1) : M;
   f.nrhs = o->nrhs;
-  f.nch = (o->kernel == PFMM_STOKES) ? 4 : 1;
+  f.nch = (o->kernel == PFMM_STOKES) ? 4 : (ms ? 2 : 1);
   f.rows3 = p1 ? 0 : 1;
+  f.msfam = 0;
 
-  std::vector<double> nodes;
-  we_quadrature(g, o->kernel, f.beta, o->tol, nodes);
-  p->Nq = (int)(nodes.size() / 2);
-  f.Nq = p->Nq;
+  std::vector<double> nodes, nodes2;
+  // the modified Stokes beta family integrates in kappa = sqrt(lambda^2 + beta^2)
+  // like modified Helmholtz, the Laplace family in |lambda| like Laplace
+  we_quadrature(g, ms ? PFMM_MODHELM : o->kernel, f.beta, o->tol, nodes);
+  f.Nq = (int)(nodes.size() / 2);
   f.nterm = 2 * f.nsn + 2 * f.Nq;
+  p->far2 = f;
+  p->far2.nterm = 0;
+  p->far2.Nq = 0;
+  if (ms) {
+    we_quadrature(g, PFMM_LAPLACE, 0.0, o->tol, nodes2);
+    Far& f2 = p->far2;
+    f2.msfam = 1;
+    f2.mode0 = 0;
+    f2.nsn = M;
+    f2.Nq = (int)(nodes2.size() / 2);
+    f2.nterm = 2 * f2.nsn + 2 * f2.Nq;
+  }
+  nodes.insert(nodes.end(), nodes2.begin(), nodes2.end());
+  p->Nq = (int)(nodes.size() / 2);
   p->nodes_h = (double*)std::malloc(std::max<size_t>(1, nodes.size()) * sizeof(double));
   if (!nodes.empty()) std::memcpy(p->nodes_h, nodes.data(), nodes.size() * sizeof(double));
 
@@ -380,7 +407,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int path = o->path;
   // the single-block shared-memory FFT handles fine grids up to 8192 points
   if (path == PFMM_PATH_AUTO)
-    path = (M >= 64 && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+    path = (M >= 64 && nf <= 8192 && !ms) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
     pfmm_plan_destroy(p);
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
@@ -448,8 +475,9 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     L.sortd = take(2 * sizeof(pfmm::SortCell));
     L.sortscr = take(mixed ? pfmm::sort_scratch_bytes((int64_t)ns_m + (int64_t)nt_m, 2) : 0);
   }
-  L.coef = take((size_t)nrhs * f.nch * std::max(1, f.nterm) * 2 * sizeof(double));
-  L.wts = take((size_t)nrhs * 4 * std::max(1, f.nterm) * 2 * sizeof(double));
+  // (modified Stokes: both families' coefficients and weights, one after the other)
+  L.coef = take((size_t)nrhs * f.nch * std::max(1, f.nterm + p->far2.nterm) * 2 * sizeof(double));
+  L.wts = take((size_t)nrhs * 4 * std::max(1, f.nterm + p->far2.nterm) * 2 * sizeof(double));
   size_t nuf = 0;
   if (path == PFMM_PATH_NUFFT) {
     // FP64 spread grid [nrhs][nch][n_gl][nf], FP64 spectra F_n(k) [nrhs][nch][n_gl][M+1],
@@ -508,7 +536,7 @@ pfmm_status pfmm_plan_describe(const pfmm_plan* p, pfmm_plan_desc* d) {
   d->we_dir[0] = p->geom.wc;
   d->we_dir[1] = p->geom.ws;
   d->M = p->far.M;
-  d->mode0 = (p->opts.kernel == PFMM_MODHELM) ? p->far.mode0 : 1;
+  d->mode0 = (p->opts.kernel == PFMM_MODHELM || p->opts.kernel == PFMM_MSTOKES) ? p->far.mode0 : 1;
   d->Nq = p->Nq;
   d->path = p->path;
   d->n_gl = p->n_gl; d->nf = p->nf; d->nufft_w = p->nufft_w; d->es_beta = p->es_beta;
@@ -570,8 +598,8 @@ pfmm_status pfmm_execute(pfmm_plan* p, void* workspace, size_t ws_bytes, int64_t
                 (long long)nt, (long long)p->ns_max, (long long)p->nt_max);
   if (!workspace || ws_bytes < p->lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
-  bool stokes = p->opts.kernel == PFMM_STOKES;
-  if (stokes && grad) return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for the Stokes kernel");
+  bool stokes = p->opts.kernel == PFMM_STOKES || p->opts.kernel == PFMM_MSTOKES;
+  if (stokes && grad) return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for the Stokes kernels");
   if (p->opts.flags & PFMM_NO_GRAD) grad = nullptr;
   if (nt > 0 && !pot && !grad) return fail(PFMM_ERR_INVALID_ARG, "no output requested");
   if (nt > 0 && !trg) return fail(PFMM_ERR_INVALID_ARG, "NULL targets");
@@ -592,7 +620,8 @@ pfmm_status pfmm_execute_host(pfmm_plan* p, void* workspace, size_t ws_bytes, in
   if (!workspace || ws_bytes < p->lay.total_host || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total_host);
   if (ns < 0 || nt < 0 || ns > p->ns_max || nt > p->nt_max) return fail(PFMM_ERR_INVALID_ARG, "sizes");
-  if (p->opts.kernel == PFMM_STOKES && grad) return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for Stokes");
+  if ((p->opts.kernel == PFMM_STOKES || p->opts.kernel == PFMM_MSTOKES) && grad)
+    return fail(PFMM_ERR_INVALID_ARG, "grad must be NULL for the Stokes kernels");
   if (p->opts.flags & PFMM_NO_GRAD) grad = nullptr;
   bool self = (trg == src) && (nt == ns);
   cudaStream_t st = (cudaStream_t)stream;
@@ -657,6 +686,7 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* p, void* workspace, size_t ws_bytes,
     return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
   const bool stokes = p->opts.kernel == PFMM_STOKES;
   if (stokes && (dsrc || dtrg)) return fail(PFMM_ERR_INVALID_ARG, "Stokes adjoint: strengths only (dq)");
+  if (p->opts.kernel == PFMM_MSTOKES) return fail(PFMM_ERR_INVALID_ARG, "no adjoint for the modified Stokes kernel");
   if (dtrg && !grad_fwd) return fail(PFMM_ERR_INVALID_ARG, "dtrg needs the forward gradient grad_fwd");
   if (p->opts.flags & (PFMM_FAR_ONLY | PFMM_NEAR_ONLY))
     return fail(PFMM_ERR_INVALID_ARG, "the adjoint is defined for the full operator");

@@ -17,7 +17,9 @@ import numpy as np
 
 from . import _lib
 
-_KER = {"laplace": _lib.PFMM_LAPLACE, "modhelm": _lib.PFMM_MODHELM, "stokes": _lib.PFMM_STOKES}
+_KER = {"laplace": _lib.PFMM_LAPLACE, "modhelm": _lib.PFMM_MODHELM, "stokes": _lib.PFMM_STOKES,
+        "mstokes": _lib.PFMM_MSTOKES}
+_VEC = ("stokes", "mstokes")  # force in, velocity out
 _PREC = {"fp64": _lib.PFMM_FP64, "mixed": _lib.PFMM_MIXED}
 _PATH = {"auto": _lib.PFMM_PATH_AUTO, "direct": _lib.PFMM_PATH_DIRECT, "nufft": _lib.PFMM_PATH_NUFFT}
 _PART = {"total": 0, "far": _lib.PFMM_FAR_ONLY, "near": _lib.PFMM_NEAR_ONLY}
@@ -92,7 +94,7 @@ class PeriodicOp:
         if self_t:
             trg = src
         ns, nt = src.shape[1], trg.shape[1]
-        stokes = self.kernel == "stokes"
+        stokes = self.kernel in _VEC
         if out is None:
             pot = torch.empty((self.nrhs, 2, nt) if stokes else (self.nrhs, nt), dtype=torch.float64,
                               device=src.device)
@@ -113,7 +115,7 @@ class PeriodicOp:
         self_t = trg is None
         trg = src if self_t else np.ascontiguousarray(trg, np.float64)
         ns, nt = src.shape[1], trg.shape[1]
-        stokes = self.kernel == "stokes"
+        stokes = self.kernel in _VEC
         pot = np.empty((self.nrhs, 2, nt) if stokes else (self.nrhs, nt))
         g = np.empty((self.nrhs, 2, nt)) if (grad and not stokes) else None
         ws = self.workspace(host=True)
@@ -227,7 +229,7 @@ class BatchOp:
 
     def alloc_out(self, device, grad=True):
         import torch
-        stokes = self.kernel == "stokes"
+        stokes = self.kernel in _VEC
         pot = torch.empty((self.nrhs, 2, self.NT) if stokes else (self.nrhs, self.NT), dtype=torch.float64,
                           device=device)
         g = torch.empty((self.nrhs, 2, self.NT), dtype=torch.float64, device=device) if (grad and not stokes) else None
@@ -390,7 +392,7 @@ def _make_function():
 
         @staticmethod
         def forward(ctx, op, src, q, trg):
-            pot, grad = op(src, q, trg, grad=op.kernel != "stokes")
+            pot, grad = op(src, q, trg, grad=op.kernel not in _VEC)
             ctx.op = op
             ctx.self_t = trg is None
             ctx.save_for_backward(src, q, trg if trg is not None else src, grad if grad is not None else pot)

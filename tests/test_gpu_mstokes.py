@@ -1,0 +1,113 @@
+"""GPU parity of the modified Stokes kernel (Eq. msgreen; Theorems
+south_thm_ms, west_thm_ms): the CUDA library (through the C ABI) against the
+FP64 oracle's plain method (near images + the paper's factorized far parts,
+pinned in tests/test_oracle_mstokes_pins.py against exact image-row sums).
+
+Tolerances: FP64 path 1e-10, mixed path 1e-6 (relative l2 over all targets,
+rhs and components; no constant is removed: the modified Stokes velocity is
+unique).  Sizes span several 128-source tiles and 256-target blocks with
+ragged tails; forces need no zero net force.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_util import oracle, run_lib
+from oracle import api as oapi
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "mixed": 1e-6}
+LAT = {
+    "square": ((1.0, 0.0), (0.0, 1.0)),
+    "skew": ((1.0, 0.0), (0.3, 0.8)),
+    "hex": ((1.0, 0.0), (0.5, math.sqrt(3) / 2)),
+    "rotated": ((1.2, 0.4), (-0.5, 0.9)),
+    "rect8": ((8.0, 0.0), (0.0, 1.0)),
+}
+
+
+def _case(lat, ns, nt=None, seed=0, nrhs=1, dist="uniform"):
+    e1, e2 = LAT[lat]
+    rng = np.random.default_rng(seed)
+    src = workloads.points(rng, e1, e2, ns, dist)
+    f = rng.standard_normal((nrhs, 2, ns))  # net force not zero
+    trg = None if nt is None else workloads.points(rng, e1, e2, nt)
+    return e1, e2, src, f, trg
+
+
+def _err(got, ref):
+    return oapi.rel_err(got, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("beta", [0.5, 3.0])
+@pytest.mark.parametrize("lat", ["square", "skew", "hex", "rotated", "rect8"])
+def test_total(precision, beta, lat):
+    e1, e2, src, f, trg = _case(lat, 700, nt=333, seed=70)
+    got = run_lib("mstokes", e1, e2, src, f, trg, beta=beta, tol=TOL[precision], precision=precision, grad=False)
+    ref = oracle("mstokes", e1, e2, src, f, trg, beta=beta, how="plain", grad=False)
+    assert _err(got[0], ref[0]) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nrhs", [3, 5])
+def test_self_targets_multi_rhs(precision, nrhs):
+    """targets = sources (self pairs skipped), clustered points, rhs groups of 4/2/1."""
+    e1, e2, src, f, _ = _case("skew", 1100, seed=71, nrhs=nrhs, dist="gmm")
+    got = run_lib("mstokes", e1, e2, src, f, None, beta=2.0, tol=TOL[precision], precision=precision, grad=False)
+    ref = oracle("mstokes", e1, e2, src, f, None, beta=2.0, how="plain", grad=False)
+    assert _err(got[0], ref[0]) < TOL[precision]
+
+
+@pytest.mark.parametrize("part", ["far", "near"])
+@pytest.mark.parametrize("we", ["rotated", "axis"])
+def test_parts_fp64(part, we):
+    e1, e2, src, f, trg = _case("hex", 400, nt=257, seed=72)
+    got = run_lib("mstokes", e1, e2, src, f, trg, beta=1.5, tol=1e-10, precision="fp64", part=part, grad=False, we=we)
+    assert got[2].describe()["m0"] == (1 if we == "rotated" else 2)
+    ref = oracle("mstokes", e1, e2, src, f, trg, beta=1.5, part=part, how="plain", grad=False, we=we)
+    assert _err(got[0], ref[0]) < 1e-10
+
+
+@pytest.mark.parametrize("ns,nt", [(1, 5), (2, 1), (129, 1), (300, 0)])
+def test_tiny_and_empty(ns, nt):
+    e1, e2 = LAT["skew"]
+    rng = np.random.default_rng(73)
+    src = workloads.points(rng, e1, e2, ns)
+    f = rng.standard_normal((1, 2, ns))
+    trg = workloads.points(rng, e1, e2, nt)
+    for precision in ("fp64", "mixed"):
+        got = run_lib("mstokes", e1, e2, src, f, trg, beta=1.0, tol=TOL[precision], precision=precision, grad=False)
+        if nt == 0:
+            assert got[0].size == 0
+            continue
+        ref = oracle("mstokes", e1, e2, src, f, trg, beta=1.0, how="plain", grad=False)
+        assert _err(got[0], ref[0]) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_periodicity(precision, tol):
+    """The field just inside one edge equals the field just inside the
+    opposite edge (Sec. 7), on a 4 x 1 skewed cell."""
+    e1, e2 = (4.0, 0.0), (0.7, 1.0)
+    rng = np.random.default_rng(74)
+    src = workloads.points(rng, e1, e2, 1500, "gmm")
+    f = rng.standard_normal((1, 2, 1500))
+    E = np.array([e1, e2]).T
+    s = rng.uniform(-0.45, 0.45, 200)
+    pairs = []
+    for w in (0, 1):
+        a = np.zeros((2, 200))
+        b = np.zeros((2, 200))
+        a[w], b[w] = -0.5 + 1e-13, 0.5 - 1e-13
+        a[1 - w] = b[1 - w] = s
+        pairs.append((E @ a, E @ b))
+    trg = np.concatenate([x for pr in pairs for x in pr], axis=1)
+    u, _, _ = run_lib("mstokes", e1, e2, src, f, trg, beta=1.0, tol=tol, precision=precision, grad=False)
+    u = u[0]
+    for k in range(2):
+        ua, ub = u[:, 400 * k:400 * k + 200], u[:, 400 * k + 200:400 * k + 400]
+        assert np.linalg.norm(ua - ub) / np.linalg.norm(u) < 2 * tol

@@ -43,7 +43,9 @@ def single_cell(kernel, e1, e2, ns, nt=None, seed=0, dist="uniform", nrhs=1, bet
     """One cell. nt=None means targets = sources (same array)."""
     rng = np.random.default_rng(seed)
     src = points(rng, e1, e2, ns, dist)
-    q = strengths(rng, nrhs, ns, stokes=(kernel == "stokes"))
+    # forces for the Stokes kernels; zero mean except for modified Stokes
+    # (which needs no net-force condition)
+    q = strengths(rng, nrhs, ns, stokes=kernel in ("stokes", "mstokes"), neutral=kernel != "mstokes")
     trg = src if nt is None else points(rng, e1, e2, nt, "uniform")
     return dict(kernel=kernel, beta=beta, e1=tuple(e1), e2=tuple(e2), src=src, q=q, trg=trg,
                 self_targets=nt is None)
@@ -62,6 +64,10 @@ CONFIGS = {
     # near block, the rotated one (e2-perp) a 3 x 3 block
     "stokes_hex_n2e5": dict(kernel="stokes", e1=(1.0, 0.0), e2=(0.5, 0.8660254037844386), ns=200000,
                             nt=200000, seed=7, dist="uniform", tol=1e-6, precision="mixed"),
+    # modified Stokeslet (Brinkman) with beta = 1 on the skew cell: 1e5 sources
+    # with N(0,1) forces (no zero-net-force condition), 1e5 separate targets
+    "mstokes_skew_beta1_n1e5": dict(kernel="mstokes", beta=1.0, e1=(1.0, 0.0), e2=(0.3, 0.8), ns=100000,
+                                    nt=100000, seed=8, dist="uniform", tol=1e-6, precision="mixed"),
     "laplace_adjoint_4x1_n5e4": dict(kernel="laplace", e1=(4.0, 0.0), e2=(0.0, 1.0), ns=50000,
                                      seed=4, dist="uniform", tol=1e-6, precision="mixed"),
     # singly periodic (P1): period e1, 1e5 uniform sources in the strip segment
@@ -79,7 +85,7 @@ def make(name, scale=1.0, seed=None):
     if nt is not None:
         nt = max(1, int(round(nt * scale)))
     w = single_cell(c["kernel"], c["e1"], c["e2"], ns, nt, seed if seed is not None else c["seed"],
-                    c.get("dist", "uniform"))
+                    c.get("dist", "uniform"), beta=c.get("beta", 0.0))
     for k in ("tol", "precision", "path", "nufft_w", "n_gl", "singly"):
         if k in c:
             w[k] = c[k]
