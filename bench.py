@@ -675,7 +675,7 @@ def main():
     nimg = 3 if singly else 3 * (2 * desc["m0"] + 1)
     kname = "k_p2p_ms" if kernel == "mstokes" else "k_p2p_mixed"
     roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
-                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", "k_p2p_mixed_" + args.workload), nimg=nimg)
+                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", f"{kname}_{args.workload}"), nimg=nimg)
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
