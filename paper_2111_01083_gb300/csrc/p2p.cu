@@ -358,18 +358,25 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
-  float thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
+  // hi/lo target coordinates per image, one column per thread in shared
+  // memory (read once per 16-source subtile; registers go to the pair loops)
+  __shared__ float s_tc[4][NIMG][kP2PThreads];
   {
     const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
       double vx = tx - a.g.off[i][0], vy = ty - a.g.off[i][1];
-      thx[i] = (float)vx;
-      tlx[i] = (float)(vx - (double)thx[i]);
-      thy[i] = (float)vy;
-      tly[i] = (float)(vy - (double)thy[i]);
+      const float hx = (float)vx, hy = (float)vy;
+      s_tc[0][i][threadIdx.x] = hx;
+      s_tc[1][i][threadIdx.x] = (float)(vx - (double)hx);
+      s_tc[2][i][threadIdx.x] = hy;
+      s_tc[3][i][threadIdx.x] = (float)(vy - (double)hy);
     }
   }
+  auto thx = [&](int i) { return s_tc[0][i][threadIdx.x]; };
+  auto tlx = [&](int i) { return s_tc[1][i][threadIdx.x]; };
+  auto thy = [&](int i) { return s_tc[2][i][threadIdx.x]; };
+  auto tly = [&](int i) { return s_tc[3][i][threadIdx.x]; };
   KahanF K[NR][NA];
   float S[NR][NA];
 #pragma unroll
@@ -384,7 +391,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   const float cut2 = (50.0f / beta) * (50.0f / beta);
   const float4 tb = a.t_box[bx];
   const float rsm = 2.0f / beta * 1.001f + 1e-6f;  // beta r <= 2 region, with margin
-  float txr[NIMG], tyr[NIMG], txb[NIMG], tyb[NIMG];
+  float txr[NIMG], tyr[NIMG];
 
   // image sums of one source over the images in `any` (`all`: no per-pair
   // cutoff test), then one FMA per rhs
@@ -437,7 +444,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   // Branch-free variant for subtiles where no pair of the warp can have
   // beta r <= 2: every image takes the large-argument fit (K0 at beta r > 88
   // underflows to 0), so the nine chains are independent and interleave.
-  // Coordinates here are pre-scaled by beta (txb, tyb per subtile, the
+  // Coordinates here are scaled by beta (beta txr, beta tyr per pair, the
   // source's in shared memory), so x^2 = dx^2 + dy^2 and K1(x)/x multiplies
   // the scaled difference directly; the fits' variable y = 2/x is folded into
   // their coefficients (c_k 2^k).  ALL: every image active, no per-image test.
@@ -553,31 +560,32 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         const float sxe = e.x + rsm, sye = e.y + rsm;
 #pragma unroll
         for (int i = 0; i < NIMG; ++i) {
-          txr[i] = (thx[i] - c.x) + (tlx[i] - c.y);
-          tyr[i] = (thy[i] - c.z) + (tly[i] - c.w);
+          txr[i] = (thx(i) - c.x) + (tlx(i) - c.y);
+          tyr[i] = (thy(i) - c.z) + (tly(i) - c.w);
           const bool act = (any & (1u << i)) != 0u;
           near |= act && fabsf(txr[i]) < bxe && fabsf(tyr[i]) < bye;
           small |= act && fabsf(txr[i]) < sxe && fabsf(tyr[i]) < sye;
         }
       }
       if (!__any_sync(0xffffffffu, near || small)) {
-#pragma unroll
-        for (int i = 0; i < NIMG; ++i) {
-          txb[i] = beta * txr[i];
-          tyb[i] = beta * tyr[i];
-        }
         if (any == (1u << NIMG) - 1u) {
 #pragma unroll 2
           for (int jj = js; jj < js + kP2PSub; ++jj) {
             const float2 p = s_pb[jj];
-            source_far(jj, any, [&](int i, float& dx, float& dy) { dx = txb[i] - p.x; dy = tyb[i] - p.y; },
+            source_far(jj, any, [&](int i, float& dx, float& dy) {
+              dx = fmaf(beta, txr[i], -p.x);
+              dy = fmaf(beta, tyr[i], -p.y);
+            },
                        std::true_type{});
           }
         } else {
 #pragma unroll 2
           for (int jj = js; jj < js + kP2PSub; ++jj) {
             const float2 p = s_pb[jj];
-            source_far(jj, any, [&](int i, float& dx, float& dy) { dx = txb[i] - p.x; dy = tyb[i] - p.y; },
+            source_far(jj, any, [&](int i, float& dx, float& dy) {
+              dx = fmaf(beta, txr[i], -p.x);
+              dy = fmaf(beta, tyr[i], -p.y);
+            },
                        std::false_type{});
           }
         }
@@ -588,8 +596,8 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         for (int jj = js; jj < js + kP2PSub; ++jj) {
           const float4 h = s_h[jj];
           source_far(jj, any, [&](int i, float& dx, float& dy) {
-            dx = beta * ((thx[i] - h.x) + (tlx[i] - h.y));
-            dy = beta * ((thy[i] - h.z) + (tly[i] - h.w));
+            dx = beta * ((thx(i) - h.x) + (tlx(i) - h.y));
+            dy = beta * ((thy(i) - h.z) + (tly(i) - h.w));
           }, std::false_type{});
         }
       } else {
@@ -600,8 +608,8 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         for (int jj = js; jj < js + kP2PSub; ++jj) {
           const float4 h = s_h[jj];
           source(jj, any, all, [&](int i, float& dx, float& dy) {
-            dx = (thx[i] - h.x) + (tlx[i] - h.y);
-            dy = (thy[i] - h.z) + (tly[i] - h.w);
+            dx = (thx(i) - h.x) + (tlx(i) - h.y);
+            dy = (thy(i) - h.z) + (tly(i) - h.w);
           });
         }
       }
@@ -629,8 +637,13 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   }
 }
 
+// Six resident blocks per SM for the potential-only variants (80 registers,
+// a small spill): measured 7 / 1 / 12 % faster on the 256-cell batch at
+// beta = 1 / 10 / 100 than the unconstrained 121 registers, whose four blocks
+// left the latency of the tile loop exposed.  The gradient variants keep
+// their registers (six blocks would spill ~0.6 KB).
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(const __grid_constant__ P2PArgs a) {
+__global__ void __launch_bounds__(kP2PThreads, GRAD ? 1 : 6) k_p2p_mixed_mh(const __grid_constant__ P2PArgs a) {
   const int j0 = blockIdx.y * a.chunk;
   p2p_mixed_mh_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
 }
@@ -642,7 +655,7 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_mixed_mh(const __grid_const
 // P2PItem is declared in p2p.h
 
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_batch(const P2PArgs* __restrict__ cells,
+__global__ void __launch_bounds__(kP2PThreads, (KER == PFMM_MODHELM && !GRAD) ? 6 : 1) k_p2p_batch(const P2PArgs* __restrict__ cells,
                                                            const P2PItem* __restrict__ items, int nitems,
                                                            int* __restrict__ counter) {
   __shared__ int s_item;
