@@ -206,3 +206,44 @@ def test_total_independent_of_split_and_basis():
     d, _ = api.evaluate("mstokes", 1.7, e1, e2, src, f, trg + np.array(e2)[:, None], how="plain")
     for x in (b, c, d):
         assert api.rel_err(x, a) < 1e-12
+
+
+def test_solves_the_pde():
+    """(beta^2 - Lap) u + grad p = 0 and div u = 0 away from the sources
+    (4th-order differences), zero net force, p = -(d/dx phi[f_x] + d/dy phi[f_y])
+    from the periodic Laplace potential (the modified Stokeslet shares the
+    Stokes pressurelet): pins the whole periodic sum, constant included (the
+    beta^2 u term leaves no free constant)."""
+    from oracle import api
+    rng = np.random.default_rng(81)
+    e1, e2 = (1.0, 0.0), (0.3, 0.8)
+    beta = 1.7
+    src = workloads.points(rng, e1, e2, 12)
+    f = rng.standard_normal((1, 2, 12))
+    f -= f.mean(-1, keepdims=True)
+    E = np.array([e1, e2]).T
+    pts = []
+    while len(pts) < 4:
+        c = workloads.points(rng, e1, e2, 1)[:, 0]
+        dmin = min(np.hypot(*(c[:, None] - src - (E @ np.array([a, b]))[:, None])).min()
+                   for a in (-1, 0, 1) for b in (-1, 0, 1))
+        if dmin > 0.12:
+            pts.append(c)
+    h = 2e-3
+    sh = np.arange(-2, 3) * h
+    d1 = np.array([1, -8, 0, 8, -1]) / (12 * h)
+    d2 = np.array([-1, 16, -30, 16, -1]) / (12 * h * h)
+    P = np.array([c + [s_, 0] for c in pts for s_ in sh] + [c + [0, s_] for c in pts for s_ in sh]).T
+    # reorder to [point][direction][stencil]
+    n = len(pts)
+    P = P.reshape(2, 2, n, 5).transpose(0, 2, 1, 3).reshape(2, -1)
+    u, _ = api.evaluate("mstokes", beta, e1, e2, src, f, P, how="plain")
+    p = api.stokes_pressure(e1, e2, src, f, P, how="plain")
+    u = u[0].reshape(2, n, 2, 5)
+    p = p[0].reshape(n, 2, 5)
+    lap = u[:, :, 0, :] @ d2 + u[:, :, 1, :] @ d2
+    gp = np.stack([p[:, 0, :] @ d1, p[:, 1, :] @ d1])
+    res = beta ** 2 * u[:, :, 0, 2] - lap + gp
+    assert np.abs(res).max() < 1e-7 * np.abs(gp).max()
+    div = u[0, :, 0, :] @ d1 + u[1, :, 1, :] @ d1
+    assert np.abs(div).max() < 1e-6 * np.abs(u[:, :, 0, :] @ d1).max()
