@@ -62,9 +62,8 @@ extern "C" {
  * the fundamental solution of (beta^2 - Lap) u + grad p = 0, div u = 0
  * (beta > 0; no net-force condition).  Forces and velocities are laid out as
  * for STOKES.  Far field by Theorems south_thm_ms / west_thm_ms (direct path
- * only), periodic sum in the paper's order (image rows).  Single-cell
- * pfmm_execute / pfmm_execute_host / pfmm_execute_static only: not in a batch,
- * not for the adjoint, not singly periodic. */
+ * only), periodic sum in the paper's order (image rows).  Single cells and
+ * batches; not for the adjoint, not singly periodic. */
 typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2, PFMM_MSTOKES = 3 } pfmm_kernel;
 
 /* FP64: every step in double precision.

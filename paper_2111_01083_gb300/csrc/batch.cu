@@ -73,8 +73,6 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
       return set_error(PFMM_ERR_INVALID_ARG, "batch cells compute the full operator (cell %d)", c);
     if (cells[c].flags & PFMM_SINGLY_PERIODIC)
       return set_error(PFMM_ERR_INVALID_ARG, "batch cells are doubly periodic (cell %d)", c);
-    if (cells[c].kernel == PFMM_MSTOKES)
-      return set_error(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel runs single cells only");
     if (src_off[c + 1] < src_off[c] || (trg_off && trg_off[c + 1] < trg_off[c]))
       return set_error(PFMM_ERR_INVALID_ARG, "offsets must be non-decreasing (cell %d)", c);
   }
@@ -238,7 +236,8 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
     return set_error(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", b->total);
   if (!src || !q || !pot) return set_error(PFMM_ERR_INVALID_ARG, "NULL sources, strengths or potential");
   if (!b->self && !trg) return set_error(PFMM_ERR_INVALID_ARG, "NULL targets");
-  if (b->kernel == PFMM_STOKES && grad) return set_error(PFMM_ERR_INVALID_ARG, "grad must be NULL for Stokes");
+  if ((b->kernel == PFMM_STOKES || b->kernel == PFMM_MSTOKES) && grad)
+    return set_error(PFMM_ERR_INVALID_ARG, "grad must be NULL for the Stokes kernels");
   cudaStream_t st = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   const double* tr = b->self ? src : trg;

@@ -654,6 +654,9 @@ __global__ void __launch_bounds__(kP2PThreads, GRAD ? 1 : 6) k_p2p_mixed_mh(cons
 // another; the counter is the only shared state.
 // P2PItem is declared in p2p.h
 
+template <int NIMG, int NR>
+__device__ __forceinline__ void p2p_ms_body(const P2PArgs& a, int bx, int j0, int j1, int r0);
+
 template <int KER, int NIMG, int NR, bool GRAD>
 __global__ void __launch_bounds__(kP2PThreads, (KER == PFMM_MODHELM && !GRAD) ? 6 : 1) k_p2p_batch(const P2PArgs* __restrict__ cells,
                                                            const P2PItem* __restrict__ items, int nitems,
@@ -668,6 +671,8 @@ __global__ void __launch_bounds__(kP2PThreads, (KER == PFMM_MODHELM && !GRAD) ? 
     const P2PItem w = items[it];
     if constexpr (KER == PFMM_MODHELM)
       p2p_mixed_mh_body<KER, NIMG, NR, GRAD>(cells[w.cell], w.bx, w.j0, w.j1, w.r0);
+    else if constexpr (KER == PFMM_MSTOKES)
+      p2p_ms_body<NIMG, NR>(cells[w.cell], w.bx, w.j0, w.j1, w.r0);
     else
       p2p_mixed_body<KER, NIMG, NR, GRAD>(cells[w.cell], w.bx, w.j0, w.j1, w.r0);
   }
@@ -683,13 +688,12 @@ __global__ void __launch_bounds__(kP2PThreads, (KER == PFMM_MODHELM && !GRAD) ? 
 // order with outputs through the permutation.  Per-source terms are summed
 // 16 at a time in FP32 and those partial sums Kahan-added.
 template <int NIMG, int NR>
-__global__ void __launch_bounds__(kP2PThreads) k_p2p_ms(const __grid_constant__ P2PArgs a) {
+__device__ __forceinline__ void p2p_ms_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   constexpr int CENTER = NIMG / 2;
   __shared__ float4 s_h[kP2PTile];
   __shared__ float2 s_f[NR][kP2PTile];
-  const int l = blockIdx.x * kP2PThreads + threadIdx.x;
+  const int l = bx * kP2PThreads + threadIdx.x;
   const bool in = l < a.nt;
-  const int r0 = a.r0 + blockIdx.z * NR;
   const int nr = min(NR, a.nrhs - r0);
   float thx[NIMG], tlx[NIMG], thy[NIMG], tly[NIMG];
   {
@@ -713,8 +717,6 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_ms(const __grid_constant__ 
       K[r][k].s = K[r][k].c = 0.f;
       S[r][k] = 0.f;
     }
-  const int j0 = blockIdx.y * a.chunk;
-  const int j1 = min(a.ns, j0 + a.chunk);
   for (int jb = j0; jb < j1; jb += kP2PTile) {
     const int nb = min(kP2PTile, j1 - jb);
     __syncthreads();
@@ -778,6 +780,12 @@ __global__ void __launch_bounds__(kP2PThreads) k_p2p_ms(const __grid_constant__ 
     atomicAdd(a.pot + ((size_t)(r0 + r) * 2) * a.os + lo, R[0] * ux + R[2] * uy);
     atomicAdd(a.pot + ((size_t)(r0 + r) * 2 + 1) * a.os + lo, R[1] * ux + R[3] * uy);
   }
+}
+
+template <int NIMG, int NR>
+__global__ void __launch_bounds__(kP2PThreads) k_p2p_ms(const __grid_constant__ P2PArgs a) {
+  const int j0 = blockIdx.y * a.chunk;
+  p2p_ms_body<NIMG, NR>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
 }
 
 // FP64 reference-precision kernel.
@@ -1170,13 +1178,28 @@ static int grid_t() {
   PFMM_P2P_CASES_KI(FN, PFMM_MODHELM, 1, __VA_ARGS__)            \
   PFMM_P2P_CASES_KI(FN, PFMM_STOKES, 2, __VA_ARGS__)
 
+// modified Stokes: velocity only, nimg in {9, 15}, nr in {1, 2, 4}
+#define PFMM_P2P_MS_DISPATCH(FN, ...)                                           \
+  do {                                                                          \
+    switch ((nimg == 9 ? 0 : 3) + (nr == 4 ? 2 : (nr == 2 ? 1 : 0))) {          \
+      case 0: return FN<PFMM_MSTOKES, 9, 1, false>(__VA_ARGS__);                \
+      case 1: return FN<PFMM_MSTOKES, 9, 2, false>(__VA_ARGS__);                \
+      case 2: return FN<PFMM_MSTOKES, 9, 4, false>(__VA_ARGS__);                \
+      case 3: return FN<PFMM_MSTOKES, 15, 1, false>(__VA_ARGS__);               \
+      case 4: return FN<PFMM_MSTOKES, 15, 2, false>(__VA_ARGS__);               \
+      default: return FN<PFMM_MSTOKES, 15, 4, false>(__VA_ARGS__);              \
+    }                                                                           \
+  } while (0)
+
 cudaError_t launch_p2p_batch(int kernel, int nimg, int nr, bool grad, const P2PArgs* cells, const P2PItem* items,
                              int nitems, int* counter, int grid, cudaStream_t st) {
+  if (kernel == PFMM_MSTOKES) PFMM_P2P_MS_DISPATCH(launch_batch_t, cells, items, nitems, counter, grid, st);
   if (kernel == PFMM_STOKES) grad = false;
   PFMM_P2P_BATCH_DISPATCH(launch_batch_t, cells, items, nitems, counter, grid, st);
 }
 
 int p2p_batch_grid(int kernel, int nimg, int nr, bool grad) {
+  if (kernel == PFMM_MSTOKES) PFMM_P2P_MS_DISPATCH(grid_t);
   if (kernel == PFMM_STOKES) grad = false;
   PFMM_P2P_BATCH_DISPATCH(grid_t);
 }
