@@ -17,6 +17,11 @@
 // and the y-derivative through v^y_n(m) = -chi_m w^S_m e^{-chi ybar} + chi_m w^N_m e^{chi ybar}.
 // Stokes: u_k(t) = sum_n gamma(y, n) (Ga_{k,n}(x) + y Gb_{k,n}(x)), with the
 // lines of the weights Wa and Wb of Theorem south_thm_s.
+// Modified Stokes (Theorem south_thm_ms): the two force channels are spread
+// once; both plane-wave families (decay chi_m and |alpha_m|) are formed from
+// the same line spectra F_n(m) with their own line factors e^{+-decay ybar_n},
+// weighted by their 2 x 2 blocks, and summed into one evaluation line per GL
+// line (u_x + i u_y).
 //
 // Type-1/type-2 transforms: exponential-of-semicircle kernel
 // phi(z) = exp(b (sqrt(1 - z^2) - 1)) of width w grid points, b = 2.30 w,
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
   const int ngrid = a.n_gl * a.nf;
   const int j0 = blockIdx.x * chunk, j1 = min(a.ns, j0 + chunk);
   const T beta = (T)a.es_beta;
-  const int ncomp = a.nch == 4 ? 2 : 1;
+  const int ncomp = a.nch >= 2 ? 2 : 1;  // Stokes (4 channels) and modified Stokes (2) spread forces
   for (int v = 0; v < a.nrhs * a.nch; ++v) {
     const int r = v / a.nch, c = v % a.nch;
     const T* qrow = qv + ((size_t)r * ncomp + (c & 1)) * a.ns;
@@ -242,6 +247,39 @@ __global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, doubl
     const double2 v = Fk[(((size_t)r * a.nch + c) * a.n_gl + n) * (a.M + 1) + m];
     return dcx{v.x, v.y};
   };
+  if (KER == PFMM_MSTOKES) {
+    dcx v[32][2];
+    for (int n = 0; n < a.n_gl; ++n) v[n][0] = v[n][1] = dcx{0, 0};
+    const double fac = (m == 0) ? 1.0 : 2.0;  // the +-m pair
+    for (int fam = 0; fam < 2; ++fam) {
+      if (fam == 1 && m == 0) break;  // the Laplace family has no m = 0 term
+      const double dec = fam == 0 ? sqrt(al * al + a.beta * a.beta) : fabs(al);
+      dcx cS[2] = {{0, 0}, {0, 0}}, cN[2] = {{0, 0}, {0, 0}};
+      for (int n = 0; n < a.n_gl; ++n) {
+        const double yb = a.gl[2 * n];
+        const double ep = exp(dec * yb), em = exp(-dec * yb);
+        for (int k = 0; k < 2; ++k) {
+          const dcx f = F(k, n);
+          cS[k] = cadd(cS[k], cscale(f, ep));
+          cN[k] = cadd(cN[k], cscale(f, em));
+        }
+      }
+      dcx DS[2][2], DN[2][2], wS[2], wN[2];
+      lw::ms_sn(a.d, a.xi, a.eta, al, dec, a.beta, fam, false, DS);
+      lw::ms_sn(a.d, a.xi, a.eta, al, dec, a.beta, fam, true, DN);
+      for (int i = 0; i < 2; ++i) {
+        wS[i] = cscale(cadd(cmul(DS[i][0], cS[0]), cmul(DS[i][1], cS[1])), fac);
+        wN[i] = cscale(cadd(cmul(DN[i][0], cN[0]), cmul(DN[i][1], cN[1])), fac);
+      }
+      for (int n = 0; n < a.n_gl; ++n) {
+        const double yb = a.gl[2 * n];
+        const double es = exp(-dec * yb), en = exp(dec * yb);
+        for (int i = 0; i < 2; ++i) v[n][i] = cadd(v[n][i], cadd(cscale(wS[i], es), cscale(wN[i], en)));
+      }
+    }
+    for (int n = 0; n < a.n_gl; ++n) put(n, v[n][0], v[n][1]);
+    return;
+  }
   if (KER != PFMM_STOKES) {
     // Theorem south_thm_lap / south_thm: D^S, D^N = conj(D^S); w = fac D c (fac 2: the +-m pair)
     const dcx DS = lw::sn_scalar(a.d, a.xi, a.eta, al, chi, false);
@@ -332,6 +370,24 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
   const double* R = g.rot;
   for (int r = 0; r < a.nrhs; ++r) {
     const double2* base = spec + (size_t)r * a.npk * a.nf;
+    if (KER == PFMM_MSTOKES) {
+      dm::KSum<T> ux, uy;
+      for (int n = 0; n < a.n_gl; ++n) {
+        const double2* ra = base + (size_t)n * a.nf;
+        T sx = 0, sy = 0;
+        for (int k = 0; k < a.w; ++k) {
+          const double2 va = ra[(l0 + k) & (a.nf - 1)];
+          sx += ker[k] * (T)va.x;
+          sy += ker[k] * (T)va.y;
+        }
+        ux.add(gam[n] * sx);
+        uy.add(gam[n] * sy);
+      }
+      const double uxd = ux.value(), uyd = uy.value();
+      pot[((size_t)r * 2) * a.os + l] += R[0] * uxd + R[2] * uyd;
+      pot[((size_t)r * 2 + 1) * a.os + l] += R[1] * uxd + R[3] * uyd;
+      continue;
+    }
     if (KER == PFMM_STOKES) {
       dm::KSum<T> ux, uy;
       for (int n = 0; n < a.n_gl; ++n) {
@@ -478,6 +534,11 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
       k_nufft_interp<T, PFMM_MODHELM><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, grad);
       break;
+    case PFMM_MSTOKES:
+      k_nufft_modes<PFMM_MSTOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_interp<T, PFMM_MSTOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, nullptr);
+      break;
     default:
       k_nufft_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
@@ -496,6 +557,9 @@ cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   q.far.nsn = 0;
   q.far.M = 0;
   q.far.nterm = 2 * q.far.Nq;
+  q.far2.nsn = 0;  // modified Stokes: the Laplace family's west/east terms
+  q.far2.M = 0;
+  q.far2.nterm = 2 * q.far2.Nq;
   cudaError_t e = launch_far_direct(&q, ws, ns, nt, self, pot, grad, st);
   if (e != cudaSuccess) return e;
   if (p->far.M > 0) {

@@ -46,11 +46,14 @@ struct Far {
 };
 
 // NUFFT path: charge channels per rhs (scalar q; Stokes f_x, f_y, y' f_x,
-// y' f_y) and complex evaluation-spectrum lines per rhs (scalar: potential +
-// y-derivative per GL line, x-derivatives two lines per spectrum; Stokes:
-// the a and b weight lines per GL line).
-inline int nufft_nch(int kernel) { return kernel == PFMM_STOKES ? 4 : 1; }
-inline int nufft_npk(int kernel, int n_gl) { return kernel == PFMM_STOKES ? 2 * n_gl : n_gl + (n_gl + 1) / 2; }
+// y' f_y; modified Stokes f_x, f_y) and complex evaluation-spectrum lines per
+// rhs (scalar: potential + y-derivative per GL line, x-derivatives two lines
+// per spectrum; Stokes: the a and b weight lines per GL line; modified
+// Stokes: one line u_x + i u_y per GL line).
+inline int nufft_nch(int kernel) { return kernel == PFMM_STOKES ? 4 : (kernel == PFMM_MSTOKES ? 2 : 1); }
+inline int nufft_npk(int kernel, int n_gl) {
+  return kernel == PFMM_STOKES ? 2 * n_gl : (kernel == PFMM_MSTOKES ? n_gl : n_gl + (n_gl + 1) / 2);
+}
 
 // Workspace layout (byte offsets from the workspace base, all 256-aligned).
 struct Layout {

@@ -292,7 +292,6 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   if (o->kernel == PFMM_MSTOKES) {
     if (o->flags & PFMM_SINGLY_PERIODIC)
       return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel is doubly periodic only");
-    if (o->path == PFMM_PATH_NUFFT) return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel uses the direct path");
   }
   if (o->flags & ~127u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~127u);
   if ((o->flags & PFMM_FAR_ONLY) && (o->flags & PFMM_NEAR_ONLY))
@@ -407,7 +406,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int path = o->path;
   // the single-block shared-memory FFT handles fine grids up to 8192 points
   if (path == PFMM_PATH_AUTO)
-    path = (M >= 64 && nf <= 8192 && !ms) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+    path = (M >= 64 && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
     pfmm_plan_destroy(p);
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);

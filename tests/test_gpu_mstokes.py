@@ -146,3 +146,33 @@ def test_batch(precision, self_t):
         ref = oracle("mstokes", e1, e2, s_, f_, None if self_t else t_, beta=beta, how="plain", grad=False)
         assert _err(vel[:, :, o:o + n], ref[0]) < tol
         o += n
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("beta", [0.5, 3.0])
+@pytest.mark.parametrize("e1,e2", [((40.0, 0.0), (0.0, 1.0)), ((48.0, 0.0), (0.5, 1.0))])
+def test_nufft_path(precision, beta, e1, e2):
+    """Long cells on the NUFFT south/north path (both plane-wave families from
+    one spread), west/east on the direct kernels."""
+    rng = np.random.default_rng(76)
+    src = workloads.points(rng, e1, e2, 900)
+    f = rng.standard_normal((2, 2, 900))
+    trg = workloads.points(rng, e1, e2, 400)
+    got = run_lib("mstokes", e1, e2, src, f, trg, beta=beta, tol=TOL[precision], precision=precision, grad=False,
+                  path="nufft")
+    assert got[2].describe()["path"] == 2
+    ref = oracle("mstokes", e1, e2, src, f, trg, beta=beta, how="plain", grad=False)
+    assert _err(got[0], ref[0]) < TOL[precision]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nufft_matches_direct(precision):
+    e1, e2 = (24.0, 0.0), (0.2, 1.0)
+    rng = np.random.default_rng(77)
+    src = workloads.points(rng, e1, e2, 3000, "gmm")
+    f = rng.standard_normal((1, 2, 3000))
+    a = run_lib("mstokes", e1, e2, src, f, None, beta=1.0, tol=TOL[precision], precision=precision, grad=False,
+                path="nufft")
+    b = run_lib("mstokes", e1, e2, src, f, None, beta=1.0, tol=TOL[precision], precision=precision, grad=False,
+                path="direct")
+    assert _err(a[0], b[0]) < TOL[precision]

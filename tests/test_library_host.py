@@ -115,17 +115,17 @@ def test_west_east_flag_errors(L, kw):
 
 def test_mstokes_plan(L):
     """Modified Stokes: two plane-wave families (beta: m = 0..M, Laplace:
-    m = 1..M, each with its west/east nodes), direct path even where AUTO
-    would take the NUFFT for the other kernels; the NUFFT path, the singly
-    periodic operator and beta <= 0 are refused."""
+    m = 1..M, each with its west/east nodes); AUTO takes the NUFFT like the
+    other kernels; the singly periodic operator and beta <= 0 are refused."""
     from paper_2111_01083_gb300 import _lib
     d = _op(kernel="mstokes", beta=2.0, e1=(40.0, 0.0)).describe()
     lap = _op(kernel="laplace", e1=(40.0, 0.0)).describe()
-    assert d["path"] == 1 and lap["path"] == 2
+    assert d["path"] == 2 and lap["path"] == 2
+    assert _op(kernel="mstokes", beta=2.0).describe()["path"] == 1
     assert d["M"] == lap["M"] and d["mode0"] == 1
     mh = _op(kernel="modhelm", beta=2.0, e1=(40.0, 0.0), path="direct").describe()
     assert d["Nq"] > mh["Nq"]  # both families' nodes
-    for kw in (dict(path="nufft"), dict(singly=True), dict(beta=0.0)):
+    for kw in (dict(singly=True), dict(beta=0.0)):
         args = dict(kernel="mstokes", beta=2.0)
         args.update(kw)
         with pytest.raises(_lib.PfmmError):
