@@ -26,19 +26,10 @@
 
 namespace pfmm {
 
-#ifndef PFMM_P2P_SUB
-#define PFMM_P2P_SUB 16
-#endif
-#ifndef PFMM_P2P_MINB
-#define PFMM_P2P_MINB 1
-#endif
-#ifndef PFMM_P2P_UNROLL
-#define PFMM_P2P_UNROLL 4
-#endif
 constexpr int kP2PThreads = 128;
 constexpr int kP2PTile = 128;
-constexpr int kP2PSub = PFMM_P2P_SUB;  // sources per FP32 partial sum (then Kahan)
-constexpr int kP2PUnroll = PFMM_P2P_UNROLL;
+constexpr int kP2PSub = 16;    // sources per FP32 partial sum (then Kahan)
+constexpr int kP2PUnroll = 4;
 
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
@@ -329,7 +320,7 @@ __device__ __forceinline__ void p2p_mixed_body(const P2PArgs& a, int bx, int j0,
 }
 
 template <int KER, int NIMG, int NR, bool GRAD>
-__global__ void __launch_bounds__(kP2PThreads, PFMM_P2P_MINB) k_p2p_mixed(const __grid_constant__ P2PArgs a) {
+__global__ void __launch_bounds__(kP2PThreads, 1) k_p2p_mixed(const __grid_constant__ P2PArgs a) {
   const int j0 = blockIdx.y * a.chunk;
   p2p_mixed_body<KER, NIMG, NR, GRAD>(a, blockIdx.x, j0, min(a.ns, j0 + a.chunk), a.r0 + blockIdx.z * NR);
 }
