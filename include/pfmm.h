@@ -63,7 +63,8 @@ extern "C" {
  * (beta > 0; no net-force condition).  Forces and velocities are laid out as
  * for STOKES.  Far field by Theorems south_thm_ms / west_thm_ms (direct path
  * only), periodic sum in the paper's order (image rows).  Single cells and
- * batches; not for the adjoint, not singly periodic. */
+ * batches; the adjoint for the strengths (the operator is symmetric); not
+ * singly periodic. */
 typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2, PFMM_MSTOKES = 3 } pfmm_kernel;
 
 /* FP64: every step in double precision.
@@ -262,7 +263,8 @@ pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const double* src, 
  *                     the sum of both roles in that one array.
  * Laplace/Stokes potentials are defined up to a constant, so only the
  * mean-free part of g matters; g is projected to zero mean per rhs (and
- * component) before use.  Stokes: dq only (g is [nrhs][2][nt], dq [nrhs][2][ns]).
+ * component) before use.  Stokes and modified Stokes: dq only (g is [nrhs][2][nt],
+ * dq [nrhs][2][ns]; modified Stokes uses g as given: its velocity has no free constant).
  * The plan must admit the swapped sizes: nt <= ns_max and ns <= nt_max
  * (automatic when targets = sources).  src, q, trg as in the forward call.
  * Nothing is stored between the forward and the adjoint: the plane-wave

@@ -683,9 +683,12 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* p, void* workspace, size_t ws_bytes,
                 (long long)nt);
   if (!workspace || ws_bytes < p->lay.total || (reinterpret_cast<uintptr_t>(workspace) & 255))
     return fail(PFMM_ERR_WORKSPACE, "workspace NULL, misaligned or smaller than %zu bytes", p->lay.total);
-  const bool stokes = p->opts.kernel == PFMM_STOKES;
+  // Stokes kernels: strengths only.  Modified Stokes: G^MS(r) is a symmetric
+  // matrix and even in r, and the image-row sum is symmetric under l -> -l, so
+  // the operator is its own transpose; no gauge, so g is used as given (the
+  // neutral projection below applies to Laplace and Stokes only).
+  const bool stokes = p->opts.kernel == PFMM_STOKES || p->opts.kernel == PFMM_MSTOKES;
   if (stokes && (dsrc || dtrg)) return fail(PFMM_ERR_INVALID_ARG, "Stokes adjoint: strengths only (dq)");
-  if (p->opts.kernel == PFMM_MSTOKES) return fail(PFMM_ERR_INVALID_ARG, "no adjoint for the modified Stokes kernel");
   if (dtrg && !grad_fwd) return fail(PFMM_ERR_INVALID_ARG, "dtrg needs the forward gradient grad_fwd");
   if (p->opts.flags & (PFMM_FAR_ONLY | PFMM_NEAR_ONLY))
     return fail(PFMM_ERR_INVALID_ARG, "the adjoint is defined for the full operator");

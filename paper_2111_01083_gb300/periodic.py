@@ -408,9 +408,9 @@ def _make_function():
             need_s, need_q, need_t = ctx.needs_input_grad[1], ctx.needs_input_grad[2], ctx.needs_input_grad[3]
             if ctx.self_t:
                 need_t = need_s
-            dq, dsrc, dtrg = _adjoint(op, src, q, None if ctx.self_t else trg, g_pot, grad if op.kernel != "stokes"
-                                      else None, need_q, need_s and op.kernel != "stokes",
-                                      need_t and op.kernel != "stokes")
+            vec = op.kernel in _VEC  # Stokes kernels: strengths only
+            dq, dsrc, dtrg = _adjoint(op, src, q, None if ctx.self_t else trg, g_pot, None if vec else grad,
+                                      need_q, need_s and not vec, need_t and not vec)
             return None, dsrc, dq, dtrg
 
     return PeriodicFunction

@@ -176,3 +176,30 @@ def test_nufft_matches_direct(precision):
     b = run_lib("mstokes", e1, e2, src, f, None, beta=1.0, tol=TOL[precision], precision=precision, grad=False,
                 path="direct")
     assert _err(a[0], b[0]) < TOL[precision]
+
+
+@pytest.mark.parametrize("self_t", [False, True])
+def test_adjoint_strengths(self_t):
+    """dL/df for L = sum w . u through periodic() (pfmm_execute_adjoint): the
+    operator is symmetric, so dL/df_j = (P w)(s_j), the velocity at the
+    sources of forces w at the targets, checked against the oracle."""
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp, periodic
+    e1, e2 = LAT["hex"]
+    rng = np.random.default_rng(78)
+    ns, nt = 400, 250
+    src = workloads.points(rng, e1, e2, ns)
+    trg = src if self_t else workloads.points(rng, e1, e2, nt)
+    nt = trg.shape[1]
+    f = rng.standard_normal((1, 2, ns))
+    w = rng.standard_normal((1, 2, nt))
+    dev = torch.device("cuda", 0)
+    S = torch.tensor(src, device=dev)
+    T = None if self_t else torch.tensor(trg, device=dev)
+    F = torch.tensor(f, device=dev, requires_grad=True)
+    n = max(ns, nt)
+    op = PeriodicOp("mstokes", e1, e2, beta=1.3, tol=1e-10, precision="fp64", ns_max=n, nt_max=n)
+    vel = periodic(op, S, F, T)
+    (torch.tensor(w, device=dev) * vel).sum().backward()
+    ref, _ = oracle("mstokes", e1, e2, trg, w, None if self_t else src, beta=1.3, how="plain", grad=False)
+    assert _err(F.grad.detach().cpu().numpy(), ref) < 1e-10
