@@ -1,6 +1,7 @@
 """GB300-native periodizing operator for 2D doubly periodic Laplace, modified
-Helmholtz and Stokes kernels (Pei, Askham, Greengard & Jiang, "Periodic Fast
-Multipole Method", arXiv 2111.01083).
+Helmholtz, Stokes and modified Stokes kernels, with the singly periodic
+variant and the Stokes pressure (Pei, Askham, Greengard & Jiang, "Periodic
+Fast Multipole Method", arXiv 2111.01083).
 
 The computation lives in the CUDA library ``libpfmm.so`` (C ABI in
 ``include/pfmm.h``); this package only marshals arguments.  Importing the

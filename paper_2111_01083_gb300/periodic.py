@@ -4,10 +4,15 @@ device memory and the current CUDA stream).
     op = PeriodicOp("laplace", e1=(16, 0), e2=(0, 1), tol=1e-6, precision="mixed",
                     ns_max=N, nt_max=N)
     pot, grad = op(src, q)            # targets = sources
-    vel, _ = stokes_op(src, f, trg)   # Stokes: velocity
+    vel, _ = stokes_op(src, f, trg)   # Stokes / modified Stokes: velocity
 
-Tensors: src/trg [2, n] float64 (CUDA), q [nrhs, n] or [nrhs, 2, n] (Stokes).
-Outputs: pot [nrhs, nt] (Stokes: [nrhs, 2, nt]), grad [nrhs, 2, nt] or None.
+Kernels: "laplace", "modhelm" (beta > 0), "stokes", "mstokes" (the modified
+Stokeslet, beta > 0).  Options beyond the kernel: singly=True (periodic
+along e1 only), we="auto" | "rotated" | "axis" (the west/east plane-wave
+direction), part="total" | "far" | "near".
+Tensors: src/trg [2, n] float64 (CUDA), q [nrhs, n] or [nrhs, 2, n] (Stokes
+kernels).  Outputs: pot [nrhs, nt] (Stokes kernels: velocity [nrhs, 2, nt]),
+grad [nrhs, 2, nt] or None.
 Every step of the computation runs in the CUDA library; nothing here
 computes.
 """
