@@ -204,3 +204,33 @@ def test_singly_periodic_plan(L):
     assert tall["Nq"] > wide["Nq"]
     with pytest.raises(PfmmError):
         PeriodicOp("laplace", (1.0, 0.0), (0.0, 2.0), singly=True, path="nufft", ns_max=8, nt_max=8)
+
+
+@pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 1.0), ("stokes", 0.0), ("mstokes", 1.0)])
+def test_plans_for_the_paper_cells(L, kernel, beta):
+    """Every cell of the paper's Tables 1-3 (rectangles and theta = pi/3, pi/6
+    parallelograms, A = d/eta up to 1000, eta = 1) plans without error at the
+    tables' precisions: near block 3 x 3 (m0 = 1) after reduction and the
+    west/east direction rule, M from Eq. mpk0s on the reduced cell, a NUFFT
+    fine grid that fits the single-block FFT whenever AUTO picks the NUFFT
+    (longer cells at high precision take the direct path), and a workspace
+    linear in the point count."""
+    from oracle import lattice
+    for shape in ("rectangle", math.pi / 3, math.pi / 6):
+        for A in (1, 2, 10, 100, 1000):
+            e1 = (float(A), 0.0)
+            e2 = (0.0, 1.0) if shape == "rectangle" else (1.0 / math.tan(shape), 1.0)
+            for tol in (1e-12, 1e-9, 1e-6):
+                d = _op(kernel=kernel, beta=beta, e1=e1, e2=e2, tol=tol, ns_max=1000, nt_max=1000).describe()
+                c = lattice.canonicalize(e1, e2)
+                assert d["m0"] == 1
+                if kernel in ("laplace", "stokes", "mstokes"):
+                    assert d["M"] == _mpk0s(c["d"], c["eta"], tol / 10)
+                # modified Helmholtz: no west/east nodes once the far columns are
+                # beyond the K0 decay (beta d large)
+                assert d["Nq"] < 4000 and (d["Nq"] > 0 or kernel == "modhelm")
+                if d["path"] == 2:
+                    assert d["nf"] <= 8192 and d["nf"] >= 2 * (2 * d["M"] + 1)
+    small = _op(kernel=kernel, beta=beta, e1=(100.0, 0.0), tol=1e-9, ns_max=1000, nt_max=1000)
+    big = _op(kernel=kernel, beta=beta, e1=(100.0, 0.0), tol=1e-9, ns_max=100000, nt_max=100000)
+    assert big.ws_bytes < 150 * small.ws_bytes
