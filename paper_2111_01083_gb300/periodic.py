@@ -35,6 +35,52 @@ def _ptr(t):
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+def _check_tensor(name, t, shape, device):
+    """Raise ValueError unless t is a contiguous float64 tensor of `shape` on
+    `device`: the library reads raw pointers with these sizes, so a wrong
+    dtype or shape must not reach it."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch.Tensor, got {type(t).__name__}")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected torch.float64")
+    if t.device != device:
+        raise ValueError(f"{name}: on {t.device}, expected {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: not contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def check_inputs(kernel, nrhs, src, q, trg, out=None, grad=True):
+    """Validate the tensors of one PeriodicOp call (see _check_tensor); returns
+    (ns, nt).  src [2, ns], q [nrhs, ns] or [nrhs, 2, ns] (Stokes kernels),
+    trg [2, nt] or None, out (pot, grad) of the output shapes or None."""
+    import torch
+    if not isinstance(src, torch.Tensor) or src.dim() != 2:
+        raise ValueError("src: expected a [2, ns] tensor")
+    dev = src.device
+    ns = src.shape[1]
+    vec = kernel in _VEC
+    _check_tensor("src", src, (2, ns), dev)
+    _check_tensor("q", q, (nrhs, 2, ns) if vec else (nrhs, ns), dev)
+    if trg is None:
+        nt = ns
+    else:
+        if not isinstance(trg, torch.Tensor) or trg.dim() != 2:
+            raise ValueError("trg: expected a [2, nt] tensor")
+        nt = trg.shape[1]
+        _check_tensor("trg", trg, (2, nt), dev)
+    if out is not None:
+        pot, g = out
+        _check_tensor("out pot", pot, (nrhs, 2, nt) if vec else (nrhs, nt), dev)
+        if g is not None:
+            if vec:
+                raise ValueError("out grad: must be None for the Stokes kernels")
+            _check_tensor("out grad", g, (nrhs, 2, nt), dev)
+    return ns, nt
+
+
 class PeriodicOp:
     def __init__(self, kernel, e1, e2, beta=0.0, tol=1e-6, precision="mixed", path="auto", nufft_w=0, n_gl=0,
                  nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False, we="auto"):
@@ -94,11 +140,12 @@ class PeriodicOp:
     def __call__(self, src, q, trg=None, grad=True, out=None, stream=None):
         """Device tensors in, device tensors out (float64).  trg None -> targets = sources."""
         import torch
-        assert src.dtype == torch.float64 and src.is_cuda and src.is_contiguous()
+        ns, nt = check_inputs(self.kernel, self.nrhs, src, q, trg, out, grad)
+        if not src.is_cuda:
+            raise ValueError("src: expected CUDA tensors")
         self_t = trg is None
         if self_t:
             trg = src
-        ns, nt = src.shape[1], trg.shape[1]
         stokes = self.kernel in _VEC
         if out is None:
             pot = torch.empty((self.nrhs, 2, nt) if stokes else (self.nrhs, nt), dtype=torch.float64,
@@ -215,6 +262,7 @@ class BatchOp:
         self.kernel, self.nrhs, self.ncell = kernel, int(nrhs), n
         self.NS = int(so[-1])
         self.NT = int(self.NS if trg_counts is None else np.sum(trg_counts))
+        self.self_t = trg_counts is None
         self._ws = None
 
     def __del__(self):
@@ -242,6 +290,10 @@ class BatchOp:
 
     def __call__(self, src, q, trg=None, out=None, grad=True, stream=None):
         import torch
+        ns, nt = check_inputs(self.kernel, self.nrhs, src, q, trg, out, grad)
+        if not src.is_cuda or ns != self.NS or nt != self.NT or (trg is None) != self.self_t:
+            raise ValueError(f"batch inputs: CUDA tensors with {self.NS} sources and "
+                             f"{'targets = sources' if self.self_t else f'{self.NT} targets'} expected")
         if out is None:
             out = self.alloc_out(src.device, grad)
         pot, g = out
@@ -306,10 +358,13 @@ class StokesPressure:
 
     def __call__(self, src, f, trg=None, out=None, stream=None):
         import torch
+        ns, nt = check_inputs("stokes", self.nrhs, src, f, trg)
+        if not src.is_cuda:
+            raise ValueError("src: expected CUDA tensors")
         tr = src if trg is None else trg
-        ns, nt = src.shape[1], tr.shape[1]
         if out is None:
             out = torch.empty((self.nrhs, nt), dtype=torch.float64, device=src.device)
+        _check_tensor("out", out, (self.nrhs, nt), src.device)
         ws = self.op.workspace()
         st = stream if stream is not None else torch.cuda.current_stream(src.device).cuda_stream
         _lib.check(_lib.lib().pfmm_stokes_pressure(self.op._h, _ptr(ws), ws.numel(), ns, _ptr(src),
@@ -371,6 +426,7 @@ def _adjoint(op, src, q, trg, g, grad_fwd, need_q, need_s, need_t):
     tr = src if self_t else trg
     ns, nt = src.shape[1], tr.shape[1]
     g = g.contiguous()
+    _check_tensor("grad of the output", g, (op.nrhs, 2, nt) if op.kernel in _VEC else (op.nrhs, nt), src.device)
     dq = torch.empty_like(q) if need_q else None
     dsrc = torch.empty_like(src) if need_s else None
     if self_t and need_s and need_t:

@@ -234,3 +234,30 @@ def test_plans_for_the_paper_cells(L, kernel, beta):
     small = _op(kernel=kernel, beta=beta, e1=(100.0, 0.0), tol=1e-9, ns_max=1000, nt_max=1000)
     big = _op(kernel=kernel, beta=beta, e1=(100.0, 0.0), tol=1e-9, ns_max=100000, nt_max=100000)
     assert big.ws_bytes < 150 * small.ws_bytes
+
+
+def test_binding_validates_tensors():
+    """The binding refuses tensors the library would misread (wrong dtype,
+    shape, device or layout) before any call; checked on CPU tensors."""
+    import torch
+    from paper_2111_01083_gb300.periodic import check_inputs
+    src = torch.zeros(2, 10, dtype=torch.float64)
+    q = torch.zeros(3, 10, dtype=torch.float64)
+    assert check_inputs("laplace", 3, src, q, None) == (10, 10)
+    assert check_inputs("laplace", 3, src, q, torch.zeros(2, 4, dtype=torch.float64)) == (10, 4)
+    f = torch.zeros(3, 2, 10, dtype=torch.float64)
+    assert check_inputs("mstokes", 3, src, f, None) == (10, 10)
+    bad = [
+        ("laplace", q.float(), None, None),                                # dtype
+        ("laplace", torch.zeros(3, 9, dtype=torch.float64), None, None),  # ns mismatch
+        ("laplace", torch.zeros(2, 10, dtype=torch.float64), None, None), # nrhs mismatch
+        ("stokes", q, None, None),                                        # forces need [nrhs, 2, ns]
+        ("laplace", torch.zeros(10, 3, dtype=torch.float64).t(), None, None),  # not contiguous
+        ("laplace", q, torch.zeros(3, 4, dtype=torch.float64), None),     # trg not [2, nt]
+        ("laplace", q, None, (torch.zeros(3, 9, dtype=torch.float64), None)),  # out pot shape
+        ("stokes", f, None, (torch.zeros(3, 2, 10, dtype=torch.float64),
+                             torch.zeros(3, 2, 10, dtype=torch.float64))),    # grad out for Stokes
+    ]
+    for kernel, qq, trg, out in bad:
+        with pytest.raises(ValueError):
+            check_inputs(kernel, 3, src, qq, trg, out)
