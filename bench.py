@@ -146,11 +146,15 @@ for nsamp in %(samples)r:
     t0 = time.perf_counter()
     if singly:
         p1.near_sum(kernel, beta, cell, tt, s, q, want_grad=not vec)
-        p1.far_field(kernel, beta, cell, tt, s, q, eps=%(eps)r, want_grad=not vec)
     else:
         ewald.near_sum(kernel, beta, cell, tt, s, q, want_grad=not vec)
+    t1 = time.perf_counter()
+    if singly:
+        p1.far_field(kernel, beta, cell, tt, s, q, eps=%(eps)r, want_grad=not vec)
+    else:
         method.far_field(kernel, beta, cell, tt, s, q, eps=%(eps)r, want_grad=not vec)
-    res.append((nsamp, time.perf_counter() - t0))
+    # (targets, near-sum seconds, far-field seconds)
+    res.append((nsamp, t1 - t0, time.perf_counter() - t1))
 print(json.dumps({"samples": res, "ns": int(s.shape[1]), "nt": int(t.shape[1])}))
 """
 
@@ -164,12 +168,17 @@ def oracle_time(name, samples=(16, 48), eps=1e-6):
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    (n1, t1), (n2, t2) = d["samples"]
-    per_target = (t2 - t1) / (n2 - n1)
-    fixed = max(0.0, t1 - per_target * n1)
+    (n1, a1, f1), (n2, a2, f2) = d["samples"]
+    # the near sum has no source-side fixed cost: per-target time from the
+    # larger sample; the far field has one (coefficient formation over all
+    # sources): fixed + slope n, the slope clamped at >= 0 against timing noise
+    per_near = a2 / n2
+    slope = max(0.0, (f2 - f1) / (n2 - n1))
+    fixed = max(0.0, f1 - slope * n1)
+    per_target = per_near + slope
     t_full = fixed + per_target * d["nt"]
     return dict(t_full=t_full, per_target=per_target, fixed=fixed, ns=d["ns"], nt=d["nt"],
-                wall=t1 + t2, samples=d["samples"])
+                wall=a1 + f1 + a2 + f2, samples=[(n, a + f) for n, a, f in d["samples"]])
 
 
 def cpu_baseline_obj(name, ot, unit):
