@@ -61,9 +61,9 @@ extern "C" {
  * G = (grad grad^T - Lap I) G_MB, G_MB = -(1/(2 pi beta^2))(K0(beta r) - log(1/r)),
  * the fundamental solution of (beta^2 - Lap) u + grad p = 0, div u = 0
  * (beta > 0; no net-force condition).  Forces and velocities are laid out as
- * for STOKES.  Far field by Theorems south_thm_ms / west_thm_ms (direct path
- * only), periodic sum in the paper's order (image rows).  Single cells and
- * batches; the adjoint for the strengths (the operator is symmetric); not
+ * for STOKES.  Far field by Theorems south_thm_ms / west_thm_ms (direct and
+ * NUFFT paths), periodic sum in the paper's order (image rows).  Single cells
+ * and batches; the adjoint for the strengths (the operator is symmetric); not
  * singly periodic. */
 typedef enum { PFMM_LAPLACE = 0, PFMM_MODHELM = 1, PFMM_STOKES = 2, PFMM_MSTOKES = 3 } pfmm_kernel;
 
@@ -77,9 +77,8 @@ typedef enum { PFMM_FP64 = 0, PFMM_MIXED = 1 } pfmm_precision;
 
 /* Far-field south/north application: DIRECT = L (D (R q)) (Sec. 6);
  * NUFFT = GL anterpolation + ES-kernel NUFFT (Sec. 6, Eqs. fastanterp and
- * fastinterp), for the Laplace, modified Helmholtz and Stokes kernels.  AUTO
- * picks NUFFT when M >= 64 and the fine grid (power of two >= 2 (2M + 1)) has
- * at most 8192 points; MSTOKES always takes DIRECT (NUFFT: INVALID_ARG). */
+ * fastinterp), for all four kernels.  AUTO picks NUFFT when M >= 64 and the
+ * fine grid (power of two >= 2 (2M + 1)) has at most 8192 points. */
 typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } pfmm_path;
 
 /* flags */
