@@ -33,6 +33,7 @@
 //            b = IFFT(v(k) / phihat(alpha k)).
 // Two real lines share one complex FFT (real + i imag).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include "pfmm_impl.h"
 #include "devmath.cuh"
@@ -440,15 +441,20 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
 
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
 // that executes after the first (including ones captured in a CUDA graph)
-// make no attribute calls.
+// make no attribute calls.  The cache is atomic: plans may execute from
+// several host threads (a lost update only repeats the idempotent call).
 static cudaError_t raise_smem(const void* fn, int slot, size_t bytes) {
-  static int done[32][4] = {};
+  static std::atomic<int> done[32][4] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
   const bool cached = dev >= 0 && dev < 32;
-  if (cached && done[dev][slot] >= (int)bytes) return cudaSuccess;
+  if (cached && done[dev][slot].load(std::memory_order_relaxed) >= (int)bytes) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess && cached) done[dev][slot] = (int)bytes;
+  if (e == cudaSuccess && cached) {
+    int cur = done[dev][slot].load(std::memory_order_relaxed);
+    while (cur < (int)bytes && !done[dev][slot].compare_exchange_weak(cur, (int)bytes, std::memory_order_relaxed)) {
+    }
+  }
   return e;
 }
 
