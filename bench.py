@@ -34,8 +34,29 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "laplace_aspect16_gmm_n1e5"
 METRIC = "targets+sources/s of periodic Laplace/Stokes op, mixed vs FP64 at rel err 1e-6"
-SMS = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_FALLBACK = 2070.0  # GB300 maximum SM clock, used only if neither nvidia-smi nor MEASURED_PEAKS.json has it
+
+
+def device_sms(dev):
+    """Streaming multiprocessors of the benchmarked device (read from the device)."""
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def peak_clock_mhz(clocks):
+    """SM clock for per-clock peaks: the median SM clock sampled under load
+    during the timed region (so a box held below its maximum clock is not
+    charged for it), else the maximum SM clock nvidia-smi reports, else the
+    measured maximum, else the GB300 maximum."""
+    if clocks and clocks.get("sm_mhz"):
+        return float(clocks["sm_mhz"]), "median SM clock sampled during the timed region"
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"]), "maximum SM clock (nvidia-smi)"
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["sm_max_mhz"]), "maximum SM clock (MEASURED_PEAKS.json)"
+    except Exception:
+        return SM_MAX_MHZ_FALLBACK, "GB300 maximum SM clock (fallback)"
 
 # Per-pair work of the near-image P2P, one pair = (target, source, near
 # image): (FP32 operations, MUFU operations in units of the 16/clk/SM rate;
@@ -72,8 +93,8 @@ def p2p_work(kernel, nrhs, grad, nimg=9):
 
 
 def alu_rates():
-    """Results per clock per SM measured on this GPU model by
-    paper_2111_01083_gb300/alu_peaks.py (committed as profiles/alu_peaks.json):
+    """Results per clock per SM measured on this GPU model by an issue-rate
+    probe (recorded in profiles/alu_peaks.json, method in profiles/alu_peaks.md):
     FP32 = scalar FFMA rate, MUFU = the lg2/rcp/rsqrt rate."""
     try:
         d = json.load(open(os.path.join(ROOT, "profiles", "alu_peaks.json")))
@@ -83,19 +104,20 @@ def alu_rates():
         return {"fp32": 128.0, "mufu": 16.0, "source": "fallback: nominal 128 FP32 / 16 MUFU per clock per SM"}
 
 
-def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, traffic=None, nimg=9):
+def p2p_roofline(kernel, nrhs, grad, pairs, launch_ms, step_ms, name, sms, clocks, traffic=None, nimg=9):
     """Bound = min(FP32 rate / FP32 ops per pair, MUFU rate / MUFU ops per pair)
-    x 152 SMs x the maximum SM clock; achieved = pairs per launch / launch time."""
+    x SMs x SM clock (peak_clock_mhz); achieved = pairs per launch / launch time."""
     fp32_ops, mufu_ops = p2p_work(kernel, nrhs, grad, nimg)
     r = alu_rates()
+    mhz, mhz_src = peak_clock_mhz(clocks)
     f_fp32 = r["fp32"] / fp32_ops
     f_mufu = r["mufu"] / mufu_ops
-    peak = SMS * min(f_fp32, f_mufu) * SM_MAX_MHZ * 1e6 / 1e9
+    peak = sms * min(f_fp32, f_mufu) * mhz * 1e6 / 1e9
     achieved = pairs / (launch_ms * 1e-3) / 1e9
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpair/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_basis": (f"min(FP32 {r['fp32']:.1f}/clk/SM / {fp32_ops:.2f} ops, MUFU {r['mufu']:.1f}/clk/SM / "
-                           f"{mufu_ops:.2f} ops) per pair x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz; "
+                           f"{mufu_ops:.2f} ops) per pair x {sms} SMs x {mhz:.0f} MHz ({mhz_src}); "
                            f"{'FP32' if f_fp32 < f_mufu else 'MUFU'}-bound; rates from {r['source']}"),
             "pairs_per_launch": pairs, "launch_ms": launch_ms, "share_of_step": launch_ms / step_ms}
 
@@ -114,6 +136,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--we", default=None, choices=["auto", "axis", "rotated"],
                     help="override the west/east plane-wave direction")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: skip the batched modified-Helmholtz sub-records")
     return ap.parse_args()
 
 
@@ -140,8 +164,9 @@ q = w["q"]
 if vec:
     q = np.einsum("ij,rjn->rin", cell["rot"], q)
 res = []
+rng = np.random.default_rng(%(seed)d)
 for nsamp in %(samples)r:
-    idx = np.random.default_rng(123).choice(t.shape[1], nsamp, replace=False)
+    idx = rng.choice(t.shape[1], nsamp, replace=False)
     tt = t[:, idx]
     t0 = time.perf_counter()
     if singly:
@@ -159,36 +184,89 @@ print(json.dumps({"samples": res, "ns": int(s.shape[1]), "nt": int(t.shape[1])})
 """
 
 
-def oracle_time(name, samples=(16, 48), eps=1e-6):
+def _oracle_env():
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET % dict(root=ROOT, name=name, samples=list(samples), eps=eps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return env
+
+
+def _fit_oracle(d):
+    """Time per full workload from two target samples: the near sum has no
+    source-side fixed cost (per-target time from the larger sample); the far
+    field has one (coefficient formation over all sources): fixed + slope n,
+    the slope clamped at >= 0 against timing noise."""
     (n1, a1, f1), (n2, a2, f2) = d["samples"]
-    # the near sum has no source-side fixed cost: per-target time from the
-    # larger sample; the far field has one (coefficient formation over all
-    # sources): fixed + slope n, the slope clamped at >= 0 against timing noise
     per_near = a2 / n2
     slope = max(0.0, (f2 - f1) / (n2 - n1))
     fixed = max(0.0, f1 - slope * n1)
-    per_target = per_near + slope
-    t_full = fixed + per_target * d["nt"]
-    return dict(t_full=t_full, per_target=per_target, fixed=fixed, ns=d["ns"], nt=d["nt"],
-                wall=a1 + f1 + a2 + f2, samples=[(n, a + f) for n, a, f in d["samples"]])
+    return fixed, per_near + slope
 
 
-def cpu_baseline_obj(name, ot, unit):
-    return {"value": (ot["ns"] + ot["nt"]) / ot["t_full"], "unit": unit, "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 oracle (plain method, eps 1e-6 far field + direct near sum) on all "
-                       f"{ot['ns']} sources and {ot['samples'][0][0]} / {ot['samples'][1][0]} sampled targets "
-                       f"({ot['wall']:.1f} s); time extrapolated linearly to {ot['nt']} targets")}
+def oracle_time(name, samples=(32, 256), eps=1e-6, procs=1):
+    """The FP64 oracle (plain method far field at eps + direct near sum), each
+    process single-threaded, on `samples` sampled targets and all sources.
+    procs > 1 runs that many such processes at once (distinct target samples),
+    one per host core: the oracle's work over targets is independent, so the
+    all-core time of the workload is fixed + per_target * N_T / procs with the
+    per-target and fixed costs measured under the concurrent load."""
+    env = _oracle_env()
+    runs = []
+    for k in range(procs):
+        code = ORACLE_SNIPPET % dict(root=ROOT, name=name, samples=list(samples), eps=eps, seed=123 + k)
+        runs.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                     text=True, env=env))
+    t0 = time.perf_counter()
+    outs = [r.communicate(timeout=1800) for r in runs]
+    wall = time.perf_counter() - t0
+    fits, d = [], None
+    for r, (out, err) in zip(runs, outs):
+        if r.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        d = json.loads(out.strip().splitlines()[-1])
+        fits.append(_fit_oracle(d))
+    fixed = statistics.median(f for f, _ in fits)
+    per_target = statistics.mean(p for _, p in fits)
+    t_full = fixed + per_target * d["nt"] / procs
+    return dict(t_full=t_full, per_target=per_target, fixed=fixed, ns=d["ns"], nt=d["nt"], wall=wall,
+                samples=list(samples), procs=procs)
+
+
+def cpu_baseline(name, unit="targets+sources/s"):
+    """The oracle timed single-threaded and on all host cores (see oracle_time)."""
+    ot1 = oracle_time(name)
+    n = host_cores()
+    otn = oracle_time(name, procs=n) if n > 1 else None
+    return cpu_baseline_obj(name, ot1, unit, otn)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_obj(name, ot1, unit, otn=None):
+    """ot1: the oracle single-threaded; otn: on all host cores (or None)."""
+    one = (ot1["ns"] + ot1["nt"]) / ot1["t_full"]
+    base = (f"FP64 oracle (plain method, eps 1e-6 far field + direct near sum), one thread per process, on all "
+            f"{ot1['ns']} sources and {ot1['samples'][0]} / {ot1['samples'][1]} sampled targets; time extrapolated "
+            f"linearly to {ot1['nt']} targets (single thread: {ot1['wall']:.1f} s)")
+    if otn is None:
+        return {"value": one, "unit": unit, "cores": 1, "kind": "oracle", "sample": base,
+                "single_thread_value": one}
+    alln = (otn["ns"] + otn["nt"]) / otn["t_full"]
+    return {"value": alln, "unit": unit, "cores": otn["procs"], "kind": "oracle",
+            "sample": base + (f"; all cores: {otn['procs']} such processes at once on distinct target samples "
+                              f"({otn['wall']:.1f} s), targets split over the processes"),
+            "single_thread_value": one, "all_cores_value": alln, "nproc": host_cores()}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle on the host cores, each step a
+    bounded sample of the workload (all sources, 4 / 12 sampled targets,
+    single-threaded), extrapolated to the whole workload."""
     if rank != 0:
         return 0
     vals = []
@@ -247,7 +325,7 @@ def stop_clocks(proc, f, path, gpu_index):
                 reasons.add(n)
     if not sm:
         return None
-    loaded = [x for x in sm if x > 0.5 * (mx or SM_MAX_MHZ)] or sm
+    loaded = [x for x in sm if x > 0.5 * (mx or SM_MAX_MHZ_FALLBACK)] or sm
     return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
@@ -341,11 +419,13 @@ def job_value(world, units_per_rank, seconds):
     return world * units_per_rank / seconds
 
 
-def timed_region(step, args, dist, dev, local):
+def timed_region(step, args, dist, dev, local, after=None):
     """W untimed steps, then K steps timed with CUDA events on the launching
     stream (L2 flushed by a 256 MiB write before each, outside the events),
     with a barrier + synchronize on both sides; clocks sampled meanwhile.
-    Returns (mean ms per step, max over ranks; clocks)."""
+    after(): called after each timed step, outside the events (reads phase
+    events recorded by the step).  Returns (mean ms per step, max over ranks;
+    clocks)."""
     import torch
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
@@ -367,6 +447,8 @@ def timed_region(step, args, dist, dev, local):
         e1.record()
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
+        if after:
+            after()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -374,19 +456,18 @@ def timed_region(step, args, dist, dev, local):
     return max_over_ranks(dist, sum(ts) / len(ts), dev), clocks
 
 
-def run_batch(args, rank, world, local):
-    """Batched modified Helmholtz: 256 cells (eta = 1, d log-uniform in [1, 64],
-    N log-uniform in [500, 5e4]), 8 rhs, one beta per run, the whole batch
-    captured in one CUDA graph and replayed per step."""
+def time_batch(beta, args, dist, dev, local, scale=1.0):
+    """The batched modified-Helmholtz workload at one beta: 256 cells, 8 rhs,
+    captured in one CUDA graph; each timed step is one graph.replay().  The
+    graph carries external event-record nodes around the per-cell phases and
+    the batched P2P, so the P2P time of every timed replay is read from the
+    replay itself.  Evaluated pairs and the launch count come from one eager
+    execute with pair counting after the timing (the counters add atomics)."""
     import numpy as np
     import torch
     import workloads
     from paper_2111_01083_gb300 import BatchOp
-    beta = float(args.workload.split("beta")[-1])
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = init_dist(world, dev)
-    cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8, scale=args.scale)
+    cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8, scale=scale)
     counts = [c["src"].shape[1] for c in cells]
     S_h = torch.from_numpy(np.ascontiguousarray(np.concatenate([c["src"] for c in cells], axis=1))).pin_memory()
     Q_h = torch.from_numpy(np.ascontiguousarray(np.concatenate([c["q"] for c in cells], axis=1))).pin_memory()
@@ -394,24 +475,50 @@ def run_batch(args, rank, world, local):
     Q = Q_h.to(dev)
     op = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=beta) for c in cells], counts, precision="mixed",
                  nrhs=8, tol=1e-6)
+    op.profile(True, count_pairs=False)
     graph, out = op.capture(S, Q, grad=False)
     torch.cuda.synchronize()
     op.status(dev)
-    ms, clocks = timed_region(graph.replay, args, dist, dev, local)
+    phases = []
+    ms, clocks = timed_region(graph.replay, args, dist, dev, local, after=lambda: phases.append(op.phase_ms()))
+    cell_ms = statistics.mean(p[0] for p in phases)
+    p2p_ms = statistics.mean(p[1] for p in phases)
+    op.profile(True, count_pairs=True)
+    op(S, Q, out=out, grad=False)
+    _, _, nlaunch, evaluated = op.phase_ms()
+    # counters off again (an eager execute switches them); profiling stays on:
+    # the graph's event nodes record into the profiling events, which must
+    # outlive every replay
+    op.profile(True, count_pairs=False)
+    op(S, Q, out=out, grad=False)
+    torch.cuda.synchronize()
     ns = int(sum(counts))
-    pairs = int(sum(9 * n * n for n in counts))
+    sms = device_sms(dev)
+    rec = {"beta": beta, "ms_per_step": ms, "targets+sources/s": 2 * ns / (ms * 1e-3),
+           "phases_ms": {"per_cell_prep_and_far_field": cell_ms, "batched_p2p": p2p_ms,
+                         "measured": "CUDA events inside the replayed graph, mean over the timed replays"},
+           "near_block_pairs": int(sum(9 * n * n for n in counts)), "near_pairs_evaluated": evaluated,
+           "roofline": p2p_roofline("modhelm", 8, False, evaluated, p2p_ms, ms,
+                                    "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
+                                    "pairs = those evaluated: triples beyond beta r = 50 are skipped)", sms, clocks),
+           "clocks": clocks, "gpu_launches_per_step": nlaunch, "n_sources_total": ns}
+    return rec, dict(S=S, Q=Q, S_h=S_h, Q_h=Q_h, graph=graph, out=out, ns=ns, counts=counts)
 
-    # phase split and launch count: eager executes on the same buffers, profiled
-    op.profile(True)
-    ph = []
-    for _ in range(3):
-        op(S, Q, out=out, grad=False)
-        ph.append(op.phase_ms())
-    op.profile(False)
-    cell_ms = statistics.median(p[0] for p in ph)
-    p2p_ms = statistics.median(p[1] for p in ph)
-    nlaunch = ph[-1][2]
-    evaluated = ph[-1][3]
+
+def run_batch(args, rank, world, local):
+    """Batched modified Helmholtz: 256 cells (eta = 1, d log-uniform in [1, 64],
+    N log-uniform in [500, 5e4]), 8 rhs, one beta per run, the whole batch
+    captured in one CUDA graph and replayed per step."""
+    import torch
+    beta = float(args.workload.split("beta")[-1])
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = init_dist(world, dev)
+    rec, bufs = time_batch(beta, args, dist, dev, local, scale=args.scale)
+    S, Q, S_h, Q_h, graph, out, ns = (bufs[k] for k in ("S", "Q", "S_h", "Q_h", "graph", "out", "ns"))
+    counts = bufs["counts"]
+    ms, clocks = rec["ms_per_step"], rec["clocks"]
+    pairs, evaluated, nlaunch = rec["near_block_pairs"], rec["near_pairs_evaluated"], rec["gpu_launches_per_step"]
 
     # end to end: pinned host inputs -> device, graph replay, potentials -> pinned host
     pot_h = torch.empty(tuple(out[0].shape), dtype=torch.float64).pin_memory()
@@ -446,10 +553,8 @@ def run_batch(args, rank, world, local):
                        "near_pairs_evaluated": evaluated,
                        "execution": "one CUDA graph per step (per-cell far field + one persistent P2P kernel)",
                        "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
-            "phases_ms": {"per_cell_prep_and_far_field": cell_ms, "batched_p2p": p2p_ms, "measured": "eager execute"},
-            "roofline": p2p_roofline("modhelm", 8, False, evaluated, p2p_ms, cell_ms + p2p_ms,
-                                     "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
-                                     "pairs = those evaluated: triples beyond beta r = 50 are skipped)"),
+            "phases_ms": rec["phases_ms"],
+            "roofline": rec["roofline"],
             "cpu_baseline": cpu, "clocks": clocks,
             "e2e": {"value": job_value(world, 2 * ns, e2e_s), "unit": "targets+sources/s",
                     "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8, "d2h_bytes_per_step": pot_h.numel() * 8,
@@ -523,8 +628,7 @@ def run_adjoint(args, rank, world, local):
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
-            ot = oracle_time(args.workload)
-            cpu = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
+            cpu = cpu_baseline(args.workload)
             cpu["sample"] += "; one oracle evaluation (potential + gradient) gives dE/dq and dE/dx"
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[:200]}
@@ -535,7 +639,7 @@ def run_adjoint(args, rank, world, local):
                        "kernel": "laplace", "n": n, "step": "forward + backward (dE/dq, dE/dx)",
                        "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
             "roofline": p2p_roofline("laplace", 1, True, desc["npairs"], p2p_ms, ms,
-                                     "k_p2p_mixed (near-image P2P of the adjoint execute)"),
+                                     "k_p2p_mixed (near-image P2P of the adjoint execute)", device_sms(dev), clocks),
             "cpu_baseline": cpu, "clocks": clocks,
             "e2e": {"value": job_value(world, 2 * n, e2e_s), "unit": "targets+sources/s",
                     "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8,
@@ -588,9 +692,10 @@ def main():
     singly = cfg.get("singly", False)
     we = args.we or cfg.get("we", "auto")
     beta = cfg.get("beta", 0.0)
+    nrhs = int(Q.shape[0])
     op = PeriodicOp(kernel, w["e1"], w["e2"], beta=beta, tol=cfg["tol"], precision="mixed", path=path,
                     nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly,
-                    we=we)
+                    we=we, nrhs=nrhs)
     op.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = op(S, Q, T, grad=grad)
@@ -652,7 +757,7 @@ def main():
     acc = None
     if not args.skip_fp64 and rank == 0:
         op64 = PeriodicOp(kernel, w["e1"], w["e2"], beta=beta, tol=1e-10, precision="fp64", path="direct",
-                          ns_max=ns, nt_max=nt, singly=singly, we=we)
+                          ns_max=ns, nt_max=nt, singly=singly, we=we, nrhs=nrhs)
         op64.profile(True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -682,23 +787,44 @@ def main():
     # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
     p2p = sum(p2p_ms) / len(p2p_ms)
     nimg = 3 if singly else 3 * (2 * desc["m0"] + 1)
-    kname = "k_p2p_ms" if kernel == "mstokes" else "k_p2p_mixed"
-    roof = p2p_roofline(kernel, 1, grad, desc["npairs"], p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
+    kname = {"mstokes": "k_p2p_ms", "modhelm": "k_p2p_mixed_mh"}.get(kernel, "k_p2p_mixed")
+    # modified Helmholtz skips (target block, source tile, image) triples beyond
+    # beta r = 50: its roofline counts the pairs it evaluates
+    npairs = op.pairs() if kernel == "modhelm" else desc["npairs"]
+    roof = p2p_roofline(kernel, nrhs, grad, npairs, p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
+                        device_sms(dev), clocks,
                         traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", f"{kname}_{args.workload}"), nimg=nimg)
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
-            ot = oracle_time(args.workload)
-            cpu = cpu_baseline_obj(args.workload, ot, "targets+sources/s")
+            cpu = cpu_baseline(args.workload)
         except Exception as e:  # reported, not fatal
             cpu = {"error": str(e)[:200]}
+    # the batched workload (256 cells, 8 rhs) at each beta, graph-replay timed,
+    # as sub-records of the default line
+    batch = None
+    if world == 1 and args.workload == WORKLOAD and args.scale == 1.0 and not args.no_batch:
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup = max(3, min(args.steps, 5)), 3
+        batch = {"workload": "batch_modhelm (256 cells, N log-uniform in [500, 5e4], aspect log-uniform in [1, 64], "
+                             "8 rhs, tol 1e-6, mixed)", "steps": sub.steps, "warmup": sub.warmup,
+                 "l2": "flushed (256 MiB write) before each timed replay"}
+        for b in (1.0, 10.0, 100.0):
+            try:
+                rec, bufs = time_batch(b, sub, None, dev, local)
+                del bufs
+                batch[f"beta{int(b)}"] = rec
+            except Exception as e:  # reported, not fatal
+                batch[f"beta{int(b)}"] = {"error": str(e)[:300]}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": "targets+sources/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64acc", "data": "synthetic",
         "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
                    "kernel": kernel, "e1": list(w["e1"]), "e2": list(w["e2"]),
-                   "n_sources": ns, "n_targets": nt, "targets_are_sources": self_t,
+                   "n_sources": ns, "n_targets": nt, "targets_are_sources": self_t, "nrhs": nrhs,
                    "dist": cfg.get("dist"), "tol": cfg["tol"], "path": ["direct", "direct", "nufft"][desc["path"]],
                    "nufft_w": desc["nufft_w"], "n_gl": desc["n_gl"], "M": desc["M"], "Nq": desc["Nq"],
                    "m0": desc["m0"], "outputs": "pot+grad" if grad else "velocity",
@@ -711,6 +837,8 @@ def main():
                 "d2h_bytes_per_step": d2h, "api": "pfmm_execute_host (pinned host buffers)"},
         "gpu_launches": launches, "accuracy": acc,
     }
+    if batch is not None:
+        line["batch_modhelm"] = batch
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

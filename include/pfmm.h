@@ -130,7 +130,9 @@ typedef struct {
   int nufft_w;          /* ES kernel width (2..16); 0 = ceil(log10(1/tol)) + 2  */
   int n_gl;             /* GL interpolation lines (4..32); 0 = 8 (tol>=1e-7), else 16 */
   int nrhs;             /* number of right-hand sides (>= 1)                    */
-  unsigned flags;       /* PFMM_FAR_ONLY | PFMM_NEAR_ONLY | PFMM_NO_GRAD        */
+  unsigned flags;       /* OR of PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD,
+                           PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC,
+                           PFMM_WE_ROTATED, PFMM_WE_AXIS (see the enum above) */
 } pfmm_opts;
 
 /* Parameters chosen by a plan (read-only; for inspection and tests). */
@@ -219,14 +221,22 @@ pfmm_status pfmm_batch_execute(pfmm_batch* batch, void* workspace, size_t ws_byt
 /* Synchronise and return the first device status error of any cell (see pfmm_get_status). */
 pfmm_status pfmm_batch_get_status(pfmm_batch* batch, void* workspace, void* stream);
 /* Phase timing of batch executes with CUDA events (library tracing, not in
- * the paper).  While enabled, each execute that is not being captured into a
- * graph records three events on its stream.  pfmm_batch_profile_read waits
- * for them and writes ms[0] = the per-cell phases (preparation and far field
- * of every cell), ms[1] = the batched near-image P2P (n >= 2),
- * *nlaunch (may be NULL) = kernels launched by the last execute and *pairs
- * (may be NULL) = near-image pairs evaluated (see pfmm_profile_pairs).
- * Errors: PFMM_ERR_INVALID_ARG (NULL batch, n < 2, no timed execute yet),
- * PFMM_ERR_CUDA. */
+ * the paper).  on = 0 off; 1 events and evaluated-pair counting; 2 events
+ * only.  While enabled, each execute records three events on its stream; an
+ * execute captured into a CUDA graph records them as external event nodes
+ * (cudaEventRecordExternal), so that every replay of the graph records them.
+ * Pair counting (mode 1) adds atomics to the P2P and is switched by eager
+ * executes only: a capture keeps the counting state of the last eager
+ * execute on the same buffers.  pfmm_batch_profile_read waits for the events
+ * and writes ms[0] = the per-cell phases (preparation and far field of every
+ * cell), ms[1] = the batched near-image P2P (n >= 2), of the last execute or
+ * replay, *nlaunch (may be NULL) = kernels launched by the last execute and
+ * *pairs (may be NULL) = near-image pairs evaluated by the last counted
+ * execute (see pfmm_profile_pairs).  Switching profiling off destroys the
+ * events: do not switch it off while a graph captured with it on may still
+ * be replayed.
+ * Errors: PFMM_ERR_INVALID_ARG (NULL batch, bad mode, n < 2, no timed
+ * execute yet), PFMM_ERR_CUDA. */
 pfmm_status pfmm_batch_profile_enable(pfmm_batch* batch, int on);
 pfmm_status pfmm_batch_profile_read(pfmm_batch* batch, float* ms, int n, int* nlaunch, double* pairs);
 void pfmm_batch_destroy(pfmm_batch* batch);
@@ -243,7 +253,11 @@ void pfmm_batch_destroy(pfmm_batch* batch);
  * on each device looks up the array's device address (make it before any
  * stream capture).  All calls on one device share the array: calls that
  * overlap on the GPU race and must be serialised by the caller.  Arguments,
- * outputs and errors otherwise as pfmm_execute (device pointers). */
+ * outputs and host-side errors otherwise as pfmm_execute (device pointers).
+ * Conditions only visible on the device go to the array's status word:
+ * read them with pfmm_get_status(plan, NULL, stream) before the next call
+ * (which clears the word).  The cached address belongs to the device's
+ * context: do not use the library across cudaDeviceReset. */
 pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const double* src, const double* q, int64_t nt,
                                 const double* trg, double* pot, double* grad, void* stream);
 
@@ -273,9 +287,6 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* plan, void* workspace, size_t ws_byt
                                  const double* g, const double* grad_fwd, double* dq, double* dsrc,
                                  double* dtrg, void* stream);
 
-/* Synchronise the stream and read the device status word written by the
- * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,
- * PFMM_ERR_NOT_NEUTRAL, PFMM_ERR_TIMEOUT) and clears it. */
 /* Pressure of the periodic Stokeslet sum (the Stokes kernel of Sec. 5 and
  * its lattice sum, Eq. psum): for the Stokeslet u = (1/4pi)(-log r I +
  * r r^T / r^2) f the pressure is p = (1/2pi) f . r / r^2 = -f . grad G_L with
@@ -291,6 +302,12 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* plan, void* workspace, size_t ws_byt
 pfmm_status pfmm_stokes_pressure(pfmm_plan* plan, void* workspace, size_t ws_bytes, int64_t ns, const double* src,
                                  const double* f, int64_t nt, const double* trg, double* pres, void* stream);
 
+/* Synchronise the stream and read the device status word written by the
+ * last execute on this workspace; returns it (PFMM_OK, PFMM_ERR_NONFINITE,
+ * PFMM_ERR_NOT_NEUTRAL, PFMM_ERR_TIMEOUT, or PFMM_ERR_INVALID_ARG for points
+ * outside a singly periodic strip) and clears it.  workspace == NULL reads
+ * the status word of pfmm_execute_static's scratch array on the current
+ * device.  Errors: PFMM_ERR_INVALID_ARG (NULL plan), PFMM_ERR_CUDA. */
 pfmm_status pfmm_get_status(pfmm_plan* plan, void* workspace, void* stream);
 
 /* Per-phase GPU timing (tracing).  When enabled (on != 0), pfmm_execute

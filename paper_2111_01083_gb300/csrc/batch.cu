@@ -46,6 +46,7 @@ struct pfmm_batch {
   int p2p_chunk = 4096;
   // tracing (pfmm_batch_profile_*)
   bool prof = false, timed = false, counting = false;
+  bool count_pairs = true;  // profiling mode 1 counts evaluated pairs, mode 2 records events only
   cudaEvent_t ev[3] = {};
   int nlaunch = 0;
   // per-cell phases fan out over kFan streams (fork/join with events), so the
@@ -187,6 +188,8 @@ static cudaError_t fan_setup(pfmm_batch* b) {
 
 pfmm_status pfmm_batch_profile_enable(pfmm_batch* b, int on) {
   if (!b) return set_error(PFMM_ERR_INVALID_ARG, "NULL batch");
+  if (on < 0 || on > 2) return set_error(PFMM_ERR_INVALID_ARG, "profiling mode must be 0, 1 or 2");
+  if (on) b->count_pairs = on == 1;
   if (on && !b->prof) {
     for (auto& e : b->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "cudaEventCreate failed");
@@ -284,15 +287,25 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
-  const bool rec = b->prof && cap == cudaStreamCaptureStatusNone;
-  if (mixed && b->kernel == PFMM_MODHELM && rec != b->counting) {
-    // evaluated-pair counters in the P2P descriptors only while profiling
-    for (int c = 0; c < b->ncell; ++c) set_work_counter(b->plans[c], ws + b->wsoff[c], rec, &b->hcells[c]);
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  // Phase events: plain records on an eager execute; under stream capture
+  // they become external event-record nodes, so each replay of the graph
+  // records them and pfmm_batch_profile_read times the replayed phases.
+  const bool rec = b->prof;
+  auto record = [&](cudaEvent_t ev) {
+    return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+  };
+  // Evaluated-pair counters in the P2P descriptors only while profiling in
+  // mode 1.  They are switched on an eager execute only (the switch uploads
+  // descriptors); a capture keeps the state of the last eager execute.
+  const bool count = b->prof && b->count_pairs && !capturing;
+  if (mixed && b->kernel == PFMM_MODHELM && !capturing && count != b->counting) {
+    for (int c = 0; c < b->ncell; ++c) set_work_counter(b->plans[c], ws + b->wsoff[c], count, &b->hcells[c]);
     e = cudaMemcpyAsync(ws + b->off_cells, b->hcells.data(), sizeof(P2PArgs) * b->ncell, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload descriptors: %s", cudaGetErrorString(e));
-    b->counting = rec;
+    b->counting = count;
   }
-  if (rec) cudaEventRecord(b->ev[0], st);
+  if (rec && (e = record(b->ev[0])) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event record: %s", cudaGetErrorString(e));
   b->nlaunch = 0;
   // per-cell phases: cell c on fan stream c % kFan, forked from and joined
   // back into the caller's stream
@@ -318,7 +331,7 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
     }
     if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "join: %s", cudaGetErrorString(e));
   }
-  if (rec) cudaEventRecord(b->ev[1], st);
+  if (rec && (e = record(b->ev[1])) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event record: %s", cudaGetErrorString(e));
   if (mixed) {
     int nl = 0;
     e = sort_cells((const SortCell*)(ws + b->off_sort), b->hsort.data(), (int)b->hsort.size(), b->sort_total,
@@ -336,7 +349,7 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
     }
   }
   if (rec) {
-    cudaEventRecord(b->ev[2], st);
+    if ((e = record(b->ev[2])) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event record: %s", cudaGetErrorString(e));
     b->timed = true;
   }
   return PFMM_OK;

@@ -18,7 +18,12 @@
 // must start at zero are cleared on every call, so the contents left by an
 // earlier call do not matter.  All calls on a device share the one array:
 // calls whose work overlaps on the GPU (different streams, or different host
-// threads) race on it and must be serialised by the caller.
+// threads) race on it and must be serialised by the caller.  Conditions the
+// kernels detect (non-finite input, non-zero net charge or force, points
+// outside a singly periodic strip) go to the status word inside the array, as
+// they go to a workspace's status word for pfmm_execute; the caller reads and
+// clears it with pfmm_get_status(plan, NULL, stream), which synchronises the
+// stream.  The next call clears the word as it starts, so read it before.
 #include <mutex>
 
 #include "pfmm_impl.h"
@@ -35,6 +40,30 @@ void* g_static_ptr[kMaxDevices] = {};
 
 }  // namespace
 
+namespace pfmm {
+
+// Device address of the static scratch array on the current device (looked
+// up on the first use per device and cached; see the file comment).  The
+// cache assumes the device's context lives as long as the process: the
+// library must not be used across cudaDeviceReset.
+pfmm_status static_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(PFMM_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+    if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return PFMM_OK;
+}
+
+}  // namespace pfmm
+
 extern "C" pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const double* src, const double* q, int64_t nt,
                                            const double* trg, double* pot, double* grad, void* stream) {
   if (!plan) return pfmm::set_error(PFMM_ERR_INVALID_ARG, "NULL plan");
@@ -46,20 +75,8 @@ extern "C" pfmm_status pfmm_execute_static(pfmm_plan* plan, int64_t ns, const do
                            "pfmm_execute_static: this plan needs %zu bytes of scratch, the static array holds %zu "
                            "(use pfmm_execute with a caller workspace, or smaller ns_max/nt_max/nrhs)",
                            need, kStaticScratchBytes);
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return pfmm::set_error(PFMM_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return pfmm::set_error(PFMM_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
   void* ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-      e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-      if (e != cudaSuccess)
-        return pfmm::set_error(PFMM_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      g_static_ptr[dev] = ptr;
-    }
-    ptr = g_static_ptr[dev];
-  }
+  s = pfmm::static_scratch(&ptr);
+  if (s != PFMM_OK) return s;
   return pfmm_execute(plan, ptr, kStaticScratchBytes, ns, src, q, nt, trg, pot, grad, stream);
 }

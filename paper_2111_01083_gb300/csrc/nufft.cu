@@ -33,7 +33,7 @@
 //            b = IFFT(v(k) / phihat(alpha k)).
 // Two real lines share one complex FFT (real + i imag).
 #include <algorithm>
-#include <atomic>
+#include <mutex>
 #include <cmath>
 #include "pfmm_impl.h"
 #include "devmath.cuh"
@@ -441,20 +441,21 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
 
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
 // that executes after the first (including ones captured in a CUDA graph)
-// make no attribute calls.  The cache is atomic: plans may execute from
-// several host threads (a lost update only repeats the idempotent call).
+// make no attribute calls.  cudaFuncSetAttribute sets the limit (it may also
+// lower it), so the call and the cache update happen under one lock and the
+// value set is never below what an earlier call established: plans may
+// execute from several host threads with different sizes.
 static cudaError_t raise_smem(const void* fn, int slot, size_t bytes) {
-  static std::atomic<int> done[32][4] = {};
+  static std::mutex mu;
+  static int done[32][4] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+  std::lock_guard<std::mutex> lock(mu);
   const bool cached = dev >= 0 && dev < 32;
-  if (cached && done[dev][slot].load(std::memory_order_relaxed) >= (int)bytes) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess && cached) {
-    int cur = done[dev][slot].load(std::memory_order_relaxed);
-    while (cur < (int)bytes && !done[dev][slot].compare_exchange_weak(cur, (int)bytes, std::memory_order_relaxed)) {
-    }
-  }
+  if (cached && done[dev][slot] >= (int)bytes) return cudaSuccess;
+  const int want = cached ? std::max(done[dev][slot], (int)bytes) : (int)bytes;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (e == cudaSuccess && cached) done[dev][slot] = want;
   return e;
 }
 

@@ -158,6 +158,8 @@ cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st);
 pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q, int64_t nt,
                          const double* trg, double* pot, double* grad, cudaStream_t st, bool self, bool upload,
                          bool near);
+// device address of pfmm_execute_static's scratch array on the current device
+pfmm_status static_scratch(void** out);
 // kernels launched by the most recent launch_* call (set by each launcher)
 extern thread_local int g_launches;
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st);

@@ -729,7 +729,12 @@ pfmm_status pfmm_execute_adjoint(pfmm_plan* p, void* workspace, size_t ws_bytes,
 }
 
 pfmm_status pfmm_get_status(pfmm_plan* p, void* workspace, void* stream) {
-  if (!p || !workspace) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
+  if (!workspace) {
+    // the status word of pfmm_execute_static's scratch array on this device
+    pfmm_status s = static_scratch(&workspace);
+    if (s != PFMM_OK) return s;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   int h[kStatusWords];
   cudaError_t e = cudaMemcpyAsync(h, (char*)workspace + p->lay.status, sizeof h, cudaMemcpyDeviceToHost, st);

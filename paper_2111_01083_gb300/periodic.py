@@ -309,10 +309,12 @@ class BatchOp:
         st = stream if stream is not None else torch.cuda.current_stream(device).cuda_stream
         _lib.check(_lib.lib().pfmm_batch_get_status(self._h, _ptr(ws), ctypes.c_void_p(st)))
 
-    def profile(self, on=True):
-        """Record CUDA events around the per-cell phases and the batched P2P
-        of every execute not captured in a graph (pfmm_batch_profile_enable)."""
-        _lib.check(_lib.lib().pfmm_batch_profile_enable(self._h, int(bool(on))))
+    def profile(self, on=True, count_pairs=True):
+        """Record CUDA events around the per-cell phases and the batched P2P of
+        every execute, also inside a captured graph (pfmm_batch_profile_enable);
+        count_pairs: also count the near-image pairs evaluated (eager executes)."""
+        mode = 0 if not on else (1 if count_pairs else 2)
+        _lib.check(_lib.lib().pfmm_batch_profile_enable(self._h, mode))
 
     def phase_ms(self):
         """(per-cell phases ms, batched P2P ms, kernels launched, near-image

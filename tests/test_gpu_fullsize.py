@@ -117,9 +117,63 @@ def test_laplace_adjoint_full():
     assert _cmp(S.grad.detach().cpu().numpy()[:, idx], force, False) < 1e-6
 
 
-def test_batch_modhelm_full_beta1():
-    """256 cells, N log-uniform in [500, 5e4], aspect in [1, 64], 8 rhs, beta = 1,
-    one graph replay; sampled cells and targets against the oracle."""
+def test_laplace_adjoint_fd_full():
+    """Central finite differences (h = 1e-6, FP64 oracle) of E = 1/2 sum q_i phi(x_i)
+    at the full differentiation workload (5e4 charges, 4 x 1 cell), 64 seeded
+    position directions and 64 paired charge directions, against the adjoint.
+
+    Only the terms of E that change are evaluated.  Moving x_i by +-h d changes
+    the pair terms of i with every other charge and image; by the symmetry of
+    the periodic kernel, E(x_i + h d) - E(x_i - h d) = q_i (phi(x_i + h d) -
+    phi(x_i - h d)), phi the potential of all charges evaluated at the two
+    displaced points (the i-i image terms do not depend on x_i, and the
+    singular q_i G(+-h d) terms are equal and cancel).  E is quadratic in q, so
+    for the neutral direction v = e_i - e_j, E(q + h v) - E(q - h v) = 2 h v.K q
+    = 2 h (phi(x_i) - phi(x_j)) exactly."""
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp, periodic
+    w = workloads.make("laplace_adjoint_4x1_n5e4")
+    dev = torch.device("cuda", 0)
+    n = w["src"].shape[1]
+    S = torch.tensor(w["src"], device=dev, requires_grad=True)
+    Q = torch.tensor(w["q"], device=dev, requires_grad=True)
+    op = PeriodicOp("laplace", w["e1"], w["e2"], tol=1e-6, precision="mixed", ns_max=n, nt_max=n)
+    pot, _ = periodic(op, S, Q)
+    (0.5 * (Q * pot).sum()).backward()
+    dq = Q.grad.detach().cpu().numpy()[0]
+    dx = S.grad.detach().cpu().numpy()
+    h = 1e-6
+    rng = np.random.default_rng(64)
+    # positions: 64 seeded indices and unit directions
+    idx = rng.choice(n, 64, replace=False)
+    ang = rng.uniform(0.0, 2.0 * math.pi, 64)
+    d = np.stack([np.cos(ang), np.sin(ang)])
+    x = w["src"][:, idx]
+    pts = np.concatenate([x + h * d, x - h * d], axis=1)
+    phi, _ = _oracle_at("laplace", 0.0, w["e1"], w["e2"], w["src"], w["q"], pts)
+    fd_x = w["q"][0, idx] * (phi[0, :64] - phi[0, 64:]) / (2 * h)
+    ad_x = np.einsum("kn,kn->n", dx[:, idx], d)
+    assert _cmp(ad_x, fd_x, False) < 1e-5
+    # charges: 64 seeded pairs (i, j), direction e_i - e_j
+    pi = rng.choice(n, 64, replace=False)
+    pj = rng.choice(n, 64, replace=False)
+    keep = pi != pj
+    pi, pj = pi[keep], pj[keep]
+    phi_q, _ = _oracle_at("laplace", 0.0, w["e1"], w["e2"], w["src"], w["q"],
+                          np.concatenate([w["src"][:, pi], w["src"][:, pj]], axis=1))
+    m = len(pi)
+    fd_q = (2 * h * (phi_q[0, :m] - phi_q[0, m:])) / (2 * h)
+    assert _cmp(dq[pi] - dq[pj], fd_q, False) < 1e-5
+
+
+@pytest.mark.parametrize("beta", [1.0, 10.0, 100.0])
+def test_batch_modhelm_full(beta):
+    """256 cells, N log-uniform in [500, 5e4], aspect in [1, 64], 8 rhs, one
+    graph replay, for each beta of the batched workload; the largest cell and
+    3 seeded cells, 48 sampled targets each, against the oracle.  At beta =
+    100 the south/north far field is pruned (below eps) and the P2P skips
+    (target block, source tile, image) triples beyond beta r = 50, so this is
+    the configuration that checks those two shortcuts at full size."""
     import torch
     from paper_2111_01083_gb300 import BatchOp
     cells = workloads.batch_cells(ncell=256, seed=3, nrhs=8)
@@ -127,7 +181,7 @@ def test_batch_modhelm_full_beta1():
     dev = torch.device("cuda", 0)
     S = torch.tensor(np.concatenate([c["src"] for c in cells], axis=1), device=dev)
     Q = torch.tensor(np.concatenate([c["q"] for c in cells], axis=1), device=dev)
-    op = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=1.0) for c in cells], counts, precision="mixed",
+    op = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=beta) for c in cells], counts, precision="mixed",
                  nrhs=8, tol=1e-6)
     graph, out = op.capture(S, Q, grad=False)
     graph.replay()
@@ -141,9 +195,9 @@ def test_batch_modhelm_full_beta1():
         cell = cells[c]
         n = counts[c]
         idx = rng.choice(n, min(48, n), replace=False)
-        ref, _ = _oracle_at("modhelm", 1.0, cell["e1"], cell["e2"], cell["src"], cell["q"], cell["src"][:, idx])
+        ref, _ = _oracle_at("modhelm", beta, cell["e1"], cell["e2"], cell["src"], cell["q"], cell["src"][:, idx])
         got = pot[:, edges[c]:edges[c + 1]][:, idx]
-        assert _cmp(got, ref, False) < 1e-6, (c, n)
+        assert _cmp(got, ref, False) < 1e-6, (beta, c, n)
 
 
 def test_laplace_p1_strip_full():

@@ -51,3 +51,29 @@ def test_execute_static_rejects_large_plans():
     code = _lib.lib().pfmm_execute_static(op._h, 10, None, None, 10, None, None, None, None)
     assert code == 5  # PFMM_ERR_WORKSPACE
     assert b"static array" in _lib.lib().pfmm_last_error()
+
+
+def test_execute_static_reports_device_status():
+    """Conditions only the kernels can see (here a NaN strength) land in the
+    static array's status word; pfmm_get_status with a NULL workspace reads
+    and clears it, and a clean call afterwards reports PFMM_OK."""
+    import torch
+    from paper_2111_01083_gb300 import PeriodicOp, _lib
+    from paper_2111_01083_gb300.periodic import _ptr
+
+    dev = torch.device("cuda", 0)
+    e1, e2 = (2.0, 0.0), (0.3, 1.0)
+    rng = np.random.default_rng(7)
+    src = torch.tensor(workloads.points(rng, e1, e2, 500), device=dev)
+    q = torch.tensor(workloads.strengths(rng, 1, 500), device=dev)
+    op = PeriodicOp("laplace", e1, e2, tol=1e-6, precision="mixed", ns_max=500, nt_max=500)
+    pot = torch.empty((1, 500), dtype=torch.float64, device=dev)
+    grad = torch.empty((1, 2, 500), dtype=torch.float64, device=dev)
+    L = _lib.lib()
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    bad = q.clone()
+    bad[0, 17] = float("nan")
+    _lib.check(L.pfmm_execute_static(op._h, 500, _ptr(src), _ptr(bad), 500, _ptr(src), _ptr(pot), _ptr(grad), st))
+    assert L.pfmm_get_status(op._h, None, st) == 7  # PFMM_ERR_NONFINITE
+    _lib.check(L.pfmm_execute_static(op._h, 500, _ptr(src), _ptr(q), 500, _ptr(src), _ptr(pot), _ptr(grad), st))
+    assert L.pfmm_get_status(op._h, None, st) == 0

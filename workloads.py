@@ -74,6 +74,11 @@ CONFIGS = {
     # [-1/2, 1/2) x [-2, 2), targets = sources (the paper's P1 rectangle cases)
     "laplace_p1_strip4_n1e5": dict(kernel="laplace", e1=(1.0, 0.0), e2=(0.0, 4.0), ns=100000,
                                    seed=6, dist="uniform", tol=1e-6, precision="mixed", singly=True),
+    # one long cell of the batched workload's shape (aspect 64, beta = 1, 8 rhs):
+    # the far-field kernels (NUFFT spread/interpolation, direct formation and
+    # evaluation) at the size where the batch's per-cell phases are largest
+    "modhelm_aspect64_beta1_n5e4_r8": dict(kernel="modhelm", beta=1.0, e1=(64.0, 0.0), e2=(0.0, 1.0), ns=50000,
+                                           seed=9, dist="uniform", tol=1e-6, precision="mixed", nrhs=8),
 }
 
 
@@ -85,7 +90,7 @@ def make(name, scale=1.0, seed=None):
     if nt is not None:
         nt = max(1, int(round(nt * scale)))
     w = single_cell(c["kernel"], c["e1"], c["e2"], ns, nt, seed if seed is not None else c["seed"],
-                    c.get("dist", "uniform"), beta=c.get("beta", 0.0))
+                    c.get("dist", "uniform"), nrhs=c.get("nrhs", 1), beta=c.get("beta", 0.0))
     for k in ("tol", "precision", "path", "nufft_w", "n_gl", "singly"):
         if k in c:
             w[k] = c[k]
