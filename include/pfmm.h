@@ -100,11 +100,23 @@ enum {
                                (App. A, Eq. k0west2): the near block is 3 x 3 images
                                (m0 = 1) for every parallelogram, at the price of more
                                west/east quadrature nodes on strongly skewed cells */
-  PFMM_WE_AXIS = 64        /* west/east plane waves decay along e1; m0 = 1 unless the
+  PFMM_WE_AXIS = 64,       /* west/east plane waves decay along e1; m0 = 1 unless the
                                canonical skew |xi| > 3d/8, then m0 = 2 (15 images).
                                Neither flag (default): rotated exactly when the axis
                                direction would need m0 = 2.  Both: PFMM_ERR_INVALID_ARG.
                                The singly periodic operator always uses the axis. */
+  PFMM_NEAR_DIRECT = 128,  /* near-image sum by the direct P2P over all pairs            */
+  PFMM_NEAR_FMM = 256      /* near-image sum by the tree code (the paper evaluates the
+                               near field with an FMM, Sec. 7): one quadtree of the unit
+                               cell's sources, its image copies shifted by l (sharing the
+                               unit cell's expansions), one of the targets; complex
+                               multipole/local expansions of p terms, boxes expanded when
+                               r_t + r_s <= theta |c_t - c_s - l| (theta = 1/2), neighbouring
+                               leaves summed directly.  Laplace and Stokes, mixed precision.
+                               Neither flag (default): the tree code when the kernel and
+                               precision allow it and ns * nt * images >= 2e9, else the
+                               direct P2P.  Both: PFMM_ERR_INVALID_ARG.  The FMM flag with
+                               another kernel or FP64 selects the direct P2P. */
 };
 
 typedef enum {
@@ -132,7 +144,11 @@ typedef struct {
   int nrhs;             /* number of right-hand sides (>= 1)                    */
   unsigned flags;       /* OR of PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD,
                            PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC,
-                           PFMM_WE_ROTATED, PFMM_WE_AXIS (see the enum above) */
+                           PFMM_WE_ROTATED, PFMM_WE_AXIS, PFMM_NEAR_DIRECT,
+                           PFMM_NEAR_FMM (see the enum above) */
+  int near_order;       /* tree-code expansion terms p (8..32, rounded up to 12, 16, 20,
+                           24 or 32); 0 = from tol: theta^p <= tol / 10 */
+  int near_leaf;        /* tree code: a box with more points is split (8..1024); 0 = 48 */
 } pfmm_opts;
 
 /* Parameters chosen by a plan (read-only; for inspection and tests). */
@@ -151,6 +167,10 @@ typedef struct {
   int we_rotated;       /* 1 if the west/east plane waves decay along e2-perp   */
   double we_dir[2];     /* (cos, sin) of that direction's rotation: canonical
                            (x, y) -> (cos x - sin y, sin x + cos y); (1, 0) on the axis */
+  int near_fmm;         /* 1 if the near-image sum runs through the tree code      */
+  int near_order;       /* its expansion terms p                                    */
+  int near_leaf;        /* its leaf size                                            */
+  double near_theta;    /* its acceptance parameter                                 */
 } pfmm_plan_desc;
 
 typedef struct pfmm_plan pfmm_plan;
@@ -313,17 +333,31 @@ pfmm_status pfmm_get_status(pfmm_plan* plan, void* workspace, void* stream);
 /* Per-phase GPU timing (tracing).  When enabled (on != 0), pfmm_execute
  * records CUDA events on the caller's stream around its phases; the events
  * are created here (no device memory).  pfmm_profile_read waits for the last
- * recorded event and returns milliseconds per phase in ms[0..n-1]:
+ * recorded event and returns milliseconds per phase in ms[0..n-1] (n <= 8):
  * [0] prep (wrap, convert, moments), [1] far field (periodizing operator),
- * [2] near-image P2P.  Errors: PFMM_ERR_INVALID_ARG, PFMM_ERR_CUDA. */
+ * [2] near-image sum; when the tree code ran, [3..7] split [2] into tree
+ * construction, upward pass (P2M, M2M), traversal and list grouping,
+ * downward pass (M2L, L2L) and leaves (L2P + direct sums), else they are 0.
+ * Errors: PFMM_ERR_INVALID_ARG, PFMM_ERR_CUDA. */
 pfmm_status pfmm_profile_enable(pfmm_plan* plan, int on);
 pfmm_status pfmm_profile_read(pfmm_plan* plan, float* ms, int n);
 /* Near-image pairs (target, source, image) the P2P evaluated in the last
  * profiled execute on `workspace`: ns * nt * images, except for the mixed
  * modified Helmholtz kernel, which skips (target block, source tile, image)
- * triples beyond beta r = 50 and counts what it evaluates.  Synchronises
+ * triples beyond beta r = 50 and counts what it evaluates, and for the
+ * tree code, which counts the pairs of neighbouring leaves it sums directly.  Synchronises
  * `stream`.  Errors: PFMM_ERR_INVALID_ARG (NULL, profiling off), PFMM_ERR_CUDA. */
 pfmm_status pfmm_profile_pairs(pfmm_plan* plan, const void* workspace, void* stream, double* pairs);
+
+/* Statistics of the tree code in the last execute on `workspace` (tracing;
+ * synchronises `stream`): out[0] tree boxes (sources and targets), out[1]
+ * M2L interactions, out[2] leaf pairs summed directly (list entries), out[3]
+ * (target, source) point pairs summed directly (counted only while profiling
+ * is on, else 0), out[4] overflow bits (0 = none; otherwise a capacity ran
+ * out and the direct sum replaced the tree code).  Errors:
+ * PFMM_ERR_INVALID_ARG (NULL, or the plan does not use the tree code),
+ * PFMM_ERR_CUDA. */
+pfmm_status pfmm_near_stats(pfmm_plan* plan, const void* workspace, void* stream, int64_t out[5]);
 
 const char* pfmm_last_error(void);
 void pfmm_plan_destroy(pfmm_plan* plan);

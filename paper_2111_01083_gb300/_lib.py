@@ -15,6 +15,7 @@ PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
 PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC = 1, 2, 4, 8, 16
 PFMM_WE_ROTATED, PFMM_WE_AXIS = 32, 64
+PFMM_NEAR_DIRECT, PFMM_NEAR_FMM = 128, 256
 
 STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PFMM_ERR_NOT_NEUTRAL",
           4: "PFMM_ERR_TOLERANCE", 5: "PFMM_ERR_WORKSPACE", 6: "PFMM_ERR_CUDA", 7: "PFMM_ERR_NONFINITE",
@@ -26,14 +27,15 @@ EXPORTS = ["pfmm_plan_create", "pfmm_workspace_size", "pfmm_workspace_size_host"
            "pfmm_version", "pfmm_profile_enable", "pfmm_profile_read", "pfmm_profile_pairs", "pfmm_execute_static",
            "pfmm_batch_create", "pfmm_batch_workspace_size", "pfmm_batch_execute", "pfmm_batch_get_status",
            "pfmm_batch_destroy", "pfmm_batch_profile_enable", "pfmm_batch_profile_read", "pfmm_execute_adjoint",
-           "pfmm_stokes_pressure"]
+           "pfmm_stokes_pressure", "pfmm_near_stats"]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("e1", ctypes.c_double * 2), ("e2", ctypes.c_double * 2), ("kernel", ctypes.c_int),
                 ("beta", ctypes.c_double), ("tol", ctypes.c_double), ("precision", ctypes.c_int),
                 ("path", ctypes.c_int), ("nufft_w", ctypes.c_int), ("n_gl", ctypes.c_int),
-                ("nrhs", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("nrhs", ctypes.c_int), ("flags", ctypes.c_uint), ("near_order", ctypes.c_int),
+                ("near_leaf", ctypes.c_int)]
 
 
 class PlanDesc(ctypes.Structure):
@@ -41,7 +43,9 @@ class PlanDesc(ctypes.Structure):
                 ("rot", ctypes.c_double * 4), ("m0", ctypes.c_int), ("M", ctypes.c_int), ("mode0", ctypes.c_int),
                 ("Nq", ctypes.c_int), ("path", ctypes.c_int), ("n_gl", ctypes.c_int), ("nf", ctypes.c_int),
                 ("nufft_w", ctypes.c_int), ("es_beta", ctypes.c_double), ("nlaunch", ctypes.c_int),
-                ("npairs", ctypes.c_int64), ("we_rotated", ctypes.c_int), ("we_dir", ctypes.c_double * 2)]
+                ("npairs", ctypes.c_int64), ("we_rotated", ctypes.c_int), ("we_dir", ctypes.c_double * 2),
+                ("near_fmm", ctypes.c_int), ("near_order", ctypes.c_int), ("near_leaf", ctypes.c_int),
+                ("near_theta", ctypes.c_double)]
 
 
 class PfmmError(RuntimeError):
@@ -107,6 +111,8 @@ def lib():
     L.pfmm_profile_read.restype = ctypes.c_int
     L.pfmm_profile_pairs.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.pfmm_profile_pairs.restype = ctypes.c_int
+    L.pfmm_near_stats.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    L.pfmm_near_stats.restype = ctypes.c_int
     L.pfmm_version.argtypes = []
     L.pfmm_version.restype = ctypes.c_char_p
     _lib = L

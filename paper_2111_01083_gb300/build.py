@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpfmm.so")
-SOURCES = ["plan.cu", "far_direct.cu", "p2p.cu", "nufft.cu", "batch.cu", "noalloc.cu", "sort.cu"]
+SOURCES = ["plan.cu", "far_direct.cu", "p2p.cu", "nufft.cu", "batch.cu", "noalloc.cu", "sort.cu", "fmm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr"]

@@ -96,7 +96,11 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
   for (int c = 0; c < ncell; ++c) {
     int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
     pfmm_plan* p = nullptr;
-    pfmm_status s = pfmm_plan_create(&cells[c], ns, nt, &p);
+    // the near field of a batch is the batched P2P (or the per-cell direct
+    // P2P on the FP64 path): plans without the tree code's workspace
+    pfmm_opts oc = cells[c];
+    oc.flags = (oc.flags & ~(unsigned)PFMM_NEAR_FMM) | PFMM_NEAR_DIRECT;
+    pfmm_status s = pfmm_plan_create(&oc, ns, nt, &p);
     if (s != PFMM_OK) {
       for (auto* q : b->plans) pfmm_plan_destroy(q);
       delete b;

@@ -8,6 +8,7 @@
 namespace pfmm {
 
 constexpr int kMaxNear = 32;      // (2 m0 + 1) * 3 images; m0 <= 3 after reduction
+constexpr int kPlanEvents = 8;    // profiling events of a plan
 constexpr int kStatusWords = 8;   // status word region (ints)
 
 // device status bits (combined with atomicOr; mapped to pfmm_status by the host)
@@ -83,8 +84,33 @@ struct Layout {
   size_t wts;              // weights for evaluation: double2 or float2 [nrhs][nwch][nterm]
   size_t nufft;            // NUFFT scratch (grids, spectra)
   size_t adj;              // adjoint scratch (gradient of the adjoint field, potential if dq is not wanted)
+  size_t fmm;              // near-field tree code (FmmPlan offsets are relative to this)
   size_t stage;            // host-staging region (pfmm_execute_host only)
   size_t total, total_host;
+};
+
+// Near field by the tree code of fmm.cu (see there): sizes and byte offsets
+// of its region of the workspace, fixed at plan creation from ns_max, nt_max.
+constexpr int kFmmL = 11;                  // finest tree level: boxes of side s0 / 2^11
+constexpr int kFmmIter = 2 * (kFmmL + 1);  // traversal sweeps (each descends at least one tree)
+constexpr int kFmmMaxP = 32;               // expansion terms are lanes of a warp
+struct FmmPlan {
+  int on;              // 1: the near field runs through the tree code
+  int p;               // expansion terms (coefficients 0 .. p-1)
+  int nleaf;           // a box with more points than this is split (down to level kFmmL)
+  double theta;        // a (target box, source box, image) triple is expanded when r_t + r_s <= theta |c_t - c_s - l|
+  int ncol;            // root boxes (squares of side s0) along x
+  double x0, y0, s0;   // lower-left corner of the root row, root side
+  int nchan;           // complex expansions per source box: nrhs (Laplace), 4 nrhs (Stokes)
+  int64_t npts;        // ns_max + nt_max
+  int64_t node_cap;    // bound on tree boxes of both point sets (never exceeded)
+  int64_t exp_cap;     // boxes with expansions; more boxes, or longer lists, switch to the direct fallback
+  int64_t m2l_cap, p2p_cap, front_cap;
+  // byte offsets inside the region
+  size_t o_ctl, o_key, o_val, o_key2, o_val2, o_hist, o_xy, o_hl, o_perm, o_qd, o_qf, o_cnt, o_lf, o_off,
+      o_bsum, o_lo, o_hi, o_lev, o_par, o_nend, o_nch, o_done, o_ctr, o_half, o_rad, o_mult, o_loc, o_front,
+      o_m2l, o_p2p, o_gcnt, o_gcur, o_glist, o_roots;
+  size_t bytes;
 };
 
 }  // namespace pfmm
@@ -115,6 +141,7 @@ struct pfmm_plan {
   double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
   double* tw_h;             // [nf/2][2] FFT twiddles (cos, sin)(2 pi k / nf), NUFFT path only
   pfmm::Layout lay;
+  pfmm::FmmPlan fmm;        // near field by the tree code (fmm.on)
   // host copies of the sort descriptors of the last execute (sources, targets);
   // kept in the plan so that the asynchronous upload reads live memory
   pfmm::SortCell* sort_h;
@@ -125,7 +152,8 @@ struct pfmm_plan {
   int64_t s_stride, t_stride, o_stride;
   // tracing / bookkeeping
   bool prof;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[pfmm::kPlanEvents];  // phase boundaries (0-3), tree-code sub-phases (4-7)
+  bool near_fmm_ran;                  // the last execute ran the tree code
   int nlaunch;
   int64_t npairs;
 };
@@ -152,6 +180,13 @@ cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
                              double* pot, double* grad, cudaStream_t st);
 cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
                        double* pot, double* grad, bool accumulate, cudaStream_t st);
+// near field through the tree code (fmm.cu); adds to pot/grad like launch_p2p
+cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                            double* grad, cudaStream_t st);
+// sizes and offsets of the tree code's workspace region (p->fmm.bytes = 0 when it is off)
+void fmm_setup(pfmm_plan* p);
+// statistics of the last tree-code execute (see pfmm_near_stats); synchronises st
+cudaError_t fmm_stats(const pfmm_plan* p, const char* ws, cudaStream_t st, int64_t out[5]);
 // records a thread-local error message (pfmm_last_error) and returns s
 pfmm_status set_error(pfmm_status s, const char* fmt, ...);
 cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st);

@@ -261,9 +261,11 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
     if (e != cudaSuccess) return cuda_fail(e, "zero outputs");
   }
   rec(2);
+  p->near_fmm_ran = do_near && p->fmm.on;
   if (do_near) {
-    e = launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
-    if (e != cudaSuccess) return cuda_fail(e, "p2p kernel");
+    e = p->fmm.on ? launch_fmm_near(p, ws, ns, nt, self, pot, grad, st)
+                  : launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
+    if (e != cudaSuccess) return cuda_fail(e, p->fmm.on ? "near-field tree code" : "p2p kernel");
     p->nlaunch += g_launches;
     p->npairs = (int64_t)ns * nt * p->geom.nimg;
   }
@@ -293,7 +295,13 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     if (o->flags & PFMM_SINGLY_PERIODIC)
       return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel is doubly periodic only");
   }
-  if (o->flags & ~127u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~127u);
+  if (o->flags & ~511u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~511u);
+  if ((o->flags & PFMM_NEAR_DIRECT) && (o->flags & PFMM_NEAR_FMM))
+    return fail(PFMM_ERR_INVALID_ARG, "NEAR_DIRECT and NEAR_FMM are exclusive");
+  if (o->near_order != 0 && (o->near_order < 8 || o->near_order > 32))
+    return fail(PFMM_ERR_INVALID_ARG, "near_order in [8, 32]");
+  if (o->near_leaf != 0 && (o->near_leaf < 8 || o->near_leaf > 1024))
+    return fail(PFMM_ERR_INVALID_ARG, "near_leaf in [8, 1024]");
   if ((o->flags & PFMM_FAR_ONLY) && (o->flags & PFMM_NEAR_ONLY))
     return fail(PFMM_ERR_INVALID_ARG, "FAR_ONLY and NEAR_ONLY are exclusive");
   if (o->nufft_w != 0 && (o->nufft_w < 2 || o->nufft_w > 16)) return fail(PFMM_ERR_INVALID_ARG, "nufft_w in [2,16]");
@@ -491,6 +499,8 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   // gradient of the adjoint field at the sources needs [nrhs][2][max n]
   L.adj = take((size_t)nrhs * 2 * std::max(ns_max, nt_max) * sizeof(double) +
                (size_t)nrhs * p->ncomp * std::max(ns_max, nt_max) * sizeof(double));
+  pfmm::fmm_setup(p);
+  L.fmm = take(p->fmm.bytes);
   L.total = off;
   size_t ncq = (size_t)nrhs * p->ncomp;
   L.stage = off;
@@ -505,7 +515,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
 void pfmm_plan_destroy(pfmm_plan* p) {
   if (!p) return;
   if (p->prof)
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
+    for (int i = 0; i < kPlanEvents; ++i) cudaEventDestroy(p->ev[i]);
   std::free(p->nodes_h);
   std::free(p->gl_h);
   std::free(p->phihat_h);
@@ -541,13 +551,25 @@ pfmm_status pfmm_plan_describe(const pfmm_plan* p, pfmm_plan_desc* d) {
   d->n_gl = p->n_gl; d->nf = p->nf; d->nufft_w = p->nufft_w; d->es_beta = p->es_beta;
   d->nlaunch = p->nlaunch;
   d->npairs = p->npairs;
+  d->near_fmm = p->fmm.on;
+  d->near_order = p->fmm.p;
+  d->near_leaf = p->fmm.nleaf;
+  d->near_theta = p->fmm.theta;
+  return PFMM_OK;
+}
+
+pfmm_status pfmm_near_stats(pfmm_plan* p, const void* workspace, void* stream, int64_t out[5]) {
+  if (!p || !workspace || !out) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
+  if (!p->fmm.on) return fail(PFMM_ERR_INVALID_ARG, "the plan does not use the near-field tree code");
+  cudaError_t e = fmm_stats(p, (const char*)workspace, (cudaStream_t)stream, out);
+  if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "read tree-code statistics: %s", cudaGetErrorString(e));
   return PFMM_OK;
 }
 
 pfmm_status pfmm_profile_enable(pfmm_plan* p, int on) {
   if (!p) return fail(PFMM_ERR_INVALID_ARG, "NULL plan");
   if (on && !p->prof) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kPlanEvents; ++i) {
       cudaError_t e = cudaEventCreate(&p->ev[i]);
       if (e != cudaSuccess) {
         for (int k = 0; k < i; ++k) cudaEventDestroy(p->ev[k]);
@@ -556,7 +578,7 @@ pfmm_status pfmm_profile_enable(pfmm_plan* p, int on) {
     }
     p->prof = true;
   } else if (!on && p->prof) {
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
+    for (int i = 0; i < kPlanEvents; ++i) cudaEventDestroy(p->ev[i]);
     p->prof = false;
   }
   return PFMM_OK;
@@ -571,6 +593,15 @@ pfmm_status pfmm_profile_read(pfmm_plan* p, float* ms, int n) {
     e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
     if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
   }
+  // tree-code sub-phases of the near field: tree, upward pass, traversal and
+  // grouping, downward pass, leaves (events 2, 4, 5, 6, 7, 3)
+  static const int from[5] = {2, 4, 5, 6, 7}, to[5] = {4, 5, 6, 7, 3};
+  for (int i = 3; i < n && i < 8; ++i) {
+    ms[i] = 0.0f;
+    if (!p->near_fmm_ran) continue;
+    e = cudaEventElapsedTime(&ms[i], p->ev[from[i - 3]], p->ev[to[i - 3]]);
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
+  }
   return PFMM_OK;
 }
 
@@ -578,6 +609,13 @@ pfmm_status pfmm_profile_pairs(pfmm_plan* p, const void* workspace, void* stream
   if (!p || !workspace || !pairs) return fail(PFMM_ERR_INVALID_ARG, "NULL argument");
   if (!p->prof) return fail(PFMM_ERR_INVALID_ARG, "profiling not enabled");
   *pairs = (double)p->npairs;
+  if (p->fmm.on) {
+    int64_t st[5];
+    cudaError_t e = fmm_stats(p, (const char*)workspace, (cudaStream_t)stream, st);
+    if (e != cudaSuccess) return fail(PFMM_ERR_CUDA, "read pair count: %s", cudaGetErrorString(e));
+    *pairs = (double)st[3];
+    return PFMM_OK;
+  }
   if (p->opts.kernel != PFMM_MODHELM || p->opts.precision != PFMM_MIXED) return PFMM_OK;
   unsigned long long w = 0;
   cudaError_t e = cudaMemcpyAsync(&w, (const char*)workspace + p->lay.work, sizeof w, cudaMemcpyDeviceToHost,

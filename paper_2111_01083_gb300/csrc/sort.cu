@@ -226,6 +226,32 @@ size_t sort_scratch_bytes(int64_t total, int ncell) {
   return 4 * al256(t * 4) + al256((size_t)256 * rs_blocks(total) * sizeof(int));
 }
 
+int64_t radix_hist_ints(int64_t n) { return (int64_t)256 * rs_blocks(n); }
+
+cudaError_t radix_sort_pairs(uint32_t* ka, int* va, uint32_t* kb, int* vb, int* hist, int64_t n, int bits,
+                             cudaStream_t st, bool* in_b, int* nlaunch) {
+  *in_b = false;
+  if (n <= 0) return cudaSuccess;
+  const int nblk = rs_blocks(n);
+  bool b = false;
+  for (int shift = 0; shift < bits; shift += 8) {
+    k_rs_hist<<<nblk, kRsThreads, 0, st>>>(b ? kb : ka, n, shift, nblk, hist);
+    k_rs_scan<<<1, 1024, 0, st>>>(hist, 256 * nblk);
+    k_rs_scatter<<<nblk, kRsThreads, 0, st>>>(b ? kb : ka, b ? vb : va, b ? ka : kb, b ? va : vb, n, shift, nblk,
+                                              hist);
+    b = !b;
+    if (nlaunch) *nlaunch += 3;
+  }
+  *in_b = b;
+  return cudaGetLastError();
+}
+
+cudaError_t scan_small(int* a, int m, cudaStream_t st) {
+  if (m <= 0) return cudaSuccess;
+  k_rs_scan<<<1, 1024, 0, st>>>(a, m);
+  return cudaGetLastError();
+}
+
 cudaError_t sort_cells(const SortCell* cells, const SortCell* hcells, int ncell, int64_t total, char* scratch,
                        cudaStream_t st, int* nlaunch) {
   if (total <= 0 || ncell <= 0) return cudaSuccess;

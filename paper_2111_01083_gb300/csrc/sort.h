@@ -51,4 +51,15 @@ size_t sort_scratch_bytes(int64_t total, int ncell);
 cudaError_t sort_cells(const SortCell* cells, const SortCell* hcells, int ncell, int64_t total, char* scratch,
                        cudaStream_t st, int* nlaunch);
 
+// Stable LSD radix sort of n (key, value) pairs on the low `bits` bits of the
+// keys, 8 bits per pass.  After an even number of passes the sorted pairs are
+// in (ka, va), after an odd number in (kb, vb); *in_b tells which.  hist:
+// radix_hist_ints(n) ints of scratch.
+int64_t radix_hist_ints(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t* ka, int* va, uint32_t* kb, int* vb, int* hist, int64_t n, int bits,
+                             cudaStream_t st, bool* in_b, int* nlaunch);
+// Exclusive scan of m ints in place by one block of 1024 threads (for m up
+// to a few times 1e5).
+cudaError_t scan_small(int* a, int m, cudaStream_t st);
+
 }  // namespace pfmm

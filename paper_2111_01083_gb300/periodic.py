@@ -29,6 +29,7 @@ _PREC = {"fp64": _lib.PFMM_FP64, "mixed": _lib.PFMM_MIXED}
 _PATH = {"auto": _lib.PFMM_PATH_AUTO, "direct": _lib.PFMM_PATH_DIRECT, "nufft": _lib.PFMM_PATH_NUFFT}
 _PART = {"total": 0, "far": _lib.PFMM_FAR_ONLY, "near": _lib.PFMM_NEAR_ONLY}
 _WE = {"auto": 0, "rotated": _lib.PFMM_WE_ROTATED, "axis": _lib.PFMM_WE_AXIS}
+_NEAR = {"auto": 0, "direct": _lib.PFMM_NEAR_DIRECT, "fmm": _lib.PFMM_NEAR_FMM}
 
 
 def _ptr(t):
@@ -83,7 +84,8 @@ def check_inputs(kernel, nrhs, src, q, trg, out=None, grad=True):
 
 class PeriodicOp:
     def __init__(self, kernel, e1, e2, beta=0.0, tol=1e-6, precision="mixed", path="auto", nufft_w=0, n_gl=0,
-                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False, we="auto"):
+                 nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False, we="auto", near="auto",
+                 near_order=0, near_leaf=0):
         L = _lib.lib()
         o = _lib.Opts()
         o.e1[0], o.e1[1] = float(e1[0]), float(e1[1])
@@ -96,7 +98,9 @@ class PeriodicOp:
         o.nufft_w = int(nufft_w)
         o.n_gl = int(n_gl)
         o.nrhs = int(nrhs)
-        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0) | _WE[we]
+        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0) | _WE[we] | _NEAR[near]
+        o.near_order = int(near_order)
+        o.near_leaf = int(near_leaf)
         self.kernel = kernel
         self.nrhs = int(nrhs)
         self.ns_max, self.nt_max = int(ns_max), int(nt_max)
@@ -191,10 +195,13 @@ class PeriodicOp:
         """Enable per-phase CUDA-event timing inside pfmm_execute."""
         _lib.check(_lib.lib().pfmm_profile_enable(self._h, 1 if on else 0))
 
-    def phase_ms(self):
-        """Milliseconds of [prep, far field, near P2P] of the last execute."""
-        ms = (ctypes.c_float * 3)()
-        _lib.check(_lib.lib().pfmm_profile_read(self._h, ms, 3))
+    def phase_ms(self, sub=False):
+        """Milliseconds of [prep, far field, near field] of the last execute;
+        sub=True appends the tree code's [tree, upward, traversal, downward,
+        leaves] (zeros when the direct P2P ran)."""
+        n = 8 if sub else 3
+        ms = (ctypes.c_float * n)()
+        _lib.check(_lib.lib().pfmm_profile_read(self._h, ms, n))
         return list(ms)
 
     def pairs(self, stream=None):
@@ -206,6 +213,17 @@ class PeriodicOp:
         v = ctypes.c_double()
         _lib.check(_lib.lib().pfmm_profile_pairs(self._h, _ptr(ws), ctypes.c_void_p(st), ctypes.byref(v)))
         return float(v.value)
+
+    def near_stats(self, stream=None):
+        """Tree-code statistics of the last execute (pfmm_near_stats; synchronises):
+        boxes, M2L interactions, directly summed leaf pairs, directly summed
+        point pairs (while profiling), overflow bits."""
+        import torch
+        ws = self.workspace()
+        st = stream if stream is not None else torch.cuda.current_stream(ws.device).cuda_stream
+        out = (ctypes.c_int64 * 5)()
+        _lib.check(_lib.lib().pfmm_near_stats(self._h, _ptr(ws), ctypes.c_void_p(st), out))
+        return dict(boxes=out[0], m2l=out[1], p2p_leaf_pairs=out[2], p2p_pairs=out[3], overflow=out[4])
 
     def status(self, stream=None):
         """Synchronise and return the device status of the last execute (raises on error)."""

@@ -102,7 +102,7 @@ def test_west_east_direction_flags(L):
     assert (skew["m0"], skew["we_rotated"]) == (1, 0)
 
 
-@pytest.mark.parametrize("kw", [dict(flags=96), dict(flags=128), dict(flags=48)])
+@pytest.mark.parametrize("kw", [dict(flags=96), dict(flags=512), dict(flags=48)])
 def test_west_east_flag_errors(L, kw):
     from paper_2111_01083_gb300 import _lib
     o = _lib.Opts()
@@ -261,3 +261,51 @@ def test_binding_validates_tensors():
     for kernel, qq, trg, out in bad:
         with pytest.raises(ValueError):
             check_inputs(kernel, 3, src, qq, trg, out)
+
+
+def test_near_field_mode_selection(L):
+    """The tree code runs the near field of large mixed Laplace/Stokes plans by
+    default; the flags force either sum; other kernels and FP64 stay direct."""
+    big = dict(ns_max=100000, nt_max=100000)
+    assert _op(**big).describe()["near_fmm"] == 1
+    assert _op(kernel="stokes", **big).describe()["near_fmm"] == 1
+    assert _op(**big, near="direct").describe()["near_fmm"] == 0
+    assert _op(**big, precision="fp64").describe()["near_fmm"] == 0
+    assert _op(kernel="modhelm", beta=1.0, **big).describe()["near_fmm"] == 0
+    # small problems: direct unless forced
+    assert _op().describe()["near_fmm"] == 0
+    d = _op(near="fmm").describe()
+    assert d["near_fmm"] == 1 and d["near_theta"] == 0.5 and d["near_leaf"] == 48
+    # expansion terms from the tolerance (theta^p <= tol / 10), rounded up to a compiled order
+    assert _op(near="fmm", tol=1e-6).describe()["near_order"] == 24
+    assert _op(near="fmm", tol=1e-2).describe()["near_order"] == 12
+    assert _op(near="fmm", near_order=14).describe()["near_order"] == 16
+    assert _op(near="fmm", near_leaf=16).describe()["near_leaf"] == 16
+    # the tree code's workspace only when it runs
+    assert _op(near="fmm").ws_bytes > _op(near="direct").ws_bytes
+
+
+@pytest.mark.parametrize("kw", [dict(near_order=7), dict(near_order=33), dict(near_leaf=4), dict(near_leaf=2000)])
+def test_near_field_option_errors(L, kw):
+    from paper_2111_01083_gb300 import _lib
+    with pytest.raises(_lib.PfmmError) as ei:
+        _op(near="fmm", **kw)
+    assert ei.value.code == 1
+
+
+def test_near_field_flags_exclusive(L):
+    from paper_2111_01083_gb300 import _lib
+    o = _lib.Opts()
+    o.e1[0], o.e2[1] = 1.0, 1.0
+    o.tol, o.precision, o.nrhs = 1e-6, 1, 1
+    o.flags = _lib.PFMM_NEAR_DIRECT | _lib.PFMM_NEAR_FMM
+    h = ctypes.c_void_p()
+    assert L.pfmm_plan_create(ctypes.byref(o), 10, 10, ctypes.byref(h)) == 1
+    o.flags = 512
+    assert L.pfmm_plan_create(ctypes.byref(o), 10, 10, ctypes.byref(h)) == 1
+
+
+def test_near_stats_requires_tree_code(L):
+    op = _op(near="direct")
+    out = (ctypes.c_int64 * 5)()
+    assert L.pfmm_near_stats(op._h, ctypes.c_void_p(256), None, out) == 1
