@@ -890,8 +890,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_fmm_leaf(FmmArgs a) {
                 const float dy = (tyh - s.z) + (tyl - s.w);
                 const float r2 = dx * dx + dy * dy;
                 if (r2 > 0.f) {
-                  const float lg = log2f(r2);
-                  const float inv = 1.0f / r2;
+                  const float lg = __log2f(r2);
+                  const float inv = __fdividef(1.0f, r2);
                   if (KER == PFMM_LAPLACE) {
                     const float qq = s_q[0][jj];
                     f0 += qq * lg;
@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_fmm_fallback(FmmArgs a) {
               const float dy = (tyh - s.z) + (tyl - s.w);
               const float r2 = dx * dx + dy * dy;
               if (r2 > 0.f) {
-                const float lg = log2f(r2), inv = 1.0f / r2;
+                const float lg = __log2f(r2), inv = __fdividef(1.0f, r2);
                 if (KER == PFMM_LAPLACE) {
                   const float qq = s_q[0][jj];
                   f0 += qq * lg;

@@ -72,14 +72,15 @@ __device__ __forceinline__ void grid_pos(T x, int U, const NufftArgs& a, int* i,
   }
 }
 
-// ES kernel values at the w grid points around u = i + f (grid units).
-// Returns l0, the first grid index (not reduced mod nf); z_k = (u - (l0 + k)) / (w/2).
-template <typename T>
+// ES kernel values at the w grid points around u = i + f (grid units); WA is
+// the array length (a compile-time bound >= w).  Returns l0, the first grid
+// index (not reduced mod nf); z_k = (u - (l0 + k)) / (w/2).
+template <typename T, int WA>
 __device__ __forceinline__ int es_weights(int i, T f, int w, T beta, T* ker) {
   const T half = T(0.5) * w;
   const int c = (int)ceil(f - half);
-#pragma unroll 16
-  for (int k = 0; k < 16; ++k) {
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {
     if (k < w) {
       const T z = (f - (T)(c + k)) / half;
       const T s = T(1) - z * z;
@@ -89,75 +90,94 @@ __device__ __forceinline__ int es_weights(int i, T f, int w, T beta, T* ker) {
   return i + c;
 }
 
-// Barycentric interpolation weights gamma(y, n) (second form).
-template <typename T>
+// Barycentric interpolation weights gamma(y, n) (second form); GA is the
+// array length (a compile-time bound >= n_gl).
+template <typename T, int GA>
 __device__ __forceinline__ void bary(T y, const double* gl, int n_gl, T* g) {
   T sum = T(0);
   int hit = -1;
-  for (int n = 0; n < n_gl; ++n) {
-    const T dy = y - (T)gl[2 * n];
-    if (dy == T(0)) hit = n;
-    g[n] = (T)gl[2 * n + 1] / (dy == T(0) ? T(1) : dy);
-    sum += g[n];
-  }
-  if (hit >= 0) {
-    for (int n = 0; n < n_gl; ++n) g[n] = (n == hit) ? T(1) : T(0);
-    return;
+#pragma unroll
+  for (int n = 0; n < GA; ++n) {
+    if (n < n_gl) {
+      const T dy = y - (T)gl[2 * n];
+      if (dy == T(0)) hit = n;
+      g[n] = (T)gl[2 * n + 1] / (dy == T(0) ? T(1) : dy);
+      sum += g[n];
+    }
   }
   const T inv = T(1) / sum;
-  for (int n = 0; n < n_gl; ++n) g[n] *= inv;
+#pragma unroll
+  for (int n = 0; n < GA; ++n)
+    if (n < n_gl) g[n] = hit >= 0 ? (n == hit ? T(1) : T(0)) : g[n] * inv;
 }
 
 // ---------------------------------------------------------------------------
-// K4: anterpolation + spreading.  One block per source chunk; the block
-// spreads into a shared-memory grid [n_gl][nf] for one charge vector at a
-// time (rhs r, channel c) and adds it to the global FP64 grid
-// [nrhs][nch][n_gl][nf].  Channels: scalar q; Stokes f_x, f_y, y' f_x, y' f_y.
+// K4: anterpolation + spreading.  One block per source chunk.  The charge
+// vectors v = (rhs r, channel c) are spread in groups of `vg` that share one
+// shared-memory grid each ([vg][n_gl][nf] FP32 on the mixed path): per point
+// the grid position, the w ES values and the n_gl barycentric weights are
+// computed once per group and serve every vector of it; each group is then
+// added to the global FP64 grid [nrhs][nch][n_gl][nf].  Channels: scalar q;
+// Stokes f_x, f_y, y' f_x, y' f_y; modified Stokes f_x, f_y.  W and NGL are
+// the ES width and the number of GL lines when known at compile time (the
+// weight arrays then stay in registers), 0 for the general case.
 // ---------------------------------------------------------------------------
 constexpr int kSpreadThreads = 256;
 
-template <typename T>
+template <typename T, int W, int NGL>
 __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, int chunk, const T* __restrict__ sx,
                                                                  const T* __restrict__ sy, const int* __restrict__ sU,
                                                                  const T* __restrict__ qv, double* __restrict__ grid,
-                                                                 int use_smem) {
+                                                                 int use_smem, int vg) {
   extern __shared__ unsigned char smem_raw[];
-  T* sg = reinterpret_cast<T*>(smem_raw);  // [n_gl][nf] when use_smem
-  const int ngrid = a.n_gl * a.nf;
+  T* sg = reinterpret_cast<T*>(smem_raw);  // [vg][n_gl][nf] when use_smem
+  constexpr int WA = W ? W : 16, GA = NGL ? NGL : 32;
+  const int w = W ? W : a.w, ngl = NGL ? NGL : a.n_gl;
+  const int ngrid = ngl * a.nf;
   const int j0 = blockIdx.x * chunk, j1 = min(a.ns, j0 + chunk);
   const T beta = (T)a.es_beta;
   const int ncomp = a.nch >= 2 ? 2 : 1;  // Stokes (4 channels) and modified Stokes (2) spread forces
-  for (int v = 0; v < a.nrhs * a.nch; ++v) {
-    const int r = v / a.nch, c = v % a.nch;
-    const T* qrow = qv + ((size_t)r * ncomp + (c & 1)) * a.ns;
-    const bool ymul = c >= 2;
+  const int nv = a.nrhs * a.nch;
+  for (int v0 = 0; v0 < nv; v0 += vg) {
+    const int nvg = min(vg, nv - v0);
     if (use_smem)
-      for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) sg[k] = T(0);
+      for (int k = threadIdx.x; k < nvg * ngrid; k += kSpreadThreads) sg[k] = T(0);
     __syncthreads();
     for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
       const T x = sx[j], y = sy[j];
-      const T q = ymul ? qrow[j] * y : qrow[j];
       int gi;
-      T gf, ker[16], gam[32];
+      T gf, ker[WA], gam[GA];
       grid_pos(x, sU[j], a, &gi, &gf);
-      const int l0 = es_weights(gi, gf, a.w, beta, ker);
-      bary(y, a.gl, a.n_gl, gam);
-      double* gr = grid + (size_t)v * ngrid;
-      for (int n = 0; n < a.n_gl; ++n) {
-        const T gq = gam[n] * q;
-        for (int k = 0; k < a.w; ++k) {
-          const int l = (l0 + k) & (a.nf - 1);
-          if (use_smem)
-            atomicAdd(sg + n * a.nf + l, gq * ker[k]);
-          else
-            atomicAdd(gr + n * a.nf + l, (double)(gq * ker[k]));
+      const int l0 = es_weights<T, WA>(gi, gf, w, beta, ker);
+      bary<T, GA>(y, a.gl, ngl, gam);
+      for (int vv = 0; vv < nvg; ++vv) {
+        const int v = v0 + vv, r = v / a.nch, c = v % a.nch;
+        const T q0 = qv[((size_t)r * ncomp + (c & 1)) * a.ns + j];
+        const T q = c >= 2 ? q0 * y : q0;
+        T* sgv = sg + (size_t)vv * ngrid;
+        double* gr = grid + (size_t)v * ngrid;
+#pragma unroll
+        for (int n = 0; n < GA; ++n) {
+          if (n < ngl) {
+            const T gq = gam[n] * q;
+#pragma unroll
+            for (int k = 0; k < WA; ++k) {
+              if (k < w) {
+                const int l = (l0 + k) & (a.nf - 1);
+                if (use_smem)
+                  atomicAdd(sgv + n * a.nf + l, gq * ker[k]);
+                else
+                  atomicAdd(gr + n * a.nf + l, (double)(gq * ker[k]));
+              }
+            }
+          }
         }
       }
     }
     __syncthreads();
     if (use_smem) {
-      double* g = grid + (size_t)v * ngrid;
-      for (int k = threadIdx.x; k < ngrid; k += kSpreadThreads) {
+      double* g = grid + (size_t)v0 * ngrid;
+      for (int k = threadIdx.x; k < nvg * ngrid; k += kSpreadThreads) {
         const T val = sg[k];
         if (val != T(0)) atomicAdd(g + k, (double)val);
       }
@@ -355,31 +375,42 @@ __global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec) {
 
 // Interpolation at targets + barycentric combination over lines; adds the
 // south/north field to pot / grad (input frame).  The spectra are FP64; the
-// mixed path interpolates in FP32 and sums over lines with compensation.
-template <typename T, int KER>
+// mixed path interpolates in FP32 and sums over lines with compensation.  The
+// ES and barycentric weights are computed once per target and serve every
+// right-hand side; W, NGL as for the spreading kernel.
+template <typename T, int KER, int W, int NGL>
 __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, const T* __restrict__ ty,
                                const int* __restrict__ tU, const double2* __restrict__ spec, double* __restrict__ pot,
                                double* __restrict__ grad) {
+  constexpr int WA = W ? W : 16, GA = NGL ? NGL : 32;
+  const int w = W ? W : a.w, ngl = NGL ? NGL : a.n_gl;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= a.nt) return;
   const T x = tx[l], y = ty[l];
   int gi;
-  T gf, ker[16], gam[32];
+  T gf, ker[WA], gam[GA];
   grid_pos(x, tU[l], a, &gi, &gf);
-  const int l0 = es_weights(gi, gf, a.w, (T)a.es_beta, ker);
-  bary(y, a.gl, a.n_gl, gam);
+  const int l0 = es_weights<T, WA>(gi, gf, w, (T)a.es_beta, ker);
+  bary<T, GA>(y, a.gl, ngl, gam);
+  int li[WA];
+#pragma unroll
+  for (int k = 0; k < WA; ++k) li[k] = (l0 + k) & (a.nf - 1);
   const double* R = g.rot;
   for (int r = 0; r < a.nrhs; ++r) {
     const double2* base = spec + (size_t)r * a.npk * a.nf;
     if (KER == PFMM_MSTOKES) {
       dm::KSum<T> ux, uy;
-      for (int n = 0; n < a.n_gl; ++n) {
+#pragma unroll 1
+      for (int n = 0; n < ngl; ++n) {
         const double2* ra = base + (size_t)n * a.nf;
         T sx = 0, sy = 0;
-        for (int k = 0; k < a.w; ++k) {
-          const double2 va = ra[(l0 + k) & (a.nf - 1)];
-          sx += ker[k] * (T)va.x;
-          sy += ker[k] * (T)va.y;
+#pragma unroll
+        for (int k = 0; k < WA; ++k) {
+          if (k < w) {
+            const double2 va = ra[li[k]];
+            sx += ker[k] * (T)va.x;
+            sy += ker[k] * (T)va.y;
+          }
         }
         ux.add(gam[n] * sx);
         uy.add(gam[n] * sy);
@@ -391,17 +422,20 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
     }
     if (KER == PFMM_STOKES) {
       dm::KSum<T> ux, uy;
-      for (int n = 0; n < a.n_gl; ++n) {
+#pragma unroll 1
+      for (int n = 0; n < ngl; ++n) {
         const double2* ra = base + (size_t)n * a.nf;
-        const double2* rb = base + (size_t)(a.n_gl + n) * a.nf;
+        const double2* rb = base + (size_t)(ngl + n) * a.nf;
         T sax = 0, say = 0, sbx = 0, sby = 0;
-        for (int k = 0; k < a.w; ++k) {
-          const int li = (l0 + k) & (a.nf - 1);
-          const double2 va = ra[li], vb = rb[li];
-          sax += ker[k] * (T)va.x;
-          say += ker[k] * (T)va.y;
-          sbx += ker[k] * (T)vb.x;
-          sby += ker[k] * (T)vb.y;
+#pragma unroll
+        for (int k = 0; k < WA; ++k) {
+          if (k < w) {
+            const double2 va = ra[li[k]], vb = rb[li[k]];
+            sax += ker[k] * (T)va.x;
+            say += ker[k] * (T)va.y;
+            sbx += ker[k] * (T)vb.x;
+            sby += ker[k] * (T)vb.y;
+          }
         }
         ux.add(gam[n] * (sax + y * sbx));
         uy.add(gam[n] * (say + y * sby));
@@ -412,18 +446,21 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
       continue;
     }
     dm::KSum<T> p, gx, gy;
-    for (int n = 0; n < a.n_gl; ++n) {
+#pragma unroll 1
+    for (int n = 0; n < ngl; ++n) {
       const double2* row = base + (size_t)n * a.nf;
-      const double2* rowx = base + (size_t)(a.n_gl + n / 2) * a.nf;
+      const double2* rowx = base + (size_t)(ngl + n / 2) * a.nf;
       T sp = 0, sy = 0, sx = 0;
-      for (int k = 0; k < a.w; ++k) {
-        const int li = (l0 + k) & (a.nf - 1);
-        const double2 v = row[li];
-        sp += ker[k] * (T)v.x;
-        sy += ker[k] * (T)v.y;
-        if (grad) {
-          const double2 vx = rowx[li];
-          sx += ker[k] * (T)((n & 1) ? vx.y : vx.x);
+#pragma unroll
+      for (int k = 0; k < WA; ++k) {
+        if (k < w) {
+          const double2 v = row[li[k]];
+          sp += ker[k] * (T)v.x;
+          sy += ker[k] * (T)v.y;
+          if (grad) {
+            const double2 vx = rowx[li[k]];
+            sx += ker[k] * (T)((n & 1) ? vx.y : vx.x);
+          }
         }
       }
       p.add(gam[n] * sp);
@@ -447,7 +484,7 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
 // execute from several host threads with different sizes.
 static cudaError_t raise_smem(const void* fn, int slot, size_t bytes) {
   static std::mutex mu;
-  static int done[32][4] = {};
+  static int done[32][16] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
   std::lock_guard<std::mutex> lock(mu);
@@ -457,6 +494,37 @@ static cudaError_t raise_smem(const void* fn, int slot, size_t bytes) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
   if (e == cudaSuccess && cached) done[dev][slot] = want;
   return e;
+}
+
+// (ES width, GL lines) compiled with the weight arrays in registers: the
+// defaults at tol 1e-6, 1e-10 and 1e-12; other pairs take the general kernels.
+static int nufft_spec(int w, int n_gl) {
+  if (w == 8 && n_gl == 8) return 1;
+  if (w == 12 && n_gl == 16) return 2;
+  if (w == 14 && n_gl == 16) return 3;
+  return 0;
+}
+
+template <typename T, int W, int NGL>
+static cudaError_t spread_t(const NufftArgs& a, int nchunk, int chunk, const T* sx, const T* sy, const int* sU,
+                            const T* qv, double* grid, int use_smem, int vg, size_t smem, int slot, cudaStream_t st) {
+  if (smem > 48 * 1024) {
+    cudaError_t e = raise_smem((const void*)k_nufft_spread<T, W, NGL>, slot, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_nufft_spread<T, W, NGL><<<nchunk, kSpreadThreads, smem, st>>>(a, chunk, sx, sy, sU, qv, grid, use_smem, vg);
+  return cudaGetLastError();
+}
+
+template <typename T, int KER>
+static void interp_k(int spec, int ni, const NufftArgs& a, const Geom& g, const T* tx, const T* ty, const int* tU,
+                     const double2* sp, double* pot, double* grad, cudaStream_t st) {
+  switch (spec) {
+    case 1: k_nufft_interp<T, KER, 8, 8><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
+    case 2: k_nufft_interp<T, KER, 12, 16><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
+    case 3: k_nufft_interp<T, KER, 14, 16><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
+    default: k_nufft_interp<T, KER, 0, 0><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -507,20 +575,28 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   int nchunk = std::max(1, std::min((int)((ns + 255) / 256), 2 * 152));
   int chunk = (int)((ns + nchunk - 1) / nchunk);
   nchunk = (int)((ns + chunk - 1) / chunk);
-  size_t sm_spread = (size_t)a.n_gl * a.nf * sizeof(T);
-  const int use_smem = sm_spread <= 96 * 1024;
-  if (!use_smem) sm_spread = 0;
-  if (sm_spread > 48 * 1024) {
-    e = raise_smem((const void*)k_nufft_spread<T>, sizeof(T) == 4 ? 0 : 1, sm_spread);
-    if (e != cudaSuccess) return e;
-  }
+  // one shared grid per charge vector of a group; as many vectors per group
+  // as fit in ~100 KB, so that the weights are computed once per group
+  const size_t per_v = (size_t)a.n_gl * a.nf * sizeof(T);
+  const int use_smem = per_v <= 96 * 1024;
+  const int nv = a.nrhs * a.nch;
+  const int vg = use_smem ? (int)std::max<size_t>(1, std::min<size_t>(nv, (100 * 1024) / per_v)) : nv;
+  const size_t sm_spread = use_smem ? vg * per_v : 0;
   const int* sU = (const int*)(ws + L.srcU);
-  k_nufft_spread<T><<<nchunk, kSpreadThreads, sm_spread, st>>>(a, chunk, sx, sx + ns, sU, qv, grid, use_smem);
+  const int wspec = nufft_spec(a.w, a.n_gl);
+  const int slot = (sizeof(T) == 4 ? 0 : 4) + wspec;
+  switch (wspec) {
+    case 1: e = spread_t<T, 8, 8>(a, nchunk, chunk, sx, sx + ns, sU, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    case 2: e = spread_t<T, 12, 16>(a, nchunk, chunk, sx, sx + ns, sU, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    case 3: e = spread_t<T, 14, 16>(a, nchunk, chunk, sx, sx + ns, sU, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    default: e = spread_t<T, 0, 0>(a, nchunk, chunk, sx, sx + ns, sU, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+  }
+  if (e != cudaSuccess) return e;
   const int fth = std::min(512, std::max(32, a.nf / 2));
   const size_t sm_fft = (size_t)a.nf * sizeof(double2);
   if (sm_fft > 48 * 1024) {
-    e = raise_smem((const void*)k_nufft_fwd, 2, sm_fft);
-    if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 3, sm_fft);
+    e = raise_smem((const void*)k_nufft_fwd, 8, sm_fft);
+    if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 9, sm_fft);
     if (e != cudaSuccess) return e;
   }
   k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
@@ -534,22 +610,22 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
     case PFMM_LAPLACE:
       k_nufft_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, PFMM_LAPLACE><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, grad);
+      interp_k<T, PFMM_LAPLACE>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MODHELM:
       k_nufft_modes<PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, PFMM_MODHELM><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, grad);
+      interp_k<T, PFMM_MODHELM>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MSTOKES:
       k_nufft_modes<PFMM_MSTOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, PFMM_MSTOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, nullptr);
+      interp_k<T, PFMM_MSTOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
     default:
       k_nufft_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
       k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
-      k_nufft_interp<T, PFMM_STOKES><<<ni, 128, 0, st>>>(a, p->geom, tx, tx + nt, tU, spec, pot, nullptr);
+      interp_k<T, PFMM_STOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
   }
   g_launches += 5;
