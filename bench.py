@@ -78,6 +78,13 @@ def peak_clock_mhz(clocks):
 #                       per (t, s) nrhs FMAs; with K1: + fit (6), scaling (2),
 #                       two sums (2) per pair and 2 nrhs more FMAs per (t, s)
 def p2p_work(kernel, nrhs, grad, nimg=9):
+    # tree-code leaves (direct sums of neighbouring leaves, one pair per image):
+    #   Laplace: dx, dy from hi/lo parts (6), r^2 (2), q lg2, q dx/r^2, q dy/r^2 (5) = 13; lg2 + rcp
+    #   Stokes:  dx, dy (6), r^2 (2), d.f / r^2 (3), the two components (6) = 17; lg2 + rcp
+    if kernel == "laplace_leaf":
+        return (13.0, 2.0)
+    if kernel == "stokes_leaf":
+        return (17.0, 2.0)
     if kernel == "laplace":
         return (8.0 + 3.0 / nimg, 1.0 + 1.0 / nimg) if grad else (6.0 + 1.0 / nimg, 1.0 / nimg)
     if kernel == "stokes":
@@ -711,7 +718,7 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    step_ms, p2p_ms, far_ms = [], [], []
+    step_ms, p2p_ms, far_ms, sub_ms = [], [], [], []
     launches = 0
     for _ in range(args.steps):
         flush.zero_()
@@ -722,9 +729,10 @@ def main():
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        ph = op.phase_ms()
+        ph = op.phase_ms(sub=True)
         far_ms.append(ph[1])
         p2p_ms.append(ph[2])
+        sub_ms.append(ph[3:])
         launches += op.describe()["nlaunch"]
     torch.cuda.synchronize()
     if dist:
@@ -784,16 +792,28 @@ def main():
         if dist:
             dist.destroy_process_group()
         return 0
-    # roofline of the dominant kernel (near-image P2P): pairs per launch / event time
+    # roofline of the dominant kernel: pairs per launch / event time
     p2p = sum(p2p_ms) / len(p2p_ms)
     nimg = 3 if singly else 3 * (2 * desc["m0"] + 1)
-    kname = {"mstokes": "k_p2p_ms", "modhelm": "k_p2p_mixed_mh"}.get(kernel, "k_p2p_mixed")
-    # modified Helmholtz skips (target block, source tile, image) triples beyond
-    # beta r = 50: its roofline counts the pairs it evaluates
-    npairs = op.pairs() if kernel == "modhelm" else desc["npairs"]
-    roof = p2p_roofline(kernel, nrhs, grad, npairs, p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
-                        device_sms(dev), clocks,
-                        traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", f"{kname}_{args.workload}"), nimg=nimg)
+    near_sub, near_stats = None, None
+    if desc["near_fmm"]:
+        names = ["tree", "upward", "traversal", "downward", "leaves"]
+        near_sub = {k: sum(x[i] for x in sub_ms) / len(sub_ms) for i, k in enumerate(names)}
+        near_stats = op.near_stats()
+        # the tree code's leaf kernel (L2P + direct sums of neighbouring leaves);
+        # its pairs are the ones it sums directly (counted while profiling)
+        npairs = op.pairs()
+        roof = p2p_roofline(f"{kernel}_leaf", nrhs, grad, npairs, near_sub["leaves"], ms,
+                            f"k_fmm_leaf (tree-code leaves: L2P + direct sums of neighbouring leaves, {nimg} images)",
+                            device_sms(dev), clocks, None, nimg=nimg)
+    else:
+        kname = {"mstokes": "k_p2p_ms", "modhelm": "k_p2p_mixed_mh"}.get(kernel, "k_p2p_mixed")
+        # modified Helmholtz skips (target block, source tile, image) triples beyond
+        # beta r = 50: its roofline counts the pairs it evaluates
+        npairs = op.pairs() if kernel == "modhelm" else desc["npairs"]
+        roof = p2p_roofline(kernel, nrhs, grad, npairs, p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
+                            device_sms(dev), clocks,
+                            traffic_for("paper_2111_01083_gb300/csrc/p2p.cu", f"{kname}_{args.workload}"), nimg=nimg)
     cpu = None
     if world == 1 and not args.no_cpu and args.scale == 1.0:
         try:
@@ -831,7 +851,10 @@ def main():
                    "periodicity": "singly (e1)" if singly else "doubly",
                    "west_east": "rotated (e2-perp)" if desc["we_rotated"] else "axis (e1)",
                    "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
-        "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_p2p": p2p},
+        "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_field": p2p},
+        "near_field": {"method": "tree code" if desc["near_fmm"] else "direct P2P", "phases_ms": near_sub,
+                       "stats": near_stats, "order": desc["near_order"] if desc["near_fmm"] else None,
+                       "leaf": desc["near_leaf"] if desc["near_fmm"] else None},
         "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         "e2e": {"value": job_value(world, ns + nt, e2e_s), "unit": "targets+sources/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "pfmm_execute_host (pinned host buffers)"},

@@ -555,6 +555,9 @@ __global__ void __launch_bounds__(32 * kUpWarps) k_fmm_up(FmmArgs a) {
     if (is_source(a, X)) p2m<P, KER>(a, X, box_scale(r, a.half[X]), lane);
     int cur = X;
     for (;;) {
+      // every lane's writes of this box (radius, expansion) before lane 0's
+      // signal to the parent: warp barrier, then a device-scope fence
+      __syncwarp();
       __threadfence();
       const int parent = a.par[cur];
       if (parent < 0) break;
