@@ -509,7 +509,9 @@ def time_batch(beta, args, dist, dev, local, scale=1.0):
                                     "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
                                     "pairs = those evaluated: triples beyond beta r = 50 are skipped)", sms, clocks),
            "clocks": clocks, "gpu_launches_per_step": nlaunch, "n_sources_total": ns}
-    return rec, dict(S=S, Q=Q, S_h=S_h, Q_h=Q_h, graph=graph, out=out, ns=ns, counts=counts)
+    # the operator owns the graph's workspace and phase events: it must live as
+    # long as the graph is replayed
+    return rec, dict(S=S, Q=Q, S_h=S_h, Q_h=Q_h, graph=graph, out=out, ns=ns, counts=counts, op=op)
 
 
 def run_batch(args, rank, world, local):

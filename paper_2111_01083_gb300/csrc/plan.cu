@@ -146,7 +146,13 @@ void set_we_frame(Geom* g, bool rotated) {
 // where exp(-kappa' x_min') < tol/10 with x_min' the smallest scaled gap
 // between a point and a far image column: (m0 d - 2|xi|)/d on the axis,
 // m0 d c / d rotated.
-void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vector<double>& nodes) {
+// nsrc: sources the plan admits.  For the modified Helmholtz decay the
+// truncation and the decision to drop the whole west/east part use the bound
+// per unit charge times sqrt(nsrc): the dropped field of nsrc random-sign
+// charges grows like their l2 norm, while the short-range potential it is
+// compared with does not (a per-unit-charge tol/10 left 4e-6 relative error
+// on a 4.7e4-point cell at beta = 10).
+void we_quadrature(const Geom& g, int kernel, double beta, double tol, double nsrc, std::vector<double>& nodes) {
   nodes.clear();
   // largest lambda-frequency of the integrand, over d: axis: |y - y'| < eta
   // plus the row shifts +-eta (eta alone for the singly periodic row);
@@ -157,7 +163,8 @@ void we_quadrature(const Geom& g, int kernel, double beta, double tol, std::vect
   const double pw = yspan > 2.0 ? 4.0 / yspan : 2.0;
   double xmin = g.we_rot ? g.m0 * g.wdx / g.d : (g.m0 * g.d - 2.0 * std::fabs(g.xi)) / g.d;
   double bt = (kernel == PFMM_MODHELM) ? beta * g.d : 0.0;
-  double top = std::log(10.0 / tol) / xmin;
+  const double tol_t = kernel == PFMM_MODHELM ? tol / std::sqrt(std::max(1.0, nsrc)) : tol;
+  double top = std::log(10.0 / tol_t) / xmin;
   if (top <= bt) return;
   double lmax = std::sqrt(top * top - bt * bt);
   int npts = tol >= 1e-7 ? 8 : (tol >= 1e-11 ? 12 : 16);
@@ -354,13 +361,17 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   // moment term -(1/(2 d eta)) y sum q y' (Eq. phis3, Eq. pss0) added separately.
   int mode0 = (o->kernel == PFMM_MODHELM && !p1) ? 1 : 0;
   if (o->kernel == PFMM_MODHELM && !p1) {
+    // drop threshold: the per-unit-charge bound times sqrt(ns_max) (see
+    // we_quadrature: the dropped field of many charges grows like their l2
+    // norm, the short-range potential does not)
+    const double eps_drop = eps / std::sqrt(std::max<double>(1.0, (double)ns_max));
     auto bound = [&](int m) {
       double al = 2 * M_PI * m / g.d, chi = std::sqrt(al * al + o->beta * o->beta);
       double e = std::exp(-chi * g.eta);
       return e / (g.d * chi * (1 - e));
     };
-    while (M >= 1 && bound(M) < eps) --M;
-    if (bound(0) < eps) { mode0 = 0; M = 0; }
+    while (M >= 1 && bound(M) < eps_drop) --M;
+    if (bound(0) < eps_drop) { mode0 = 0; M = 0; }
   }
   // modified Stokes (Theorem south_thm_ms): the beta family has an m = 0 term
   // (its block [[beta, 0], [0, 0]]); the Laplace family has none (each image
@@ -382,14 +393,14 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   std::vector<double> nodes, nodes2;
   // the modified Stokes beta family integrates in kappa = sqrt(lambda^2 + beta^2)
   // like modified Helmholtz, the Laplace family in |lambda| like Laplace
-  we_quadrature(g, ms ? PFMM_MODHELM : o->kernel, f.beta, o->tol, nodes);
+  we_quadrature(g, ms ? PFMM_MODHELM : o->kernel, f.beta, o->tol, (double)ns_max, nodes);
   f.Nq = (int)(nodes.size() / 2);
   f.nterm = 2 * f.nsn + 2 * f.Nq;
   p->far2 = f;
   p->far2.nterm = 0;
   p->far2.Nq = 0;
   if (ms) {
-    we_quadrature(g, PFMM_LAPLACE, 0.0, o->tol, nodes2);
+    we_quadrature(g, PFMM_LAPLACE, 0.0, o->tol, (double)ns_max, nodes2);
     Far& f2 = p->far2;
     f2.msfam = 1;
     f2.mode0 = 0;
