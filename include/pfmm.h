@@ -106,7 +106,7 @@ enum {
                                direction would need m0 = 2.  Both: PFMM_ERR_INVALID_ARG.
                                The singly periodic operator always uses the axis. */
   PFMM_NEAR_DIRECT = 128,  /* near-image sum by the direct P2P over all pairs            */
-  PFMM_NEAR_FMM = 256      /* near-image sum by the tree code (the paper evaluates the
+  PFMM_NEAR_FMM = 256,     /* near-image sum by the tree code (the paper evaluates the
                                near field with an FMM, Sec. 7): one quadtree of the unit
                                cell's sources, its image copies shifted by l (sharing the
                                unit cell's expansions), one of the targets; complex
@@ -117,6 +117,13 @@ enum {
                                precision allow it and ns * nt * images >= 2e9, else the
                                direct P2P.  Both: PFMM_ERR_INVALID_ARG.  The FMM flag with
                                another kernel or FP64 selects the direct P2P. */
+  PFMM_DETERMINISTIC = 512 /* bit-identical results for identical inputs: every cross-block
+                               sum (moments, coefficient formation) goes through per-block
+                               partials added in a fixed order instead of atomics, the P2P
+                               gives each output one addition, the far field takes the
+                               direct path and the near field the direct P2P (with NUFFT or
+                               NEAR_FMM: PFMM_ERR_INVALID_ARG).  Single-cell calls only (a
+                               batch refuses it).  Not in the paper. */
 };
 
 typedef enum {
@@ -145,7 +152,7 @@ typedef struct {
   unsigned flags;       /* OR of PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD,
                            PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC,
                            PFMM_WE_ROTATED, PFMM_WE_AXIS, PFMM_NEAR_DIRECT,
-                           PFMM_NEAR_FMM (see the enum above) */
+                           PFMM_NEAR_FMM, PFMM_DETERMINISTIC (see the enum above) */
   int near_order;       /* tree-code expansion terms p (8..32, rounded up to 12, 16, 20,
                            24 or 32); 0 = from tol: theta^p <= tol / 10 */
   int near_leaf;        /* tree code: a box with more points is split (8..1024); 0 = 48 */

@@ -15,7 +15,7 @@ PFMM_FP64, PFMM_MIXED = 0, 1
 PFMM_PATH_AUTO, PFMM_PATH_DIRECT, PFMM_PATH_NUFFT = 0, 1, 2
 PFMM_FAR_ONLY, PFMM_NEAR_ONLY, PFMM_NO_GRAD, PFMM_PROJECT_NEUTRAL, PFMM_SINGLY_PERIODIC = 1, 2, 4, 8, 16
 PFMM_WE_ROTATED, PFMM_WE_AXIS = 32, 64
-PFMM_NEAR_DIRECT, PFMM_NEAR_FMM = 128, 256
+PFMM_NEAR_DIRECT, PFMM_NEAR_FMM, PFMM_DETERMINISTIC = 128, 256, 512
 
 STATUS = {0: "PFMM_OK", 1: "PFMM_ERR_INVALID_ARG", 2: "PFMM_ERR_LATTICE", 3: "PFMM_ERR_NOT_NEUTRAL",
           4: "PFMM_ERR_TOLERANCE", 5: "PFMM_ERR_WORKSPACE", 6: "PFMM_ERR_CUDA", 7: "PFMM_ERR_NONFINITE",

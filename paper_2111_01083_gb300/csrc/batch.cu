@@ -74,6 +74,8 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
       return set_error(PFMM_ERR_INVALID_ARG, "batch cells compute the full operator (cell %d)", c);
     if (cells[c].flags & PFMM_SINGLY_PERIODIC)
       return set_error(PFMM_ERR_INVALID_ARG, "batch cells are doubly periodic (cell %d)", c);
+    if (cells[c].flags & PFMM_DETERMINISTIC)
+      return set_error(PFMM_ERR_INVALID_ARG, "DETERMINISTIC is for single-cell calls (cell %d)", c);
     if (src_off[c + 1] < src_off[c] || (trg_off && trg_off[c + 1] < trg_off[c]))
       return set_error(PFMM_ERR_INVALID_ARG, "offsets must be non-decreasing (cell %d)", c);
   }

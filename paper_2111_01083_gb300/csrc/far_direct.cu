@@ -62,24 +62,43 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
 // Optional projection to zero net charge / force: net sums per rhs and
 // component (input frame) into mom[r*8 + 5 + c]; k_prep_q then subtracts the
 // mean before using the strengths.
+// part != NULL (deterministic mode): each warp writes its sums to
+// part[warp][r * ncomp + c] instead of adding them to mom; k_ordered_sum adds
+// them up in warp order afterwards.
 __global__ void k_net(int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
-                      double* __restrict__ mom) {
+                      double* __restrict__ mom, double* __restrict__ part) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int lane = threadIdx.x & 31;
+  const int64_t warp = i >> 5;
   for (int r = 0; r < nrhs; ++r)
     for (int c = 0; c < ncomp; ++c) {
       double v = (i < ns) ? q[((size_t)r * ncomp + c) * qs + i] : 0.0;
       if (!isfinite(v)) v = 0.0;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) atomicAdd(mom + r * 8 + 5 + c, v);
+      if (lane == 0) {
+        if (part) part[(size_t)warp * nrhs * ncomp + r * ncomp + c] = v;
+        else atomicAdd(mom + r * 8 + 5 + c, v);
+      }
     }
+}
+
+// out[(i / g) * ostride + i % g] += sum_{b < nb} part[b * m + i], i < m, in
+// the order b = 0, 1, ... (the deterministic mode's fixed-order reduction of
+// per-warp or per-block partial sums)
+__global__ void k_ordered_sum(const double* __restrict__ part, int nb, int m, int g, int ostride,
+                              double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += part[(size_t)b * m + i];
+  out[(size_t)(i / g) * ostride + i % g] += s;
 }
 
 // K0: strengths (canonical frame) and FP64 moments per rhs:
 //   mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y, [2] = sum |q| (all comps), [3] = sum q y' (f_x y')
 __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
                          const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
-                         double* __restrict__ mom, int* __restrict__ status, int project) {
+                         double* __restrict__ mom, int* __restrict__ status, int project, double* __restrict__ part) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool in = i < ns;
   double y = in ? src64[ns + i] : 0.0;
@@ -122,10 +141,18 @@ __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, co
       v3 += __shfl_down_sync(0xffffffffu, v3, o);
     }
     if (lane == 0) {
-      atomicAdd(mom + r * 8 + 0, v0);
-      atomicAdd(mom + r * 8 + 1, v1);
-      atomicAdd(mom + r * 8 + 2, v2);
-      atomicAdd(mom + r * 8 + 3, v3);
+      if (part) {  // deterministic mode: part[warp][r * 4 + k]
+        double* w = part + ((size_t)(i >> 5) * nrhs + r) * 4;
+        w[0] = v0;
+        w[1] = v1;
+        w[2] = v2;
+        w[3] = v3;
+      } else {
+        atomicAdd(mom + r * 8 + 0, v0);
+        atomicAdd(mom + r * 8 + 1, v1);
+        atomicAdd(mom + r * 8 + 2, v2);
+        atomicAdd(mom + r * 8 + 3, v3);
+      }
     }
   }
 }
@@ -179,7 +206,8 @@ constexpr int kRB = 4;  // rhs per block
 template <typename T, int KER>
 __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns, int chunk, const T* __restrict__ sx,
                                                            const T* __restrict__ sy, const int* __restrict__ sU,
-                                                           const T* __restrict__ qv, double* __restrict__ coef) {
+                                                           const T* __restrict__ qv, double* __restrict__ coef,
+                                                           double* __restrict__ part) {
   constexpr int NC = (KER == PFMM_STOKES || KER == PFMM_MSTOKES) ? 2 : 1;
   constexpr int NCH = (KER == PFMM_STOKES) ? 4 : NC;
   __shared__ T s_x[kFormSub], s_y[kFormSub];
@@ -294,12 +322,20 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
       }
   }
   if (!active) return;
+  // deterministic mode: this source chunk's sums go to part[chunk][...] (same
+  // layout as coef), added in chunk order by k_ordered_sum
+  double* base = part ? part + (size_t)blockIdx.x * f.nrhs * NCH * f.nterm * 2 : coef;
   for (int r = 0; r < nr; ++r)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
-      double* dst = coef + (((size_t)(r0 + r) * NCH + c) * f.nterm + t) * 2;
-      atomicAdd(dst, acc[r][c][0]);
-      atomicAdd(dst + 1, acc[r][c][1]);
+      double* dst = base + (((size_t)(r0 + r) * NCH + c) * f.nterm + t) * 2;
+      if (part) {
+        dst[0] = acc[r][c][0];
+        dst[1] = acc[r][c][1];
+      } else {
+        atomicAdd(dst, acc[r][c][0]);
+        atomicAdd(dst + 1, acc[r][c][1]);
+      }
     }
 }
 
@@ -541,13 +577,25 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   g_launches = (!self && nt > 0) ? 3 : 2;
   const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) &&
                       (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);
+  // deterministic mode: per-warp partial sums, added in warp order
+  double* part = (p->opts.flags & PFMM_DETERMINISTIC) ? (double*)(ws + L.det) : nullptr;
+  const int nwarp = cdiv_i(ns, 32), nrhs = p->opts.nrhs;
+  double* mom = (double*)(ws + L.moments);
   if (project) {
-    k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (double*)(ws + L.moments));
+    k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, nrhs, ns, p->s_stride, q, mom, part);
+    ++g_launches;
+    if (part) {
+      const int m = nrhs * p->ncomp;
+      k_ordered_sum<<<cdiv_i(m, 128), 128, 0, st>>>(part, nwarp, m, p->ncomp, 8, mom + 5);
+      ++g_launches;
+    }
+  }
+  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
+                                            (double*)(ws + L.qc), (float*)(ws + L.qf), mom, status, project, part);
+  if (part) {
+    k_ordered_sum<<<cdiv_i(4 * nrhs, 128), 128, 0, st>>>(part, nwarp, 4 * nrhs, 4, 8, mom);
     ++g_launches;
   }
-  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, p->opts.nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
-                                            (double*)(ws + L.qc), (float*)(ws + L.qf), (double*)(ws + L.moments),
-                                            status, project);
   return cudaGetLastError();
 }
 
@@ -572,13 +620,22 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
   int nrg = cdiv_i(f.nrhs, kRB);
   g_launches = (f.nterm > 0) ? 3 : 2;
   if (f.nterm > 0) {
+    const bool det = (p->opts.flags & PFMM_DETERMINISTIC) != 0;
     int ny = cdiv_i(f.nterm, kFormThreads);
     int want = 4 * 152 * 4;  // enough blocks to fill every SM several times
     int nchunk = std::max(1, std::min(cdiv_i(ns, kFormSub), want / std::max(1, ny * nrg)));
+    if (det) nchunk = std::min(nchunk, kDetChunks);
     int chunk = cdiv_i(cdiv_i(ns, nchunk), kFormSub) * kFormSub;
     nchunk = cdiv_i(ns, chunk);
     dim3 grid(nchunk, ny, nrg);
-    k_far_form<T, KER><<<grid, kFormThreads, 0, st>>>(f, g, (int)ns, chunk, sx, sy, sU, qv, coef);
+    double* part = det ? (double*)(ws + L.det) : nullptr;
+    k_far_form<T, KER><<<grid, kFormThreads, 0, st>>>(f, g, (int)ns, chunk, sx, sy, sU, qv, coef, part);
+    if (det) {
+      // every (rhs, channel, term) of every chunk is written (inactive terms as 0)
+      const int m = f.nrhs * f.nch * f.nterm * 2;
+      k_ordered_sum<<<cdiv_i(m, 128), 128, 0, st>>>(part, nchunk, m, m, 0, coef);
+      ++g_launches;
+    }
   }
   T2* w = (T2*)(ws + L.wts) + (second ? (size_t)f.nrhs * nw * p->far.nterm : 0);
   dim3 gw(cdiv_i(std::max(1, f.nterm), 128), f.nrhs);

@@ -1073,7 +1073,8 @@ void fmm_setup(pfmm_plan* p) {
   FmmPlan& F = p->fmm;
   F = FmmPlan{};
   const pfmm_opts& o = p->opts;
-  const bool capable = (o.kernel == PFMM_LAPLACE || o.kernel == PFMM_STOKES) && o.precision == PFMM_MIXED;
+  const bool capable = (o.kernel == PFMM_LAPLACE || o.kernel == PFMM_STOKES) && o.precision == PFMM_MIXED &&
+                       !(o.flags & PFMM_DETERMINISTIC);
   bool on = false;
   if (o.flags & PFMM_NEAR_FMM) on = capable;
   else if (!(o.flags & PFMM_NEAR_DIRECT))

@@ -1183,6 +1183,9 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
   const int nrg = mixed ? 1 : cdivl(a.nrhs, 4);
   // split the sources so that the grid holds >= ~32 blocks per SM
   int nsc = std::max(1, std::min(cdivl(ns, kP2PTile), cdivl(32 * 152, (int64_t)ntb * nrg)));
+  // deterministic mode: one source chunk per target block, so each output
+  // receives exactly one addition from the P2P
+  if (p->opts.flags & PFMM_DETERMINISTIC) nsc = 1;
   a.chunk = cdivl(cdivl(ns, nsc), kP2PTile) * kP2PTile;
   nsc = cdivl(ns, a.chunk);
   const bool g = grad != nullptr;

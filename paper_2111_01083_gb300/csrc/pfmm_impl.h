@@ -9,6 +9,7 @@ namespace pfmm {
 
 constexpr int kMaxNear = 32;      // (2 m0 + 1) * 3 images; m0 <= 3 after reduction
 constexpr int kPlanEvents = 8;    // profiling events of a plan
+constexpr int kDetChunks = 128;   // deterministic mode: source chunks of the coefficient formation
 constexpr int kStatusWords = 8;   // status word region (ints)
 
 // device status bits (combined with atomicOr; mapped to pfmm_status by the host)
@@ -85,6 +86,7 @@ struct Layout {
   size_t nufft;            // NUFFT scratch (grids, spectra)
   size_t adj;              // adjoint scratch (gradient of the adjoint field, potential if dq is not wanted)
   size_t fmm;              // near-field tree code (FmmPlan offsets are relative to this)
+  size_t det;              // deterministic mode: partial sums reduced in a fixed order
   size_t stage;            // host-staging region (pfmm_execute_host only)
   size_t total, total_host;
 };

@@ -302,7 +302,11 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     if (o->flags & PFMM_SINGLY_PERIODIC)
       return fail(PFMM_ERR_INVALID_ARG, "the modified Stokes kernel is doubly periodic only");
   }
-  if (o->flags & ~511u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~511u);
+  if (o->flags & ~1023u) return fail(PFMM_ERR_INVALID_ARG, "unknown flag bits 0x%x", o->flags & ~1023u);
+  if ((o->flags & PFMM_DETERMINISTIC) && (o->flags & PFMM_NEAR_FMM))
+    return fail(PFMM_ERR_INVALID_ARG, "DETERMINISTIC uses the direct near sum (not NEAR_FMM)");
+  if ((o->flags & PFMM_DETERMINISTIC) && o->path == PFMM_PATH_NUFFT)
+    return fail(PFMM_ERR_INVALID_ARG, "DETERMINISTIC uses the direct far-field path (not NUFFT)");
   if ((o->flags & PFMM_NEAR_DIRECT) && (o->flags & PFMM_NEAR_FMM))
     return fail(PFMM_ERR_INVALID_ARG, "NEAR_DIRECT and NEAR_FMM are exclusive");
   if (o->near_order != 0 && (o->near_order < 8 || o->near_order > 32))
@@ -425,7 +429,7 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int path = o->path;
   // the single-block shared-memory FFT handles fine grids up to 8192 points
   if (path == PFMM_PATH_AUTO)
-    path = (M >= 64 && nf <= 8192) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+    path = (M >= 64 && nf <= 8192 && !(o->flags & PFMM_DETERMINISTIC)) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
     pfmm_plan_destroy(p);
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
@@ -512,6 +516,18 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
                (size_t)nrhs * p->ncomp * std::max(ns_max, nt_max) * sizeof(double));
   pfmm::fmm_setup(p);
   L.fmm = take(p->fmm.bytes);
+  {
+    // deterministic mode: per-warp moment partials (k_prep_q / k_net, whole
+    // blocks of 8 warps) and per-chunk formation partials, one use at a time
+    size_t det = 0;
+    if (o->flags & PFMM_DETERMINISTIC) {
+      const size_t warps = (size_t)((ns_max + 255) / 256) * 8;
+      const size_t prep = warps * nrhs * 4 * sizeof(double);
+      const size_t form = (size_t)kDetChunks * nrhs * f.nch * std::max(f.nterm, p->far2.nterm) * 2 * sizeof(double);
+      det = std::max(prep, form);
+    }
+    L.det = take(det);
+  }
   L.total = off;
   size_t ncq = (size_t)nrhs * p->ncomp;
   L.stage = off;

@@ -85,7 +85,7 @@ def check_inputs(kernel, nrhs, src, q, trg, out=None, grad=True):
 class PeriodicOp:
     def __init__(self, kernel, e1, e2, beta=0.0, tol=1e-6, precision="mixed", path="auto", nufft_w=0, n_gl=0,
                  nrhs=1, part="total", ns_max=0, nt_max=0, device=None, singly=False, we="auto", near="auto",
-                 near_order=0, near_leaf=0):
+                 near_order=0, near_leaf=0, deterministic=False):
         L = _lib.lib()
         o = _lib.Opts()
         o.e1[0], o.e1[1] = float(e1[0]), float(e1[1])
@@ -98,7 +98,8 @@ class PeriodicOp:
         o.nufft_w = int(nufft_w)
         o.n_gl = int(n_gl)
         o.nrhs = int(nrhs)
-        o.flags = _PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0) | _WE[we] | _NEAR[near]
+        o.flags = (_PART[part] | (_lib.PFMM_SINGLY_PERIODIC if singly else 0) | _WE[we] | _NEAR[near] |
+                   (_lib.PFMM_DETERMINISTIC if deterministic else 0))
         o.near_order = int(near_order)
         o.near_leaf = int(near_leaf)
         self.kernel = kernel

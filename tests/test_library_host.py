@@ -102,7 +102,7 @@ def test_west_east_direction_flags(L):
     assert (skew["m0"], skew["we_rotated"]) == (1, 0)
 
 
-@pytest.mark.parametrize("kw", [dict(flags=96), dict(flags=512), dict(flags=48)])
+@pytest.mark.parametrize("kw", [dict(flags=96), dict(flags=1024), dict(flags=48)])
 def test_west_east_flag_errors(L, kw):
     from paper_2111_01083_gb300 import _lib
     o = _lib.Opts()
@@ -301,7 +301,7 @@ def test_near_field_flags_exclusive(L):
     o.flags = _lib.PFMM_NEAR_DIRECT | _lib.PFMM_NEAR_FMM
     h = ctypes.c_void_p()
     assert L.pfmm_plan_create(ctypes.byref(o), 10, 10, ctypes.byref(h)) == 1
-    o.flags = 512
+    o.flags = 1024
     assert L.pfmm_plan_create(ctypes.byref(o), 10, 10, ctypes.byref(h)) == 1
 
 
@@ -309,3 +309,27 @@ def test_near_stats_requires_tree_code(L):
     op = _op(near="direct")
     out = (ctypes.c_int64 * 5)()
     assert L.pfmm_near_stats(op._h, ctypes.c_void_p(256), None, out) == 1
+
+
+def test_deterministic_plans(L):
+    """PFMM_DETERMINISTIC: the direct far path and the direct near sum; the
+    NUFFT path or the tree code with it are argument errors; batches refuse it."""
+    from paper_2111_01083_gb300 import BatchOp, _lib
+    big = dict(e1=(16.0, 0.0), ns_max=100000, nt_max=100000)
+    d = _op(**big, deterministic=True).describe()
+    assert d["path"] == 1 and d["near_fmm"] == 0
+    assert _op(**big).describe()["path"] == 1 or _op(**big).describe()["M"] < 64
+    assert _op(e1=(64.0, 0.0), ns_max=1000, nt_max=1000).describe()["path"] == 2
+    assert _op(e1=(64.0, 0.0), ns_max=1000, nt_max=1000, deterministic=True).describe()["path"] == 1
+    for kw in (dict(path="nufft"), dict(near="fmm")):
+        with pytest.raises(_lib.PfmmError) as ei:
+            _op(deterministic=True, **kw)
+        assert ei.value.code == 1
+    o = _lib.Opts()
+    o.e1[0], o.e2[1] = 1.0, 1.0
+    o.tol, o.precision, o.nrhs, o.kernel = 1e-6, 1, 1, 0
+    o.flags = _lib.PFMM_DETERMINISTIC
+    arr = (_lib.Opts * 1)(o)
+    so = (ctypes.c_int64 * 2)(0, 10)
+    h = ctypes.c_void_p()
+    assert L.pfmm_batch_create(arr, 1, so, None, 0, ctypes.byref(h)) == 1
