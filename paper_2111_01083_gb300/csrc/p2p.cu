@@ -476,6 +476,56 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
     }
   };
 
+  // Packed form of source_far for subtiles where every image is active, on
+  // the potential: the images go two per FADD2/FMUL2/FFMA2 (the MUFU
+  // operations stay one per value), which halves the issue slots of the
+  // arithmetic; bx2/by2 hold the beta-scaled target coordinates relative to
+  // the subtile centre for the image pairs (2k, 2k + 1), (bxs, bys) those of
+  // the last image (NIMG is odd).
+  auto source_far_pk = [&](int jj, const float2* bx2, const float2* by2, float bxs, float bys) {
+    const float2 p = s_pb[jj];
+    const float2 npx = f2(-p.x), npy = f2(-p.y);
+    float2 acc = f2(0.f);
+#pragma unroll
+    for (int k = 0; k < NIMG / 2; ++k) {
+      const float2 dx = add2(bx2[k], npx), dy = add2(by2[k], npy);
+      const float2 x2 = fma2(dx, dx, mul2(dy, dy));
+      const float2 ix = make_float2(bes::mufu::rsqrt(x2.x), bes::mufu::rsqrt(x2.y));
+      const float2 x = mul2(x2, ix);
+      const float2 ar = mul2(x, f2(-1.4426950408889634f));
+      const float2 e = mul2(make_float2(bes::mufu::ex2(ar.x), bes::mufu::ex2(ar.y)),
+                            make_float2(bes::mufu::rsqrt(x.x), bes::mufu::rsqrt(x.y)));
+      float2 pl = fma2(ix, f2(0.03405312f), f2(-0.0804928f));
+      pl = fma2(ix, pl, f2(0.09405952f));
+      pl = fma2(ix, pl, f2(-0.08499568f));
+      pl = fma2(ix, pl, f2(0.08758272f));
+      pl = fma2(ix, pl, f2(-0.15664716f));
+      pl = fma2(ix, pl, f2(1.25331414f));
+      acc = fma2(e, pl, acc);
+    }
+    float K0s;
+    {
+      const float dx = bxs - p.x, dy = bys - p.y;
+      const float x2 = fmaf(dx, dx, dy * dy);
+      const float ix = bes::mufu::rsqrt(x2);
+      const float x = x2 * ix;
+      const float e = bes::mufu::ex2(-1.4426950408889634f * x) * bes::mufu::rsqrt(x);
+      const float k0 = e * (1.25331414f + ix * (-0.15664716f + ix * (0.08758272f + ix * (-0.08499568f + ix * (0.09405952f + ix * (-0.0804928f + ix * 0.03405312f))))));
+      K0s = (acc.x + acc.y) + k0;
+    }
+#pragma unroll
+    for (int g = 0; g < NQ4; ++g) {
+      const float4 q4 = s_q4[g][jj];
+      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int r = 4 * g + k;
+        if (r >= NR) break;
+        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
+      }
+    }
+  };
+
   // Tiles are classified kP2PThreads at a time, one thread per tile: per
   // image, some pair within the cutoff (any) or every pair within it (all).
   // FP32 on the outward-rounded boxes with a relative margin: a tile
@@ -559,7 +609,17 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         }
       }
       if (!__any_sync(0xffffffffu, near || small)) {
-        if (any == (1u << NIMG) - 1u) {
+        if (!GRAD && (NIMG & 1) && any == (1u << NIMG) - 1u) {
+          float2 bx2[NIMG / 2], by2[NIMG / 2];
+#pragma unroll
+          for (int k = 0; k < NIMG / 2; ++k) {
+            bx2[k] = make_float2(beta * txr[2 * k], beta * txr[2 * k + 1]);
+            by2[k] = make_float2(beta * tyr[2 * k], beta * tyr[2 * k + 1]);
+          }
+          const float bxs = beta * txr[NIMG - 1], bys = beta * tyr[NIMG - 1];
+#pragma unroll 2
+          for (int jj = js; jj < js + kP2PSub; ++jj) source_far_pk(jj, bx2, by2, bxs, bys);
+        } else if (any == (1u << NIMG) - 1u) {
 #pragma unroll 2
           for (int jj = js; jj < js + kP2PSub; ++jj) {
             const float2 p = s_pb[jj];
