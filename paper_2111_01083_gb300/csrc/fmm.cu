@@ -130,6 +130,7 @@ struct FmmArgs {
   int* gcnt;              // [2 node_cap + 1] counts, then offsets (M2L lists, then P2P lists)
   int* gcur;              // [2 node_cap] scatter cursors
   int* glist;             // C | image << 26, grouped by target box
+  int* gtgt;              // target box of each grouped M2L entry
   int* roots;             // [2][256] source roots, target roots
   int64_t node_cap, exp_cap, m2l_cap, p2p_cap, front_cap;
   const double* src64;    // canonical coordinates [2][ns] / [2][nt]
@@ -165,6 +166,15 @@ __device__ __forceinline__ float2 cpowf(float2 z, int k) {
   return r;
 }
 __device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ double dpowi(double x, int k) {
+  double r = 1.0;
+  while (k) {
+    if (k & 1) r *= x;
+    x *= x;
+    k >>= 1;
+  }
+  return r;
+}
 
 __device__ __forceinline__ uint32_t spread11(uint32_t v) {
   v &= 0x7FFu;
@@ -401,57 +411,54 @@ __device__ __forceinline__ bool is_source(const FmmArgs& a, int X) { return a.lo
 // 7: upward pass
 //
 // Channel charges: Laplace q_r; Stokes, per rhs, f_1, f_2, f, f conj(s - c).
+// P2M of a source leaf; one warp.  The scaled offsets u = (s - c)/R have
+// |u| <= 1, so the powers and the per-lane and per-warp sums are formed in
+// FP32 (relative error ~1e-7 of sum |q|); the coefficients are stored FP64.
 template <int KER>
-__device__ __forceinline__ double2 channel_charge(const FmmArgs& a, int ch, int j, double2 s, double2 c) {
-  if (KER == PFMM_LAPLACE) return make_double2(a.qd[(size_t)ch * a.ns + j], 0.0);
+__device__ __forceinline__ float2 channel_charge_f(const FmmArgs& a, int ch, int j, double2 s, double2 c) {
+  if (KER == PFMM_LAPLACE) return make_float2(a.qf[(size_t)ch * a.ns + j], 0.f);
   const int r = ch >> 2, k = ch & 3;
-  const double f1 = a.qd[((size_t)r * 2) * a.ns + j], f2 = a.qd[((size_t)r * 2 + 1) * a.ns + j];
-  if (k == 0) return make_double2(f1, 0.0);
-  if (k == 1) return make_double2(f2, 0.0);
-  if (k == 2) return make_double2(f1, f2);
-  const double dx = s.x - c.x, dy = s.y - c.y;  // f conj(s - c)
-  return make_double2(f1 * dx + f2 * dy, f2 * dx - f1 * dy);
+  const float f1 = a.qf[((size_t)r * 2) * a.ns + j], f2 = a.qf[((size_t)r * 2 + 1) * a.ns + j];
+  if (k == 0) return make_float2(f1, 0.f);
+  if (k == 1) return make_float2(f2, 0.f);
+  if (k == 2) return make_float2(f1, f2);
+  const float dx = (float)(s.x - c.x), dy = (float)(s.y - c.y);  // f conj(s - c)
+  return make_float2(f1 * dx + f2 * dy, f2 * dx - f1 * dy);
 }
 
-template <int P>
-__device__ __forceinline__ double2 warp_sum2(double2 v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
-
-// P2M of a source leaf; one warp
 template <int P, int KER>
 __device__ void p2m(const FmmArgs& a, int X, double R, int lane) {
   const int lo = a.lo[X], hi = a.hi[X];
   const double2 c = a.ctr[X];
   const double iR = 1.0 / R;
   for (int ch = 0; ch < a.nchan; ++ch) {
-    double2 acc[P];
+    float2 acc[P];
 #pragma unroll
-    for (int k = 0; k < P; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < P; ++k) acc[k] = make_float2(0.f, 0.f);
     for (int j = lo + lane; j < hi; j += 32) {
       const double2 s = a.xy[j];
-      const double2 u = make_double2((s.x - c.x) * iR, (s.y - c.y) * iR);
-      const double2 q = channel_charge<KER>(a, ch, j, s, c);
+      const float2 u = make_float2((float)((s.x - c.x) * iR), (float)((s.y - c.y) * iR));
+      const float2 q = channel_charge_f<KER>(a, ch, j, s, c);
       acc[0].x += q.x;
       acc[0].y += q.y;
-      double2 pw = u;
+      float2 pw = u;
 #pragma unroll
       for (int k = 1; k < P; ++k) {
-        const double2 t = cmul(q, pw);
+        const float2 t = cmulf(q, pw);
         acc[k].x += t.x;
         acc[k].y += t.y;
-        pw = cmul(pw, u);
+        pw = cmulf(pw, u);
       }
     }
     double2 mine = make_double2(0.0, 0.0);
 #pragma unroll
     for (int k = 0; k < P; ++k) {
-      const double2 v = warp_sum2<P>(acc[k]);
-      if (lane == k) mine = v;
+      float2 v = acc[k];
+      for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane == k) mine = make_double2((double)v.x, (double)v.y);
     }
     if (lane < P) {
       if (lane > 0) mine = make_double2(-mine.x / lane, -mine.y / lane);
@@ -501,7 +508,7 @@ __device__ void m2m(const FmmArgs& a, int X, int lane, double2* sT, double2* sW)
       const double rho = RC / R;
       __syncwarp();
       if (lane < P) sW[lane] = cpow(w, lane);
-      const double rk = lane < P ? pow(rho, (double)lane) : 0.0;
+      const double rk = lane < P ? dpowi(rho, lane) : 0.0;
       double2 prev = make_double2(0.0, 0.0);
       for (int q = 0; q < G; ++q) {
         const double2* mc = a.mult + ((size_t)C * a.nchan + g0 + q) * P;
@@ -674,71 +681,58 @@ __global__ void k_fmm_scatter(FmmArgs a) {
     const int64_t slot = (e < nm ? 0 : a.node_cap) + v.x;
     const int pos = a.gcnt[slot] + atomicAdd(a.gcur + slot, 1);
     a.glist[pos] = v.y;
+    if (e < nm) a.gtgt[pos] = v.x;
   }
 }
 
 // ---------------------------------------------------------------------------
-// 10: downward pass, one level per launch; one warp per target box
+// 10: downward pass.
+// (a) M2L over the flat list grouped by target box: each warp takes
+// kM2LChunk consecutive entries, lane l holds local coefficient l (FP32
+// arithmetic, FP64 partial sums) and adds its partial sums to the box's local
+// expansion (zeroed before) with FP64 atomics whenever the target box changes
+// and at the end of its chunk.  Boxes with long lists are spread over many
+// warps, so the pass is not bound by one warp walking one box's list.
+constexpr int kM2LChunk = 8;
+
 template <int P, int KER>
-__global__ void __launch_bounds__(32 * kDownWarps) k_fmm_down(FmmArgs a, int level) {
+__device__ __forceinline__ void m2l_flush(const FmmArgs& a, int X, int g0, int G, int lane, const double2* acc) {
+  if (lane >= P) return;
+  for (int q = 0; q < G; ++q) {
+    double2* d = a.loc + ((size_t)X * a.nchan + g0 + q) * P + lane;
+    atomicAdd(&d->x, acc[q].x);
+    atomicAdd(&d->y, acc[q].y);
+  }
+}
+
+template <int P, int KER>
+__global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
-  __shared__ double2 shB[kDownWarps][kFmmMaxP], shW[kDownWarps][kFmmMaxP];
   __shared__ float2 shT[kDownWarps][kFmmMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double2* sB = shB[wib];
-  double2* sW = shW[wib];
   float2* sT = shT[wib];
-  const int nn = a.ctl[C_NNODES];
-  const int nw = gridDim.x * kDownWarps;
+  const int nm = a.ctl[C_NM2L];
   const int G = KER == PFMM_STOKES ? 4 : 1;
-  for (int X = blockIdx.x * kDownWarps + wib; X < nn; X += nw) {
-    if (level_of(a, X) != level) continue;
-    if (a.self ? !is_source(a, X) : is_source(a, X)) continue;
-    const double2 cX = a.ctr[X];
-    const double RX = box_scale(a.rad[X], a.half[X]);
-    const int parent = a.par[X];
-    const int m0 = a.gcnt[X], m1 = a.gcnt[X + 1];
+  const int nw = gridDim.x * kDownWarps;
+  for (int e0 = (blockIdx.x * kDownWarps + wib) * kM2LChunk; e0 < nm; e0 += nw * kM2LChunk) {
+    const int e1 = min(nm, e0 + kM2LChunk);
     for (int g0 = 0; g0 < a.nchan; g0 += G) {
       double2 acc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
-      // L2L from the parent (FP64)
-      if (parent >= 0) {
-        const double2 cP = a.ctr[parent];
-        const double RP = box_scale(a.rad[parent], a.half[parent]);
-        const double2 z2 = make_double2(cX.x - cP.x, cX.y - cP.y);
-        const double2 w = make_double2(z2.x / RP, z2.y / RP);
-        const double rm = lane < P ? pow(RX / RP, (double)lane) : 0.0;
-        __syncwarp();
-        if (lane < P) sW[lane] = cpow(w, lane);
-        double2 prev = make_double2(0.0, 0.0);
-        for (int q = 0; q < G; ++q) {
-          __syncwarp();
-          if (lane < P) sB[lane] = a.loc[((size_t)parent * a.nchan + g0 + q) * P + lane];
-          __syncwarp();
-          double2 s = make_double2(0.0, 0.0);
-          if (lane < P) {
-            for (int l = lane; l < P; ++l) {
-              const double b = g_binom.c[l][lane];
-              const double2 t = cmul(sB[l], sW[l - lane]);
-              s.x += b * t.x;
-              s.y += b * t.y;
-            }
-            s.x *= rm;
-            s.y *= rm;
-          }
-          if (KER == PFMM_STOKES && q == 3) {
-            // f conj(w - c_X) = f conj(w - c_P) - conj(z2) f
-            const double2 t = cmul(make_double2(z2.x, -z2.y), prev);
-            s.x -= t.x;
-            s.y -= t.y;
-          }
-          prev = s;
-          acc[q] = s;
+      int cur = a.gtgt[e0];
+      double2 cX = a.ctr[cur];
+      double RX = box_scale(a.rad[cur], a.half[cur]);
+      for (int e = e0; e < e1; ++e) {
+        const int X = a.gtgt[e];
+        if (X != cur) {
+          m2l_flush<P, KER>(a, cur, g0, G, lane, acc);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+          cur = X;
+          cX = a.ctr[X];
+          RX = box_scale(a.rad[X], a.half[X]);
         }
-      }
-      // M2L (FP32 arithmetic, FP64 accumulation)
-      for (int e = m0; e < m1; ++e) {
         const int ci = a.glist[e];
         const int C = ci & kBoxMask, img = ci >> kImgShift;
         const double2 cC = a.ctr[C];
@@ -759,72 +753,208 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_down(FmmArgs a, int lev
           if (lane < P) sT[lane] = cmulf(make_float2((float)ak.x, (float)ak.y), pM);
           __syncwarp();
           const float2 Q = sT[0];
-          float2 s = make_float2(0.f, 0.f);
+          float2 sv = make_float2(0.f, 0.f);
           if (lane < P) {
 #pragma unroll 4
             for (int k = 1; k < P; ++k) {
               const float b = g_binom_f.c[k + lane - 1][lane];
-              s.x += b * sT[k].x;
-              s.y += b * sT[k].y;
+              sv.x += b * sT[k].x;
+              sv.y += b * sT[k].y;
             }
             if (lane == 0) {
               // Q log(z - c_C) about c_X: Q log(-z0) + ...; only its real part is used.
               // Stokes log channels carry the -f/2 of the Stokeslet in their constant.
               const float c0 = (KER == PFMM_STOKES && q < 2) ? lgz - 0.5f : lgz;
-              s.x += Q.x * c0;
-              s.y += Q.y * c0;
+              sv.x += Q.x * c0;
+              sv.y += Q.y * c0;
             } else {
               const float il = 1.0f / (float)lane;
-              s = cmulf(pL, make_float2(s.x - Q.x * il, s.y - Q.y * il));
+              sv = cmulf(pL, make_float2(sv.x - Q.x * il, sv.y - Q.y * il));
             }
           }
           if (KER == PFMM_STOKES && q == 3) {
             // f conj(w - c_X) = f conj(s - c_C) + conj(z0) f
             const float2 t = cmulf(make_float2(z0f.x, -z0f.y), prev);
-            s.x += t.x;
-            s.y += t.y;
+            sv.x += t.x;
+            sv.y += t.y;
           }
-          prev = s;
-          acc[q].x += (double)s.x;
-          acc[q].y += (double)s.y;
+          prev = sv;
+          acc[q].x += (double)sv.x;
+          acc[q].y += (double)sv.y;
         }
       }
-      if (lane < P)
-        for (int q = 0; q < G; ++q) a.loc[((size_t)X * a.nchan + g0 + q) * P + lane] = acc[q];
+      m2l_flush<P, KER>(a, cur, g0, G, lane, acc);
+    }
+  }
+}
+
+// (b) L2L, one level per launch (parents are final when their level is):
+// one warp per target box of the level adds the translated parent expansion
+// to its own (FP64).
+template <int P, int KER>
+__global__ void __launch_bounds__(32 * kDownWarps) k_fmm_l2l(FmmArgs a, int level) {
+  if (a.ctl[C_OVERFLOW]) return;
+  __shared__ double2 shB[kDownWarps][kFmmMaxP], shW[kDownWarps][kFmmMaxP];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double2* sB = shB[wib];
+  double2* sW = shW[wib];
+  const int nn = a.ctl[C_NNODES];
+  const int nw = gridDim.x * kDownWarps;
+  const int G = KER == PFMM_STOKES ? 4 : 1;
+  for (int X = blockIdx.x * kDownWarps + wib; X < nn; X += nw) {
+    if (level_of(a, X) != level) continue;
+    if (a.self ? !is_source(a, X) : is_source(a, X)) continue;
+    const int parent = a.par[X];
+    if (parent < 0) continue;
+    const double2 cX = a.ctr[X], cP = a.ctr[parent];
+    const double RX = box_scale(a.rad[X], a.half[X]);
+    const double RP = box_scale(a.rad[parent], a.half[parent]);
+    const double2 z2 = make_double2(cX.x - cP.x, cX.y - cP.y);
+    const double2 w = make_double2(z2.x / RP, z2.y / RP);
+    const double rm = lane < P ? dpowi(RX / RP, lane) : 0.0;
+    __syncwarp();
+    if (lane < P) sW[lane] = cpow(w, lane);
+    for (int g0 = 0; g0 < a.nchan; g0 += G) {
+      double2 prev = make_double2(0.0, 0.0);
+      for (int q = 0; q < G; ++q) {
+        __syncwarp();
+        if (lane < P) sB[lane] = a.loc[((size_t)parent * a.nchan + g0 + q) * P + lane];
+        __syncwarp();
+        double2 sv = make_double2(0.0, 0.0);
+        if (lane < P) {
+          for (int l = lane; l < P; ++l) {
+            const double b = g_binom.c[l][lane];
+            const double2 t = cmul(sB[l], sW[l - lane]);
+            sv.x += b * t.x;
+            sv.y += b * t.y;
+          }
+          sv.x *= rm;
+          sv.y *= rm;
+        }
+        if (KER == PFMM_STOKES && q == 3) {
+          // f conj(w - c_X) = f conj(w - c_P) - conj(z2) f
+          const double2 t = cmul(make_double2(z2.x, -z2.y), prev);
+          sv.x -= t.x;
+          sv.y -= t.y;
+        }
+        prev = sv;
+        if (lane < P) {
+          double2* d = a.loc + ((size_t)X * a.nchan + g0 + q) * P + lane;
+          d->x += sv.x;
+          d->y += sv.y;
+        }
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
-// 11: target leaves: L2P + P2P
+// 11: target leaves: L2P + P2P.  One block per target leaf (grid-stride);
+// the leaf's direct-list entries are spread over the block's warps (entry e
+// to warp e mod kLeafWarps), each warp stages its entry's sources in its own
+// shared-memory slice (no block barrier in the entry loop) and lane l sums
+// targets l and l + 32 of the current pass of kLeafTgt targets.  The warps'
+// partial sums are then added in a fixed order with the L2P value by one
+// thread per target, which writes the output (no atomics).
+constexpr int kLeafWarps = 4;
+constexpr int kLeafTgt = 64;
+
+template <int KER>
+__device__ __forceinline__ void pair_sum(float txh, float txl, float tyh, float tyl, float4 s, float q0, float q1,
+                                         float& f0, float& f1, float& f2) {
+  const float dx = (txh - s.x) + (txl - s.y);
+  const float dy = (tyh - s.z) + (tyl - s.w);
+  const float r2 = dx * dx + dy * dy;
+  if (r2 > 0.f) {
+    const float lg = __log2f(r2);
+    const float inv = __fdividef(1.0f, r2);
+    if (KER == PFMM_LAPLACE) {
+      f0 += q0 * lg;
+      f1 += q0 * dx * inv;
+      f2 += q0 * dy * inv;
+    } else {
+      // -(1/4pi)[f log r - d (d.f)/r^2]; log r = (ln 2 / 2) log2 r^2
+      const float rf = (dx * q0 + dy * q1) * inv;
+      f0 += q0 * lg * 0.34657359f - dx * rf;
+      f1 += q1 * lg * 0.34657359f - dy * rf;
+    }
+  }
+}
+
 template <int P, int KER>
-__global__ void __launch_bounds__(kLeafThreads) k_fmm_leaf(FmmArgs a) {
+__global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
-  __shared__ float4 s_hl[kLeafThreads];
-  __shared__ float s_q[2][kLeafThreads];
+  __shared__ float4 s_hl[kLeafWarps][32];
+  __shared__ float s_q[kLeafWarps][2][32];
+  __shared__ double s_red[kLeafWarps][3][kLeafTgt];
   __shared__ float2 s_b[4][kFmmMaxP];
   __shared__ double s_b0[4];
   __shared__ unsigned long long s_pairs;
   const int nn = a.ctl[C_NNODES];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   const int ncomp = KER == PFMM_STOKES ? 2 : 1;
   const int G = KER == PFMM_STOKES ? 4 : 1;
   if (tid == 0) s_pairs = 0;
+  unsigned long long my_pairs = 0;
   for (int X = blockIdx.x; X < nn; X += gridDim.x) {
     if (!is_leaf(a, X) || (a.self ? !is_source(a, X) : is_source(a, X))) continue;
     const int lo = a.lo[X], hi = a.hi[X];
     const double2 cX = a.ctr[X];
     const double RX = box_scale(a.rad[X], a.half[X]);
-    const int p0 = a.gcnt[a.node_cap + X] - a.gcnt[a.node_cap], p1 = a.gcnt[a.node_cap + X + 1] - a.gcnt[a.node_cap];
-    const int pbase = a.gcnt[a.node_cap];  // P2P lists start after all M2L lists
-    for (int t0 = lo; t0 < hi; t0 += kLeafThreads) {
-      const int t = t0 + tid;
-      const bool valid = t < hi;
-      const double2 tp = valid ? a.xy[t] : cX;
+    const int pbeg = a.gcnt[a.node_cap + X], pend = a.gcnt[a.node_cap + X + 1];
+    for (int t0 = lo; t0 < hi; t0 += kLeafTgt) {
+      // this pass: targets t0 .. t0 + kLeafTgt - 1; lane owns slots lane, lane + 32
+      double2 tp[2];
+      bool tv[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int t = t0 + lane + 32 * k;
+        tv[k] = t < hi;
+        tp[k] = tv[k] ? a.xy[t] : cX;
+      }
       for (int r = 0; r < a.nrhs; ++r) {
-        double out0 = 0.0, out1 = 0.0, out2 = 0.0;  // Laplace: pot, grad x, grad y; Stokes: u1, u2
-        // L2P (FP64 Horner) on the channels of rhs r
-        __syncthreads();
+        double acc[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        for (int e = pbeg + wib; e < pend; e += kLeafWarps) {
+          const int ci = a.glist[e];
+          const int C = ci & kBoxMask, img = ci >> kImgShift;
+          const int clo = a.lo[C], chi = a.hi[C];
+          if (a.count_pairs && r == 0 && lane == 0)
+            my_pairs += (unsigned long long)(min(hi, t0 + kLeafTgt) - t0) * (unsigned long long)(chi - clo);
+          float th[2][4];
+#pragma unroll
+          for (int k = 0; k < 2; ++k) {
+            const double sx = tp[k].x - a.off[img][0], sy = tp[k].y - a.off[img][1];
+            th[k][0] = (float)sx;
+            th[k][1] = (float)(sx - (double)th[k][0]);
+            th[k][2] = (float)sy;
+            th[k][3] = (float)(sy - (double)th[k][2]);
+          }
+          for (int c0 = clo; c0 < chi; c0 += 32) {
+            __syncwarp();
+            const int j = c0 + lane;
+            if (j < chi) {
+              s_hl[wib][lane] = a.hl[j];
+              for (int c = 0; c < ncomp; ++c) s_q[wib][c][lane] = a.qf[((size_t)r * ncomp + c) * a.ns + j];
+            }
+            __syncwarp();
+            const int m = min(32, chi - c0);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+              if (!tv[k]) continue;
+              float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+              for (int jj = 0; jj < m; ++jj)
+                pair_sum<KER>(th[k][0], th[k][1], th[k][2], th[k][3], s_hl[wib][jj], s_q[wib][0][jj],
+                              KER == PFMM_STOKES ? s_q[wib][1][jj] : 0.f, f0, f1, f2);
+              acc[k][0] += (double)f0;
+              acc[k][1] += (double)f1;
+              acc[k][2] += (double)f2;
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) s_red[wib][c][lane + 32 * k] = acc[k][c];
         if (tid < G * P) {
           const int q = tid / P, k = tid % P;
           const double2 b = a.loc[((size_t)X * a.nchan + r * G + q) * P + k];
@@ -832,10 +962,18 @@ __global__ void __launch_bounds__(kLeafThreads) k_fmm_leaf(FmmArgs a) {
           if (k == 0) s_b0[q] = b.x;
         }
         __syncthreads();
-        {
-          // FP32 Horner for sum_{l>=1} b_l u^l and its derivative (|u| <= 1,
-          // terms decaying); the constant b_0 (the bulk of the potential) in FP64
-          const float2 u = make_float2((float)((tp.x - cX.x) / RX), (float)((tp.y - cX.y) / RX));
+        if (tid < kLeafTgt && t0 + tid < hi) {
+          const int t = t0 + tid;
+          const double2 tq = a.xy[t];
+          double n0 = 0.0, n1 = 0.0, n2 = 0.0;
+          for (int w = 0; w < kLeafWarps; ++w) {
+            n0 += s_red[w][0][tid];
+            n1 += s_red[w][1][tid];
+            n2 += s_red[w][2][tid];
+          }
+          // L2P: FP32 Horner for sum_{l>=1} b_l u^l and its derivative (|u| <= 1,
+          // decaying terms); the constant b_0 (the bulk of the potential) in FP64
+          const float2 u = make_float2((float)((tq.x - cX.x) / RX), (float)((tq.y - cX.y) / RX));
           double2 F[4], D[4];
           for (int q = 0; q < G; ++q) {
             float2 f = s_b[q][P - 1], d = make_float2(0.f, 0.f);
@@ -847,99 +985,44 @@ __global__ void __launch_bounds__(kLeafThreads) k_fmm_leaf(FmmArgs a) {
               f.x += s_b[q][l].x;
               f.y += s_b[q][l].y;
             }
-            // now f = sum_{l>=1} b_l u^(l-1), d = its derivative
             const float2 fu = cmulf(f, u);
             const float2 du = cmulf(d, u);
             F[q] = make_double2(s_b0[q] + (double)fu.x, (double)fu.y);
             D[q] = make_double2((double)(f.x + du.x) / RX, (double)(f.y + du.y) / RX);
           }
+          double o0, o1, o2 = 0.0;
           if (KER == PFMM_LAPLACE) {
-            out0 = -F[0].x / (2.0 * M_PI);
-            out1 = -D[0].x / (2.0 * M_PI);
-            out2 = D[0].y / (2.0 * M_PI);
+            o0 = -F[0].x / (2.0 * M_PI) - n0 * (0.69314718055994531 / (4.0 * M_PI));
+            o1 = -D[0].x / (2.0 * M_PI) - n1 / (2.0 * M_PI);
+            o2 = D[0].y / (2.0 * M_PI) - n2 / (2.0 * M_PI);
           } else {
-            const double2 du = make_double2(tp.x - cX.x, tp.y - cX.y);
+            const double2 du = make_double2(tq.x - cX.x, tq.y - cX.y);
             // conj(u) C_1 - C_d
-            const double2 w = make_double2(du.x * D[2].x + du.y * D[2].y - D[3].x,
-                                           du.x * D[2].y - du.y * D[2].x - D[3].y);
-            out0 = -F[0].x / (4.0 * M_PI) + w.x / (8.0 * M_PI);
-            out1 = -F[1].x / (4.0 * M_PI) - w.y / (8.0 * M_PI);
+            const double2 wv = make_double2(du.x * D[2].x + du.y * D[2].y - D[3].x,
+                                            du.x * D[2].y - du.y * D[2].x - D[3].y);
+            o0 = -F[0].x / (4.0 * M_PI) + wv.x / (8.0 * M_PI) - n0 / (4.0 * M_PI);
+            o1 = -F[1].x / (4.0 * M_PI) - wv.y / (8.0 * M_PI) - n1 / (4.0 * M_PI);
           }
-        }
-        // P2P over the leaf's list
-        for (int e = p0; e < p1; ++e) {
-          const int ci = a.glist[pbase + e];
-          const int C = ci & kBoxMask, img = ci >> kImgShift;
-          const int clo = a.lo[C], chi = a.hi[C];
-          const double sx = tp.x - a.off[img][0], sy = tp.y - a.off[img][1];
-          const float txh = (float)sx, txl = (float)(sx - (double)txh);
-          const float tyh = (float)sy, tyl = (float)(sy - (double)tyh);
-          if (a.count_pairs && tid == 0 && r == 0 && t0 == lo)
-            s_pairs += (unsigned long long)(hi - lo) * (unsigned long long)(chi - clo);
-          for (int c0 = clo; c0 < chi; c0 += kLeafThreads) {
-            __syncthreads();
-            const int j = c0 + tid;
-            if (j < chi) {
-              s_hl[tid] = a.hl[j];
-              for (int c = 0; c < ncomp; ++c) s_q[c][tid] = a.qf[((size_t)r * ncomp + c) * a.ns + j];
-            }
-            __syncthreads();
-            const int m = min(kLeafThreads, chi - c0);
-            float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-            if (valid) {
-              for (int jj = 0; jj < m; ++jj) {
-                const float4 s = s_hl[jj];
-                const float dx = (txh - s.x) + (txl - s.y);
-                const float dy = (tyh - s.z) + (tyl - s.w);
-                const float r2 = dx * dx + dy * dy;
-                if (r2 > 0.f) {
-                  const float lg = __log2f(r2);
-                  const float inv = __fdividef(1.0f, r2);
-                  if (KER == PFMM_LAPLACE) {
-                    const float qq = s_q[0][jj];
-                    f0 += qq * lg;
-                    f1 += qq * dx * inv;
-                    f2 += qq * dy * inv;
-                  } else {
-                    const float g1 = s_q[0][jj], g2 = s_q[1][jj];
-                    const float rf = (dx * g1 + dy * g2) * inv;
-                    // -(1/4pi)[f log r - d (d.f)/r^2]; log r = (ln 2 / 2) log2 r^2
-                    f0 += g1 * lg * 0.34657359f - dx * rf;
-                    f1 += g2 * lg * 0.34657359f - dy * rf;
-                  }
-                }
-              }
-            }
-            if (KER == PFMM_LAPLACE) {
-              out0 += -(double)f0 * (0.69314718055994531 / (4.0 * M_PI));
-              out1 += -(double)f1 / (2.0 * M_PI);
-              out2 += -(double)f2 / (2.0 * M_PI);
-            } else {
-              out0 += -(double)f0 / (4.0 * M_PI);
-              out1 += -(double)f1 / (4.0 * M_PI);
-            }
-          }
-        }
-        if (valid) {
           const int o = a.perm[t];
           const double* R = a.rot;
           if (KER == PFMM_LAPLACE) {
-            if (a.pot) a.pot[(size_t)r * a.os + o] += out0;
+            if (a.pot) a.pot[(size_t)r * a.os + o] += o0;
             if (a.grad) {
-              a.grad[((size_t)r * 2) * a.os + o] += R[0] * out1 + R[2] * out2;
-              a.grad[((size_t)r * 2 + 1) * a.os + o] += R[1] * out1 + R[3] * out2;
+              a.grad[((size_t)r * 2) * a.os + o] += R[0] * o1 + R[2] * o2;
+              a.grad[((size_t)r * 2 + 1) * a.os + o] += R[1] * o1 + R[3] * o2;
             }
           } else {
-            a.pot[((size_t)r * 2) * a.os + o] += R[0] * out0 + R[2] * out1;
-            a.pot[((size_t)r * 2 + 1) * a.os + o] += R[1] * out0 + R[3] * out1;
+            a.pot[((size_t)r * 2) * a.os + o] += R[0] * o0 + R[2] * o1;
+            a.pot[((size_t)r * 2 + 1) * a.os + o] += R[1] * o0 + R[3] * o1;
           }
         }
+        __syncthreads();
       }
     }
   }
+  if (a.count_pairs && lane == 0 && my_pairs) atomicAdd(&s_pairs, my_pairs);
   __syncthreads();
-  if (a.count_pairs && tid == 0 && s_pairs)
-    atomicAdd((unsigned long long*)(a.ctl + C_PAIRS), s_pairs);
+  if (a.count_pairs && tid == 0 && s_pairs) atomicAdd((unsigned long long*)(a.ctl + C_PAIRS), s_pairs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1044,9 +1127,12 @@ cudaError_t run_expansions(const FmmArgs& a, int grid, cudaStream_t st, int* nl)
 
 template <int P, int KER>
 cudaError_t run_down(const FmmArgs& a, int grid, cudaStream_t st, int* nl, cudaEvent_t mid) {
-  for (int l = 0; l <= kFmmL; ++l) k_fmm_down<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a, l);
+  cudaError_t e = cudaMemsetAsync(a.loc, 0, (size_t)a.exp_cap * a.nchan * P * sizeof(double2), st);
+  if (e != cudaSuccess) return e;
+  k_fmm_m2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a);
+  for (int l = 1; l <= kFmmL; ++l) k_fmm_l2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a, l);
   if (mid) cudaEventRecord(mid, st);
-  k_fmm_leaf<P, KER><<<grid, kLeafThreads, 0, st>>>(a);
+  k_fmm_leaf<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
   *nl += kFmmL + 2;
   return cudaGetLastError();
 }
@@ -1145,6 +1231,7 @@ void fmm_setup(pfmm_plan* p) {
   F.o_gcnt = take((2 * NC + 1) * 4);
   F.o_gcur = take(2 * NC * 4);
   F.o_glist = take((size_t)(F.m2l_cap + F.p2p_cap) * sizeof(int));
+  F.o_gtgt = take((size_t)F.m2l_cap * sizeof(int));
   F.o_roots = take(512 * 4);
   F.bytes = off;
 }
@@ -1207,6 +1294,7 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   a.gcnt = (int*)(base + F.o_gcnt);
   a.gcur = (int*)(base + F.o_gcur);
   a.glist = (int*)(base + F.o_glist);
+  a.gtgt = (int*)(base + F.o_gtgt);
   a.roots = (int*)(base + F.o_roots);
   a.node_cap = F.node_cap;
   a.exp_cap = F.exp_cap;
