@@ -8,7 +8,7 @@ The computation lives in the CUDA library ``libpfmm.so`` (C ABI in
 package does not load the library; the first call does, and raises if it is
 missing (there is no CPU fallback).
 """
-from .periodic import BatchOp, PeriodicOp, StokesPressure, autotune_batch, periodic  # noqa: F401
+from .periodic import BatchOp, PeriodicOp, StokesPressure, autotune_batch, periodic, tune_batch, tuned_batch  # noqa: F401
 from . import _lib  # noqa: F401
 
-__all__ = ["PeriodicOp", "BatchOp", "StokesPressure", "autotune_batch", "periodic"]
+__all__ = ["PeriodicOp", "BatchOp", "StokesPressure", "autotune_batch", "periodic", "tune_batch", "tuned_batch"]

@@ -253,7 +253,8 @@ def _opts(kernel, e1, e2, beta, tol, precision, path, nufft_w, n_gl, nrhs, flags
 class BatchOp:
     """Many independent cells in one call (pfmm_batch_*).
 
-    cells: list of dicts with e1, e2 and optionally beta, tol; shared kernel,
+    cells: list of dicts with e1, e2 and optionally beta, tol, path, nufft_w
+    (per-cell far-field path and ES width, e.g. from tune_batch); shared kernel,
     precision and nrhs.  src_counts / trg_counts: points per cell (targets
     default to the sources).  Inputs are the concatenated arrays
     src [2, NS], q [nrhs, NS] (Stokes [nrhs, 2, NS]), trg [2, NT]."""
@@ -264,8 +265,8 @@ class BatchOp:
         n = len(cells)
         arr = (_lib.Opts * n)()
         for i, c in enumerate(cells):
-            arr[i] = _opts(kernel, c["e1"], c["e2"], c.get("beta", 0.0), c.get("tol", tol), precision, path, 0, 0,
-                           nrhs, _WE[c.get("we", "auto")])
+            arr[i] = _opts(kernel, c["e1"], c["e2"], c.get("beta", 0.0), c.get("tol", tol), precision,
+                           c.get("path", path), c.get("nufft_w", 0), 0, nrhs, _WE[c.get("we", "auto")])
         so = np.concatenate([[0], np.cumsum(src_counts)]).astype(np.int64)
         self._so = (ctypes.c_int64 * (n + 1))(*so.tolist())
         self._to = None
@@ -439,6 +440,104 @@ def autotune_batch(make_op, src, q, trg=None, candidates=(1024, 2048, 4096, 8192
         os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
         json.dump(d, open(cache, "w"), indent=1)
     return chunk, times
+
+
+def _time_graph(op, src, q, trg, reps, grad):
+    """Median of `reps` CUDA-graph replays of one batch execute (CUDA events)."""
+    import statistics
+    import torch
+    graph, _ = op.capture(src, q, trg, grad=grad)
+    torch.cuda.synchronize()
+    graph.replay()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    del graph
+    return statistics.median(ts)
+
+
+def tune_batch(kernel, cells, src_counts, src, q, trg=None, trg_counts=None, precision="mixed", nrhs=1, tol=1e-6,
+               chunks=(1024, 2048, 4096, 8192), crossovers=(32, 64, 128, None), reps=3, grad=False, cache=None,
+               key=None):
+    """Tune a batch's execution choices by timing CUDA-graph replays:
+
+      - the direct / NUFFT crossover: cells with M >= crossover take the NUFFT
+        south/north path (None: no NUFFT), M from each cell's plan;
+      - the ES spreading width w of the NUFFT cells, among the widths whose
+        error bound meets the tolerance (w >= ceil(log10(1/tol)) + 1, up to
+        the plan's default ceil(log10(1/tol)) + 2);
+      - the P2P source chunk.
+
+    Coordinate search in that order, each step keeping the best so far.
+    Every candidate is exact to the tolerance by construction (both paths and
+    every admissible width meet it), so the choice is by time alone.  Returns
+    (config, timings) with config = {"crossover", "nufft_w", "p2p_chunk"}; with
+    a cache path and key the result persists as JSON.  Build the tuned batch
+    with tuned_batch(kernel, cells, src_counts, config, ...)."""
+    import json
+    import math
+    import os
+    if cache and key and os.path.exists(cache):
+        try:
+            d = json.load(open(cache))
+            if key in d:
+                return d[key]["config"], d[key]["ms"]
+        except Exception:
+            pass
+    wmin = max(2, math.ceil(math.log10(1.0 / tol) + 1e-9) + 1)
+    widths = tuple(range(wmin, min(16, wmin + 1) + 1))
+    timings = {}
+
+    def run(cfg):
+        name = json.dumps(cfg, sort_keys=True)
+        if name not in timings:
+            op = tuned_batch(kernel, cells, src_counts, cfg, trg_counts=trg_counts, precision=precision, nrhs=nrhs,
+                             tol=tol)
+            timings[name] = _time_graph(op, src, q, trg, reps, grad)
+            del op
+        return timings[name]
+
+    cfg = {"crossover": 64, "nufft_w": 0, "p2p_chunk": 4096}
+    for field, cands in (("crossover", crossovers), ("nufft_w", widths), ("p2p_chunk", chunks)):
+        best = None
+        for c in cands:
+            trial = dict(cfg, **{field: c})
+            t = run(trial)
+            if best is None or t < best[0]:
+                best = (t, c)
+        cfg[field] = best[1]
+    if cache and key:
+        d = {}
+        if os.path.exists(cache):
+            try:
+                d = json.load(open(cache))
+            except Exception:
+                d = {}
+        d[key] = {"config": cfg, "ms": timings}
+        os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+        json.dump(d, open(cache, "w"), indent=1)
+    return cfg, timings
+
+
+def tuned_batch(kernel, cells, src_counts, config, trg_counts=None, precision="mixed", nrhs=1, tol=1e-6):
+    """A BatchOp with tune_batch's choices: per-cell path from the crossover on
+    the cell's mode count M, the ES width for its NUFFT cells, the P2P chunk."""
+    cx = config.get("crossover")
+    w = int(config.get("nufft_w") or 0)
+    cc = []
+    for c in cells:
+        m = PeriodicOp(kernel, c["e1"], c["e2"], beta=c.get("beta", 0.0), tol=c.get("tol", tol), precision=precision,
+                       nrhs=nrhs, ns_max=1, nt_max=1).describe()["M"]
+        nufft = cx is not None and m >= cx and m <= 2047  # the single-block FFT holds fine grids up to 8192
+        cc.append(dict(c, path="nufft" if nufft else "direct", nufft_w=w if nufft else 0))
+    return BatchOp(kernel, cc, src_counts, trg_counts, precision=precision, nrhs=nrhs, tol=tol,
+                   p2p_chunk=int(config.get("p2p_chunk") or 0))
 
 
 def _adjoint(op, src, q, trg, g, grad_fwd, need_q, need_s, need_t):

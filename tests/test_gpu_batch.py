@@ -8,6 +8,7 @@ import pytest
 
 import workloads
 from gpu_util import errs, oracle, run_lib
+from oracle import api as oapi
 
 pytestmark = pytest.mark.gpu
 
@@ -146,3 +147,43 @@ def test_autotune_picks_a_candidate(tmp_path):
     assert best in (256, 1024) and len(times) == 2
     best2, _ = autotune_batch(mk, S, Q, candidates=(256, 1024), cache=cache, key="k")
     assert best2 == best
+
+
+def test_tune_batch_crossover_width_chunk(tmp_path):
+    """tune_batch picks the direct/NUFFT crossover, the ES width (only widths
+    whose bound meets the tolerance) and the P2P chunk by graph-replay time;
+    the tuned batch is the fastest configuration it timed, matches the oracle
+    at 1e-6 on sampled cells, and the cached choice is returned unchanged."""
+    import torch
+    from paper_2111_01083_gb300 import tune_batch, tuned_batch
+    rng = np.random.default_rng(12)
+    cells, srcs, qs = [], [], []
+    for A in (1.0, 3.0, 20.0, 40.0, 64.0, 64.0):
+        n = int(rng.integers(800, 3000))
+        e1, e2 = (A, 0.0), (0.0, 1.0)
+        cells.append(dict(e1=e1, e2=e2, beta=1.0))
+        srcs.append(workloads.points(rng, e1, e2, n))
+        qs.append(rng.standard_normal((8, n)))
+    counts = [s.shape[1] for s in srcs]
+    dev = torch.device("cuda", 0)
+    S = torch.tensor(np.concatenate(srcs, axis=1), device=dev)
+    Q = torch.tensor(np.concatenate(qs, axis=-1), device=dev)
+    cache = str(tmp_path / "tune.json")
+    cfg, times = tune_batch("modhelm", cells, counts, S, Q, nrhs=8, tol=1e-6, chunks=(1024, 4096),
+                            crossovers=(64, 128, None), reps=2, cache=cache, key="k")
+    assert cfg["nufft_w"] in (7, 8) and cfg["p2p_chunk"] in (1024, 4096) and cfg["crossover"] in (64, 128, None)
+    import json
+    assert times[json.dumps(cfg, sort_keys=True)] == min(times.values())
+    cfg2, _ = tune_batch("modhelm", cells, counts, S, Q, nrhs=8, tol=1e-6, cache=cache, key="k")
+    assert cfg2 == cfg
+    op = tuned_batch("modhelm", cells, counts, cfg, nrhs=8, tol=1e-6)
+    pot, _ = op(S, Q, grad=False)
+    torch.cuda.synchronize()
+    op.status(dev)
+    pot = pot.cpu().numpy()
+    edges = np.concatenate([[0], np.cumsum(counts)])
+    for c in (1, 4):
+        idx = rng.choice(counts[c], 40, replace=False)
+        ref, _ = oracle("modhelm", cells[c]["e1"], cells[c]["e2"], srcs[c], qs[c], srcs[c][:, idx], beta=1.0, grad=False)
+        got = pot[:, edges[c]:edges[c + 1]][:, idx]
+        assert oapi.rel_err(got, ref) < 1e-6
