@@ -426,21 +426,38 @@ __device__ __forceinline__ float2 channel_charge_f(const FmmArgs& a, int ch, int
   return make_float2(f1 * dx + f2 * dy, f2 * dx - f1 * dy);
 }
 
+template <int KER>
+__device__ __forceinline__ double2 channel_charge_d(const FmmArgs& a, int ch, int j, double2 s, double2 c) {
+  if (KER == PFMM_LAPLACE) return make_double2(a.qd[(size_t)ch * a.ns + j], 0.0);
+  const int r = ch >> 2, k = ch & 3;
+  const double f1 = a.qd[((size_t)r * 2) * a.ns + j], f2 = a.qd[((size_t)r * 2 + 1) * a.ns + j];
+  if (k == 0) return make_double2(f1, 0.0);
+  if (k == 1) return make_double2(f2, 0.0);
+  if (k == 2) return make_double2(f1, f2);
+  const double dx = s.x - c.x, dy = s.y - c.y;  // f conj(s - c)
+  return make_double2(f1 * dx + f2 * dy, f2 * dx - f1 * dy);
+}
+
 template <int P, int KER>
 __device__ void p2m(const FmmArgs& a, int X, double R, int lane) {
   const int lo = a.lo[X], hi = a.hi[X];
   const double2 c = a.ctr[X];
   const double iR = 1.0 / R;
   for (int ch = 0; ch < a.nchan; ++ch) {
+    // the box charge Q (coefficient 0) in FP64 from the FP64 strengths: its
+    // Q log|z - c| term is the bulk of the far potential of the box, and an
+    // FP32 rounding of Q would put a smooth error of that size on every target
     float2 acc[P];
+    double2 q0 = make_double2(0.0, 0.0);
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = make_float2(0.f, 0.f);
     for (int j = lo + lane; j < hi; j += 32) {
       const double2 s = a.xy[j];
       const float2 u = make_float2((float)((s.x - c.x) * iR), (float)((s.y - c.y) * iR));
       const float2 q = channel_charge_f<KER>(a, ch, j, s, c);
-      acc[0].x += q.x;
-      acc[0].y += q.y;
+      const double2 qd = channel_charge_d<KER>(a, ch, j, s, c);
+      q0.x += qd.x;
+      q0.y += qd.y;
       float2 pw = u;
 #pragma unroll
       for (int k = 1; k < P; ++k) {
@@ -451,8 +468,13 @@ __device__ void p2m(const FmmArgs& a, int X, double R, int lane) {
       }
     }
     double2 mine = make_double2(0.0, 0.0);
+    for (int o = 16; o > 0; o >>= 1) {
+      q0.x += __shfl_xor_sync(0xffffffffu, q0.x, o);
+      q0.y += __shfl_xor_sync(0xffffffffu, q0.y, o);
+    }
+    if (lane == 0) mine = q0;
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
+    for (int k = 1; k < P; ++k) {
       float2 v = acc[k];
       for (int o = 16; o > 0; o >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
@@ -744,9 +766,10 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
         const float2 rL = make_float2((float)(RX * zx * iz2), (float)(-RX * zy * iz2));
         const float2 pM = cpowf(rM, lane < P ? lane : 0);
         const float2 pL = cpowf(rL, lane < P ? lane : 0);
-        const float lgz = (float)(0.5 * log(zx * zx + zy * zy));
+        const double lgz = 0.5 * log(zx * zx + zy * zy);
         const float2 z0f = make_float2((float)zx, (float)zy);
         float2 prev = make_float2(0.f, 0.f);
+        double2 prevQ = make_double2(0.0, 0.0);
         for (int q = 0; q < G; ++q) {
           const double2 ak = lane < P ? a.mult[((size_t)C * a.nchan + g0 + q) * P + lane] : make_double2(0.0, 0.0);
           __syncwarp();
@@ -754,6 +777,10 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
           __syncwarp();
           const float2 Q = sT[0];
           float2 sv = make_float2(0.f, 0.f);
+          // the Q log(-z0) constant (real part used), FP64 on lane 0: the bulk of
+          // the box's far potential.  Stokes log channels carry the Stokeslet's
+          // -f/2 in their constant.
+          double2 cq = make_double2(0.0, 0.0);
           if (lane < P) {
 #pragma unroll 4
             for (int k = 1; k < P; ++k) {
@@ -762,11 +789,8 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
               sv.y += b * sT[k].y;
             }
             if (lane == 0) {
-              // Q log(z - c_C) about c_X: Q log(-z0) + ...; only its real part is used.
-              // Stokes log channels carry the -f/2 of the Stokeslet in their constant.
-              const float c0 = (KER == PFMM_STOKES && q < 2) ? lgz - 0.5f : lgz;
-              sv.x += Q.x * c0;
-              sv.y += Q.y * c0;
+              const double c0 = (KER == PFMM_STOKES && q < 2) ? lgz - 0.5 : lgz;
+              cq = make_double2(ak.x * c0, ak.y * c0);
             } else {
               const float il = 1.0f / (float)lane;
               sv = cmulf(pL, make_float2(sv.x - Q.x * il, sv.y - Q.y * il));
@@ -777,10 +801,13 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
             const float2 t = cmulf(make_float2(z0f.x, -z0f.y), prev);
             sv.x += t.x;
             sv.y += t.y;
+            cq.x += zx * prevQ.x + zy * prevQ.y;
+            cq.y += zx * prevQ.y - zy * prevQ.x;
           }
           prev = sv;
-          acc[q].x += (double)sv.x;
-          acc[q].y += (double)sv.y;
+          prevQ = cq;
+          acc[q].x += (double)sv.x + cq.x;
+          acc[q].y += (double)sv.y + cq.y;
         }
       }
       m2l_flush<P, KER>(a, cur, g0, G, lane, acc);
