@@ -122,6 +122,8 @@ struct FmmArgs {
   double2* ctr;
   double* half;
   double* rad;
+  float* scl;             // expansion scale box_scale(rad, half) in FP32
+  float offh[kMaxNear][2], offl[kMaxNear][2];  // image offsets as FP32 hi/lo pairs
   double2* mult;          // [exp_cap][nchan][p]
   double2* loc;           // [exp_cap][nchan][p]
   int2* front;            // 2 x front_cap (A, C | image << 26)
@@ -166,6 +168,15 @@ __device__ __forceinline__ float2 cpowf(float2 z, int k) {
   return r;
 }
 __device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float fpowi(float x, int k) {
+  float r = 1.0f;
+  while (k) {
+    if (k & 1) r *= x;
+    x *= x;
+    k >>= 1;
+  }
+  return r;
+}
 __device__ __forceinline__ double dpowi(double x, int k) {
   double r = 1.0;
   while (k) {
@@ -502,10 +513,13 @@ __device__ double leaf_radius(const FmmArgs& a, int X, int lane) {
   return sqrt(r2) * (1.0 + 1e-12);
 }
 
-// radius of an inner box from its children (an upper bound), and M2M; one warp.
-// Children are read with L2 loads: other warps wrote them before their fence.
+// radius of an inner box from its children (an upper bound), and M2M; one
+// warp.  Children are read with L2 loads: other warps wrote them before their
+// fence.  Coefficients 1 .. p-1 are translated in FP32 (|w| + rho <= 1, so
+// the re-expansion is well conditioned); the box charge Q (coefficient 0)
+// is summed in FP64.
 template <int P, int KER>
-__device__ void m2m(const FmmArgs& a, int X, int lane, double2* sT, double2* sW) {
+__device__ void m2m(const FmmArgs& a, int X, int lane, float2* sT, float2* sW) {
   const double2 cX = a.ctr[X];
   const int end = a.nend[X];
   double r = 0.0;
@@ -515,72 +529,92 @@ __device__ void m2m(const FmmArgs& a, int X, int lane, double2* sT, double2* sW)
   }
   r *= (1.0 + 1e-12);
   const double R = box_scale(r, a.half[X]);
-  if (lane == 0) a.rad[X] = r;
+  if (lane == 0) {
+    a.rad[X] = r;
+    a.scl[X] = (float)R;
+  }
   if (!is_source(a, X)) return;
+  const float Rf = (float)R;
   const int G = KER == PFMM_STOKES ? 4 : 1;
   for (int g0 = 0; g0 < a.nchan; g0 += G) {
-    double2 acc[4];
+    float2 acc[4];
+    double2 accQ[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int q = 0; q < 4; ++q) {
+      acc[q] = make_float2(0.f, 0.f);
+      accQ[q] = make_double2(0.0, 0.0);
+    }
     for (int C = X + 1; C < end; C = a.nend[C]) {
       const double2 cc = a.ctr[C];
       const double2 z1 = make_double2(cc.x - cX.x, cc.y - cX.y);
-      const double RC = box_scale(__ldcg(a.rad + C), a.half[C]);
-      const double2 w = make_double2(z1.x / R, z1.y / R);
-      const double rho = RC / R;
+      const float2 w = make_float2((float)z1.x / Rf, (float)z1.y / Rf);
+      const float rho = __ldcg(a.scl + C) / Rf;
       __syncwarp();
-      if (lane < P) sW[lane] = cpow(w, lane);
-      const double rk = lane < P ? dpowi(rho, lane) : 0.0;
-      double2 prev = make_double2(0.0, 0.0);
+      if (lane < P) sW[lane] = cpowf(w, lane);
+      const float rk = fpowi(rho, lane < P ? lane : 0);
+      float2 prevF = make_float2(0.f, 0.f);
+      double2 prevQ = make_double2(0.0, 0.0);
       for (int q = 0; q < G; ++q) {
         const double2* mc = a.mult + ((size_t)C * a.nchan + g0 + q) * P;
         const double2 ak = lane < P ? ldcg2(mc + lane) : make_double2(0.0, 0.0);
         __syncwarp();
-        if (lane < P) sT[lane] = make_double2(ak.x * rk, ak.y * rk);
+        if (lane < P) sT[lane] = make_float2((float)ak.x * rk, (float)ak.y * rk);
         __syncwarp();
-        const double2 Q = sT[0];  // rho^0 = 1
-        double2 s = make_double2(0.0, 0.0);
         if (lane == 0) {
-          s = Q;
-        } else if (lane < P) {
-          for (int k = 1; k <= lane; ++k) {
-            const double b = g_binom.c[lane - 1][k - 1];
-            const double2 t = cmul(sT[k], sW[lane - k]);
-            s.x += b * t.x;
-            s.y += b * t.y;
+          double2 sq = ak;
+          if (KER == PFMM_STOKES && q == 3) {
+            // f conj(s - c_X) = f conj(s - c_C) + conj(z1) f
+            sq.x += z1.x * prevQ.x + z1.y * prevQ.y;
+            sq.y += z1.x * prevQ.y - z1.y * prevQ.x;
           }
-          const double2 wl = sW[lane];
-          s.x -= (Q.x * wl.x - Q.y * wl.y) / lane;
-          s.y -= (Q.x * wl.y + Q.y * wl.x) / lane;
+          prevQ = sq;
+          accQ[q].x += sq.x;
+          accQ[q].y += sq.y;
+        } else if (lane < P) {
+          const float2 Qc = sT[0];
+          float2 sv = make_float2(0.f, 0.f);
+          for (int k = 1; k <= lane; ++k) {
+            const float b = g_binom_f.c[lane - 1][k - 1];
+            const float2 t = cmulf(sT[k], sW[lane - k]);
+            sv.x += b * t.x;
+            sv.y += b * t.y;
+          }
+          const float2 wl = sW[lane];
+          const float il = 1.0f / (float)lane;
+          sv.x -= (Qc.x * wl.x - Qc.y * wl.y) * il;
+          sv.y -= (Qc.x * wl.y + Qc.y * wl.x) * il;
+          if (KER == PFMM_STOKES && q == 3) {
+            const float2 t = cmulf(make_float2((float)z1.x, -(float)z1.y), prevF);
+            sv.x += t.x;
+            sv.y += t.y;
+          }
+          prevF = sv;
+          acc[q].x += sv.x;
+          acc[q].y += sv.y;
         }
-        if (KER == PFMM_STOKES && q == 3) {
-          // f conj(s - c_X) = f conj(s - c_C) + conj(z1) f
-          const double2 cz = make_double2(z1.x, -z1.y);
-          const double2 t = cmul(cz, prev);
-          s.x += t.x;
-          s.y += t.y;
-        }
-        prev = s;
-        acc[q].x += s.x;
-        acc[q].y += s.y;
       }
     }
     if (lane < P)
-      for (int q = 0; q < G; ++q) a.mult[((size_t)X * a.nchan + g0 + q) * P + lane] = acc[q];
+      for (int q = 0; q < G; ++q)
+        a.mult[((size_t)X * a.nchan + g0 + q) * P + lane] =
+            lane == 0 ? accQ[q] : make_double2((double)acc[q].x, (double)acc[q].y);
   }
 }
 
 template <int P, int KER>
 __global__ void __launch_bounds__(32 * kUpWarps) k_fmm_up(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
-  __shared__ double2 shT[kUpWarps][kFmmMaxP], shW[kUpWarps][kFmmMaxP];
+  __shared__ float2 shT[kUpWarps][kFmmMaxP], shW[kUpWarps][kFmmMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nn = a.ctl[C_NNODES];
   const int nw = gridDim.x * kUpWarps;
   for (int X = blockIdx.x * kUpWarps + wib; X < nn; X += nw) {
     if (!is_leaf(a, X)) continue;
     const double r = leaf_radius(a, X, lane);
-    if (lane == 0) a.rad[X] = r;
+    if (lane == 0) {
+      a.rad[X] = r;
+      a.scl[X] = (float)box_scale(r, a.half[X]);
+    }
     if (is_source(a, X)) p2m<P, KER>(a, X, box_scale(r, a.half[X]), lane);
     int cur = X;
     for (;;) {
@@ -718,15 +752,20 @@ __global__ void k_fmm_scatter(FmmArgs a) {
 constexpr int kM2LChunk = 8;
 
 template <int P, int KER>
-__device__ __forceinline__ void m2l_flush(const FmmArgs& a, int X, int g0, int G, int lane, const double2* acc) {
+__device__ __forceinline__ void m2l_flush(const FmmArgs& a, int X, int g0, int G, int lane, const float2* acc) {
   if (lane >= P) return;
   for (int q = 0; q < G; ++q) {
     double2* d = a.loc + ((size_t)X * a.nchan + g0 + q) * P + lane;
-    atomicAdd(&d->x, acc[q].x);
-    atomicAdd(&d->y, acc[q].y);
+    atomicAdd(&d->x, (double)acc[q].x);
+    atomicAdd(&d->y, (double)acc[q].y);
   }
 }
 
+// The entry's geometry is FP32 except the difference of the FP64 box centres
+// (z0 = c_C + l - c_X, |z0| >= (r_X + r_C) / theta, so its FP32 rounding is
+// relative); the chunk's partial sums are FP32 (at most kM2LChunk terms) and
+// are added to the FP64 expansion by the flush.  (FP64 arithmetic here made
+// the pass FP64-pipe bound on this part, whose FP64 rate is ~1/74 of FP32.)
 template <int P, int KER>
 __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
@@ -736,40 +775,40 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
   const int nm = a.ctl[C_NM2L];
   const int G = KER == PFMM_STOKES ? 4 : 1;
   const int nw = gridDim.x * kDownWarps;
+  const int pl = lane < P ? lane : 0;
   for (int e0 = (blockIdx.x * kDownWarps + wib) * kM2LChunk; e0 < nm; e0 += nw * kM2LChunk) {
     const int e1 = min(nm, e0 + kM2LChunk);
     for (int g0 = 0; g0 < a.nchan; g0 += G) {
-      double2 acc[4];
+      float2 acc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+      for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
       int cur = a.gtgt[e0];
       double2 cX = a.ctr[cur];
-      double RX = box_scale(a.rad[cur], a.half[cur]);
+      float RX = a.scl[cur];
       for (int e = e0; e < e1; ++e) {
         const int X = a.gtgt[e];
         if (X != cur) {
           m2l_flush<P, KER>(a, cur, g0, G, lane, acc);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[q] = make_double2(0.0, 0.0);
+          for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
           cur = X;
           cX = a.ctr[X];
-          RX = box_scale(a.rad[X], a.half[X]);
+          RX = a.scl[X];
         }
         const int ci = a.glist[e];
         const int C = ci & kBoxMask, img = ci >> kImgShift;
         const double2 cC = a.ctr[C];
-        const double zx = cC.x + a.off[img][0] - cX.x, zy = cC.y + a.off[img][1] - cX.y;
-        const double RC = box_scale(a.rad[C], a.half[C]);
-        const double iz2 = 1.0 / (zx * zx + zy * zy);
+        const float zx = (float)(cC.x + a.off[img][0] - cX.x), zy = (float)(cC.y + a.off[img][1] - cX.y);
+        const float RC = a.scl[C];
+        const float z2 = zx * zx + zy * zy;
+        const float iz2 = 1.0f / z2;
         // rho_M = -R_C / z0, rho_L = R_X / z0
-        const float2 rM = make_float2((float)(-RC * zx * iz2), (float)(RC * zy * iz2));
-        const float2 rL = make_float2((float)(RX * zx * iz2), (float)(-RX * zy * iz2));
-        const float2 pM = cpowf(rM, lane < P ? lane : 0);
-        const float2 pL = cpowf(rL, lane < P ? lane : 0);
-        const double lgz = 0.5 * log(zx * zx + zy * zy);
-        const float2 z0f = make_float2((float)zx, (float)zy);
+        const float2 rM = make_float2(-RC * zx * iz2, RC * zy * iz2);
+        const float2 rL = make_float2(RX * zx * iz2, -RX * zy * iz2);
+        const float2 pM = cpowf(rM, pl);
+        const float2 pL = cpowf(rL, pl);
+        const float lgz = 0.5f * logf(z2);
         float2 prev = make_float2(0.f, 0.f);
-        double2 prevQ = make_double2(0.0, 0.0);
         for (int q = 0; q < G; ++q) {
           const double2 ak = lane < P ? a.mult[((size_t)C * a.nchan + g0 + q) * P + lane] : make_double2(0.0, 0.0);
           __syncwarp();
@@ -777,10 +816,6 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
           __syncwarp();
           const float2 Q = sT[0];
           float2 sv = make_float2(0.f, 0.f);
-          // the Q log(-z0) constant (real part used), FP64 on lane 0: the bulk of
-          // the box's far potential.  Stokes log channels carry the Stokeslet's
-          // -f/2 in their constant.
-          double2 cq = make_double2(0.0, 0.0);
           if (lane < P) {
 #pragma unroll 4
             for (int k = 1; k < P; ++k) {
@@ -789,8 +824,11 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
               sv.y += b * sT[k].y;
             }
             if (lane == 0) {
-              const double c0 = (KER == PFMM_STOKES && q < 2) ? lgz - 0.5 : lgz;
-              cq = make_double2(ak.x * c0, ak.y * c0);
+              // Q log(z - c_C) about c_X: Q log(-z0) + ...; only its real part is
+              // used.  Stokes log channels carry the Stokeslet's -f/2 in their constant.
+              const float c0 = (KER == PFMM_STOKES && q < 2) ? lgz - 0.5f : lgz;
+              sv.x += Q.x * c0;
+              sv.y += Q.y * c0;
             } else {
               const float il = 1.0f / (float)lane;
               sv = cmulf(pL, make_float2(sv.x - Q.x * il, sv.y - Q.y * il));
@@ -798,16 +836,13 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
           }
           if (KER == PFMM_STOKES && q == 3) {
             // f conj(w - c_X) = f conj(s - c_C) + conj(z0) f
-            const float2 t = cmulf(make_float2(z0f.x, -z0f.y), prev);
+            const float2 t = cmulf(make_float2(zx, -zy), prev);
             sv.x += t.x;
             sv.y += t.y;
-            cq.x += zx * prevQ.x + zy * prevQ.y;
-            cq.y += zx * prevQ.y - zy * prevQ.x;
           }
           prev = sv;
-          prevQ = cq;
-          acc[q].x += (double)sv.x + cq.x;
-          acc[q].y += (double)sv.y + cq.y;
+          acc[q].x += sv.x;
+          acc[q].y += sv.y;
         }
       }
       m2l_flush<P, KER>(a, cur, g0, G, lane, acc);
@@ -817,14 +852,15 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_m2l(FmmArgs a) {
 
 // (b) L2L, one level per launch (parents are final when their level is):
 // one warp per target box of the level adds the translated parent expansion
-// to its own (FP64).
+// to its own.  Coefficients 1 .. p-1 in FP32 (|w| + rho <= 1); the constant
+// term, the bulk of the potential, keeps b_0 of the parent in FP64.
 template <int P, int KER>
 __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_l2l(FmmArgs a, int level) {
   if (a.ctl[C_OVERFLOW]) return;
-  __shared__ double2 shB[kDownWarps][kFmmMaxP], shW[kDownWarps][kFmmMaxP];
+  __shared__ float2 shB[kDownWarps][kFmmMaxP], shW[kDownWarps][kFmmMaxP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double2* sB = shB[wib];
-  double2* sW = shW[wib];
+  float2* sB = shB[wib];
+  float2* sW = shW[wib];
   const int nn = a.ctl[C_NNODES];
   const int nw = gridDim.x * kDownWarps;
   const int G = KER == PFMM_STOKES ? 4 : 1;
@@ -834,41 +870,55 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_l2l(FmmArgs a, int leve
     const int parent = a.par[X];
     if (parent < 0) continue;
     const double2 cX = a.ctr[X], cP = a.ctr[parent];
-    const double RX = box_scale(a.rad[X], a.half[X]);
-    const double RP = box_scale(a.rad[parent], a.half[parent]);
+    const float RP = a.scl[parent];
     const double2 z2 = make_double2(cX.x - cP.x, cX.y - cP.y);
-    const double2 w = make_double2(z2.x / RP, z2.y / RP);
-    const double rm = lane < P ? dpowi(RX / RP, lane) : 0.0;
+    const float2 w = make_float2((float)z2.x / RP, (float)z2.y / RP);
+    const float rm = fpowi(a.scl[X] / RP, lane < P ? lane : 0);
     __syncwarp();
-    if (lane < P) sW[lane] = cpow(w, lane);
+    if (lane < P) sW[lane] = cpowf(w, lane);
     for (int g0 = 0; g0 < a.nchan; g0 += G) {
-      double2 prev = make_double2(0.0, 0.0);
+      float2 prevF = make_float2(0.f, 0.f);
+      double2 prevD = make_double2(0.0, 0.0);
       for (int q = 0; q < G; ++q) {
+        const double2 b = lane < P ? a.loc[((size_t)parent * a.nchan + g0 + q) * P + lane] : make_double2(0.0, 0.0);
         __syncwarp();
-        if (lane < P) sB[lane] = a.loc[((size_t)parent * a.nchan + g0 + q) * P + lane];
+        if (lane < P) sB[lane] = lane == 0 ? make_float2(0.f, 0.f) : make_float2((float)b.x, (float)b.y);
         __syncwarp();
-        double2 sv = make_double2(0.0, 0.0);
+        float2 sv = make_float2(0.f, 0.f);
         if (lane < P) {
-          for (int l = lane; l < P; ++l) {
-            const double b = g_binom.c[l][lane];
-            const double2 t = cmul(sB[l], sW[l - lane]);
-            sv.x += b * t.x;
-            sv.y += b * t.y;
+          for (int l = max(lane, 1); l < P; ++l) {
+            const float bc = g_binom_f.c[l][lane];
+            const float2 t = cmulf(sB[l], sW[l - lane]);
+            sv.x += bc * t.x;
+            sv.y += bc * t.y;
           }
           sv.x *= rm;
           sv.y *= rm;
         }
+        double2 dv = make_double2(0.0, 0.0);
+        if (lane == 0) dv = make_double2(b.x + (double)sv.x, b.y + (double)sv.y);
         if (KER == PFMM_STOKES && q == 3) {
           // f conj(w - c_X) = f conj(w - c_P) - conj(z2) f
-          const double2 t = cmul(make_double2(z2.x, -z2.y), prev);
-          sv.x -= t.x;
-          sv.y -= t.y;
+          if (lane == 0) {
+            dv.x -= z2.x * prevD.x + z2.y * prevD.y;
+            dv.y -= z2.x * prevD.y - z2.y * prevD.x;
+          } else {
+            const float2 t = cmulf(make_float2((float)z2.x, -(float)z2.y), prevF);
+            sv.x -= t.x;
+            sv.y -= t.y;
+          }
         }
-        prev = sv;
+        prevF = sv;
+        prevD = dv;
         if (lane < P) {
           double2* d = a.loc + ((size_t)X * a.nchan + g0 + q) * P + lane;
-          d->x += sv.x;
-          d->y += sv.y;
+          if (lane == 0) {
+            d->x += dv.x;
+            d->y += dv.y;
+          } else {
+            d->x += (double)sv.x;
+            d->y += (double)sv.y;
+          }
         }
       }
     }
@@ -908,6 +958,29 @@ __device__ __forceinline__ void pair_sum(float txh, float txl, float tyh, float 
   }
 }
 
+// (h + l) - (oh + ol) as an unevaluated FP32 pair (two-sum of the high
+// parts, low parts added to its error): the image-shifted target coordinate
+// with ~2^-47 relative precision, no FP64 arithmetic.
+__device__ __forceinline__ void shift_hl(float h, float l, float oh, float ol, float& sh, float& sl) {
+  const float sm = h - oh;
+  const float bb = sm - h;
+  const float err = (h - (sm - bb)) + (-oh - bb);
+  sh = sm;
+  sl = err + (l - ol);
+}
+
+// compensated FP32 sum (Kahan): value() = s - c
+struct KSumF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 template <int P, int KER>
 __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
@@ -931,16 +1004,16 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
     const int pbeg = a.gcnt[a.node_cap + X], pend = a.gcnt[a.node_cap + X + 1];
     for (int t0 = lo; t0 < hi; t0 += kLeafTgt) {
       // this pass: targets t0 .. t0 + kLeafTgt - 1; lane owns slots lane, lane + 32
-      double2 tp[2];
+      float4 thl[2];  // (x_hi, x_lo, y_hi, y_lo) of the lane's two targets
       bool tv[2];
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int t = t0 + lane + 32 * k;
         tv[k] = t < hi;
-        tp[k] = tv[k] ? a.xy[t] : cX;
+        thl[k] = tv[k] ? a.hl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       for (int r = 0; r < a.nrhs; ++r) {
-        double acc[2][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+        KSumF acc[2][3];
         for (int e = pbeg + wib; e < pend; e += kLeafWarps) {
           const int ci = a.glist[e];
           const int C = ci & kBoxMask, img = ci >> kImgShift;
@@ -950,11 +1023,8 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
           float th[2][4];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            const double sx = tp[k].x - a.off[img][0], sy = tp[k].y - a.off[img][1];
-            th[k][0] = (float)sx;
-            th[k][1] = (float)(sx - (double)th[k][0]);
-            th[k][2] = (float)sy;
-            th[k][3] = (float)(sy - (double)th[k][2]);
+            shift_hl(thl[k].x, thl[k].y, a.offh[img][0], a.offl[img][0], th[k][0], th[k][1]);
+            shift_hl(thl[k].z, thl[k].w, a.offh[img][1], a.offl[img][1], th[k][2], th[k][3]);
           }
           for (int c0 = clo; c0 < chi; c0 += 32) {
             __syncwarp();
@@ -972,16 +1042,16 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
               for (int jj = 0; jj < m; ++jj)
                 pair_sum<KER>(th[k][0], th[k][1], th[k][2], th[k][3], s_hl[wib][jj], s_q[wib][0][jj],
                               KER == PFMM_STOKES ? s_q[wib][1][jj] : 0.f, f0, f1, f2);
-              acc[k][0] += (double)f0;
-              acc[k][1] += (double)f1;
-              acc[k][2] += (double)f2;
+              acc[k][0].add(f0);
+              acc[k][1].add(f1);
+              acc[k][2].add(f2);
             }
           }
         }
 #pragma unroll
         for (int k = 0; k < 2; ++k)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) s_red[wib][c][lane + 32 * k] = acc[k][c];
+          for (int c = 0; c < 3; ++c) s_red[wib][c][lane + 32 * k] = acc[k][c].value();
         if (tid < G * P) {
           const int q = tid / P, k = tid % P;
           const double2 b = a.loc[((size_t)X * a.nchan + r * G + q) * P + k];
@@ -1250,6 +1320,7 @@ void fmm_setup(pfmm_plan* p) {
   F.o_ctr = take(NC * sizeof(double2));
   F.o_half = take(NC * 8);
   F.o_rad = take(NC * 8);
+  F.o_scl = take(NC * 4);
   F.o_mult = take((size_t)F.exp_cap * F.nchan * F.p * sizeof(double2));
   F.o_loc = take((size_t)F.exp_cap * F.nchan * F.p * sizeof(double2));
   F.o_front = take((size_t)2 * F.front_cap * sizeof(int2));
@@ -1286,10 +1357,12 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   a.y0 = F.y0;
   a.s0 = F.s0;
   a.ncol = F.ncol;
-  for (int i = 0; i < a.nimg; ++i) {
-    a.off[i][0] = p->geom.off[i][0];
-    a.off[i][1] = p->geom.off[i][1];
-  }
+  for (int i = 0; i < a.nimg; ++i)
+    for (int k = 0; k < 2; ++k) {
+      a.off[i][k] = p->geom.off[i][k];
+      a.offh[i][k] = (float)a.off[i][k];
+      a.offl[i][k] = (float)(a.off[i][k] - (double)a.offh[i][k]);
+    }
   for (int k = 0; k < 4; ++k) a.rot[k] = p->geom.rot[k];
   a.os = p->o_stride;
   a.ctl = (int*)(base + F.o_ctl);
@@ -1313,6 +1386,7 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   a.ctr = (double2*)(base + F.o_ctr);
   a.half = (double*)(base + F.o_half);
   a.rad = (double*)(base + F.o_rad);
+  a.scl = (float*)(base + F.o_scl);
   a.mult = (double2*)(base + F.o_mult);
   a.loc = (double2*)(base + F.o_loc);
   a.front = (int2*)(base + F.o_front);

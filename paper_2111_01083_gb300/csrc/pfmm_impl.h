@@ -110,7 +110,7 @@ struct FmmPlan {
   int64_t m2l_cap, p2p_cap, front_cap;
   // byte offsets inside the region
   size_t o_ctl, o_key, o_val, o_key2, o_val2, o_hist, o_xy, o_hl, o_perm, o_qd, o_qf, o_cnt, o_lf, o_off,
-      o_bsum, o_lo, o_hi, o_lev, o_par, o_nend, o_nch, o_done, o_ctr, o_half, o_rad, o_mult, o_loc, o_front,
+      o_bsum, o_lo, o_hi, o_lev, o_par, o_nend, o_nch, o_done, o_ctr, o_half, o_rad, o_scl, o_mult, o_loc, o_front,
       o_m2l, o_p2p, o_gcnt, o_gcur, o_glist, o_gtgt, o_roots;
   size_t bytes;
 };
