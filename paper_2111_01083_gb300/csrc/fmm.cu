@@ -741,6 +741,38 @@ __global__ void k_fmm_scatter(FmmArgs a) {
   }
 }
 
+// Sort each target box's M2L and P2P segments by their entries (C | image,
+// unique within a segment), one warp per segment, rank by counting in shared
+// memory.  The scatter fills segments in atomic order; sorted, the chunks of
+// the M2L pass and the warps' shares of the leaf pass see the same entries
+// in the same order on every execute, so their FP32 partial sums repeat.
+// Segments longer than kSegMax keep the scatter's order.
+constexpr int kSegMax = 256;
+constexpr int kSortWarps = 4;
+
+__global__ void __launch_bounds__(32 * kSortWarps) k_fmm_sortseg(FmmArgs a) {
+  if (a.ctl[C_OVERFLOW]) return;
+  __shared__ int sk[kSortWarps][kSegMax];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nn = a.ctl[C_NNODES];
+  const int nw = gridDim.x * kSortWarps;
+  for (int idx = blockIdx.x * kSortWarps + wib; idx < 2 * nn; idx += nw) {
+    const int X = idx >> 1;
+    const int64_t base = (idx & 1) ? a.node_cap : 0;
+    const int b = a.gcnt[base + X], e = a.gcnt[base + X + 1], n = e - b;
+    if (n <= 1 || n > kSegMax) continue;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) sk[wib][i] = a.glist[b + i];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+      const int key = sk[wib][i];
+      int rank = 0;
+      for (int j = 0; j < n; ++j) rank += sk[wib][j] < key;
+      a.glist[b + rank] = key;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 10: downward pass.
 // (a) M2L over the flat list grouped by target box: each warp takes
@@ -1463,7 +1495,8 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   e = scan_inplace(a.gcnt, 2 * (int)F.node_cap + 1, a.bsum + cdiv(a.n + 1, kScanBlock) + 4, st, &nl);
   if (e != cudaSuccess) return e;
   k_fmm_scatter<<<grid, 256, 0, st>>>(a);
-  ++nl;
+  k_fmm_sortseg<<<grid, 32 * kSortWarps, 0, st>>>(a);
+  nl += 2;
   rec(6);
   // 10-11 down, leaves
   e = PFMM_FMM_P_DISPATCH(run_down, F.p, K, a, grid, st, &nl, p->prof ? p->ev[7] : nullptr);
