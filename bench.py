@@ -507,7 +507,7 @@ def time_batch(beta, args, dist, dev, local, scale=1.0):
            "near_block_pairs": int(sum(9 * n * n for n in counts)), "near_pairs_evaluated": evaluated,
            "roofline": p2p_roofline("modhelm", 8, False, evaluated, p2p_ms, ms,
                                     "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
-                                    "pairs = those evaluated: triples beyond beta r = 50 are skipped)", sms, clocks),
+                                    "pairs = those evaluated: triples beyond the K0 cutoff are skipped)", sms, clocks),
            "clocks": clocks, "gpu_launches_per_step": nlaunch, "n_sources_total": ns}
     # the operator owns the graph's workspace and phase events: it must live as
     # long as the graph is replayed
@@ -811,7 +811,7 @@ def main():
     else:
         kname = {"mstokes": "k_p2p_ms", "modhelm": "k_p2p_mixed_mh"}.get(kernel, "k_p2p_mixed")
         # modified Helmholtz skips (target block, source tile, image) triples beyond
-        # beta r = 50: its roofline counts the pairs it evaluates
+        # the K0 cutoff: its roofline counts the pairs it evaluates
         npairs = op.pairs() if kernel == "modhelm" else desc["npairs"]
         roof = p2p_roofline(kernel, nrhs, grad, npairs, p2p, ms, f"{kname} (near-image P2P, {nimg} images)",
                             device_sms(dev), clocks,

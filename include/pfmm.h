@@ -351,7 +351,9 @@ pfmm_status pfmm_profile_read(pfmm_plan* plan, float* ms, int n);
 /* Near-image pairs (target, source, image) the P2P evaluated in the last
  * profiled execute on `workspace`: ns * nt * images, except for the mixed
  * modified Helmholtz kernel, which skips (target block, source tile, image)
- * triples beyond beta r = 50 and counts what it evaluates, and for the
+ * triples beyond beta r = x_c (x_c from the tolerance: every skipped term
+ * below tol/10 / (images * ns_max), between 10 and 50) and counts what it
+ * evaluates, and for the
  * tree code, which counts the pairs of neighbouring leaves it sums directly.  Synchronises
  * `stream`.  Errors: PFMM_ERR_INVALID_ARG (NULL, profiling off), PFMM_ERR_CUDA. */
 pfmm_status pfmm_profile_pairs(pfmm_plan* plan, const void* workspace, void* stream, double* pairs);

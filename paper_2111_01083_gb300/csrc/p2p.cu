@@ -328,9 +328,11 @@ __global__ void __launch_bounds__(kP2PThreads, 1) k_p2p_mixed(const __grid_const
 // Modified Helmholtz mixed kernel: one target per thread, targets and sources
 // in spatially sorted order, per-source image sums K0s = sum_i K0(beta r_i),
 // K1x = sum_i K1(beta r_i) dx_i / r_i (and y), then one FMA per rhs (strengths
-// read four at a time).  K0(x) < 1e-22 for x > 50: per (target block, source
+// read four at a time).  Pairs with beta r > x_c are skipped (plan: every skipped
+// term below tol/10 / (images * ns)): per (target block, source
 // tile, image) an FP64 test on the outward-rounded boxes classifies the image
-// as skipped (boxes farther apart than 50 / beta), complete (every pair within
+// as skipped (boxes farther apart than x_c / beta, x_c from the plan: every
+// skipped term below tol/10 / (images * ns)), complete (every pair within
 // the cutoff: no per-pair test) or partial (pairs beyond the cutoff skipped).
 // Two targets per thread in packed FP32 was measured slower here (register
 // pressure halves the resident warps of this branch-heavy kernel).
@@ -379,7 +381,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
     }
   const float beta = a.beta_f;
   const float beta2 = beta * beta;
-  const float cut2 = (50.0f / beta) * (50.0f / beta);
+  const float cut2 = a.cut * a.cut;
   const float4 tb = a.t_box[bx];
   const float rsm = 2.0f / beta * 1.001f + 1e-6f;  // beta r <= 2 region, with margin
   float txr[NIMG], tyr[NIMG];
@@ -399,7 +401,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
         msk = (r2 > 0.0f) ? 1.0f : 0.0f;
         r2 = (r2 > 0.0f) ? r2 : 1.0f;
       }
-      // K0(beta r) < 1e-22 for beta r > 50: such pairs of a partial image are
+      // pairs beyond the cutoff x_c / beta of a partial image are
       // skipped (the branch is not taken at all when no lane of the warp needs it)
       if ((all & (1u << i)) || r2 < cut2) {
         const float x2 = beta2 * r2;
@@ -529,7 +531,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   // Tiles are classified kP2PThreads at a time, one thread per tile: per
   // image, some pair within the cutoff (any) or every pair within it (all).
   // FP32 on the outward-rounded boxes with a relative margin: a tile
-  // misjudged at the margin only adds or drops terms of size K0(50) ~ 1e-22.
+  // misjudged at the margin only adds or drops terms below the cutoff's bound.
   // Culled tiles then cost no barrier.
   __shared__ unsigned s_tany[kP2PThreads], s_tall[kP2PThreads];
   const int ntile = (j1 - j0 + kP2PTile - 1) / kP2PTile;
@@ -1146,7 +1148,7 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
     a.t_perm = self ? (const int*)(ws + L.s_perm) : (const int*)(ws + L.t_perm);
     a.t_box = self ? (const float4*)(ws + L.s_box) : (const float4*)(ws + L.t_box);
   }
-  a.cut = (float)(50.0 / std::max(p->far.beta, 1e-300));
+  a.cut = (float)(p->mh_cut / std::max(p->far.beta, 1e-300));
   for (int i = 0; i < p->geom.nimg; ++i) {
     a.offf[i][0] = (float)p->geom.off[i][0];
     a.offf[i][1] = (float)p->geom.off[i][1];

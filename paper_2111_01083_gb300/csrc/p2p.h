@@ -21,7 +21,7 @@ struct P2PArgs {
   const float2* s_ext;   // [ceil(ns/16)] subtile half extents
   const float4* s_box;   // [ceil(ns/128)] source tile boxes
   const float* qs;       // [nrhs][ncomp][ns] FP32 strengths in sorted order
-  float cut;             // modified Helmholtz: pairs with beta r > 50 are skipped (cut = 50 / beta)
+  float cut;             // modified Helmholtz: pairs with r > cut = x_c / beta are skipped (x_c from the plan)
   const double* src64;   // [2][ns] (FP64 kernel)
   const double* qc;      // [nrhs][ncomp][ns] (FP64 kernel)
   float beta_f;

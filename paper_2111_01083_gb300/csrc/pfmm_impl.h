@@ -144,6 +144,7 @@ struct pfmm_plan {
   double* tw_h;             // [nf/2][2] FFT twiddles (cos, sin)(2 pi k / nf), NUFFT path only
   pfmm::Layout lay;
   pfmm::FmmPlan fmm;        // near field by the tree code (fmm.on)
+  double mh_cut;            // modified Helmholtz P2P: pairs with beta r > mh_cut are skipped
   // host copies of the sort descriptors of the last execute (sources, targets);
   // kept in the plan so that the asynchronous upload reads live memory
   pfmm::SortCell* sort_h;

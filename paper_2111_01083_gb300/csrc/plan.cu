@@ -514,6 +514,17 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   // gradient of the adjoint field at the sources needs [nrhs][2][max n]
   L.adj = take((size_t)nrhs * 2 * std::max(ns_max, nt_max) * sizeof(double) +
                (size_t)nrhs * p->ncomp * std::max(ns_max, nt_max) * sizeof(double));
+  // modified Helmholtz near field: pairs with beta r > x_c are skipped, x_c
+  // chosen so that every skipped term is below tol/10 / (images * ns_max):
+  // even if all the terms a target skips had one sign and that bound, they
+  // would stay below tol/10 in total (K0(x) < sqrt(pi/(2x)) e^-x; fixed point
+  // of x = ln(sqrt(pi/(2x)) / thr)); between 10 and 50.
+  {
+    const double thr = o->tol * 0.1 / ((double)g.nimg * std::max<double>(1.0, (double)ns_max));
+    double x = 30.0;
+    for (int it = 0; it < 30; ++it) x = std::log(std::sqrt(M_PI / (2.0 * x)) / thr);
+    p->mh_cut = std::min(50.0, std::max(10.0, x + 0.5));
+  }
   pfmm::fmm_setup(p);
   L.fmm = take(p->fmm.bytes);
   {

@@ -172,7 +172,7 @@ def test_batch_modhelm_full(beta):
     graph replay, for each beta of the batched workload; the largest cell and
     3 seeded cells, 48 sampled targets each, against the oracle.  At beta =
     100 the south/north far field is pruned (below eps) and the P2P skips
-    (target block, source tile, image) triples beyond beta r = 50, so this is
+    (target block, source tile, image) triples beyond the K0 cutoff, so this is
     the configuration that checks those two shortcuts at full size."""
     import torch
     from paper_2111_01083_gb300 import BatchOp
