@@ -806,7 +806,8 @@ def main():
         # its pairs are the ones it sums directly (counted while profiling)
         npairs = op.pairs()
         roof = p2p_roofline(f"{kernel}_leaf", nrhs, grad, npairs, near_sub["leaves"], ms,
-                            f"k_fmm_leaf (tree-code leaves: L2P + direct sums of neighbouring leaves, {nimg} images)",
+                            f"k_fmm_p2p + k_fmm_l2p (tree-code leaves: direct sums of neighbouring leaves and L2P, "
+                            f"{nimg} images)",
                             device_sms(dev), clocks, None, nimg=nimg)
     else:
         kname = {"mstokes": "k_p2p_ms", "modhelm": "k_p2p_mixed_mh"}.get(kernel, "k_p2p_mixed")

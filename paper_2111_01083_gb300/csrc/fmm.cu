@@ -42,9 +42,10 @@
 //  8 traverse  dual tree sweeps over (target box, source box, image) triples:
 //              accepted -> M2L list, two leaves -> P2P list, else split
 //  9 group     M2L and P2P lists grouped by target box (counting sort)
-// 10 down      per level: L2L from the parent + the box's M2L list
-// 11 leaf      per target leaf: L2P + direct P2P with hi/lo FP32 differences,
-//              added to the outputs (one thread per target, no atomics)
+// 10 down      M2L over the flat grouped list (chunks per warp), then per
+//              level L2L from the parent
+// 11 leaf      per target leaf L2P, then the direct sums of neighbouring
+//              leaves over the flat grouped list with hi/lo FP32 differences
 // 12 fallback  if any list or the box count overran its capacity, the direct
 //              sum over all pairs replaces steps 7-11 (their kernels return early)
 #include <algorithm>
@@ -737,7 +738,7 @@ __global__ void k_fmm_scatter(FmmArgs a) {
     const int64_t slot = (e < nm ? 0 : a.node_cap) + v.x;
     const int pos = a.gcnt[slot] + atomicAdd(a.gcur + slot, 1);
     a.glist[pos] = v.y;
-    if (e < nm) a.gtgt[pos] = v.x;
+    a.gtgt[pos] = v.x;
   }
 }
 
@@ -958,15 +959,9 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_l2l(FmmArgs a, int leve
 }
 
 // ---------------------------------------------------------------------------
-// 11: target leaves: L2P + P2P.  One block per target leaf (grid-stride);
-// the leaf's direct-list entries are spread over the block's warps (entry e
-// to warp e mod kLeafWarps), each warp stages its entry's sources in its own
-// shared-memory slice (no block barrier in the entry loop) and lane l sums
-// targets l and l + 32 of the current pass of kLeafTgt targets.  The warps'
-// partial sums are then added in a fixed order with the L2P value by one
-// thread per target, which writes the output (no atomics).
+// 11: target leaves: L2P (one writer per target), then the direct sums of
+// neighbouring leaves over the flat grouped list (FP64 atomics).
 constexpr int kLeafWarps = 4;
-constexpr int kLeafTgt = 64;
 
 template <int KER>
 __device__ __forceinline__ void pair_sum(float txh, float txl, float tyh, float tyl, float4 s, float q0, float q1,
@@ -1013,145 +1008,188 @@ struct KSumF {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// L2P: one thread per target of a target leaf (block per leaf,
+// grid-stride), the local expansion evaluated and added to the outputs (the
+// far field wrote them before; this is their only writer at this point).
 template <int P, int KER>
-__global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_leaf(FmmArgs a) {
+__global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
   if (a.ctl[C_OVERFLOW]) return;
-  __shared__ float4 s_hl[kLeafWarps][32];
-  __shared__ float s_q[kLeafWarps][2][32];
-  __shared__ double s_red[kLeafWarps][3][kLeafTgt];
   __shared__ float2 s_b[4][kFmmMaxP];
   __shared__ double s_b0[4];
-  __shared__ unsigned long long s_pairs;
   const int nn = a.ctl[C_NNODES];
-  const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-  const int ncomp = KER == PFMM_STOKES ? 2 : 1;
+  const int tid = threadIdx.x;
   const int G = KER == PFMM_STOKES ? 4 : 1;
-  if (tid == 0) s_pairs = 0;
-  unsigned long long my_pairs = 0;
   for (int X = blockIdx.x; X < nn; X += gridDim.x) {
     if (!is_leaf(a, X) || (a.self ? !is_source(a, X) : is_source(a, X))) continue;
     const int lo = a.lo[X], hi = a.hi[X];
     const double2 cX = a.ctr[X];
     const double RX = box_scale(a.rad[X], a.half[X]);
-    const int pbeg = a.gcnt[a.node_cap + X], pend = a.gcnt[a.node_cap + X + 1];
-    for (int t0 = lo; t0 < hi; t0 += kLeafTgt) {
-      // this pass: targets t0 .. t0 + kLeafTgt - 1; lane owns slots lane, lane + 32
-      float4 thl[2];  // (x_hi, x_lo, y_hi, y_lo) of the lane's two targets
-      bool tv[2];
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int t = t0 + lane + 32 * k;
-        tv[k] = t < hi;
-        thl[k] = tv[k] ? a.hl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < a.nrhs; ++r) {
+      __syncthreads();
+      if (tid < G * P) {
+        const int q = tid / P, k = tid % P;
+        const double2 b = a.loc[((size_t)X * a.nchan + r * G + q) * P + k];
+        s_b[q][k] = make_float2((float)b.x, (float)b.y);
+        if (k == 0) s_b0[q] = b.x;
       }
-      for (int r = 0; r < a.nrhs; ++r) {
-        KSumF acc[2][3];
-        for (int e = pbeg + wib; e < pend; e += kLeafWarps) {
-          const int ci = a.glist[e];
-          const int C = ci & kBoxMask, img = ci >> kImgShift;
-          const int clo = a.lo[C], chi = a.hi[C];
-          if (a.count_pairs && r == 0 && lane == 0)
-            my_pairs += (unsigned long long)(min(hi, t0 + kLeafTgt) - t0) * (unsigned long long)(chi - clo);
-          float th[2][4];
+      __syncthreads();
+      for (int t = lo + tid; t < hi; t += blockDim.x) {
+        const double2 tq = a.xy[t];
+        // FP32 Horner for sum_{l>=1} b_l u^l and its derivative (|u| <= 1,
+        // decaying terms); the constant b_0 (the bulk of the potential) in FP64
+        const float2 u = make_float2((float)((tq.x - cX.x) / RX), (float)((tq.y - cX.y) / RX));
+        double2 F[4], D[4];
+        for (int q = 0; q < G; ++q) {
+          float2 f = s_b[q][P - 1], d = make_float2(0.f, 0.f);
+          for (int l = P - 2; l >= 1; --l) {
+            d = cmulf(d, u);
+            d.x += f.x;
+            d.y += f.y;
+            f = cmulf(f, u);
+            f.x += s_b[q][l].x;
+            f.y += s_b[q][l].y;
+          }
+          const float2 fu = cmulf(f, u);
+          const float2 du = cmulf(d, u);
+          F[q] = make_double2(s_b0[q] + (double)fu.x, (double)fu.y);
+          D[q] = make_double2((double)(f.x + du.x) / RX, (double)(f.y + du.y) / RX);
+        }
+        const int o = a.perm[t];
+        const double* R = a.rot;
+        if (KER == PFMM_LAPLACE) {
+          const double o0 = -F[0].x / (2.0 * M_PI), o1 = -D[0].x / (2.0 * M_PI), o2 = D[0].y / (2.0 * M_PI);
+          if (a.pot) a.pot[(size_t)r * a.os + o] += o0;
+          if (a.grad) {
+            a.grad[((size_t)r * 2) * a.os + o] += R[0] * o1 + R[2] * o2;
+            a.grad[((size_t)r * 2 + 1) * a.os + o] += R[1] * o1 + R[3] * o2;
+          }
+        } else {
+          const double2 du = make_double2(tq.x - cX.x, tq.y - cX.y);
+          // conj(u) C_1 - C_d
+          const double2 wv = make_double2(du.x * D[2].x + du.y * D[2].y - D[3].x,
+                                          du.x * D[2].y - du.y * D[2].x - D[3].y);
+          const double o0 = -F[0].x / (4.0 * M_PI) + wv.x / (8.0 * M_PI);
+          const double o1 = -F[1].x / (4.0 * M_PI) - wv.y / (8.0 * M_PI);
+          a.pot[((size_t)r * 2) * a.os + o] += R[0] * o0 + R[2] * o1;
+          a.pot[((size_t)r * 2 + 1) * a.os + o] += R[1] * o0 + R[3] * o1;
+        }
+      }
+    }
+  }
+}
+
+// Direct sums of neighbouring leaves over the flat P2P list grouped by
+// target leaf: each warp takes kP2PChunk consecutive entries (so a leaf with
+// a long list is spread over many warps), lane l sums targets l and l + 32 of
+// the entry's target leaf (leaves with more targets take several passes),
+// sources staged in the warp's slice of shared memory.  Partial sums are
+// compensated FP32 and go to the outputs with FP64 atomics at each change of
+// target leaf and at the end of the chunk.
+constexpr int kP2PChunk = 4;
+
+template <int KER>
+__device__ __forceinline__ void p2p_flush(const FmmArgs& a, int X, int t0, int r, int lane, const KSumF (*acc)[3]) {
+  const int hi = a.hi[X];
+  const double* R = a.rot;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int t = t0 + lane + 32 * k;
+    if (t >= hi) continue;
+    const double n0 = acc[k][0].value(), n1 = acc[k][1].value(), n2 = acc[k][2].value();
+    const int o = a.perm[t];
+    if (KER == PFMM_LAPLACE) {
+      const double o0 = -n0 * (0.69314718055994531 / (4.0 * M_PI)), o1 = -n1 / (2.0 * M_PI), o2 = -n2 / (2.0 * M_PI);
+      if (a.pot) atomicAdd(a.pot + (size_t)r * a.os + o, o0);
+      if (a.grad) {
+        atomicAdd(a.grad + ((size_t)r * 2) * a.os + o, R[0] * o1 + R[2] * o2);
+        atomicAdd(a.grad + ((size_t)r * 2 + 1) * a.os + o, R[1] * o1 + R[3] * o2);
+      }
+    } else {
+      const double o0 = -n0 / (4.0 * M_PI), o1 = -n1 / (4.0 * M_PI);
+      atomicAdd(a.pot + ((size_t)r * 2) * a.os + o, R[0] * o0 + R[2] * o1);
+      atomicAdd(a.pot + ((size_t)r * 2 + 1) * a.os + o, R[1] * o0 + R[3] * o1);
+    }
+  }
+}
+
+template <int P, int KER>
+__global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_p2p(FmmArgs a) {
+  if (a.ctl[C_OVERFLOW]) return;
+  __shared__ float4 s_hl[kLeafWarps][32];
+  __shared__ float s_q[kLeafWarps][2][32];
+  __shared__ unsigned long long s_pairs;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int ncomp = KER == PFMM_STOKES ? 2 : 1;
+  const int64_t pb = a.gcnt[a.node_cap], pe = a.gcnt[2 * a.node_cap];  // the P2P part of the grouped list
+  const int np = (int)(pe - pb);
+  const int nw = gridDim.x * kLeafWarps;
+  if (threadIdx.x == 0) s_pairs = 0;
+  __syncthreads();
+  unsigned long long my_pairs = 0;
+  for (int c0e = (blockIdx.x * kLeafWarps + wib) * kP2PChunk; c0e < np; c0e += nw * kP2PChunk) {
+    const int c1e = min(np, c0e + kP2PChunk);
+    for (int r = 0; r < a.nrhs; ++r) {
+      // the chunk's entries, in order; a leaf with more than 64 targets is
+      // summed in passes of 64 (t0), each pass over the chunk's entries of it
+      int e = c0e;
+      while (e < c1e) {
+        const int X = a.gtgt[pb + e];
+        int ee = e + 1;
+        while (ee < c1e && a.gtgt[pb + ee] == X) ++ee;
+        const int lo = a.lo[X], hi = a.hi[X];
+        for (int t0 = lo; t0 < hi; t0 += 64) {
+          float4 thl[2];
+          bool tv[2];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
-            shift_hl(thl[k].x, thl[k].y, a.offh[img][0], a.offl[img][0], th[k][0], th[k][1]);
-            shift_hl(thl[k].z, thl[k].w, a.offh[img][1], a.offl[img][1], th[k][2], th[k][3]);
+            const int t = t0 + lane + 32 * k;
+            tv[k] = t < hi;
+            thl[k] = tv[k] ? a.hl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
           }
-          for (int c0 = clo; c0 < chi; c0 += 32) {
-            __syncwarp();
-            const int j = c0 + lane;
-            if (j < chi) {
-              s_hl[wib][lane] = a.hl[j];
-              for (int c = 0; c < ncomp; ++c) s_q[wib][c][lane] = a.qf[((size_t)r * ncomp + c) * a.ns + j];
-            }
-            __syncwarp();
-            const int m = min(32, chi - c0);
+          KSumF acc[2][3];
+          for (int j = e; j < ee; ++j) {
+            const int ci = a.glist[pb + j];
+            const int C = ci & kBoxMask, img = ci >> kImgShift;
+            const int clo = a.lo[C], chi = a.hi[C];
+            if (a.count_pairs && r == 0 && lane == 0)
+              my_pairs += (unsigned long long)(min(hi, t0 + 64) - t0) * (unsigned long long)(chi - clo);
+            float th[2][4];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-              if (!tv[k]) continue;
-              float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-              for (int jj = 0; jj < m; ++jj)
-                pair_sum<KER>(th[k][0], th[k][1], th[k][2], th[k][3], s_hl[wib][jj], s_q[wib][0][jj],
-                              KER == PFMM_STOKES ? s_q[wib][1][jj] : 0.f, f0, f1, f2);
-              acc[k][0].add(f0);
-              acc[k][1].add(f1);
-              acc[k][2].add(f2);
+              shift_hl(thl[k].x, thl[k].y, a.offh[img][0], a.offl[img][0], th[k][0], th[k][1]);
+              shift_hl(thl[k].z, thl[k].w, a.offh[img][1], a.offl[img][1], th[k][2], th[k][3]);
             }
-          }
-        }
+            for (int cs = clo; cs < chi; cs += 32) {
+              __syncwarp();
+              const int jj0 = cs + lane;
+              if (jj0 < chi) {
+                s_hl[wib][lane] = a.hl[jj0];
+                for (int c = 0; c < ncomp; ++c) s_q[wib][c][lane] = a.qf[((size_t)r * ncomp + c) * a.ns + jj0];
+              }
+              __syncwarp();
+              const int m = min(32, chi - cs);
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) s_red[wib][c][lane + 32 * k] = acc[k][c].value();
-        if (tid < G * P) {
-          const int q = tid / P, k = tid % P;
-          const double2 b = a.loc[((size_t)X * a.nchan + r * G + q) * P + k];
-          s_b[q][k] = make_float2((float)b.x, (float)b.y);
-          if (k == 0) s_b0[q] = b.x;
-        }
-        __syncthreads();
-        if (tid < kLeafTgt && t0 + tid < hi) {
-          const int t = t0 + tid;
-          const double2 tq = a.xy[t];
-          double n0 = 0.0, n1 = 0.0, n2 = 0.0;
-          for (int w = 0; w < kLeafWarps; ++w) {
-            n0 += s_red[w][0][tid];
-            n1 += s_red[w][1][tid];
-            n2 += s_red[w][2][tid];
-          }
-          // L2P: FP32 Horner for sum_{l>=1} b_l u^l and its derivative (|u| <= 1,
-          // decaying terms); the constant b_0 (the bulk of the potential) in FP64
-          const float2 u = make_float2((float)((tq.x - cX.x) / RX), (float)((tq.y - cX.y) / RX));
-          double2 F[4], D[4];
-          for (int q = 0; q < G; ++q) {
-            float2 f = s_b[q][P - 1], d = make_float2(0.f, 0.f);
-            for (int l = P - 2; l >= 1; --l) {
-              d = cmulf(d, u);
-              d.x += f.x;
-              d.y += f.y;
-              f = cmulf(f, u);
-              f.x += s_b[q][l].x;
-              f.y += s_b[q][l].y;
+              for (int k = 0; k < 2; ++k) {
+                if (!tv[k]) continue;
+                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                for (int jj = 0; jj < m; ++jj)
+                  pair_sum<KER>(th[k][0], th[k][1], th[k][2], th[k][3], s_hl[wib][jj], s_q[wib][0][jj],
+                                KER == PFMM_STOKES ? s_q[wib][1][jj] : 0.f, f0, f1, f2);
+                acc[k][0].add(f0);
+                acc[k][1].add(f1);
+                acc[k][2].add(f2);
+              }
             }
-            const float2 fu = cmulf(f, u);
-            const float2 du = cmulf(d, u);
-            F[q] = make_double2(s_b0[q] + (double)fu.x, (double)fu.y);
-            D[q] = make_double2((double)(f.x + du.x) / RX, (double)(f.y + du.y) / RX);
           }
-          double o0, o1, o2 = 0.0;
-          if (KER == PFMM_LAPLACE) {
-            o0 = -F[0].x / (2.0 * M_PI) - n0 * (0.69314718055994531 / (4.0 * M_PI));
-            o1 = -D[0].x / (2.0 * M_PI) - n1 / (2.0 * M_PI);
-            o2 = D[0].y / (2.0 * M_PI) - n2 / (2.0 * M_PI);
-          } else {
-            const double2 du = make_double2(tq.x - cX.x, tq.y - cX.y);
-            // conj(u) C_1 - C_d
-            const double2 wv = make_double2(du.x * D[2].x + du.y * D[2].y - D[3].x,
-                                            du.x * D[2].y - du.y * D[2].x - D[3].y);
-            o0 = -F[0].x / (4.0 * M_PI) + wv.x / (8.0 * M_PI) - n0 / (4.0 * M_PI);
-            o1 = -F[1].x / (4.0 * M_PI) - wv.y / (8.0 * M_PI) - n1 / (4.0 * M_PI);
-          }
-          const int o = a.perm[t];
-          const double* R = a.rot;
-          if (KER == PFMM_LAPLACE) {
-            if (a.pot) a.pot[(size_t)r * a.os + o] += o0;
-            if (a.grad) {
-              a.grad[((size_t)r * 2) * a.os + o] += R[0] * o1 + R[2] * o2;
-              a.grad[((size_t)r * 2 + 1) * a.os + o] += R[1] * o1 + R[3] * o2;
-            }
-          } else {
-            a.pot[((size_t)r * 2) * a.os + o] += R[0] * o0 + R[2] * o1;
-            a.pot[((size_t)r * 2 + 1) * a.os + o] += R[1] * o0 + R[3] * o1;
-          }
+          p2p_flush<KER>(a, X, t0, r, lane, acc);
         }
-        __syncthreads();
+        e = ee;
       }
     }
   }
   if (a.count_pairs && lane == 0 && my_pairs) atomicAdd(&s_pairs, my_pairs);
   __syncthreads();
-  if (a.count_pairs && tid == 0 && s_pairs) atomicAdd((unsigned long long*)(a.ctl + C_PAIRS), s_pairs);
+  if (a.count_pairs && threadIdx.x == 0 && s_pairs) atomicAdd((unsigned long long*)(a.ctl + C_PAIRS), s_pairs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1261,8 +1299,9 @@ cudaError_t run_down(const FmmArgs& a, int grid, cudaStream_t st, int* nl, cudaE
   k_fmm_m2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a);
   for (int l = 1; l <= kFmmL; ++l) k_fmm_l2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a, l);
   if (mid) cudaEventRecord(mid, st);
-  k_fmm_leaf<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
-  *nl += kFmmL + 2;
+  k_fmm_l2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
+  k_fmm_p2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
+  *nl += kFmmL + 3;
   return cudaGetLastError();
 }
 
@@ -1361,7 +1400,7 @@ void fmm_setup(pfmm_plan* p) {
   F.o_gcnt = take((2 * NC + 1) * 4);
   F.o_gcur = take(2 * NC * 4);
   F.o_glist = take((size_t)(F.m2l_cap + F.p2p_cap) * sizeof(int));
-  F.o_gtgt = take((size_t)F.m2l_cap * sizeof(int));
+  F.o_gtgt = take((size_t)(F.m2l_cap + F.p2p_cap) * sizeof(int));
   F.o_roots = take(512 * 4);
   F.bytes = off;
 }
