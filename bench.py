@@ -710,9 +710,27 @@ def main():
     out = op(S, Q, T, grad=grad)
     torch.cuda.synchronize()
     op.status()
-    for _ in range(max(0, args.warmup - 1)):
+    # eager executes (one library call per step), for reference
+    eager = []
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         op(S, Q, T, grad=grad, out=out)
+        e1.record()
+        e1.synchronize()
+        eager.append(e0.elapsed_time(e1))
+    eager_ms = statistics.median(eager[1:])
+    nlaunch_step = op.describe()["nlaunch"]
+    # the timed step: one replay of the execute captured in a CUDA graph (the
+    # many small launches of the tree code and the far field are replayed
+    # without per-launch host overhead); phases from the graph's event nodes
+    graph, out = op.capture(S, Q, T, grad=grad, out=out)
+    for _ in range(max(0, args.warmup - 1)):
+        graph.replay()
     torch.cuda.synchronize()
+    op.status()
 
     clk_path = os.path.join(tempfile.gettempdir(), f"pfmm_clocks_{os.getpid()}.csv")
     proc, fh = start_clocks(clk_path)
@@ -727,7 +745,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        op(S, Q, T, grad=grad, out=out)
+        graph.replay()
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -735,7 +753,7 @@ def main():
         far_ms.append(ph[1])
         p2p_ms.append(ph[2])
         sub_ms.append(ph[3:])
-        launches += op.describe()["nlaunch"]
+        launches += nlaunch_step
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -855,6 +873,8 @@ def main():
                    "west_east": "rotated (e2-perp)" if desc["we_rotated"] else "axis (e1)",
                    "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
         "phases_ms": {"far_field": sum(far_ms) / len(far_ms), "near_field": p2p},
+        "execution": "CUDA-graph replay of one execute per step (PeriodicOp.capture)",
+        "eager_ms_per_step": eager_ms,
         "near_field": {"method": "tree code" if desc["near_fmm"] else "direct P2P", "phases_ms": near_sub,
                        "stats": near_stats, "order": desc["near_order"] if desc["near_fmm"] else None,
                        "leaf": desc["near_leaf"] if desc["near_fmm"] else None},

@@ -1298,7 +1298,7 @@ cudaError_t run_down(const FmmArgs& a, int grid, cudaStream_t st, int* nl, cudaE
   if (e != cudaSuccess) return e;
   k_fmm_m2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a);
   for (int l = 1; l <= kFmmL; ++l) k_fmm_l2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a, l);
-  if (mid) cudaEventRecord(mid, st);
+  if (mid) record_event(mid, st);
   k_fmm_l2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
   k_fmm_p2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
   *nl += kFmmL + 3;
@@ -1511,7 +1511,7 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   if (e != cudaSuccess) return e;
   k_fmm_fill<<<cdiv(a.n, 256), 256, 0, st>>>(a);
   ++nl;
-  auto rec = [&](int i) { if (p->prof) cudaEventRecord(p->ev[i], st); };
+  auto rec = [&](int i) { if (p->prof) record_event(p->ev[i], st); };
   rec(4);
   // 7 up
   int dev = 0, sms = 152;

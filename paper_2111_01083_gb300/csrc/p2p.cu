@@ -1232,8 +1232,23 @@ cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, boo
     // spatial sort of the sources (and modified Helmholtz targets) of this cell
     const int nc = fill_sort_cells(p, ws, ns, nt, self, 0, ns, p->sort_h);
     SortCell* dcells = (SortCell*)(ws + p->lay.sortd);
-    cudaError_t e = cudaMemcpyAsync(dcells, p->sort_h, nc * sizeof(SortCell), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
+    // the descriptors depend only on (workspace, ns, nt, self): under stream
+    // capture they must be the ones an eager execute uploaded (a copy from
+    // pageable host memory cannot be captured)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    cudaError_t e = cudaSuccess;
+    if (cap != cudaStreamCaptureStatusNone) {
+      if (!(p->sort_ws == ws && p->sort_ns == ns && p->sort_nt == nt && p->sort_self == self))
+        return cudaErrorStreamCaptureUnsupported;
+    } else {
+      e = cudaMemcpyAsync(dcells, p->sort_h, nc * sizeof(SortCell), cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return e;
+      p->sort_ws = ws;
+      p->sort_ns = ns;
+      p->sort_nt = nt;
+      p->sort_self = self;
+    }
     e = sort_cells(dcells, p->sort_h, nc, ns + (nc > 1 ? nt : 0), ws + p->lay.sortscr, st, &sort_launches);
     if (e != cudaSuccess) return e;
   }

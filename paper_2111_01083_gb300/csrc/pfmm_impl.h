@@ -145,6 +145,13 @@ struct pfmm_plan {
   pfmm::Layout lay;
   pfmm::FmmPlan fmm;        // near field by the tree code (fmm.on)
   double mh_cut;            // modified Helmholtz P2P: pairs with beta r > mh_cut are skipped
+  // what the last eager execute left in a workspace (a captured execute
+  // reuses it instead of uploading from pageable host memory): the node
+  // tables, and the P2P sort descriptors for (workspace, ns, nt, self)
+  mutable const char* tables_ws;
+  mutable const char* sort_ws;
+  mutable int64_t sort_ns, sort_nt;
+  mutable bool sort_self;
   // host copies of the sort descriptors of the last execute (sources, targets);
   // kept in the plan so that the asynchronous upload reads live memory
   pfmm::SortCell* sort_h;
@@ -172,6 +179,16 @@ inline size_t off_twiddle(const pfmm_plan* p) {
 }
 inline size_t node_region_bytes(const pfmm_plan* p) {
   return off_twiddle(p) + (p->tw_h ? (size_t)p->nf * sizeof(double) : 0);
+}
+
+// Record a profiling event on st; under stream capture as an external event
+// node, so that every replay of the graph records it (a plain record during
+// capture only orders the graph's nodes).
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+  return cap != cudaStreamCaptureStatusNone ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+                                            : cudaEventRecord(ev, st);
 }
 
 // kernels.cu entry points (host-side launchers)

@@ -238,12 +238,23 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
   e = cudaMemsetAsync(ws + p->lay.coef, 0, p->lay.wts - p->lay.coef, st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   if (upload) {
-    e = upload_tables(p, ws, st);
-    if (e != cudaSuccess) return cuda_fail(e, "upload tables");
+    // Under stream capture the tables must already be in this workspace (an
+    // eager execute on it put them there): a copy from pageable host memory
+    // cannot be captured.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) cap = cudaStreamCaptureStatusActive;
+    if (cap != cudaStreamCaptureStatusNone) {
+      if (p->tables_ws != ws)
+        return fail(PFMM_ERR_INVALID_ARG, "stream capture: execute once on this workspace before capturing");
+    } else {
+      e = upload_tables(p, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "upload tables");
+      p->tables_ws = ws;
+    }
   }
   p->nlaunch = 0;
   p->npairs = 0;
-  auto rec = [&](int i) { if (p->prof) cudaEventRecord(p->ev[i], st); };
+  auto rec = [&](int i) { if (p->prof) record_event(p->ev[i], st); };
   rec(0);
   if (nt == 0) {
     rec(1); rec(2); rec(3);

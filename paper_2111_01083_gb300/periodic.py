@@ -215,6 +215,24 @@ class PeriodicOp:
         _lib.check(_lib.lib().pfmm_profile_pairs(self._h, _ptr(ws), ctypes.c_void_p(st), ctypes.byref(v)))
         return float(v.value)
 
+    def capture(self, src, q, trg=None, grad=True, out=None):
+        """Record one execute in a CUDA graph, after an eager execute on the
+        same buffers (which uploads the plan's tables into its workspace; the
+        captured execute reuses them).  Replaying the graph re-runs the
+        operator on the current contents of src, q, trg into out.  Another plan
+        must not use this workspace between replays.  Returns (graph, out)."""
+        import torch
+        out = self(src, q, trg, grad=grad, out=out)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream(src.device)
+        s.wait_stream(torch.cuda.current_stream(src.device))
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(graph, stream=s):
+                self(src, q, trg, grad=grad, out=out, stream=s.cuda_stream)
+        torch.cuda.current_stream(src.device).wait_stream(s)
+        return graph, out
+
     def near_stats(self, stream=None):
         """Tree-code statistics of the last execute (pfmm_near_stats; synchronises):
         boxes, M2L interactions, directly summed leaf pairs, directly summed
