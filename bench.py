@@ -145,6 +145,8 @@ def parse():
                     help="override the west/east plane-wave direction")
     ap.add_argument("--no-batch", action="store_true",
                     help="default workload: skip the batched modified-Helmholtz sub-records")
+    ap.add_argument("--near", default="auto", choices=["auto", "direct", "fmm"],
+                    help="near-image sum: direct P2P or the tree code (auto: the library's rule)")
     return ap.parse_args()
 
 
@@ -704,7 +706,7 @@ def main():
     nrhs = int(Q.shape[0])
     op = PeriodicOp(kernel, w["e1"], w["e2"], beta=beta, tol=cfg["tol"], precision="mixed", path=path,
                     nufft_w=cfg.get("nufft_w", 0), n_gl=cfg.get("n_gl", 0), ns_max=ns, nt_max=nt, singly=singly,
-                    we=we, nrhs=nrhs)
+                    we=we, nrhs=nrhs, near=args.near)
     op.profile(True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = op(S, Q, T, grad=grad)

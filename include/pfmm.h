@@ -78,7 +78,9 @@ typedef enum { PFMM_FP64 = 0, PFMM_MIXED = 1 } pfmm_precision;
 /* Far-field south/north application: DIRECT = L (D (R q)) (Sec. 6);
  * NUFFT = GL anterpolation + ES-kernel NUFFT (Sec. 6, Eqs. fastanterp and
  * fastinterp), for all four kernels.  AUTO picks NUFFT when M >= 64 and the
- * fine grid (power of two >= 2 (2M + 1)) has at most 8192 points. */
+ * fine grid (power of two >= 2 (2M + 1)) has at most 8192 points.  For the
+ * singly periodic operator the path applies to its west/east parts (see
+ * PFMM_SINGLY_PERIODIC). */
 typedef enum { PFMM_PATH_AUTO = 0, PFMM_PATH_DIRECT = 1, PFMM_PATH_NUFFT = 2 } pfmm_path;
 
 /* flags */
@@ -94,8 +96,12 @@ enum {
                                PFMM_ERR_INVALID_ARG.  Near images m e1, |m| <= 1; the far
                                images through the west/east factorization restricted to
                                the image row n = 0 (Theorems west_thm, west_thm_lap,
-                               west_thm_s), no south/north parts; direct path only;
-                               single-cell calls only (not in a batch). */
+                               west_thm_s), no south/north parts; single-cell calls
+                               only (not in a batch).  The NUFFT path (Sec. 6.1 with x
+                               and y exchanged, for strips with eta >> d) takes the
+                               west/east sums through GL lines in x, a type-1 transform
+                               in y and ES interpolation onto the quadrature nodes; AUTO
+                               picks it when at least 128 nodes qualify. */
   PFMM_WE_ROTATED = 32,    /* west/east plane waves decay along e2-perp instead of e1
                                (App. A, Eq. k0west2): the near block is 3 x 3 images
                                (m0 = 1) for every parallelogram, at the price of more
@@ -178,6 +184,9 @@ typedef struct {
   int near_order;       /* its expansion terms p                                    */
   int near_leaf;        /* its leaf size                                            */
   double near_theta;    /* its acceptance parameter                                 */
+  int p1_nufft_nodes;   /* singly periodic operator on the NUFFT path: west/east nodes
+                           whose sums go through the transforms (the others, lambda below
+                           (w/2 + 2) pi / eta, stay direct); 0 otherwise                 */
 } pfmm_plan_desc;
 
 typedef struct pfmm_plan pfmm_plan;

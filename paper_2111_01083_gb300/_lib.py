@@ -45,7 +45,8 @@ class PlanDesc(ctypes.Structure):
                 ("nufft_w", ctypes.c_int), ("es_beta", ctypes.c_double), ("nlaunch", ctypes.c_int),
                 ("npairs", ctypes.c_int64), ("we_rotated", ctypes.c_int), ("we_dir", ctypes.c_double * 2),
                 ("near_fmm", ctypes.c_int), ("near_order", ctypes.c_int), ("near_leaf", ctypes.c_int),
-                ("near_theta", ctypes.c_double)]
+                ("near_theta", ctypes.c_double),
+                ("p1_nufft_nodes", ctypes.c_int)]
 
 
 class PfmmError(RuntimeError):

@@ -29,7 +29,7 @@ namespace pfmm {
 // ----------------------------------------------------------------------------
 __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* __restrict__ pts, double* __restrict__ c64,
                               float* __restrict__ cf, int* __restrict__ U,
-                              int* __restrict__ status) {
+                              int* __restrict__ status, int* __restrict__ V, double invY) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = pts[i], y = pts[istride + i];
@@ -57,6 +57,9 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   double v = xc / g.d;
   v -= floor(v + 0.5);
   U[i] = (int)(unsigned)(long long)llrint(v * 4294967296.0);
+  // singly periodic NUFFT: fixed-point phase 2^32 y / Y of the transform in y
+  // (|y| < eta/2 = Y/4, so the signed value is exact to 2^-32 Y)
+  if (V) V[i] = (int)llrint(yc * invY * 4294967296.0);
 }
 
 // Optional projection to zero net charge / force: net sums per rhs and
@@ -568,12 +571,15 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   const Layout& L = p->lay;
   int* status = (int*)(ws + L.status);
   bool mixed = p->opts.precision == PFMM_MIXED;
+  const bool wantV = p->p1_nu && p->path == PFMM_PATH_NUFFT;
+  const double invY = p->p1_nu ? 1.0 / p->p1_Y : 0.0;
   k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
-                                                 (int*)(ws + L.srcU),
-                                                 status);
+                                                 (int*)(ws + L.srcU), status,
+                                                 wantV ? (int*)(ws + L.srcV) : nullptr, invY);
   if (!self && nt > 0)
     k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
-                                                   (int*)(ws + L.trgU), status);
+                                                   (int*)(ws + L.trgU), status,
+                                                   wantV ? (int*)(ws + L.trgV) : nullptr, invY);
   g_launches = (!self && nt > 0) ? 3 : 2;
   const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) &&
                       (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);

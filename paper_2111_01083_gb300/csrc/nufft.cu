@@ -49,7 +49,33 @@ struct NufftArgs {
   const double* gl;      // [n_gl][2] (ybar_n, sigma_n)
   const double* phihat;  // [M+1] phihat(alpha k), k = 0..M
   const double* tw;      // [nf/2][2] (cos, sin)(2 pi k / nf)
+  // singly periodic west/east: Chebyshev coefficients [kRhoCheb] of 1/Psi(y)
+  // in t = rho_c y (NULL otherwise), applied to the GL weights of every point
+  const double* rho;
+  double rho_c;
 };
+
+// Transform coordinate in FP64: the FP32 path reads it from the signed
+// fixed-point phase U = 2^32 y / Y (singly periodic transforms only, |y| < Y/4).
+template <typename T>
+__device__ __forceinline__ double spread_coord(T x, int U, const NufftArgs& a) {
+  if constexpr (sizeof(T) == 4)
+    return (double)U * (a.d * 2.3283064365386963e-10);
+  else
+    return (double)x;
+}
+
+// 1/Psi(y) by Clenshaw's recurrence on the plan's Chebyshev series.
+__device__ __forceinline__ double rho_at(const NufftArgs& a, double y) {
+  const double t = y * a.rho_c, t2 = 2.0 * t;
+  double b1 = 0.0, b2 = 0.0;
+  for (int k = kRhoCheb - 1; k >= 1; --k) {
+    const double b0 = fma(t2, b1, a.rho[k] - b2);
+    b2 = b1;
+    b1 = b0;
+  }
+  return fma(t, b1, a.rho[0] - b2);
+}
 
 // Position on the fine grid, u = theta / h = nf x / d (mod nf), split as
 // u = i + f with i an integer and 0 <= f <= 1.  FP32 path: from the 32-bit
@@ -150,6 +176,11 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
       grid_pos(x, sU[j], a, &gi, &gf);
       const int l0 = es_weights<T, WA>(gi, gf, w, beta, ker);
       bary<T, GA>(y, a.gl, ngl, gam);
+      if (a.rho) {
+        const T rh = (T)rho_at(a, spread_coord(x, sU[j], a));
+#pragma unroll
+        for (int n = 0; n < GA; ++n) gam[n] *= rh;
+      }
       for (int vv = 0; vv < nvg; ++vv) {
         const int v = v0 + vv, r = v / a.nch, c = v % a.nch;
         const T q0 = qv[((size_t)r * ncomp + (c & 1)) * a.ns + j];
@@ -392,6 +423,11 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
   grid_pos(x, tU[l], a, &gi, &gf);
   const int l0 = es_weights<T, WA>(gi, gf, w, (T)a.es_beta, ker);
   bary<T, GA>(y, a.gl, ngl, gam);
+  if (a.rho) {
+    const T rh = (T)rho_at(a, spread_coord(x, tU[l], a));
+#pragma unroll
+    for (int n = 0; n < GA; ++n) gam[n] *= rh;
+  }
   int li[WA];
 #pragma unroll
   for (int k = 0; k < WA; ++k) li[k] = (l0 + k) & (a.nf - 1);
@@ -474,6 +510,169 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
       grad[((size_t)r * 2 + 1) * a.os + l] += R[1] * gxd + R[3] * gyd;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Singly periodic operator, west/east parts through the transforms (Sec. 6.1
+// with x and y exchanged; Theorems west_thm, west_thm_lap, west_thm_s on the
+// image row n = 0).  The plane waves e^{-+kappa_n x} e^{i lambda_n y} are
+// smooth in x (GL lines xbar_k on [-d/2, d/2], barycentric weights in x) and
+// oscillatory in y, at the piecewise-GL quadrature nodes lambda_n.  Per GL
+// line the sums over sources S_k(lambda) = sum_j gamma(x'_j, k) q_j e^{-i lambda y'_j}
+// are a type-3 transform: with psi the ES kernel in lambda (half-width
+// alpha = w dl / 2, dl = 2 pi / Y) and Psi(y) its Fourier transform,
+//   S_k(lambda) ~= dl sum_u psi(lambda - u dl) F_k(u),
+//   F_k(u) = sum_j gamma(x'_j, k) (q_j / Psi(y'_j)) e^{-i u dl y'_j}
+// (Poisson summation; the aliases Psi(y - p Y) / Psi(y), p != 0, are below the
+// ES kernel's error for |y| <= Y/4), and F_k is the type-1 transform of the
+// south/north path with y as the transform coordinate over the period Y.
+// The evaluation is the adjoint: sum_n V(n) e^{i lambda_n y} ~= (1/Psi(y)) Re-part
+// of the type-2 transform of H(u) = dl sum_n psi(lambda_n - u dl) V(n).
+// ---------------------------------------------------------------------------
+
+// Formation and weights at the nodes.  One thread per (node n = nq0 + j, rhs):
+//   c^W_n = sum_k e^{ kappa_n xbar_k} S_k(lambda_n),  c^E_n = sum_k e^{-kappa_n xbar_k} S_k(lambda_n)
+// (Stokes: the channels f_x, f_y, x' f_x, x' f_y give c_a and c_b), w = D c
+// with the row-0 blocks of the direct path, and the evaluation lines
+//   V_k(n) = w^W_n e^{-kappa_n xbar_k} + w^E_n e^{kappa_n xbar_k}
+// with kappa_n (w^E e^{kappa xbar} - w^W e^{-kappa xbar}) the x-derivative line
+// (scalar), or the a_x, a_y, b_x, b_y lines (Stokes), written to
+// lines[r][line][j].  The ES weights are FP64 (the node count is small).
+template <int KER>
+__global__ void k_p1_modes(NufftArgs a, Geom g, const double* __restrict__ nodes, int nq0, int nnu, double dl,
+                           double alpha, const double2* __restrict__ Fk, double2* __restrict__ lines) {
+  constexpr int NCH = KER == PFMM_STOKES ? 4 : 1;
+  constexpr int WU = 17;  // frequencies in a window of width 2 alpha = w dl, w <= 16
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= nnu) return;
+  const int n = nq0 + j;
+  const double lam = nodes[2 * n], wq = nodes[2 * n + 1];
+  const double kap = (KER == PFMM_MODHELM) ? sqrt(lam * lam + a.beta * a.beta) : lam;
+  const int u0 = max(1, (int)ceil((lam - alpha) / dl));
+  const int u1 = min(min(a.M, (int)floor((lam + alpha) / dl)), u0 + WU - 1);
+  double psi[WU];
+#pragma unroll
+  for (int i = 0; i < WU; ++i) {
+    const double z = (lam - (u0 + i) * dl) / alpha, t = 1.0 - z * z;
+    psi[i] = (u0 + i <= u1 && t > 0.0) ? dl * exp(a.es_beta * (sqrt(t) - 1.0)) : 0.0;
+  }
+  dcx cW[NCH], cE[NCH];
+#pragma unroll
+  for (int c = 0; c < NCH; ++c) cW[c] = cE[c] = dcx{0, 0};
+  for (int k = 0; k < a.n_gl; ++k) {
+    const double xb = a.gl[2 * k];
+    const double ep = exp(kap * xb), em = exp(-kap * xb);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+      const double2* F = Fk + (((size_t)r * a.nch + c) * a.n_gl + k) * (a.M + 1);
+      dcx sk{0, 0};
+#pragma unroll
+      for (int i = 0; i < WU; ++i)
+        if (u0 + i <= u1) {
+          const double2 f = F[u0 + i];
+          sk = cadd(sk, dcx{psi[i] * f.x, psi[i] * f.y});
+        }
+      cW[c] = cadd(cW[c], cscale(sk, ep));
+      cE[c] = cadd(cE[c], cscale(sk, em));
+    }
+  }
+  const lw::WeFrame fr{g.wdx, g.wdy, g.wxr, g.wyr};
+  const int ngl = a.n_gl;
+  if (KER != PFMM_STOKES) {
+    double2* out = lines + (size_t)r * 2 * ngl * nnu;
+    const dcx wW = cmul(lw::we_scalar(fr, g.m0, lam, kap, wq, false, false), cW[0]);
+    const dcx wE = cmul(lw::we_scalar(fr, g.m0, lam, kap, wq, true, false), cE[0]);
+    for (int k = 0; k < ngl; ++k) {
+      const double xb = a.gl[2 * k];
+      const dcx vw = cscale(wW, exp(-kap * xb)), ve = cscale(wE, exp(kap * xb));
+      const dcx v = cadd(vw, ve), vx = cscale(csub(ve, vw), kap);
+      out[(size_t)k * nnu + j] = make_double2(v.r, v.i);
+      out[(size_t)(ngl + k) * nnu + j] = make_double2(vx.r, vx.i);
+    }
+    return;
+  }
+  double2* out = lines + (size_t)r * 4 * ngl * nnu;
+  dcx Da[2][2], Db[2][2], waW[2], wbW[2], waE[2], wbE[2];
+  {
+    const dcx ca[2] = {cW[0], cW[1]}, cb[2] = {cW[2], cW[3]};
+    lw::we_stokes(fr, g.wc, g.ws, g.m0, lam, wq, false, Da, Db, false);
+    lw::stokes_apply(Da, Db, ca, cb, false, 1.0, waW, wbW);
+  }
+  {
+    const dcx ca[2] = {cE[0], cE[1]}, cb[2] = {cE[2], cE[3]};
+    lw::we_stokes(fr, g.wc, g.ws, g.m0, lam, wq, true, Da, Db, false);
+    lw::stokes_apply(Da, Db, ca, cb, true, 1.0, waE, wbE);
+  }
+  for (int k = 0; k < ngl; ++k) {
+    const double xb = a.gl[2 * k];
+    const double es = exp(-kap * xb), en = exp(kap * xb);
+    for (int i = 0; i < 2; ++i) {
+      const dcx va = cadd(cscale(waW[i], es), cscale(waE[i], en));
+      const dcx vb = cadd(cscale(wbW[i], es), cscale(wbE[i], en));
+      out[(size_t)(i * ngl + k) * nnu + j] = make_double2(va.r, va.i);
+      out[(size_t)((2 + i) * ngl + k) * nnu + j] = make_double2(vb.r, vb.i);
+    }
+  }
+}
+
+// Evaluation-line spectra on the uniform frequencies u = 1..M:
+//   H(u) = dl sum_n psi(lambda_n - u dl) V(n)   (nodes ascending: a binary
+// search finds the window), deconvolved by the y-kernel's phihat and packed
+// two real lines per complex line as in k_nufft_modes:
+//   scalar: line k: V_k + i (x-derivative line k);  line n_gl + p: the
+//           y-derivative lines (i lambda V) 2p and 2p + 1
+//   Stokes: line k: a_x + i a_y;  line n_gl + k: b_x + i b_y.
+// One thread per (u, packed line, rhs); spec was cleared before.
+template <int KER>
+__global__ void k_p1_gather(NufftArgs a, const double* __restrict__ nodes, int nq0, int nnu, double dl, double alpha,
+                            const double2* __restrict__ lines, double2* __restrict__ spec, int want_grad) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  const int s = blockIdx.y, r = blockIdx.z;
+  if (u > a.M) return;
+  const int ngl = a.n_gl;
+  const int nl = (KER == PFMM_STOKES ? 4 : 2) * ngl;
+  const double2* L = lines + (size_t)r * nl * nnu;
+  int la, lb;
+  bool dy = false;  // multiply the node values by i lambda (y-derivative lines)
+  if (KER == PFMM_STOKES) {
+    la = s < ngl ? s : 2 * ngl + (s - ngl);
+    lb = s < ngl ? ngl + s : 3 * ngl + (s - ngl);
+  } else if (s < ngl) {
+    la = s;
+    lb = want_grad ? ngl + s : -1;
+  } else {
+    const int p = s - ngl;
+    la = 2 * p;
+    lb = 2 * p + 1 < ngl ? 2 * p + 1 : -1;
+    dy = true;
+  }
+  const double uc = u * dl, lo = uc - alpha, hi = uc + alpha;
+  int b = 0, e = nnu;  // first node with lambda > lo
+  while (b < e) {
+    const int m = (b + e) >> 1;
+    if (nodes[2 * (nq0 + m)] <= lo) b = m + 1;
+    else e = m;
+  }
+  dcx A{0, 0}, B{0, 0};
+  for (int m = b; m < nnu; ++m) {
+    const double lam = nodes[2 * (nq0 + m)];
+    if (lam >= hi) break;
+    const double z = (lam - uc) / alpha, t = 1.0 - z * z;
+    if (t <= 0.0) continue;
+    const double ps = exp(a.es_beta * (sqrt(t) - 1.0));
+    const double f = dy ? ps * lam : ps;
+    const double2 va = L[(size_t)la * nnu + m];
+    A = cadd(A, dy ? dcx{-f * va.y, f * va.x} : dcx{f * va.x, f * va.y});
+    if (lb >= 0) {
+      const double2 vb = L[(size_t)lb * nnu + m];
+      B = cadd(B, dy ? dcx{-f * vb.y, f * vb.x} : dcx{f * vb.x, f * vb.y});
+    }
+  }
+  const double pre = dl * (2.0 / a.w) / a.phihat[u];
+  double2* row = spec + ((size_t)r * a.npk + s) * a.nf;
+  row[u] = {0.5 * pre * (A.r - B.i), 0.5 * pre * (A.i + B.r)};
+  row[a.nf - u] = {0.5 * pre * (A.r + B.i), 0.5 * pre * (-A.i + B.r)};
 }
 
 // Raise a kernel's dynamic shared-memory limit once per device and size, so
@@ -632,8 +831,137 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   return cudaGetLastError();
 }
 
+// Singly periodic west/east nodes [p1_nq0, Nq) through the transforms (see
+// k_p1_modes); adds to pot / grad, which the direct kernels wrote first.
+template <typename T>
+static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
+                                double* grad, cudaStream_t st) {
+  const Layout& L = p->lay;
+  const bool mixed = sizeof(T) == 4;
+  const int K = p->opts.kernel;
+  NufftArgs a{};
+  a.nf = p->nf;
+  a.logn = 0;
+  while ((1 << a.logn) < a.nf) ++a.logn;
+  a.w = p->nufft_w;
+  a.M = p->p1_M;
+  a.n_gl = p->n_gl;
+  a.nrhs = p->opts.nrhs;
+  a.ns = (int)ns;
+  a.nt = (int)nt;
+  a.kernel = K;
+  a.nch = nufft_nch(K);
+  a.npk = nufft_npk(K, a.n_gl);
+  a.mlo = 1;
+  a.os = p->o_stride;
+  a.es_beta = p->es_beta;
+  a.d = p->p1_Y;  // the transform's period
+  a.eta = p->geom.d;
+  a.xi = 0.0;
+  a.beta = p->far.beta;
+  const char* tab = ws + L.nodes;
+  a.gl = (const double*)(tab + off_gl(p));
+  a.phihat = (const double*)(tab + off_phihat(p));
+  a.tw = (const double*)(tab + off_twiddle(p));
+  a.rho = (const double*)(tab + off_rho(p));
+  a.rho_c = 2.0 / p->geom.eta;
+  const double* nodes = (const double*)tab;
+  const int nq0 = p->p1_nq0, nnu = p->Nq - p->p1_nq0;
+  const double dl = p->p1_dl, alpha = p->p1_alpha;
+  const int nline = a.nrhs * a.nch * a.n_gl;
+  char* base = ws + L.nufft;
+  double* grid = (double*)base;  // [nrhs][nch][n_gl][nf]
+  size_t off = (size_t)nline * a.nf * sizeof(double);
+  double2* Fk = (double2*)(base + off);  // [nrhs][nch][n_gl][M+1]
+  off += (size_t)nline * (a.M + 1) * sizeof(double2);
+  off = (off + 255) & ~size_t(255);
+  double2* spec = (double2*)(base + off);  // [nrhs][npk][nf]
+  off += (size_t)a.nrhs * a.npk * a.nf * sizeof(double2);
+  off = (off + 255) & ~size_t(255);
+  double2* lines = (double2*)(base + off);  // [nrhs][p1_node_lines][nnu]
+  cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)nline * a.nf * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * a.npk * a.nf * sizeof(double2), st);
+  if (e != cudaSuccess) return e;
+  // transform coordinate y, GL coordinate x, fixed-point phase of y
+  const T* s64 = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
+  const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
+  const int* sV = (const int*)(ws + L.srcV);
+  int nchunk = std::max(1, std::min((int)((ns + 255) / 256), 2 * 152));
+  int chunk = (int)((ns + nchunk - 1) / nchunk);
+  nchunk = (int)((ns + chunk - 1) / chunk);
+  const size_t per_v = (size_t)a.n_gl * a.nf * sizeof(T);
+  const int use_smem = per_v <= 96 * 1024;
+  const int nv = a.nrhs * a.nch;
+  const int vg = use_smem ? (int)std::max<size_t>(1, std::min<size_t>(nv, (100 * 1024) / per_v)) : nv;
+  const size_t sm_spread = use_smem ? vg * per_v : 0;
+  const int wspec = nufft_spec(a.w, a.n_gl);
+  const int slot = (sizeof(T) == 4 ? 0 : 4) + wspec;
+  const T* sy_ = s64 + ns;  // y
+  switch (wspec) {
+    case 1: e = spread_t<T, 8, 8>(a, nchunk, chunk, sy_, s64, sV, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    case 2: e = spread_t<T, 12, 16>(a, nchunk, chunk, sy_, s64, sV, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    case 3: e = spread_t<T, 14, 16>(a, nchunk, chunk, sy_, s64, sV, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+    default: e = spread_t<T, 0, 0>(a, nchunk, chunk, sy_, s64, sV, qv, grid, use_smem, vg, sm_spread, slot, st); break;
+  }
+  if (e != cudaSuccess) return e;
+  const int fth = std::min(512, std::max(32, a.nf / 2));
+  const size_t sm_fft = (size_t)a.nf * sizeof(double2);
+  if (sm_fft > 48 * 1024) {
+    e = raise_smem((const void*)k_nufft_fwd, 8, sm_fft);
+    if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 9, sm_fft);
+    if (e != cudaSuccess) return e;
+  }
+  k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
+  const int wg = grad != nullptr && K != PFMM_STOKES;
+  const dim3 gm((nnu + 127) / 128, a.nrhs);
+  const dim3 gg((a.M + 127) / 128, (K == PFMM_STOKES || wg) ? a.npk : a.n_gl, a.nrhs);
+  const Geom& g = p->geom;
+  if (K == PFMM_STOKES) {
+    k_p1_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, g, nodes, nq0, nnu, dl, alpha, Fk, lines);
+    k_p1_gather<PFMM_STOKES><<<gg, 128, 0, st>>>(a, nodes, nq0, nnu, dl, alpha, lines, spec, 0);
+  } else if (K == PFMM_MODHELM) {
+    k_p1_modes<PFMM_MODHELM><<<gm, 128, 0, st>>>(a, g, nodes, nq0, nnu, dl, alpha, Fk, lines);
+    k_p1_gather<PFMM_MODHELM><<<gg, 128, 0, st>>>(a, nodes, nq0, nnu, dl, alpha, lines, spec, wg);
+  } else {
+    k_p1_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, g, nodes, nq0, nnu, dl, alpha, Fk, lines);
+    k_p1_gather<PFMM_LAPLACE><<<gg, 128, 0, st>>>(a, nodes, nq0, nnu, dl, alpha, lines, spec, wg);
+  }
+  k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+  const T* t64 = self ? s64 : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
+  const int* tV = self ? sV : (const int*)(ws + L.trgV);
+  const int ni = (int)((nt + 127) / 128);
+  if (K == PFMM_STOKES) {
+    // velocity components are not coordinates: the plain frame
+    interp_k<T, PFMM_STOKES>(wspec, ni, a, g, t64 + nt, t64, tV, spec, pot, nullptr, st);
+  } else {
+    // the interpolation's "x" derivative is along its transform coordinate
+    // (y here) and its "y" derivative along the GL lines (x): swap the
+    // columns of the rotation that maps the canonical gradient back
+    Geom gs = g;
+    gs.rot[0] = g.rot[2];
+    gs.rot[1] = g.rot[3];
+    gs.rot[2] = g.rot[0];
+    gs.rot[3] = g.rot[1];
+    interp_k<T, PFMM_LAPLACE>(wspec, ni, a, gs, t64 + nt, t64, tV, spec, pot, wg ? grad : nullptr, st);
+  }
+  g_launches += 6;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
                              double* grad, cudaStream_t st) {
+  if (p->p1_nu) {
+    // singly periodic: the nodes below the cut on the direct kernels (they
+    // write the outputs), the rest through the transforms (they add)
+    pfmm_plan q = *p;
+    q.far.Nq = p->p1_nq0;
+    q.far.nterm = 2 * p->p1_nq0;
+    cudaError_t e = launch_far_direct(&q, ws, ns, nt, self, pot, grad, st);
+    if (e != cudaSuccess) return e;
+    return (p->opts.precision == PFMM_MIXED) ? run_p1_nufft<float>(p, ws, ns, nt, self, pot, grad, st)
+                                             : run_p1_nufft<double>(p, ws, ns, nt, self, pot, grad, st);
+  }
   // west/east terms and the m = 0 moment term on the direct kernels (their
   // number of nodes does not grow with the aspect ratio), south/north here.
   pfmm_plan q = *p;

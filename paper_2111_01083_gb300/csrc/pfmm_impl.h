@@ -9,6 +9,7 @@ namespace pfmm {
 
 constexpr int kMaxNear = 32;      // (2 m0 + 1) * 3 images; m0 <= 3 after reduction
 constexpr int kPlanEvents = 8;    // profiling events of a plan
+constexpr int kRhoCheb = 40;      // Chebyshev terms of the singly periodic NUFFT deconvolution 1/Psi(y)
 constexpr int kDetChunks = 128;   // deterministic mode: source chunks of the coefficient formation
 constexpr int kStatusWords = 8;   // status word region (ints)
 
@@ -53,6 +54,9 @@ struct Far {
 // per spectrum; Stokes: the a and b weight lines per GL line; modified
 // Stokes: one line u_x + i u_y per GL line).
 inline int nufft_nch(int kernel) { return kernel == PFMM_STOKES ? 4 : (kernel == PFMM_MSTOKES ? 2 : 1); }
+// singly periodic NUFFT: evaluation lines per rhs at the nodes (scalar: value
+// and x-derivative per GL line; Stokes: a_x, a_y, b_x, b_y per GL line)
+inline int p1_node_lines(int kernel, int n_gl) { return (kernel == PFMM_STOKES ? 4 : 2) * n_gl; }
 inline int nufft_npk(int kernel, int n_gl) {
   return kernel == PFMM_STOKES ? 2 * n_gl : (kernel == PFMM_MSTOKES ? n_gl : n_gl + (n_gl + 1) / 2);
 }
@@ -65,6 +69,7 @@ struct Layout {
   size_t src64, trg64;     // double [2][n] canonical coordinates
   size_t srcf, trgf;       // float  [2][n] canonical coordinates (mixed far field)
   size_t srcU, trgU;       // int32 [n] fixed-point x/d phase (mixed south/north)
+  size_t srcV, trgV;       // int32 [n] fixed-point y/Y phase (singly periodic NUFFT, mixed)
   // mixed P2P: spatially sorted sources (and, for modified Helmholtz, targets)
   size_t s_rel;            // float2 [ns] coordinates relative to the subtile centre
   size_t s_hl;             // float4 [ns] sorted (x_hi, x_lo, y_hi, y_lo)
@@ -142,6 +147,17 @@ struct pfmm_plan {
   double* gl_h;             // [n_gl][2] (ybar_n, sigma_n) on [-eta/2, eta/2]
   double* phihat_h;         // [M+1] ES kernel Fourier transform at modes 0..M
   double* tw_h;             // [nf/2][2] FFT twiddles (cos, sin)(2 pi k / nf), NUFFT path only
+  int nphihat;              // entries of phihat_h (M + 1; singly periodic NUFFT: p1_M + 1)
+  // singly periodic operator on the NUFFT path (west/east parts through the
+  // transforms with the roles of x and y exchanged): west/east nodes
+  // [0, p1_nq0) stay on the direct kernels, [p1_nq0, Nq) go through a type-1
+  // transform in y over the virtual period p1_Y = 2 eta (uniform frequencies
+  // u p1_dl, u = 0..p1_M) and ES interpolation in lambda (half-width p1_alpha);
+  // gl_h then holds GL nodes in x on [-d/2, d/2]
+  int p1_nu;                // 1: on
+  int p1_nq0, p1_M;
+  double p1_Y, p1_dl, p1_alpha;
+  double* rho_h;            // [kRhoCheb] Chebyshev coefficients of 1/Psi(y) on |y| <= eta/2
   pfmm::Layout lay;
   pfmm::FmmPlan fmm;        // near field by the tree code (fmm.on)
   double mh_cut;            // modified Helmholtz P2P: pairs with beta r > mh_cut are skipped
@@ -170,15 +186,18 @@ struct pfmm_plan {
 
 namespace pfmm {
 // Byte offsets inside the node-table region (L.nodes): west/east nodes
-// [max(1,Nq)][2], GL lines [n_gl][2], phihat [M+1], then (16-aligned) the FFT
-// twiddles [nf/2][2].
+// [max(1,Nq)][2], GL lines [n_gl][2], phihat [nphihat], then (16-aligned) the
+// FFT twiddles [nf/2][2] and the singly periodic NUFFT's Chebyshev table.
 inline size_t off_gl(const pfmm_plan* p) { return (size_t)(p->Nq > 0 ? p->Nq : 1) * 2 * sizeof(double); }
 inline size_t off_phihat(const pfmm_plan* p) { return off_gl(p) + (size_t)p->n_gl * 2 * sizeof(double); }
 inline size_t off_twiddle(const pfmm_plan* p) {
-  return (off_phihat(p) + (size_t)(p->far.M + 1) * sizeof(double) + 15) & ~size_t(15);
+  return (off_phihat(p) + (size_t)p->nphihat * sizeof(double) + 15) & ~size_t(15);
+}
+inline size_t off_rho(const pfmm_plan* p) {
+  return off_twiddle(p) + (p->tw_h ? (size_t)p->nf * sizeof(double) : 0);
 }
 inline size_t node_region_bytes(const pfmm_plan* p) {
-  return off_twiddle(p) + (p->tw_h ? (size_t)p->nf * sizeof(double) : 0);
+  return off_rho(p) + (p->rho_h ? (size_t)kRhoCheb * sizeof(double) : 0);
 }
 
 // Record a profiling event on st; under stream capture as an external event

@@ -219,10 +219,11 @@ cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(base + off_gl(p), p->gl_h, p->n_gl * 2 * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(base + off_phihat(p), p->phihat_h, (p->far.M + 1) * sizeof(double), cudaMemcpyHostToDevice,
-                        st);
+    e = cudaMemcpyAsync(base + off_phihat(p), p->phihat_h, p->nphihat * sizeof(double), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess && p->tw_h)
     e = cudaMemcpyAsync(base + off_twiddle(p), p->tw_h, p->nf * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && p->rho_h)
+    e = cudaMemcpyAsync(base + off_rho(p), p->rho_h, kRhoCheb * sizeof(double), cudaMemcpyHostToDevice, st);
   return e;
 }
 
@@ -333,7 +334,6 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   const bool p1 = (o->flags & PFMM_SINGLY_PERIODIC) != 0;
   if (p1) {
     if (!canonicalize_strip(o->e1, o->e2, &g)) return fail(PFMM_ERR_LATTICE, "degenerate strip vectors");
-    if (o->path == PFMM_PATH_NUFFT) return fail(PFMM_ERR_INVALID_ARG, "the singly periodic operator uses the direct path");
     g.p1 = 1;
     g.m0 = 1;  // |x - x'| < d after wrapping: images |m| >= 2 are separated by >= d
   } else {
@@ -434,32 +434,85 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   int w = o->nufft_w ? o->nufft_w : std::min(16, std::max(2, (int)std::ceil(std::log10(1.0 / o->tol)) + 2));
   p->nufft_w = w;
   p->es_beta = 2.30 * w;
+  // Singly periodic operator on the NUFFT path (Sec. 6.1 with the roles of x
+  // and y exchanged: a fast algorithm is needed when eta >> d, where the
+  // west/east rank grows like eta/d).  The nodes lambda_n are piecewise GL, not
+  // uniform, so each GL line's transform in y is a type-3 one: a type-1
+  // transform onto the uniform frequencies u dl (dl = 2 pi / Y, Y = 2 eta, so
+  // that |y| <= Y/4 like the modes of a sigma = 2 grid) of the strengths divided
+  // by Psi(y), then ES interpolation in lambda (width w, half-width
+  // alpha = w dl / 2; Psi is the kernel's Fourier transform).  Nodes below
+  // alpha + 2 dl stay on the direct kernels: they would need frequencies
+  // u <= 0, and their lattice weight grows like 1/lambda^2.
+  int p1_M = 0, p1_nq0 = p->Nq;
+  double p1_Y = 0, p1_dl = 0, p1_alpha = 0;
+  if (p1 && p->Nq > 0 && o->path != PFMM_PATH_DIRECT) {
+    p1_Y = 2.0 * g.eta;
+    p1_dl = 2.0 * M_PI / p1_Y;
+    p1_alpha = 0.5 * w * p1_dl;
+    const double lcut = p1_alpha + 2.0 * p1_dl;
+    p1_nq0 = 0;
+    while (p1_nq0 < p->Nq && nodes[2 * p1_nq0] < lcut) ++p1_nq0;
+    if (p1_nq0 < p->Nq) p1_M = (int)std::ceil((nodes[2 * (p->Nq - 1)] + p1_alpha) / p1_dl) + 1;
+  }
+  const int p1_nnu = p->Nq - p1_nq0;
+  const int Mt = p1 ? p1_M : M;  // uniform modes of the transforms
   int nf = 16;
-  while (nf < 2 * (2 * M + 1) || nf < 2 * w) nf *= 2;
+  while (nf < 2 * (2 * Mt + 1) || nf < 2 * w) nf *= 2;
   p->nf = nf;
   int path = o->path;
   // the single-block shared-memory FFT handles fine grids up to 8192 points
-  if (path == PFMM_PATH_AUTO)
-    path = (M >= 64 && nf <= 8192 && !(o->flags & PFMM_DETERMINISTIC)) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+  if (path == PFMM_PATH_AUTO) {
+    const bool big = p1 ? p1_nnu >= 128 : M >= 64;
+    path = (big && nf <= 8192 && !(o->flags & PFMM_DETERMINISTIC)) ? PFMM_PATH_NUFFT : PFMM_PATH_DIRECT;
+  }
   if (path == PFMM_PATH_NUFFT && nf > 8192) {
     pfmm_plan_destroy(p);
     return fail(PFMM_ERR_INVALID_ARG, "NUFFT fine grid of %d points exceeds 8192 (use the direct path)", nf);
   }
-  if (M == 0) path = PFMM_PATH_DIRECT;
+  if (p1 ? p1_nnu == 0 : M == 0) path = PFMM_PATH_DIRECT;
   p->path = path;
+  p->p1_nu = p1 && path == PFMM_PATH_NUFFT;
+  p->p1_nq0 = p->p1_nu ? p1_nq0 : p->Nq;
+  p->p1_M = p->p1_nu ? p1_M : 0;
+  p->p1_Y = p1_Y;
+  p->p1_dl = p1_dl;
+  p->p1_alpha = p1_alpha;
+  p->rho_h = nullptr;
   {
     std::vector<double> gx, gw;
     gauss_legendre(p->n_gl, gx, gw);
     p->gl_h = (double*)std::malloc(2 * p->n_gl * sizeof(double));
+    // GL lines across the non-oscillatory direction: y in [-eta/2, eta/2]
+    // (south/north), x in [-d/2, d/2] (singly periodic west/east)
+    const double ext = p->p1_nu ? g.d : g.eta;
     for (int i = 0; i < p->n_gl; ++i) {
       double s = 1.0;  // barycentric weight 1/prod_{j != i}(t_i - t_j) (Eq. baryweights), scaled node
       for (int j = 0; j < p->n_gl; ++j)
         if (j != i) s /= (gx[i] - gx[j]);
-      p->gl_h[2 * i] = 0.5 * g.eta * gx[i];
+      p->gl_h[2 * i] = 0.5 * ext * gx[i];
       p->gl_h[2 * i + 1] = s;
     }
-    p->phihat_h = (double*)std::malloc((M + 1) * sizeof(double));
-    for (int m = 0; m <= M; ++m) p->phihat_h[m] = es_phihat(p->es_beta, 2.0 * M_PI * m * (w * 0.5) / nf);
+    p->nphihat = Mt + 1;
+    p->phihat_h = (double*)std::malloc((Mt + 1) * sizeof(double));
+    for (int m = 0; m <= Mt; ++m) p->phihat_h[m] = es_phihat(p->es_beta, 2.0 * M_PI * m * (w * 0.5) / nf);
+    if (p->p1_nu) {
+      // 1/Psi(y), Psi(y) = alpha phihat(alpha y), on |y| <= eta/2 as a
+      // Chebyshev series in t = 2 y / eta (64-point interpolation; the
+      // coefficients beyond 40 are at rounding level for w <= 16)
+      constexpr int N = 64;
+      double f[N];
+      for (int i = 0; i < N; ++i) {
+        const double t = std::cos(M_PI * (i + 0.5) / N);
+        f[i] = 1.0 / (p1_alpha * es_phihat(p->es_beta, p1_alpha * 0.5 * g.eta * t));
+      }
+      p->rho_h = (double*)std::malloc(kRhoCheb * sizeof(double));
+      for (int k = 0; k < kRhoCheb; ++k) {
+        double c = 0.0;
+        for (int i = 0; i < N; ++i) c += f[i] * std::cos(k * M_PI * (i + 0.5) / N);
+        p->rho_h[k] = (k == 0 ? 1.0 : 2.0) * c / N;
+      }
+    }
     p->tw_h = nullptr;
     if (path == PFMM_PATH_NUFFT) {
       // FP64 twiddles for the shared-memory FFT: (cos, sin)(2 pi k / nf), k < nf/2
@@ -486,6 +539,8 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
   L.trgf = take(2 * nt_max * sizeof(float));
   L.srcU = take(ns_max * sizeof(int));
   L.trgU = take(nt_max * sizeof(int));
+  L.srcV = take(p->p1_nu ? ns_max * sizeof(int) : 0);
+  L.trgV = take(p->p1_nu ? nt_max * sizeof(int) : 0);
   L.qc = take((size_t)nrhs * p->ncomp * ns_max * sizeof(double));
   L.qf = take((size_t)nrhs * p->ncomp * ns_max * sizeof(float));
   {
@@ -517,8 +572,10 @@ pfmm_status pfmm_plan_create(const pfmm_opts* o, int64_t ns_max, int64_t nt_max,
     // evaluation spectra [nrhs][npk][nf] complex (float2 for mixed, double2 for fp64)
     size_t cplx = 16;  // FFTs and spectra are FP64 on both precision paths
     size_t nline = (size_t)nrhs * pfmm::nufft_nch(o->kernel) * p->n_gl;
-    nuf = nline * nf * 8 + nline * (M + 1) * 16 + 256 +
+    nuf = nline * nf * 8 + nline * (Mt + 1) * 16 + 256 +
           (size_t)nrhs * pfmm::nufft_npk(o->kernel, p->n_gl) * nf * cplx + 256;
+    // singly periodic: evaluation lines at the nodes [nrhs][lines][nodes] complex
+    if (p->p1_nu) nuf += (size_t)nrhs * pfmm::p1_node_lines(o->kernel, p->n_gl) * p1_nnu * cplx + 256;
   }
   L.nufft = take(nuf);
   // adjoint scratch: dL/dpot projected as strengths is handled in place; the
@@ -569,6 +626,7 @@ void pfmm_plan_destroy(pfmm_plan* p) {
   std::free(p->gl_h);
   std::free(p->phihat_h);
   std::free(p->tw_h);
+  std::free(p->rho_h);
   delete[] p->sort_h;
   delete p;
 }
@@ -604,6 +662,7 @@ pfmm_status pfmm_plan_describe(const pfmm_plan* p, pfmm_plan_desc* d) {
   d->near_order = p->fmm.p;
   d->near_leaf = p->fmm.nleaf;
   d->near_theta = p->fmm.theta;
+  d->p1_nufft_nodes = p->p1_nu ? p->Nq - p->p1_nq0 : 0;
   return PFMM_OK;
 }
 

@@ -508,7 +508,9 @@ def tune_batch(kernel, cells, src_counts, src, q, trg=None, trg_counts=None, pre
                 return d[key]["config"], d[key]["ms"]
         except Exception:
             pass
-    wmin = max(2, math.ceil(math.log10(1.0 / tol) + 1e-9) + 1)
+    # ceil(log10(1/tol)) with a guard below (log10 of an exact power of ten
+    # may round up past the integer)
+    wmin = max(2, math.ceil(math.log10(1.0 / tol) - 1e-9) + 1)
     widths = tuple(range(wmin, min(16, wmin + 1) + 1))
     timings = {}
 

@@ -71,3 +71,72 @@ def test_p1_point_outside_strip_is_reported():
     q = workloads.strengths(rng, 1, 50)
     with pytest.raises(PfmmError):
         run_lib("laplace", e1, e2, src, q, None, tol=1e-6, precision="mixed", singly=True)
+
+
+TALL = {
+    "1x16": ((1.0, 0.0), (0.0, 16.0)),
+    "rot1x12": ((0.8, 0.6), (-7.2, 9.6)),
+    "skew1x10": ((1.0, 0.0), (0.4, 10.0)),
+}
+
+
+_TALL_CACHE = {}
+
+
+def _tall_case(strip, kernel, beta):
+    """Seeded input and its oracle field, shared by both precisions."""
+    key = (strip, kernel, beta)
+    if key not in _TALL_CACHE:
+        e1, e2 = TALL[strip]
+        rng = np.random.default_rng(81)
+        ns, nt = 2000, 300
+        src = _points(e1, e2, ns, rng)
+        trg = _points(e1, e2, nt, rng)
+        stokes = kernel == "stokes"
+        q = workloads.strengths(rng, 2, ns, stokes=stokes, neutral=kernel != "modhelm")
+        ref = p1.evaluate(kernel, beta, e1, e2, src, q, trg, want_grad=not stokes)
+        _TALL_CACHE[key] = (src, q, trg, ref)
+    return _TALL_CACHE[key]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("strip", list(TALL))
+@pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 1.5), ("stokes", 0.0)])
+def test_p1_nufft_total(precision, strip, kernel, beta):
+    """Tall strips on the NUFFT path (the west/east sums through GL lines in
+    x, a type-1 transform in y and ES interpolation onto the nodes) against
+    the P1 oracle."""
+    e1, e2 = TALL[strip]
+    src, q, trg, ref = _tall_case(strip, kernel, beta)
+    stokes = kernel == "stokes"
+    pot, g, op = run_lib(kernel, e1, e2, src, q, trg, beta=beta, tol=TOL[precision], precision=precision,
+                         grad=not stokes, singly=True, path="nufft")
+    d = op.describe()
+    assert d["path"] == 2 and d["p1_nufft_nodes"] > 0, d
+    ep, eg = errs(kernel, (pot, g), ref)
+    assert ep < TOL[precision], ep
+    if eg is not None:
+        assert eg < TOL[precision], eg
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 0.5), ("stokes", 0.0)])
+def test_p1_nufft_far_matches_direct(precision, kernel, beta):
+    """The far part alone (1 x 24 strip, targets = sources) through the
+    transforms and through the direct kernels on the same input: equal to
+    the tolerance relative to the far part itself (modulo the constant the
+    two Laplace/Stokes gauges differ by)."""
+    e1, e2 = (1.0, 0.0), (0.0, 24.0)
+    rng = np.random.default_rng(82)
+    n = 5000
+    src = _points(e1, e2, n, rng)
+    stokes = kernel == "stokes"
+    q = workloads.strengths(rng, 1, n, stokes=stokes, neutral=kernel != "modhelm")
+    kw = dict(beta=beta, tol=TOL[precision], precision=precision, grad=not stokes, singly=True, part="far")
+    pn, gn, op = run_lib(kernel, e1, e2, src, q, None, path="nufft", **kw)
+    assert op.describe()["p1_nufft_nodes"] > 0
+    pd, gd, _ = run_lib(kernel, e1, e2, src, q, None, path="direct", **kw)
+    ep, eg = errs(kernel, (pn, gn), (pd, gd))
+    assert ep < TOL[precision], ep
+    if eg is not None:
+        assert eg < TOL[precision], eg

@@ -193,17 +193,27 @@ def test_workspace_size_grows_with_n(L):
 
 
 def test_singly_periodic_plan(L):
-    """P1: 3 near images, no south/north modes, direct path; west/east nodes
-    grow for a tall strip; NUFFT rejected."""
+    """P1: 3 near images, no south/north modes; west/east nodes grow for a
+    tall strip, and AUTO then takes the west/east sums through the transforms
+    (nodes above (w/2 + 2) pi / eta; the rest stay direct); a wide strip has no
+    node above that cut and stays on the direct path even when NUFFT is asked for."""
     from paper_2111_01083_gb300 import PeriodicOp
-    from paper_2111_01083_gb300._lib import PfmmError
     wide = PeriodicOp("laplace", (1.0, 0.0), (0.3, 0.5), singly=True, ns_max=8, nt_max=8).describe()
     assert wide["M"] == 0 and wide["path"] == 1 and wide["m0"] == 1 and wide["Nq"] > 0
     assert abs(wide["d"] - 1.0) < 1e-15 and abs(wide["eta"] - 0.5) < 1e-15 and wide["xi"] == 0.0
+    assert wide["p1_nufft_nodes"] == 0
+    forced = PeriodicOp("laplace", (1.0, 0.0), (0.3, 0.5), singly=True, path="nufft", ns_max=8, nt_max=8).describe()
+    assert forced["path"] == 1 and forced["p1_nufft_nodes"] == 0
     tall = PeriodicOp("laplace", (1.0, 0.0), (0.0, 20.0), singly=True, ns_max=8, nt_max=8).describe()
     assert tall["Nq"] > wide["Nq"]
-    with pytest.raises(PfmmError):
-        PeriodicOp("laplace", (1.0, 0.0), (0.0, 2.0), singly=True, path="nufft", ns_max=8, nt_max=8)
+    assert tall["path"] == 2 and 128 <= tall["p1_nufft_nodes"] < tall["Nq"] and tall["M"] == 0
+    w = tall["nufft_w"]
+    # uniform frequencies u pi / eta up to the top node plus the kernel's half-width
+    assert tall["nf"] <= 8192 and tall["nf"] >= 2 * (2 * int(16.1 * 20 / math.pi) + 1)
+    direct = PeriodicOp("laplace", (1.0, 0.0), (0.0, 20.0), singly=True, path="direct", ns_max=8, nt_max=8).describe()
+    assert direct["path"] == 1 and direct["p1_nufft_nodes"] == 0 and direct["Nq"] == tall["Nq"]
+    mid = PeriodicOp("stokes", (1.0, 0.0), (0.0, 2.0), singly=True, path="nufft", ns_max=8, nt_max=8).describe()
+    assert mid["path"] == 2 and 0 < mid["p1_nufft_nodes"] < mid["Nq"] and w == mid["nufft_w"]
 
 
 @pytest.mark.parametrize("kernel,beta", [("laplace", 0.0), ("modhelm", 1.0), ("stokes", 0.0), ("mstokes", 1.0)])
