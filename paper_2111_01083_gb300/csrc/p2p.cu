@@ -326,220 +326,116 @@ __global__ void __launch_bounds__(kP2PThreads, 1) k_p2p_mixed(const __grid_const
 }
 
 // Modified Helmholtz mixed kernel: one target per thread, targets and sources
-// in spatially sorted order, per-source image sums K0s = sum_i K0(beta r_i),
-// K1x = sum_i K1(beta r_i) dx_i / r_i (and y), then one FMA per rhs (strengths
-// read four at a time).  Pairs with beta r > x_c are skipped (plan: every skipped
-// term below tol/10 / (images * ns)): per (target block, source
-// tile, image) an FP64 test on the outward-rounded boxes classifies the image
-// as skipped (boxes farther apart than x_c / beta, x_c from the plan: every
-// skipped term below tol/10 / (images * ns)), complete (every pair within
-// the cutoff: no per-pair test) or partial (pairs beyond the cutoff skipped).
-// Two targets per thread in packed FP32 was measured slower here (register
-// pressure halves the resident warps of this branch-heavy kernel).
+// in spatially sorted order, per (target, source) the image sums
+// K0s = sum_i K0(beta r_i), K1x = sum_i K1(beta r_i) dx_i / r_i (and y), then
+// one FMA per rhs.  Two sources go through each packed FP32 instruction
+// (FFMA2 / FADD2 / FMUL2 on the source pair), four per step.
+//
+// Culling: pairs with beta r > x_c are skipped (x_c from the plan: every
+// skipped term below tol/10 / (images * ns)).  Per (target block, source tile)
+// one thread classifies each image with an FP32 test on the outward-rounded
+// boxes: an image with no pair within the cutoff is skipped for the tile.
+//
+// Per 16-source subtile and image, warp-uniform routing:
+//  - exact: some lane of the warp lies within about two subtile extents of
+//    the subtile (close pairs: differences from the hi/lo coordinates), or
+//    within 2 / beta of it (beta r <= 2 possible).  K0 from the small- or the
+//    large-argument fit per pair; a warp vote decides which fits run, so a
+//    warp whose pairs all fall on one side evaluates one fit only.
+//  - fast: every other active image.  Every pair of the warp has beta r > 2,
+//    so only the large-argument fit runs, on beta-scaled coordinates relative
+//    to the subtile centre; the image list is compacted per thread in shared
+//    memory, so the loop runs over the active images only.
+// Pairs of the exact images beyond the cutoff are evaluated as well (their
+// terms lie below the cutoff's bound).
 template <int KER, int NIMG, int NR, bool GRAD>
 __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int j0, int j1, int r0) {
   constexpr int CENTER = NIMG / 2;
   constexpr int NA = GRAD ? 3 : 1;
   constexpr int NSUB = kP2PTile / kSubtile;
-  __shared__ float2 s_p[kP2PTile];
-  __shared__ float2 s_pb[kP2PTile];  // beta-scaled relative coordinates (far path)
-  __shared__ float4 s_h[kP2PTile];
+  constexpr unsigned kFull = 0xffffffffu;
+  static_assert(kP2PTile == kP2PThreads, "one thread loads one source of the tile");
+  // the source tile, component-major: consecutive sources are the two lanes
+  // of a packed operation
+  __shared__ __align__(16) float s_bs[2][kP2PTile];  // beta (s - subtile centre)
+  __shared__ __align__(16) float s_hs[4][kP2PTile];  // x_hi, x_lo, y_hi, y_lo
+  __shared__ __align__(16) float s_q[NR][kP2PTile];
   __shared__ float4 s_c[NSUB];
   __shared__ float2 s_e[NSUB];
-  constexpr int NQ4 = (NR + 3) / 4;
-  __shared__ float4 s_q4[NQ4][kP2PTile];
-  const int l = bx * kP2PThreads + threadIdx.x;
+  // hi/lo target coordinates per image, one column per thread
+  __shared__ float s_tc[4][NIMG][kP2PThreads];
+  // the fast images of the current subtile: beta (target - image - centre)
+  __shared__ float2 s_bt[NIMG][kP2PThreads];
+  __shared__ unsigned s_tany[kP2PThreads];
+  const int tid = threadIdx.x;
+  const int l = bx * kP2PThreads + tid;
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
-  // hi/lo target coordinates per image, one column per thread in shared
-  // memory (read once per 16-source subtile; registers go to the pair loops)
-  __shared__ float s_tc[4][NIMG][kP2PThreads];
   {
     const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
       double vx = tx - a.g.off[i][0], vy = ty - a.g.off[i][1];
       const float hx = (float)vx, hy = (float)vy;
-      s_tc[0][i][threadIdx.x] = hx;
-      s_tc[1][i][threadIdx.x] = (float)(vx - (double)hx);
-      s_tc[2][i][threadIdx.x] = hy;
-      s_tc[3][i][threadIdx.x] = (float)(vy - (double)hy);
+      s_tc[0][i][tid] = hx;
+      s_tc[1][i][tid] = (float)(vx - (double)hx);
+      s_tc[2][i][tid] = hy;
+      s_tc[3][i][tid] = (float)(vy - (double)hy);
     }
   }
-  auto thx = [&](int i) { return s_tc[0][i][threadIdx.x]; };
-  auto tlx = [&](int i) { return s_tc[1][i][threadIdx.x]; };
-  auto thy = [&](int i) { return s_tc[2][i][threadIdx.x]; };
-  auto tly = [&](int i) { return s_tc[3][i][threadIdx.x]; };
   KahanF K[NR][NA];
-  float S[NR][NA];
+  float2 S[NR][NA];
 #pragma unroll
   for (int r = 0; r < NR; ++r)
 #pragma unroll
     for (int k = 0; k < NA; ++k) {
       K[r][k].s = K[r][k].c = 0.f;
-      S[r][k] = 0.f;
+      S[r][k] = f2(0.f);
     }
   const float beta = a.beta_f;
   const float beta2 = beta * beta;
-  const float cut2 = a.cut * a.cut;
   const float4 tb = a.t_box[bx];
   const float rsm = 2.0f / beta * 1.001f + 1e-6f;  // beta r <= 2 region, with margin
-  float txr[NIMG], tyr[NIMG];
 
-  // image sums of one source over the images in `any` (`all`: no per-pair
-  // cutoff test), then one FMA per rhs
-  auto source = [&](int jj, unsigned any, unsigned all, auto diff) {
-    float K0s = 0.f, K1x = 0.f, K1y = 0.f;
-#pragma unroll
-    for (int i = 0; i < NIMG; ++i) {
-      if (!(any & (1u << i))) continue;
-      float dx, dy;
-      diff(i, dx, dy);
-      float r2 = fmaf(dx, dx, dy * dy);
-      float msk = 1.0f;
-      if (i == CENTER) {
-        msk = (r2 > 0.0f) ? 1.0f : 0.0f;
-        r2 = (r2 > 0.0f) ? r2 : 1.0f;
-      }
-      // pairs beyond the cutoff x_c / beta of a partial image are
-      // skipped (the branch is not taken at all when no lane of the warp needs it)
-      if ((all & (1u << i)) || r2 < cut2) {
-        const float x2 = beta2 * r2;
-        if (GRAD) {
-          float k0, k1ix;
-          bes::k01f_x2(x2, &k0, &k1ix);  // k1ix = K1(x) / x
-          K0s = fmaf(k0, msk, K0s);
-          const float k1r = k1ix * beta * msk;  // K1(beta r) / r = beta K1(x) / x
-          K1x = fmaf(k1r, dx, K1x);
-          K1y = fmaf(k1r, dy, K1y);
-        } else {
-          K0s = fmaf(bes::k0f_x2(x2), msk, K0s);
-        }
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < NQ4; ++g) {
-      const float4 q4 = s_q4[g][jj];
-      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = 4 * g + k;
-        if (r >= NR) break;
-        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
-        if (GRAD) {
-          S[r][1 % NA] = fmaf(qv[k], K1x, S[r][1 % NA]);
-          S[r][2 % NA] = fmaf(qv[k], K1y, S[r][2 % NA]);
-        }
-      }
+  // large-argument fit on beta-scaled differences of a source pair: K0 and
+  // K1(x) / x times the scaled difference; the fit variable y = 2/x folded
+  // into the coefficients (c_k 2^k)
+  auto far_pair = [&](float2 dx, float2 dy, float2& k0, float2& gx, float2& gy) {
+    const float2 x2 = fma2(dx, dx, mul2(dy, dy));
+    const float2 ix = make_float2(bes::mufu::rsqrt(x2.x), bes::mufu::rsqrt(x2.y));
+    const float2 x = mul2(x2, ix);
+    const float2 ar = mul2(x, f2(-1.4426950408889634f));
+    const float2 e = mul2(make_float2(bes::mufu::ex2(ar.x), bes::mufu::ex2(ar.y)),
+                          make_float2(bes::mufu::rsqrt(x.x), bes::mufu::rsqrt(x.y)));
+    float2 pl = fma2(ix, f2(0.03405312f), f2(-0.0804928f));
+    pl = fma2(ix, pl, f2(0.09405952f));
+    pl = fma2(ix, pl, f2(-0.08499568f));
+    pl = fma2(ix, pl, f2(0.08758272f));
+    pl = fma2(ix, pl, f2(-0.15664716f));
+    pl = fma2(ix, pl, f2(1.25331414f));
+    k0 = fma2(e, pl, k0);
+    if (GRAD) {
+      float2 p1 = fma2(ix, f2(-0.0436768f), f2(0.10419648f));
+      p1 = fma2(ix, p1, f2(-0.12485648f));
+      p1 = fma2(ix, p1, f2(0.12034144f));
+      p1 = fma2(ix, p1, f2(-0.1462248f));
+      p1 = fma2(ix, p1, f2(0.46997238f));
+      p1 = fma2(ix, p1, f2(1.25331414f));
+      const float2 k1ix = mul2(mul2(e, ix), p1);
+      gx = fma2(k1ix, dx, gx);
+      gy = fma2(k1ix, dy, gy);
     }
   };
 
-  // Branch-free variant for subtiles where no pair of the warp can have
-  // beta r <= 2: every image takes the large-argument fit (K0 at beta r > 88
-  // underflows to 0), so the nine chains are independent and interleave.
-  // Coordinates here are scaled by beta (beta txr, beta tyr per pair, the
-  // source's in shared memory), so x^2 = dx^2 + dy^2 and K1(x)/x multiplies
-  // the scaled difference directly; the fits' variable y = 2/x is folded into
-  // their coefficients (c_k 2^k).  ALL: every image active, no per-image test.
-  auto source_far = [&](int jj, unsigned any, auto diff, auto all_tag) {
-    constexpr bool ALL = decltype(all_tag)::value;
-    float K0s = 0.f, K1x = 0.f, K1y = 0.f;
-#pragma unroll
-    for (int i = 0; i < NIMG; ++i) {
-      if (!ALL && !(any & (1u << i))) continue;
-      float dx, dy;
-      diff(i, dx, dy);
-      const float x2 = fmaf(dx, dx, dy * dy);
-      const float ix = bes::mufu::rsqrt(x2);
-      const float x = x2 * ix;
-      const float e = bes::mufu::ex2(-1.4426950408889634f * x) * bes::mufu::rsqrt(x);
-      const float k0 = e * (1.25331414f + ix * (-0.15664716f + ix * (0.08758272f + ix * (-0.08499568f + ix * (0.09405952f + ix * (-0.0804928f + ix * 0.03405312f))))));
-      K0s += k0;
-      if (GRAD) {
-        const float k1ix = e * ix * (1.25331414f + ix * (0.46997238f + ix * (-0.1462248f + ix * (0.12034144f + ix * (-0.12485648f + ix * (0.10419648f + ix * (-0.0436768f)))))));
-        K1x = fmaf(k1ix, dx, K1x);
-        K1y = fmaf(k1ix, dy, K1y);
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < NQ4; ++g) {
-      const float4 q4 = s_q4[g][jj];
-      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = 4 * g + k;
-        if (r >= NR) break;
-        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
-        if (GRAD) {
-          S[r][1 % NA] = fmaf(qv[k], K1x, S[r][1 % NA]);
-          S[r][2 % NA] = fmaf(qv[k], K1y, S[r][2 % NA]);
-        }
-      }
-    }
-  };
-
-  // Packed form of source_far for subtiles where every image is active, on
-  // the potential: the images go two per FADD2/FMUL2/FFMA2 (the MUFU
-  // operations stay one per value), which halves the issue slots of the
-  // arithmetic; bx2/by2 hold the beta-scaled target coordinates relative to
-  // the subtile centre for the image pairs (2k, 2k + 1), (bxs, bys) those of
-  // the last image (NIMG is odd).
-  auto source_far_pk = [&](int jj, const float2* bx2, const float2* by2, float bxs, float bys) {
-    const float2 p = s_pb[jj];
-    const float2 npx = f2(-p.x), npy = f2(-p.y);
-    float2 acc = f2(0.f);
-#pragma unroll
-    for (int k = 0; k < NIMG / 2; ++k) {
-      const float2 dx = add2(bx2[k], npx), dy = add2(by2[k], npy);
-      const float2 x2 = fma2(dx, dx, mul2(dy, dy));
-      const float2 ix = make_float2(bes::mufu::rsqrt(x2.x), bes::mufu::rsqrt(x2.y));
-      const float2 x = mul2(x2, ix);
-      const float2 ar = mul2(x, f2(-1.4426950408889634f));
-      const float2 e = mul2(make_float2(bes::mufu::ex2(ar.x), bes::mufu::ex2(ar.y)),
-                            make_float2(bes::mufu::rsqrt(x.x), bes::mufu::rsqrt(x.y)));
-      float2 pl = fma2(ix, f2(0.03405312f), f2(-0.0804928f));
-      pl = fma2(ix, pl, f2(0.09405952f));
-      pl = fma2(ix, pl, f2(-0.08499568f));
-      pl = fma2(ix, pl, f2(0.08758272f));
-      pl = fma2(ix, pl, f2(-0.15664716f));
-      pl = fma2(ix, pl, f2(1.25331414f));
-      acc = fma2(e, pl, acc);
-    }
-    float K0s;
-    {
-      const float dx = bxs - p.x, dy = bys - p.y;
-      const float x2 = fmaf(dx, dx, dy * dy);
-      const float ix = bes::mufu::rsqrt(x2);
-      const float x = x2 * ix;
-      const float e = bes::mufu::ex2(-1.4426950408889634f * x) * bes::mufu::rsqrt(x);
-      const float k0 = e * (1.25331414f + ix * (-0.15664716f + ix * (0.08758272f + ix * (-0.08499568f + ix * (0.09405952f + ix * (-0.0804928f + ix * 0.03405312f))))));
-      K0s = (acc.x + acc.y) + k0;
-    }
-#pragma unroll
-    for (int g = 0; g < NQ4; ++g) {
-      const float4 q4 = s_q4[g][jj];
-      const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int r = 4 * g + k;
-        if (r >= NR) break;
-        S[r][0] = fmaf(qv[k], K0s, S[r][0]);
-      }
-    }
-  };
-
-  // Tiles are classified kP2PThreads at a time, one thread per tile: per
-  // image, some pair within the cutoff (any) or every pair within it (all).
-  // FP32 on the outward-rounded boxes with a relative margin: a tile
-  // misjudged at the margin only adds or drops terms below the cutoff's bound.
-  // Culled tiles then cost no barrier.
-  __shared__ unsigned s_tany[kP2PThreads], s_tall[kP2PThreads];
   const int ntile = (j1 - j0 + kP2PTile - 1) / kP2PTile;
   for (int g0 = 0; g0 < ntile; g0 += kP2PThreads) {
     __syncthreads();
     {
-      const int t = g0 + threadIdx.x;
-      unsigned many = 0u, mall = 0u;
+      // per tile and image: some pair within the cutoff (FP32 on the
+      // outward-rounded boxes with a relative margin: a tile misjudged at the
+      // margin only adds or drops terms below the cutoff's bound)
+      const int t = g0 + tid;
+      unsigned many = 0u;
       if (t < ntile) {
         const float4 sb = a.s_box[(j0 + t * kP2PTile) / kBoxTile];
         const float c2 = a.cut * a.cut;
@@ -550,9 +446,7 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
           const float mx = 1e-5f * (fabsf(tb.x) + fabsf(sb.x) + fabsf(a.offf[i][0])) + 1e-6f * hx;
           const float my = 1e-5f * (fabsf(tb.y) + fabsf(sb.y) + fabsf(a.offf[i][1])) + 1e-6f * hy;
           const float ex = fmaxf(0.f, cx - hx - mx), ey = fmaxf(0.f, cy - hy - my);
-          const float fx = cx + hx + mx, fy = cy + hy + my;
           if (ex * ex + ey * ey <= c2) many |= 1u << i;
-          if (fx * fx + fy * fy < c2) mall |= 1u << i;
         }
         if (a.work && many) {
           const int nbt = min(kP2PTile, j1 - (j0 + t * kP2PTile));
@@ -560,121 +454,162 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
                                 (unsigned long long)min(kP2PThreads, a.nt - bx * kP2PThreads));
         }
       }
-      s_tany[threadIdx.x] = many;
-      s_tall[threadIdx.x] = mall;
+      s_tany[tid] = many;
     }
     __syncthreads();
     const int gn = min(kP2PThreads, ntile - g0);
-  for (int tt = 0; tt < gn; ++tt) {
-    const unsigned any = s_tany[tt], all = s_tall[tt];
-    if (any == 0u) continue;
-    const int jb = j0 + (g0 + tt) * kP2PTile;
-    const int nb = min(kP2PTile, j1 - jb);
-    __syncthreads();
-    for (int k = threadIdx.x; k < kP2PTile; k += kP2PThreads) {
-      // padding: zero strength at the subtile centre (finite distances)
-      const bool v = k < nb;
-      s_p[k] = v ? a.s_rel[jb + k] : make_float2(0.f, 0.f);
-      s_pb[k] = make_float2(beta * s_p[k].x, beta * s_p[k].y);
-      s_h[k] = v ? a.s_hl[jb + k] : s_c_src(a, jb, k, nb);
-      if (k < NSUB) {
-        s_c[k] = (k * kSubtile < nb) ? a.s_sub[jb / kSubtile + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        s_e[k] = (k * kSubtile < nb) ? a.s_ext[jb / kSubtile + k] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int g = 0; g < NQ4; ++g) {
-        float qv[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int r = 4 * g + t;
-          qv[t] = (v && r < nr) ? a.qs[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
-        }
-        s_q4[g][k] = make_float4(qv[0], qv[1], qv[2], qv[3]);
-      }
-    }
-    __syncthreads();
-    for (int js = 0; js < nb; js += kP2PSub) {
-      bool near = false, small = false;
+    for (int tt = 0; tt < gn; ++tt) {
+      const unsigned any = s_tany[tt];
+      if (any == 0u) continue;
+      const int jb = j0 + (g0 + tt) * kP2PTile;
+      const int nb = min(kP2PTile, j1 - jb);
+      __syncthreads();
       {
-        const float4 c = s_c[js / kSubtile];
-        const float2 e = s_e[js / kSubtile];
-        const float bxe = 2.f * e.x + e.y, bye = e.x + 2.f * e.y;
-        // beta r <= 2 possible: target within 2 / beta (+ margin) of the subtile box
-        const float sxe = e.x + rsm, sye = e.y + rsm;
-#pragma unroll
-        for (int i = 0; i < NIMG; ++i) {
-          txr[i] = (thx(i) - c.x) + (tlx(i) - c.y);
-          tyr[i] = (thy(i) - c.z) + (tly(i) - c.w);
-          const bool act = (any & (1u << i)) != 0u;
-          near |= act && fabsf(txr[i]) < bxe && fabsf(tyr[i]) < bye;
-          small |= act && fabsf(txr[i]) < sxe && fabsf(tyr[i]) < sye;
+        // padding: zero strength at the subtile centre (finite distances)
+        const int k = tid;
+        const bool v = k < nb;
+        const float2 p = v ? a.s_rel[jb + k] : make_float2(0.f, 0.f);
+        s_bs[0][k] = beta * p.x;
+        s_bs[1][k] = beta * p.y;
+        const float4 h = v ? a.s_hl[jb + k] : s_c_src(a, jb, k, nb);
+        s_hs[0][k] = h.x;
+        s_hs[1][k] = h.y;
+        s_hs[2][k] = h.z;
+        s_hs[3][k] = h.w;
+        if (k < NSUB) {
+          s_c[k] = (k * kSubtile < nb) ? a.s_sub[jb / kSubtile + k] : make_float4(0.f, 0.f, 0.f, 0.f);
+          s_e[k] = (k * kSubtile < nb) ? a.s_ext[jb / kSubtile + k] : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s_q[r][k] = (v && r < nr) ? a.qs[(size_t)(r0 + r) * a.ns + jb + k] : 0.f;
       }
-      if (!__any_sync(0xffffffffu, near || small)) {
-        if (!GRAD && (NIMG & 1) && any == (1u << NIMG) - 1u) {
-          float2 bx2[NIMG / 2], by2[NIMG / 2];
+      __syncthreads();
+      for (int js = 0; js < nb; js += kP2PSub) {
+        // routing of the active images for this subtile (warp-uniform)
+        unsigned slow = 0u;
+        int nf = 0;
+        {
+          const float4 c = s_c[js / kSubtile];
+          const float2 e = s_e[js / kSubtile];
+          const float bxe = 2.f * e.x + e.y, bye = e.x + 2.f * e.y;
+          const float sxe = e.x + rsm, sye = e.y + rsm;
+          float bxr[NIMG], byr[NIMG];
+          unsigned mine = 0u;
 #pragma unroll
-          for (int k = 0; k < NIMG / 2; ++k) {
-            bx2[k] = make_float2(beta * txr[2 * k], beta * txr[2 * k + 1]);
-            by2[k] = make_float2(beta * tyr[2 * k], beta * tyr[2 * k + 1]);
+          for (int i = 0; i < NIMG; ++i) {
+            bxr[i] = byr[i] = 0.f;
+            if (!(any & (1u << i))) continue;
+            const float xr = (s_tc[0][i][tid] - c.x) + (s_tc[1][i][tid] - c.y);
+            const float yr = (s_tc[2][i][tid] - c.z) + (s_tc[3][i][tid] - c.w);
+            bxr[i] = beta * xr;
+            byr[i] = beta * yr;
+            const float ax = fabsf(xr), ay = fabsf(yr);
+            if (in && ((ax < bxe && ay < bye) || (ax < sxe && ay < sye))) mine |= 1u << i;
           }
-          const float bxs = beta * txr[NIMG - 1], bys = beta * tyr[NIMG - 1];
-#pragma unroll 2
-          for (int jj = js; jj < js + kP2PSub; ++jj) source_far_pk(jj, bx2, by2, bxs, bys);
-        } else if (any == (1u << NIMG) - 1u) {
-#pragma unroll 2
-          for (int jj = js; jj < js + kP2PSub; ++jj) {
-            const float2 p = s_pb[jj];
-            source_far(jj, any, [&](int i, float& dx, float& dy) {
-              dx = fmaf(beta, txr[i], -p.x);
-              dy = fmaf(beta, tyr[i], -p.y);
-            },
-                       std::true_type{});
-          }
-        } else {
-#pragma unroll 2
-          for (int jj = js; jj < js + kP2PSub; ++jj) {
-            const float2 p = s_pb[jj];
-            source_far(jj, any, [&](int i, float& dx, float& dy) {
-              dx = fmaf(beta, txr[i], -p.x);
-              dy = fmaf(beta, tyr[i], -p.y);
-            },
-                       std::false_type{});
-          }
+          slow = any & __reduce_or_sync(kFull, mine);
+          const unsigned fast = any & ~slow;
+#pragma unroll
+          for (int i = 0; i < NIMG; ++i)
+            if (fast & (1u << i)) s_bt[nf++][tid] = make_float2(bxr[i], byr[i]);
         }
-      } else if (!__any_sync(0xffffffffu, small)) {
-        // close pairs but none with beta r <= 2: exact differences (beta-scaled),
-        // the branch-free large-argument fit
+        for (int jj = js; jj < js + kP2PSub; jj += 4) {
+          float2 kA = f2(0.f), kB = f2(0.f), gxA = f2(0.f), gyA = f2(0.f), gxB = f2(0.f), gyB = f2(0.f);
+          if (nf) {
+            const float4 px = *reinterpret_cast<const float4*>(&s_bs[0][jj]);
+            const float4 py = *reinterpret_cast<const float4*>(&s_bs[1][jj]);
+            const float2 npxA = make_float2(-px.x, -px.y), npxB = make_float2(-px.z, -px.w);
+            const float2 npyA = make_float2(-py.x, -py.y), npyB = make_float2(-py.z, -py.w);
+#pragma unroll 3
+            for (int k = 0; k < nf; ++k) {
+              const float2 bt = s_bt[k][tid];
+              far_pair(add2(f2(bt.x), npxA), add2(f2(bt.y), npyA), kA, gxA, gyA);
+              far_pair(add2(f2(bt.x), npxB), add2(f2(bt.y), npyB), kB, gxB, gyB);
+            }
+          }
+          if (slow) {
+            const float4 hx = *reinterpret_cast<const float4*>(&s_hs[0][jj]);
+            const float4 lx = *reinterpret_cast<const float4*>(&s_hs[1][jj]);
+            const float4 hy = *reinterpret_cast<const float4*>(&s_hs[2][jj]);
+            const float4 ly = *reinterpret_cast<const float4*>(&s_hs[3][jj]);
 #pragma unroll 1
-        for (int jj = js; jj < js + kP2PSub; ++jj) {
-          const float4 h = s_h[jj];
-          source_far(jj, any, [&](int i, float& dx, float& dy) {
-            dx = beta * ((thx(i) - h.x) + (tlx(i) - h.y));
-            dy = beta * ((thy(i) - h.z) + (tly(i) - h.w));
-          }, std::false_type{});
+            for (unsigned m = slow; m; m &= m - 1u) {
+              const int i = __ffs(m) - 1;
+              const float thx = s_tc[0][i][tid], tlx = s_tc[1][i][tid];
+              const float thy = s_tc[2][i][tid], tly = s_tc[3][i][tid];
+              // exact differences (t_hi - s_hi) + (t_lo - s_lo)
+              const float2 dxA = add2(add2(f2(thx), make_float2(-hx.x, -hx.y)), add2(f2(tlx), make_float2(-lx.x, -lx.y)));
+              const float2 dxB = add2(add2(f2(thx), make_float2(-hx.z, -hx.w)), add2(f2(tlx), make_float2(-lx.z, -lx.w)));
+              const float2 dyA = add2(add2(f2(thy), make_float2(-hy.x, -hy.y)), add2(f2(tly), make_float2(-ly.x, -ly.y)));
+              const float2 dyB = add2(add2(f2(thy), make_float2(-hy.z, -hy.w)), add2(f2(tly), make_float2(-ly.z, -ly.w)));
+              float2 r2A = fma2(dxA, dxA, mul2(dyA, dyA)), r2B = fma2(dxB, dxB, mul2(dyB, dyB));
+              float2 mA = f2(1.f), mB = f2(1.f);
+              if (i == CENTER) {
+                // a zero distance (the target itself) is skipped
+                mA = make_float2(r2A.x > 0.f ? 1.f : 0.f, r2A.y > 0.f ? 1.f : 0.f);
+                mB = make_float2(r2B.x > 0.f ? 1.f : 0.f, r2B.y > 0.f ? 1.f : 0.f);
+                r2A = make_float2(r2A.x > 0.f ? r2A.x : 1.f, r2A.y > 0.f ? r2A.y : 1.f);
+                r2B = make_float2(r2B.x > 0.f ? r2B.x : 1.f, r2B.y > 0.f ? r2B.y : 1.f);
+              }
+              const float2 x2A = mul2(r2A, f2(beta2)), x2B = mul2(r2B, f2(beta2));
+              const bool sml = fminf(fminf(x2A.x, x2A.y), fminf(x2B.x, x2B.y)) <= 4.0f;
+              const bool lrg = fmaxf(fmaxf(x2A.x, x2A.y), fmaxf(x2B.x, x2B.y)) > 4.0f;
+              const bool doS = __any_sync(kFull, sml), doL = __any_sync(kFull, lrg);
+              float2 k0A = f2(0.f), k0B = f2(0.f), k1A = f2(0.f), k1B = f2(0.f);
+              if (doS) {
+                if (GRAD) {
+                  bes::pk::k01_small(x2A, &k0A, &k1A);
+                  bes::pk::k01_small(x2B, &k0B, &k1B);
+                } else {
+                  k0A = bes::pk::k0_small(x2A);
+                  k0B = bes::pk::k0_small(x2B);
+                }
+              }
+              if (doL) {
+                float2 l0A, l0B, l1A = f2(0.f), l1B = f2(0.f);
+                if (GRAD) {
+                  bes::pk::k01_large(x2A, &l0A, &l1A);
+                  bes::pk::k01_large(x2B, &l0B, &l1B);
+                } else {
+                  l0A = bes::pk::k0_large(x2A);
+                  l0B = bes::pk::k0_large(x2B);
+                }
+                if (x2A.x > 4.0f) { k0A.x = l0A.x; k1A.x = l1A.x; }
+                if (x2A.y > 4.0f) { k0A.y = l0A.y; k1A.y = l1A.y; }
+                if (x2B.x > 4.0f) { k0B.x = l0B.x; k1B.x = l1B.x; }
+                if (x2B.y > 4.0f) { k0B.y = l0B.y; k1B.y = l1B.y; }
+              }
+              kA = fma2(k0A, mA, kA);
+              kB = fma2(k0B, mB, kB);
+              if (GRAD) {
+                // K1(beta r) / r = beta K1(x) / x
+                const float2 k1rA = mul2(mul2(k1A, f2(beta)), mA), k1rB = mul2(mul2(k1B, f2(beta)), mB);
+                gxA = fma2(k1rA, dxA, gxA);
+                gyA = fma2(k1rA, dyA, gyA);
+                gxB = fma2(k1rB, dxB, gxB);
+                gyB = fma2(k1rB, dyB, gyB);
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const float4 q = *reinterpret_cast<const float4*>(&s_q[r][jj]);
+            const float2 qA = make_float2(q.x, q.y), qB = make_float2(q.z, q.w);
+            S[r][0] = fma2(qB, kB, fma2(qA, kA, S[r][0]));
+            if (GRAD) {
+              S[r][1 % NA] = fma2(qB, gxB, fma2(qA, gxA, S[r][1 % NA]));
+              S[r][2 % NA] = fma2(qB, gyB, fma2(qA, gyA, S[r][2 % NA]));
+            }
+          }
         }
-      } else {
-        // close pairs or beta r <= 2 in reach: exact differences, both K0 fits
-        // (one code path for both cases keeps the kernel small in the
-        // instruction cache)
-#pragma unroll 1
-        for (int jj = js; jj < js + kP2PSub; ++jj) {
-          const float4 h = s_h[jj];
-          source(jj, any, all, [&](int i, float& dx, float& dy) {
-            dx = (thx(i) - h.x) + (tlx(i) - h.y);
-            dy = (thy(i) - h.z) + (tly(i) - h.w);
-          });
-        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+#pragma unroll
+          for (int k = 0; k < NA; ++k) {
+            K[r][k].add(S[r][k].x + S[r][k].y);
+            S[r][k] = f2(0.f);
+          }
       }
-#pragma unroll
-      for (int r = 0; r < NR; ++r)
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-          K[r][k].add(S[r][k]);
-          S[r][k] = 0.f;
-        }
     }
-  }
   }
   if (!in) return;
   const int lo = a.t_perm ? a.t_perm[l] : l;
