@@ -35,6 +35,21 @@ __device__ __forceinline__ void expm1c(T a, T b, T* re, T* im) {
   *im = (em + T(1)) * (T(2) * sh * ch);
 }
 
+// Exact FP32 -> FP64 conversion by bit operations on the integer pipes.  On
+// this GPU the conversion instruction runs on the FP64 unit (about 1/64 of
+// the FP32 rate), so FP32 kernels that hand many partial sums to FP64
+// outputs convert this way: sign | (exponent + 1023 - 127) << 52 |
+// mantissa << 29 for normal numbers, infinities and NaNs kept, zero and FP32
+// subnormals to a signed zero (the FP32 kernels flush subnormals anyway).
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned ed = e == 0xffu ? 0x7ffu : e + 896u;
+  const unsigned hi = (u & 0x80000000u) | (e ? ((ed << 20) | ((u >> 3) & 0xfffffu)) : 0u);
+  const unsigned lo = e ? (u << 29) : 0u;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // Running sum of many terms.  FP32: Kahan compensation (the error stays at a
 // few ulp of the result instead of growing with the number of terms); FP64:
 // plain sum.
@@ -51,7 +66,12 @@ struct KSum {
       s += v;
     }
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ double value() const {
+    if constexpr (sizeof(T) == 4)
+      return f2d(s) - f2d(c);
+    else
+      return (double)s - (double)c;
+  }
 };
 
 }  // namespace dm

@@ -29,7 +29,7 @@ namespace pfmm {
 // ----------------------------------------------------------------------------
 __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* __restrict__ pts, double* __restrict__ c64,
                               float* __restrict__ cf, int* __restrict__ U,
-                              int* __restrict__ status, int* __restrict__ V, double invY) {
+                              int* __restrict__ status, int* __restrict__ V, double invY, double xid) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = pts[i], y = pts[istride + i];
@@ -54,7 +54,8 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   c64[n + i] = yc;
   cf[i] = (float)xc;
   cf[n + i] = (float)yc;
-  double v = xc / g.d;
+  // x / d = u1 + u2 xi / d (no FP64 division)
+  double v = fma(u2, xid, u1);
   v -= floor(v + 0.5);
   U[i] = (int)(unsigned)(long long)llrint(v * 4294967296.0);
   // singly periodic NUFFT: fixed-point phase 2^32 y / Y of the transform in y
@@ -97,67 +98,85 @@ __global__ void k_ordered_sum(const double* __restrict__ part, int nb, int m, in
   out[(size_t)(i / g) * ostride + i % g] += s;
 }
 
-// K0: strengths (canonical frame) and FP64 moments per rhs:
+// K0: strengths (canonical frame) and the moments per rhs:
 //   mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y, [2] = sum |q| (all comps), [3] = sum q y' (f_x y')
+// The cancelling sums 0, 1 and 3 are FP64; sum |q| (only the scale of the
+// neutrality test) is FP32.  Each thread sums kPrepPts points (a block covers
+// kPrepPts * blockDim.x consecutive points, coalesced per step), so the warp
+// reductions in FP64 (slow on this GPU) are amortised over several points.
+constexpr int kPrepPts = 8;
+
+__device__ __forceinline__ bool finite64(double v) {
+  return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
+}
+
 __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
                          const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
                          double* __restrict__ mom, int* __restrict__ status, int project, double* __restrict__ part) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  bool in = i < ns;
-  double y = in ? src64[ns + i] : 0.0;
-  int lane = threadIdx.x & 31;
+  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kPrepPts + threadIdx.x;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const double inv_ns = project ? 1.0 / (double)ns : 0.0;
+  bool bad = false;
   for (int r = 0; r < nrhs; ++r) {
-    double a = 0, b = 0;
-    if (in) {
+    const double mx = project ? mom[r * 8 + 5] * inv_ns : 0.0;
+    const double my = (project && ncomp == 2) ? mom[r * 8 + 6] * inv_ns : 0.0;
+    double v0 = 0.0, v1 = 0.0, v3 = 0.0;
+    float v2 = 0.f;
+#pragma unroll 2
+    for (int k = 0; k < kPrepPts; ++k) {
+      const int64_t i = base + (int64_t)k * blockDim.x;
+      if (i >= ns) break;
+      double a, b = 0.0;
       if (ncomp == 1) {
-        a = q[(size_t)r * qs + i];
-        if (project) a -= mom[r * 8 + 5] / (double)ns;
+        a = q[(size_t)r * qs + i] - mx;
       } else {
-        double fx = q[((size_t)r * 2) * qs + i], fy = q[((size_t)r * 2 + 1) * qs + i];
-        if (project) {
-          fx -= mom[r * 8 + 5] / (double)ns;
-          fy -= mom[r * 8 + 6] / (double)ns;
-        }
+        const double fx = q[((size_t)r * 2) * qs + i] - mx, fy = q[((size_t)r * 2 + 1) * qs + i] - my;
         a = g.rot[0] * fx + g.rot[1] * fy;
         b = g.rot[2] * fx + g.rot[3] * fy;
       }
-      if (!isfinite(a) || !isfinite(b)) {
-        atomicOr(status, ST_NONFINITE);
-        a = 0;
-        b = 0;
+      if (!finite64(a) || !finite64(b)) {
+        bad = true;
+        a = 0.0;
+        b = 0.0;
       }
+      const float af = (float)a, bf = (float)b;
       if (ncomp == 1) {
         if (qc) qc[(size_t)r * ns + i] = a;
-        qf[(size_t)r * ns + i] = (float)a;
+        qf[(size_t)r * ns + i] = af;
       } else {
         qc[((size_t)r * 2) * ns + i] = a;
         qc[((size_t)r * 2 + 1) * ns + i] = b;
-        qf[((size_t)r * 2) * ns + i] = (float)a;
-        qf[((size_t)r * 2 + 1) * ns + i] = (float)b;
+        qf[((size_t)r * 2) * ns + i] = af;
+        qf[((size_t)r * 2 + 1) * ns + i] = bf;
+        v1 += b;
       }
+      v0 += a;
+      v3 = fma(a, src64[ns + i], v3);
+      v2 += fabsf(af) + fabsf(bf);
     }
-    double v0 = a, v1 = b, v2 = fabs(a) + fabs(b), v3 = a * y;
     for (int o = 16; o > 0; o >>= 1) {
       v0 += __shfl_down_sync(0xffffffffu, v0, o);
-      v1 += __shfl_down_sync(0xffffffffu, v1, o);
+      if (ncomp == 2) v1 += __shfl_down_sync(0xffffffffu, v1, o);
       v2 += __shfl_down_sync(0xffffffffu, v2, o);
       v3 += __shfl_down_sync(0xffffffffu, v3, o);
     }
     if (lane == 0) {
       if (part) {  // deterministic mode: part[warp][r * 4 + k]
-        double* w = part + ((size_t)(i >> 5) * nrhs + r) * 4;
+        double* w = part + ((size_t)warp * nrhs + r) * 4;
         w[0] = v0;
         w[1] = v1;
-        w[2] = v2;
+        w[2] = (double)v2;
         w[3] = v3;
       } else {
         atomicAdd(mom + r * 8 + 0, v0);
-        atomicAdd(mom + r * 8 + 1, v1);
-        atomicAdd(mom + r * 8 + 2, v2);
+        if (ncomp == 2) atomicAdd(mom + r * 8 + 1, v1);
+        atomicAdd(mom + r * 8 + 2, (double)v2);
         atomicAdd(mom + r * 8 + 3, v3);
       }
     }
   }
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 // ----------------------------------------------------------------------------
@@ -196,6 +215,38 @@ __device__ __forceinline__ Term decode_term(const Far& f, const Geom& g, int t) 
   return T;
 }
 
+// The same decoding in FP32 for the mixed kernels (no FP64 division or
+// square root per term): alpha_m = m (2 pi / d), decays from an FP32 square
+// root.  The south/north phases of the mixed path come from the fixed-point
+// phase, so alpha_m enters only the gradient factors.
+struct TermF {
+  int part, m;
+  float a, b;
+};
+__device__ __forceinline__ TermF decode_term_f(const Far& f, int t) {
+  TermF T;
+  const int mlo = f.mode0 ? 0 : 1;
+  const float b2 = f.beta_f * f.beta_f;
+  if (t < 2 * f.nsn) {
+    T.part = t < f.nsn ? 0 : 1;
+    T.m = (t < f.nsn ? t : t - f.nsn) + mlo;
+    T.a = (float)T.m * f.alpha1f;
+    T.b = decays_beta(f) ? sqrtf(fmaf(T.a, T.a, b2)) : fabsf(T.a);
+  } else {
+    int n = t - 2 * f.nsn;
+    T.part = n < f.Nq ? 2 : 3;
+    if (n >= f.Nq) n -= f.Nq;
+    T.m = n;
+    T.a = __double2float_rn(f.nodes[2 * n]);
+    T.b = decays_beta(f) ? sqrtf(fmaf(T.a, T.a, b2)) : T.a;
+  }
+  return T;
+}
+
+// FP64 value of a kernel-precision number (FP32: the integer-pipe conversion)
+__device__ __forceinline__ double to_d(float v) { return dm::f2d(v); }
+__device__ __forceinline__ double to_d(double v) { return v; }
+
 // ----------------------------------------------------------------------------
 // K1: coefficient formation.  grid (chunks, term blocks, rhs groups).
 // coef layout [nrhs][nch][nterm] complex double; Stokes channels:
@@ -222,12 +273,26 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
   const bool active = t < f.nterm;
   const int r0 = blockIdx.z * kRB;
   const int nr = min(kRB, f.nrhs - r0);
-  Term tm = decode_term(f, g, active ? t : 0);
-  const T a = (T)tm.a, b = (T)tm.b;
-  const T sgn = (tm.part == 0 || tm.part == 2) ? T(1) : T(-1);
-  const bool sn = tm.part < 2;
+  int tpart, tmm;
+  T a, b;
+  double inv_d = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    const TermF tf = decode_term_f(f, active ? t : 0);
+    tpart = tf.part;
+    tmm = tf.m;
+    a = tf.a;
+    b = tf.b;
+  } else {
+    const Term tm = decode_term(f, g, active ? t : 0);
+    tpart = tm.part;
+    tmm = tm.m;
+    a = (T)tm.a;
+    b = (T)tm.b;
+    inv_d = 1.0 / g.d;
+  }
+  const T sgn = (tpart == 0 || tpart == 2) ? T(1) : T(-1);
+  const bool sn = tpart < 2;
   const bool we_m1 = !sn && (KER == PFMM_LAPLACE || KER == PFMM_STOKES);
-  const double inv_d = 1.0 / g.d;
 
   double acc[kRB][NCH][2];
 #pragma unroll
@@ -267,9 +332,9 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
         T e = dm::ex(sgn * b * y);
         T sp, cp;
         if constexpr (sizeof(T) == 4)
-          dm::phase_fixed(tm.m, s_U[jj], &sp, &cp);
+          dm::phase_fixed(tmm, s_U[jj], &sp, &cp);
         else
-          dm::sincospi_(T(2.0 * tm.m * ((double)x * inv_d)), &sp, &cp);
+          dm::sincospi_(T(2.0 * tmm * ((double)x * inv_d)), &sp, &cp);
         Rr = e * cp;
         Ri = -e * sp;
         Qr = Rr;
@@ -449,7 +514,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   const T wc = T(g.wc), ws = T(g.ws);
   const T xw = wc * x - ws * y, yw = ws * x + wc * y;
   const int U = (in && tU) ? tU[l] : 0;
-  const double xd = in ? (double)x / g.d : 0.0;
+  const double xd = (sizeof(T) == 8 && in) ? (double)x / g.d : 0.0;  // FP64 path's phase
   // accumulators: scalar [pot, gx, gy]; Stokes [ux, uy].  Compensated in FP32:
   // a few hundred terms of the size of the result are summed per target.
   constexpr int NA = VEC ? 2 : 3;
@@ -459,11 +524,19 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
     const int nc = min(kEvalChunk, f.nterm - t0);
     __syncthreads();
     for (int k = threadIdx.x; k < nc; k += kEvalThreads) {
-      Term tm = decode_term(f, g, t0 + k);
-      s_a[k] = (T)tm.a;
-      s_b[k] = (T)tm.b;
-      s_m[k] = tm.m;
-      s_part[k] = tm.part;
+      if constexpr (sizeof(T) == 4) {
+        const TermF tm = decode_term_f(f, t0 + k);
+        s_a[k] = tm.a;
+        s_b[k] = tm.b;
+        s_m[k] = tm.m;
+        s_part[k] = tm.part;
+      } else {
+        const Term tm = decode_term(f, g, t0 + k);
+        s_a[k] = (T)tm.a;
+        s_b[k] = (T)tm.b;
+        s_m[k] = tm.m;
+        s_part[k] = tm.part;
+      }
     }
     for (int k = threadIdx.x; k < kRB * NW * kEvalChunk; k += kEvalThreads) {
       int r = k / (NW * kEvalChunk), rem = k % (NW * kEvalChunk), c = rem / kEvalChunk, tt = rem % kEvalChunk;
@@ -540,9 +613,9 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   }
   if (!in) return;
   const double* R = g.rot;  // input = rot^T canonical
+  const double yd = to_d(y);
   for (int r = 0; r < nr; ++r) {
     const double cc = mom[(r0 + r) * 8 + 4];
-    const double yd = (double)y;
     if (VEC) {
       double ux = acc[r][0].value() + cc * yd, uy = acc[r][1].value();
       double* px = pot + ((size_t)(r0 + r) * 2) * os + l;
@@ -550,10 +623,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
       *px = (accum ? *px : 0.0) + R[0] * ux + R[2] * uy;
       *py = (accum ? *py : 0.0) + R[1] * ux + R[3] * uy;
     } else {
-      double p = acc[r][0].value() + cc * yd;
-      double gx = acc[r][1].value(), gy = acc[r][2].value() + cc;
+      double p = acc[r][0].value();
+      if (cc != 0.0) p += cc * yd;
       if (pot) pot[(size_t)(r0 + r) * os + l] = p;
       if (grad) {
+        const double gx = acc[r][1].value(), gy = acc[r][2].value() + cc;
         grad[((size_t)(r0 + r) * 2) * os + l] = R[0] * gx + R[2] * gy;
         grad[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * gx + R[3] * gy;
       }
@@ -573,19 +647,22 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
   bool mixed = p->opts.precision == PFMM_MIXED;
   const bool wantV = p->p1_nu && p->path == PFMM_PATH_NUFFT;
   const double invY = p->p1_nu ? 1.0 / p->p1_Y : 0.0;
+  const double xid = p->geom.xi / p->geom.d;
   k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
                                                  (int*)(ws + L.srcU), status,
-                                                 wantV ? (int*)(ws + L.srcV) : nullptr, invY);
+                                                 wantV ? (int*)(ws + L.srcV) : nullptr, invY, xid);
   if (!self && nt > 0)
     k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
                                                    (int*)(ws + L.trgU), status,
-                                                   wantV ? (int*)(ws + L.trgV) : nullptr, invY);
+                                                   wantV ? (int*)(ws + L.trgV) : nullptr, invY, xid);
   g_launches = (!self && nt > 0) ? 3 : 2;
   const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) &&
                       (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);
   // deterministic mode: per-warp partial sums, added in warp order
   double* part = (p->opts.flags & PFMM_DETERMINISTIC) ? (double*)(ws + L.det) : nullptr;
   const int nwarp = cdiv_i(ns, 32), nrhs = p->opts.nrhs;
+  // k_prep_q: kPrepPts points per thread, every warp of its grid writes a partial
+  const int qblocks = cdiv_i(ns, 256 * kPrepPts), qwarps = qblocks * 8;
   double* mom = (double*)(ws + L.moments);
   if (project) {
     k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, nrhs, ns, p->s_stride, q, mom, part);
@@ -596,10 +673,10 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
       ++g_launches;
     }
   }
-  k_prep_q<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, p->ncomp, nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
-                                            (double*)(ws + L.qc), (float*)(ws + L.qf), mom, status, project, part);
+  k_prep_q<<<qblocks, 256, 0, st>>>(p->geom, p->ncomp, nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
+                                     (double*)(ws + L.qc), (float*)(ws + L.qf), mom, status, project, part);
   if (part) {
-    k_ordered_sum<<<cdiv_i(4 * nrhs, 128), 128, 0, st>>>(part, nwarp, 4 * nrhs, 4, 8, mom);
+    k_ordered_sum<<<cdiv_i(4 * nrhs, 128), 128, 0, st>>>(part, qwarps, 4 * nrhs, 4, 8, mom);
     ++g_launches;
   }
   return cudaGetLastError();
@@ -616,6 +693,8 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
   const int nw = (KER == PFMM_STOKES) ? 4 : (KER == PFMM_MSTOKES ? 2 : 1);  // weight rows per rhs
   f.nodes = (const double*)(ws + L.nodes) + (second ? 2 * p->far.Nq : 0);
   const Geom& g = p->geom;
+  f.alpha1f = (float)(2.0 * M_PI / g.d);
+  f.beta_f = (float)f.beta;
   const bool mixed = sizeof(T) == 4;
   const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
   const T* sy = sx + ns;

@@ -33,6 +33,7 @@
 //            b = IFFT(v(k) / phihat(alpha k)).
 // Two real lines share one complex FFT (real + i imag).
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <cmath>
 #include "pfmm_impl.h"
@@ -53,7 +54,12 @@ struct NufftArgs {
   // in t = rho_c y (NULL otherwise), applied to the GL weights of every point
   const double* rho;
   double rho_c;
+  float glf[64];  // (ybar_n, sigma_n) in FP32 for the mixed kernels (n_gl <= 32)
 };
+
+// FP64 value of a kernel-precision number (FP32: the integer-pipe conversion)
+__device__ __forceinline__ double to_d(float v) { return dm::f2d(v); }
+__device__ __forceinline__ double to_d(double v) { return v; }
 
 // Transform coordinate in FP64: the FP32 path reads it from the signed
 // fixed-point phase U = 2^32 y / Y (singly periodic transforms only, |y| < Y/4).
@@ -119,15 +125,18 @@ __device__ __forceinline__ int es_weights(int i, T f, int w, T beta, T* ker) {
 // Barycentric interpolation weights gamma(y, n) (second form); GA is the
 // array length (a compile-time bound >= n_gl).
 template <typename T, int GA>
-__device__ __forceinline__ void bary(T y, const double* gl, int n_gl, T* g) {
+__device__ __forceinline__ void bary(T y, const NufftArgs& a, int n_gl, T* g) {
   T sum = T(0);
   int hit = -1;
 #pragma unroll
   for (int n = 0; n < GA; ++n) {
     if (n < n_gl) {
-      const T dy = y - (T)gl[2 * n];
+      // the mixed kernels read the FP32 copy of the nodes (no FP64 conversions)
+      const T yb = sizeof(T) == 4 ? (T)a.glf[2 * n] : (T)a.gl[2 * n];
+      const T sg = sizeof(T) == 4 ? (T)a.glf[2 * n + 1] : (T)a.gl[2 * n + 1];
+      const T dy = y - yb;
       if (dy == T(0)) hit = n;
-      g[n] = (T)gl[2 * n + 1] / (dy == T(0) ? T(1) : dy);
+      g[n] = sg / (dy == T(0) ? T(1) : dy);
       sum += g[n];
     }
   }
@@ -157,6 +166,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
                                                                  int use_smem, int vg) {
   extern __shared__ unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);  // [vg][n_gl][nf] when use_smem
+  __shared__ int s_lo, s_hi;
   constexpr int WA = W ? W : 16, GA = NGL ? NGL : 32;
   const int w = W ? W : a.w, ngl = NGL ? NGL : a.n_gl;
   const int ngrid = ngl * a.nf;
@@ -164,10 +174,41 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
   const T beta = (T)a.es_beta;
   const int ncomp = a.nch >= 2 ? 2 : 1;  // Stokes (4 channels) and modified Stokes (2) spread forces
   const int nv = a.nrhs * a.nch;
+  // The grid columns this block touches: the sources are spatially sorted,
+  // so a block's chunk covers a short range of columns in a long cell; only
+  // that range (modulo nf) is cleared and added to the global grid.
+  int cl = 0, span = a.nf;
+  if (use_smem) {
+    if (threadIdx.x == 0) {
+      s_lo = INT_MAX;
+      s_hi = INT_MIN;
+    }
+    __syncthreads();
+    int lo = INT_MAX, hi = INT_MIN;
+    const T half = T(0.5) * w;
+    for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
+      int gi;
+      T gf;
+      grid_pos(sx[j], sU[j], a, &gi, &gf);
+      const int l0 = gi + (int)ceil(gf - half);
+      lo = min(lo, l0);
+      hi = max(hi, l0 + w - 1);
+    }
+    atomicMin(&s_lo, lo);
+    atomicMax(&s_hi, hi);
+    __syncthreads();
+    if (s_hi >= s_lo && s_hi - s_lo + 1 < a.nf) {
+      cl = s_lo;
+      span = s_hi - s_lo + 1;
+    }
+  }
   for (int v0 = 0; v0 < nv; v0 += vg) {
     const int nvg = min(vg, nv - v0);
     if (use_smem)
-      for (int k = threadIdx.x; k < nvg * ngrid; k += kSpreadThreads) sg[k] = T(0);
+      for (int k = threadIdx.x; k < nvg * ngl * span; k += kSpreadThreads) {
+        const int row = k / span, col = (cl + k % span) & (a.nf - 1);
+        sg[(size_t)row * a.nf + col] = T(0);
+      }
     __syncthreads();
     for (int j = j0 + threadIdx.x; j < j1; j += kSpreadThreads) {
       const T x = sx[j], y = sy[j];
@@ -175,7 +216,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
       T gf, ker[WA], gam[GA];
       grid_pos(x, sU[j], a, &gi, &gf);
       const int l0 = es_weights<T, WA>(gi, gf, w, beta, ker);
-      bary<T, GA>(y, a.gl, ngl, gam);
+      bary<T, GA>(y, a, ngl, gam);
       if (a.rho) {
         const T rh = (T)rho_at(a, spread_coord(x, sU[j], a));
 #pragma unroll
@@ -198,7 +239,7 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
                 if (use_smem)
                   atomicAdd(sgv + n * a.nf + l, gq * ker[k]);
                 else
-                  atomicAdd(gr + n * a.nf + l, (double)(gq * ker[k]));
+                  atomicAdd(gr + n * a.nf + l, to_d(gq * ker[k]));
               }
             }
           }
@@ -208,9 +249,11 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
     __syncthreads();
     if (use_smem) {
       double* g = grid + (size_t)v0 * ngrid;
-      for (int k = threadIdx.x; k < nvg * ngrid; k += kSpreadThreads) {
-        const T val = sg[k];
-        if (val != T(0)) atomicAdd(g + k, (double)val);
+      for (int k = threadIdx.x; k < nvg * ngl * span; k += kSpreadThreads) {
+        const int row = k / span, col = (cl + k % span) & (a.nf - 1);
+        const size_t o = (size_t)row * a.nf + col;
+        const T val = sg[o];
+        if (val != T(0)) atomicAdd(g + o, to_d(val));
       }
       __syncthreads();
     }
@@ -393,19 +436,29 @@ __global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, doubl
   }
 }
 
-// Inverse FFT of each packed line spectrum in place (bit-reversed load into smem).
-__global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec) {
+// Inverse FFT of each packed line spectrum in place (bit-reversed load into
+// smem).  out32 (mixed path): the line is written back as FP32 pairs into the
+// first half of its own storage (float2 index i of the row), so that the
+// interpolation reads FP32 values with no FP64 conversions; the row was read
+// into shared memory in full before any write.
+__global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec, int out32) {
   extern __shared__ unsigned char smem_raw[];
   double2* s = reinterpret_cast<double2*>(smem_raw);
   double2* row = spec + (size_t)blockIdx.x * a.nf;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) s[bitrev(i, a.logn)] = row[i];
   __syncthreads();
   fft_smem(s, a.nf, a.tw, +1);
-  for (int i = threadIdx.x; i < a.nf; i += blockDim.x) row[i] = s[i];
+  if (out32) {
+    float2* rf = reinterpret_cast<float2*>(row);
+    for (int i = threadIdx.x; i < a.nf; i += blockDim.x) rf[i] = make_float2((float)s[i].x, (float)s[i].y);
+  } else {
+    for (int i = threadIdx.x; i < a.nf; i += blockDim.x) row[i] = s[i];
+  }
 }
 
 // Interpolation at targets + barycentric combination over lines; adds the
-// south/north field to pot / grad (input frame).  The spectra are FP64; the
+// south/north field to pot / grad (input frame).  The lines are FP64 (FP32
+// on the mixed path, converted once per grid value by k_nufft_inv); the
 // mixed path interpolates in FP32 and sums over lines with compensation.  The
 // ES and barycentric weights are computed once per target and serve every
 // right-hand side; W, NGL as for the spreading kernel.
@@ -422,7 +475,7 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
   T gf, ker[WA], gam[GA];
   grid_pos(x, tU[l], a, &gi, &gf);
   const int l0 = es_weights<T, WA>(gi, gf, w, (T)a.es_beta, ker);
-  bary<T, GA>(y, a.gl, ngl, gam);
+  bary<T, GA>(y, a, ngl, gam);
   if (a.rho) {
     const T rh = (T)rho_at(a, spread_coord(x, tU[l], a));
 #pragma unroll
@@ -432,20 +485,32 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
 #pragma unroll
   for (int k = 0; k < WA; ++k) li[k] = (l0 + k) & (a.nf - 1);
   const double* R = g.rot;
+  // value k of evaluation line `line` of rhs r: FP32 rows on the mixed path
+  // (written by k_nufft_inv with out32, row stride 2 nf float2), FP64 otherwise
+  struct V2 {
+    T x, y;
+  };
+  auto val = [&](int r, int line, int k) -> V2 {
+    if constexpr (sizeof(T) == 4) {
+      const float2 v = reinterpret_cast<const float2*>(spec)[((size_t)r * a.npk + line) * 2 * a.nf + li[k]];
+      return V2{v.x, v.y};
+    } else {
+      const double2 v = spec[((size_t)r * a.npk + line) * a.nf + li[k]];
+      return V2{v.x, v.y};
+    }
+  };
   for (int r = 0; r < a.nrhs; ++r) {
-    const double2* base = spec + (size_t)r * a.npk * a.nf;
     if (KER == PFMM_MSTOKES) {
       dm::KSum<T> ux, uy;
 #pragma unroll 1
       for (int n = 0; n < ngl; ++n) {
-        const double2* ra = base + (size_t)n * a.nf;
         T sx = 0, sy = 0;
 #pragma unroll
         for (int k = 0; k < WA; ++k) {
           if (k < w) {
-            const double2 va = ra[li[k]];
-            sx += ker[k] * (T)va.x;
-            sy += ker[k] * (T)va.y;
+            const V2 va = val(r, n, k);
+            sx += ker[k] * va.x;
+            sy += ker[k] * va.y;
           }
         }
         ux.add(gam[n] * sx);
@@ -460,17 +525,15 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
       dm::KSum<T> ux, uy;
 #pragma unroll 1
       for (int n = 0; n < ngl; ++n) {
-        const double2* ra = base + (size_t)n * a.nf;
-        const double2* rb = base + (size_t)(ngl + n) * a.nf;
         T sax = 0, say = 0, sbx = 0, sby = 0;
 #pragma unroll
         for (int k = 0; k < WA; ++k) {
           if (k < w) {
-            const double2 va = ra[li[k]], vb = rb[li[k]];
-            sax += ker[k] * (T)va.x;
-            say += ker[k] * (T)va.y;
-            sbx += ker[k] * (T)vb.x;
-            sby += ker[k] * (T)vb.y;
+            const V2 va = val(r, n, k), vb = val(r, ngl + n, k);
+            sax += ker[k] * va.x;
+            say += ker[k] * va.y;
+            sbx += ker[k] * vb.x;
+            sby += ker[k] * vb.y;
           }
         }
         ux.add(gam[n] * (sax + y * sbx));
@@ -484,18 +547,16 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
     dm::KSum<T> p, gx, gy;
 #pragma unroll 1
     for (int n = 0; n < ngl; ++n) {
-      const double2* row = base + (size_t)n * a.nf;
-      const double2* rowx = base + (size_t)(ngl + n / 2) * a.nf;
       T sp = 0, sy = 0, sx = 0;
 #pragma unroll
       for (int k = 0; k < WA; ++k) {
         if (k < w) {
-          const double2 v = row[li[k]];
-          sp += ker[k] * (T)v.x;
-          sy += ker[k] * (T)v.y;
+          const V2 v = val(r, n, k);
+          sp += ker[k] * v.x;
+          sy += ker[k] * v.y;
           if (grad) {
-            const double2 vx = rowx[li[k]];
-            sx += ker[k] * (T)((n & 1) ? vx.y : vx.x);
+            const V2 vx = val(r, ngl + n / 2, k);
+            sx += ker[k] * ((n & 1) ? vx.y : vx.x);
           }
         }
       }
@@ -754,6 +815,7 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   a.xi = p->geom.xi;
   a.beta = p->far.beta;
   a.gl = (const double*)(ws + L.nodes + off_gl(p));
+  for (int i = 0; i < 2 * a.n_gl && i < 64; ++i) a.glf[i] = (float)p->gl_h[i];
   a.phihat = (const double*)(ws + L.nodes + off_phihat(p));
   a.tw = (const double*)(ws + L.nodes + off_twiddle(p));
   // workspace partition of the NUFFT scratch
@@ -808,22 +870,22 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   switch (K) {
     case PFMM_LAPLACE:
       k_nufft_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
       interp_k<T, PFMM_LAPLACE>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MODHELM:
       k_nufft_modes<PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
       interp_k<T, PFMM_MODHELM>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MSTOKES:
       k_nufft_modes<PFMM_MSTOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
       interp_k<T, PFMM_MSTOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
     default:
       k_nufft_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
       interp_k<T, PFMM_STOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
   }
@@ -861,6 +923,7 @@ static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_
   a.beta = p->far.beta;
   const char* tab = ws + L.nodes;
   a.gl = (const double*)(tab + off_gl(p));
+  for (int i = 0; i < 2 * a.n_gl && i < 64; ++i) a.glf[i] = (float)p->gl_h[i];
   a.phihat = (const double*)(tab + off_phihat(p));
   a.tw = (const double*)(tab + off_twiddle(p));
   a.rho = (const double*)(tab + off_rho(p));
@@ -927,7 +990,7 @@ static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_
     k_p1_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, g, nodes, nq0, nnu, dl, alpha, Fk, lines);
     k_p1_gather<PFMM_LAPLACE><<<gg, 128, 0, st>>>(a, nodes, nq0, nnu, dl, alpha, lines, spec, wg);
   }
-  k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec);
+  k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
   const T* t64 = self ? s64 : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
   const int* tV = self ? sV : (const int*)(ws + L.trgV);
   const int ni = (int)((nt + 127) / 128);

@@ -46,6 +46,8 @@ struct Far {
   int rows3;         // west/east over the image rows n = -1, 0, 1 (doubly periodic) or n = 0 only (P1)
   int msfam;         // modified Stokes: 0 the beta family (decay chi, kappa), 1 the Laplace family (|alpha|, |lambda|)
   const double* nodes;  // device [Nq][2] (lambda_n, w_n), in workspace
+  // FP32 term decoding of the mixed kernels (set at launch): 2 pi / d, beta
+  float alpha1f = 0.f, beta_f = 0.f;
 };
 
 // NUFFT path: charge channels per rhs (scalar q; Stokes f_x, f_y, y' f_x,
