@@ -3,8 +3,12 @@
 //
 // Each cell keeps its own plan and a private region of the workspace; the
 // inputs and outputs are concatenated structure-of-arrays with per-cell
-// offsets.  The small per-cell phases (prep, far field: < 1 % of the work) are
-// launched per cell.  The near-image P2P, which carries almost all the work
+// offsets.  On the mixed path the per-cell phases (memsets, point and
+// strength preparation, far-field formation, weights and evaluation, the
+// NUFFT stages) run as one launch per phase over all cells (multi.cuh): the
+// cells' launches are recorded once per set of buffers and merged by
+// (phase, kernel), with per-cell argument tables in the workspace.  The
+// FP64 path launches them per cell.  The near-image P2P, which carries almost all the work
 // and the N^2 imbalance between cells, runs as one persistent kernel per
 // near-block shape over a global list of (cell, target block, source range,
 // rhs group) items sorted by decreasing cost and pulled from an atomic
@@ -18,6 +22,7 @@
 
 #include "pfmm_impl.h"
 #include "p2p.h"
+#include "multi.cuh"
 
 using namespace pfmm;
 
@@ -56,9 +61,95 @@ struct pfmm_batch {
   cudaStream_t fan[kFan] = {};
   cudaEvent_t fork = nullptr, join[kFan] = {};
   bool fan_ready = false;
+  // mixed path: multi-cell launches of the per-cell phases, in phase order;
+  // argument tables at off_multi (multi_bytes reserved at creation)
+  struct MGroup {
+    const void* fn;
+    int phase, block, n, nblocks;
+    size_t smem, argsz;
+    size_t o_args, o_off, o_dims;  // offsets within the multi region
+  };
+  std::vector<MGroup> mgroups;
+  std::vector<unsigned char> mblob;  // host copy of the tables (kept for the async upload)
+  size_t off_multi = 0, multi_bytes = 0;
 };
 
 static size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Record the per-cell phases of every cell (mixed path) with the given
+// buffers: nothing is launched.
+static pfmm_status record_cells(pfmm_batch* b, char* ws, const double* src, const double* q, const double* tr,
+                                double* pot, double* grad, Recorder* rec) {
+  for (int c = 0; c < b->ncell; ++c) {
+    pfmm_plan* p = b->plans[c];
+    p->s_stride = b->NS;
+    p->t_stride = b->NT;
+    p->o_stride = b->NT;
+  }
+  g_rec = rec;
+  pfmm_status s = PFMM_OK;
+  for (int c = 0; c < b->ncell && s == PFMM_OK; ++c) {
+    int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
+    s = execute_cell(b->plans[c], ws + b->wsoff[c], ns, src + b->soff[c], q + b->soff[c], nt, tr + b->toff[c],
+                     pot + b->toff[c], grad ? grad + b->toff[c] : nullptr, (cudaStream_t)0, b->self, false, false);
+  }
+  g_rec = nullptr;
+  return s;
+}
+
+// Merge the recorded launches by (phase, kernel), in phase order, and lay out
+// their tables (arguments, first blocks, grids) in `blob`; returns its size.
+static size_t build_groups(const Recorder& rec, std::vector<pfmm_batch::MGroup>* groups,
+                           std::vector<unsigned char>* blob) {
+  groups->clear();
+  std::vector<std::vector<const LaunchRec*>> members;
+  for (int ph = 0; ph < PH_COUNT; ++ph) {
+    const size_t first = groups->size();
+    for (const LaunchRec& r : rec.recs) {
+      if (r.phase != ph) continue;
+      size_t k = first;
+      while (k < groups->size() && (*groups)[k].fn != r.fn) ++k;
+      if (k == groups->size()) {
+        pfmm_batch::MGroup g{};
+        g.fn = r.fn;
+        g.phase = ph;
+        g.argsz = r.args.size();
+        groups->push_back(g);
+        members.emplace_back();
+      }
+      members[k].push_back(&r);
+    }
+  }
+  size_t off = 0;
+  for (size_t k = 0; k < groups->size(); ++k) {
+    pfmm_batch::MGroup& g = (*groups)[k];
+    g.n = (int)members[k].size();
+    g.o_args = off;
+    off = al256(off + g.argsz * g.n);
+    g.o_off = off;
+    off = al256(off + sizeof(int) * g.n);
+    g.o_dims = off;
+    off = al256(off + sizeof(uint3) * g.n);
+  }
+  if (blob) {
+    blob->assign(off, 0);
+    for (size_t k = 0; k < groups->size(); ++k) {
+      pfmm_batch::MGroup& g = (*groups)[k];
+      int nb = 0;
+      for (int i = 0; i < g.n; ++i) {
+        const LaunchRec& r = *members[k][i];
+        std::memcpy(blob->data() + g.o_args + g.argsz * i, r.args.data(), g.argsz);
+        std::memcpy(blob->data() + g.o_off + sizeof(int) * i, &nb, sizeof(int));
+        std::memcpy(blob->data() + g.o_dims + sizeof(uint3) * i, &r.grid, sizeof(uint3));
+        nb += (int)(r.grid.x * r.grid.y * r.grid.z);
+        g.block = std::max(g.block, r.block);
+        g.smem = std::max(g.smem, r.smem);
+      }
+      g.nblocks = nb;
+    }
+  }
+  return off;
+}
 
 extern "C" {
 
@@ -145,6 +236,22 @@ pfmm_status pfmm_batch_create(const pfmm_opts* cells, int ncell, const int64_t* 
     off = al256(off + sizeof(SortCell) * b->hsort.size());
     b->off_sortscr = off;
     off = al256(off + sort_scratch_bytes(b->sort_total, (int)b->hsort.size()));
+  }
+  if (b->precision == PFMM_MIXED) {
+    // size of the multi-cell launch tables: a recording with placeholder
+    // addresses (the tables' sizes do not depend on them)
+    Recorder rec;
+    char* fake = reinterpret_cast<char*>(uintptr_t(1) << 20);
+    double* fd = reinterpret_cast<double*>(fake);
+    pfmm_status s = record_cells(b, fake, fd, fd, fd, fd, fd, &rec);
+    if (s != PFMM_OK) {
+      pfmm_batch_destroy(b);
+      return s;
+    }
+    std::vector<pfmm_batch::MGroup> groups;
+    b->multi_bytes = build_groups(rec, &groups, nullptr);
+    b->off_multi = off;
+    off = al256(off + b->multi_bytes);
   }
   b->off_cells = off;
   off = al256(off + sizeof(P2PArgs) * ncell);
@@ -287,6 +394,21 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
                           cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "upload descriptors: %s", cudaGetErrorString(e));
     for (auto& g : b->groups) g.grid = p2p_batch_grid(b->kernel, g.nimg, g.nr, grad != nullptr);
+    if (mixed) {
+      // the per-cell phases with these buffers, merged into multi-cell launches
+      Recorder rec;
+      pfmm_status s = record_cells(b, ws, src, q, tr, pot, grad, &rec);
+      if (s != PFMM_OK) return s;
+      const size_t need = build_groups(rec, &b->mgroups, &b->mblob);
+      if (need > b->multi_bytes)
+        return set_error(PFMM_ERR_INTERNAL, "multi-cell launch tables need %zu bytes, %zu reserved", need,
+                         b->multi_bytes);
+      if (need) e = cudaMemcpyAsync(ws + b->off_multi, b->mblob.data(), need, cudaMemcpyHostToDevice, st);
+      for (auto& g : b->mgroups)
+        if (e == cudaSuccess && g.smem > 48 * 1024)
+          e = cudaFuncSetAttribute(g.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem);
+      if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "multi-cell tables: %s", cudaGetErrorString(e));
+    }
     std::memcpy(b->last, cur, sizeof cur);
   }
   e = cudaMemsetAsync(ws + b->off_counter, 0, 256, st);
@@ -313,15 +435,30 @@ pfmm_status pfmm_batch_execute(pfmm_batch* b, void* workspace, size_t ws_bytes, 
   }
   if (rec && (e = record(b->ev[0])) != cudaSuccess) return set_error(PFMM_ERR_CUDA, "event record: %s", cudaGetErrorString(e));
   b->nlaunch = 0;
-  // per-cell phases: cell c on fan stream c % kFan, forked from and joined
-  // back into the caller's stream
-  const bool fan = b->ncell > 1 && (b->fan_ready || (cap == cudaStreamCaptureStatusNone && fan_setup(b) == cudaSuccess));
+  if (mixed) {
+    // per-cell phases: one launch per (phase, kernel) over all cells
+    for (const auto& g : b->mgroups) {
+      const void* pa = ws + b->off_multi + g.o_args;
+      const void* po = ws + b->off_multi + g.o_off;
+      const void* pd = ws + b->off_multi + g.o_dims;
+      int n = g.n;
+      void* params[] = {(void*)&pa, (void*)&po, (void*)&pd, (void*)&n};
+      e = cudaLaunchKernel(g.fn, dim3(g.nblocks), dim3(g.block), params, g.smem, st);
+      if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "multi-cell launch (phase %d): %s", g.phase,
+                                             cudaGetErrorString(e));
+      ++b->nlaunch;
+    }
+  }
+  // FP64 path: per-cell phases, cell c on fan stream c % kFan, forked from
+  // and joined back into the caller's stream
+  const bool fan = !mixed && b->ncell > 1 &&
+                   (b->fan_ready || (cap == cudaStreamCaptureStatusNone && fan_setup(b) == cudaSuccess));
   if (fan) {
     e = cudaEventRecord(b->fork, st);
     for (int k = 0; k < pfmm_batch::kFan && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->fan[k], b->fork, 0);
     if (e != cudaSuccess) return set_error(PFMM_ERR_CUDA, "fork: %s", cudaGetErrorString(e));
   }
-  for (int c = 0; c < b->ncell; ++c) {
+  for (int c = 0; c < b->ncell && !mixed; ++c) {
     int64_t ns = b->soff[c + 1] - b->soff[c], nt = b->toff[c + 1] - b->toff[c];
     cudaStream_t sc = fan ? b->fan[c % pfmm_batch::kFan] : st;
     pfmm_status s = execute_cell(b->plans[c], ws + b->wsoff[c], ns, src + b->soff[c], q + b->soff[c], nt,

@@ -21,16 +21,36 @@
 #include "pfmm_impl.h"
 #include "devmath.cuh"
 #include "lattice_weights.cuh"
+#include "multi.cuh"
 
 namespace pfmm {
 
 // ----------------------------------------------------------------------------
 // K0: points
 // ----------------------------------------------------------------------------
-__global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* __restrict__ pts, double* __restrict__ c64,
-                              float* __restrict__ cf, int* __restrict__ U,
-                              int* __restrict__ status, int* __restrict__ V, double invY, double xid) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct PtsArgs {
+  Geom g;
+  int64_t n, istride;
+  const double* pts;
+  double* c64;
+  float* cf;
+  int* U;
+  int* status;
+  int* V;
+  double invY, xid;
+};
+
+__device__ __forceinline__ void k_prep_points_body(uint3 bid, const PtsArgs& A) {
+  const Geom& g = A.g;
+  const int64_t n = A.n, istride = A.istride;
+  const double* __restrict__ pts = A.pts;
+  double* __restrict__ c64 = A.c64;
+  float* __restrict__ cf = A.cf;
+  int* __restrict__ U = A.U;
+  int* __restrict__ status = A.status;
+  int* __restrict__ V = A.V;
+  const double invY = A.invY, xid = A.xid;
+  int64_t i = bid.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double x = pts[i], y = pts[istride + i];
   if (!isfinite(x) || !isfinite(y)) {
@@ -62,6 +82,7 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
   // (|y| < eta/2 = Y/4, so the signed value is exact to 2^-32 Y)
   if (V) V[i] = (int)llrint(yc * invY * 4294967296.0);
 }
+PFMM_CELL_KERNELS(k_prep_points, PtsArgs, )
 
 // Optional projection to zero net charge / force: net sums per rhs and
 // component (input frame) into mom[r*8 + 5 + c]; k_prep_q then subtracts the
@@ -69,9 +90,21 @@ __global__ void k_prep_points(Geom g, int64_t n, int64_t istride, const double* 
 // part != NULL (deterministic mode): each warp writes its sums to
 // part[warp][r * ncomp + c] instead of adding them to mom; k_ordered_sum adds
 // them up in warp order afterwards.
-__global__ void k_net(int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
-                      double* __restrict__ mom, double* __restrict__ part) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+struct NetArgs {
+  int ncomp, nrhs;
+  int64_t ns, qs;
+  const double* q;
+  double* mom;
+  double* part;
+};
+
+__device__ __forceinline__ void k_net_body(uint3 bid, const NetArgs& A) {
+  const int ncomp = A.ncomp, nrhs = A.nrhs;
+  const int64_t ns = A.ns, qs = A.qs;
+  const double* __restrict__ q = A.q;
+  double* __restrict__ mom = A.mom;
+  double* __restrict__ part = A.part;
+  int64_t i = bid.x * (int64_t)blockDim.x + threadIdx.x;
   int lane = threadIdx.x & 31;
   const int64_t warp = i >> 5;
   for (int r = 0; r < nrhs; ++r)
@@ -85,6 +118,7 @@ __global__ void k_net(int ncomp, int nrhs, int64_t ns, int64_t qs, const double*
       }
     }
 }
+PFMM_CELL_KERNELS(k_net, NetArgs, )
 
 // out[(i / g) * ostride + i % g] += sum_{b < nb} part[b * m + i], i < m, in
 // the order b = 0, 1, ... (the deterministic mode's fixed-order reduction of
@@ -110,11 +144,33 @@ __device__ __forceinline__ bool finite64(double v) {
   return (__double2hiint(v) & 0x7ff00000) != 0x7ff00000;
 }
 
-__global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, const double* __restrict__ q,
-                         const double* __restrict__ src64, double* __restrict__ qc, float* __restrict__ qf,
-                         double* __restrict__ mom, int* __restrict__ status, int project, double* __restrict__ part) {
-  const int64_t base = (int64_t)blockIdx.x * blockDim.x * kPrepPts + threadIdx.x;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+struct QArgs {
+  Geom g;
+  int ncomp, nrhs;
+  int64_t ns, qs;
+  const double* q;
+  const double* src64;
+  double* qc;
+  float* qf;
+  double* mom;
+  int* status;
+  int project;
+  double* part;
+};
+
+__device__ __forceinline__ void k_prep_q_body(uint3 bid, const QArgs& A) {
+  const Geom& g = A.g;
+  const int ncomp = A.ncomp, nrhs = A.nrhs, project = A.project;
+  const int64_t ns = A.ns, qs = A.qs;
+  const double* __restrict__ q = A.q;
+  const double* __restrict__ src64 = A.src64;
+  double* __restrict__ qc = A.qc;
+  float* __restrict__ qf = A.qf;
+  double* __restrict__ mom = A.mom;
+  int* __restrict__ status = A.status;
+  double* __restrict__ part = A.part;
+  const int64_t base = (int64_t)bid.x * blockDim.x * kPrepPts + threadIdx.x;
+  const int64_t warp = ((int64_t)bid.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const double inv_ns = project ? 1.0 / (double)ns : 0.0;
   bool bad = false;
@@ -178,6 +234,7 @@ __global__ void k_prep_q(Geom g, int ncomp, int nrhs, int64_t ns, int64_t qs, co
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
+PFMM_CELL_KERNELS(k_prep_q, QArgs, )
 
 // ----------------------------------------------------------------------------
 // term decoding.  Term list: [south m_lo..M | north m_lo..M | west 0..Nq-1 | east 0..Nq-1]
@@ -257,11 +314,30 @@ constexpr int kFormThreads = 128;
 constexpr int kFormSub = 64;
 constexpr int kRB = 4;  // rhs per block
 
+template <typename T>
+struct FormArgs {
+  Far f;
+  Geom g;
+  int ns, chunk;
+  const T* sx;
+  const T* sy;
+  const int* sU;
+  const T* qv;
+  double* coef;
+  double* part;
+};
+
 template <typename T, int KER>
-__global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns, int chunk, const T* __restrict__ sx,
-                                                           const T* __restrict__ sy, const int* __restrict__ sU,
-                                                           const T* __restrict__ qv, double* __restrict__ coef,
-                                                           double* __restrict__ part) {
+__device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A) {
+  const Far& f = A.f;
+  const Geom& g = A.g;
+  const int ns = A.ns, chunk = A.chunk;
+  const T* __restrict__ sx = A.sx;
+  const T* __restrict__ sy = A.sy;
+  const int* __restrict__ sU = A.sU;
+  const T* __restrict__ qv = A.qv;
+  double* __restrict__ coef = A.coef;
+  double* __restrict__ part = A.part;
   constexpr int NC = (KER == PFMM_STOKES || KER == PFMM_MSTOKES) ? 2 : 1;
   constexpr int NCH = (KER == PFMM_STOKES) ? 4 : NC;
   __shared__ T s_x[kFormSub], s_y[kFormSub];
@@ -269,9 +345,9 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
   __shared__ int s_U[kFormSub];
   __shared__ T s_q[kRB][NC][kFormSub];
 
-  const int t = blockIdx.y * kFormThreads + threadIdx.x;
+  const int t = bid.y * kFormThreads + threadIdx.x;
   const bool active = t < f.nterm;
-  const int r0 = blockIdx.z * kRB;
+  const int r0 = bid.z * kRB;
   const int nr = min(kRB, f.nrhs - r0);
   int tpart, tmm;
   T a, b;
@@ -300,7 +376,7 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
 
-  const int j0 = blockIdx.x * chunk;
+  const int j0 = bid.x * chunk;
   const int j1 = min(ns, j0 + chunk);
   for (int jb = j0; jb < j1; jb += kFormSub) {
     const int nb = min(kFormSub, j1 - jb);
@@ -392,7 +468,7 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
   if (!active) return;
   // deterministic mode: this source chunk's sums go to part[chunk][...] (same
   // layout as coef), added in chunk order by k_ordered_sum
-  double* base = part ? part + (size_t)blockIdx.x * f.nrhs * NCH * f.nterm * 2 : coef;
+  double* base = part ? part + (size_t)bid.x * f.nrhs * NCH * f.nterm * 2 : coef;
   for (int r = 0; r < nr; ++r)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) {
@@ -405,6 +481,18 @@ __global__ void __launch_bounds__(kFormThreads) k_far_form(Far f, Geom g, int ns
         atomicAdd(dst + 1, acc[r][c][1]);
       }
     }
+}
+
+template <typename T, int KER>
+__global__ void __launch_bounds__(kFormThreads) k_far_form(const __grid_constant__ FormArgs<T> A) {
+  k_far_form_body<T, KER>(blockIdx, A);
+}
+template <typename T, int KER>
+__global__ void __launch_bounds__(kFormThreads) k_far_form_multi(const FormArgs<T>* __restrict__ cells,
+                                                                 const int* __restrict__ off,
+                                                                 const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_far_form_body<T, KER>(s.bid, cells[s.cell]);
 }
 
 // ----------------------------------------------------------------------------
@@ -421,10 +509,25 @@ __device__ __forceinline__ void store_w(T2* p, dcx v) {
 }
 
 template <typename T2>
-__global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, double* __restrict__ mom,
-                              T2* __restrict__ wts, int* __restrict__ status) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int r = blockIdx.y;
+struct WArgs {
+  Far f;
+  Geom g;
+  const double* coef;
+  double* mom;
+  T2* wts;
+  int* status;
+};
+
+template <typename T2>
+__device__ __forceinline__ void k_far_weights_body(uint3 bid, const WArgs<T2>& A) {
+  const Far& f = A.f;
+  const Geom& g = A.g;
+  const double* __restrict__ coef = A.coef;
+  double* __restrict__ mom = A.mom;
+  T2* __restrict__ wts = A.wts;
+  int* __restrict__ status = A.status;
+  int t = bid.x * blockDim.x + threadIdx.x;
+  int r = bid.y;
   const int K = f.kernel;
   if (t == 0) {
     double mq = mom[r * 8 + 0], mfy = mom[r * 8 + 1], mabs = mom[r * 8 + 2], my = mom[r * 8 + 3];
@@ -487,6 +590,17 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
   }
 }
 
+template <typename T2>
+__global__ void k_far_weights(const __grid_constant__ WArgs<T2> A) {
+  k_far_weights_body<T2>(blockIdx, A);
+}
+template <typename T2>
+__global__ void k_far_weights_multi(const WArgs<T2>* __restrict__ cells, const int* __restrict__ off,
+                                    const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_far_weights_body<T2>(s.bid, cells[s.cell]);
+}
+
 // ----------------------------------------------------------------------------
 // K3: evaluation at targets.  grid (target blocks, rhs groups); terms staged
 // in shared memory in chunks.
@@ -494,20 +608,43 @@ __global__ void k_far_weights(Far f, Geom g, const double* __restrict__ coef, do
 constexpr int kEvalThreads = 128;
 constexpr int kEvalChunk = 64;
 
+template <typename T, typename T2>
+struct EvalArgs {
+  Far f;
+  Geom g;
+  int nt;
+  const T* tx;
+  const T* ty;
+  const int* tU;
+  const T2* wts;
+  const double* mom;
+  int64_t os;
+  double* pot;
+  double* grad;
+  int accum;
+};
+
 template <typename T, typename T2, int KER>
-__global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt, const T* __restrict__ tx,
-                                                           const T* __restrict__ ty, const int* __restrict__ tU,
-                                                           const T2* __restrict__ wts, const double* __restrict__ mom,
-                                                           int64_t os, double* __restrict__ pot, double* __restrict__ grad,
-                                                           int accum) {
+__device__ __forceinline__ void k_far_eval_body(uint3 bid, const EvalArgs<T, T2>& A) {
+  const Far& f = A.f;
+  const Geom& g = A.g;
+  const int nt = A.nt, accum = A.accum;
+  const T* __restrict__ tx = A.tx;
+  const T* __restrict__ ty = A.ty;
+  const int* __restrict__ tU = A.tU;
+  const T2* __restrict__ wts = A.wts;
+  const double* __restrict__ mom = A.mom;
+  const int64_t os = A.os;
+  double* __restrict__ pot = A.pot;
+  double* __restrict__ grad = A.grad;
   constexpr bool VEC = KER == PFMM_STOKES || KER == PFMM_MSTOKES;
   constexpr int NW = (KER == PFMM_STOKES) ? 4 : (KER == PFMM_MSTOKES ? 2 : 1);
   __shared__ T s_a[kEvalChunk], s_b[kEvalChunk];
   __shared__ int s_m[kEvalChunk], s_part[kEvalChunk];
   __shared__ T2 s_w[kRB][NW][kEvalChunk];
-  const int l = blockIdx.x * kEvalThreads + threadIdx.x;
+  const int l = bid.x * kEvalThreads + threadIdx.x;
   const bool in = l < nt;
-  const int r0 = blockIdx.y * kRB;
+  const int r0 = bid.y * kRB;
   const int nr = min(kRB, f.nrhs - r0);
   const T x = in ? tx[l] : T(0), y = in ? ty[l] : T(0);
   // west/east frame coordinates; its gradient is rotated back per term
@@ -635,6 +772,32 @@ __global__ void __launch_bounds__(kEvalThreads) k_far_eval(Far f, Geom g, int nt
   }
 }
 
+template <typename T, typename T2, int KER>
+__global__ void __launch_bounds__(kEvalThreads) k_far_eval(const __grid_constant__ EvalArgs<T, T2> A) {
+  k_far_eval_body<T, T2, KER>(blockIdx, A);
+}
+template <typename T, typename T2, int KER>
+__global__ void __launch_bounds__(kEvalThreads) k_far_eval_multi(const EvalArgs<T, T2>* __restrict__ cells,
+                                                                 const int* __restrict__ off,
+                                                                 const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_far_eval_body<T, T2, KER>(s.bid, cells[s.cell]);
+}
+
+// memsets of 8-byte words (multi-cell zeroing)
+__device__ __forceinline__ void k_zero_body(uint3 bid, const ZeroArgs& A) {
+  const long long i = (long long)bid.x * 256 + threadIdx.x;
+  if (i < A.n) A.p[i] = 0ull;
+}
+PFMM_CELL_KERNELS(k_zero, ZeroArgs, __launch_bounds__(256))
+
+cudaError_t zero_or_record(void* p, size_t bytes, cudaStream_t st) {
+  if (!g_rec) return bytes ? cudaMemsetAsync(p, 0, bytes, st) : cudaSuccess;
+  if ((bytes & 7) || (reinterpret_cast<uintptr_t>(p) & 7)) return cudaErrorInvalidValue;
+  const ZeroArgs a{(unsigned long long*)p, (long long)(bytes / 8)};
+  return launch_or_record(k_zero, k_zero_multi, PH_ZERO, dim3((unsigned)((a.n + 255) / 256)), 256, 0, st, a);
+}
+
 // ----------------------------------------------------------------------------
 // launchers
 // ----------------------------------------------------------------------------
@@ -644,28 +807,36 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
                         const double* trg, bool self, cudaStream_t st) {
   const Layout& L = p->lay;
   int* status = (int*)(ws + L.status);
-  bool mixed = p->opts.precision == PFMM_MIXED;
   const bool wantV = p->p1_nu && p->path == PFMM_PATH_NUFFT;
   const double invY = p->p1_nu ? 1.0 / p->p1_Y : 0.0;
   const double xid = p->geom.xi / p->geom.d;
-  k_prep_points<<<cdiv_i(ns, 256), 256, 0, st>>>(p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
-                                                 (int*)(ws + L.srcU), status,
-                                                 wantV ? (int*)(ws + L.srcV) : nullptr, invY, xid);
-  if (!self && nt > 0)
-    k_prep_points<<<cdiv_i(nt, 256), 256, 0, st>>>(p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
-                                                   (int*)(ws + L.trgU), status,
-                                                   wantV ? (int*)(ws + L.trgV) : nullptr, invY, xid);
+  cudaError_t e;
+  {
+    const PtsArgs a{p->geom, ns, p->s_stride, src, (double*)(ws + L.src64), (float*)(ws + L.srcf),
+                    (int*)(ws + L.srcU), status, wantV ? (int*)(ws + L.srcV) : nullptr, invY, xid};
+    e = launch_or_record(k_prep_points, k_prep_points_multi, PH_PTS, dim3(cdiv_i(ns, 256)), 256, 0, st, a);
+    if (e != cudaSuccess) return e;
+  }
+  if (!self && nt > 0) {
+    const PtsArgs a{p->geom, nt, p->t_stride, trg, (double*)(ws + L.trg64), (float*)(ws + L.trgf),
+                    (int*)(ws + L.trgU), status, wantV ? (int*)(ws + L.trgV) : nullptr, invY, xid};
+    e = launch_or_record(k_prep_points, k_prep_points_multi, PH_PTS, dim3(cdiv_i(nt, 256)), 256, 0, st, a);
+    if (e != cudaSuccess) return e;
+  }
   g_launches = (!self && nt > 0) ? 3 : 2;
   const int project = (p->opts.flags & PFMM_PROJECT_NEUTRAL) &&
                       (p->opts.kernel == PFMM_LAPLACE || p->opts.kernel == PFMM_STOKES);
   // deterministic mode: per-warp partial sums, added in warp order
   double* part = (p->opts.flags & PFMM_DETERMINISTIC) ? (double*)(ws + L.det) : nullptr;
+  if (part && g_rec) return cudaErrorNotSupported;
   const int nwarp = cdiv_i(ns, 32), nrhs = p->opts.nrhs;
   // k_prep_q: kPrepPts points per thread, every warp of its grid writes a partial
   const int qblocks = cdiv_i(ns, 256 * kPrepPts), qwarps = qblocks * 8;
   double* mom = (double*)(ws + L.moments);
   if (project) {
-    k_net<<<cdiv_i(ns, 256), 256, 0, st>>>(p->ncomp, nrhs, ns, p->s_stride, q, mom, part);
+    const NetArgs a{p->ncomp, nrhs, ns, p->s_stride, q, mom, part};
+    e = launch_or_record(k_net, k_net_multi, PH_NET, dim3(cdiv_i(ns, 256)), 256, 0, st, a);
+    if (e != cudaSuccess) return e;
     ++g_launches;
     if (part) {
       const int m = nrhs * p->ncomp;
@@ -673,8 +844,12 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
       ++g_launches;
     }
   }
-  k_prep_q<<<qblocks, 256, 0, st>>>(p->geom, p->ncomp, nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
-                                     (double*)(ws + L.qc), (float*)(ws + L.qf), mom, status, project, part);
+  {
+    const QArgs a{p->geom, p->ncomp, nrhs, ns, p->s_stride, q, (const double*)(ws + L.src64),
+                  (double*)(ws + L.qc), (float*)(ws + L.qf), mom, status, project, part};
+    e = launch_or_record(k_prep_q, k_prep_q_multi, PH_Q, dim3(qblocks), 256, 0, st, a);
+    if (e != cudaSuccess) return e;
+  }
   if (part) {
     k_ordered_sum<<<cdiv_i(4 * nrhs, 128), 128, 0, st>>>(part, qwarps, 4 * nrhs, 4, 8, mom);
     ++g_launches;
@@ -702,19 +877,27 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
   const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
   double* coef = (double*)(ws + L.coef) + (second ? (size_t)f.nrhs * p->far.nch * p->far.nterm * 2 : 0);
   double* mom = (double*)(ws + L.moments);
+  const int ph = second ? PH_FORM2 : PH_FORM;
   int nrg = cdiv_i(f.nrhs, kRB);
   g_launches = (f.nterm > 0) ? 3 : 2;
+  cudaError_t e;
   if (f.nterm > 0) {
     const bool det = (p->opts.flags & PFMM_DETERMINISTIC) != 0;
+    if (det && g_rec) return cudaErrorNotSupported;
     int ny = cdiv_i(f.nterm, kFormThreads);
-    int want = 4 * 152 * 4;  // enough blocks to fill every SM several times
+    // single cell: enough blocks to fill every SM several times; one of many
+    // cells of a batch: source chunks of at least 2048 (the cells together
+    // fill the GPU)
+    int want = g_rec ? std::max(1, cdiv_i(ns, 2048) * ny * nrg) : 4 * 152 * 4;
     int nchunk = std::max(1, std::min(cdiv_i(ns, kFormSub), want / std::max(1, ny * nrg)));
     if (det) nchunk = std::min(nchunk, kDetChunks);
     int chunk = cdiv_i(cdiv_i(ns, nchunk), kFormSub) * kFormSub;
     nchunk = cdiv_i(ns, chunk);
     dim3 grid(nchunk, ny, nrg);
     double* part = det ? (double*)(ws + L.det) : nullptr;
-    k_far_form<T, KER><<<grid, kFormThreads, 0, st>>>(f, g, (int)ns, chunk, sx, sy, sU, qv, coef, part);
+    const FormArgs<T> a{f, g, (int)ns, chunk, sx, sy, sU, qv, coef, part};
+    e = launch_or_record(k_far_form<T, KER>, k_far_form_multi<T, KER>, ph, grid, kFormThreads, 0, st, a);
+    if (e != cudaSuccess) return e;
     if (det) {
       // every (rhs, channel, term) of every chunk is written (inactive terms as 0)
       const int m = f.nrhs * f.nch * f.nterm * 2;
@@ -723,14 +906,21 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
     }
   }
   T2* w = (T2*)(ws + L.wts) + (second ? (size_t)f.nrhs * nw * p->far.nterm : 0);
-  dim3 gw(cdiv_i(std::max(1, f.nterm), 128), f.nrhs);
-  k_far_weights<T2><<<gw, 128, 0, st>>>(f, g, coef, mom, w, (int*)(ws + L.status));
+  {
+    const dim3 gw(cdiv_i(std::max(1, f.nterm), 128), f.nrhs);
+    const WArgs<T2> a{f, g, coef, mom, w, (int*)(ws + L.status)};
+    e = launch_or_record(k_far_weights<T2>, k_far_weights_multi<T2>, ph + 1, gw, 128, 0, st, a);
+    if (e != cudaSuccess) return e;
+  }
   const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
   const T* ty = tx + nt;
   const int* tU = self ? sU : (const int*)(ws + L.trgU);
-  dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
-  k_far_eval<T, T2, KER><<<ge, kEvalThreads, 0, st>>>(f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad,
-                                                       second ? 1 : 0);
+  {
+    const dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
+    const EvalArgs<T, T2> a{f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad, second ? 1 : 0};
+    e = launch_or_record(k_far_eval<T, T2, KER>, k_far_eval_multi<T, T2, KER>, ph + 2, ge, kEvalThreads, 0, st, a);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
@@ -809,8 +999,8 @@ cudaError_t launch_pressure(int nrhs, int64_t nt, const double* g, double* pres,
 cudaError_t launch_zero_out(const pfmm_plan* p, int64_t nt, double* pot, double* grad, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   size_t nr = p->opts.nrhs;
-  if (pot) e = cudaMemsetAsync(pot, 0, nr * p->nout * nt * sizeof(double), st);
-  if (e == cudaSuccess && grad) e = cudaMemsetAsync(grad, 0, nr * 2 * nt * sizeof(double), st);
+  if (pot) e = zero_or_record(pot, nr * p->nout * nt * sizeof(double), st);
+  if (e == cudaSuccess && grad) e = zero_or_record(grad, nr * 2 * nt * sizeof(double), st);
   return e;
 }
 

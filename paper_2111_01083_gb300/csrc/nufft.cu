@@ -39,6 +39,7 @@
 #include "pfmm_impl.h"
 #include "devmath.cuh"
 #include "lattice_weights.cuh"
+#include "multi.cuh"
 
 namespace pfmm {
 
@@ -159,18 +160,34 @@ __device__ __forceinline__ void bary(T y, const NufftArgs& a, int n_gl, T* g) {
 // ---------------------------------------------------------------------------
 constexpr int kSpreadThreads = 256;
 
+template <typename T>
+struct SpreadArgs {
+  NufftArgs a;
+  int chunk;
+  const T* sx;
+  const T* sy;
+  const int* sU;
+  const T* qv;
+  double* grid;
+  int use_smem, vg;
+};
+
 template <typename T, int W, int NGL>
-__global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, int chunk, const T* __restrict__ sx,
-                                                                 const T* __restrict__ sy, const int* __restrict__ sU,
-                                                                 const T* __restrict__ qv, double* __restrict__ grid,
-                                                                 int use_smem, int vg) {
+__device__ __forceinline__ void k_nufft_spread_body(uint3 bid, const SpreadArgs<T>& A) {
+  const NufftArgs& a = A.a;
+  const int chunk = A.chunk, use_smem = A.use_smem, vg = A.vg;
+  const T* __restrict__ sx = A.sx;
+  const T* __restrict__ sy = A.sy;
+  const int* __restrict__ sU = A.sU;
+  const T* __restrict__ qv = A.qv;
+  double* __restrict__ grid = A.grid;
   extern __shared__ unsigned char smem_raw[];
   T* sg = reinterpret_cast<T*>(smem_raw);  // [vg][n_gl][nf] when use_smem
   __shared__ int s_lo, s_hi;
   constexpr int WA = W ? W : 16, GA = NGL ? NGL : 32;
   const int w = W ? W : a.w, ngl = NGL ? NGL : a.n_gl;
   const int ngrid = ngl * a.nf;
-  const int j0 = blockIdx.x * chunk, j1 = min(a.ns, j0 + chunk);
+  const int j0 = bid.x * chunk, j1 = min(a.ns, j0 + chunk);
   const T beta = (T)a.es_beta;
   const int ncomp = a.nch >= 2 ? 2 : 1;  // Stokes (4 channels) and modified Stokes (2) spread forces
   const int nv = a.nrhs * a.nch;
@@ -260,6 +277,18 @@ __global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(NufftArgs a, in
   }
 }
 
+template <typename T, int W, int NGL>
+__global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread(const __grid_constant__ SpreadArgs<T> A) {
+  k_nufft_spread_body<T, W, NGL>(blockIdx, A);
+}
+template <typename T, int W, int NGL>
+__global__ void __launch_bounds__(kSpreadThreads) k_nufft_spread_multi(const SpreadArgs<T>* __restrict__ cells,
+                                                                       const int* __restrict__ off,
+                                                                       const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_nufft_spread_body<T, W, NGL>(s.bid, cells[s.cell]);
+}
+
 // ---------------------------------------------------------------------------
 // K5: radix-2 complex FFT in shared memory (iterative, decimation in time,
 // bit-reversed load), FP64 with twiddles from the plan's FP64 table.  One
@@ -287,11 +316,20 @@ __device__ __forceinline__ int bitrev(int i, int logn) { return __brev(i) >> (32
 // Forward transforms of the spread grids, two real lines per FFT, then
 // deconvolution: F(k) for k = 0..M of every line (charge vector, GL line)
 // written to Fk [nrhs][nch][n_gl][M+1] (double2).
-__global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double2* __restrict__ Fk) {
+struct FwdArgs {
+  NufftArgs a;
+  const double* grid;
+  double2* Fk;
+};
+
+__device__ __forceinline__ void k_nufft_fwd_body(uint3 bid, const FwdArgs& A) {
+  const NufftArgs& a = A.a;
+  const double* __restrict__ grid = A.grid;
+  double2* __restrict__ Fk = A.Fk;
   extern __shared__ unsigned char smem_raw[];
   double2* s = reinterpret_cast<double2*>(smem_raw);
   const int nline = a.nrhs * a.nch * a.n_gl;
-  const int n0 = 2 * blockIdx.x, n1 = 2 * blockIdx.x + 1;
+  const int n0 = 2 * bid.x, n1 = 2 * bid.x + 1;
   const double* g0 = grid + (size_t)n0 * a.nf;
   const double* g1 = (n1 < nline) ? grid + (size_t)n1 * a.nf : nullptr;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) {
@@ -311,6 +349,7 @@ __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double
     if (n1 < nline) Fk[(size_t)n1 * (a.M + 1) + k] = make_double2(yr * dec, yi * dec);
   }
 }
+PFMM_CELL_KERNELS(k_nufft_fwd, FwdArgs, )
 
 // Mode combination, lattice weights and evaluation-line spectra (FP64).
 // One thread per (rhs, mode m = mlo..M).  Writes the type-2 input spectra,
@@ -320,10 +359,21 @@ __global__ void k_nufft_fwd(NufftArgs a, const double* __restrict__ grid, double
 // A real output line Re sum_m e^{i m theta} a_m packed with a second one
 // (b_m) into a complex line has H_m = (a_m + i b_m)/2, H_-m = (conj a_m + i conj b_m)/2
 // for m >= 1, and H_0 = a_0 + i b_0 (a_0, b_0 real).
+struct ModesArgs {
+  NufftArgs a;
+  const double2* Fk;
+  double2* spec;
+  int want_grad;
+};
+
 template <int KER>
-__global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, double2* __restrict__ spec, int want_grad) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x + a.mlo;
-  const int r = blockIdx.y;
+__device__ __forceinline__ void k_nufft_modes_body(uint3 bid, const ModesArgs& A) {
+  const NufftArgs& a = A.a;
+  const double2* __restrict__ Fk = A.Fk;
+  double2* __restrict__ spec = A.spec;
+  const int want_grad = A.want_grad;
+  const int m = bid.x * blockDim.x + threadIdx.x + a.mlo;
+  const int r = bid.y;
   if (m > a.M) return;
   const double al = 2.0 * M_PI * m / a.d;
   const double chi = (KER == PFMM_MODHELM) ? sqrt(al * al + a.beta * a.beta) : fabs(al);
@@ -436,15 +486,35 @@ __global__ void k_nufft_modes(NufftArgs a, const double2* __restrict__ Fk, doubl
   }
 }
 
+template <int KER>
+__global__ void k_nufft_modes(const __grid_constant__ ModesArgs A) {
+  k_nufft_modes_body<KER>(blockIdx, A);
+}
+template <int KER>
+__global__ void k_nufft_modes_multi(const ModesArgs* __restrict__ cells, const int* __restrict__ off,
+                                    const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_nufft_modes_body<KER>(s.bid, cells[s.cell]);
+}
+
 // Inverse FFT of each packed line spectrum in place (bit-reversed load into
 // smem).  out32 (mixed path): the line is written back as FP32 pairs into the
 // first half of its own storage (float2 index i of the row), so that the
 // interpolation reads FP32 values with no FP64 conversions; the row was read
 // into shared memory in full before any write.
-__global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec, int out32) {
+struct InvArgs {
+  NufftArgs a;
+  double2* spec;
+  int out32;
+};
+
+__device__ __forceinline__ void k_nufft_inv_body(uint3 bid, const InvArgs& A) {
+  const NufftArgs& a = A.a;
+  double2* __restrict__ spec = A.spec;
+  const int out32 = A.out32;
   extern __shared__ unsigned char smem_raw[];
   double2* s = reinterpret_cast<double2*>(smem_raw);
-  double2* row = spec + (size_t)blockIdx.x * a.nf;
+  double2* row = spec + (size_t)bid.x * a.nf;
   for (int i = threadIdx.x; i < a.nf; i += blockDim.x) s[bitrev(i, a.logn)] = row[i];
   __syncthreads();
   fft_smem(s, a.nf, a.tw, +1);
@@ -455,6 +525,7 @@ __global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec, int out32) 
     for (int i = threadIdx.x; i < a.nf; i += blockDim.x) row[i] = s[i];
   }
 }
+PFMM_CELL_KERNELS(k_nufft_inv, InvArgs, )
 
 // Interpolation at targets + barycentric combination over lines; adds the
 // south/north field to pot / grad (input frame).  The lines are FP64 (FP32
@@ -462,13 +533,31 @@ __global__ void k_nufft_inv(NufftArgs a, double2* __restrict__ spec, int out32) 
 // mixed path interpolates in FP32 and sums over lines with compensation.  The
 // ES and barycentric weights are computed once per target and serve every
 // right-hand side; W, NGL as for the spreading kernel.
+template <typename T>
+struct InterpArgs {
+  NufftArgs a;
+  Geom g;
+  const T* tx;
+  const T* ty;
+  const int* tU;
+  const double2* spec;
+  double* pot;
+  double* grad;
+};
+
 template <typename T, int KER, int W, int NGL>
-__global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, const T* __restrict__ ty,
-                               const int* __restrict__ tU, const double2* __restrict__ spec, double* __restrict__ pot,
-                               double* __restrict__ grad) {
+__device__ __forceinline__ void k_nufft_interp_body(uint3 bid, const InterpArgs<T>& A) {
+  const NufftArgs& a = A.a;
+  const Geom& g = A.g;
+  const T* __restrict__ tx = A.tx;
+  const T* __restrict__ ty = A.ty;
+  const int* __restrict__ tU = A.tU;
+  const double2* __restrict__ spec = A.spec;
+  double* __restrict__ pot = A.pot;
+  double* __restrict__ grad = A.grad;
   constexpr int WA = W ? W : 16, GA = NGL ? NGL : 32;
   const int w = W ? W : a.w, ngl = NGL ? NGL : a.n_gl;
-  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = bid.x * blockDim.x + threadIdx.x;
   if (l >= a.nt) return;
   const T x = tx[l], y = ty[l];
   int gi;
@@ -571,6 +660,17 @@ __global__ void k_nufft_interp(NufftArgs a, Geom g, const T* __restrict__ tx, co
       grad[((size_t)r * 2 + 1) * a.os + l] += R[1] * gxd + R[3] * gyd;
     }
   }
+}
+
+template <typename T, int KER, int W, int NGL>
+__global__ void k_nufft_interp(const __grid_constant__ InterpArgs<T> A) {
+  k_nufft_interp_body<T, KER, W, NGL>(blockIdx, A);
+}
+template <typename T, int KER, int W, int NGL>
+__global__ void k_nufft_interp_multi(const InterpArgs<T>* __restrict__ cells, const int* __restrict__ off,
+                                     const uint3* __restrict__ dims, int n) {
+  const SubBlock s = sub_block(off, dims, n);
+  k_nufft_interp_body<T, KER, W, NGL>(s.bid, cells[s.cell]);
 }
 
 // ---------------------------------------------------------------------------
@@ -768,23 +868,40 @@ static int nufft_spec(int w, int n_gl) {
 template <typename T, int W, int NGL>
 static cudaError_t spread_t(const NufftArgs& a, int nchunk, int chunk, const T* sx, const T* sy, const int* sU,
                             const T* qv, double* grid, int use_smem, int vg, size_t smem, int slot, cudaStream_t st) {
-  if (smem > 48 * 1024) {
+  if (!g_rec && smem > 48 * 1024) {
     cudaError_t e = raise_smem((const void*)k_nufft_spread<T, W, NGL>, slot, smem);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_spread<T, W, NGL><<<nchunk, kSpreadThreads, smem, st>>>(a, chunk, sx, sy, sU, qv, grid, use_smem, vg);
-  return cudaGetLastError();
+  const SpreadArgs<T> A{a, chunk, sx, sy, sU, qv, grid, use_smem, vg};
+  return launch_or_record(k_nufft_spread<T, W, NGL>, k_nufft_spread_multi<T, W, NGL>, PH_SPREAD, dim3(nchunk),
+                          kSpreadThreads, smem, st, A);
 }
 
 template <typename T, int KER>
-static void interp_k(int spec, int ni, const NufftArgs& a, const Geom& g, const T* tx, const T* ty, const int* tU,
-                     const double2* sp, double* pot, double* grad, cudaStream_t st) {
+static cudaError_t interp_k(int spec, int ni, const NufftArgs& a, const Geom& g, const T* tx, const T* ty,
+                            const int* tU, const double2* sp, double* pot, double* grad, cudaStream_t st) {
+  const InterpArgs<T> A{a, g, tx, ty, tU, sp, pot, grad};
+  const dim3 gi(ni);
   switch (spec) {
-    case 1: k_nufft_interp<T, KER, 8, 8><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
-    case 2: k_nufft_interp<T, KER, 12, 16><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
-    case 3: k_nufft_interp<T, KER, 14, 16><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
-    default: k_nufft_interp<T, KER, 0, 0><<<ni, 128, 0, st>>>(a, g, tx, ty, tU, sp, pot, grad); break;
+    case 1:
+      return launch_or_record(k_nufft_interp<T, KER, 8, 8>, k_nufft_interp_multi<T, KER, 8, 8>, PH_INTERP, gi, 128, 0,
+                              st, A);
+    case 2:
+      return launch_or_record(k_nufft_interp<T, KER, 12, 16>, k_nufft_interp_multi<T, KER, 12, 16>, PH_INTERP, gi, 128,
+                              0, st, A);
+    case 3:
+      return launch_or_record(k_nufft_interp<T, KER, 14, 16>, k_nufft_interp_multi<T, KER, 14, 16>, PH_INTERP, gi, 128,
+                              0, st, A);
+    default:
+      return launch_or_record(k_nufft_interp<T, KER, 0, 0>, k_nufft_interp_multi<T, KER, 0, 0>, PH_INTERP, gi, 128, 0,
+                              st, A);
   }
+}
+
+template <int KER>
+static cudaError_t modes_k(const NufftArgs& a, dim3 gm, const double2* Fk, double2* spec, int wg, cudaStream_t st) {
+  return launch_or_record(k_nufft_modes<KER>, k_nufft_modes_multi<KER>, PH_MODES, gm, 128, 0, st,
+                          ModesArgs{a, Fk, spec, wg});
 }
 
 // ---------------------------------------------------------------------------
@@ -827,9 +944,9 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   off += (size_t)nline * (a.M + 1) * sizeof(double2);
   off = (off + 255) & ~size_t(255);
   double2* spec = (double2*)(base + off);                         // [nrhs][npk][nf]
-  cudaError_t e = cudaMemsetAsync(grid, 0, (size_t)nline * a.nf * sizeof(double), st);
+  cudaError_t e = zero_or_record(grid, (size_t)nline * a.nf * sizeof(double), st);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(spec, 0, (size_t)a.nrhs * a.npk * a.nf * sizeof(double2), st);
+  e = zero_or_record(spec, (size_t)a.nrhs * a.npk * a.nf * sizeof(double2), st);
   if (e != cudaSuccess) return e;
   const T* sx = mixed ? (const T*)(ws + L.srcf) : (const T*)(ws + L.src64);
   const T* qv = mixed ? (const T*)(ws + L.qf) : (const T*)(ws + L.qc);
@@ -855,40 +972,50 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   if (e != cudaSuccess) return e;
   const int fth = std::min(512, std::max(32, a.nf / 2));
   const size_t sm_fft = (size_t)a.nf * sizeof(double2);
-  if (sm_fft > 48 * 1024) {
+  if (!g_rec && sm_fft > 48 * 1024) {
     e = raise_smem((const void*)k_nufft_fwd, 8, sm_fft);
     if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 9, sm_fft);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
+  e = launch_or_record(k_nufft_fwd, k_nufft_fwd_multi, PH_FWD, dim3((nline + 1) / 2), fth, sm_fft, st,
+                       FwdArgs{a, grid, Fk});
+  if (e != cudaSuccess) return e;
+  const InvArgs inv{a, spec, mixed ? 1 : 0};
+  const dim3 ginv(a.nrhs * a.npk);
   const int nmode = a.M - a.mlo + 1;
   dim3 gm((nmode + 127) / 128, a.nrhs);
   const T* tx = self ? sx : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
   const int* tU = self ? sU : (const int*)(ws + L.trgU);
   const int ni = (int)((nt + 127) / 128);
   const int wg = grad != nullptr;
+  auto inv_k = [&]() {
+    return launch_or_record(k_nufft_inv, k_nufft_inv_multi, PH_INV, ginv, fth, sm_fft, st, inv);
+  };
   switch (K) {
     case PFMM_LAPLACE:
-      k_nufft_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
-      interp_k<T, PFMM_LAPLACE>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
+      e = modes_k<PFMM_LAPLACE>(a, gm, Fk, spec, wg, st);
+      if (e == cudaSuccess) e = inv_k();
+      if (e == cudaSuccess) e = interp_k<T, PFMM_LAPLACE>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MODHELM:
-      k_nufft_modes<PFMM_MODHELM><<<gm, 128, 0, st>>>(a, Fk, spec, wg);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
-      interp_k<T, PFMM_MODHELM>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
+      e = modes_k<PFMM_MODHELM>(a, gm, Fk, spec, wg, st);
+      if (e == cudaSuccess) e = inv_k();
+      if (e == cudaSuccess) e = interp_k<T, PFMM_MODHELM>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, grad, st);
       break;
     case PFMM_MSTOKES:
-      k_nufft_modes<PFMM_MSTOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
-      interp_k<T, PFMM_MSTOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
+      e = modes_k<PFMM_MSTOKES>(a, gm, Fk, spec, 0, st);
+      if (e == cudaSuccess) e = inv_k();
+      if (e == cudaSuccess)
+        e = interp_k<T, PFMM_MSTOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
     default:
-      k_nufft_modes<PFMM_STOKES><<<gm, 128, 0, st>>>(a, Fk, spec, 0);
-      k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
-      interp_k<T, PFMM_STOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
+      e = modes_k<PFMM_STOKES>(a, gm, Fk, spec, 0, st);
+      if (e == cudaSuccess) e = inv_k();
+      if (e == cudaSuccess)
+        e = interp_k<T, PFMM_STOKES>(wspec, ni, a, p->geom, tx, tx + nt, tU, spec, pot, nullptr, st);
       break;
   }
+  if (e != cudaSuccess) return e;
   g_launches += 5;
   return cudaGetLastError();
 }
@@ -975,7 +1102,9 @@ static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_
     if (e == cudaSuccess) e = raise_smem((const void*)k_nufft_inv, 9, sm_fft);
     if (e != cudaSuccess) return e;
   }
-  k_nufft_fwd<<<(nline + 1) / 2, fth, sm_fft, st>>>(a, grid, Fk);
+  e = launch_or_record(k_nufft_fwd, k_nufft_fwd_multi, PH_FWD, dim3((nline + 1) / 2), fth, sm_fft, st,
+                       FwdArgs{a, grid, Fk});
+  if (e != cudaSuccess) return e;
   const int wg = grad != nullptr && K != PFMM_STOKES;
   const dim3 gm((nnu + 127) / 128, a.nrhs);
   const dim3 gg((a.M + 127) / 128, (K == PFMM_STOKES || wg) ? a.npk : a.n_gl, a.nrhs);
@@ -990,13 +1119,16 @@ static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_
     k_p1_modes<PFMM_LAPLACE><<<gm, 128, 0, st>>>(a, g, nodes, nq0, nnu, dl, alpha, Fk, lines);
     k_p1_gather<PFMM_LAPLACE><<<gg, 128, 0, st>>>(a, nodes, nq0, nnu, dl, alpha, lines, spec, wg);
   }
-  k_nufft_inv<<<a.nrhs * a.npk, fth, sm_fft, st>>>(a, spec, mixed ? 1 : 0);
+  e = launch_or_record(k_nufft_inv, k_nufft_inv_multi, PH_INV, dim3(a.nrhs * a.npk), fth, sm_fft, st,
+                       InvArgs{a, spec, mixed ? 1 : 0});
+  if (e != cudaSuccess) return e;
   const T* t64 = self ? s64 : (mixed ? (const T*)(ws + L.trgf) : (const T*)(ws + L.trg64));
   const int* tV = self ? sV : (const int*)(ws + L.trgV);
   const int ni = (int)((nt + 127) / 128);
   if (K == PFMM_STOKES) {
     // velocity components are not coordinates: the plain frame
-    interp_k<T, PFMM_STOKES>(wspec, ni, a, g, t64 + nt, t64, tV, spec, pot, nullptr, st);
+    e = interp_k<T, PFMM_STOKES>(wspec, ni, a, g, t64 + nt, t64, tV, spec, pot, nullptr, st);
+    if (e != cudaSuccess) return e;
   } else {
     // the interpolation's "x" derivative is along its transform coordinate
     // (y here) and its "y" derivative along the GL lines (x): swap the
@@ -1006,7 +1138,8 @@ static cudaError_t run_p1_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_
     gs.rot[1] = g.rot[3];
     gs.rot[2] = g.rot[0];
     gs.rot[3] = g.rot[1];
-    interp_k<T, PFMM_LAPLACE>(wspec, ni, a, gs, t64 + nt, t64, tV, spec, pot, wg ? grad : nullptr, st);
+    e = interp_k<T, PFMM_LAPLACE>(wspec, ni, a, gs, t64 + nt, t64, tV, spec, pot, wg ? grad : nullptr, st);
+    if (e != cudaSuccess) return e;
   }
   g_launches += 6;
   return cudaGetLastError();

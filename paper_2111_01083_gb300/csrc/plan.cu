@@ -11,6 +11,7 @@
 #include <vector>
 #include <algorithm>
 
+#include "multi.cuh"
 #include "pfmm_impl.h"
 #include "sort.h"
 
@@ -18,6 +19,7 @@ using namespace pfmm;
 
 namespace pfmm {
 thread_local int g_launches = 0;
+thread_local Recorder* g_rec = nullptr;
 }
 
 namespace {
@@ -234,9 +236,9 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
                          const double* trg, double* pot, double* grad, cudaStream_t st, bool self, bool upload,
                          bool near) {
   cudaError_t e;
-  e = cudaMemsetAsync(ws + p->lay.status, 0, p->lay.nodes - p->lay.status, st);
+  e = zero_or_record(ws + p->lay.status, p->lay.nodes - p->lay.status, st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
-  e = cudaMemsetAsync(ws + p->lay.coef, 0, p->lay.wts - p->lay.coef, st);
+  e = zero_or_record(ws + p->lay.coef, p->lay.wts - p->lay.coef, st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   if (upload) {
     // Under stream capture the tables must already be in this workspace (an
@@ -255,7 +257,7 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
   }
   p->nlaunch = 0;
   p->npairs = 0;
-  auto rec = [&](int i) { if (p->prof) record_event(p->ev[i], st); };
+  auto rec = [&](int i) { if (p->prof && !g_rec) record_event(p->ev[i], st); };
   rec(0);
   if (nt == 0) {
     rec(1); rec(2); rec(3);
