@@ -312,7 +312,12 @@ __device__ __forceinline__ double to_d(double v) { return v; }
 // ----------------------------------------------------------------------------
 constexpr int kFormThreads = 128;
 constexpr int kFormSub = 64;
-constexpr int kRB = 4;  // rhs per block
+constexpr int kRB = 4;  // rhs per block (FP64 path, Stokes kernels)
+// rhs per block: 8 for the FP32 scalar kernels (one plane wave serves all 8)
+template <typename T, int KER>
+constexpr int rb_of() {
+  return (sizeof(T) == 4 && (KER == PFMM_LAPLACE || KER == PFMM_MODHELM)) ? 8 : kRB;
+}
 
 template <typename T>
 struct FormArgs {
@@ -343,12 +348,13 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
   __shared__ T s_x[kFormSub], s_y[kFormSub];
   __shared__ T s_xw[kFormSub], s_yw[kFormSub];  // west/east frame coordinates
   __shared__ int s_U[kFormSub];
-  __shared__ T s_q[kRB][NC][kFormSub];
+  constexpr int RB = rb_of<T, KER>();
+  __shared__ T s_q[RB][NC][kFormSub];
 
   const int t = bid.y * kFormThreads + threadIdx.x;
   const bool active = t < f.nterm;
-  const int r0 = bid.z * kRB;
-  const int nr = min(kRB, f.nrhs - r0);
+  const int r0 = bid.z * RB;
+  const int nr = min(RB, f.nrhs - r0);
   int tpart, tmm;
   T a, b;
   double inv_d = 0.0;
@@ -370,9 +376,9 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
   const bool sn = tpart < 2;
   const bool we_m1 = !sn && (KER == PFMM_LAPLACE || KER == PFMM_STOKES);
 
-  double acc[kRB][NCH][2];
+  double acc[RB][NCH][2];
 #pragma unroll
-  for (int r = 0; r < kRB; ++r)
+  for (int r = 0; r < RB; ++r)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) acc[r][c][0] = acc[r][c][1] = 0.0;
 
@@ -389,15 +395,15 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
       s_yw[k] = T(g.ws) * x + T(g.wc) * y;
       s_U[k] = sU ? sU[jb + k] : 0;
     }
-    for (int k = threadIdx.x; k < kRB * NC * kFormSub; k += kFormThreads) {
+    for (int k = threadIdx.x; k < RB * NC * kFormSub; k += kFormThreads) {
       int r = k / (NC * kFormSub), rem = k % (NC * kFormSub), c = rem / kFormSub, jj = rem % kFormSub;
       s_q[r][c][jj] = (r < nr && jj < nb) ? qv[((size_t)(r0 + r) * NC + c) * ns + jb + jj] : T(0);
     }
     __syncthreads();
     if (!active) continue;
-    T sub[kRB][NCH][2];
+    T sub[RB][NCH][2];
 #pragma unroll
-    for (int r = 0; r < kRB; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int c = 0; c < NCH; ++c) sub[r][c][0] = sub[r][c][1] = T(0);
     for (int jj = 0; jj < nb; ++jj) {
@@ -405,25 +411,35 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
       const T x = sn ? s_x[jj] : s_xw[jj], y = sn ? s_y[jj] : s_yw[jj];
       T Rr, Ri, Qr, Qi;  // R (for c_b / plain) and Q (for c_a: R or R - 1)
       if (sn) {
-        T e = dm::ex(sgn * b * y);
-        T sp, cp;
-        if constexpr (sizeof(T) == 4)
-          dm::phase_fixed(tmm, s_U[jj], &sp, &cp);
-        else
+        T e, sp, cp;
+        if constexpr (sizeof(T) == 4) {
+          e = dm::ex_fast(sgn * b * y);
+          dm::sincos_turns((unsigned)tmm * (unsigned)s_U[jj], &sp, &cp);
+        } else {
+          e = dm::ex(sgn * b * y);
           dm::sincospi_(T(2.0 * tmm * ((double)x * inv_d)), &sp, &cp);
+        }
         Rr = e * cp;
         Ri = -e * sp;
         Qr = Rr;
         Qi = Ri;
       } else {
         if (we_m1) {
-          dm::expm1c(sgn * b * x, -a * y, &Qr, &Qi);
+          if constexpr (sizeof(T) == 4)
+            dm::expm1c_fast(sgn * b * x, -a * y, &Qr, &Qi);
+          else
+            dm::expm1c(sgn * b * x, -a * y, &Qr, &Qi);
           Rr = Qr + T(1);
           Ri = Qi;
         } else {
-          T e = dm::ex(sgn * b * x);
-          T sp, cp;
-          dm::sincos_(a * y, &sp, &cp);
+          T e, sp, cp;
+          if constexpr (sizeof(T) == 4) {
+            e = dm::ex_fast(sgn * b * x);
+            dm::sincos_red(a * y, &sp, &cp);
+          } else {
+            e = dm::ex(sgn * b * x);
+            dm::sincos_(a * y, &sp, &cp);
+          }
           Rr = e * cp;
           Ri = -e * sp;
           Qr = Rr;
@@ -431,7 +447,7 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
         }
       }
 #pragma unroll
-      for (int r = 0; r < kRB; ++r) {
+      for (int r = 0; r < RB; ++r) {
         if (NC == 1) {
           const T s = s_q[r][0][jj];
           sub[r][0][0] += Qr * s;
@@ -458,11 +474,11 @@ __device__ __forceinline__ void k_far_form_body(uint3 bid, const FormArgs<T>& A)
       }
     }
 #pragma unroll
-    for (int r = 0; r < kRB; ++r)
+    for (int r = 0; r < RB; ++r)
 #pragma unroll
       for (int c = 0; c < NCH; ++c) {
-        acc[r][c][0] += (double)sub[r][c][0];
-        acc[r][c][1] += (double)sub[r][c][1];
+        acc[r][c][0] += to_d(sub[r][c][0]);
+        acc[r][c][1] += to_d(sub[r][c][1]);
       }
   }
   if (!active) return;
@@ -625,7 +641,7 @@ struct EvalArgs {
 };
 
 template <typename T, typename T2, int KER>
-__device__ __forceinline__ void k_far_eval_body(uint3 bid, const EvalArgs<T, T2>& A) {
+__device__ __forceinline__ void k_far_eval_body64(uint3 bid, const EvalArgs<T, T2>& A) {
   const Far& f = A.f;
   const Geom& g = A.g;
   const int nt = A.nt, accum = A.accum;
@@ -772,16 +788,182 @@ __device__ __forceinline__ void k_far_eval_body(uint3 bid, const EvalArgs<T, T2>
   }
 }
 
-template <typename T, typename T2, int KER>
-__global__ void __launch_bounds__(kEvalThreads) k_far_eval(const __grid_constant__ EvalArgs<T, T2> A) {
-  k_far_eval_body<T, T2, KER>(blockIdx, A);
+// FP32 evaluation (mixed path).  Per (target, term): the plane wave from one
+// MUFU exponential and the FMA-pipe sine/cosine (the south/north phase from
+// the fixed-point coordinate, exact range reduction), then per rhs the real
+// part of L w; RB right-hand sides per block (8 for the scalar kernels, so
+// that each plane wave serves all of them), the gradient only when asked
+// for (GRAD).  Terms are summed in FP32 over groups of kEvalGroup and the
+// group sums added with Kahan compensation.  Term data are staged once per
+// chunk as (a, b, m, part) in shared memory.
+constexpr int kEvalGroup = 16;
+
+template <typename T2, int KER, bool GRAD>
+__device__ __forceinline__ void k_far_eval_body32(uint3 bid, const EvalArgs<float, T2>& A) {
+  using T = float;
+  const Far& f = A.f;
+  const Geom& g = A.g;
+  const int nt = A.nt, accum = A.accum;
+  const int64_t os = A.os;
+  constexpr bool VEC = KER == PFMM_STOKES || KER == PFMM_MSTOKES;
+  constexpr int NW = (KER == PFMM_STOKES) ? 4 : (KER == PFMM_MSTOKES ? 2 : 1);
+  constexpr int RB = rb_of<T, KER>();
+  // accumulators: scalar [pot, gx, gy] (gradient only with GRAD); Stokes [ux, uy]
+  constexpr int NA = VEC ? 2 : (GRAD ? 3 : 1);
+  __shared__ float4 s_t[kEvalChunk];  // a, b, m (int bits), part (int bits)
+  __shared__ T2 s_w[RB][NW][kEvalChunk];
+  const int l = bid.x * kEvalThreads + threadIdx.x;
+  const bool in = l < nt;
+  const int r0 = bid.y * RB;
+  const int nr = min(RB, f.nrhs - r0);
+  const T x = in ? A.tx[l] : T(0), y = in ? A.ty[l] : T(0);
+  const T wc = T(g.wc), ws = T(g.ws);
+  const T xw = wc * x - ws * y, yw = ws * x + wc * y;
+  const unsigned U = (in && A.tU) ? (unsigned)A.tU[l] : 0u;
+  dm::KSum<T> acc[RB][NA];
+  T sum[RB][NA];
+#pragma unroll
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int c = 0; c < NA; ++c) sum[r][c] = T(0);
+
+  for (int t0 = 0; t0 < f.nterm; t0 += kEvalChunk) {
+    const int nc = min(kEvalChunk, f.nterm - t0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nc; k += kEvalThreads) {
+      const TermF tm = decode_term_f(f, t0 + k);
+      s_t[k] = make_float4(tm.a, tm.b, __int_as_float(tm.m), __int_as_float(tm.part));
+    }
+    for (int k = threadIdx.x; k < RB * NW * kEvalChunk; k += kEvalThreads) {
+      const int r = k / (NW * kEvalChunk), rem = k % (NW * kEvalChunk), c = rem / kEvalChunk, tt = rem % kEvalChunk;
+      T2 v;
+      v.x = T(0);
+      v.y = T(0);
+      if (r < nr && tt < nc) v = A.wts[((size_t)(r0 + r) * NW + c) * f.nterm + t0 + tt];
+      s_w[r][c][tt] = v;
+    }
+    __syncthreads();
+    if (!in) continue;
+    for (int k = 0; k < nc; ++k) {
+      const float4 tm = s_t[k];
+      const int part = __float_as_int(tm.w);
+      const T a = tm.x, b = tm.y;
+      T Lr, Li, Mr, Mi;  // L and the potential factor (L - 1 for Laplace/Stokes W/E)
+      if (part < 2) {
+        const T e = dm::ex_fast(part == 0 ? -b * y : b * y);
+        T sp, cp;
+        dm::sincos_turns((unsigned)__float_as_int(tm.z) * U, &sp, &cp);
+        Lr = e * cp;
+        Li = e * sp;
+        Mr = Lr;
+        Mi = Li;
+      } else {
+        const T sx = part == 2 ? T(1) : T(-1);
+        if (KER == PFMM_LAPLACE || KER == PFMM_STOKES) {
+          // e^{-sx b xw + i a yw} - 1 without cancellation
+          const T em = expm1f(-sx * b * xw);
+          T sh, ch;
+          dm::sincos_red(T(0.5) * a * yw, &sh, &ch);
+          const T s2 = T(2) * sh * sh;
+          Mr = em * (T(1) - s2) - s2;
+          Mi = (em + T(1)) * (T(2) * sh * ch);
+          Lr = Mr + T(1);
+          Li = Mi;
+        } else {
+          const T e = dm::ex_fast(-sx * b * xw);
+          T sp, cp;
+          dm::sincos_red(a * yw, &sp, &cp);
+          Lr = e * cp;
+          Li = e * sp;
+          Mr = Lr;
+          Mi = Li;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r) {
+        if (KER == PFMM_MSTOKES) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const T2 w = s_w[r][c][k];
+            sum[r][c] = fmaf(Lr, w.x, fmaf(-Li, w.y, sum[r][c]));
+          }
+        } else if (KER != PFMM_STOKES) {
+          const T2 w = s_w[r][0][k];
+          sum[r][0] = fmaf(Mr, w.x, fmaf(-Mi, w.y, sum[r][0]));
+          if (GRAD) {
+            const T Pr = Lr * w.x - Li * w.y, Pi = Lr * w.y + Li * w.x;
+            if (part < 2) {
+              sum[r][1 % NA] = fmaf(-a, Pi, sum[r][1 % NA]);
+              sum[r][2 % NA] = fmaf(-(part == 0 ? b : -b), Pr, sum[r][2 % NA]);
+            } else {
+              const T gx = -(part == 2 ? b : -b) * Pr, gy = -a * Pi;  // in the west/east frame
+              sum[r][1 % NA] += wc * gx + ws * gy;
+              sum[r][2 % NA] += wc * gy - ws * gx;
+            }
+          }
+        } else {
+          const T cd = part < 2 ? y : xw;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const T2 wa = s_w[r][c][k], wb = s_w[r][2 + c][k];
+            sum[r][c] += (Mr * wa.x - Mi * wa.y) + cd * (Lr * wb.x - Li * wb.y);
+          }
+        }
+      }
+      if ((k & (kEvalGroup - 1)) == kEvalGroup - 1 || k == nc - 1) {
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+#pragma unroll
+          for (int c = 0; c < NA; ++c) {
+            acc[r][c].add(sum[r][c]);
+            sum[r][c] = T(0);
+          }
+      }
+    }
+  }
+  if (!in) return;
+  const double* R = g.rot;  // input = rot^T canonical
+  const double yd = dm::f2d(y);
+  for (int r = 0; r < nr; ++r) {
+    const double cc = A.mom[(r0 + r) * 8 + 4];
+    if (VEC) {
+      double ux = acc[r][0].value(), uy = acc[r][1 % NA].value();
+      if (cc != 0.0) ux += cc * yd;
+      double* px = A.pot + ((size_t)(r0 + r) * 2) * os + l;
+      double* py = A.pot + ((size_t)(r0 + r) * 2 + 1) * os + l;
+      *px = (accum ? *px : 0.0) + R[0] * ux + R[2] * uy;
+      *py = (accum ? *py : 0.0) + R[1] * ux + R[3] * uy;
+    } else {
+      double p = acc[r][0].value();
+      if (cc != 0.0) p += cc * yd;
+      if (A.pot) A.pot[(size_t)(r0 + r) * os + l] = p;
+      if (GRAD && A.grad) {
+        const double gx = acc[r][1 % NA].value(), gy = acc[r][2 % NA].value() + cc;
+        A.grad[((size_t)(r0 + r) * 2) * os + l] = R[0] * gx + R[2] * gy;
+        A.grad[((size_t)(r0 + r) * 2 + 1) * os + l] = R[1] * gx + R[3] * gy;
+      }
+    }
+  }
 }
-template <typename T, typename T2, int KER>
+
+template <typename T, typename T2, int KER, bool GRAD>
+__device__ __forceinline__ void k_far_eval_body(uint3 bid, const EvalArgs<T, T2>& A) {
+  if constexpr (sizeof(T) == 4)
+    k_far_eval_body32<T2, KER, GRAD>(bid, A);
+  else
+    k_far_eval_body64<T, T2, KER>(bid, A);
+}
+
+template <typename T, typename T2, int KER, bool GRAD>
+__global__ void __launch_bounds__(kEvalThreads) k_far_eval(const __grid_constant__ EvalArgs<T, T2> A) {
+  k_far_eval_body<T, T2, KER, GRAD>(blockIdx, A);
+}
+template <typename T, typename T2, int KER, bool GRAD>
 __global__ void __launch_bounds__(kEvalThreads) k_far_eval_multi(const EvalArgs<T, T2>* __restrict__ cells,
                                                                  const int* __restrict__ off,
                                                                  const uint3* __restrict__ dims, int n) {
   const SubBlock s = sub_block(off, dims, n);
-  k_far_eval_body<T, T2, KER>(s.bid, cells[s.cell]);
+  k_far_eval_body<T, T2, KER, GRAD>(s.bid, cells[s.cell]);
 }
 
 // memsets of 8-byte words (multi-cell zeroing)
@@ -878,7 +1060,7 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
   double* coef = (double*)(ws + L.coef) + (second ? (size_t)f.nrhs * p->far.nch * p->far.nterm * 2 : 0);
   double* mom = (double*)(ws + L.moments);
   const int ph = second ? PH_FORM2 : PH_FORM;
-  int nrg = cdiv_i(f.nrhs, kRB);
+  int nrg = cdiv_i(f.nrhs, rb_of<T, KER>());
   g_launches = (f.nterm > 0) ? 3 : 2;
   cudaError_t e;
   if (f.nterm > 0) {
@@ -916,9 +1098,15 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
   const T* ty = tx + nt;
   const int* tU = self ? sU : (const int*)(ws + L.trgU);
   {
-    const dim3 ge(cdiv_i(nt, kEvalThreads), nrg);
+    const dim3 ge(cdiv_i(nt, kEvalThreads), cdiv_i(f.nrhs, rb_of<T, KER>()));
     const EvalArgs<T, T2> a{f, g, (int)nt, tx, ty, tU, w, mom, p->o_stride, pot, grad, second ? 1 : 0};
-    e = launch_or_record(k_far_eval<T, T2, KER>, k_far_eval_multi<T, T2, KER>, ph + 2, ge, kEvalThreads, 0, st, a);
+    constexpr bool SC = KER == PFMM_LAPLACE || KER == PFMM_MODHELM;
+    if (SC && grad)
+      e = launch_or_record(k_far_eval<T, T2, KER, SC>, k_far_eval_multi<T, T2, KER, SC>, ph + 2, ge, kEvalThreads, 0,
+                           st, a);
+    else
+      e = launch_or_record(k_far_eval<T, T2, KER, false>, k_far_eval_multi<T, T2, KER, false>, ph + 2, ge,
+                           kEvalThreads, 0, st, a);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
