@@ -605,16 +605,30 @@ def run_adjoint(args, rank, world, local):
     torch.cuda.synchronize()
     op.status()
     ms, clocks = timed_region(step, args, dist, dev, local)
-    # the adjoint execute is the last one of a step: its P2P phase and launch count
+    # the adjoint execute is the last one of a step: its near-field phase (the
+    # direct P2P, or the tree code's leaf kernels and the pairs they sum) and
+    # launch count
     op.profile(True)
-    p2p, nl = [], []
+    p2p, nl, leaves, lpairs = [], [], [], []
     for _ in range(3):
         step()
-        p2p.append(op.phase_ms()[2])
+        ph = op.phase_ms(sub=True)
+        p2p.append(ph[2])
+        leaves.append(ph[7])
         nl.append(op.describe()["nlaunch"])
+        if op.describe()["near_fmm"]:
+            lpairs.append(op.pairs())
     op.profile(False)
     desc = op.describe()
     p2p_ms = statistics.median(p2p)
+    nimg = 3 * (2 * desc["m0"] + 1)
+    if desc["near_fmm"]:
+        roof = p2p_roofline("laplace_leaf", 1, True, statistics.median(lpairs), statistics.median(leaves), ms,
+                            f"k_fmm_p2p + k_fmm_l2p (tree-code leaves of the adjoint execute: direct sums of "
+                            f"neighbouring leaves and L2P, {nimg} images)", device_sms(dev), clocks, nimg=nimg)
+    else:
+        roof = p2p_roofline("laplace", 1, True, desc["npairs"], p2p_ms, ms,
+                            "k_p2p_mixed (near-image P2P of the adjoint execute)", device_sms(dev), clocks, nimg=nimg)
     # end to end: pinned host inputs -> device, forward + backward, gradients -> pinned host
     dq_h = torch.empty((1, n), dtype=torch.float64).pin_memory()
     dx_h = torch.empty((2, n), dtype=torch.float64).pin_memory()
@@ -649,8 +663,7 @@ def run_adjoint(args, rank, world, local):
             "config": {"workload": args.workload if args.scale == 1.0 else f"{args.workload}@scale{args.scale}",
                        "kernel": "laplace", "n": n, "step": "forward + backward (dE/dq, dE/dx)",
                        "l2": "flushed (256 MiB write) before each timed step", "parallelism": f"replicas{world}"},
-            "roofline": p2p_roofline("laplace", 1, True, desc["npairs"], p2p_ms, ms,
-                                     "k_p2p_mixed (near-image P2P of the adjoint execute)", device_sms(dev), clocks),
+            "roofline": roof,
             "cpu_baseline": cpu, "clocks": clocks,
             "e2e": {"value": job_value(world, 2 * n, e2e_s), "unit": "targets+sources/s",
                     "h2d_bytes_per_step": S_h.numel() * 8 + Q_h.numel() * 8,

@@ -1292,13 +1292,21 @@ cudaError_t run_expansions(const FmmArgs& a, int grid, cudaStream_t st, int* nl)
   return cudaGetLastError();
 }
 
+// Downward pass on st_tree, then the leaf kernels (which add into the
+// outputs) on st, after st_tree's work through `join` when the streams differ.
 template <int P, int KER>
-cudaError_t run_down(const FmmArgs& a, int grid, cudaStream_t st, int* nl, cudaEvent_t mid) {
-  cudaError_t e = cudaMemsetAsync(a.loc, 0, (size_t)a.exp_cap * a.nchan * P * sizeof(double2), st);
+cudaError_t run_down(const FmmArgs& a, int grid, cudaStream_t st_tree, int* nl, cudaEvent_t mid, cudaStream_t st,
+                     cudaEvent_t join) {
+  cudaError_t e = cudaMemsetAsync(a.loc, 0, (size_t)a.exp_cap * a.nchan * P * sizeof(double2), st_tree);
   if (e != cudaSuccess) return e;
-  k_fmm_m2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a);
-  for (int l = 1; l <= kFmmL; ++l) k_fmm_l2l<P, KER><<<grid, 32 * kDownWarps, 0, st>>>(a, l);
-  if (mid) record_event(mid, st);
+  k_fmm_m2l<P, KER><<<grid, 32 * kDownWarps, 0, st_tree>>>(a);
+  for (int l = 1; l <= kFmmL; ++l) k_fmm_l2l<P, KER><<<grid, 32 * kDownWarps, 0, st_tree>>>(a, l);
+  if (mid) record_event(mid, st_tree);
+  if (st_tree != st) {
+    e = cudaEventRecord(join, st_tree);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+    if (e != cudaSuccess) return e;
+  }
   k_fmm_l2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
   k_fmm_p2p<P, KER><<<grid, 32 * kLeafWarps, 0, st>>>(a);
   *nl += kFmmL + 3;
@@ -1406,7 +1414,9 @@ void fmm_setup(pfmm_plan* p) {
 }
 
 cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot, double* grad,
-                            cudaStream_t st) {
+                            cudaStream_t st_main, cudaStream_t st_tree, cudaEvent_t join) {
+  // every phase before the leaf kernels on `st` (= st_tree when given)
+  cudaStream_t st = (st_tree && join) ? st_tree : st_main;
   const FmmPlan& F = p->fmm;
   const Layout& L = p->lay;
   char* base = ws + L.fmm;
@@ -1538,11 +1548,11 @@ cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt
   nl += 2;
   rec(6);
   // 10-11 down, leaves
-  e = PFMM_FMM_P_DISPATCH(run_down, F.p, K, a, grid, st, &nl, p->prof ? p->ev[7] : nullptr);
+  e = PFMM_FMM_P_DISPATCH(run_down, F.p, K, a, grid, st, &nl, p->prof ? p->ev[7] : nullptr, st_main, join);
   if (e != cudaSuccess) return e;
   // 12 fallback (returns at once unless a capacity overflowed)
-  if (K == PFMM_LAPLACE) k_fmm_fallback<PFMM_LAPLACE><<<grid, kLeafThreads, 0, st>>>(a);
-  else k_fmm_fallback<PFMM_STOKES><<<grid, kLeafThreads, 0, st>>>(a);
+  if (K == PFMM_LAPLACE) k_fmm_fallback<PFMM_LAPLACE><<<grid, kLeafThreads, 0, st_main>>>(a);
+  else k_fmm_fallback<PFMM_STOKES><<<grid, kLeafThreads, 0, st_main>>>(a);
   ++nl;
   g_launches = nl;
   return cudaGetLastError();

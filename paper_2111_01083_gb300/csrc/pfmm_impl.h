@@ -182,6 +182,14 @@ struct pfmm_plan {
   bool prof;
   cudaEvent_t ev[pfmm::kPlanEvents];  // phase boundaries (0-3), tree-code sub-phases (4-7)
   bool near_fmm_ran;                  // the last execute ran the tree code
+  // tree-code executes: the tree phases (sort, build, upward pass, traversal,
+  // downward pass) run on a second stream beside the far field, which they
+  // do not touch; the leaf kernels, which add into the outputs, join back
+  // (created at the first execute outside stream capture)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  bool side_ready = false;
+  bool near_overlap = false;          // the last execute overlapped them
   int nlaunch;
   int64_t npairs;
 };
@@ -222,8 +230,10 @@ cudaError_t launch_far_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
 cudaError_t launch_p2p(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self,
                        double* pot, double* grad, bool accumulate, cudaStream_t st);
 // near field through the tree code (fmm.cu); adds to pot/grad like launch_p2p
+// Tree code: its tree phases on st_tree; the leaf kernels on st (after
+// st_tree's work, through `join`, when the two differ).
 cudaError_t launch_fmm_near(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,
-                            double* grad, cudaStream_t st);
+                            double* grad, cudaStream_t st, cudaStream_t st_tree = nullptr, cudaEvent_t join = nullptr);
 // sizes and offsets of the tree code's workspace region (p->fmm.bytes = 0 when it is off)
 void fmm_setup(pfmm_plan* p);
 // statistics of the last tree-code execute (see pfmm_near_stats); synchronises st

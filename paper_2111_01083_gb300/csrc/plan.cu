@@ -232,6 +232,26 @@ cudaError_t upload_tables(const pfmm_plan* p, char* ws, cudaStream_t st) {
 // One cell: clear accumulators, (optionally) upload tables, prep, far field,
 // (optionally) near-image P2P.  Arguments were validated by the caller, which
 // also set p->s_stride / t_stride / o_stride.
+// The tree code's second stream and its fork/join events, created at the
+// first execute outside stream capture (nothing is created while capturing;
+// a capture before any eager execute runs the phases in sequence).
+static bool side_setup(pfmm_plan* p, cudaStream_t st) {
+  if (p->side_ready) return true;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return false;
+  if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    cudaStreamDestroy(p->side);
+    p->side = nullptr;
+    p->fork_ev = nullptr;
+    return false;
+  }
+  p->side_ready = true;
+  return true;
+}
+
 pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, const double* q, int64_t nt,
                          const double* trg, double* pot, double* grad, cudaStream_t st, bool self, bool upload,
                          bool near) {
@@ -272,6 +292,13 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
   unsigned fl = p->opts.flags;
   bool do_far = !(fl & PFMM_NEAR_ONLY) && ns > 0;
   bool do_near = near && ns > 0;
+  // tree code beside the far field: fork its stream after the preparation
+  p->near_overlap = do_near && do_far && p->fmm.on && !g_rec && side_setup(p, st);
+  if (p->near_overlap) {
+    e = cudaEventRecord(p->fork_ev, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->side, p->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "fork");
+  }
   if (do_far) {
     e = (p->path == PFMM_PATH_NUFFT) ? launch_far_nufft(p, ws, ns, nt, self, pot, grad, st)
                                      : launch_far_direct(p, ws, ns, nt, self, pot, grad, st);
@@ -284,7 +311,8 @@ pfmm_status execute_cell(pfmm_plan* p, char* ws, int64_t ns, const double* src, 
   rec(2);
   p->near_fmm_ran = do_near && p->fmm.on;
   if (do_near) {
-    e = p->fmm.on ? launch_fmm_near(p, ws, ns, nt, self, pot, grad, st)
+    e = p->fmm.on ? (p->near_overlap ? launch_fmm_near(p, ws, ns, nt, self, pot, grad, st, p->side, p->join_ev)
+                                     : launch_fmm_near(p, ws, ns, nt, self, pot, grad, st))
                   : launch_p2p(p, ws, ns, nt, self, pot, grad, true, st);
     if (e != cudaSuccess) return cuda_fail(e, p->fmm.on ? "near-field tree code" : "p2p kernel");
     p->nlaunch += g_launches;
@@ -624,6 +652,11 @@ void pfmm_plan_destroy(pfmm_plan* p) {
   if (!p) return;
   if (p->prof)
     for (int i = 0; i < kPlanEvents; ++i) cudaEventDestroy(p->ev[i]);
+  if (p->side_ready) {
+    cudaStreamDestroy(p->side);
+    cudaEventDestroy(p->fork_ev);
+    cudaEventDestroy(p->join_ev);
+  }
   std::free(p->nodes_h);
   std::free(p->gl_h);
   std::free(p->phihat_h);
@@ -705,7 +738,9 @@ pfmm_status pfmm_profile_read(pfmm_plan* p, float* ms, int n) {
   }
   // tree-code sub-phases of the near field: tree, upward pass, traversal and
   // grouping, downward pass, leaves (events 2, 4, 5, 6, 7, 3)
-  static const int from[5] = {2, 4, 5, 6, 7}, to[5] = {4, 5, 6, 7, 3};
+  // (with the tree phases beside the far field, the tree starts after the
+  // preparation, event 1)
+  const int from[5] = {p->near_overlap ? 1 : 2, 4, 5, 6, 7}, to[5] = {4, 5, 6, 7, 3};
   for (int i = 3; i < n && i < 8; ++i) {
     ms[i] = 0.0f;
     if (!p->near_fmm_ran) continue;
