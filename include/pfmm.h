@@ -161,7 +161,7 @@ typedef struct {
                            PFMM_NEAR_FMM, PFMM_DETERMINISTIC (see the enum above) */
   int near_order;       /* tree-code expansion terms p (8..32, rounded up to 12, 16, 20,
                            24 or 32); 0 = from tol: theta^p <= tol / 10 */
-  int near_leaf;        /* tree code: a box with more points is split (8..1024); 0 = 48 */
+  int near_leaf;        /* tree code: a box with more points is split (8..1024); 0 = 128 */
 } pfmm_opts;
 
 /* Parameters chosen by a plan (read-only; for inspection and tests). */

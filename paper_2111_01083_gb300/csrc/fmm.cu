@@ -54,6 +54,8 @@
 #include <cstring>
 
 #include "pfmm_impl.h"
+#include "devmath.cuh"
+#include "packed.cuh"
 #include "sort.h"
 
 namespace pfmm {
@@ -962,28 +964,12 @@ __global__ void __launch_bounds__(32 * kDownWarps) k_fmm_l2l(FmmArgs a, int leve
 // 11: target leaves: L2P (one writer per target), then the direct sums of
 // neighbouring leaves over the flat grouped list (FP64 atomics).
 constexpr int kLeafWarps = 4;
-
-template <int KER>
-__device__ __forceinline__ void pair_sum(float txh, float txl, float tyh, float tyl, float4 s, float q0, float q1,
-                                         float& f0, float& f1, float& f2) {
-  const float dx = (txh - s.x) + (txl - s.y);
-  const float dy = (tyh - s.z) + (tyl - s.w);
-  const float r2 = dx * dx + dy * dy;
-  if (r2 > 0.f) {
-    const float lg = __log2f(r2);
-    const float inv = __fdividef(1.0f, r2);
-    if (KER == PFMM_LAPLACE) {
-      f0 += q0 * lg;
-      f1 += q0 * dx * inv;
-      f2 += q0 * dy * inv;
-    } else {
-      // -(1/4pi)[f log r - d (d.f)/r^2]; log r = (ln 2 / 2) log2 r^2
-      const float rf = (dx * q0 + dy * q1) * inv;
-      f0 += q0 * lg * 0.34657359f - dx * rf;
-      f1 += q1 * lg * 0.34657359f - dy * rf;
-    }
-  }
-}
+// output scalings (multiplications: an FP64 division costs tens of FP64
+// operations, and FP64 runs at 1/64 of the FP32 rate on this GPU)
+constexpr double kInv2Pi = 0.15915494309189535;   // 1 / (2 pi)
+constexpr double kInv4Pi = 0.079577471545947673;  // 1 / (4 pi)
+constexpr double kInv8Pi = 0.039788735772973836;  // 1 / (8 pi)
+constexpr double kLn2_4Pi = 0.055158900038162900; // ln 2 / (4 pi)
 
 // (h + l) - (oh + ol) as an unevaluated FP32 pair (two-sum of the high
 // parts, low parts added to its error): the image-shifted target coordinate
@@ -1005,7 +991,7 @@ struct KSumF {
     c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ double value() const { return dm::f2d(s) - dm::f2d(c); }
 };
 
 // L2P: one thread per target of a target leaf (block per leaf,
@@ -1024,6 +1010,8 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
     const int lo = a.lo[X], hi = a.hi[X];
     const double2 cX = a.ctr[X];
     const double RX = box_scale(a.rad[X], a.half[X]);
+    const double iRX = 1.0 / RX;
+    const float iRXf = (float)iRX;
     for (int r = 0; r < a.nrhs; ++r) {
       __syncthreads();
       if (tid < G * P) {
@@ -1037,7 +1025,7 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
         const double2 tq = a.xy[t];
         // FP32 Horner for sum_{l>=1} b_l u^l and its derivative (|u| <= 1,
         // decaying terms); the constant b_0 (the bulk of the potential) in FP64
-        const float2 u = make_float2((float)((tq.x - cX.x) / RX), (float)((tq.y - cX.y) / RX));
+        const float2 u = make_float2((float)((tq.x - cX.x) * iRX), (float)((tq.y - cX.y) * iRX));
         double2 F[4], D[4];
         for (int q = 0; q < G; ++q) {
           float2 f = s_b[q][P - 1], d = make_float2(0.f, 0.f);
@@ -1051,13 +1039,13 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
           }
           const float2 fu = cmulf(f, u);
           const float2 du = cmulf(d, u);
-          F[q] = make_double2(s_b0[q] + (double)fu.x, (double)fu.y);
-          D[q] = make_double2((double)(f.x + du.x) / RX, (double)(f.y + du.y) / RX);
+          F[q] = make_double2(s_b0[q] + dm::f2d(fu.x), dm::f2d(fu.y));
+          D[q] = make_double2(dm::f2d((f.x + du.x) * iRXf), dm::f2d((f.y + du.y) * iRXf));
         }
         const int o = a.perm[t];
         const double* R = a.rot;
         if (KER == PFMM_LAPLACE) {
-          const double o0 = -F[0].x / (2.0 * M_PI), o1 = -D[0].x / (2.0 * M_PI), o2 = D[0].y / (2.0 * M_PI);
+          const double o0 = -F[0].x * kInv2Pi, o1 = -D[0].x * kInv2Pi, o2 = D[0].y * kInv2Pi;
           if (a.pot) a.pot[(size_t)r * a.os + o] += o0;
           if (a.grad) {
             a.grad[((size_t)r * 2) * a.os + o] += R[0] * o1 + R[2] * o2;
@@ -1068,8 +1056,8 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
           // conj(u) C_1 - C_d
           const double2 wv = make_double2(du.x * D[2].x + du.y * D[2].y - D[3].x,
                                           du.x * D[2].y - du.y * D[2].x - D[3].y);
-          const double o0 = -F[0].x / (4.0 * M_PI) + wv.x / (8.0 * M_PI);
-          const double o1 = -F[1].x / (4.0 * M_PI) - wv.y / (8.0 * M_PI);
+          const double o0 = -F[0].x * kInv4Pi + wv.x * kInv8Pi;
+          const double o1 = -F[1].x * kInv4Pi - wv.y * kInv8Pi;
           a.pot[((size_t)r * 2) * a.os + o] += R[0] * o0 + R[2] * o1;
           a.pot[((size_t)r * 2 + 1) * a.os + o] += R[1] * o0 + R[3] * o1;
         }
@@ -1081,11 +1069,13 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
 // Direct sums of neighbouring leaves over the flat P2P list grouped by
 // target leaf: each warp takes kP2PChunk consecutive entries (so a leaf with
 // a long list is spread over many warps), lane l sums targets l and l + 32 of
-// the entry's target leaf (leaves with more targets take several passes),
-// sources staged in the warp's slice of shared memory.  Partial sums are
-// compensated FP32 and go to the outputs with FP64 atomics at each change of
+// the entry's target leaf as the two halves of packed FP32 operations
+// (leaves with more targets take several passes), sources staged 32 at a
+// time in the warp's slice of shared memory and read once per lane for both
+// targets.  Partial sums over each 32-source block are FP32, added with
+// compensation, and go to the outputs with FP64 atomics at each change of
 // target leaf and at the end of the chunk.
-constexpr int kP2PChunk = 4;
+constexpr int kP2PChunk = 8;
 
 template <int KER>
 __device__ __forceinline__ void p2p_flush(const FmmArgs& a, int X, int t0, int r, int lane, const KSumF (*acc)[3]) {
@@ -1095,21 +1085,32 @@ __device__ __forceinline__ void p2p_flush(const FmmArgs& a, int X, int t0, int r
   for (int k = 0; k < 2; ++k) {
     const int t = t0 + lane + 32 * k;
     if (t >= hi) continue;
-    const double n0 = acc[k][0].value(), n1 = acc[k][1].value(), n2 = acc[k][2].value();
     const int o = a.perm[t];
     if (KER == PFMM_LAPLACE) {
-      const double o0 = -n0 * (0.69314718055994531 / (4.0 * M_PI)), o1 = -n1 / (2.0 * M_PI), o2 = -n2 / (2.0 * M_PI);
+      const double o0 = -acc[k][0].value() * kLn2_4Pi;
+      const double o1 = -acc[k][1].value() * kInv2Pi, o2 = -acc[k][2].value() * kInv2Pi;
       if (a.pot) atomicAdd(a.pot + (size_t)r * a.os + o, o0);
       if (a.grad) {
         atomicAdd(a.grad + ((size_t)r * 2) * a.os + o, R[0] * o1 + R[2] * o2);
         atomicAdd(a.grad + ((size_t)r * 2 + 1) * a.os + o, R[1] * o1 + R[3] * o2);
       }
     } else {
-      const double o0 = -n0 / (4.0 * M_PI), o1 = -n1 / (4.0 * M_PI);
+      const double o0 = -acc[k][0].value() * kInv4Pi, o1 = -acc[k][1].value() * kInv4Pi;
       atomicAdd(a.pot + ((size_t)r * 2) * a.os + o, R[0] * o0 + R[2] * o1);
       atomicAdd(a.pot + ((size_t)r * 2 + 1) * a.os + o, R[1] * o0 + R[3] * o1);
     }
   }
+}
+
+__device__ __forceinline__ float lg2_mufu(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_mufu(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 template <int P, int KER>
@@ -1139,12 +1140,10 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_p2p(FmmArgs a) {
         const int lo = a.lo[X], hi = a.hi[X];
         for (int t0 = lo; t0 < hi; t0 += 64) {
           float4 thl[2];
-          bool tv[2];
 #pragma unroll
           for (int k = 0; k < 2; ++k) {
             const int t = t0 + lane + 32 * k;
-            tv[k] = t < hi;
-            thl[k] = tv[k] ? a.hl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            thl[k] = t < hi ? a.hl[t] : make_float4(0.f, 0.f, 0.f, 0.f);
           }
           KSumF acc[2][3];
           for (int j = e; j < ee; ++j) {
@@ -1153,12 +1152,12 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_p2p(FmmArgs a) {
             const int clo = a.lo[C], chi = a.hi[C];
             if (a.count_pairs && r == 0 && lane == 0)
               my_pairs += (unsigned long long)(min(hi, t0 + 64) - t0) * (unsigned long long)(chi - clo);
-            float th[2][4];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              shift_hl(thl[k].x, thl[k].y, a.offh[img][0], a.offl[img][0], th[k][0], th[k][1]);
-              shift_hl(thl[k].z, thl[k].w, a.offh[img][1], a.offl[img][1], th[k][2], th[k][3]);
-            }
+            // the two targets shifted by the image, packed: .x target t0 + lane, .y t0 + lane + 32
+            float2 txh, txl, tyh, tyl;
+            shift_hl(thl[0].x, thl[0].y, a.offh[img][0], a.offl[img][0], txh.x, txl.x);
+            shift_hl(thl[1].x, thl[1].y, a.offh[img][0], a.offl[img][0], txh.y, txl.y);
+            shift_hl(thl[0].z, thl[0].w, a.offh[img][1], a.offl[img][1], tyh.x, tyl.x);
+            shift_hl(thl[1].z, thl[1].w, a.offh[img][1], a.offl[img][1], tyh.y, tyl.y);
             for (int cs = clo; cs < chi; cs += 32) {
               __syncwarp();
               const int jj0 = cs + lane;
@@ -1168,16 +1167,41 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_p2p(FmmArgs a) {
               }
               __syncwarp();
               const int m = min(32, chi - cs);
-#pragma unroll
-              for (int k = 0; k < 2; ++k) {
-                if (!tv[k]) continue;
-                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-                for (int jj = 0; jj < m; ++jj)
-                  pair_sum<KER>(th[k][0], th[k][1], th[k][2], th[k][3], s_hl[wib][jj], s_q[wib][0][jj],
-                                KER == PFMM_STOKES ? s_q[wib][1][jj] : 0.f, f0, f1, f2);
-                acc[k][0].add(f0);
-                acc[k][1].add(f1);
-                acc[k][2].add(f2);
+              float2 f0 = f2(0.f), f1 = f2(0.f), f2v = f2(0.f);
+              for (int jj = 0; jj < m; ++jj) {
+                const float4 sp = s_hl[wib][jj];
+                const float2 dx = add2(add2(txh, f2(-sp.x)), add2(txl, f2(-sp.y)));
+                const float2 dy = add2(add2(tyh, f2(-sp.z)), add2(tyl, f2(-sp.w)));
+                float2 r2 = fma2(dx, dx, mul2(dy, dy));
+                // a zero distance (the target itself) contributes nothing
+                const float mx = r2.x > 0.f ? 1.f : 0.f, my = r2.y > 0.f ? 1.f : 0.f;
+                r2 = make_float2(r2.x > 0.f ? r2.x : 1.f, r2.y > 0.f ? r2.y : 1.f);
+                const float2 lg = make_float2(lg2_mufu(r2.x), lg2_mufu(r2.y));
+                const float2 inv = make_float2(rcp_mufu(r2.x), rcp_mufu(r2.y));
+                const float q0 = s_q[wib][0][jj];
+                const float2 qm = make_float2(q0 * mx, q0 * my);
+                if (KER == PFMM_LAPLACE) {
+                  f0 = fma2(qm, lg, f0);
+                  const float2 qi = mul2(qm, inv);
+                  f1 = fma2(qi, dx, f1);
+                  f2v = fma2(qi, dy, f2v);
+                } else {
+                  // -(1/4pi)[f log r - d (d.f)/r^2]; log r = (ln 2 / 2) log2 r^2
+                  const float q1 = s_q[wib][1][jj];
+                  const float2 q1m = make_float2(q1 * mx, q1 * my);
+                  const float2 rf = mul2(fma2(dx, qm, mul2(dy, q1m)), inv);
+                  const float2 lgh = mul2(lg, f2(0.34657359f));
+                  f0 = fma2(qm, lgh, fma2(make_float2(-dx.x, -dx.y), rf, f0));
+                  f1 = fma2(q1m, lgh, fma2(make_float2(-dy.x, -dy.y), rf, f1));
+                }
+              }
+              acc[0][0].add(f0.x);
+              acc[1][0].add(f0.y);
+              acc[0][1].add(f1.x);
+              acc[1][1].add(f1.y);
+              if (KER == PFMM_LAPLACE) {
+                acc[0][2].add(f2v.x);
+                acc[1][2].add(f2v.y);
               }
             }
           }
@@ -1245,12 +1269,12 @@ __global__ void __launch_bounds__(kLeafThreads) k_fmm_fallback(FmmArgs a) {
               }
             }
           if (KER == PFMM_LAPLACE) {
-            out0 += -(double)f0 * (0.69314718055994531 / (4.0 * M_PI));
-            out1 += -(double)f1 / (2.0 * M_PI);
-            out2 += -(double)f2 / (2.0 * M_PI);
+            out0 += -dm::f2d(f0) * kLn2_4Pi;
+            out1 += -dm::f2d(f1) * kInv2Pi;
+            out2 += -dm::f2d(f2) * kInv2Pi;
           } else {
-            out0 += -(double)f0 / (4.0 * M_PI);
-            out1 += -(double)f1 / (4.0 * M_PI);
+            out0 += -dm::f2d(f0) * kInv4Pi;
+            out1 += -dm::f2d(f1) * kInv4Pi;
           }
         }
       }
@@ -1347,7 +1371,7 @@ void fmm_setup(pfmm_plan* p) {
   // source box's charge: p from the requested tolerance
   int pp = o.near_order ? o.near_order : (int)std::ceil(std::log(o.tol * 0.1) / std::log(F.theta));
   F.p = round_p(std::max(8, std::min(kFmmMaxP, pp)));
-  F.nleaf = o.near_leaf ? o.near_leaf : 48;
+  F.nleaf = o.near_leaf ? o.near_leaf : 128;
   const Geom& g = p->geom;
   const double W = g.d + std::fabs(g.xi), H = g.eta;
   int ncol = (int)std::ceil(W / H - 1e-9);

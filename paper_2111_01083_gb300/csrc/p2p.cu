@@ -23,6 +23,7 @@
 #include "sort.h"
 #include "packed.cuh"
 #include "bessel.cuh"
+#include "devmath.cuh"
 
 namespace pfmm {
 
@@ -55,8 +56,18 @@ struct KahanF {
     c = (t - s) - y;
     s = t;
   }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ double value() const { return dm::f2d(s) - dm::f2d(c); }
 };
+
+// (h + l) - (oh + ol) as an unevaluated FP32 pair (sh, sl): two-sum of the
+// high parts, the low parts added to its error
+__device__ __forceinline__ void shift_two(float h, float l, float oh, float ol, float& sh, float& sl) {
+  const float sm = h - oh;
+  const float bb = sm - h;
+  const float err = (h - (sm - bb)) + (-oh - bb);
+  sh = sm;
+  sl = err + (l - ol);
+}
 
 // P2PArgs is declared in p2p.h
 
@@ -372,15 +383,26 @@ __device__ __forceinline__ void p2p_mixed_mh_body(const P2PArgs& a, int bx, int 
   const bool in = l < a.nt;
   const int nr = min(NR, a.nrhs - r0);
   {
-    const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
+    // the target's hi/lo split (read with targets = sources, else from FP64),
+    // shifted by each image offset (hi/lo) with an FP32 two-sum: no FP64
+    // arithmetic per image (FP64 runs at 1/64 of the FP32 rate here)
+    float4 t;
+    if (a.t_hl) {
+      t = in ? a.t_hl[l] : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      const double tx = in ? a.trg64[l] : 0.0, ty = in ? a.trg64[a.nt + l] : 0.0;
+      const float hx = (float)tx, hy = (float)ty;
+      t = make_float4(hx, (float)(tx - (double)hx), hy, (float)(ty - (double)hy));
+    }
 #pragma unroll
     for (int i = 0; i < NIMG; ++i) {
-      double vx = tx - a.g.off[i][0], vy = ty - a.g.off[i][1];
-      const float hx = (float)vx, hy = (float)vy;
-      s_tc[0][i][tid] = hx;
-      s_tc[1][i][tid] = (float)(vx - (double)hx);
-      s_tc[2][i][tid] = hy;
-      s_tc[3][i][tid] = (float)(vy - (double)hy);
+      float h, lo;
+      shift_two(t.x, t.y, a.offf[i][0], a.offl[i][0], h, lo);
+      s_tc[0][i][tid] = h;
+      s_tc[1][i][tid] = lo;
+      shift_two(t.z, t.w, a.offf[i][1], a.offl[i][1], h, lo);
+      s_tc[2][i][tid] = h;
+      s_tc[3][i][tid] = lo;
     }
   }
   KahanF K[NR][NA];
@@ -1084,10 +1106,12 @@ void fill_p2p_args(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool se
     a.t_box = self ? (const float4*)(ws + L.s_box) : (const float4*)(ws + L.t_box);
   }
   a.cut = (float)(p->mh_cut / std::max(p->far.beta, 1e-300));
-  for (int i = 0; i < p->geom.nimg; ++i) {
-    a.offf[i][0] = (float)p->geom.off[i][0];
-    a.offf[i][1] = (float)p->geom.off[i][1];
-  }
+  for (int i = 0; i < p->geom.nimg; ++i)
+    for (int k = 0; k < 2; ++k) {
+      a.offf[i][k] = (float)p->geom.off[i][k];
+      a.offl[i][k] = (float)(p->geom.off[i][k] - (double)a.offf[i][k]);
+    }
+  a.t_hl = (p->opts.precision == PFMM_MIXED && self) ? (const float4*)(ws + L.s_hl) : nullptr;
   a.src64 = (const double*)(ws + L.src64);
   a.qc = (const double*)(ws + L.qc);
   a.beta = p->far.beta;

@@ -28,7 +28,9 @@ struct P2PArgs {
   double beta;
   float lgc;             // log2(r^2) shift (Laplace/Stokes, FP64 add-back), see below
   float kimg[kMaxNear];  // per-image scale 2^-e_i of r^2 (exact powers of two)
-  float offf[kMaxNear][2];  // image offsets in FP32 (tile culling only)
+  float offf[kMaxNear][2];  // image offsets in FP32 (tile culling; the high parts of the hi/lo split)
+  float offl[kMaxNear][2];  // low parts: offset = offf + offl to ~2^-48 relative
+  const float4* t_hl;       // [nt] target (x_hi, x_lo, y_hi, y_lo) when targets = sources (mixed), else NULL
   const double* mom;     // FP64 moments: mom[r*8+0] = sum q (Stokes: sum f_x), [1] = sum f_y
   double* pot;
   double* grad;

@@ -285,7 +285,7 @@ def test_near_field_mode_selection(L):
     # small problems: direct unless forced
     assert _op().describe()["near_fmm"] == 0
     d = _op(near="fmm").describe()
-    assert d["near_fmm"] == 1 and d["near_theta"] == 0.5 and d["near_leaf"] == 48
+    assert d["near_fmm"] == 1 and d["near_theta"] == 0.5 and d["near_leaf"] == 128
     # expansion terms from the tolerance (theta^p <= tol / 10), rounded up to a compiled order
     assert _op(near="fmm", tol=1e-6).describe()["near_order"] == 24
     assert _op(near="fmm", tol=1e-2).describe()["near_order"] == 12
