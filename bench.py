@@ -465,6 +465,35 @@ def timed_region(step, args, dist, dev, local, after=None):
     return max_over_ranks(dist, sum(ts) / len(ts), dev), clocks
 
 
+def far_units(kernel, cells, beta, nrhs, tol=1e-6):
+    """Far-field work of a batch from each cell's plan (host only): the
+    (target, term) pairs of the direct evaluation and the (source, term) pairs
+    of the direct formation (the south/north terms of cells on the NUFFT path
+    go through the transforms instead), and the number of NUFFT cells."""
+    import ctypes
+    from paper_2111_01083_gb300 import _lib
+    from paper_2111_01083_gb300.periodic import _opts
+    L = _lib.lib()
+    ev = fo = nnu = 0
+    for c in cells:
+        n = int(c["src"].shape[1])
+        o = _opts(kernel, c["e1"], c["e2"], beta, tol, "mixed", "auto", 0, 0, nrhs, 0)
+        h = ctypes.c_void_p()
+        _lib.check(L.pfmm_plan_create(ctypes.byref(o), n, n, ctypes.byref(h)))
+        d = _lib.PlanDesc()
+        try:
+            _lib.check(L.pfmm_plan_describe(h, ctypes.byref(d)))
+        finally:
+            L.pfmm_plan_destroy(h)
+        nsn = (d.M - (0 if d.mode0 else 1) + 1) if d.M > 0 else 0
+        nufft = d.path == 2
+        nterm = 2 * d.Nq + (0 if nufft else 2 * nsn)
+        ev += n * nterm
+        fo += n * nterm
+        nnu += int(nufft)
+    return ev, fo, nnu
+
+
 def time_batch(beta, args, dist, dev, local, scale=1.0):
     """The batched modified-Helmholtz workload at one beta: 256 cells, 8 rhs,
     captured in one CUDA graph; each timed step is one graph.replay().  The
@@ -503,6 +532,22 @@ def time_batch(beta, args, dist, dev, local, scale=1.0):
     torch.cuda.synchronize()
     ns = int(sum(counts))
     sms = device_sms(dev)
+    # the periodizing operator's direct formation and evaluation work against
+    # the FP32 bound: per (point, term) 2 FMAs per rhs and ~6 FP32 operations
+    # for the plane wave; the time is that of all per-cell phases (preparation,
+    # formation, weights, evaluation, NUFFT stages), so the fraction is a lower
+    # bound for the two kernels
+    ev_u, fo_u, nnu = far_units("modhelm", cells, beta, 8)
+    mhz, _ = peak_clock_mhz(clocks)
+    fp32_per_unit = 2.0 * 8 + 6.0
+    far_peak = sms * alu_rates()["fp32"] / fp32_per_unit * mhz * 1e6
+    far = {"eval_units": ev_u, "form_units": fo_u, "nufft_cells": nnu, "per_cell_phases_ms": cell_ms,
+           "units_per_s": (ev_u + fo_u) / (cell_ms * 1e-3) if cell_ms > 0 else None,
+           "fp32_bound_units_per_s": far_peak,
+           "frac_of_fp32_bound": ((ev_u + fo_u) / (cell_ms * 1e-3) / far_peak) if cell_ms > 0 else None,
+           "basis": "units = (target, term) pairs of the direct evaluation + (source, term) pairs of the direct "
+                    "formation over all cells; 2 FMA per rhs (8 rhs) + 6 FP32 for the plane wave per unit; "
+                    "time = all per-cell phases"}
     rec = {"beta": beta, "ms_per_step": ms, "targets+sources/s": 2 * ns / (ms * 1e-3),
            "phases_ms": {"per_cell_prep_and_far_field": cell_ms, "batched_p2p": p2p_ms,
                          "measured": "CUDA events inside the replayed graph, mean over the timed replays"},
@@ -510,7 +555,7 @@ def time_batch(beta, args, dist, dev, local, scale=1.0):
            "roofline": p2p_roofline("modhelm", 8, False, evaluated, p2p_ms, ms,
                                     "k_p2p_batch (persistent batched near-image P2P, modified Helmholtz; "
                                     "pairs = those evaluated: triples beyond the K0 cutoff are skipped)", sms, clocks),
-           "clocks": clocks, "gpu_launches_per_step": nlaunch, "n_sources_total": ns}
+           "far_field": far, "clocks": clocks, "gpu_launches_per_step": nlaunch, "n_sources_total": ns}
     # the operator owns the graph's workspace and phase events: it must live as
     # long as the graph is replayed
     return rec, dict(S=S, Q=Q, S_h=S_h, Q_h=Q_h, graph=graph, out=out, ns=ns, counts=counts, op=op)
