@@ -28,7 +28,11 @@
  *    pointers and stages them through the workspace.
  *  - Everything is enqueued on the caller's CUDA stream (passed as void*,
  *    a cudaStream_t; NULL = legacy default stream).  Nothing synchronises
- *    except pfmm_get_status and pfmm_execute_host.
+ *    except pfmm_get_status and pfmm_execute_host.  A plan that uses the
+ *    near-field tree code creates one stream and two events (no device
+ *    memory) at its first execute outside stream capture; its tree phases run
+ *    there beside the far field, forked from and joined back into the
+ *    caller's stream (under capture: parallel branches of the graph).
  *  - Return value: PFMM_OK (0) or an error code; pfmm_last_error() gives a
  *    thread-local message.  Argument errors are detected on the host before
  *    anything is launched.  Conditions only visible on the device
