@@ -1036,7 +1036,7 @@ cudaError_t launch_prep(const pfmm_plan* p, char* ws, int64_t ns, const double* 
     k_ordered_sum<<<cdiv_i(4 * nrhs, 128), 128, 0, st>>>(part, qwarps, 4 * nrhs, 4, 8, mom);
     ++g_launches;
   }
-  return cudaGetLastError();
+  return launch_status();
 }
 
 // One pass of formation, weights and evaluation for the terms of `f`.  The
@@ -1109,7 +1109,7 @@ static cudaError_t run_far_direct(const pfmm_plan* p, Far f, bool second, char* 
                            kEvalThreads, 0, st, a);
     if (e != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return launch_status();
 }
 
 cudaError_t launch_far_direct(const pfmm_plan* p, char* ws, int64_t ns, int64_t nt, bool self, double* pot,

@@ -82,6 +82,11 @@ inline cudaError_t launch_or_record(void (*single)(const A), void (*multi)(const
   return cudaGetLastError();
 }
 
+// Status of the launches just issued; while recording nothing was launched
+// (and a sticky error of unrelated earlier work, or a host without a GPU,
+// must not fail the recording).
+inline cudaError_t launch_status() { return g_rec ? cudaSuccess : cudaGetLastError(); }
+
 // The block of a multi-cell launch: its cell (the last one whose first block
 // is at or before it; cells with no blocks are passed over) and its index in
 // that cell's grid.

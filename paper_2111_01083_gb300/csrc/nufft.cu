@@ -1017,7 +1017,7 @@ static cudaError_t run_nufft(const pfmm_plan* p, char* ws, int64_t ns, int64_t n
   }
   if (e != cudaSuccess) return e;
   g_launches += 5;
-  return cudaGetLastError();
+  return launch_status();
 }
 
 // Singly periodic west/east nodes [p1_nq0, Nq) through the transforms (see

@@ -343,3 +343,31 @@ def test_deterministic_plans(L):
     so = (ctypes.c_int64 * 2)(0, 10)
     h = ctypes.c_void_p()
     assert L.pfmm_batch_create(arr, 1, so, None, 0, ctypes.byref(h)) == 1
+
+
+def test_batch_create_is_host_only(L):
+    """pfmm_batch_create sizes the workspace, including the argument tables of
+    the multi-cell launches (a recording of every cell's launches with
+    placeholder addresses), without touching a GPU: mixed batches of all four
+    kernels, NUFFT and direct cells, self and separate targets."""
+    import numpy as np
+    import workloads
+    from paper_2111_01083_gb300 import BatchOp
+    cells = workloads.batch_cells(ncell=12, seed=3, nrhs=8, scale=0.05)
+    counts = [c["src"].shape[1] for c in cells]
+    sizes = {}
+    for kernel, beta, nrhs in (("modhelm", 1.0, 8), ("laplace", 0.0, 1), ("stokes", 0.0, 2), ("mstokes", 2.0, 1)):
+        op = BatchOp(kernel, [dict(e1=c["e1"], e2=c["e2"], beta=beta) for c in cells], counts, precision="mixed",
+                     nrhs=nrhs)
+        assert op.ws_bytes > 0 and op.ws_bytes % 256 == 0
+        sizes[kernel] = op.ws_bytes
+    # separate targets and a forced NUFFT cell
+    trg = [max(1, n // 2) for n in counts]
+    cl = [dict(e1=c["e1"], e2=c["e2"], beta=1.0) for c in cells]
+    cl[0]["path"] = "nufft"
+    op = BatchOp("modhelm", cl, counts, trg_counts=trg, precision="mixed", nrhs=8)
+    assert op.ws_bytes > 0
+    # more cells need more table space
+    op2 = BatchOp("modhelm", [dict(e1=c["e1"], e2=c["e2"], beta=1.0) for c in cells[:4]], counts[:4],
+                  precision="mixed", nrhs=8)
+    assert op2.ws_bytes < sizes["modhelm"]
