@@ -74,6 +74,7 @@ constexpr int kBoxMask = (1 << kImgShift) - 1;
 // control words
 constexpr int C_OVERFLOW = 0, C_NNODES = 1, C_NM2L = 2, C_NP2P = 3, C_NRS = 4, C_NRT = 5, C_FRONT = 8;
 constexpr int C_PAIRS = 48;  // uint64 at word 48 (8-byte aligned): directly evaluated pairs (profiling)
+constexpr int C_P2PNEXT = 40;  // next chunk of the leaf direct sums (dynamic schedule)
 
 struct BinomTable {
   double c[64][64];
@@ -1067,15 +1068,16 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_l2p(FmmArgs a) {
 }
 
 // Direct sums of neighbouring leaves over the flat P2P list grouped by
-// target leaf: each warp takes kP2PChunk consecutive entries (so a leaf with
-// a long list is spread over many warps), lane l sums targets l and l + 32 of
+// target leaf: each warp takes chunks of kP2PChunk consecutive entries from a
+// counter (so a leaf with a long list is spread over many warps, and the
+// uneven chunks balance dynamically), lane l sums targets l and l + 32 of
 // the entry's target leaf as the two halves of packed FP32 operations
 // (leaves with more targets take several passes), sources staged 32 at a
 // time in the warp's slice of shared memory and read once per lane for both
 // targets.  Partial sums over each 32-source block are FP32, added with
 // compensation, and go to the outputs with FP64 atomics at each change of
 // target leaf and at the end of the chunk.
-constexpr int kP2PChunk = 8;
+constexpr int kP2PChunk = 4;
 
 template <int KER>
 __device__ __forceinline__ void p2p_flush(const FmmArgs& a, int X, int t0, int r, int lane, const KSumF (*acc)[3]) {
@@ -1123,11 +1125,14 @@ __global__ void __launch_bounds__(32 * kLeafWarps) k_fmm_p2p(FmmArgs a) {
   const int ncomp = KER == PFMM_STOKES ? 2 : 1;
   const int64_t pb = a.gcnt[a.node_cap], pe = a.gcnt[2 * a.node_cap];  // the P2P part of the grouped list
   const int np = (int)(pe - pb);
-  const int nw = gridDim.x * kLeafWarps;
   if (threadIdx.x == 0) s_pairs = 0;
   __syncthreads();
   unsigned long long my_pairs = 0;
-  for (int c0e = (blockIdx.x * kLeafWarps + wib) * kP2PChunk; c0e < np; c0e += nw * kP2PChunk) {
+  for (;;) {
+    int ck = 0;
+    if (lane == 0) ck = atomicAdd(a.ctl + C_P2PNEXT, 1);
+    const int c0e = __shfl_sync(0xffffffffu, ck, 0) * kP2PChunk;
+    if (c0e >= np) break;
     const int c1e = min(np, c0e + kP2PChunk);
     for (int r = 0; r < a.nrhs; ++r) {
       // the chunk's entries, in order; a leaf with more than 64 targets is
