@@ -243,15 +243,18 @@ pfmm_status pfmm_execute_host(pfmm_plan* plan, void* workspace, size_t ws_bytes,
  * cell c are columns src_off[c] .. src_off[c+1]-1 of the concatenated arrays
  * src [2][NS], q [nrhs][NS] (Stokes [nrhs][2][NS]); targets likewise with
  * trg_off (NULL: targets = sources).  Outputs pot [nrhs][NT] (Stokes
- * [nrhs][2][NT]) and grad [nrhs][2][NT].  Per-cell prep and far field are
- * launched per cell; the near-image P2P of all cells runs as one persistent
- * kernel per near-block shape over a cost-sorted list of (cell, target block,
- * source range of p2p_chunk sources, rhs group) items (p2p_chunk 0 = 4096;
- * else a multiple of 128).  The first execute on a given set of buffers
- * uploads descriptors (cudaMemcpyAsync); later executes on the same buffers
- * issue only memsets and kernels and may be captured in a CUDA graph.  The
- * paper treats one cell at a time; batching is a library feature.
- * Errors as for the single-cell calls. */
+ * [nrhs][2][NT]) and grad [nrhs][2][NT].  On the mixed path the per-cell
+ * phases (preparation, far field) of all cells run as one launch per phase
+ * and kernel (the FP64 path launches them per cell); the near-image P2P of
+ * all cells runs as one persistent kernel per near-block shape over a
+ * cost-sorted list of (cell, target block, source range of p2p_chunk
+ * sources, rhs group) items (p2p_chunk 0 = 4096; else a multiple of 128).
+ * pfmm_batch_create is host-only: it sizes the workspace, including the
+ * per-cell argument tables of those launches.  The first execute on a given
+ * set of buffers uploads descriptors and tables (cudaMemcpyAsync); later
+ * executes on the same buffers issue only memsets and kernels and may be
+ * captured in a CUDA graph.  The paper treats one cell at a time; batching
+ * is a library feature.  Errors as for the single-cell calls. */
 typedef struct pfmm_batch pfmm_batch;
 pfmm_status pfmm_batch_create(const pfmm_opts* opts, int ncell, const int64_t* src_off,
                               const int64_t* trg_off, int p2p_chunk, pfmm_batch** out);
