@@ -481,7 +481,7 @@ def _time_graph(op, src, q, trg, reps, grad):
 
 
 def tune_batch(kernel, cells, src_counts, src, q, trg=None, trg_counts=None, precision="mixed", nrhs=1, tol=1e-6,
-               chunks=(1024, 2048, 4096, 8192), crossovers=(32, 64, 128, None), reps=3, grad=False, cache=None,
+               chunks=(1024, 2048, 4096, 8192, 16384), crossovers=(32, 64, 128, None), reps=3, grad=False, cache=None,
                key=None):
     """Tune a batch's execution choices by timing CUDA-graph replays:
 
